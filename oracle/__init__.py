@@ -1,0 +1,307 @@
+"""ORACLE — test infrastructure only.
+
+Plain FP64 CPU reference of the CIL hot path (arXiv 2203.14742), written
+from the paper.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg may import it; the product package
+never does, and it shares no code with the CUDA path.
+
+Thin ctypes wrappers over ``oracle/liboracle.so`` (plain C, built by
+``oracle/build.py``).  Every function takes and returns numpy arrays.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FHN, GM, DIFF = 0, 1, 2
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        dp, fp, i64p, i32p, u8p = (C.POINTER(C.c_double), C.POINTER(C.c_float),
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_uint8))
+        L.orc_sm64.argtypes = [C.c_uint64, C.c_uint64]
+        L.orc_sm64.restype = C.c_uint64
+        L.orc_equilibrium.argtypes = [C.c_int, dp, dp, dp]
+        L.orc_init_fields.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double,
+                                      C.c_double, C.c_uint64, fp]
+        L.orc_rhs.argtypes = [C.c_int, C.c_int, dp, dp, dp]
+        L.orc_step.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_int64, dp]
+        L.orc_residual.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp]
+        L.orc_jvp.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp]
+        L.orc_vjp.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp]
+        L.orc_pair_d2.argtypes = [fp, C.c_int64, fp, C.c_int64, C.c_int64, dp]
+        L.orc_radii.argtypes = [dp, C.c_int64, C.c_double, C.c_int, dp]
+        L.orc_radii.restype = C.c_double
+        L.orc_bins_counts.argtypes = [dp, C.c_int64, dp, C.c_int, u8p, i64p]
+        L.orc_bootstrap_indices.argtypes = [C.c_uint64, C.c_int, C.c_int64, C.c_int64, i32p, i32p]
+        L.orc_resample_counts.argtypes = [u8p, C.c_int64, C.c_int64, C.c_int, C.c_int,
+                                          i32p, i32p, i64p]
+        L.orc_stats.argtypes = [i64p, C.c_int, C.c_int, C.c_int64, dp, dp, dp, dp, dp, dp,
+                                dp, u8p, C.POINTER(C.c_int)]
+        L.orc_stats.restype = C.c_int
+        L.orc_smooth_cil.argtypes = [dp, C.c_int64, dp, C.c_int64, C.c_int64, dp, C.c_int,
+                                     C.c_double, dp, dp, dp, dp]
+        L.orc_smooth_cil_grad.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_int64,
+                                          dp, C.c_int, i32p, C.c_int64, i32p, C.c_int64, dp,
+                                          C.c_int, C.c_double, dp, dp, dp]
+        L.orc_smooth_cil_grad.restype = C.c_int
+        L.orc_smooth_cil_loss.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_int64,
+                                          dp, C.c_int, i32p, C.c_int64, i32p, C.c_int64, dp,
+                                          C.c_int, C.c_double, dp, dp]
+        L.orc_smooth_cil_loss.restype = C.c_double
+        _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _params(p):
+    p = np.zeros(4, np.float64) if p is None else np.asarray(p, np.float64)
+    out = np.zeros(4, np.float64)
+    out[:len(p)] = p
+    return out
+
+
+def sm64(seed, i):
+    """SplitMix64 output number i of stream `seed`."""
+    return lib().orc_sm64(seed & 0xFFFFFFFFFFFFFFFF, i)
+
+
+def equilibrium(model, p):
+    p = _params(p)
+    u0, v0 = C.c_double(), C.c_double()
+    lib().orc_equilibrium(model, _p(p, C.c_double), C.byref(u0), C.byref(v0))
+    return u0.value, v0.value
+
+
+def init_fields(model, G, n_real, p, lo, hi, seed):
+    """Initial state [n_real, 2, G, G] float32 (equilibrium + U(lo, hi))."""
+    p = _params(p)
+    out = np.empty((n_real, 2, G, G), np.float32)
+    lib().orc_init_fields(model, G, n_real, _p(p, C.c_double), lo, hi,
+                          C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), _p(out, C.c_float))
+    return out
+
+
+def rhs(model, p, w):
+    """F(w) for one realisation w[2, G, G] (float64)."""
+    p = _params(p)
+    w = _d(w)
+    G = w.shape[-1]
+    F = np.empty_like(w)
+    lib().orc_rhs(model, G, _p(p, C.c_double), _p(w, C.c_double), _p(F, C.c_double))
+    return F
+
+
+def step(model, p, dt, n_steps, w):
+    """Forward Euler on w[n_real, 2, G, G] (float64 copy returned)."""
+    p = _params(p)
+    w = np.array(w, dtype=np.float64, order="C", copy=True)
+    n_real, G = w.shape[0], w.shape[-1]
+    lib().orc_step(model, G, n_real, _p(p, C.c_double), float(dt), int(n_steps),
+                   _p(w, C.c_double))
+    return w
+
+
+def residual(model, p, w):
+    """[n_real, 2]: max |F| and RMS of F for each realisation."""
+    p = _params(p)
+    w = _d(w)
+    n_real, G = w.shape[0], w.shape[-1]
+    out = np.empty((n_real, 2), np.float64)
+    lib().orc_residual(model, G, n_real, _p(p, C.c_double), _p(w, C.c_double),
+                       _p(out, C.c_double))
+    return out
+
+
+def jvp(model, p, w, dw, dtheta):
+    p = _params(p)
+    w, dw = _d(w), _d(dw)
+    dtheta = _d(dtheta)
+    out = np.empty_like(w)
+    lib().orc_jvp(model, w.shape[-1], _p(p, C.c_double), _p(w, C.c_double),
+                  _p(dw, C.c_double), _p(dtheta, C.c_double), _p(out, C.c_double))
+    return out
+
+
+def vjp(model, p, w, lam):
+    p = _params(p)
+    w, lam = _d(w), _d(lam)
+    ow = np.empty_like(w)
+    ot = np.empty(4, np.float64)
+    lib().orc_vjp(model, w.shape[-1], _p(p, C.c_double), _p(w, C.c_double),
+                  _p(lam, C.c_double), _p(ow, C.c_double), _p(ot, C.c_double))
+    return ow, ot
+
+
+def patterns(fields, species_mask):
+    """Pattern vectors from fields[n, 2, G, G]: selected species, flattened."""
+    sel = [s for s in (0, 1) if species_mask & (1 << s)]
+    f = np.asarray(fields)
+    return np.ascontiguousarray(f[:, sel].reshape(f.shape[0], -1))
+
+
+def pair_d2(X1, X2):
+    """Canonical squared distances [n1, n2] of float32 patterns."""
+    X1 = np.ascontiguousarray(X1, np.float32)
+    X2 = np.ascontiguousarray(X2, np.float32)
+    n1, d = X1.shape
+    n2 = X2.shape[0]
+    out = np.empty((n1, n2), np.float64)
+    lib().orc_pair_d2(_p(X1, C.c_float), n1, _p(X2, C.c_float), n2, d, _p(out, C.c_double))
+    return out
+
+
+def radii(d2, b, M):
+    """(R0, radii[M]) with R0 = sqrt(max d2), R_k = R_{k-1}/b."""
+    d2 = _d(d2)
+    out = np.empty(M, np.float64)
+    R0 = lib().orc_radii(_p(d2, C.c_double), d2.size, float(b), M, _p(out, C.c_double))
+    return R0, out
+
+
+def bins_counts(d2, radii_):
+    d2 = _d(d2)
+    r = _d(radii_)
+    M = r.size
+    bins = np.empty(d2.shape, np.uint8)
+    counts = np.empty(M, np.int64)
+    lib().orc_bins_counts(_p(d2, C.c_double), d2.size, _p(r, C.c_double), M,
+                          _p(bins, C.c_uint8), _p(counts, C.c_int64))
+    return bins, counts
+
+
+def cil(X1, X2, b=None, M=None, radii_=None):
+    """Full CIL of two FP32 pattern sets.  Returns dict with d2, R0, radii,
+    bins, counts."""
+    d2 = pair_d2(X1, X2)
+    if radii_ is None:
+        R0, r = radii(d2, b, M)
+    else:
+        r = _d(radii_)
+        R0 = float("nan")
+    bins, counts = bins_counts(d2, r)
+    return {"d2": d2, "R0": R0, "radii": r, "bins": bins, "counts": counts}
+
+
+def bootstrap_indices(seed, T, n1, n2):
+    I = np.empty((T, n1), np.int32)
+    J = np.empty((T, n2), np.int32)
+    lib().orc_bootstrap_indices(C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), T, n1, n2,
+                                _p(I, C.c_int32), _p(J, C.c_int32))
+    return I, J
+
+
+def resample_counts(bins, M, I, J):
+    bins = np.ascontiguousarray(bins, np.uint8)
+    I = np.ascontiguousarray(I, np.int32)
+    J = np.ascontiguousarray(J, np.int32)
+    n1, n2 = bins.shape
+    T = I.shape[0]
+    Y = np.empty((T, M), np.int64)
+    lib().orc_resample_counts(_p(bins, C.c_uint8), n1, n2, M, T, _p(I, C.c_int32),
+                              _p(J, C.c_int32), _p(Y, C.c_int64))
+    return Y
+
+
+def stats(Y, n_pairs, y_obs=None):
+    Y = np.ascontiguousarray(Y, np.int64)
+    T, M = Y.shape
+    mu = np.empty(M)
+    cov = np.empty((M, M))
+    chol = np.empty((M, M))
+    logdet, f, ll = C.c_double(), C.c_double(), C.c_double()
+    active = np.empty(M, np.uint8)
+    ma = C.c_int()
+    yo = None if y_obs is None else _d(y_obs)
+    st = lib().orc_stats(_p(Y, C.c_int64), T, M, int(n_pairs),
+                         None if yo is None else _p(yo, C.c_double),
+                         _p(mu, C.c_double), _p(cov, C.c_double), _p(chol, C.c_double),
+                         C.byref(logdet), C.byref(f), C.byref(ll), _p(active, C.c_uint8),
+                         C.byref(ma))
+    return {"status": st, "mu": mu, "cov": cov, "chol": chol, "logdet": logdet.value,
+            "f": f.value, "loglik": ll.value, "active": active, "m_active": ma.value}
+
+
+def synlik(bins, M, T, seed, y_obs=None):
+    """Bootstrap counts + statistics (Alg. 5 steps 2-3)."""
+    n1, n2 = bins.shape
+    I, J = bootstrap_indices(seed, T, n1, n2)
+    Y = resample_counts(bins, M, I, J)
+    out = stats(Y, n1 * n2, y_obs)
+    out["Y"] = Y
+    return out
+
+
+def smooth_cil(X1, X2, radii_, tau_frac, cot, grad=True):
+    X1, X2 = _d(X1), _d(X2)
+    n1, d = X1.shape
+    n2 = X2.shape[0]
+    r = _d(radii_)
+    c = _d(cot)
+    M = r.size
+    Cv = np.empty(M)
+    g1 = np.empty_like(X1) if grad else None
+    g2 = np.empty_like(X2) if grad else None
+    lib().orc_smooth_cil(_p(X1, C.c_double), n1, _p(X2, C.c_double), n2, d, _p(r, C.c_double),
+                         M, float(tau_frac), _p(c, C.c_double), _p(Cv, C.c_double),
+                         None if g1 is None else _p(g1, C.c_double),
+                         None if g2 is None else _p(g2, C.c_double))
+    return Cv, g1, g2
+
+
+def smooth_cil_grad(model, p, dt, n_steps, w0, species_mask, set1, set2, radii_,
+                    tau_frac, cot):
+    """(C[M], grad[4]) of loss = cot . C_tau by the FP64 discrete adjoint."""
+    p = _params(p)
+    w0 = _d(w0)
+    n_real, G = w0.shape[0], w0.shape[-1]
+    s1 = np.ascontiguousarray(set1, np.int32)
+    s2 = np.ascontiguousarray(set2, np.int32)
+    r = _d(radii_)
+    c = _d(cot)
+    M = r.size
+    Cv = np.empty(M)
+    g = np.empty(4)
+    rc = lib().orc_smooth_cil_grad(model, G, n_real, _p(p, C.c_double), float(dt), int(n_steps),
+                                   _p(w0, C.c_double), int(species_mask), _p(s1, C.c_int32),
+                                   s1.size, _p(s2, C.c_int32), s2.size, _p(r, C.c_double), M,
+                                   float(tau_frac), _p(c, C.c_double), _p(Cv, C.c_double),
+                                   _p(g, C.c_double))
+    if rc:
+        raise MemoryError("oracle adjoint: allocation failed")
+    return Cv, g
+
+
+def smooth_cil_loss(model, p, dt, n_steps, w0, species_mask, set1, set2, radii_,
+                    tau_frac, cot):
+    p = _params(p)
+    w0 = _d(w0)
+    n_real, G = w0.shape[0], w0.shape[-1]
+    s1 = np.ascontiguousarray(set1, np.int32)
+    s2 = np.ascontiguousarray(set2, np.int32)
+    r = _d(radii_)
+    c = _d(cot)
+    M = r.size
+    Cv = np.empty(M)
+    L = lib().orc_smooth_cil_loss(model, G, n_real, _p(p, C.c_double), float(dt), int(n_steps),
+                                  _p(w0, C.c_double), int(species_mask), _p(s1, C.c_int32),
+                                  s1.size, _p(s2, C.c_int32), s2.size, _p(r, C.c_double), M,
+                                  float(tau_frac), _p(c, C.c_double), _p(Cv, C.c_double))
+    return L, Cv

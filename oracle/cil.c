@@ -1,0 +1,360 @@
+/*
+ * ORACLE — test infrastructure only.  Plain, slow FP64 reference for the
+ * correlation-integral part of the CIL hot path.  Only tests/, the smoke
+ * check and the benchmark's CPU-baseline leg may load it.  It shares no code
+ * with the CUDA path.  Compiled with -O2 -ffp-contract=off.
+ *
+ * Paper: arXiv 2203.14742.
+ *   Correlation sum C(R, s, s~) with strict '<', eq. (eCDF), Sec. 2.1;
+ *   CIL vector y_m = C(R_m, s^k, s^l), eq. (CIL); power-law radii
+ *   R_m = R0 * b^-m with R0 the largest distance, Sec. 2.1 and Sec. 3.2;
+ *   mean / covariance of y over set pairs, Alg. 1 step 3;
+ *   bootstrap resampling with replacement of each half, Alg. 5 (appendix A)
+ *   and Alg. 6; cost f = (y - mu)^T Sigma^-1 (y - mu), eq. (cil:CF) and
+ *   eq. (cil:CF_synth).
+ *
+ * Readings of points the paper leaves open (each stated where used):
+ *   - distance = plain Euclidean norm of the difference vector, evaluated as
+ *     d^2 = sum_t (double(x_t) - double(y_t))^2 summed sequentially in t;
+ *   - R_k = R_{k-1} / b in FP64 (k = 1..M), thresholds T_k = R_k * R_k, and
+ *     "d < R_k" is decided as d^2 < T_k;
+ *   - covariance normaliser 1/(T-1);
+ *   - components whose count is identical across all resamples are
+ *     inactive; the Gaussian statistics use the active block only.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#include "sm64.h"
+
+int orc_adjoint_one(int model, int G, const double *p, double dt,
+                    int64_t n_steps, const double *w0, double *lam,
+                    double *grad);
+void orc_step(int model, int G, int n_real, const double *p, double dt,
+              int64_t n_steps, double *w);
+
+/* Squared distance of two FP32 patterns, sequential FP64 sum (eq. eCDF). */
+static double d2_f32(const float *x, const float *y, int64_t d)
+{
+    double acc = 0.0;
+    for (int64_t t = 0; t < d; ++t) {
+        double df = (double)x[t] - (double)y[t];
+        double sq = df * df;
+        acc = acc + sq;
+    }
+    return acc;
+}
+
+static double d2_f64(const double *x, const double *y, int64_t d)
+{
+    double acc = 0.0;
+    for (int64_t t = 0; t < d; ++t) {
+        double df = x[t] - y[t];
+        double sq = df * df;
+        acc = acc + sq;
+    }
+    return acc;
+}
+
+/* All cross-set squared distances: d2[i*n2 + j] = ||X1_i - X2_j||^2. */
+void orc_pair_d2(const float *X1, int64_t n1, const float *X2, int64_t n2,
+                 int64_t d, double *d2)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n1; ++i)
+        for (int64_t j = 0; j < n2; ++j)
+            d2[i * n2 + j] = d2_f32(X1 + i * d, X2 + j * d, d);
+}
+
+/* Radii (Sec. 2.1): R0 = sqrt(max d^2) over the given pairs,
+   R_k = R_{k-1} / b for k = 1..M.  radii[0..M-1] = R_1..R_M.  Returns R0. */
+double orc_radii(const double *d2, int64_t n_pairs, double b, int M, double *radii)
+{
+    double mx = 0.0;
+    for (int64_t k = 0; k < n_pairs; ++k)
+        if (d2[k] > mx) mx = d2[k];
+    double R = sqrt(mx);
+    double R0 = R;
+    for (int k = 0; k < M; ++k) {
+        R = R / b;
+        radii[k] = R;
+    }
+    return R0;
+}
+
+/* Bin index K_ij = #{k in 1..M : d_ij < R_k} (strict, eq. eCDF), and
+   counts[k-1] = #{(i,j) : K_ij >= k} = N1*N2 * C(R_k). */
+void orc_bins_counts(const double *d2, int64_t n_pairs, const double *radii,
+                     int M, uint8_t *bins, int64_t *counts)
+{
+    for (int k = 0; k < M; ++k) counts[k] = 0;
+    for (int64_t q = 0; q < n_pairs; ++q) {
+        int K = 0;
+        for (int k = 0; k < M; ++k) {
+            double T = radii[k] * radii[k];
+            if (d2[q] < T) K = K + 1;
+        }
+        bins[q] = (uint8_t)K;
+        for (int k = 0; k < K; ++k) counts[k] += 1;
+    }
+}
+
+/* Bootstrap indices (Alg. 5 step 2.1): resample t draws n1 indices into
+   set 1 and n2 into set 2, with replacement.  Index a of side s in resample
+   t is SplitMix64 output number ((t*2 + s) << 32 | a) of stream `seed`,
+   mapped to [0, n) by Lemire's multiply-shift. */
+void orc_bootstrap_indices(uint64_t seed, int T, int64_t n1, int64_t n2,
+                           int32_t *I, int32_t *J)
+{
+    for (int t = 0; t < T; ++t) {
+        for (int64_t a = 0; a < n1; ++a) {
+            uint64_t ctr = (((uint64_t)t * 2u + 0u) << 32) | (uint64_t)a;
+            I[(int64_t)t * n1 + a] = (int32_t)orc_index(seed, ctr, (uint32_t)n1);
+        }
+        for (int64_t b = 0; b < n2; ++b) {
+            uint64_t ctr = (((uint64_t)t * 2u + 1u) << 32) | (uint64_t)b;
+            J[(int64_t)t * n2 + b] = (int32_t)orc_index(seed, ctr, (uint32_t)n2);
+        }
+    }
+}
+
+/* Correlation counts of resampled set pairs: for each resample t,
+   Y[t][k-1] = sum_a sum_b [K_{I_a, J_b} >= k]  (the numerator of eq. eCDF
+   for the resampled sets s^1 = X1[I], s^2 = X2[J]). */
+void orc_resample_counts(const uint8_t *bins, int64_t n1, int64_t n2, int M,
+                         int T, const int32_t *I, const int32_t *J, int64_t *Y)
+{
+    for (int t = 0; t < T; ++t) {
+        int64_t *y = Y + (int64_t)t * M;
+        for (int k = 0; k < M; ++k) y[k] = 0;
+        for (int64_t a = 0; a < n1; ++a)
+            for (int64_t b = 0; b < n2; ++b) {
+                int K = bins[(int64_t)I[(int64_t)t * n1 + a] * n2 + J[(int64_t)t * n2 + b]];
+                for (int k = 0; k < K; ++k) y[k] += 1;
+            }
+    }
+}
+
+/* Synthetic-likelihood statistics (Alg. 1 step 3, eq. cil:CF, eq.
+   cil:CF_synth).  y_t = Y_t / (n1*n2).  mu = mean over t; Sigma = sample
+   covariance with 1/(T-1); active[k] = 1 unless all Y[t][k] are equal;
+   L = lower Cholesky factor of the active block (Cholesky-Banachiewicz);
+   logdet = 2*sum log L_ii; f = || L^-1 (y_obs - mu)_act ||^2;
+   loglik = -(f + logdet + M_act*log(2*pi))/2.
+   cov and chol are M x M; chol holds the factor of the active block packed
+   into its leading M_act x M_act corner.  Returns 0, or 3 when the active
+   block is not positive definite. */
+int orc_stats(const int64_t *Y, int T, int M, int64_t n_pairs,
+              const double *y_obs, double *mu, double *cov, double *chol,
+              double *logdet, double *f, double *loglik, uint8_t *active,
+              int *m_act_out)
+{
+    double *y = (double *)malloc(sizeof(double) * (size_t)T * (size_t)M);
+    for (int64_t q = 0; q < (int64_t)T * M; ++q) y[q] = (double)Y[q] / (double)n_pairs;
+    for (int k = 0; k < M; ++k) {
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) s = s + y[(int64_t)t * M + k];
+        mu[k] = s / (double)T;
+        int same = 1;
+        for (int t = 1; t < T; ++t)
+            if (Y[(int64_t)t * M + k] != Y[k]) same = 0;
+        active[k] = (uint8_t)(same ? 0 : 1);
+    }
+    for (int k = 0; k < M; ++k)
+        for (int l = 0; l < M; ++l) {
+            double s = 0.0;
+            for (int t = 0; t < T; ++t) {
+                double a = y[(int64_t)t * M + k] - mu[k];
+                double b = y[(int64_t)t * M + l] - mu[l];
+                s = s + a * b;
+            }
+            cov[k * M + l] = s / (double)(T - 1);
+        }
+    int idx[256];
+    int ma = 0;
+    for (int k = 0; k < M; ++k)
+        if (active[k]) idx[ma++] = k;
+    *m_act_out = ma;
+    for (int q = 0; q < M * M; ++q) chol[q] = 0.0;
+    int status = 0;
+    for (int i = 0; i < ma && status == 0; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = cov[idx[i] * M + idx[j]];
+            for (int k = 0; k < j; ++k) s = s - chol[i * M + k] * chol[j * M + k];
+            if (i == j) {
+                if (!(s > 0.0)) { status = 3; break; }
+                chol[i * M + i] = sqrt(s);
+            } else {
+                chol[i * M + j] = s / chol[j * M + j];
+            }
+        }
+    }
+    double ld = 0.0;
+    if (status == 0)
+        for (int i = 0; i < ma; ++i) ld = ld + log(chol[i * M + i]);
+    *logdet = status == 0 ? 2.0 * ld : NAN;
+    if (y_obs && status == 0) {
+        double z[256];
+        double ff = 0.0;
+        for (int i = 0; i < ma; ++i) {
+            double s = y_obs[idx[i]] - mu[idx[i]];
+            for (int k = 0; k < i; ++k) s = s - chol[i * M + k] * z[k];
+            z[i] = s / chol[i * M + i];
+            ff = ff + z[i] * z[i];
+        }
+        *f = ff;
+        *loglik = -0.5 * (ff + *logdet + (double)ma * log(2.0 * 3.14159265358979323846));
+    } else {
+        *f = NAN;
+        *loglik = NAN;
+    }
+    free(y);
+    return status;
+}
+
+/* ---------------------------------------------------------------------
+ * Smoothed correlation integral (the paper has no gradient; this is the
+ * differentiable surrogate whose gradient informs proposals):
+ *   C_k = (1/(n1 n2)) sum_ij sigma((R_k - d_ij)/tau_k),  tau_k = tau_frac*R_k,
+ *   sigma(z) = 1/(1+exp(-z)),  d_ij = sqrt(d^2_ij) (sequential FP64 sum).
+ * loss = sum_k cot_k C_k.  gX1/gX2 = d loss / d patterns (may be NULL).
+ * --------------------------------------------------------------------- */
+void orc_smooth_cil(const double *X1, int64_t n1, const double *X2, int64_t n2,
+                    int64_t d, const double *radii, int M, double tau_frac,
+                    const double *cot, double *C, double *gX1, double *gX2)
+{
+    for (int k = 0; k < M; ++k) C[k] = 0.0;
+    if (gX1) memset(gX1, 0, sizeof(double) * (size_t)(n1 * d));
+    if (gX2) memset(gX2, 0, sizeof(double) * (size_t)(n2 * d));
+    double inv = 1.0 / ((double)n1 * (double)n2);
+    for (int64_t i = 0; i < n1; ++i)
+        for (int64_t j = 0; j < n2; ++j) {
+            const double *x = X1 + i * d, *y = X2 + j * d;
+            double dd = sqrt(d2_f64(x, y, d));
+            double wsum = 0.0; /* d loss / d d_ij */
+            for (int k = 0; k < M; ++k) {
+                double tau = tau_frac * radii[k];
+                double z = (radii[k] - dd) / tau;
+                double s = 1.0 / (1.0 + exp(-z));
+                C[k] = C[k] + s * inv;
+                /* d sigma / d d = -sigma(1-sigma)/tau */
+                wsum = wsum + cot[k] * (-(s * (1.0 - s)) / tau) * inv;
+            }
+            if ((gX1 || gX2) && dd > 0.0) {
+                double c = wsum / dd; /* d d / d x = (x - y)/d */
+                for (int64_t t = 0; t < d; ++t) {
+                    double g = c * (x[t] - y[t]);
+                    if (gX1) gX1[i * d + t] += g;
+                    if (gX2) gX2[j * d + t] -= g;
+                }
+            }
+        }
+}
+
+/* Gradient of loss = sum_k cot_k C_k(patterns(w_N(theta))) with respect to
+   theta[4], by the FP64 discrete adjoint.  w0: initial states of n_real
+   realisations [n_real][2][G][G] (held fixed); set1/set2: realisation
+   indices of the two pattern sets; species_mask: bit0 = u, bit1 = v (the
+   pattern is the concatenation of the selected species fields).
+   Radii are held fixed.  C_out[M] receives the forward value. */
+int orc_smooth_cil_grad(int model, int G, int n_real, const double *p,
+                        double dt, int64_t n_steps, const double *w0,
+                        int species_mask, const int32_t *set1, int64_t n1,
+                        const int32_t *set2, int64_t n2, const double *radii,
+                        int M, double tau_frac, const double *cot,
+                        double *C_out, double *grad)
+{
+    int64_t cells = (int64_t)G * G, m = 2 * cells;
+    int nsp = ((species_mask & 1) ? 1 : 0) + ((species_mask & 2) ? 1 : 0);
+    int64_t d = nsp * cells;
+    double *W = (double *)malloc(sizeof(double) * (size_t)(m * n_real));
+    memcpy(W, w0, sizeof(double) * (size_t)(m * n_real));
+    orc_step(model, G, n_real, p, dt, n_steps, W);
+    double *X1 = (double *)malloc(sizeof(double) * (size_t)(n1 * d));
+    double *X2 = (double *)malloc(sizeof(double) * (size_t)(n2 * d));
+    double *g1 = (double *)malloc(sizeof(double) * (size_t)(n1 * d));
+    double *g2 = (double *)malloc(sizeof(double) * (size_t)(n2 * d));
+    for (int pass = 0; pass < 2; ++pass) {
+        const int32_t *set = pass ? set2 : set1;
+        int64_t n = pass ? n2 : n1;
+        double *X = pass ? X2 : X1;
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t o = 0;
+            for (int s = 0; s < 2; ++s)
+                if (species_mask & (1 << s)) {
+                    memcpy(X + i * d + o, W + (int64_t)set[i] * m + s * cells, sizeof(double) * (size_t)cells);
+                    o += cells;
+                }
+        }
+    }
+    orc_smooth_cil(X1, n1, X2, n2, d, radii, M, tau_frac, cot, C_out, g1, g2);
+    /* lambda_N per realisation: scatter pattern gradients into the state. */
+    double *lam = (double *)calloc((size_t)(m * n_real), sizeof(double));
+    for (int pass = 0; pass < 2; ++pass) {
+        const int32_t *set = pass ? set2 : set1;
+        int64_t n = pass ? n2 : n1;
+        double *g = pass ? g2 : g1;
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t o = 0;
+            for (int s = 0; s < 2; ++s)
+                if (species_mask & (1 << s)) {
+                    double *dst = lam + (int64_t)set[i] * m + s * cells;
+                    for (int64_t c = 0; c < cells; ++c) dst[c] += g[i * d + o + c];
+                    o += cells;
+                }
+        }
+    }
+    for (int i = 0; i < 4; ++i) grad[i] = 0.0;
+    int rc = 0;
+    double *gr = (double *)calloc((size_t)(4 * n_real), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < n_real; ++r) {
+        int nz = 0;
+        for (int64_t k = 0; k < m; ++k)
+            if (lam[(int64_t)r * m + k] != 0.0) { nz = 1; break; }
+        if (!nz) continue;
+        if (orc_adjoint_one(model, G, p, dt, n_steps, w0 + (int64_t)r * m,
+                            lam + (int64_t)r * m, gr + 4 * r))
+            rc = 1;
+    }
+    for (int r = 0; r < n_real; ++r)
+        for (int i = 0; i < 4; ++i) grad[i] = grad[i] + gr[4 * r + i];
+    free(gr); free(lam); free(W); free(X1); free(X2); free(g1); free(g2);
+    return rc;
+}
+
+/* Loss value only (for finite differences). */
+double orc_smooth_cil_loss(int model, int G, int n_real, const double *p,
+                           double dt, int64_t n_steps, const double *w0,
+                           int species_mask, const int32_t *set1, int64_t n1,
+                           const int32_t *set2, int64_t n2, const double *radii,
+                           int M, double tau_frac, const double *cot, double *C_out)
+{
+    int64_t cells = (int64_t)G * G, m = 2 * cells;
+    int nsp = ((species_mask & 1) ? 1 : 0) + ((species_mask & 2) ? 1 : 0);
+    int64_t d = nsp * cells;
+    double *W = (double *)malloc(sizeof(double) * (size_t)(m * n_real));
+    memcpy(W, w0, sizeof(double) * (size_t)(m * n_real));
+    orc_step(model, G, n_real, p, dt, n_steps, W);
+    double *X1 = (double *)malloc(sizeof(double) * (size_t)(n1 * d));
+    double *X2 = (double *)malloc(sizeof(double) * (size_t)(n2 * d));
+    for (int pass = 0; pass < 2; ++pass) {
+        const int32_t *set = pass ? set2 : set1;
+        int64_t n = pass ? n2 : n1;
+        double *X = pass ? X2 : X1;
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t o = 0;
+            for (int s = 0; s < 2; ++s)
+                if (species_mask & (1 << s)) {
+                    memcpy(X + i * d + o, W + (int64_t)set[i] * m + s * cells, sizeof(double) * (size_t)cells);
+                    o += cells;
+                }
+        }
+    }
+    orc_smooth_cil(X1, n1, X2, n2, d, radii, M, tau_frac, cot, C_out, NULL, NULL);
+    double L = 0.0;
+    for (int k = 0; k < M; ++k) L = L + cot[k] * C_out[k];
+    free(W); free(X1); free(X2);
+    return L;
+}

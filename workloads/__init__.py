@@ -1,0 +1,161 @@
+"""Seeded synthetic workloads for the CIL hot path (arXiv 2203.14742).
+
+This module holds the *inputs* only: workload sizes, parameter draws and
+synthetic pattern sets.  It contains none of the method's arithmetic (no
+stepping, no distances, no statistics), so both the oracle and the CUDA path
+may use it.  Random numbers the method itself draws (initial noise, bootstrap
+indices) are NOT made here: each side evaluates the same published
+counter-based generator (SplitMix64) from a seed given here.
+
+The paper simulates its training data at theta_0 (Table 1), so simulated
+patterns are the paper's workload; there is no dataset to stand in for.
+
+Workloads (sizes follow the paper's Table 1 models and the hot-path configs):
+  c1  FHN 32x32, 2 sets x 16, dt 2^-8, 2000 steps, both species (d = 2048),
+      M = 8 radii, b = 1.3, 50 resamples, noise U(-0.05, 0.05).
+  c2  FHN 64x64, 2 sets x 64, dt 2^-10, 10^4 steps, u only (d = 4096),
+      M = 16, 200 resamples.
+  c3  GM 128x128, rho = 1, mu = 0.5 +-10 %, 2 sets x 256, dt 2^-10,
+      2*10^4 steps, both species (d = 32768), M = 16, noise U(0, 0.01).
+  c4  64 parameter vectors x 128 realisations: 16 FHN + 16 GM at 64x64
+      (10^4 steps), 16 FHN + 16 GM at 128x128 (2*10^4 steps); per vector
+      2 sets x 64, 200 resamples, M = 16.  dt is the largest power of two
+      below the explicit diffusion limit h^2/(4 D_max): FHN 2^-10 (64^2),
+      2^-12 (128^2); GM 2^-8 (64^2), 2^-10 (128^2).
+  c5  FHN 64x64, 32 realisations (2 x 16), dt 2^-10, 5000 steps, M = 16,
+      smoothed CIL with tau_k = 0.05 R_k, cotangent 1/M.
+  glarge  the paper's SCIL scale (N_syn = 1000, Sec. 5.3): 2 sets x 1024
+      patterns of d = 32768 for the Gram kernel alone.
+"""
+import math
+
+import numpy as np
+
+FHN, GM, DIFF = 0, 1, 2
+
+SEED_BASE = 0x2203147420000000
+
+# Table 1 values (theta_0 and the diffusion coefficients), in this package's
+# species order (u, v); see the model mapping in oracle/rd.c.
+FHN_THETA0 = (2.8e-4, 0.05, 10.0, 1.0)      # Du = nu_2, Dv = nu_1, eps, a = alpha
+GM_THETA0 = (2.5e-4, 0.01, 1.0, 0.5)        # Du = nu_1, Dv = nu_2, rho, mu = mu_v
+
+
+def seed_of(cfg_index: int) -> int:
+    return SEED_BASE + cfg_index
+
+
+def draw_params(model: int, seed: int, n: int = 1):
+    """n parameter vectors, each uniform in a box around theta_0.
+
+    FHN: Du, Dv, eps within +-10 % of Table 1; a in [0.9, 1.0] (a < 1 makes
+    the equilibrium strictly stable to homogeneous perturbations).
+    GM:  mu within +-10 % of 0.5; rho = 1; Table 1 diffusions.
+    The oracle test suite checks every drawn vector for a diffusion-driven
+    instability on the discrete grid.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        if model == FHN:
+            Du = FHN_THETA0[0] * rng.uniform(0.9, 1.1)
+            Dv = FHN_THETA0[1] * rng.uniform(0.9, 1.1)
+            eps = FHN_THETA0[2] * rng.uniform(0.9, 1.1)
+            a = rng.uniform(0.9, 1.0)
+            out.append((Du, Dv, eps, a))
+        elif model == GM:
+            mu = GM_THETA0[3] * rng.uniform(0.9, 1.1)
+            out.append((GM_THETA0[0], GM_THETA0[1], 1.0, mu))
+        else:
+            raise ValueError("model")
+    return out
+
+
+def group(model, G, n_real, params, dt, n_steps, noise, seed, species_mask):
+    return {"model": model, "G": G, "n_real": n_real, "params": tuple(params),
+            "dt": dt, "n_steps": n_steps, "noise": tuple(noise), "seed": seed,
+            "species_mask": species_mask}
+
+
+def config(name: str, steps_scale: float = 1.0):
+    """Workload description.  steps_scale shortens the integration (tests)."""
+    def steps(n):
+        return max(1, int(round(n * steps_scale)))
+
+    if name == "c1":
+        s = seed_of(1)
+        p = draw_params(FHN, s)[0]
+        g = group(FHN, 32, 32, p, 2.0 ** -8, steps(2000), (-0.05, 0.05), s, 3)
+        return {"name": name, "groups": [g], "n1": 16, "n2": 16, "M": 8, "b": 1.3,
+                "T_res": 50, "seed": s}
+    if name == "c2":
+        s = seed_of(2)
+        p = draw_params(FHN, s)[0]
+        g = group(FHN, 64, 128, p, 2.0 ** -10, steps(10000), (-0.05, 0.05), s, 1)
+        return {"name": name, "groups": [g], "n1": 64, "n2": 64, "M": 16, "b": 1.3,
+                "T_res": 200, "seed": s}
+    if name == "c3":
+        s = seed_of(3)
+        p = draw_params(GM, s)[0]
+        g = group(GM, 128, 512, p, 2.0 ** -10, steps(20000), (0.0, 0.01), s, 3)
+        return {"name": name, "groups": [g], "n1": 256, "n2": 256, "M": 16, "b": 1.3,
+                "T_res": 200, "seed": s}
+    if name == "c4":
+        s = seed_of(4)
+        groups = []
+        k = 0
+        for G, n_steps in ((64, 10000), (128, 20000)):
+            for model in (FHN, GM):
+                ps = draw_params(model, s + 17 * k, 16)
+                for j, p in enumerate(ps):
+                    if model == FHN:
+                        # 128x128 FHN: h^2/(4 Dv) = 2.8e-4, so the power of two is 2^-12.
+                        dt = 2.0 ** -10 if G == 64 else 2.0 ** -12
+                        noise, mask = (-0.05, 0.05), (1 if G == 64 else 3)
+                    else:
+                        dt, noise, mask = (2.0 ** -8 if G == 64 else 2.0 ** -10), (0.0, 0.01), 3
+                    groups.append(group(model, G, 128, p, dt, steps(n_steps), noise,
+                                        s + 1000 * (k + 1) + j, mask))
+                k += 1
+        return {"name": name, "groups": groups, "n1": 64, "n2": 64, "M": 16, "b": 1.3,
+                "T_res": 200, "seed": s}
+    if name == "c5":
+        s = seed_of(5)
+        p = draw_params(FHN, s)[0]
+        g = group(FHN, 64, 32, p, 2.0 ** -10, steps(5000), (-0.05, 0.05), s, 1)
+        return {"name": name, "groups": [g], "n1": 16, "n2": 16, "M": 16, "b": 1.3,
+                "tau_frac": 0.05, "seed": s}
+    raise KeyError(name)
+
+
+def cosine_patterns(n: int, G: int, n_species: int, seed: int, n_modes: int = 6,
+                    amp: float = 1.0, offset: float = 0.0):
+    """n synthetic pattern vectors [n, n_species*G*G] float32: each species a
+    sum of n_modes random cosine modes cos(pi k (x+1/2)/G) cos(pi l (y+1/2)/G)
+    with random k, l in [1, G/4] and N(0,1) amplitudes, scaled by amp and
+    shifted by offset.  Stands in for stepped patterns where the stepper is
+    not part of what is tested."""
+    rng = np.random.default_rng(seed)
+    xs = (np.arange(G) + 0.5) / G
+    out = np.empty((n, n_species, G, G), np.float64)
+    for i in range(n):
+        for s in range(n_species):
+            f = np.zeros((G, G))
+            for _ in range(n_modes):
+                k = rng.integers(1, max(2, G // 4) + 1)
+                l = rng.integers(1, max(2, G // 4) + 1)
+                f += rng.normal() * np.outer(np.cos(math.pi * l * xs), np.cos(math.pi * k * xs))
+            out[i, s] = f
+    out = out * (amp / max(1e-30, np.abs(out).max())) + offset
+    return out.reshape(n, -1).astype(np.float32)
+
+
+def clustered_patterns(n: int, d: int, seed: int, n_centres: int = 4, spread: float = 0.2):
+    """n float32 vectors in R^d drawn around a few random centres, so that the
+    cross-set distances spread over several radii bins."""
+    rng = np.random.default_rng(seed)
+    centres = rng.normal(size=(n_centres, d))
+    which = rng.integers(0, n_centres, size=n)
+    scale = rng.uniform(0.3, 1.0, size=(n, 1)) * spread
+    X = centres[which] + scale * rng.normal(size=(n, d))
+    return X.astype(np.float32)
