@@ -1,0 +1,380 @@
+"""Benchmark of the CIL hot path on B300 (one JSON line on rank 0).
+
+One step = one pass of the whole hot path over one batch of synthetic input
+(the 64x64 FitzHugh-Nagumo workload: 2 sets x 64 realisations, 10^4 FP32
+Euler steps, u-only patterns of d = 4096, 16 radii, 200 resamples):
+  initial state -> integration (+ FP64 residual) -> pattern Gram + exact
+  recheck -> radii / bins / counts -> bootstrap counts -> mean, covariance,
+  Cholesky, log-determinant, cost and log-likelihood.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+value  = cell-updates per second of the whole step (a cell-update = one grid
+         node, both species, one time step), device-timed with CUDA events,
+         max over ranks, inputs resident in HBM.
+e2e    = the same through the public API with host buffers: every step
+         copies the initial fields host->device and the statistics back.
+--impl reference runs the plain FP64 CPU oracle on a bounded sample of the
+same workload (rank 0 only; other ranks exit).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+FP32_INST_PER_CELL = {W.FHN: 16, W.GM: 17}   # minimal FP32 pipe instructions per cell-update
+L2_BYTES = 126 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-reference-path", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[3:7]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except OSError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2203_14742_b300 as p
+    from paper_2203_14742_b300 import build as B
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg = W.config(args.config)
+    gd = dict(cfg["groups"][0])
+    gd["seed"] = gd["seed"] + 7919 * rank          # weak scaling: one independent batch per rank
+    grp = p.Group.from_dict(gd)
+    n1, n2, M, b, T = cfg["n1"], cfg["n2"], cfg["M"], cfg["b"], cfg["T_res"]
+    G = grp.G
+    mask = gd["species_mask"]
+    d = G * G * (2 if mask == 3 else 1)
+    sim = p.Simulation([grp], device=dev)
+    fv = sim.group_fields(0).reshape(grp.n_real, 2 * G * G)
+    X1, X2 = fv[:n1, :d], fv[n1:n1 + n2, :d]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    cell_updates = grp.n_real * G * G * grp.n_steps
+
+    def step(host=None):
+        if host is None:
+            sim.reinit()
+        else:
+            sim.fields.copy_(host["fields"], non_blocking=True)
+        res = sim.integrate()
+        c = p.cil(X1, X2, b=b, M=M)
+        s = p.synlik(c["bins"], M, T, cfg["seed"] + rank, y_obs=c["C"])
+        if host is not None:
+            for k in ("mu", "cov", "chol"):
+                host[k].copy_(s[k], non_blocking=True)
+            host["scal"].copy_(s["scalars"], non_blocking=True)
+            host["counts"].copy_(c["counts"], non_blocking=True)
+            host["residual"].copy_(res, non_blocking=True)
+        return res, c, s
+
+    # ---- warm-up and a correctness glance ------------------------------------
+    for _ in range(args.warmup):
+        res, c, s = step()
+    torch.cuda.synchronize()
+    assert sim.sync_status() == 0, "non-finite field during warm-up"
+
+    # ---- device-timed whole steps (L2 flushed between steps) -----------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    launches0 = p.lib().rd_kernel_launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            sim.reinit()
+            kev[i][0].record(stream)
+            res = sim.integrate()
+            kev[i][1].record(stream)
+            cev[i][0].record(stream)
+            c = p.cil(X1, X2, b=b, M=M)
+            cev[i][1].record(stream)
+            s = p.synlik(c["bins"], M, T, cfg["seed"] + rank, y_obs=c["C"])
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = p.lib().rd_kernel_launches() - launches0
+    step_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    k_ms = [a.elapsed_time(b_) for a, b_ in kev]
+    cil_ms = [a.elapsed_time(b_) for a, b_ in cev]
+    if world > 1:
+        t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t)
+    assert sim.sync_status() == 0
+    ms_per_step = step_ms / args.steps
+    value = cell_updates * world / (ms_per_step * 1e-3)
+
+    # ---- end to end through the public API with host buffers -----------------
+    host = {"fields": torch.empty(sim.fields.shape, dtype=torch.float32, pin_memory=True)}
+    sim.reinit()
+    host["fields"].copy_(sim.fields)
+    for k, shape, dt in (("mu", (M,), torch.float64), ("cov", (M, M), torch.float64),
+                         ("chol", (M, M), torch.float64), ("scal", (4,), torch.float64),
+                         ("counts", (M,), torch.int64), ("residual", (grp.n_real, 2), torch.float64)):
+        host[k] = torch.empty(shape, dtype=dt, pin_memory=True)
+    step(host)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        step(host)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t)
+    h2d = host["fields"].numel() * 4
+    d2h = sum(host[k].numel() * host[k].element_size() for k in host if k != "fields")
+
+    # ---- plain single-realisation FP32 path on a slice (same GPU) ------------
+    ref_rate = None
+    if not args.no_reference_path and rank == 0:
+        gsl = dict(gd)
+        gsl["n_real"] = 2
+        ssl = p.Simulation([p.Group.from_dict(gsl)], device=dev)
+        nsl = 500
+        ssl.integrate_reference(steps=50)
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        ssl.integrate_reference(steps=nsl)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        ref_rate = 2 * G * G * nsl / (r0.elapsed_time(r1) * 1e-3)
+
+    # ---- roofline of the dominant kernel (the resident stepper) -------------
+    pk, src = peaks()
+    k_avg_ms = sum(k_ms) / len(k_ms)
+    inst = FP32_INST_PER_CELL[gd["model"]]
+    achieved = cell_updates * inst / (k_avg_ms * 1e-3) / 1e12          # Tinst/s
+    peak_alu = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12   # FP32 lanes x clock
+    cil_avg = sum(cil_ms) / len(cil_ms)
+    pair_rate = n1 * n2 / (cil_avg * 1e-3)
+
+    out = {
+        "metric": "RD cell-updates/s + CIL pair-dists/s at stated tol; % HBM/tensor roofline",
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 stepper, bf16x3 Gram + f64 recheck, f64 statistics",
+        "data": "synthetic (seeded counter-based initial noise; the paper's data are simulated too)",
+        "config": {"workload": "c2: FHN 64x64, 2 sets x 64 realisations, 10^4 Euler steps, "
+                               "u-only d=4096, M=16, b=1.3, 200 resamples",
+                   "realisations_per_gpu": grp.n_real, "grid": G, "euler_steps": grp.n_steps,
+                   "pairs": n1 * n2, "pattern_dim": d, "radii": M, "resamples": T,
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "pair_dists_per_s": pair_rate,
+        "cil_ms": cil_avg,
+        "stepper_ms": k_avg_ms,
+        "e2e": {"value": cell_updates * world / (e2e_ms * 1e-3), "unit": "cell-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tinst/s",
+                     "frac": achieved / peak_alu, "traffic": None,
+                     "kernel": "rd_resident_kernel<FHN,64,4,4>",
+                     "note": "FP32 pipe instructions: %d per cell-update x cell-updates / kernel time; "
+                             "peak = 148 SM x 128 FP32 lanes x max SM clock (%s peaks file)" % (inst, src)},
+        "plain_fp32_path_cell_updates_per_s": ref_rate,
+        "batched_vs_plain": (cell_updates / (k_avg_ms * 1e-3)) / ref_rate if ref_rate else None,
+    }
+    cs = clk.summary()
+    if cs:
+        out["clocks"] = cs
+    return out
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) arm / baseline
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg, n_steps_sample):
+    """Time the oracle on a bounded sample: all realisations for
+    n_steps_sample Euler steps (scaled to the full step count), plus the full
+    CIL and bootstrap statistics.  Returns (cell-updates/s, seconds, note)."""
+    import oracle
+    g = cfg["groups"][0]
+    G, n = g["G"], g["n_real"]
+    t0 = time.perf_counter()
+    f0 = oracle.init_fields(g["model"], G, n, g["params"], g["noise"][0], g["noise"][1], g["seed"])
+    f = oracle.step(g["model"], g["params"], g["dt"], n_steps_sample, f0.astype(np.float64))
+    oracle.residual(g["model"], g["params"], f)
+    t_step = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    X = oracle.patterns(f.astype(np.float32), g["species_mask"])
+    o = oracle.cil(X[:cfg["n1"]], X[cfg["n1"]:cfg["n1"] + cfg["n2"]], b=cfg["b"], M=cfg["M"])
+    oracle.synlik(o["bins"], cfg["M"], cfg["T_res"], cfg["seed"], y_obs=o["counts"] / (cfg["n1"] * cfg["n2"]))
+    t_cil = time.perf_counter() - t1
+    full_cells = n * G * G * g["n_steps"]
+    t_full = t_step * (g["n_steps"] / n_steps_sample) + t_cil
+    note = ("all %d realisations x %d of %d Euler steps (stepping time scaled by %.0fx) + full CIL "
+            "and bootstrap statistics" % (n, n_steps_sample, g["n_steps"], g["n_steps"] / n_steps_sample))
+    return full_cells / t_full, t_step + t_cil, note
+
+
+def run_reference(args):
+    cfg = W.config(args.config)
+    cores = os.cpu_count()
+    n_sample = 500
+    oracle_sample(cfg, 10)           # warm (builds the library)
+    vals, secs = [], 0.0
+    for _ in range(args.warmup):
+        oracle_sample(cfg, n_sample)
+    for _ in range(args.steps):
+        v, s, note = oracle_sample(cfg, n_sample)
+        vals.append(v)
+        secs += s
+    value = statistics.mean(vals)
+    g = cfg["groups"][0]
+    return {
+        "impl": "reference",
+        "metric": "RD cell-updates/s + CIL pair-dists/s at stated tol; % HBM/tensor roofline",
+        "value": value, "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": g["n_real"] * g["G"] ** 2 * g["n_steps"] / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "c2: FHN 64x64, 2 sets x 64 realisations, 10^4 Euler steps, "
+                               "u-only d=4096, M=16, b=1.3, 200 resamples"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": note},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and not args.no_cpu_baseline:
+        cfg = W.config(args.config)
+        v, secs, note = oracle_sample(cfg, 1000)
+        out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": os.cpu_count(),
+                               "kind": "oracle", "sample": note + " (%.1f s of CPU work)" % secs}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,273 @@
+/*
+ * rdcil.h — C ABI of the B300-native Correlation Integral Likelihood hot path.
+ *
+ * Paper: A. Kazarnikov, R. Scheichl, H. Haario and A. Marciniak-Czochra,
+ * "A Bayesian Approach to Modelling Biological Pattern Formation with
+ * Limited Data", arXiv 2203.14742.  The calls follow the paper's statement of the problem:
+ * simulate N patterns at a parameter vector from random initial states
+ * (Sec. 2.1, Sec. 4.1), compare two pattern sets by the correlation sum at a
+ * ladder of radii (eq. eCDF, eq. CIL), and estimate the mean and covariance
+ * of the resulting vector over resampled set pairs to evaluate the cost
+ * (Alg. 1 step 3, Alg. 5, eq. cil:CF, eq. cil:CF_synth).
+ *
+ * Conventions for every call
+ *  - Pointers named d_* are CUDA device pointers on the current device, owned
+ *    by the caller, contiguous, and must stay valid until the stream work
+ *    that uses them has finished.  Host pointers are named without d_.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call only enqueues work and returns; nothing is
+ *    synchronised unless the call's comment says so.
+ *  - Argument errors are returned before any work is enqueued.  Errors that
+ *    can only be seen on the device (non-finite fields, a non-positive-
+ *    definite covariance) are written to the device status outputs named in
+ *    each call, or to the handle's status word read by rd_sync_status.
+ *  - No call throws; no call allocates device memory except rd_init.
+ *  - Thread-compatible: one handle per host thread.
+ */
+#ifndef RDCIL_H
+#define RDCIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rd_status;
+#define RD_OK 0
+#define RD_ERR_INVALID_ARG 1
+#define RD_ERR_CUDA 2
+#define RD_ERR_NOT_PD 3
+#define RD_ERR_TIMEOUT 4
+#define RD_ERR_NONFINITE 5
+#define RD_ERR_UNSUPPORTED 6
+#define RD_ERR_OOM 7
+
+/* Reaction kinetics (Sec. 4.1), species order (u, v):
+ *  RD_FHN  FitzHugh-Nagumo, eq. (introduction:0) with u = membrane potential
+ *          w, v = recovery variable v, mu = 1:
+ *            u_t = Du Lap u + u - u^3 - v,   v_t = Dv Lap v + eps (u - a v)
+ *          params = (Du, Dv, eps, a); equilibrium (0, 0).
+ *  RD_GM   Gierer-Meinhardt, eq. (gmSystem) with u = activator, v =
+ *          inhibitor, mu_w = 1, mu = mu_v and an overall rate rho:
+ *            u_t = Du Lap u + rho (u^2/v - mu u),  v_t = Dv Lap v + rho (u^2 - v)
+ *          params = (Du, Dv, rho, mu); equilibrium (1/mu, 1/mu^2).
+ *  RD_DIFF pure diffusion (reaction off), params = (Du, Dv, -, -); a
+ *          degenerate case with closed-form solutions, used for checks. */
+#define RD_FHN 0
+#define RD_GM 1
+#define RD_DIFF 2
+
+/* group flags */
+#define RD_GROUP_ADJOINT 1   /* reserve checkpoint memory for rd_adjoint */
+
+/* One parameter group: n_real realisations of one model on one G x G grid
+ * with one parameter vector and one step count (a theta of Alg. 3/6 step 1).
+ * Fields of realisation r live at d_fields + field_offset + r*2*G*G as
+ * [species u, v][y][x] float32, row-major.  field_offset must be a multiple
+ * of 4 floats (16-byte rows).  Supported G: 32, 64, 128.  dt must be below
+ * the explicit stability limit (h^2 / (4 max(Du, Dv)), h = 1/(G-1)); the
+ * library does not check stability, but a blow-up is reported as
+ * RD_ERR_NONFINITE. */
+typedef struct rd_group {
+    int32_t model;          /* RD_FHN / RD_GM / RD_DIFF */
+    int32_t G;              /* grid side */
+    int32_t n_real;         /* realisations in this group (>= 1) */
+    int32_t flags;          /* RD_GROUP_* */
+    int64_t n_steps;        /* explicit Euler steps for rd_integrate_batch */
+    int64_t field_offset;   /* floats from d_fields to realisation 0 */
+    double dt;              /* time step */
+    double params[4];       /* see the model list above */
+    double noise_lo;        /* initial state = equilibrium + U(noise_lo, noise_hi) */
+    double noise_hi;
+    uint64_t seed;          /* counter-based noise stream of this group */
+} rd_group;
+
+typedef struct rd_handle rd_handle;
+
+/* rd_init — plan a batch of groups and write their random initial states
+ * (Sec. 4.1: homogeneous equilibrium plus small uniform noise).
+ *
+ * Initial value of (realisation r, species s, node c) of a group:
+ *   U = (SplitMix64 output number ((r*2+s)*G*G + c) of stream group.seed
+ *        >> 11) * 2^-53,
+ *   value = float( x0_s + (noise_lo + (noise_hi - noise_lo) * U) )
+ * evaluated in FP64 without fused multiply-add and rounded once to FP32.
+ *
+ * groups/n_groups: host array, copied (may be freed after the call).
+ * d_fields: device float32 array holding every group's fields.
+ * out: receives the handle; the handle owns the device copy of the group
+ *   table, the status word and (for RD_GROUP_ADJOINT groups) checkpoint
+ *   memory.  Release with rd_free.
+ * Returns RD_ERR_INVALID_ARG for an unsupported G, model, n_real < 1,
+ * misaligned field_offset, dt <= 0 or overlapping groups; RD_ERR_OOM when
+ * the handle's device memory cannot be allocated. */
+rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_fields,
+                  void *stream, rd_handle **out);
+
+/* rd_reinit — write the initial states again (same rule as rd_init) into
+ * d_fields, for a handle created earlier.  No allocation. */
+rd_status rd_reinit(rd_handle *h, float *d_fields, void *stream);
+
+/* rd_integrate_batch — explicit Euler for every realisation of every group
+ * (Sec. 5.1, method of lines App. B.1.1):
+ *   w <- w + dt * F(w),  F = D * Lap_h(w) + R(w),
+ *   Lap_h(w)_{y,x} = (w_{y,x+1} + w_{y,x-1} + w_{y+1,x} + w_{y-1,x} - 4 w_{y,x}) (G-1)^2
+ * with mirrored Neumann ghosts (ghost = adjacent edge node).  FP32 state.
+ * steps_override < 0: each group advances its own n_steps; >= 0: every
+ *   group advances steps_override steps.
+ * d_residual (nullable): [n_real_total][2] float64, the steady-state residual
+ *   of the final state per realisation in group order: max |F| and
+ *   sqrt(mean F^2) over both species, F evaluated in FP64 from the FP32
+ *   state (the L-infinity criterion of Sec. 5.1).
+ * A realisation whose final state is not finite sets RD_ERR_NONFINITE in the
+ * handle's status word.  Integrating n then m steps equals integrating n+m. */
+rd_status rd_integrate_batch(rd_handle *h, float *d_fields, int64_t steps_override,
+                             double *d_residual, void *stream);
+
+/* rd_integrate_reference — the plain path the batched stepper is measured
+ * against: one realisation per launch, one Euler step per launch, state
+ * round-tripping through global memory.  Same arithmetic contract as
+ * rd_integrate_batch for FP32 (results agree to FP32 rounding, not bit for
+ * bit).  d_tmp: caller scratch of 2*G*G floats of the largest group. */
+rd_status rd_integrate_reference(rd_handle *h, float *d_fields, float *d_tmp,
+                                 int64_t steps_override, void *stream);
+
+/* rd_integrate_f64 — the same Euler recursion on a float64 copy of the
+ * fields (layout as d_fields, offsets in doubles), in the operation order
+ *   Lap = ((((w_{x+1} + w_{x-1}) + w_{y+1}) + w_{y-1}) - 4 w) * (G-1)^2,
+ *   F = D*Lap + R(w),  w <- w + dt*F
+ * with every operation rounded separately (no fused multiply-add), so it
+ * reproduces a plain FP64 evaluation of that order bit for bit.  d_tmp64:
+ * caller scratch of the same size as d_fields64.  For checking only (FP64
+ * is slow on this GPU). */
+rd_status rd_integrate_f64(rd_handle *h, double *d_fields64, double *d_tmp64,
+                           int64_t steps_override, void *stream);
+
+/* rd_sync_status — synchronise `stream`, read and clear the handle's device
+ * status word.  Returns RD_OK, RD_ERR_NONFINITE, RD_ERR_TIMEOUT, or
+ * RD_ERR_CUDA when the stream itself reported an error. */
+rd_status rd_sync_status(rd_handle *h, void *stream);
+
+/* rd_n_real_total — total realisations over all groups of the handle. */
+int64_t rd_n_real_total(const rd_handle *h);
+
+void rd_free(rd_handle *h);
+
+/* rd_kernel_launches — number of CUDA kernels this library has launched in
+ * this process so far (its own kernels only; memset/memcpy not counted). */
+uint64_t rd_kernel_launches(void);
+
+const char *rd_status_str(rd_status s);
+
+/* ------------------------------------------------------------------------
+ * Correlation integral (eq. eCDF, eq. CIL, Sec. 2.1).
+ *
+ * Pattern i of set 1 is the d floats at d_X1 + i*ld1 (likewise set 2), so a
+ * set can be read straight out of the field array: one species of
+ * realisation r is d = G*G floats at offset r*2*G*G, both species d = 2*G*G.
+ *
+ * Definitions (both sides of every comparison use them exactly):
+ *   d2_ij = sum_{t=0}^{d-1} (double(x_t) - double(y_t))^2, summed in t order
+ *           in FP64 without fused multiply-add;
+ *   R0    = sqrt(max_ij d2_ij)  (largest cross-set distance, Sec. 2.1);
+ *   R_k   = R_{k-1} / b, k = 1..M (power law R0 b^-k), FP64;
+ *   K_ij  = #{k : d2_ij < R_k * R_k}  (strict '<' of eq. eCDF);
+ *   counts[k-1] = #{(i,j) : K_ij >= k} = n1*n2 * C(R_k).
+ * d_radii_in (nullable): if given, the M radii R_1..R_M are taken from it
+ *   (b ignored) and R0 is not computed (radii_out[0] = NaN).
+ * Outputs: d_radii_out[M+1] = (R0, R_1..R_M); d_bins[n1*n2] uint8 K_ij
+ *   (row i, column j); d_counts[M] int64; d_C (nullable) float64[M], the
+ *   correlation integral vector C(R_k) = counts[k-1] / (n1 n2) (eq. CIL);
+ *   d_n_rechecked (nullable) int64: pairs whose distance had to be
+ *   evaluated exactly.
+ *
+ * Method: the patterns are centred and split into bf16 hi + lo parts; a
+ * tensor-core Gram product (FP32 accumulation) gives
+ * d2 ~ |x|^2 + |y|^2 - 2 x.y for every pair together with a rigorous error
+ * bound; pairs whose bound straddles a threshold (or the maximum) are
+ * re-evaluated with the exact sequential FP64 sum above, so K_ij and the
+ * counts equal the definition bit for bit.
+ * Limits: 1 <= n1, n2 <= 65535; 1 <= d; 1 <= M <= 32; b > 1.
+ * d_work: caller scratch of cil_workspace_size bytes (256-byte aligned). */
+rd_status cil_workspace_size(int64_t n1, int64_t n2, int64_t d, size_t *bytes);
+rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1,
+                       const float *d_X2, int64_t ld2, int64_t n2, int64_t d,
+                       const double *d_radii_in, double b, int32_t M,
+                       double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
+                       double *d_C, int64_t *d_n_rechecked, void *d_work, size_t work_bytes,
+                       void *stream);
+
+/* cil_features_exact — the same outputs with every pair evaluated by the
+ * exact sequential FP64 sum (no Gram product).  Slow; for checking. */
+rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1,
+                             const float *d_X2, int64_t ld2, int64_t n2, int64_t d,
+                             const double *d_radii_in, double b, int32_t M,
+                             double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
+                             double *d_C, void *d_work, size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Synthetic-likelihood statistics over resampled set pairs
+ * (Alg. 5 step 2 / Alg. 6 step 2: resample each set with replacement;
+ * Alg. 1 step 3: mean and covariance; eq. cil:CF / cil:CF_synth: cost).
+ *
+ * n_problems independent problems, packed back to back: problem p reads
+ * d_bins + p*n1*n2 and d_y_obs + p*M, writes d_Y + p*T*M, d_mu + p*M,
+ * d_cov + p*M*M, d_chol + p*M*M, d_scalars + p*4, d_active + p*M,
+ * d_status + p.
+ *
+ * Resample t (0 <= t < T) of problem p draws set-1 index a (a < n1) as
+ *   floor(SplitMix64 output number (((t*2+0) << 32) | a) of stream
+ *         seed + p  *  n1 / 2^64)
+ * (Lemire's multiply-shift), set-2 index b with ((t*2+1) << 32) | b.
+ * Y[t][k-1] = sum_a sum_b [K_{I_a J_b} >= k]   (int64)
+ * y_t = Y_t / (n1 n2);  mu = (1/T) sum_t y_t;
+ * cov = (1/(T-1)) sum_t (y_t - mu)(y_t - mu)^T;
+ * active[k] = 0 iff Y[t][k] is the same for every t;
+ * chol = lower Cholesky factor of the active block of cov, packed into the
+ *   leading M_act x M_act corner (rest zero);
+ * scalars = (logdet, f, loglik, M_act) with logdet = 2 sum log L_ii,
+ *   f = |L^-1 (y_obs - mu)_act|^2, loglik = -(f + logdet + M_act log 2pi)/2
+ *   (f and loglik NaN when d_y_obs is NULL);
+ * status[p] = RD_OK or RD_ERR_NOT_PD (active block not positive definite).
+ * mu and cov follow the plain sequential definition in t order, so they
+ * match a plain FP64 evaluation bit for bit.
+ * Limits: n1, n2 <= 65535; 1 <= M <= 32; 2 <= T; T*(n1*n2)^2 < 2^62. */
+rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2, int32_t M,
+                       int32_t T, uint64_t seed, int32_t n_problems,
+                       const double *d_y_obs, int64_t *d_Y, double *d_mu,
+                       double *d_cov, double *d_chol, double *d_scalars,
+                       uint8_t *d_active, int32_t *d_status, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Adjoint: gradient of a sigmoid-smoothed correlation integral with respect
+ * to the four parameters of one group (the paper itself is gradient-free;
+ * this serves proposal construction only, the likelihood keeps the exact
+ * indicator counts of eq. eCDF).
+ *
+ *   C_k  = (1/(n1 n2)) sum_ij sigma((R_k - d_ij)/tau_k),  tau_k = tau_frac R_k,
+ *   L    = sum_k cot_k C_k,
+ * d_ij the Euclidean distance of the patterns (species_mask bit 0 = u,
+ * bit 1 = v, concatenated) of realisations set1[i] and set2[j] of the group
+ * after n_steps Euler steps from d_fields0 (the group's initial states,
+ * same layout as d_fields, held fixed).  Radii are held fixed.
+ * Reverse mode of the FP32 Euler recursion: the forward pass stores a
+ * checkpoint every ceil(sqrt(n_steps)) steps, the reverse pass recomputes
+ * each segment from its checkpoint and runs
+ *   lambda_n = lambda_{n+1} + dt J_F(w_n)^T lambda_{n+1},
+ *   g       += dt (dF/dtheta(w_n))^T lambda_{n+1}   (accumulated in FP64).
+ * Outputs: d_C[M] (float64, nullable), d_grad[4] (float64), d_final
+ * (nullable) the group's final fields.  Requires the group to carry
+ * RD_GROUP_ADJOINT (checkpoints reserved at rd_init).  Synchronous with
+ * respect to the host only through stream order. */
+rd_status rd_adjoint(rd_handle *h, int32_t group, const float *d_fields0,
+                     int32_t species_mask, const int32_t *d_set1, int64_t n1,
+                     const int32_t *d_set2, int64_t n2, const double *d_radii,
+                     int32_t M, double tau_frac, const double *d_cotangent,
+                     double *d_C, double *d_grad, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,339 @@
+"""B300-native hot path of the Correlation Integral Likelihood (arXiv 2203.14742).
+
+Thin Python binding over the C ABI in ``include/rdcil.h`` (librdcil.so, built
+in-tree by ``paper_2203_14742_b300/build.py``).  This module only marshals
+arguments: every step of the path runs in the library's CUDA kernels.  It
+takes torch CUDA tensors for device memory and the current torch stream.
+There is no CPU fallback: importing fails loudly when the library is missing.
+
+    sim  = Simulation(groups)                  # rd_init: fields + initial noise
+    res  = sim.integrate()                     # rd_integrate_batch (+ FP64 residual)
+    out  = cil(X1, X2, b=1.3, M=16)            # cil_features: radii, bins, counts
+    st   = synlik(out["bins"], M=16, T=200, seed=...)   # synlik_stats
+    C, g = sim.adjoint(...)                    # rd_adjoint (smoothed-CIL gradient)
+"""
+import ctypes as C
+import math
+import os
+
+import torch
+
+__all__ = ["FHN", "GM", "DIFF", "Group", "Simulation", "cil", "cil_exact", "synlik",
+           "SmoothCIL", "lib", "status_str"]
+
+FHN, GM, DIFF = 0, 1, 2
+GROUP_ADJOINT = 1
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librdcil.so")
+
+
+class RdGroup(C.Structure):
+    _fields_ = [("model", C.c_int32), ("G", C.c_int32), ("n_real", C.c_int32), ("flags", C.c_int32),
+                ("n_steps", C.c_int64), ("field_offset", C.c_int64), ("dt", C.c_double),
+                ("params", C.c_double * 4), ("noise_lo", C.c_double), ("noise_hi", C.c_double),
+                ("seed", C.c_uint64)]
+
+
+_vp, _i64, _i32, _dbl, _u64, _sz = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_uint64, C.c_size_t
+
+_SIGS = {
+    "rd_init": (_i32, [C.POINTER(RdGroup), _i32, _vp, _vp, C.POINTER(_vp)]),
+    "rd_reinit": (_i32, [_vp, _vp, _vp]),
+    "rd_integrate_batch": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "rd_integrate_reference": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+    "rd_integrate_f64": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+    "rd_sync_status": (_i32, [_vp, _vp]),
+    "rd_n_real_total": (_i64, [_vp]),
+    "rd_free": (None, [_vp]),
+    "rd_status_str": (C.c_char_p, [_i32]),
+    "cil_workspace_size": (_i32, [_i64, _i64, _i64, C.POINTER(_sz)]),
+    "cil_features": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _dbl, _i32, _vp, _vp, _vp,
+                            _vp, _vp, _vp, _sz, _vp]),
+    "cil_features_exact": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _dbl, _i32, _vp, _vp,
+                                  _vp, _vp, _vp, _sz, _vp]),
+    "synlik_stats": (_i32, [_vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
+                            _vp, _vp, _vp]),
+    "rd_kernel_launches": (_u64, []),
+    "rd_adjoint": (_i32, [_vp, _i32, _vp, _i32, C.POINTER(_i32), _i64, C.POINTER(_i32), _i64, _vp,
+                          _i32, _dbl, _vp, _vp, _vp, _vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded librdcil.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("librdcil.so is not built (run `python -m paper_2203_14742_b300.build`)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_str(st):
+    return lib().rd_status_str(int(st)).decode()
+
+
+class RdError(RuntimeError):
+    def __init__(self, fn, st):
+        super().__init__("%s failed: %s (%d)" % (fn, status_str(st), st))
+        self.status = st
+
+
+def _check(fn, st):
+    if st != 0:
+        raise RdError(fn, st)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Group:
+    """One parameter group (a theta): n_real realisations of `model` on a
+    G x G grid.  params: FHN (Du, Dv, eps, a); GM (Du, Dv, rho, mu)."""
+
+    def __init__(self, model, G, n_real, params, dt, n_steps, noise=(-0.05, 0.05), seed=0,
+                 adjoint=False):
+        self.model, self.G, self.n_real = int(model), int(G), int(n_real)
+        self.params = tuple(float(p) for p in params) + (0.0,) * (4 - len(params))
+        self.dt, self.n_steps = float(dt), int(n_steps)
+        self.noise = (float(noise[0]), float(noise[1]))
+        self.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        self.adjoint = bool(adjoint)
+
+    @property
+    def floats(self):
+        return self.n_real * 2 * self.G * self.G
+
+    @classmethod
+    def from_dict(cls, d, adjoint=False):
+        return cls(d["model"], d["G"], d["n_real"], d["params"], d["dt"], d["n_steps"],
+                   d["noise"], d["seed"], adjoint=adjoint)
+
+
+class Simulation:
+    """A batch of groups sharing one field tensor (rd_init / rd_integrate_batch)."""
+
+    def __init__(self, groups, device=None, fields=None):
+        self.groups = list(groups)
+        self.device = torch.device(device or "cuda")
+        offs, off = [], 0
+        for g in self.groups:
+            offs.append(off)
+            off += g.floats
+        self.offsets = offs
+        self.total_floats = off
+        if fields is None:
+            fields = torch.empty(off, dtype=torch.float32, device=self.device)
+        if fields.numel() < off or fields.dtype != torch.float32 or not fields.is_contiguous():
+            raise ValueError("fields: contiguous float32 tensor of >= %d elements" % off)
+        self.fields = fields
+        arr = (RdGroup * len(self.groups))()
+        for i, g in enumerate(self.groups):
+            a = arr[i]
+            a.model, a.G, a.n_real = g.model, g.G, g.n_real
+            a.flags = GROUP_ADJOINT if g.adjoint else 0
+            a.n_steps, a.field_offset, a.dt = g.n_steps, offs[i], g.dt
+            for k in range(4):
+                a.params[k] = g.params[k]
+            a.noise_lo, a.noise_hi, a.seed = g.noise[0], g.noise[1], g.seed
+        self._arr = arr
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check("rd_init", lib().rd_init(arr, len(self.groups), _ptr(self.fields), _stream(),
+                                            C.byref(h)))
+        self.handle = h
+        self.n_real_total = sum(g.n_real for g in self.groups)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.rd_free(h)
+            self.handle = None
+
+    # -- views -------------------------------------------------------------
+    def group_fields(self, i, fields=None):
+        g = self.groups[i]
+        f = self.fields if fields is None else fields
+        o = self.offsets[i]
+        return f[o:o + g.floats].view(g.n_real, 2, g.G, g.G)
+
+    # -- calls -------------------------------------------------------------
+    def reinit(self):
+        _check("rd_reinit", lib().rd_reinit(self.handle, _ptr(self.fields), _stream()))
+
+    def integrate(self, steps=-1, residual=True):
+        res = None
+        if residual:
+            res = torch.empty((self.n_real_total, 2), dtype=torch.float64, device=self.device)
+        _check("rd_integrate_batch", lib().rd_integrate_batch(self.handle, _ptr(self.fields), int(steps),
+                                                              _ptr(res), _stream()))
+        return res
+
+    def integrate_reference(self, steps=-1, tmp=None):
+        if tmp is None:
+            tmp = torch.empty(max(2 * g.G * g.G for g in self.groups), dtype=torch.float32,
+                              device=self.device)
+        _check("rd_integrate_reference", lib().rd_integrate_reference(
+            self.handle, _ptr(self.fields), _ptr(tmp), int(steps), _stream()))
+
+    def integrate_f64(self, fields64, steps=-1):
+        tmp = torch.empty_like(fields64)
+        _check("rd_integrate_f64", lib().rd_integrate_f64(self.handle, _ptr(fields64), _ptr(tmp),
+                                                          int(steps), _stream()))
+        return fields64
+
+    def sync_status(self):
+        return lib().rd_sync_status(self.handle, _stream())
+
+    def adjoint(self, group, fields0, species_mask, set1, set2, radii, tau_frac, cotangent):
+        """(C[M], grad[4]) float64 tensors: smoothed CIL and its gradient."""
+        s1 = (C.c_int32 * len(set1))(*[int(x) for x in set1])
+        s2 = (C.c_int32 * len(set2))(*[int(x) for x in set2])
+        radii = radii.to(device=self.device, dtype=torch.float64).contiguous()
+        cot = cotangent.to(device=self.device, dtype=torch.float64).contiguous()
+        M = radii.numel()
+        Cv = torch.empty(M, dtype=torch.float64, device=self.device)
+        g = torch.empty(4, dtype=torch.float64, device=self.device)
+        _check("rd_adjoint", lib().rd_adjoint(self.handle, int(group), _ptr(fields0), int(species_mask),
+                                              s1, len(set1), s2, len(set2), _ptr(radii), M,
+                                              float(tau_frac), _ptr(cot), _ptr(Cv), _ptr(g), _stream()))
+        return Cv, g
+
+
+# ---------------------------------------------------------------------------
+# correlation integral
+# ---------------------------------------------------------------------------
+_work_cache = {}
+
+
+def _workspace(n1, n2, d, device):
+    sz = C.c_size_t()
+    _check("cil_workspace_size", lib().cil_workspace_size(n1, n2, d, C.byref(sz)))
+    key = (device, )
+    w = _work_cache.get(key)
+    if w is None or w.numel() < sz.value:
+        w = torch.empty(max(sz.value, 1 << 20), dtype=torch.uint8, device=device)
+        _work_cache[key] = w
+    return w, sz.value
+
+
+def _as_rows(X):
+    """(tensor, ld, n, d) for a 2-D float32 CUDA tensor with unit column stride."""
+    if X.dtype != torch.float32 or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("patterns: 2-D float32 tensor with contiguous rows")
+    return X, X.stride(0), X.shape[0], X.shape[1]
+
+
+def _cil_call(fn, X1, X2, b, M, radii, work=None):
+    X1, ld1, n1, d = _as_rows(X1)
+    X2, ld2, n2, d2 = _as_rows(X2)
+    if d != d2:
+        raise ValueError("pattern length mismatch")
+    dev = X1.device
+    if radii is not None:
+        radii = radii.to(device=dev, dtype=torch.float64).contiguous()
+        M = radii.numel()
+    radii_out = torch.empty(M + 1, dtype=torch.float64, device=dev)
+    bins = torch.empty((n1, n2), dtype=torch.uint8, device=dev)
+    counts = torch.empty(M, dtype=torch.int64, device=dev)
+    Cvec = torch.empty(M, dtype=torch.float64, device=dev)
+    nre = torch.zeros(1, dtype=torch.int64, device=dev)
+    if work is None:
+        w, wb = _workspace(n1, n2, d, dev)
+    else:
+        w, wb = work, work.numel()
+    args = [_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, d, _ptr(radii), float(b or 0.0), int(M),
+            _ptr(radii_out), _ptr(bins), _ptr(counts), _ptr(Cvec)]
+    if fn == "cil_features":
+        args.append(_ptr(nre))
+    args += [_ptr(w), wb, _stream()]
+    _check(fn, getattr(lib(), fn)(*args))
+    return {"R0": radii_out[0], "radii": radii_out[1:], "bins": bins, "counts": counts, "C": Cvec,
+            "n_rechecked": nre}
+
+
+def cil(X1, X2, b=1.3, M=16, radii=None, work=None):
+    """Correlation integral of two pattern sets (rows of X1, X2)."""
+    return _cil_call("cil_features", X1, X2, b, M, radii, work)
+
+
+def cil_exact(X1, X2, b=1.3, M=16, radii=None, work=None):
+    """Same outputs, every pair by the exact sequential FP64 sum (checking)."""
+    return _cil_call("cil_features_exact", X1, X2, b, M, radii, work)
+
+
+# ---------------------------------------------------------------------------
+# synthetic likelihood
+# ---------------------------------------------------------------------------
+def synlik(bins, M, T, seed, y_obs=None):
+    """Bootstrap statistics of bins [P, n1, n2] (or [n1, n2]) uint8."""
+    squeeze = bins.dim() == 2
+    if squeeze:
+        bins = bins.unsqueeze(0)
+    bins = bins.contiguous()
+    P, n1, n2 = bins.shape
+    dev = bins.device
+    Y = torch.empty((P, T, M), dtype=torch.int64, device=dev)
+    mu = torch.empty((P, M), dtype=torch.float64, device=dev)
+    cov = torch.empty((P, M, M), dtype=torch.float64, device=dev)
+    chol = torch.empty((P, M, M), dtype=torch.float64, device=dev)
+    sc = torch.empty((P, 4), dtype=torch.float64, device=dev)
+    act = torch.empty((P, M), dtype=torch.uint8, device=dev)
+    st = torch.empty(P, dtype=torch.int32, device=dev)
+    yo = None
+    if y_obs is not None:
+        yo = y_obs.to(device=dev, dtype=torch.float64).reshape(P, M).contiguous()
+    _check("synlik_stats", lib().synlik_stats(_ptr(bins), n1, n2, int(M), int(T),
+                                              int(seed) & 0xFFFFFFFFFFFFFFFF, P, _ptr(yo), _ptr(Y),
+                                              _ptr(mu), _ptr(cov), _ptr(chol), _ptr(sc), _ptr(act),
+                                              _ptr(st), _stream()))
+    out = {"Y": Y, "mu": mu, "cov": cov, "chol": chol, "scalars": sc, "logdet": sc[:, 0], "f": sc[:, 1],
+           "loglik": sc[:, 2], "m_active": sc[:, 3], "active": act, "status": st}
+    if squeeze:
+        out = {k: v[0] for k, v in out.items()}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+class SmoothCIL(torch.autograd.Function):
+    """C_tau(theta): the sigmoid-smoothed correlation integral of one group
+    after its n_steps, as a differentiable function of theta = params[4].
+
+    forward(theta, sim, group, fields0, species_mask, set1, set2, radii,
+            tau_frac) -> C[M].  The backward pass needs the cotangent, so the
+    forward only evaluates C; backward calls rd_adjoint with the incoming
+    gradient as cotangent (the parameters inside `sim` must equal theta)."""
+
+    @staticmethod
+    def forward(ctx, theta, sim, group, fields0, species_mask, set1, set2, radii, tau_frac):
+        M = radii.numel()
+        ones = torch.zeros(M, dtype=torch.float64, device=fields0.device)
+        Cv, _ = sim.adjoint(group, fields0, species_mask, set1, set2, radii, tau_frac, ones)
+        ctx.args = (sim, group, fields0, species_mask, set1, set2, radii, tau_frac)
+        ctx.theta_device = theta.device
+        return Cv
+
+    @staticmethod
+    def backward(ctx, gC):
+        sim, group, fields0, species_mask, set1, set2, radii, tau_frac = ctx.args
+        _, g = sim.adjoint(group, fields0, species_mask, set1, set2, radii, tau_frac,
+                           gC.detach().to(torch.float64))
+        return (g.to(ctx.theta_device), None, None, None, None, None, None, None, None)

@@ -1,0 +1,184 @@
+// C ABI entry points: handle management, argument validation, dispatch.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+#include "common.cuh"
+
+using namespace rdcil;
+
+struct rd_handle {
+    Handle h;
+};
+
+namespace rdcil {
+rd_status adjoint_reserve(Handle &h);
+void adjoint_release(Handle &h);
+}  // namespace rdcil
+
+static rd_status validate_groups(const rd_group *groups, int32_t n_groups) {
+    if (!groups || n_groups < 1) return RD_ERR_INVALID_ARG;
+    std::vector<std::pair<int64_t, int64_t>> iv;
+    for (int32_t i = 0; i < n_groups; ++i) {
+        const rd_group &g = groups[i];
+        if (g.model != RD_FHN && g.model != RD_GM && g.model != RD_DIFF) return RD_ERR_INVALID_ARG;
+        if (g.G != 32 && g.G != 64 && g.G != 128) return RD_ERR_INVALID_ARG;
+        if (g.n_real < 1 || g.n_steps < 0 || g.field_offset < 0 || (g.field_offset & 3)) return RD_ERR_INVALID_ARG;
+        if (!(g.dt > 0.0) || !std::isfinite(g.dt)) return RD_ERR_INVALID_ARG;
+        for (double p : g.params)
+            if (!std::isfinite(p)) return RD_ERR_INVALID_ARG;
+        if (g.model == RD_GM && !(g.params[3] != 0.0)) return RD_ERR_INVALID_ARG;
+        if (!(g.noise_lo <= g.noise_hi)) return RD_ERR_INVALID_ARG;
+        int64_t len = (int64_t)g.n_real * 2 * g.G * g.G;
+        iv.emplace_back(g.field_offset, g.field_offset + len);
+    }
+    std::sort(iv.begin(), iv.end());
+    for (size_t i = 1; i < iv.size(); ++i)
+        if (iv[i].first < iv[i - 1].second) return RD_ERR_INVALID_ARG;
+    return RD_OK;
+}
+
+extern "C" rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_fields, void *stream,
+                             rd_handle **out) {
+    if (!out || !d_fields || ((uintptr_t)d_fields & 15)) return RD_ERR_INVALID_ARG;
+    *out = nullptr;
+    rd_status st = validate_groups(groups, n_groups);
+    if (st) return st;
+    rd_handle *hh = new (std::nothrow) rd_handle();
+    if (!hh) return RD_ERR_OOM;
+    Handle &h = hh->h;
+    if (cudaGetDevice(&h.device) != cudaSuccess) { delete hh; return RD_ERR_CUDA; }
+    h.n_groups = n_groups;
+    h.h_groups = new (std::nothrow) GroupDev[n_groups];
+    if (!h.h_groups) { delete hh; return RD_ERR_OOM; }
+    int64_t base = 0;
+    for (int32_t i = 0; i < n_groups; ++i) {
+        const rd_group &g = groups[i];
+        GroupDev &d = h.h_groups[i];
+        d.model = g.model; d.G = g.G; d.n_real = g.n_real; d.flags = g.flags;
+        d.n_steps = g.n_steps; d.field_offset = g.field_offset; d.dt = g.dt;
+        for (int k = 0; k < 4; ++k) d.p[k] = g.params[k];
+        d.noise_lo = g.noise_lo; d.noise_hi = g.noise_hi; d.seed = g.seed;
+        d.real_base = base;
+        base += g.n_real;
+    }
+    h.n_real_total = base;
+    if (cudaMalloc(&h.d_groups, sizeof(GroupDev) * n_groups) != cudaSuccess ||
+        cudaMalloc(&h.d_status, sizeof(uint32_t)) != cudaSuccess) {
+        rd_free(hh);
+        return RD_ERR_OOM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(h.d_groups, h.h_groups, sizeof(GroupDev) * n_groups, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemsetAsync(h.d_status, 0, sizeof(uint32_t), s) != cudaSuccess) {
+        rd_free(hh);
+        return RD_ERR_CUDA;
+    }
+    st = adjoint_reserve(h);
+    if (st) { rd_free(hh); return st; }
+    for (int32_t i = 0; i < n_groups; ++i) {
+        st = launch_init_fields(h.h_groups[i], d_fields, s);
+        if (st) { rd_free(hh); return st; }
+    }
+    // the group table is read by the host copy only after this point; make
+    // sure the pageable source of the async copy is no longer needed
+    if (cudaStreamSynchronize(s) != cudaSuccess) { rd_free(hh); return RD_ERR_CUDA; }
+    *out = hh;
+    return RD_OK;
+}
+
+extern "C" rd_status rd_reinit(rd_handle *hh, float *d_fields, void *stream) {
+    if (!hh || !d_fields || ((uintptr_t)d_fields & 15)) return RD_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < hh->h.n_groups; ++i) {
+        rd_status st = launch_init_fields(hh->h.h_groups[i], d_fields, (cudaStream_t)stream);
+        if (st) return st;
+    }
+    return RD_OK;
+}
+
+extern "C" rd_status rd_integrate_batch(rd_handle *hh, float *d_fields, int64_t steps_override, double *d_residual,
+                                        void *stream) {
+    if (!hh || !d_fields || ((uintptr_t)d_fields & 15)) return RD_ERR_INVALID_ARG;
+    Handle &h = hh->h;
+    for (int32_t i = 0; i < h.n_groups; ++i) {
+        const GroupDev &g = h.h_groups[i];
+        int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
+        rd_status st = launch_integrate_group(g, d_fields, steps, d_residual, h.d_status, (cudaStream_t)stream);
+        if (st) return st;
+    }
+    return RD_OK;
+}
+
+extern "C" rd_status rd_integrate_reference(rd_handle *hh, float *d_fields, float *d_tmp, int64_t steps_override,
+                                            void *stream) {
+    if (!hh || !d_fields || !d_tmp) return RD_ERR_INVALID_ARG;
+    Handle &h = hh->h;
+    for (int32_t i = 0; i < h.n_groups; ++i) {
+        const GroupDev &g = h.h_groups[i];
+        int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
+        rd_status st = launch_integrate_reference(g, d_fields, d_tmp, steps, (cudaStream_t)stream);
+        if (st) return st;
+    }
+    return RD_OK;
+}
+
+extern "C" rd_status rd_integrate_f64(rd_handle *hh, double *d_fields64, double *d_tmp64, int64_t steps_override,
+                                      void *stream) {
+    if (!hh || !d_fields64 || !d_tmp64) return RD_ERR_INVALID_ARG;
+    Handle &h = hh->h;
+    for (int32_t i = 0; i < h.n_groups; ++i) {
+        const GroupDev &g = h.h_groups[i];
+        int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
+        rd_status st = launch_integrate_f64(g, d_fields64, d_tmp64, steps, (cudaStream_t)stream);
+        if (st) return st;
+    }
+    return RD_OK;
+}
+
+extern "C" rd_status rd_sync_status(rd_handle *hh, void *stream) {
+    if (!hh) return RD_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t v = 0;
+    if (cudaMemcpyAsync(&v, hh->h.d_status, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RD_ERR_CUDA;
+    if (cudaMemsetAsync(hh->h.d_status, 0, sizeof(uint32_t), s) != cudaSuccess) return RD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RD_ERR_CUDA;
+    if (v & ST_TIMEOUT) return RD_ERR_TIMEOUT;
+    if (v & ST_NONFINITE) return RD_ERR_NONFINITE;
+    return RD_OK;
+}
+
+extern "C" int64_t rd_n_real_total(const rd_handle *hh) { return hh ? hh->h.n_real_total : -1; }
+
+extern "C" void rd_free(rd_handle *hh) {
+    if (!hh) return;
+    Handle &h = hh->h;
+    adjoint_release(h);
+    if (h.d_groups) cudaFree(h.d_groups);
+    if (h.d_status) cudaFree(h.d_status);
+    delete[] h.h_groups;
+    delete hh;
+}
+
+extern "C" const char *rd_status_str(rd_status s) {
+    switch (s) {
+        case RD_OK: return "ok";
+        case RD_ERR_INVALID_ARG: return "invalid argument";
+        case RD_ERR_CUDA: return "CUDA error";
+        case RD_ERR_NOT_PD: return "covariance not positive definite";
+        case RD_ERR_TIMEOUT: return "device wait timed out";
+        case RD_ERR_NONFINITE: return "non-finite field";
+        case RD_ERR_UNSUPPORTED: return "unsupported configuration";
+        case RD_ERR_OOM: return "out of device memory";
+        default: return "unknown status";
+    }
+}
+
+#include <atomic>
+static std::atomic<uint64_t> g_launches{0};
+void rdcil::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" uint64_t rd_kernel_launches(void) { return g_launches.load(); }

@@ -1,0 +1,427 @@
+// Correlation integral of two pattern sets (eq. eCDF, eq. CIL, Sec. 2.1).
+//
+// Exactness contract.  For every pair the library decides K_ij =
+// #{k : d2_ij < R_k^2} for the canonical d2_ij = sum_t (x_t - y_t)^2 summed
+// in t order in FP64 without FMA.  It does so in three stages:
+//   1. pack:  centre every pattern by the set mean c (translation does not
+//      change distances), split x - c into bf16 hi + lo, and record per
+//      pattern N = |hi+lo|^2, H = |hi| + |lo|, L = |lo| and the
+//      representation error E = |(x - c) - (hi + lo)| (all FP64);
+//   2. Gram:  P_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j (bf16 products, FP32
+//      accumulation per K-chunk, chunks summed in FP64);
+//   3. bound: A = N_i + N_j - 2 P_ij approximates d2_ij with a rigorous error
+//      bound built from the FP32 accumulation model, the dropped lo.lo term,
+//      E_i + E_j and the rounding of the canonical sum.  A pair whose interval
+//      [A - m, A + m] contains a threshold (or could hold the maximum that
+//      defines R0) is re-evaluated with the canonical sum.
+// Counts per radius are reduced with warp ballot + popc.
+#include <cstdio>
+#include <cuda_bf16.h>
+#include "common.cuh"
+
+namespace rdcil {
+
+static constexpr int KCHUNK = 2048;      // split-K chunk (bounds FP32 accumulation error)
+static constexpr int PAD = 64;           // padded pattern length granularity
+
+static inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+struct CilWork {
+    int64_t n1, n2, d, dp, nchunk;
+    float *centre;          // [dp]
+    __nv_bfloat16 *hi;      // [(n1+n2)][dp]
+    __nv_bfloat16 *lo;      // [(n1+n2)][dp]
+    double *N, *H, *L, *E;  // [(n1+n2)]
+    float *Ppart;           // [nchunk][n1][n2]
+    double *A, *Mg;         // [n1*n2] approximate d2 and its error bound
+    unsigned long long *scal;  // [0] max lower bound bits, [1] exact max bits, [2] n_rechecked
+    size_t bytes;
+};
+
+static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
+    CilWork w{};
+    w.n1 = n1; w.n2 = n2; w.d = d;
+    w.dp = round_up(d, PAD);
+    w.nchunk = (w.dp + KCHUNK - 1) / KCHUNK;
+    int64_t n = n1 + n2;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = (size_t)round_up((int64_t)(off + bytes), 256);
+        return (char *)base + o;
+    };
+    w.centre = (float *)take(sizeof(float) * w.dp);
+    w.hi = (__nv_bfloat16 *)take(sizeof(__nv_bfloat16) * n * w.dp);
+    w.lo = (__nv_bfloat16 *)take(sizeof(__nv_bfloat16) * n * w.dp);
+    w.N = (double *)take(sizeof(double) * n);
+    w.H = (double *)take(sizeof(double) * n);
+    w.L = (double *)take(sizeof(double) * n);
+    w.E = (double *)take(sizeof(double) * n);
+    w.Ppart = (float *)take(sizeof(float) * w.nchunk * n1 * n2);
+    w.A = (double *)take(sizeof(double) * n1 * n2);
+    w.Mg = (double *)take(sizeof(double) * n1 * n2);
+    w.scal = (unsigned long long *)take(sizeof(unsigned long long) * 4);
+    w.bytes = off;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// canonical distance: sequential FP64, no FMA
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double canonical_d2(const float *__restrict__ x, const float *__restrict__ y,
+                                               int64_t d) {
+    double acc = 0.0;
+    for (int64_t t = 0; t < d; ++t) {
+        double df = __dsub_rn((double)__ldg(x + t), (double)__ldg(y + t));
+        acc = __dadd_rn(acc, __dmul_rn(df, df));
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// 1. centre and pack
+// ---------------------------------------------------------------------------
+__global__ void centre_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n1,
+                              const float *__restrict__ X2, int64_t ld2, int64_t n2, int64_t d,
+                              int64_t dp, float *__restrict__ centre) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= dp) return;
+    if (t >= d) { centre[t] = 0.f; return; }
+    double s = 0.0;
+    for (int64_t i = 0; i < n1; ++i) s += (double)X1[i * ld1 + t];
+    for (int64_t j = 0; j < n2; ++j) s += (double)X2[j * ld2 + t];
+    centre[t] = (float)(s / (double)(n1 + n2));
+}
+
+__global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n1,
+                            const float *__restrict__ X2, int64_t ld2, int64_t d, int64_t dp,
+                            const float *__restrict__ centre, __nv_bfloat16 *__restrict__ hi,
+                            __nv_bfloat16 *__restrict__ lo, double *__restrict__ Nn, double *__restrict__ Hn,
+                            double *__restrict__ Ln, double *__restrict__ En) {
+    const int64_t i = blockIdx.x;
+    const float *x = i < n1 ? X1 + i * ld1 : X2 + (i - n1) * ld2;
+    double sN = 0.0, sH = 0.0, sL = 0.0, sE = 0.0;
+    for (int64_t t = threadIdx.x; t < dp; t += blockDim.x) {
+        __nv_bfloat16 h = __float2bfloat16_rn(0.f), l = __float2bfloat16_rn(0.f);
+        if (t < d) {
+            float xv = x[t], cv = centre[t];
+            float xc = xv - cv;
+            h = __float2bfloat16_rn(xc);
+            float r = xc - __bfloat162float(h);   // exact in FP32
+            l = __float2bfloat16_rn(r);
+            double hd = (double)__bfloat162float(h), ld = (double)__bfloat162float(l);
+            double s = hd + ld;                    // exact
+            sN += s * s;
+            sH += hd * hd;
+            sL += ld * ld;
+            double e = ((double)xv - (double)cv) - s;
+            sE += e * e;
+        }
+        hi[i * dp + t] = h;
+        lo[i * dp + t] = l;
+    }
+    __shared__ double red[4][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sN += __shfl_xor_sync(0xffffffffu, sN, o);
+        sH += __shfl_xor_sync(0xffffffffu, sH, o);
+        sL += __shfl_xor_sync(0xffffffffu, sL, o);
+        sE += __shfl_xor_sync(0xffffffffu, sE, o);
+    }
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][warp] = sN; red[1][warp] = sH; red[2][warp] = sL; red[3][warp] = sE; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0, e = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; c += red[2][w]; e += red[3][w]; }
+        // FP64 sums of d non-negative terms: relative error below d*2^-53;
+        // inflate so the recorded values are upper bounds where needed.
+        double infl = 1.0 + (double)(dp + 8) * 2.3e-16;
+        Nn[i] = a;
+        Hn[i] = (sqrt(b) + sqrt(c)) * infl;
+        Ln[i] = sqrt(c) * infl;
+        En[i] = sqrt(e) * infl * (1.0 + 1e-12) + 1e-300;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. Gram product on CUDA cores (bf16 operands, FP32 accumulation, split-K)
+//    tile 64x64 pairs, K step 32, 256 threads, 4x4 outputs per thread
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) gram_simt_kernel(const __nv_bfloat16 *__restrict__ hi,
+                                                        const __nv_bfloat16 *__restrict__ lo, int64_t n1,
+                                                        int64_t n2, int64_t dp, float *__restrict__ Ppart) {
+    __shared__ float sAh[32][65], sAl[32][65], sBh[32][65], sBl[32][65];
+    const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
+    const int64_t k_begin = (int64_t)blockIdx.z * KCHUNK;
+    const int64_t k_end = min(dp, k_begin + KCHUNK);
+    const int tid = threadIdx.x;
+    const int ti = tid / 16, tj = tid % 16;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    const __nv_bfloat16 *Bh = hi + n1 * dp, *Bl = lo + n1 * dp;
+    for (int64_t k0 = k_begin; k0 < k_end; k0 += 32) {
+        for (int q = tid; q < 64 * 32; q += 256) {
+            int r = q / 32, c = q % 32;
+            int64_t ia = i0 + r, jb = j0 + r;
+            sAh[c][r] = ia < n1 ? __bfloat162float(hi[ia * dp + k0 + c]) : 0.f;
+            sAl[c][r] = ia < n1 ? __bfloat162float(lo[ia * dp + k0 + c]) : 0.f;
+            sBh[c][r] = jb < n2 ? __bfloat162float(Bh[jb * dp + k0 + c]) : 0.f;
+            sBl[c][r] = jb < n2 ? __bfloat162float(Bl[jb * dp + k0 + c]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int c = 0; c < 32; ++c) {
+            float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                ah[a] = sAh[c][ti * 4 + a]; al[a] = sAl[c][ti * 4 + a];
+                bh[a] = sBh[c][tj * 4 + a]; bl[a] = sBl[c][tj * 4 + a];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    acc[a][b] = fmaf(ah[a], bh[b], acc[a][b]);
+                    acc[a][b] = fmaf(ah[a], bl[b], acc[a][b]);
+                    acc[a][b] = fmaf(al[a], bh[b], acc[a][b]);
+                }
+        }
+        __syncthreads();
+    }
+    float *out = Ppart + (int64_t)blockIdx.z * n1 * n2;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int64_t i = i0 + ti * 4 + a, j = j0 + tj * 4 + b;
+            if (i < n1 && j < n2) out[i * n2 + j] = acc[a][b];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// 3a. approximate d2 and its rigorous error bound; running max lower bound
+// ---------------------------------------------------------------------------
+// Accumulation model for the Gram: a sequence of n roundings into one FP32
+// accumulator errs by at most n * u * S, S = sum of the magnitudes of the
+// products, u the unit roundoff of one accumulation step (gam = n * u is
+// passed in per Gram kernel).  Here S = sum |hi||hi'| + |hi||lo'| + |lo||hi'|
+// <= H_i H_j.  The dropped lo.lo' term is bounded by L_i L_j.
+__device__ __forceinline__ void approx_and_bound(const CilWork &w, int64_t i, int64_t j, double P,
+                                                 double gam, double &A, double &m) {
+    const int64_t a = i, b = w.n1 + j;
+    const double Ni = w.N[a], Nj = w.N[b];
+    A = (Ni + Nj) - 2.0 * P;
+    double eg = 2.0 * (gam * w.H[a] * w.H[b] + w.L[a] * w.L[b]) +
+                4.0 * (double)(w.dp + 8) * 1.1102230246251565e-16 * (Ni + Nj + 2.0 * fabs(P));
+    double up = fmax(A + eg, 0.0);
+    double D = w.E[a] + w.E[b];
+    double er = D * (2.0 * sqrt(up) + D);
+    double ec = (double)(w.d + 8) * 2.220446049250313e-16 * (up + er);
+    m = 2.0 * (eg + er + ec) + 1e-300;
+}
+
+__global__ void d2_bound_kernel(CilWork w, double gam) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t np = w.n1 * w.n2;
+    double lb = 0.0;
+    if (q < np) {
+        int64_t i = q / w.n2, j = q - i * w.n2;
+        double P = 0.0;
+        for (int64_t c = 0; c < w.nchunk; ++c) P += (double)w.Ppart[c * np + q];
+        double A, m;
+        approx_and_bound(w, i, j, P, gam, A, m);
+        w.A[q] = A;
+        w.Mg[q] = m;
+        lb = fmax(A - m, 0.0);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lb = fmax(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&w.scal[0], (unsigned long long)__double_as_longlong(lb));
+}
+
+// 3b. exact maximum over the pairs that could hold it (upper bound >= the
+//     largest lower bound); canonical sums only for those.
+__global__ void exact_max_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
+                                 const float *__restrict__ X2, int64_t ld2) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t np = w.n1 * w.n2;
+    if (q >= np) return;
+    double lbmax = __longlong_as_double((long long)w.scal[0]);
+    if (w.A[q] + w.Mg[q] < lbmax) return;
+    int64_t i = q / w.n2, j = q - i * w.n2;
+    double e = canonical_d2(X1 + i * ld1, X2 + j * ld2, w.d);
+    atomicMax(&w.scal[1], (unsigned long long)__double_as_longlong(e));
+    atomicAdd(&w.scal[2], 1ull);
+}
+
+// 3c. radii: R0 = sqrt(max), R_k = R_{k-1}/b  (or copy the given radii)
+__global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M,
+                             double *__restrict__ radii_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (radii_in) {
+        radii_out[0] = __longlong_as_double(0x7ff8000000000000ll);
+        for (int k = 0; k < M; ++k) radii_out[k + 1] = radii_in[k];
+        return;
+    }
+    double R = __dsqrt_rn(__longlong_as_double((long long)w.scal[1]));
+    radii_out[0] = R;
+    for (int k = 0; k < M; ++k) {
+        R = __ddiv_rn(R, b);
+        radii_out[k + 1] = R;
+    }
+}
+
+// 3d. bins and counts.  A pair is classified from [A - m, A + m] when no
+//     threshold T_k = R_k*R_k falls inside; otherwise from the canonical sum.
+__global__ void bins_counts_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
+                                   const float *__restrict__ X2, int64_t ld2,
+                                   const double *__restrict__ radii_out, int M, int exact_all,
+                                   uint8_t *__restrict__ bins, unsigned long long *__restrict__ counts) {
+    __shared__ double Tk[32];
+    __shared__ unsigned long long cnt[32];
+    if (threadIdx.x < 32) {
+        cnt[threadIdx.x] = 0ull;
+        if ((int)threadIdx.x < M) {
+            double r = radii_out[threadIdx.x + 1];
+            Tk[threadIdx.x] = __dmul_rn(r, r);
+        }
+    }
+    __syncthreads();
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t np = w.n1 * w.n2;
+    int K = 0;
+    if (q < np) {
+        bool amb = exact_all != 0;
+        double A = 0.0, m = 0.0;
+        if (!amb) {
+            A = w.A[q];
+            m = w.Mg[q];
+            for (int k = 0; k < M; ++k) {
+                double T = Tk[k];
+                if (A + m < T) K++;
+                else if (!(A - m >= T)) amb = true;
+            }
+        }
+        if (amb) {
+            int64_t i = q / w.n2, j = q - i * w.n2;
+            double e = canonical_d2(X1 + i * ld1, X2 + j * ld2, w.d);
+            K = 0;
+            for (int k = 0; k < M; ++k) K += (e < Tk[k]) ? 1 : 0;
+            if (!exact_all) atomicAdd(&w.scal[2], 1ull);
+        }
+        bins[q] = (uint8_t)K;
+    }
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < M; ++k) {
+        unsigned bal = __ballot_sync(0xffffffffu, K >= k + 1);
+        if (lane == 0 && bal) atomicAdd(&cnt[k], (unsigned long long)__popc(bal));
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < M && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], cnt[threadIdx.x]);
+}
+
+// exact path: canonical sum for every pair into A (used for the maximum)
+__global__ void exact_all_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
+                                 const float *__restrict__ X2, int64_t ld2) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t np = w.n1 * w.n2;
+    if (q >= np) return;
+    int64_t i = q / w.n2, j = q - i * w.n2;
+    double e = canonical_d2(X1 + i * ld1, X2 + j * ld2, w.d);
+    atomicMax(&w.scal[1], (unsigned long long)__double_as_longlong(e));
+}
+
+__global__ void finish_kernel(CilWork w, int64_t *n_rechecked, const int64_t *counts, int M, double *Cv) {
+    if (blockIdx.x != 0) return;
+    if (threadIdx.x == 0 && n_rechecked) *n_rechecked = (int64_t)w.scal[2];
+    if (Cv && (int)threadIdx.x < M)
+        Cv[threadIdx.x] = __ddiv_rn((double)counts[threadIdx.x], (double)w.n1 * (double)w.n2);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static rd_status check_args(int64_t ld1, int64_t n1, int64_t ld2, int64_t n2, int64_t d,
+                            const double *radii_in, double b, int M) {
+    if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535 || d < 1) return RD_ERR_INVALID_ARG;
+    if (ld1 < d || ld2 < d) return RD_ERR_INVALID_ARG;
+    if (M < 1 || M > 32) return RD_ERR_INVALID_ARG;
+    if (!radii_in && !(b > 1.0)) return RD_ERR_INVALID_ARG;
+    return RD_OK;
+}
+
+}  // namespace rdcil
+
+using namespace rdcil;
+
+extern "C" rd_status cil_workspace_size(int64_t n1, int64_t n2, int64_t d, size_t *bytes) {
+    if (!bytes || n1 < 1 || n2 < 1 || d < 1) return RD_ERR_INVALID_ARG;
+    CilWork w = layout(n1, n2, d, nullptr);
+    *bytes = w.bytes;
+    return RD_OK;
+}
+
+static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *X2, int64_t ld2, int64_t n2,
+                         int64_t d, const double *radii_in, double b, int32_t M, double *radii_out,
+                         uint8_t *bins, int64_t *counts, double *Cv, int64_t *n_rechecked, void *work,
+                         size_t work_bytes, void *stream, bool exact) {
+    rd_status st = check_args(ld1, n1, ld2, n2, d, radii_in, b, M);
+    if (st) return st;
+    if (!X1 || !X2 || !radii_out || !bins || !counts || !work) return RD_ERR_INVALID_ARG;
+    if (((uintptr_t)work & 255) != 0) return RD_ERR_INVALID_ARG;
+    CilWork w = layout(n1, n2, d, work);
+    if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t np = n1 * n2;
+    unsigned gp = (unsigned)((np + 255) / 256);
+    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 4 * sizeof(unsigned long long), s));
+    RD_CUDA_TRY(cudaMemsetAsync(counts, 0, M * sizeof(int64_t), s));
+    if (exact) {
+        if (!radii_in) exact_all_kernel<<<gp, 256, 0, s>>>(w, X1, ld1, X2, ld2);
+        note_launch();
+    } else {
+        centre_kernel<<<(unsigned)((w.dp + 255) / 256), 256, 0, s>>>(X1, ld1, n1, X2, ld2, n2, d, w.dp, w.centre);
+        note_launch();
+        pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(X1, ld1, n1, X2, ld2, d, w.dp, w.centre, w.hi, w.lo, w.N,
+                                                        w.H, w.L, w.E);
+        note_launch();
+        dim3 gg((unsigned)((n2 + 63) / 64), (unsigned)((n1 + 63) / 64), (unsigned)w.nchunk);
+        gram_simt_kernel<<<gg, 256, 0, s>>>(w.hi, w.lo, n1, n2, w.dp, w.Ppart);
+        note_launch();
+        // SIMT Gram: 3*KCHUNK fused multiply-adds per accumulator, each
+        // rounding to nearest (2^-24), plus margin for the chunk bookkeeping.
+        const double gam = (3.0 * KCHUNK + 64.0) * 5.9604644775390625e-8;
+        d2_bound_kernel<<<gp, 256, 0, s>>>(w, gam);
+        note_launch();
+        if (!radii_in) exact_max_kernel<<<gp, 256, 0, s>>>(w, X1, ld1, X2, ld2);
+        note_launch();
+    }
+    radii_kernel<<<1, 32, 0, s>>>(w, radii_in, b, M, radii_out);
+    note_launch();
+    bins_counts_kernel<<<gp, 256, 0, s>>>(w, X1, ld1, X2, ld2, radii_out, M, exact ? 1 : 0, bins,
+                                          (unsigned long long *)counts);
+    note_launch();
+    finish_kernel<<<1, 32, 0, s>>>(w, n_rechecked, counts, M, Cv);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
+                                  int64_t n2, int64_t d, const double *d_radii_in, double b, int32_t M,
+                                  double *d_radii_out, uint8_t *d_bins, int64_t *d_counts, double *d_C,
+                                  int64_t *d_n_rechecked, void *d_work, size_t work_bytes, void *stream) {
+    return cil_run(d_X1, ld1, n1, d_X2, ld2, n2, d, d_radii_in, b, M, d_radii_out, d_bins, d_counts, d_C,
+                   d_n_rechecked, d_work, work_bytes, stream, false);
+}
+
+extern "C" rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                        int64_t ld2, int64_t n2, int64_t d, const double *d_radii_in, double b,
+                                        int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
+                                        double *d_C, void *d_work, size_t work_bytes, void *stream) {
+    return cil_run(d_X1, ld1, n1, d_X2, ld2, n2, d, d_radii_in, b, M, d_radii_out, d_bins, d_counts, d_C,
+                   nullptr, d_work, work_bytes, stream, true);
+}

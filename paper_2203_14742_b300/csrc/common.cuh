@@ -1,0 +1,77 @@
+// Internal declarations shared by the CUDA translation units of librdcil.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+#include "../../include/rdcil.h"
+
+namespace rdcil {
+
+// Device status word bits (the handle's status word is an OR of these).
+enum : uint32_t {
+    ST_NONFINITE = 1u,
+    ST_TIMEOUT = 2u,
+};
+
+// SplitMix64 (Steele, Lea & Flood 2014): output number i of the stream that
+// starts at state `seed` is the Stafford variant-13 finaliser applied to
+// seed + (i+1)*0x9E3779B97F4A7C15.
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Device copy of one group plus derived FP32 coefficients.
+struct GroupDev {
+    int32_t model, G, n_real, flags;
+    int64_t n_steps, field_offset;
+    double dt;
+    double p[4];
+    double noise_lo, noise_hi;
+    uint64_t seed;
+    int64_t real_base;   // index of this group's first realisation overall
+};
+
+struct Handle {
+    int device;
+    int32_t n_groups;
+    int64_t n_real_total;
+    GroupDev *h_groups;       // host copy
+    GroupDev *d_groups;       // device copy
+    uint32_t *d_status;       // device status word
+    // adjoint scratch (checkpoints + per-segment trajectory + lambda)
+    float *d_ckpt;
+    size_t ckpt_floats;
+    double *d_adj_scratch;
+    size_t adj_scratch_doubles;
+    // cached launch plan
+    void *plan;
+};
+
+inline rd_status cuda_status(cudaError_t e) {
+    return e == cudaSuccess ? RD_OK : RD_ERR_CUDA;
+}
+
+#define RD_CUDA_TRY(expr)                                  \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return RD_ERR_CUDA;         \
+    } while (0)
+
+// Count of kernels this library has launched (its own kernels only).
+void note_launch();
+
+// ---- launchers implemented in the kernel translation units --------------
+rd_status launch_init_fields(const GroupDev &g, float *fields, cudaStream_t s);
+rd_status launch_integrate_group(const GroupDev &g, float *fields, int64_t steps,
+                                 double *residual, uint32_t *status, cudaStream_t s);
+rd_status launch_integrate_reference(const GroupDev &g, float *fields, float *tmp,
+                                     int64_t steps, cudaStream_t s);
+rd_status launch_integrate_f64(const GroupDev &g, double *fields, double *tmp, int64_t steps,
+                               cudaStream_t s);
+rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int64_t steps,
+                              cudaStream_t s);
+
+}  // namespace rdcil

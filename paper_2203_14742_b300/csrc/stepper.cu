@@ -1,0 +1,355 @@
+// Reaction-diffusion initial state and explicit Euler steppers.
+//
+// Paper (arXiv 2203.14742): kinetics Sec. 4.1 (FHN eq. introduction:0, GM
+// eq. gmSystem); initial state = equilibrium + U(0, delta), Sec. 4.1; method
+// of lines with the 5-point Laplacian and mirrored Neumann ghosts,
+// App. B.1.1; explicit Euler, Sec. 5.1 (the paper's earlier GPU solver also
+// keeps one whole simulation per thread block, on-chip, for the whole run).
+//
+// Kernels
+//   init_fields_kernel       counter-based noise, FP64 then one rounding to FP32
+//   rd_resident_kernel<...>  one realisation per CTA, the whole field held in
+//                            registers as TYxTX tiles per thread for the whole
+//                            run; north/south tile edges exchanged through a
+//                            double-buffered shared-memory ring (one barrier
+//                            per step), east/west edges through warp shuffles;
+//                            FP64 residual reduced with warp shuffles at exit
+//   rd_reference_step_kernel one cell per thread, one step and one realisation
+//                            per launch (the plain path for comparison)
+//   rd_f64_step_kernel       FP64 in the paper's operation order, no FMA
+#include <cstdio>
+#include "tile.cuh"
+
+namespace rdcil {
+
+// ---------------------------------------------------------------------------
+// initial state
+// ---------------------------------------------------------------------------
+__global__ void init_fields_kernel(float *__restrict__ out, int64_t n_total, int64_t cells,
+                                   uint64_t seed, double x0u, double x0v, double lo, double hi) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_total; i += stride) {
+        // i = (r*2 + s)*cells + c is exactly the generator counter
+        int64_t rs = i / cells;
+        int s = (int)(rs & 1);
+        uint64_t z = splitmix64_at(seed, (uint64_t)i);
+        double U = __dmul_rn(__ull2double_rn(z >> 11), 1.1102230246251565404e-16);  // 2^-53
+        double span = __dsub_rn(hi, lo);
+        double t = __dmul_rn(span, U);
+        double t2 = __dadd_rn(lo, t);
+        double v = __dadd_rn(s ? x0v : x0u, t2);
+        out[i] = __double2float_rn(v);
+    }
+}
+
+static void equilibrium(const GroupDev &g, double &u0, double &v0) {
+    if (g.model == RD_GM) {
+        volatile double a = 1.0 / g.p[3];
+        u0 = a;
+        v0 = a * a;
+    } else {
+        u0 = 0.0;
+        v0 = 0.0;
+    }
+}
+
+rd_status launch_init_fields(const GroupDev &g, float *fields, cudaStream_t s) {
+    double u0, v0;
+    equilibrium(g, u0, v0);
+    int64_t cells = (int64_t)g.G * g.G;
+    int64_t n = (int64_t)g.n_real * 2 * cells;
+    int block = 256;
+    int64_t grid = (n + block - 1) / block;
+    if (grid > 148 * 32) grid = 148 * 32;
+    init_fields_kernel<<<(unsigned)grid, block, 0, s>>>(fields + g.field_offset, n, cells, g.seed,
+                                                        u0, v0, g.noise_lo, g.noise_hi);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+// FP64 right-hand side at one node from FP32 neighbours (used for the
+// residual; operation order of the plain definition).
+template <int MODEL>
+__device__ __forceinline__ void rhs_f64(double u, double v, double nu, double su, double wu, double eu,
+                                        double nv, double sv, double wv, double ev, const double *p,
+                                        double h2, double &Fu, double &Fv) {
+    double lu = ((((eu + wu) + su) + nu) - 4.0 * u) * h2;
+    double lv = ((((ev + wv) + sv) + nv) - 4.0 * v) * h2;
+    double ru, rv;
+    if (MODEL == RD_FHN) {
+        ru = (u - (u * u) * u) - v;
+        rv = p[2] * (u - p[3] * v);
+    } else if (MODEL == RD_GM) {
+        double uu = u * u;
+        ru = p[2] * (uu / v - p[3] * u);
+        rv = p[2] * (uu - v);
+    } else {
+        ru = 0.0;
+        rv = 0.0;
+    }
+    Fu = p[0] * lu + ru;
+    Fv = p[1] * lv + rv;
+}
+
+// ---------------------------------------------------------------------------
+// Resident stepper: one realisation per CTA, field in registers for the
+// whole run.  RECORD = true stores the state before every step into
+// traj[n] (n = 0..steps-1, each 2*G*G floats per realisation, realisation
+// stride traj_stride) for the adjoint's segment recomputation.
+// ---------------------------------------------------------------------------
+template <int MODEL, int G, int TY, int TX, bool RECORD>
+__global__ void __launch_bounds__(Tiling<G, TY, TX>::NT, 1)
+rd_resident_kernel(float *__restrict__ fields, int64_t field_offset, int64_t steps, CoefF cf,
+                   double p0, double p1, double p2, double p3, double *__restrict__ residual,
+                   uint32_t *__restrict__ status, float *__restrict__ traj, int64_t traj_stride) {
+    using T = Tiling<G, TY, TX>;
+    constexpr int NX = T::NX;
+    extern __shared__ float4 smem_f4[];
+    float *sm = reinterpret_cast<float *>(smem_f4);
+
+    const int tid = threadIdx.x;
+    const int tx = tid % NX, ty = tid / NX;
+    const int r = blockIdx.x;
+    float *base = fields + field_offset + (int64_t)r * 2 * G * G;
+
+    float u[TY][TX], v[TY][TX];
+    tile_load<G, TY, TX>(base, tx, ty, u, v);
+
+    for (int64_t n = 0; n < steps; ++n) {
+        if (RECORD) tile_store<G, TY, TX>(traj + (int64_t)r * traj_stride + n * 2 * G * G, tx, ty, u, v);
+        float *hb = sm + (int)(n & 1) * (T::HALO_FLOATS / 2);
+        halo_put<G, TY, TX>(hb, tx, ty, u, v);
+        __syncthreads();
+        tile_step<MODEL, G, TY, TX>(hb, tx, ty, u, v, cf);
+    }
+    tile_store<G, TY, TX>(base, tx, ty, u, v);
+    if (RECORD) return;
+
+    // ---- FP64 steady-state residual of the final state -------------------
+    float *hb = sm + (int)(steps & 1) * (T::HALO_FLOATS / 2);
+    halo_put<G, TY, TX>(hb, tx, ty, u, v);
+    __syncthreads();
+    const double p[4] = {p0, p1, p2, p3};
+    const double h2 = (double)(G - 1) * (double)(G - 1);
+    double mx = 0.0, ss = 0.0;
+    bool bad = false;
+    float pu[TX], pv[TX];
+    halo_north<G, TY, TX>(hb, tx, ty, u, v, pu, pv);
+#pragma unroll
+    for (int i = 0; i < TY; ++i) {
+        float su[TX], sv[TX];
+        row_south<G, TY, TX>(hb, tx, ty, i, u, v, su, sv);
+        float wu, eu, wv, ev;
+        row_west_east<NX>(tx, u[i][0], u[i][TX - 1], wu, eu);
+        row_west_east<NX>(tx, v[i][0], v[i][TX - 1], wv, ev);
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            float Wu = c > 0 ? u[i][c - 1] : wu, Eu = c < TX - 1 ? u[i][c + 1] : eu;
+            float Wv = c > 0 ? v[i][c - 1] : wv, Ev = c < TX - 1 ? v[i][c + 1] : ev;
+            double Fu, Fv;
+            rhs_f64<MODEL>(u[i][c], v[i][c], pu[c], su[c], Wu, Eu, pv[c], sv[c], Wv, Ev, p, h2, Fu, Fv);
+            bad |= !isfinite(u[i][c]) || !isfinite(v[i][c]) || !isfinite(Fu) || !isfinite(Fv);
+            mx = fmax(mx, fmax(fabs(Fu), fabs(Fv)));
+            ss += Fu * Fu + Fv * Fv;
+        }
+#pragma unroll
+        for (int c = 0; c < TX; ++c) { pu[c] = u[i][c]; pv[c] = v[i][c]; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    }
+    int anybad = __syncthreads_or(bad ? 1 : 0);
+    // the other halo buffer is free: reuse it for the cross-warp reduction
+    double *red = reinterpret_cast<double *>(sm + (int)((steps + 1) & 1) * (T::HALO_FLOATS / 2));
+    const int warp = tid >> 5, lane = tid & 31;
+    constexpr int NW = T::NT / 32;
+    if (lane == 0) { red[warp] = mx; red[NW + warp] = ss; }
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0, s = 0.0;
+        for (int w = 0; w < NW; ++w) { m = fmax(m, red[w]); s += red[NW + w]; }
+        if (anybad) {
+            atomicOr(status, (unsigned)ST_NONFINITE);
+            m = __longlong_as_double(0x7ff8000000000000ll);
+            s = m;
+        }
+        if (residual) {
+            residual[2 * r] = m;
+            residual[2 * r + 1] = sqrt(s / (double)(2 * G * G));
+        }
+    }
+}
+
+// Tile shapes per grid side (a per-G choice; see the tuning notes in the
+// design document): G=32 and G=64 use 4x4 tiles (64 / 256 threads), G=128
+// uses 8x4 tiles (512 threads) so the 64 state registers fit.
+template <int G> struct TileOf;
+template <> struct TileOf<32> { static constexpr int TY = 4, TX = 4; };
+template <> struct TileOf<64> { static constexpr int TY = 4, TX = 4; };
+template <> struct TileOf<128> { static constexpr int TY = 8, TX = 4; };
+
+template <int MODEL, int G, bool RECORD>
+static rd_status launch_resident(const GroupDev &g, float *fields, int64_t steps, double *residual,
+                                 uint32_t *status, float *traj, int64_t traj_stride, cudaStream_t s) {
+    constexpr int TY = TileOf<G>::TY, TX = TileOf<G>::TX;
+    using T = Tiling<G, TY, TX>;
+    auto kern = rd_resident_kernel<MODEL, G, TY, TX, RECORD>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM));
+        attr_set = true;
+    }
+    CoefF cf = make_coef(g);
+    kern<<<g.n_real, T::NT, T::SMEM, s>>>(fields, g.field_offset, steps, cf, g.p[0], g.p[1], g.p[2], g.p[3],
+                                          residual ? residual + 2 * g.real_base : nullptr, status, traj,
+                                          traj_stride);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+template <int MODEL, bool RECORD>
+static rd_status dispatch_G(const GroupDev &g, float *fields, int64_t steps, double *residual, uint32_t *status,
+                            float *traj, int64_t traj_stride, cudaStream_t s) {
+    switch (g.G) {
+        case 32: return launch_resident<MODEL, 32, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        case 64: return launch_resident<MODEL, 64, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        case 128: return launch_resident<MODEL, 128, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        default: return RD_ERR_UNSUPPORTED;
+    }
+}
+
+template <bool RECORD>
+static rd_status dispatch_model(const GroupDev &g, float *fields, int64_t steps, double *residual,
+                                uint32_t *status, float *traj, int64_t traj_stride, cudaStream_t s) {
+    switch (g.model) {
+        case RD_FHN: return dispatch_G<RD_FHN, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        case RD_GM: return dispatch_G<RD_GM, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        case RD_DIFF: return dispatch_G<RD_DIFF, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        default: return RD_ERR_UNSUPPORTED;
+    }
+}
+
+rd_status launch_integrate_group(const GroupDev &g, float *fields, int64_t steps, double *residual,
+                                 uint32_t *status, cudaStream_t s) {
+    return dispatch_model<false>(g, fields, steps, residual, status, nullptr, 0, s);
+}
+
+// traj holds, per realisation, `steps` states of 2*G*G floats back to back.
+rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int64_t steps, cudaStream_t s) {
+    return dispatch_model<true>(g, fields, steps, nullptr, nullptr, traj, steps * 2 * (int64_t)g.G * g.G, s);
+}
+
+// ---------------------------------------------------------------------------
+// Plain reference path: one cell per thread, one step of one realisation per
+// launch, reading src and writing dst in global memory.
+// ---------------------------------------------------------------------------
+template <int MODEL>
+__global__ void rd_reference_step_kernel(const float *__restrict__ src, float *__restrict__ dst, int G,
+                                         CoefF cf) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= G || y >= G) return;
+    const float *u = src, *v = src + G * G;
+    int k = y * G + x;
+    int kn = (y > 0 ? y - 1 : y) * G + x, ks = (y < G - 1 ? y + 1 : y) * G + x;
+    int kw = y * G + (x > 0 ? x - 1 : x), ke = y * G + (x < G - 1 ? x + 1 : x);
+    float lu = fmaf(-4.f, u[k], (u[kn] + u[ks]) + (u[kw] + u[ke]));
+    float lv = fmaf(-4.f, v[k], (v[kn] + v[ks]) + (v[kw] + v[ke]));
+    float un, vn;
+    euler_cell<MODEL>(u[k], v[k], lu, lv, cf, un, vn);
+    dst[k] = un;
+    dst[G * G + k] = vn;
+}
+
+rd_status launch_integrate_reference(const GroupDev &g, float *fields, float *tmp, int64_t steps,
+                                     cudaStream_t s) {
+    CoefF cf = make_coef(g);
+    dim3 blk(32, 8), grd((g.G + 31) / 32, (g.G + 7) / 8);
+    int64_t m = 2 * (int64_t)g.G * g.G;
+    for (int r = 0; r < g.n_real; ++r) {
+        float *a = fields + g.field_offset + r * m;
+        for (int64_t n = 0; n < steps; ++n) {
+            const float *src = (n & 1) ? tmp : a;
+            float *dst = (n & 1) ? a : tmp;
+            switch (g.model) {
+                case RD_FHN: rd_reference_step_kernel<RD_FHN><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
+                case RD_GM: rd_reference_step_kernel<RD_GM><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
+                default: rd_reference_step_kernel<RD_DIFF><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
+            }
+        }
+        if (steps & 1) RD_CUDA_TRY(cudaMemcpyAsync(a, tmp, m * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// FP64 path in the plain operation order (no fused multiply-add):
+//   lap = ((((w_{x+1} + w_{x-1}) + w_{y+1}) + w_{y-1}) - 4 w) * (G-1)^2
+//   F_u = Du*lap_u + R_u,  w <- w + dt*F
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double lap64(const double *w, int G, int y, int x) {
+    double c = w[y * G + x];
+    double xp = (x + 1 < G) ? w[y * G + x + 1] : c;
+    double xm = (x - 1 >= 0) ? w[y * G + x - 1] : c;
+    double yp = (y + 1 < G) ? w[(y + 1) * G + x] : c;
+    double ym = (y - 1 >= 0) ? w[(y - 1) * G + x] : c;
+    double g1 = (double)(G - 1);
+    double sum = __dadd_rn(__dadd_rn(__dadd_rn(xp, xm), yp), ym);
+    return __dmul_rn(__dsub_rn(sum, __dmul_rn(4.0, c)), __dmul_rn(g1, g1));
+}
+
+__global__ void rd_f64_step_kernel(const double *__restrict__ src, double *__restrict__ dst, int G,
+                                   int n_real, int model, double dt, double p0, double p1, double p2,
+                                   double p3) {
+    int64_t cells = (int64_t)G * G;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cells * n_real) return;
+    int64_t r = i / cells;
+    int k = (int)(i - r * cells);
+    int y = k / G, x = k - y * G;
+    const double *u = src + r * 2 * cells, *v = u + cells;
+    double lu = lap64(u, G, y, x), lv = lap64(v, G, y, x);
+    double du = __dmul_rn(p0, lu), dv = __dmul_rn(p1, lv);
+    double uk = u[k], vk = v[k], ru, rv;
+    if (model == RD_FHN) {
+        double u3 = __dmul_rn(__dmul_rn(uk, uk), uk);
+        ru = __dsub_rn(__dsub_rn(uk, u3), vk);
+        rv = __dmul_rn(p2, __dsub_rn(uk, __dmul_rn(p3, vk)));
+    } else if (model == RD_GM) {
+        double uu = __dmul_rn(uk, uk);
+        double q = __ddiv_rn(uu, vk);
+        ru = __dmul_rn(p2, __dsub_rn(q, __dmul_rn(p3, uk)));
+        rv = __dmul_rn(p2, __dsub_rn(uu, vk));
+    } else {
+        ru = 0.0;
+        rv = 0.0;
+    }
+    double Fu = __dadd_rn(du, ru), Fv = __dadd_rn(dv, rv);
+    double *ou = dst + r * 2 * cells, *ov = ou + cells;
+    ou[k] = __dadd_rn(uk, __dmul_rn(dt, Fu));
+    ov[k] = __dadd_rn(vk, __dmul_rn(dt, Fv));
+}
+
+rd_status launch_integrate_f64(const GroupDev &g, double *fields, double *tmp, int64_t steps,
+                               cudaStream_t s) {
+    int64_t m = 2 * (int64_t)g.G * g.G;
+    int64_t n = (int64_t)g.G * g.G * g.n_real;
+    double *a = fields + g.field_offset;
+    double *b = tmp + g.field_offset;
+    int block = 256;
+    unsigned grid = (unsigned)((n + block - 1) / block);
+    for (int64_t k = 0; k < steps; ++k) {
+        const double *src = (k & 1) ? b : a;
+        double *dst = (k & 1) ? a : b;
+        rd_f64_step_kernel<<<grid, block, 0, s>>>(src, dst, g.G, g.n_real, g.model, g.dt, g.p[0], g.p[1],
+                                                  g.p[2], g.p[3]);
+        note_launch();
+    }
+    if (steps & 1)
+        RD_CUDA_TRY(cudaMemcpyAsync(a, b, (size_t)(m * g.n_real) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace rdcil

@@ -1,0 +1,186 @@
+// Synthetic-likelihood statistics over resampled set pairs.
+//
+// Paper (arXiv 2203.14742): bootstrap resampling with replacement of each
+// set, Alg. 5 step 2.1 (appendix A) and Alg. 6 steps 2.1-2.2; mean and
+// covariance of the CIL vector, Alg. 1 step 3; cost eq. (cil:CF) and
+// eq. (cil:CF_synth), reported with the Gaussian log-likelihood.
+//
+// bootstrap_kernel: one CTA per (resample, problem).  Indices come from the
+//   counter-based SplitMix64 stream, are staged in shared memory, and the
+//   per-radius counts of the resampled pair set are accumulated with warp
+//   ballot + popc over the stored bin indices K_ij.
+// stats_kernel: one CTA per problem.  Mean and covariance follow the plain
+//   sequential definition in t order without FMA (so they equal a plain FP64
+//   evaluation bit for bit); Cholesky of the active block, log-determinant,
+//   Mahalanobis term and log-likelihood on one thread (M <= 32).
+#include "common.cuh"
+
+namespace rdcil {
+
+__device__ __forceinline__ uint32_t lemire_index(uint64_t seed, uint64_t ctr, uint32_t n) {
+    return (uint32_t)__umul64hi(splitmix64_at(seed, ctr), (uint64_t)n);
+}
+
+__global__ void bootstrap_kernel(const uint8_t *__restrict__ bins, int n1, int n2, int M, int T,
+                                 uint64_t seed, int64_t *__restrict__ Y) {
+    extern __shared__ int32_t sidx[];
+    __shared__ unsigned long long cnt[32];
+    const int t = blockIdx.x, p = blockIdx.y;
+    const uint64_t sp = seed + (uint64_t)p;
+    int32_t *I = sidx, *J = sidx + n1;
+    for (int a = threadIdx.x; a < n1; a += blockDim.x)
+        I[a] = (int32_t)lemire_index(sp, (((uint64_t)t * 2u + 0u) << 32) | (uint64_t)a, (uint32_t)n1);
+    for (int b = threadIdx.x; b < n2; b += blockDim.x)
+        J[b] = (int32_t)lemire_index(sp, (((uint64_t)t * 2u + 1u) << 32) | (uint64_t)b, (uint32_t)n2);
+    if (threadIdx.x < 32) cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    const uint8_t *B = bins + (int64_t)p * n1 * n2;
+    const int64_t np = (int64_t)n1 * n2;
+    unsigned long long c[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) c[k] = 0ull;
+    const int lane = threadIdx.x & 31;
+    // stride so that every warp iteration is uniform (full-warp ballots)
+    for (int64_t base = (int64_t)(threadIdx.x & ~31); base < np; base += blockDim.x) {
+        int64_t q = base + lane;
+        int K = 0;
+        if (q < np) {
+            int a = (int)(q / n2), b = (int)(q - (int64_t)a * n2);
+            K = B[(int64_t)I[a] * n2 + J[b]];
+        }
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < M) c[k] += (unsigned long long)__popc(__ballot_sync(0xffffffffu, K > k));
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < M && c[k]) atomicAdd(&cnt[k], c[k]);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < M) Y[((int64_t)p * T + t) * M + threadIdx.x] = (int64_t)cnt[threadIdx.x];
+}
+
+__global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int64_t np,
+                             const double *__restrict__ y_obs_all, double *__restrict__ mu_all,
+                             double *__restrict__ cov_all, double *__restrict__ chol_all,
+                             double *__restrict__ scal_all, uint8_t *__restrict__ active_all,
+                             int32_t *__restrict__ status_all) {
+    const int p = blockIdx.x;
+    const int64_t *Y = Yall + (int64_t)p * T * M;
+    __shared__ double mu[32], cov[32 * 32], L[32 * 32];
+    __shared__ int act[32];
+    const double dnp = (double)np;
+    const int tid = threadIdx.x;
+    if (tid < M) {
+        double s = 0.0;
+        int same = 1;
+        const int64_t y0 = Y[tid];
+        for (int t = 0; t < T; ++t) {
+            int64_t yy = Y[(int64_t)t * M + tid];
+            s = __dadd_rn(s, __ddiv_rn((double)yy, dnp));
+            same &= (yy == y0);
+        }
+        mu[tid] = __ddiv_rn(s, (double)T);
+        act[tid] = same ? 0 : 1;
+    }
+    __syncthreads();
+    for (int e = tid; e < M * M; e += blockDim.x) {
+        int k = e / M, l = e - k * M;
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) {
+            double a = __dsub_rn(__ddiv_rn((double)Y[(int64_t)t * M + k], dnp), mu[k]);
+            double b = __dsub_rn(__ddiv_rn((double)Y[(int64_t)t * M + l], dnp), mu[l]);
+            s = __dadd_rn(s, __dmul_rn(a, b));
+        }
+        cov[e] = __ddiv_rn(s, (double)(T - 1));
+        L[e] = 0.0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int idx[32];
+        int ma = 0;
+        for (int k = 0; k < M; ++k)
+            if (act[k]) idx[ma++] = k;
+        int st = RD_OK;
+        for (int i = 0; i < ma && st == RD_OK; ++i) {
+            for (int j = 0; j <= i; ++j) {
+                double s = cov[idx[i] * M + idx[j]];
+                for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(L[i * M + k], L[j * M + k]));
+                if (i == j) {
+                    if (!(s > 0.0)) { st = RD_ERR_NOT_PD; break; }
+                    L[i * M + i] = __dsqrt_rn(s);
+                } else {
+                    L[i * M + j] = __ddiv_rn(s, L[j * M + j]);
+                }
+            }
+        }
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        double logdet = nan, f = nan, ll = nan;
+        if (st == RD_OK) {
+            double ld = 0.0;
+            for (int i = 0; i < ma; ++i) ld = __dadd_rn(ld, log(L[i * M + i]));
+            logdet = 2.0 * ld;
+            if (y_obs_all) {
+                const double *yo = y_obs_all + (int64_t)p * M;
+                double z[32];
+                double ff = 0.0;
+                for (int i = 0; i < ma; ++i) {
+                    double s = __dsub_rn(yo[idx[i]], mu[idx[i]]);
+                    for (int k = 0; k < i; ++k) s = __dsub_rn(s, __dmul_rn(L[i * M + k], z[k]));
+                    z[i] = __ddiv_rn(s, L[i * M + i]);
+                    ff = __dadd_rn(ff, __dmul_rn(z[i], z[i]));
+                }
+                f = ff;
+                // log(2 pi) correctly rounded
+                ll = -0.5 * (ff + logdet + (double)ma * 1.8378770664093453);
+            }
+        }
+        double *sc = scal_all + (int64_t)p * 4;
+        sc[0] = logdet; sc[1] = f; sc[2] = ll; sc[3] = (double)ma;
+        status_all[p] = st;
+    }
+    __syncthreads();
+    for (int e = tid; e < M * M; e += blockDim.x) {
+        cov_all[(int64_t)p * M * M + e] = cov[e];
+        chol_all[(int64_t)p * M * M + e] = L[e];
+    }
+    if (tid < M) {
+        mu_all[(int64_t)p * M + tid] = mu[tid];
+        active_all[(int64_t)p * M + tid] = (uint8_t)act[tid];
+    }
+}
+
+}  // namespace rdcil
+
+using namespace rdcil;
+
+extern "C" rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2, int32_t M, int32_t T,
+                                  uint64_t seed, int32_t n_problems, const double *d_y_obs, int64_t *d_Y,
+                                  double *d_mu, double *d_cov, double *d_chol, double *d_scalars,
+                                  uint8_t *d_active, int32_t *d_status, void *stream) {
+    if (!d_bins || !d_Y || !d_mu || !d_cov || !d_chol || !d_scalars || !d_active || !d_status)
+        return RD_ERR_INVALID_ARG;
+    if (n1 < 1 || n2 < 1 || n1 + n2 > 49152 || M < 1 || M > 32 || T < 2 || n_problems < 1 ||
+        n_problems > 65535)
+        return RD_ERR_INVALID_ARG;
+    double np = (double)n1 * (double)n2;
+    if ((double)T * np * np >= 4.6e18) return RD_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t smem = (size_t)(n1 + n2) * sizeof(int32_t);
+    if (smem > 48 * 1024) {
+        static size_t set = 0;
+        if (smem > set) {
+            RD_CUDA_TRY(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            set = smem;
+        }
+    }
+    dim3 g((unsigned)T, (unsigned)n_problems);
+    bootstrap_kernel<<<g, 256, smem, s>>>(d_bins, (int)n1, (int)n2, M, T, seed, d_Y);
+    note_launch();
+    stats_kernel<<<(unsigned)n_problems, 256, 0, s>>>(d_Y, M, T, n1 * n2, d_y_obs, d_mu, d_cov, d_chol,
+                                                      d_scalars, d_active, d_status);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}

@@ -1,0 +1,143 @@
+"""GPU parity of the correlation integral against the oracle: radii, bin
+indices and counts must be bit-exact (integer results of an exact
+definition), on shapes that span several tiles and ragged tails."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def p():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2203_14742_b300 as pk
+    return pk
+
+
+def run_both(p, X1, X2, b=1.3, M=16, radii=None, exact=False):
+    t1 = torch.from_numpy(np.ascontiguousarray(X1)).cuda()
+    t2 = torch.from_numpy(np.ascontiguousarray(X2)).cuda()
+    fn = p.cil_exact if exact else p.cil
+    r = torch.from_numpy(np.asarray(radii, np.float64)) if radii is not None else None
+    g = fn(t1, t2, b=b, M=M, radii=r)
+    o = oracle.cil(X1, X2, b=b, M=M, radii_=radii)
+    return g, o
+
+
+def assert_same(g, o, check_r0=True):
+    if check_r0:
+        assert float(g["R0"]) == o["R0"]
+    assert np.array_equal(g["radii"].cpu().numpy(), o["radii"])
+    assert np.array_equal(g["bins"].cpu().numpy(), o["bins"])
+    assert np.array_equal(g["counts"].cpu().numpy(), o["counts"])
+
+
+def test_hand_counted_fixture(p):
+    gd = json.load(open(os.path.join(GOLD, "hand_cil_2d.json")))
+    X1 = np.array(gd["S1"], np.float32)
+    X2 = np.array(gd["S2"], np.float32)
+    for exact in (False, True):
+        g, o = run_both(p, X1, X2, b=gd["b"], M=gd["M"], exact=exact)
+        assert_same(g, o)
+        assert list(g["counts"].cpu().numpy()) == gd["counts"]
+        assert np.array_equal(g["bins"].cpu().numpy(), np.array(gd["bins"], np.uint8))
+
+
+@pytest.mark.parametrize("n1,n2,d", [(1, 1, 1), (3, 5, 7), (16, 16, 2048), (64, 64, 4096),
+                                     (65, 130, 4100), (100, 37, 9000), (200, 200, 3000)])
+def test_clustered_patterns_bit_exact(p, n1, n2, d):
+    X1 = W.clustered_patterns(n1, d, 100 + n1)
+    X2 = W.clustered_patterns(n2, d, 200 + n2)
+    g, o = run_both(p, X1, X2, b=1.1, M=16)
+    assert_same(g, o)
+    ge, _ = run_both(p, X1, X2, b=1.1, M=16, exact=True)
+    assert_same(ge, o)
+
+
+@pytest.mark.parametrize("G,ns,n", [(32, 2, 16), (64, 1, 64), (128, 2, 40)])
+def test_cosine_patterns_bit_exact(p, G, ns, n):
+    X = W.cosine_patterns(2 * n, G, ns, 7 + G, amp=1.5, offset=2.0)
+    g, o = run_both(p, X[:n], X[n:], b=1.05, M=32)
+    assert_same(g, o)
+
+
+def test_given_radii(p):
+    X1 = W.clustered_patterns(40, 256, 1)
+    X2 = W.clustered_patterns(33, 256, 2)
+    d2 = oracle.pair_d2(X1, X2)
+    # radii placed exactly on some realised distances: ties must not count
+    qs = np.quantile(np.sqrt(d2).ravel(), [0.9, 0.7, 0.5, 0.3, 0.1])
+    exact_r = np.sqrt(np.sort(d2.ravel())[[100, 500, 900]])
+    radii = np.sort(np.concatenate([qs, exact_r]))[::-1].copy()
+    g, o = run_both(p, X1, X2, radii=radii, M=len(radii))
+    assert_same(g, o, check_r0=False)
+
+
+def test_strided_sets_from_field_array(p):
+    """Patterns read in place from [n][2][G][G] fields: u only and both."""
+    G, n = 64, 24
+    f = W.cosine_patterns(n, G, 2, 5, amp=1.0).reshape(n, 2, G, G)
+    ft = torch.from_numpy(f).cuda().reshape(n, 2 * G * G)
+    for mask in (1, 3):
+        d = G * G * (2 if mask == 3 else 1)
+        X1 = ft[:12, :d]
+        X2 = ft[12:, :d]
+        g = p.cil(X1, X2, b=1.2, M=16)
+        Xo = oracle.patterns(f, mask)
+        o = oracle.cil(Xo[:12], Xo[12:], b=1.2, M=16)
+        assert_same(g, o)
+
+
+def test_swapped_sets_transpose(p):
+    X1 = W.clustered_patterns(30, 500, 3)
+    X2 = W.clustered_patterns(45, 500, 4)
+    a = p.cil(torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda(), b=1.2, M=12)
+    b = p.cil(torch.from_numpy(X2).cuda(), torch.from_numpy(X1).cuda(), b=1.2, M=12)
+    assert torch.equal(a["bins"], b["bins"].T)
+    assert torch.equal(a["counts"], b["counts"])
+
+
+def test_full_size_c2_from_oracle_patterns(p):
+    """c2 CIL at full size (2 x 64 patterns, d = 4096, M = 16): the patterns
+    are the oracle's own FP64 FHN fields (rounded to FP32) after a short
+    integration, so both sides see the same input."""
+    cfg = W.config("c2", steps_scale=0.03)
+    g = cfg["groups"][0]
+    f0 = oracle.init_fields(g["model"], g["G"], g["n_real"], g["params"], g["noise"][0],
+                            g["noise"][1], g["seed"]).astype(np.float64)
+    f = oracle.step(g["model"], g["params"], g["dt"], g["n_steps"], f0).astype(np.float32)
+    X = oracle.patterns(f, g["species_mask"])
+    res, o = run_both(p, X[:64], X[64:], b=cfg["b"], M=cfg["M"])
+    assert_same(res, o)
+    assert int(res["n_rechecked"]) < 0.05 * 64 * 64
+
+
+def test_full_size_c3_shape(p):
+    """c3 shape: 2 x 256 patterns of d = 32768 (GM 128x128, both species),
+    synthetic cosine fields around the GM equilibrium."""
+    X = W.cosine_patterns(512, 128, 2, 33, amp=0.8, offset=2.0)
+    res, o = run_both(p, X[:256], X[256:], b=1.3, M=16)
+    assert_same(res, o)
+    assert int(res["n_rechecked"]) < 0.05 * 256 * 256
+
+
+def test_bound_holds_against_exact_path(p):
+    """The fast path's classification equals the exact path's on every pair,
+    including data far from the origin (centring matters)."""
+    X1 = W.clustered_patterns(90, 2000, 9) + 50.0
+    X2 = W.clustered_patterns(70, 2000, 10) + 50.0
+    t1, t2 = torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda()
+    a = p.cil(t1, t2, b=1.02, M=32)
+    e = p.cil_exact(t1, t2, b=1.02, M=32)
+    assert float(a["R0"]) == float(e["R0"])
+    assert torch.equal(a["bins"], e["bins"])
+    assert torch.equal(a["counts"], e["counts"])

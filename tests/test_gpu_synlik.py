@@ -1,0 +1,88 @@
+"""GPU parity of the bootstrap counts and synthetic-likelihood statistics.
+
+Resampled counts are integers: bit-exact.  Mean, covariance and the
+Cholesky factor follow the same sequential operation order with every
+operation rounded separately on both sides: bit-exact.  log() is the only
+library function involved (log-determinant, log-likelihood): relative 1e-13.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def p():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2203_14742_b300 as pk
+    return pk
+
+
+def oracle_bins(n1, n2, d, M, b, seed):
+    X1 = W.clustered_patterns(n1, d, seed)
+    X2 = W.clustered_patterns(n2, d, seed + 1)
+    return oracle.cil(X1, X2, b=b, M=M)
+
+
+@pytest.mark.parametrize("n1,n2,M,T", [(16, 16, 8, 50), (64, 64, 16, 200), (37, 90, 12, 33),
+                                       (256, 256, 16, 200)])
+def test_bootstrap_and_stats_match(p, n1, n2, M, T):
+    o = oracle_bins(n1, n2, 64, M, 1.08, n1 * 7 + n2)
+    seed = 0x5EED + n1
+    y_obs = o["counts"] / float(n1 * n2)
+    so = oracle.synlik(o["bins"], M, T, seed, y_obs=y_obs)
+    bins = torch.from_numpy(o["bins"]).cuda()
+    s = p.synlik(bins, M, T, seed, y_obs=torch.from_numpy(y_obs))
+    assert np.array_equal(s["Y"].cpu().numpy(), so["Y"])
+    assert np.array_equal(s["mu"].cpu().numpy(), so["mu"])
+    assert np.array_equal(s["cov"].cpu().numpy(), so["cov"])
+    assert np.array_equal(s["active"].cpu().numpy(), so["active"])
+    assert int(s["status"]) == so["status"]
+    if so["status"] == 0:
+        assert np.array_equal(s["chol"].cpu().numpy(), so["chol"])
+        for k in ("logdet", "f", "loglik"):
+            assert float(s[k]) == pytest.approx(so[k], rel=1e-13, abs=1e-300)
+    assert int(s["m_active"]) == so["m_active"]
+
+
+def test_batched_problems(p):
+    M, T = 16, 40
+    bins, ys, refs = [], [], []
+    for q in range(5):
+        o = oracle_bins(20, 24, 32, M, 1.1, 300 + q)
+        bins.append(o["bins"])
+        y = o["counts"] / 480.0
+        ys.append(y)
+        refs.append(oracle.synlik(o["bins"], M, T, 77 + q, y_obs=y))
+    s = p.synlik(torch.from_numpy(np.stack(bins)).cuda(), M, T, 77,
+                 y_obs=torch.from_numpy(np.stack(ys)))
+    for q in range(5):
+        assert np.array_equal(s["Y"][q].cpu().numpy(), refs[q]["Y"])
+        assert np.array_equal(s["cov"][q].cpu().numpy(), refs[q]["cov"])
+
+
+def test_not_positive_definite_reported(p):
+    # bins take only the values 0 and 2: counts of radius 1 and 2 coincide in
+    # every resample, so the active block is singular
+    rng = np.random.default_rng(0)
+    bins = (2 * rng.integers(0, 2, size=(20, 20))).astype(np.uint8)
+    so = oracle.synlik(bins, 4, 30, 5)
+    s = p.synlik(torch.from_numpy(bins).cuda(), 4, 30, 5)
+    assert so["status"] == 3 and int(s["status"]) == 3
+    assert list(s["active"].cpu().numpy()) == [1, 1, 0, 0]
+
+
+def test_identity_like_counts_are_resample_invariant_when_constant(p):
+    # every pair in bin M: all components constant, nothing active, logdet 0
+    bins = np.full((8, 9), 6, np.uint8)
+    s = p.synlik(torch.from_numpy(bins).cuda(), 6, 10, 1, y_obs=torch.ones(6, dtype=torch.float64))
+    assert int(s["status"]) == 0 and int(s["m_active"]) == 0
+    assert float(s["logdet"]) == 0.0 and float(s["f"]) == 0.0
+    assert torch.all(s["Y"] == 72)
