@@ -145,6 +145,20 @@ rd_status rd_integrate_reference(rd_handle *h, float *d_fields, float *d_tmp,
 rd_status rd_integrate_f64(rd_handle *h, double *d_fields64, double *d_tmp64,
                            int64_t steps_override, void *stream);
 
+/* Tile-shape variants of the resident stepper.  Every variant performs the
+ * same per-node arithmetic in the same order, so all give bit-identical
+ * fields; the choice (per model and G, process-wide) only affects speed.
+ * rd_n_variants: number of variants (indices 0..n-1, 0 = default).
+ * rd_set_variant / rd_get_variant: choose / read the variant of (model, G).
+ * rd_autotune: time every variant on the largest group of each (model, G)
+ *   class present in h for `steps` Euler steps, keep the fastest, then
+ *   re-initialise d_fields (rd_reinit).  Synchronous.  chosen (nullable,
+ *   host int32[9]) receives the choice per [model][G index 32/64/128]. */
+int32_t rd_n_variants(void);
+rd_status rd_set_variant(int32_t model, int32_t G, int32_t variant);
+int32_t rd_get_variant(int32_t model, int32_t G);
+rd_status rd_autotune(rd_handle *h, float *d_fields, int64_t steps, void *stream, int32_t *chosen);
+
 /* rd_sync_status — synchronise `stream`, read and clear the handle's device
  * status word.  Returns RD_OK, RD_ERR_NONFINITE, RD_ERR_TIMEOUT, or
  * RD_ERR_CUDA when the stream itself reported an error. */
@@ -233,7 +247,8 @@ rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1,
  * status[p] = RD_OK or RD_ERR_NOT_PD (active block not positive definite).
  * mu and cov follow the plain sequential definition in t order, so they
  * match a plain FP64 evaluation bit for bit.
- * Limits: n1, n2 <= 65535; 1 <= M <= 32; 2 <= T; T*(n1*n2)^2 < 2^62. */
+ * Limits: n1 + n2 <= 49152; 1 <= M <= 32; 2 <= T; T*M <= 24576;
+ * T*(n1*n2)^2 < 4.6e18.  Violations return RD_ERR_INVALID_ARG. */
 rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2, int32_t M,
                        int32_t T, uint64_t seed, int32_t n_problems,
                        const double *d_y_obs, int64_t *d_Y, double *d_mu,

@@ -54,6 +54,10 @@ _SIGS = {
     "synlik_stats": (_i32, [_vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                             _vp, _vp, _vp]),
     "rd_kernel_launches": (_u64, []),
+    "rd_n_variants": (_i32, []),
+    "rd_set_variant": (_i32, [_i32, _i32, _i32]),
+    "rd_get_variant": (_i32, [_i32, _i32]),
+    "rd_autotune": (_i32, [_vp, _vp, _i64, _vp, C.POINTER(_i32)]),
     "rd_adjoint": (_i32, [_vp, _i32, _vp, _i32, C.POINTER(_i32), _i64, C.POINTER(_i32), _i64, _vp,
                           _i32, _dbl, _vp, _vp, _vp, _vp]),
 }
@@ -197,6 +201,13 @@ class Simulation:
         _check("rd_integrate_f64", lib().rd_integrate_f64(self.handle, _ptr(fields64), _ptr(tmp),
                                                           int(steps), _stream()))
         return fields64
+
+    def autotune(self, steps=200):
+        """Pick the fastest tile shape per (model, G); re-initialises the fields."""
+        chosen = (C.c_int32 * 9)(*([-1] * 9))
+        _check("rd_autotune", lib().rd_autotune(self.handle, _ptr(self.fields), int(steps), _stream(),
+                                                chosen))
+        return list(chosen)
 
     def sync_status(self):
         return lib().rd_sync_status(self.handle, _stream())

@@ -182,3 +182,65 @@ static std::atomic<uint64_t> g_launches{0};
 void rdcil::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 extern "C" uint64_t rd_kernel_launches(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// tile-shape variants and the autotuner
+// ---------------------------------------------------------------------------
+extern "C" int32_t rd_n_variants(void) { return n_variants(); }
+
+extern "C" rd_status rd_set_variant(int32_t model, int32_t G, int32_t variant) {
+    if (model < 0 || model > 2 || (G != 32 && G != 64 && G != 128) || variant < 0 || variant >= n_variants())
+        return RD_ERR_INVALID_ARG;
+    set_variant_choice(model, G, variant);
+    return RD_OK;
+}
+
+extern "C" int32_t rd_get_variant(int32_t model, int32_t G) {
+    if (model < 0 || model > 2 || (G != 32 && G != 64 && G != 128)) return -1;
+    return get_variant_choice(model, G);
+}
+
+extern "C" rd_status rd_autotune(rd_handle *hh, float *d_fields, int64_t steps, void *stream, int32_t *chosen) {
+    if (!hh || !d_fields || steps < 1) return RD_ERR_INVALID_ARG;
+    Handle &h = hh->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    RD_CUDA_TRY(cudaEventCreate(&e0));
+    RD_CUDA_TRY(cudaEventCreate(&e1));
+    rd_status st = RD_OK;
+    for (int model = 0; model < 3 && st == RD_OK; ++model)
+        for (int G : {32, 64, 128}) {
+            // the largest group of this (model, G) class stands for the class
+            int best_g = -1;
+            for (int i = 0; i < h.n_groups; ++i)
+                if (h.h_groups[i].model == model && h.h_groups[i].G == G &&
+                    (best_g < 0 || h.h_groups[i].n_real > h.h_groups[best_g].n_real))
+                    best_g = i;
+            if (best_g < 0) continue;
+            const GroupDev &g = h.h_groups[best_g];
+            float best_ms = 1e30f;
+            int best_v = get_variant_choice(model, G);
+            for (int v = 0; v < n_variants() && st == RD_OK; ++v) {
+                st = launch_integrate_variant(g, d_fields, steps, nullptr, h.d_status, s, v);   // warm
+                if (st) break;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 2 && st == RD_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    st = launch_integrate_variant(g, d_fields, steps, nullptr, h.d_status, s, v);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { st = RD_ERR_CUDA; break; }
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    ms = t < ms ? t : ms;
+                }
+                if (ms < best_ms) { best_ms = ms; best_v = v; }
+            }
+            set_variant_choice(model, G, best_v);
+            if (chosen) chosen[model * 3 + (G == 32 ? 0 : G == 64 ? 1 : 2)] = best_v;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    // the tuning runs advanced the fields: restore the initial states
+    return rd_reinit(hh, d_fields, stream);
+}

@@ -21,20 +21,21 @@
 
 namespace rdcil {
 
-static constexpr int KCHUNK = 2048;      // split-K chunk (bounds FP32 accumulation error)
+static constexpr int KCHUNK_MAX = 2048;  // longest split-K chunk (bounds FP32 accumulation error)
 static constexpr int PAD = 64;           // padded pattern length granularity
+static constexpr int TILE = 64;          // Gram output tile (pairs per side)
 
 static inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 struct CilWork {
-    int64_t n1, n2, d, dp, nchunk;
+    int64_t n1, n2, d, dp, kc, nchunk;
     float *centre;          // [dp]
     __nv_bfloat16 *hi;      // [(n1+n2)][dp]
     __nv_bfloat16 *lo;      // [(n1+n2)][dp]
     double *N, *H, *L, *E;  // [(n1+n2)]
     float *Ppart;           // [nchunk][n1][n2]
     double *A, *Mg;         // [n1*n2] approximate d2 and its error bound
-    unsigned long long *scal;  // [0] max lower bound bits, [1] exact max bits, [2] n_rechecked
+    unsigned long long *scal;  // [0] max lower bound, [1] max upper bound, [2] exact max (FP64 bits), [3] n_rechecked
     size_t bytes;
 };
 
@@ -42,7 +43,13 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     CilWork w{};
     w.n1 = n1; w.n2 = n2; w.d = d;
     w.dp = round_up(d, PAD);
-    w.nchunk = (w.dp + KCHUNK - 1) / KCHUNK;
+    // split-K chunk: enough CTAs to cover the GPU twice, at most KCHUNK_MAX
+    int64_t tiles = ((n1 + TILE - 1) / TILE) * ((n2 + TILE - 1) / TILE);
+    int64_t want = (2 * 148 + tiles - 1) / tiles;
+    int64_t kc = round_up((w.dp + want - 1) / want, PAD);
+    if (kc > KCHUNK_MAX) kc = KCHUNK_MAX;
+    w.kc = kc;
+    w.nchunk = (w.dp + kc - 1) / kc;
     int64_t n = n1 + n2;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -68,13 +75,33 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
 // ---------------------------------------------------------------------------
 // canonical distance: sequential FP64, no FMA
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double sq_diff(float a, float b) {
+    double df = __dsub_rn((double)a, (double)b);
+    return __dmul_rn(df, df);
+}
+
 __device__ __forceinline__ double canonical_d2(const float *__restrict__ x, const float *__restrict__ y,
                                                int64_t d) {
     double acc = 0.0;
-    for (int64_t t = 0; t < d; ++t) {
-        double df = __dsub_rn((double)__ldg(x + t), (double)__ldg(y + t));
-        acc = __dadd_rn(acc, __dmul_rn(df, df));
+    int64_t t = 0;
+    if ((((uintptr_t)x | (uintptr_t)y) & 15) == 0) {
+        // 8 elements per iteration from float4 loads issued ahead of the
+        // (strictly sequential) FP64 accumulation
+        for (; t + 8 <= d; t += 8) {
+            float4 a0 = __ldg(reinterpret_cast<const float4 *>(x + t));
+            float4 a1 = __ldg(reinterpret_cast<const float4 *>(x + t + 4));
+            float4 b0 = __ldg(reinterpret_cast<const float4 *>(y + t));
+            float4 b1 = __ldg(reinterpret_cast<const float4 *>(y + t + 4));
+            double q0 = sq_diff(a0.x, b0.x), q1 = sq_diff(a0.y, b0.y), q2 = sq_diff(a0.z, b0.z),
+                   q3 = sq_diff(a0.w, b0.w), q4 = sq_diff(a1.x, b1.x), q5 = sq_diff(a1.y, b1.y),
+                   q6 = sq_diff(a1.z, b1.z), q7 = sq_diff(a1.w, b1.w);
+            acc = __dadd_rn(acc, q0); acc = __dadd_rn(acc, q1);
+            acc = __dadd_rn(acc, q2); acc = __dadd_rn(acc, q3);
+            acc = __dadd_rn(acc, q4); acc = __dadd_rn(acc, q5);
+            acc = __dadd_rn(acc, q6); acc = __dadd_rn(acc, q7);
+        }
     }
+    for (; t < d; ++t) acc = __dadd_rn(acc, sq_diff(__ldg(x + t), __ldg(y + t)));
     return acc;
 }
 
@@ -150,11 +177,12 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) gram_simt_kernel(const __nv_bfloat16 *__restrict__ hi,
                                                         const __nv_bfloat16 *__restrict__ lo, int64_t n1,
-                                                        int64_t n2, int64_t dp, float *__restrict__ Ppart) {
+                                                        int64_t n2, int64_t dp, int64_t kc,
+                                                        float *__restrict__ Ppart) {
     __shared__ float sAh[32][65], sAl[32][65], sBh[32][65], sBl[32][65];
     const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
-    const int64_t k_begin = (int64_t)blockIdx.z * KCHUNK;
-    const int64_t k_end = min(dp, k_begin + KCHUNK);
+    const int64_t k_begin = (int64_t)blockIdx.z * kc;
+    const int64_t k_end = min(dp, k_begin + kc);
     const int tid = threadIdx.x;
     const int ti = tid / 16, tj = tid % 16;
     float acc[4][4];
@@ -227,7 +255,7 @@ __device__ __forceinline__ void approx_and_bound(const CilWork &w, int64_t i, in
 __global__ void d2_bound_kernel(CilWork w, double gam) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t np = w.n1 * w.n2;
-    double lb = 0.0;
+    double lb = 0.0, ub = 0.0;
     if (q < np) {
         int64_t i = q / w.n2, j = q - i * w.n2;
         double P = 0.0;
@@ -237,25 +265,59 @@ __global__ void d2_bound_kernel(CilWork w, double gam) {
         w.A[q] = A;
         w.Mg[q] = m;
         lb = fmax(A - m, 0.0);
+        ub = fmax(A + m, 0.0);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lb = fmax(lb, __shfl_xor_sync(0xffffffffu, lb, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&w.scal[0], (unsigned long long)__double_as_longlong(lb));
+    for (int o = 16; o > 0; o >>= 1) {
+        lb = fmax(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+        ub = fmax(ub, __shfl_xor_sync(0xffffffffu, ub, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        // non-negative doubles order like their bit patterns
+        atomicMax(&w.scal[0], (unsigned long long)__double_as_longlong(lb));
+        atomicMax(&w.scal[1], (unsigned long long)__double_as_longlong(ub));
+    }
 }
 
-// 3b. exact maximum over the pairs that could hold it (upper bound >= the
-//     largest lower bound); canonical sums only for those.
-__global__ void exact_max_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
-                                 const float *__restrict__ X2, int64_t ld2) {
+// 3b. exact pass: the canonical sum for every pair that could hold the
+//     maximum (upper bound >= the largest lower bound) or whose interval
+//     could contain a threshold.  Before R0 is known exactly, R0^2 lies in
+//     [lbmax, ubmax], so T_k = (R0 b^-k)^2 lies in [lbmax b^-2k, ubmax b^-2k]
+//     up to the rounding of the radius recursion (relative 1e-13 margin).
+//     Exact values overwrite A with Mg = -1 as the flag.
+__global__ void exact_pass_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
+                                  const float *__restrict__ X2, int64_t ld2, const double *__restrict__ radii_in,
+                                  double b, int M) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t np = w.n1 * w.n2;
     if (q >= np) return;
-    double lbmax = __longlong_as_double((long long)w.scal[0]);
-    if (w.A[q] + w.Mg[q] < lbmax) return;
+    const double A = w.A[q], m = w.Mg[q];
+    const double lo = A - m, hi = A + m;
+    bool need = false;
+    if (!radii_in) {
+        const double lbmax = __longlong_as_double((long long)w.scal[0]);
+        const double ubmax = __longlong_as_double((long long)w.scal[1]);
+        need = hi >= lbmax;
+        double f = 1.0;
+        for (int k = 0; k < M && !need; ++k) {
+            f = f / (b * b);
+            double tlo = lbmax * f * (1.0 - 1e-13), thi = ubmax * f * (1.0 + 1e-13);
+            need = !(hi < tlo || lo > thi);
+        }
+    } else {
+        for (int k = 0; k < M && !need; ++k) {
+            double T = __dmul_rn(radii_in[k], radii_in[k]);
+            need = !(hi < T || lo >= T);
+        }
+    }
+    if (!need) return;
     int64_t i = q / w.n2, j = q - i * w.n2;
     double e = canonical_d2(X1 + i * ld1, X2 + j * ld2, w.d);
-    atomicMax(&w.scal[1], (unsigned long long)__double_as_longlong(e));
-    atomicAdd(&w.scal[2], 1ull);
+    w.A[q] = e;
+    w.Mg[q] = -1.0;
+    if (!radii_in && hi >= __longlong_as_double((long long)w.scal[0]))
+        atomicMax(&w.scal[2], (unsigned long long)__double_as_longlong(e));
+    atomicAdd(&w.scal[3], 1ull);
 }
 
 // 3c. radii: R0 = sqrt(max), R_k = R_{k-1}/b  (or copy the given radii)
@@ -267,7 +329,7 @@ __global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, dou
         for (int k = 0; k < M; ++k) radii_out[k + 1] = radii_in[k];
         return;
     }
-    double R = __dsqrt_rn(__longlong_as_double((long long)w.scal[1]));
+    double R = __dsqrt_rn(__longlong_as_double((long long)w.scal[2]));
     radii_out[0] = R;
     for (int k = 0; k < M; ++k) {
         R = __ddiv_rn(R, b);
@@ -296,22 +358,25 @@ __global__ void bins_counts_kernel(CilWork w, const float *__restrict__ X1, int6
     int K = 0;
     if (q < np) {
         bool amb = exact_all != 0;
-        double A = 0.0, m = 0.0;
         if (!amb) {
-            A = w.A[q];
-            m = w.Mg[q];
-            for (int k = 0; k < M; ++k) {
-                double T = Tk[k];
-                if (A + m < T) K++;
-                else if (!(A - m >= T)) amb = true;
+            const double A = w.A[q], m = w.Mg[q];
+            if (m < 0.0) {
+                for (int k = 0; k < M; ++k) K += (A < Tk[k]) ? 1 : 0;
+            } else {
+                for (int k = 0; k < M; ++k) {
+                    double T = Tk[k];
+                    if (A + m < T) K++;
+                    else if (!(A - m >= T)) amb = true;
+                }
             }
         }
         if (amb) {
+            // exact path, or a pair the exact pass did not foresee (defensive)
             int64_t i = q / w.n2, j = q - i * w.n2;
             double e = canonical_d2(X1 + i * ld1, X2 + j * ld2, w.d);
             K = 0;
             for (int k = 0; k < M; ++k) K += (e < Tk[k]) ? 1 : 0;
-            if (!exact_all) atomicAdd(&w.scal[2], 1ull);
+            if (!exact_all) atomicAdd(&w.scal[3], 1ull);
         }
         bins[q] = (uint8_t)K;
     }
@@ -332,12 +397,12 @@ __global__ void exact_all_kernel(CilWork w, const float *__restrict__ X1, int64_
     if (q >= np) return;
     int64_t i = q / w.n2, j = q - i * w.n2;
     double e = canonical_d2(X1 + i * ld1, X2 + j * ld2, w.d);
-    atomicMax(&w.scal[1], (unsigned long long)__double_as_longlong(e));
+    atomicMax(&w.scal[2], (unsigned long long)__double_as_longlong(e));
 }
 
 __global__ void finish_kernel(CilWork w, int64_t *n_rechecked, const int64_t *counts, int M, double *Cv) {
     if (blockIdx.x != 0) return;
-    if (threadIdx.x == 0 && n_rechecked) *n_rechecked = (int64_t)w.scal[2];
+    if (threadIdx.x == 0 && n_rechecked) *n_rechecked = (int64_t)w.scal[3];
     if (Cv && (int)threadIdx.x < M)
         Cv[threadIdx.x] = __ddiv_rn((double)counts[threadIdx.x], (double)w.n1 * (double)w.n2);
 }
@@ -390,14 +455,14 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
                                                         w.H, w.L, w.E);
         note_launch();
         dim3 gg((unsigned)((n2 + 63) / 64), (unsigned)((n1 + 63) / 64), (unsigned)w.nchunk);
-        gram_simt_kernel<<<gg, 256, 0, s>>>(w.hi, w.lo, n1, n2, w.dp, w.Ppart);
+        gram_simt_kernel<<<gg, 256, 0, s>>>(w.hi, w.lo, n1, n2, w.dp, w.kc, w.Ppart);
         note_launch();
-        // SIMT Gram: 3*KCHUNK fused multiply-adds per accumulator, each
+        // SIMT Gram: 3*kc fused multiply-adds per accumulator, each
         // rounding to nearest (2^-24), plus margin for the chunk bookkeeping.
-        const double gam = (3.0 * KCHUNK + 64.0) * 5.9604644775390625e-8;
+        const double gam = (3.0 * (double)w.kc + 64.0) * 5.9604644775390625e-8;
         d2_bound_kernel<<<gp, 256, 0, s>>>(w, gam);
         note_launch();
-        if (!radii_in) exact_max_kernel<<<gp, 256, 0, s>>>(w, X1, ld1, X2, ld2);
+        exact_pass_kernel<<<gp, 256, 0, s>>>(w, X1, ld1, X2, ld2, radii_in, b, M);
         note_launch();
     }
     radii_kernel<<<1, 32, 0, s>>>(w, radii_in, b, M, radii_out);

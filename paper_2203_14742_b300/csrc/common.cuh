@@ -73,5 +73,10 @@ rd_status launch_integrate_f64(const GroupDev &g, double *fields, double *tmp, i
                                cudaStream_t s);
 rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int64_t steps,
                               cudaStream_t s);
+rd_status launch_integrate_variant(const GroupDev &g, float *fields, int64_t steps, double *residual,
+                                   uint32_t *status, cudaStream_t s, int vi);
+void set_variant_choice(int model, int G, int vi);
+int get_variant_choice(int model, int G);
+int n_variants();
 
 }  // namespace rdcil

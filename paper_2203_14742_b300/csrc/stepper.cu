@@ -92,68 +92,101 @@ __device__ __forceinline__ void rhs_f64(double u, double v, double nu, double su
 }
 
 // ---------------------------------------------------------------------------
-// Resident stepper: one realisation per CTA, field in registers for the
-// whole run.  RECORD = true stores the state before every step into
-// traj[n] (n = 0..steps-1, each 2*G*G floats per realisation, realisation
-// stride traj_stride) for the adjoint's segment recomputation.
+// Resident stepper: one realisation per CTA, the field held in registers as
+// packed (u, v) tiles for the whole run.  RECORD = true stores the state
+// before every step into traj[n] (n = 0..steps-1, each 2*G*G floats per
+// realisation, realisation stride traj_stride) for the adjoint's segment
+// recomputation.
 // ---------------------------------------------------------------------------
 template <int MODEL, int G, int TY, int TX, bool RECORD>
-__global__ void __launch_bounds__(Tiling<G, TY, TX>::NT, 1)
+__global__ void __launch_bounds__(Tiling2<G, TY, TX>::NT, 1)
 rd_resident_kernel(float *__restrict__ fields, int64_t field_offset, int64_t steps, CoefF cf,
                    double p0, double p1, double p2, double p3, double *__restrict__ residual,
                    uint32_t *__restrict__ status, float *__restrict__ traj, int64_t traj_stride) {
-    using T = Tiling<G, TY, TX>;
-    constexpr int NX = T::NX;
+    using T = Tiling2<G, TY, TX>;
+    constexpr int NX = T::NX, NY = T::NY;
     extern __shared__ float4 smem_f4[];
-    float *sm = reinterpret_cast<float *>(smem_f4);
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
 
     const int tid = threadIdx.x;
     const int tx = tid % NX, ty = tid / NX;
     const int r = blockIdx.x;
     float *base = fields + field_offset + (int64_t)r * 2 * G * G;
 
-    float u[TY][TX], v[TY][TX];
-    tile_load<G, TY, TX>(base, tx, ty, u, v);
+    float2 w[TY][TX];
+    tile2_load<G, TY, TX>(base, tx, ty, w);
+#pragma unroll
+    for (int i = 0; i < TY; ++i)
+#pragma unroll
+        for (int c = 0; c < TX; ++c) w[i][c] = to_state2<MODEL>(w[i][c], cf);
 
     for (int64_t n = 0; n < steps; ++n) {
-        if (RECORD) tile_store<G, TY, TX>(traj + (int64_t)r * traj_stride + n * 2 * G * G, tx, ty, u, v);
-        float *hb = sm + (int)(n & 1) * (T::HALO_FLOATS / 2);
-        halo_put<G, TY, TX>(hb, tx, ty, u, v);
+        if (RECORD) {
+            float2 f[TY][TX];
+#pragma unroll
+            for (int i = 0; i < TY; ++i)
+#pragma unroll
+                for (int c = 0; c < TX; ++c) f[i][c] = from_state2<MODEL>(w[i][c], cf);
+            tile2_store<G, TY, TX>(traj + (int64_t)r * traj_stride + n * 2 * G * G, tx, ty, f);
+        }
+        float2 *hb = sm + (int)(n & 1) * (T::HALO_F2 / 2);
+        halo2_put<G, TY, TX>(hb, tx, ty, w);
         __syncthreads();
-        tile_step<MODEL, G, TY, TX>(hb, tx, ty, u, v, cf);
+        tile2_step<MODEL, G, TY, TX>(hb, tx, ty, w, cf);
     }
-    tile_store<G, TY, TX>(base, tx, ty, u, v);
+#pragma unroll
+    for (int i = 0; i < TY; ++i)
+#pragma unroll
+        for (int c = 0; c < TX; ++c) w[i][c] = from_state2<MODEL>(w[i][c], cf);
+    tile2_store<G, TY, TX>(base, tx, ty, w);
     if (RECORD) return;
 
-    // ---- FP64 steady-state residual of the final state -------------------
-    float *hb = sm + (int)(steps & 1) * (T::HALO_FLOATS / 2);
-    halo_put<G, TY, TX>(hb, tx, ty, u, v);
+    // ---- FP64 steady-state residual of the final (stored FP32) state -----
+    float2 *hb = sm + (int)(steps & 1) * (T::HALO_F2 / 2);
+    halo2_put<G, TY, TX>(hb, tx, ty, w);
     __syncthreads();
     const double p[4] = {p0, p1, p2, p3};
     const double h2 = (double)(G - 1) * (double)(G - 1);
     double mx = 0.0, ss = 0.0;
     bool bad = false;
-    float pu[TX], pv[TX];
-    halo_north<G, TY, TX>(hb, tx, ty, u, v, pu, pv);
+    float2 pw[TX];
+    if (ty > 0) {
+        ld_row2<TX>(hb + (1 * NY + ty - 1) * G + tx * TX, pw);
+    } else {
+#pragma unroll
+        for (int c = 0; c < TX; ++c) pw[c] = w[0][c];
+    }
 #pragma unroll
     for (int i = 0; i < TY; ++i) {
-        float su[TX], sv[TX];
-        row_south<G, TY, TX>(hb, tx, ty, i, u, v, su, sv);
-        float wu, eu, wv, ev;
-        row_west_east<NX>(tx, u[i][0], u[i][TX - 1], wu, eu);
-        row_west_east<NX>(tx, v[i][0], v[i][TX - 1], wv, ev);
+        float2 sw[TX];
+        if (i + 1 < TY) {
+#pragma unroll
+            for (int c = 0; c < TX; ++c) sw[c] = w[i + 1][c];
+        } else if (ty < NY - 1) {
+            ld_row2<TX>(hb + (0 * NY + ty + 1) * G + tx * TX, sw);
+        } else {
+#pragma unroll
+            for (int c = 0; c < TX; ++c) sw[c] = w[TY - 1][c];
+        }
+        float2 west, east;
+        west.x = __shfl_up_sync(0xffffffffu, w[i][TX - 1].x, 1, NX);
+        west.y = __shfl_up_sync(0xffffffffu, w[i][TX - 1].y, 1, NX);
+        east.x = __shfl_down_sync(0xffffffffu, w[i][0].x, 1, NX);
+        east.y = __shfl_down_sync(0xffffffffu, w[i][0].y, 1, NX);
+        if (tx == 0) west = w[i][0];
+        if (tx == NX - 1) east = w[i][TX - 1];
 #pragma unroll
         for (int c = 0; c < TX; ++c) {
-            float Wu = c > 0 ? u[i][c - 1] : wu, Eu = c < TX - 1 ? u[i][c + 1] : eu;
-            float Wv = c > 0 ? v[i][c - 1] : wv, Ev = c < TX - 1 ? v[i][c + 1] : ev;
+            float2 Wn = c > 0 ? w[i][c - 1] : west, En = c < TX - 1 ? w[i][c + 1] : east;
             double Fu, Fv;
-            rhs_f64<MODEL>(u[i][c], v[i][c], pu[c], su[c], Wu, Eu, pv[c], sv[c], Wv, Ev, p, h2, Fu, Fv);
-            bad |= !isfinite(u[i][c]) || !isfinite(v[i][c]) || !isfinite(Fu) || !isfinite(Fv);
+            rhs_f64<MODEL>(w[i][c].x, w[i][c].y, pw[c].x, sw[c].x, Wn.x, En.x, pw[c].y, sw[c].y, Wn.y, En.y,
+                           p, h2, Fu, Fv);
+            bad |= !isfinite(w[i][c].x) || !isfinite(w[i][c].y) || !isfinite(Fu) || !isfinite(Fv);
             mx = fmax(mx, fmax(fabs(Fu), fabs(Fv)));
             ss += Fu * Fu + Fv * Fv;
         }
 #pragma unroll
-        for (int c = 0; c < TX; ++c) { pu[c] = u[i][c]; pv[c] = v[i][c]; }
+        for (int c = 0; c < TX; ++c) pw[c] = w[i][c];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -162,14 +195,14 @@ rd_resident_kernel(float *__restrict__ fields, int64_t field_offset, int64_t ste
     }
     int anybad = __syncthreads_or(bad ? 1 : 0);
     // the other halo buffer is free: reuse it for the cross-warp reduction
-    double *red = reinterpret_cast<double *>(sm + (int)((steps + 1) & 1) * (T::HALO_FLOATS / 2));
+    double *red = reinterpret_cast<double *>(sm + (int)((steps + 1) & 1) * (T::HALO_F2 / 2));
     const int warp = tid >> 5, lane = tid & 31;
     constexpr int NW = T::NT / 32;
     if (lane == 0) { red[warp] = mx; red[NW + warp] = ss; }
     __syncthreads();
     if (tid == 0) {
         double m = 0.0, s = 0.0;
-        for (int w = 0; w < NW; ++w) { m = fmax(m, red[w]); s += red[NW + w]; }
+        for (int wi = 0; wi < NW; ++wi) { m = fmax(m, red[wi]); s += red[NW + wi]; }
         if (anybad) {
             atomicOr(status, (unsigned)ST_NONFINITE);
             m = __longlong_as_double(0x7ff8000000000000ll);
@@ -182,20 +215,33 @@ rd_resident_kernel(float *__restrict__ fields, int64_t field_offset, int64_t ste
     }
 }
 
-// Tile shapes per grid side (a per-G choice; see the tuning notes in the
-// design document): G=32 and G=64 use 4x4 tiles (64 / 256 threads), G=128
-// uses 8x4 tiles (512 threads) so the 64 state registers fit.
-template <int G> struct TileOf;
-template <> struct TileOf<32> { static constexpr int TY = 4, TX = 4; };
-template <> struct TileOf<64> { static constexpr int TY = 4, TX = 4; };
-template <> struct TileOf<128> { static constexpr int TY = 8, TX = 4; };
+// ---------------------------------------------------------------------------
+// Tile-shape variants.  Every variant performs the same per-node arithmetic
+// in the same order (only the data movement differs), so all variants give
+// bit-identical fields; the choice is a pure performance knob, picked by
+// rd_autotune or the default table below.
+// ---------------------------------------------------------------------------
+struct Variant {
+    int TY, TX;
+};
+static constexpr int NVAR = 4;
+static constexpr Variant VAR32[NVAR] = {{4, 4}, {2, 4}, {4, 2}, {2, 8}};
+static constexpr Variant VAR64[NVAR] = {{4, 4}, {2, 8}, {4, 8}, {8, 4}};
+static constexpr Variant VAR128[NVAR] = {{8, 4}, {4, 8}, {8, 8}, {16, 4}};
 
-template <int MODEL, int G, bool RECORD>
-static rd_status launch_resident(const GroupDev &g, float *fields, int64_t steps, double *residual,
-                                 uint32_t *status, float *traj, int64_t traj_stride, cudaStream_t s) {
-    constexpr int TY = TileOf<G>::TY, TX = TileOf<G>::TX;
-    using T = Tiling<G, TY, TX>;
-    auto kern = rd_resident_kernel<MODEL, G, TY, TX, RECORD>;
+template <int G> constexpr Variant var_of(int i) {
+    return G == 32 ? VAR32[i] : (G == 64 ? VAR64[i] : VAR128[i]);
+}
+
+static int g_choice[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // [model][G index]
+static inline int gidx(int G) { return G == 32 ? 0 : (G == 64 ? 1 : 2); }
+
+template <int MODEL, int G, int VI, bool RECORD>
+static rd_status launch_variant(const GroupDev &g, float *fields, int64_t steps, double *residual,
+                                uint32_t *status, float *traj, int64_t traj_stride, cudaStream_t s) {
+    constexpr Variant V = var_of<G>(VI);
+    using T = Tiling2<G, V.TY, V.TX>;
+    auto kern = rd_resident_kernel<MODEL, G, V.TY, V.TX, RECORD>;
     static bool attr_set = false;
     if (!attr_set) {
         RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM));
@@ -209,36 +255,58 @@ static rd_status launch_resident(const GroupDev &g, float *fields, int64_t steps
     return cuda_status(cudaGetLastError());
 }
 
+template <int MODEL, int G, bool RECORD>
+static rd_status launch_resident(const GroupDev &g, float *fields, int64_t steps, double *residual,
+                                 uint32_t *status, float *traj, int64_t traj_stride, cudaStream_t s, int vi) {
+    if (RECORD) vi = 0;   // the recording pass always uses the default shape
+    switch (vi) {
+        case 1: return launch_variant<MODEL, G, 1, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        case 2: return launch_variant<MODEL, G, 2, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        case 3: return launch_variant<MODEL, G, 3, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        default: return launch_variant<MODEL, G, 0, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+    }
+}
+
 template <int MODEL, bool RECORD>
 static rd_status dispatch_G(const GroupDev &g, float *fields, int64_t steps, double *residual, uint32_t *status,
-                            float *traj, int64_t traj_stride, cudaStream_t s) {
+                            float *traj, int64_t traj_stride, cudaStream_t s, int vi) {
     switch (g.G) {
-        case 32: return launch_resident<MODEL, 32, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
-        case 64: return launch_resident<MODEL, 64, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
-        case 128: return launch_resident<MODEL, 128, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        case 32: return launch_resident<MODEL, 32, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
+        case 64: return launch_resident<MODEL, 64, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
+        case 128: return launch_resident<MODEL, 128, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
         default: return RD_ERR_UNSUPPORTED;
     }
 }
 
 template <bool RECORD>
 static rd_status dispatch_model(const GroupDev &g, float *fields, int64_t steps, double *residual,
-                                uint32_t *status, float *traj, int64_t traj_stride, cudaStream_t s) {
+                                uint32_t *status, float *traj, int64_t traj_stride, cudaStream_t s, int vi) {
     switch (g.model) {
-        case RD_FHN: return dispatch_G<RD_FHN, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
-        case RD_GM: return dispatch_G<RD_GM, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
-        case RD_DIFF: return dispatch_G<RD_DIFF, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+        case RD_FHN: return dispatch_G<RD_FHN, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
+        case RD_GM: return dispatch_G<RD_GM, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
+        case RD_DIFF: return dispatch_G<RD_DIFF, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
         default: return RD_ERR_UNSUPPORTED;
     }
 }
 
 rd_status launch_integrate_group(const GroupDev &g, float *fields, int64_t steps, double *residual,
                                  uint32_t *status, cudaStream_t s) {
-    return dispatch_model<false>(g, fields, steps, residual, status, nullptr, 0, s);
+    return dispatch_model<false>(g, fields, steps, residual, status, nullptr, 0, s, g_choice[g.model][gidx(g.G)]);
 }
+
+rd_status launch_integrate_variant(const GroupDev &g, float *fields, int64_t steps, double *residual,
+                                   uint32_t *status, cudaStream_t s, int vi) {
+    if (vi < 0 || vi >= NVAR) return RD_ERR_INVALID_ARG;
+    return dispatch_model<false>(g, fields, steps, residual, status, nullptr, 0, s, vi);
+}
+
+void set_variant_choice(int model, int G, int vi) { g_choice[model][gidx(G)] = vi; }
+int get_variant_choice(int model, int G) { return g_choice[model][gidx(G)]; }
+int n_variants() { return NVAR; }
 
 // traj holds, per realisation, `steps` states of 2*G*G floats back to back.
 rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int64_t steps, cudaStream_t s) {
-    return dispatch_model<true>(g, fields, steps, nullptr, nullptr, traj, steps * 2 * (int64_t)g.G * g.G, s);
+    return dispatch_model<true>(g, fields, steps, nullptr, nullptr, traj, steps * 2 * (int64_t)g.G * g.G, s, 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -68,18 +68,20 @@ __global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int
                              int32_t *__restrict__ status_all) {
     const int p = blockIdx.x;
     const int64_t *Y = Yall + (int64_t)p * T * M;
+    extern __shared__ double ys[];   // [T][M]: y_t = Y_t / (n1 n2), one division each
     __shared__ double mu[32], cov[32 * 32], L[32 * 32];
     __shared__ int act[32];
     const double dnp = (double)np;
     const int tid = threadIdx.x;
+    for (int e = tid; e < T * M; e += blockDim.x) ys[e] = __ddiv_rn((double)Y[e], dnp);
+    __syncthreads();
     if (tid < M) {
         double s = 0.0;
         int same = 1;
         const int64_t y0 = Y[tid];
         for (int t = 0; t < T; ++t) {
-            int64_t yy = Y[(int64_t)t * M + tid];
-            s = __dadd_rn(s, __ddiv_rn((double)yy, dnp));
-            same &= (yy == y0);
+            s = __dadd_rn(s, ys[t * M + tid]);
+            same &= (Y[(int64_t)t * M + tid] == y0);
         }
         mu[tid] = __ddiv_rn(s, (double)T);
         act[tid] = same ? 0 : 1;
@@ -88,13 +90,20 @@ __global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int
     for (int e = tid; e < M * M; e += blockDim.x) {
         int k = e / M, l = e - k * M;
         double s = 0.0;
-        for (int t = 0; t < T; ++t) {
-            double a = __dsub_rn(__ddiv_rn((double)Y[(int64_t)t * M + k], dnp), mu[k]);
-            double b = __dsub_rn(__ddiv_rn((double)Y[(int64_t)t * M + l], dnp), mu[l]);
-            s = __dadd_rn(s, __dmul_rn(a, b));
+        if (l >= k) {   // symmetric: the (l, k) entry is the same sequence of operations
+            for (int t = 0; t < T; ++t) {
+                double a = __dsub_rn(ys[t * M + k], mu[k]);
+                double b = __dsub_rn(ys[t * M + l], mu[l]);
+                s = __dadd_rn(s, __dmul_rn(a, b));
+            }
+            cov[e] = __ddiv_rn(s, (double)(T - 1));
         }
-        cov[e] = __ddiv_rn(s, (double)(T - 1));
         L[e] = 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < M * M; e += blockDim.x) {
+        int k = e / M, l = e - k * M;
+        if (l < k) cov[e] = cov[l * M + k];
     }
     __syncthreads();
     if (tid == 0) {
@@ -166,6 +175,7 @@ extern "C" rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2,
         return RD_ERR_INVALID_ARG;
     double np = (double)n1 * (double)n2;
     if ((double)T * np * np >= 4.6e18) return RD_ERR_INVALID_ARG;
+    if ((int64_t)T * M > 24576) return RD_ERR_INVALID_ARG;   // y_t staged in shared memory
     cudaStream_t s = (cudaStream_t)stream;
     size_t smem = (size_t)(n1 + n2) * sizeof(int32_t);
     if (smem > 48 * 1024) {
@@ -179,7 +189,16 @@ extern "C" rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2,
     dim3 g((unsigned)T, (unsigned)n_problems);
     bootstrap_kernel<<<g, 256, smem, s>>>(d_bins, (int)n1, (int)n2, M, T, seed, d_Y);
     note_launch();
-    stats_kernel<<<(unsigned)n_problems, 256, 0, s>>>(d_Y, M, T, n1 * n2, d_y_obs, d_mu, d_cov, d_chol,
+    size_t smem2 = (size_t)T * M * sizeof(double);
+    if (smem2 > 48 * 1024) {
+        static size_t set2 = 0;
+        if (smem2 > set2) {
+            RD_CUDA_TRY(cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem2));
+            set2 = smem2;
+        }
+    }
+    stats_kernel<<<(unsigned)n_problems, 256, smem2, s>>>(d_Y, M, T, n1 * n2, d_y_obs, d_mu, d_cov, d_chol,
                                                       d_scalars, d_active, d_status);
     note_launch();
     return cuda_status(cudaGetLastError());

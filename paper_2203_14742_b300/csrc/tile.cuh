@@ -106,29 +106,52 @@ __device__ __forceinline__ void row_west_east(int tx, float first, float last, f
 // FP32 kinetics with coefficients folded with dt and (G-1)^2 on the host:
 //   cu = Du dt (G-1)^2, cv = Dv dt (G-1)^2, k1 = dt,
 //   FHN: k2 = eps dt, k3 = a;   GM: k2 = rho dt, k3 = mu.
+// GM is stepped in deviation form (see euler_cell): u0, v0 = the FP32
+// equilibrium (1/mu, 1/mu^2), tu0 = 2 u0, e0 = u0 - mu v0 and e1 = u0^2 - v0
+// (evaluated in FP64, rounded once; both are 0 when 1/mu is exact).
 struct CoefF {
     float cu, cv, k1, k2, k3;
+    float u0, v0, tu0, e0, e1;
 };
 
 inline CoefF make_coef(const GroupDev &g) {
     double g1 = (double)(g.G - 1);
     double h2 = g1 * g1;
-    CoefF c;
+    CoefF c{};
     c.cu = (float)(g.p[0] * g.dt * h2);
     c.cv = (float)(g.p[1] * g.dt * h2);
     c.k1 = (float)g.dt;
     if (g.model == RD_FHN || g.model == RD_GM) {
         c.k2 = (float)(g.p[2] * g.dt);
         c.k3 = (float)g.p[3];
-    } else {
-        c.k2 = 0.f;
-        c.k3 = 0.f;
+    }
+    if (g.model == RD_GM) {
+        double mu = g.p[3];
+        float u0 = (float)(1.0 / mu);
+        float v0 = (float)((double)u0 * (double)u0);
+        c.u0 = u0;
+        c.v0 = v0;
+        c.tu0 = 2.0f * u0;
+        c.e0 = (float)((double)u0 - mu * (double)v0);
+        c.e1 = (float)((double)u0 * (double)u0 - (double)v0);
     }
     return c;
 }
 
+// State registers hold (u, v) for FHN and DIFF, and the deviation (a, b) =
+// (u - u0, v - v0) from the FP32 equilibrium for GM.  These convert.
+template <int MODEL>
+__device__ __forceinline__ void to_state(float &u, float &v, const CoefF &c) {
+    if (MODEL == RD_GM) { u -= c.u0; v -= c.v0; }
+}
+template <int MODEL>
+__device__ __forceinline__ void from_state(float &u, float &v, const CoefF &c) {
+    if (MODEL == RD_GM) { u += c.u0; v += c.v0; }
+}
+
 // One explicit Euler update of a node given the unscaled 5-point sums
-// lu = (N + S + W + E - 4 c) for both species.
+// lu = (N + S + W + E - 4 c) for both species (of the state registers;
+// the Laplacian of a deviation equals that of the field).
 template <int MODEL>
 __device__ __forceinline__ void euler_cell(float u, float v, float lu, float lv, const CoefF &c, float &un,
                                            float &vn) {
@@ -138,11 +161,17 @@ __device__ __forceinline__ void euler_cell(float u, float v, float lu, float lv,
         un = fmaf(c.cu, lu, fmaf(c.k1, ru, u));
         vn = fmaf(c.cv, lv, fmaf(c.k2, fmaf(-c.k3, v, u), v));
     } else if (MODEL == RD_GM) {
-        // u + dt (Du Lap u + rho (u^2/v - mu u)),  v + dt (Dv Lap v + rho (u^2 - v))
-        float uu = u * u;
-        float q = __fdividef(uu, v);
-        un = fmaf(c.cu, lu, fmaf(c.k2, fmaf(-c.k3, u, q), u));
-        vn = fmaf(c.cv, lv, fmaf(c.k2, uu - v, v));
+        // Deviation form, exact in real arithmetic for U = u0 + a, V = v0 + b:
+        //   U^2/V - mu U = U (a - mu b + e0) / V,   U^2 - V = a (2 u0 + a) - b + e1
+        // so the increments carry the relative precision of the deviation
+        // rather than of the equilibrium value.
+        const float a = u, b = v;
+        float U = a + c.u0, V = b + c.v0;
+        float t = fmaf(-c.k3, b, a + c.e0);
+        float f = __fdividef(U * t, V);
+        float g = fmaf(a, a + c.tu0, c.e1 - b);
+        un = fmaf(c.cu, lu, fmaf(c.k2, f, a));
+        vn = fmaf(c.cv, lv, fmaf(c.k2, g, b));
     } else {
         un = fmaf(c.cu, lu, u);
         vn = fmaf(c.cv, lv, v);
@@ -180,6 +209,21 @@ __device__ __forceinline__ void tile_step(const float *hb, int tx, int ty, float
     }
 }
 
+template <int MODEL, int TY, int TX>
+__device__ __forceinline__ void tile_to_state(float (&u)[TY][TX], float (&v)[TY][TX], const CoefF &c) {
+#pragma unroll
+    for (int i = 0; i < TY; ++i)
+#pragma unroll
+        for (int j = 0; j < TX; ++j) to_state<MODEL>(u[i][j], v[i][j], c);
+}
+template <int MODEL, int TY, int TX>
+__device__ __forceinline__ void tile_from_state(float (&u)[TY][TX], float (&v)[TY][TX], const CoefF &c) {
+#pragma unroll
+    for (int i = 0; i < TY; ++i)
+#pragma unroll
+        for (int j = 0; j < TX; ++j) from_state<MODEL>(u[i][j], v[i][j], c);
+}
+
 template <int G, int TY, int TX>
 __device__ __forceinline__ void tile_load(const float *base, int tx, int ty, float (&u)[TY][TX], float (&v)[TY][TX]) {
     const int x0 = tx * TX, y0 = ty * TY;
@@ -198,6 +242,180 @@ __device__ __forceinline__ void tile_store(float *base, int tx, int ty, const fl
     for (int i = 0; i < TY; ++i) {
         st_row<TX>(base + (y0 + i) * G + x0, u[i]);
         st_row<TX>(base + G * G + (y0 + i) * G + x0, v[i]);
+    }
+}
+
+}  // namespace rdcil
+
+// ===========================================================================
+// Packed (u, v) tiles for the forward stepper.  Each node's two species sit
+// in one float2, so the 5-point sums of both species are single packed FP32
+// instructions (add.f32x2 / fma.f32x2 of sm_100-family GPUs) and the halo
+// moves are float4 (two nodes) wide.  Halo ring: [buf 2][edge 2][NY][G]
+// float2 (edge 0 = tile top row, 1 = tile bottom row).
+// ===========================================================================
+namespace rdcil {
+
+template <int G, int TY, int TX>
+struct Tiling2 {
+    static constexpr int NX = G / TX;
+    static constexpr int NY = G / TY;
+    static constexpr int NT = NX * NY;
+    static constexpr int HALO_F2 = 2 * 2 * NY * G;          // float2 entries, both buffers
+    static constexpr size_t SMEM = (size_t)HALO_F2 * sizeof(float2);
+    static_assert(TX % 2 == 0, "tile width must be even (float4 halo moves)");
+    static_assert(NX <= 32 && (NX & (NX - 1)) == 0, "tile row must fit a warp");
+    static_assert(NT % 32 == 0 && NT <= 1024, "block size");
+};
+
+template <int TX>
+__device__ __forceinline__ void st_row2(float2 *dst, const float2 (&a)[TX]) {
+#pragma unroll
+    for (int c = 0; c < TX; c += 2)
+        *reinterpret_cast<float4 *>(dst + c) = make_float4(a[c].x, a[c].y, a[c + 1].x, a[c + 1].y);
+}
+
+template <int TX>
+__device__ __forceinline__ void ld_row2(const float2 *src, float2 (&a)[TX]) {
+#pragma unroll
+    for (int c = 0; c < TX; c += 2) {
+        float4 t = *reinterpret_cast<const float4 *>(src + c);
+        a[c] = make_float2(t.x, t.y);
+        a[c + 1] = make_float2(t.z, t.w);
+    }
+}
+
+// global layout is [species][y][x]: load/store one tile row of each species
+template <int G, int TX>
+__device__ __forceinline__ void ld_row_g(const float *base, int y, int x0, float2 (&a)[TX]) {
+#pragma unroll
+    for (int c = 0; c < TX; c += 4) {
+        if (c + 4 <= TX) {
+            float4 u = *reinterpret_cast<const float4 *>(base + y * G + x0 + c);
+            float4 v = *reinterpret_cast<const float4 *>(base + G * G + y * G + x0 + c);
+            a[c] = make_float2(u.x, v.x); a[c + 1] = make_float2(u.y, v.y);
+            a[c + 2] = make_float2(u.z, v.z); a[c + 3] = make_float2(u.w, v.w);
+        } else {
+            float2 u = *reinterpret_cast<const float2 *>(base + y * G + x0 + c);
+            float2 v = *reinterpret_cast<const float2 *>(base + G * G + y * G + x0 + c);
+            a[c] = make_float2(u.x, v.x); a[c + 1] = make_float2(u.y, v.y);
+        }
+    }
+}
+
+template <int G, int TX>
+__device__ __forceinline__ void st_row_g(float *base, int y, int x0, const float2 (&a)[TX]) {
+#pragma unroll
+    for (int c = 0; c < TX; c += 4) {
+        if (c + 4 <= TX) {
+            *reinterpret_cast<float4 *>(base + y * G + x0 + c) = make_float4(a[c].x, a[c + 1].x, a[c + 2].x, a[c + 3].x);
+            *reinterpret_cast<float4 *>(base + G * G + y * G + x0 + c) =
+                make_float4(a[c].y, a[c + 1].y, a[c + 2].y, a[c + 3].y);
+        } else {
+            *reinterpret_cast<float2 *>(base + y * G + x0 + c) = make_float2(a[c].x, a[c + 1].x);
+            *reinterpret_cast<float2 *>(base + G * G + y * G + x0 + c) = make_float2(a[c].y, a[c + 1].y);
+        }
+    }
+}
+
+template <int G, int TY, int TX>
+__device__ __forceinline__ void tile2_load(const float *base, int tx, int ty, float2 (&w)[TY][TX]) {
+#pragma unroll
+    for (int i = 0; i < TY; ++i) ld_row_g<G, TX>(base, ty * TY + i, tx * TX, w[i]);
+}
+
+template <int G, int TY, int TX>
+__device__ __forceinline__ void tile2_store(float *base, int tx, int ty, const float2 (&w)[TY][TX]) {
+#pragma unroll
+    for (int i = 0; i < TY; ++i) st_row_g<G, TX>(base, ty * TY + i, tx * TX, w[i]);
+}
+
+template <int MODEL>
+__device__ __forceinline__ float2 to_state2(float2 w, const CoefF &c) {
+    if (MODEL == RD_GM) return __fadd2_rn(w, make_float2(-c.u0, -c.v0));
+    return w;
+}
+template <int MODEL>
+__device__ __forceinline__ float2 from_state2(float2 w, const CoefF &c) {
+    if (MODEL == RD_GM) return __fadd2_rn(w, make_float2(c.u0, c.v0));
+    return w;
+}
+
+// One Euler update of a node: C = (u, v) (or the GM deviation (a, b)),
+// L = packed unscaled 5-point sums of both species.
+template <int MODEL>
+__device__ __forceinline__ float2 euler2(float2 C, float2 L, const CoefF &c) {
+    const float2 cd = make_float2(c.cu, c.cv);
+    if (MODEL == RD_FHN) {
+        // (u - u^3 - v, u - a v) = (-u^2, -a) * (u, v) + (u - v, u)
+        const float u = C.x, v = C.y;
+        float2 R = __ffma2_rn(make_float2(-u * u, -c.k3), C, make_float2(u - v, u));
+        float2 in = __ffma2_rn(make_float2(c.k1, c.k2), R, C);
+        return __ffma2_rn(cd, L, in);
+    } else if (MODEL == RD_GM) {
+        const float a = C.x, b = C.y;
+        float2 UV = __fadd2_rn(C, make_float2(c.u0, c.v0));
+        float t = fmaf(-c.k3, b, a + c.e0);
+        float f = __fdividef(UV.x * t, UV.y);
+        float g = fmaf(a, a + c.tu0, c.e1 - b);
+        float2 in = __ffma2_rn(make_float2(c.k2, c.k2), make_float2(f, g), C);
+        return __ffma2_rn(cd, L, in);
+    } else {
+        return __ffma2_rn(cd, L, C);
+    }
+}
+
+template <int G, int TY, int TX>
+__device__ __forceinline__ void halo2_put(float2 *hb, int tx, int ty, const float2 (&w)[TY][TX]) {
+    constexpr int NY = Tiling2<G, TY, TX>::NY;
+    st_row2<TX>(hb + (0 * NY + ty) * G + tx * TX, w[0]);
+    st_row2<TX>(hb + (1 * NY + ty) * G + tx * TX, w[TY - 1]);
+}
+
+// One explicit Euler step of a packed tile (after halo2_put and a barrier).
+template <int MODEL, int G, int TY, int TX>
+__device__ __forceinline__ void tile2_step(const float2 *hb, int tx, int ty, float2 (&w)[TY][TX], const CoefF &cf) {
+    constexpr int NX = Tiling2<G, TY, TX>::NX, NY = Tiling2<G, TY, TX>::NY;
+    const float2 m4 = make_float2(-4.f, -4.f);
+    float2 pw[TX];
+    if (ty > 0) {
+        ld_row2<TX>(hb + (1 * NY + ty - 1) * G + tx * TX, pw);
+    } else {
+#pragma unroll
+        for (int c = 0; c < TX; ++c) pw[c] = w[0][c];
+    }
+#pragma unroll
+    for (int i = 0; i < TY; ++i) {
+        float2 sw[TX];
+        if (i + 1 < TY) {
+#pragma unroll
+            for (int c = 0; c < TX; ++c) sw[c] = w[i + 1][c];
+        } else if (ty < NY - 1) {
+            ld_row2<TX>(hb + (0 * NY + ty + 1) * G + tx * TX, sw);
+        } else {
+#pragma unroll
+            for (int c = 0; c < TX; ++c) sw[c] = w[TY - 1][c];
+        }
+        float2 west, east;
+        west.x = __shfl_up_sync(0xffffffffu, w[i][TX - 1].x, 1, NX);
+        west.y = __shfl_up_sync(0xffffffffu, w[i][TX - 1].y, 1, NX);
+        east.x = __shfl_down_sync(0xffffffffu, w[i][0].x, 1, NX);
+        east.y = __shfl_down_sync(0xffffffffu, w[i][0].y, 1, NX);
+        if (tx == 0) west = w[i][0];
+        if (tx == NX - 1) east = w[i][TX - 1];
+        float2 cw[TX];
+#pragma unroll
+        for (int c = 0; c < TX; ++c) cw[c] = w[i][c];
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            float2 Wn = c > 0 ? cw[c - 1] : west;
+            float2 En = c < TX - 1 ? cw[c + 1] : east;
+            float2 L = __fadd2_rn(__fadd2_rn(pw[c], sw[c]), __fadd2_rn(Wn, En));
+            L = __ffma2_rn(m4, cw[c], L);
+            w[i][c] = euler2<MODEL>(cw[c], L, cf);
+        }
+#pragma unroll
+        for (int c = 0; c < TX; ++c) pw[c] = cw[c];
     }
 }
 

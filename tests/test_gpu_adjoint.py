@@ -2,9 +2,13 @@
 adjoint, which the CPU suite pins to central finite differences.
 
 Tolerances: the GPU runs the forward and reverse recursions in FP32 (FP64
-only for the parameter accumulators), the oracle in FP64.  The smoothed
-integral C is compared at 1e-5 relative; the gradient at 2e-3 relative to
-its largest component (FP32 rounding of lambda through every reverse step).
+only for the parameter accumulators), the oracle in FP64.  A distance error
+dd moves C_k by at most max(sigma')/tau_k * dd = dd / (4 tau_k) =
+5 dd / R_k, so with field errors within the 1e-5 field tolerance and
+d <= R_0 the smoothed integral may differ by 5e-5 * R_0 / R_M absolute at
+most; the test uses 5e-5 absolute plus 1e-4 relative.  The gradient is
+compared at 2e-3 relative to its largest component (FP32 rounding of lambda
+through every reverse step).
 """
 import numpy as np
 import pytest
@@ -43,7 +47,7 @@ def compare(sim, f0, w0, set1, set2, radii, cot, model, par, dt, steps, mask, ta
     Cg, gg = sim.adjoint(0, f0, mask, set1, set2, torch.from_numpy(radii), tau, torch.from_numpy(cot))
     Co, go = oracle.smooth_cil_grad(model, par, dt, steps, w0, mask, set1, set2, radii, tau, cot)
     Cg, gg = Cg.cpu().numpy(), gg.cpu().numpy()
-    assert np.allclose(Cg, Co, rtol=1e-5, atol=1e-9)
+    assert np.allclose(Cg, Co, rtol=1e-4, atol=5e-5)
     scale = np.abs(go).max()
     assert np.abs(gg - go).max() <= 2e-3 * scale, (gg, go)
     return gg, go
