@@ -14,8 +14,9 @@
  *   eq. (cil:CF_synth).
  *
  * Readings of points the paper leaves open (each stated where used):
- *   - distance = plain Euclidean norm of the difference vector, evaluated as
- *     d^2 = sum_t (double(x_t) - double(y_t))^2 summed sequentially in t;
+ *   - distance = plain Euclidean norm of the difference vector; its FP64
+ *     evaluation order, which the paper does not fix, is fixed here (see
+ *     d2_f32): 256 interleaved partial sums combined by a halving tree;
  *   - R_k = R_{k-1} / b in FP64 (k = 1..M), thresholds T_k = R_k * R_k, and
  *     "d < R_k" is decided as d^2 < T_k;
  *   - covariance normaliser 1/(T-1);
@@ -34,16 +35,31 @@ int orc_adjoint_one(int model, int G, const double *p, double dt,
 void orc_step(int model, int G, int n_real, const double *p, double dt,
               int64_t n_steps, double *w);
 
-/* Squared distance of two FP32 patterns, sequential FP64 sum (eq. eCDF). */
+/* Squared distance of two FP32 patterns (eq. eCDF) in one fixed FP64 order:
+   term t = (double(x_t) - double(y_t))^2 goes to partial sum p[t mod 256],
+   each partial accumulated in increasing t; then every group of 32
+   consecutive partials is combined by halving (q[i] = q[i] + q[i + s] for
+   s = 16, 8, 4, 2, 1) and the 8 group results the same way (s = 4, 2, 1).
+   Every operation is rounded separately. */
 static double d2_f32(const float *x, const float *y, int64_t d)
 {
-    double acc = 0.0;
+    double p[256];
+    for (int j = 0; j < 256; ++j) p[j] = 0.0;
     for (int64_t t = 0; t < d; ++t) {
         double df = (double)x[t] - (double)y[t];
         double sq = df * df;
-        acc = acc + sq;
+        p[t % 256] = p[t % 256] + sq;
     }
-    return acc;
+    for (int g = 0; g < 8; ++g) {
+        double *q = p + 32 * g;
+        for (int s = 16; s >= 1; s /= 2)
+            for (int i = 0; i < s; ++i) q[i] = q[i] + q[i + s];
+    }
+    double w[8];
+    for (int g = 0; g < 8; ++g) w[g] = p[32 * g];
+    for (int s = 4; s >= 1; s /= 2)
+        for (int i = 0; i < s; ++i) w[i] = w[i] + w[i + s];
+    return w[0];
 }
 
 static double d2_f64(const double *x, const double *y, int64_t d)

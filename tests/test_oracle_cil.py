@@ -223,3 +223,30 @@ def test_inactive_constant_components():
     s = oracle.stats(Y, 10)
     assert list(s["active"]) == [0, 1, 0, 1]
     assert s["m_active"] == 2 and s["status"] == 0
+
+
+def test_canonical_order_matches_written_out_tree():
+    """The oracle's fixed FP64 order, written out here independently with
+    numpy float64 scalars: 256 interleaved partials, halving tree per group
+    of 32, then across the 8 groups."""
+    rng = np.random.default_rng(11)
+    for d in (1, 7, 255, 256, 257, 1000, 4100):
+        x = rng.normal(size=d).astype(np.float32)
+        y = rng.normal(size=d).astype(np.float32)
+        terms = [(np.float64(a) - np.float64(b)) ** 2 for a, b in zip(x, y)]
+        p = [np.float64(0.0)] * 256
+        for t, v in enumerate(terms):
+            p[t % 256] = p[t % 256] + v
+        for g in range(8):
+            s = 16
+            while s >= 1:
+                for i in range(s):
+                    p[32 * g + i] = p[32 * g + i] + p[32 * g + i + s]
+                s //= 2
+        w = [p[32 * g] for g in range(8)]
+        s = 4
+        while s >= 1:
+            for i in range(s):
+                w[i] = w[i] + w[i + s]
+            s //= 2
+        assert oracle.pair_d2(x[None], y[None])[0, 0] == w[0]
