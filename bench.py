@@ -136,6 +136,8 @@ def run_ours(args, rank, world, local_rank):
     mask = gd["species_mask"]
     d = G * G * (2 if mask == 3 else 1)
     sim = p.Simulation([grp], device=dev)
+    chosen = sim.autotune(steps=300)      # tile shape per (model, G); untimed set-up
+    variant = chosen[gd["model"] * 3 + {32: 0, 64: 1, 128: 2}[G]]
     fv = sim.group_fields(0).reshape(grp.n_real, 2 * G * G)
     X1, X2 = fv[:n1, :d], fv[n1:n1 + n2, :d]
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -273,6 +275,8 @@ def run_ours(args, rank, world, local_rank):
                    "pairs": n1 * n2, "pattern_dim": d, "radii": M, "resamples": T,
                    "l2": "flushed between timed steps (256 MB write)"},
         "pair_dists_per_s": pair_rate,
+        "cil_pairs_rechecked_exactly": int(c["n_rechecked"]),
+        "stepper_variant": variant,
         "cil_ms": cil_avg,
         "stepper_ms": k_avg_ms,
         "e2e": {"value": cell_updates * world / (e2e_ms * 1e-3), "unit": "cell-updates/s",

@@ -1,8 +1,10 @@
 // Correlation integral of two pattern sets (eq. eCDF, eq. CIL, Sec. 2.1).
 //
 // Exactness contract.  For every pair the library decides K_ij =
-// #{k : d2_ij < R_k^2} for the canonical d2_ij = sum_t (x_t - y_t)^2 summed
-// in t order in FP64 without FMA.  It does so in three stages:
+// #{k : d2_ij < R_k^2} for the canonical d2_ij = sum_t (x_t - y_t)^2
+// evaluated in FP64 in one fixed order (term t into partial t mod 256, each
+// partial in increasing t, partials combined by a halving tree within groups
+// of 32 and then across the 8 groups; no FMA).  It does so in three stages:
 //   1. pack:  centre every pattern by the set mean c (translation does not
 //      change distances), split x - c into bf16 hi + lo, and record per
 //      pattern N = |hi+lo|^2, H = |hi| + |lo|, L = |lo| and the
@@ -34,8 +36,10 @@ struct CilWork {
     __nv_bfloat16 *lo;      // [(n1+n2)][dp]
     double *N, *H, *L, *E;  // [(n1+n2)]
     float *Ppart;           // [nchunk][n1][n2]
-    double *A, *Mg;         // [n1*n2] approximate d2 and its error bound
-    unsigned long long *scal;  // [0] max lower bound, [1] max upper bound, [2] exact max (FP64 bits), [3] n_rechecked
+    double *A, *Mg;         // [n1*n2] approximate d2 and its error bound (Mg < 0: A is exact)
+    unsigned long long *queue; // [n1*n2] pairs to evaluate exactly (bit 63: may hold the maximum)
+    unsigned long long *scal;  // [0] max lower bound, [1] max upper bound, [2] exact max (FP64 bits),
+                               // [3] n_rechecked, [4] queue length
     size_t bytes;
 };
 
@@ -67,7 +71,8 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     w.Ppart = (float *)take(sizeof(float) * w.nchunk * n1 * n2);
     w.A = (double *)take(sizeof(double) * n1 * n2);
     w.Mg = (double *)take(sizeof(double) * n1 * n2);
-    w.scal = (unsigned long long *)take(sizeof(unsigned long long) * 4);
+    w.queue = (unsigned long long *)take(sizeof(unsigned long long) * n1 * n2);
+    w.scal = (unsigned long long *)take(sizeof(unsigned long long) * 8);
     w.bytes = off;
     return w;
 }
@@ -80,29 +85,42 @@ __device__ __forceinline__ double sq_diff(float a, float b) {
     return __dmul_rn(df, df);
 }
 
-__device__ __forceinline__ double canonical_d2(const float *__restrict__ x, const float *__restrict__ y,
-                                               int64_t d) {
+// Canonical d2 of one pair by a whole 256-thread block, in the fixed order
+// above.  FP64 has a long dependent-operation latency on this GPU, so the
+// order is chosen for a short dependency chain: d/256 + 8 additions.
+// Result valid in thread 0; sw = 8 doubles of shared memory.
+__device__ double canonical_block(const float *__restrict__ x, const float *__restrict__ y, int64_t d,
+                                  double *sw) {
+    const int j = threadIdx.x, lane = j & 31, warp = j >> 5;
     double acc = 0.0;
-    int64_t t = 0;
-    if ((((uintptr_t)x | (uintptr_t)y) & 15) == 0) {
-        // 8 elements per iteration from float4 loads issued ahead of the
-        // (strictly sequential) FP64 accumulation
-        for (; t + 8 <= d; t += 8) {
-            float4 a0 = __ldg(reinterpret_cast<const float4 *>(x + t));
-            float4 a1 = __ldg(reinterpret_cast<const float4 *>(x + t + 4));
-            float4 b0 = __ldg(reinterpret_cast<const float4 *>(y + t));
-            float4 b1 = __ldg(reinterpret_cast<const float4 *>(y + t + 4));
-            double q0 = sq_diff(a0.x, b0.x), q1 = sq_diff(a0.y, b0.y), q2 = sq_diff(a0.z, b0.z),
-                   q3 = sq_diff(a0.w, b0.w), q4 = sq_diff(a1.x, b1.x), q5 = sq_diff(a1.y, b1.y),
-                   q6 = sq_diff(a1.z, b1.z), q7 = sq_diff(a1.w, b1.w);
-            acc = __dadd_rn(acc, q0); acc = __dadd_rn(acc, q1);
-            acc = __dadd_rn(acc, q2); acc = __dadd_rn(acc, q3);
-            acc = __dadd_rn(acc, q4); acc = __dadd_rn(acc, q5);
-            acc = __dadd_rn(acc, q6); acc = __dadd_rn(acc, q7);
-        }
+    for (int64_t t = j; t < d; t += 256) acc = __dadd_rn(acc, sq_diff(__ldg(x + t), __ldg(y + t)));
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(0xffffffffu, acc, s));
+    if (lane == 0) sw[warp] = acc;
+    __syncthreads();
+    double r = 0.0;
+    if (j == 0) {
+        double w[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) w[g] = sw[g];
+#pragma unroll
+        for (int s = 4; s >= 1; s >>= 1)
+#pragma unroll
+            for (int i = 0; i < s; ++i) w[i] = __dadd_rn(w[i], w[i + s]);
+        r = w[0];
     }
-    for (; t < d; ++t) acc = __dadd_rn(acc, sq_diff(__ldg(x + t), __ldg(y + t)));
-    return acc;
+    __syncthreads();
+    return r;
+}
+
+// FP32 error-free sum accumulation (Knuth TwoSum): (hi, lo) holds a value
+// whose lo part collects the rounding errors of the hi part.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
+    float s = hi + v;
+    float bb = s - hi;
+    float e = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += e;
 }
 
 // ---------------------------------------------------------------------------
@@ -114,10 +132,12 @@ __global__ void centre_kernel(const float *__restrict__ X1, int64_t ld1, int64_t
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= dp) return;
     if (t >= d) { centre[t] = 0.f; return; }
-    double s = 0.0;
-    for (int64_t i = 0; i < n1; ++i) s += (double)X1[i * ld1 + t];
-    for (int64_t j = 0; j < n2; ++j) s += (double)X2[j * ld2 + t];
-    centre[t] = (float)(s / (double)(n1 + n2));
+    // any centre is valid (distances are translation invariant); a good one
+    // keeps |x - c| small so the bf16 split loses little
+    float s = 0.f;
+    for (int64_t i = 0; i < n1; ++i) s += X1[i * ld1 + t];
+    for (int64_t j = 0; j < n2; ++j) s += X2[j * ld2 + t];
+    centre[t] = s / (float)(n1 + n2);
 }
 
 __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n1,
@@ -127,47 +147,62 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
                             double *__restrict__ Ln, double *__restrict__ En) {
     const int64_t i = blockIdx.x;
     const float *x = i < n1 ? X1 + i * ld1 : X2 + (i - n1) * ld2;
-    double sN = 0.0, sH = 0.0, sL = 0.0, sE = 0.0;
+    // N = |hi + lo|^2 to ~2^-44 relative (compensated FP32); H, L, E are
+    // upper bounds (plain FP32 sums, inflated below)
+    float nh = 0.f, nl = 0.f, sH = 0.f, sL = 0.f, sE = 0.f;
     for (int64_t t = threadIdx.x; t < dp; t += blockDim.x) {
         __nv_bfloat16 h = __float2bfloat16_rn(0.f), l = __float2bfloat16_rn(0.f);
         if (t < d) {
             float xv = x[t], cv = centre[t];
             float xc = xv - cv;
+            // exact rounding error of x - c (TwoSum of x and -c)
+            float bb = xc - xv;
+            float dc = (xv - (xc - bb)) - (cv + bb);
             h = __float2bfloat16_rn(xc);
-            float r = xc - __bfloat162float(h);   // exact in FP32
+            float hf = __bfloat162float(h);
+            float r = xc - hf;                 // exact
             l = __float2bfloat16_rn(r);
-            double hd = (double)__bfloat162float(h), ld = (double)__bfloat162float(l);
-            double s = hd + ld;                    // exact
-            sN += s * s;
-            sH += hd * hd;
-            sL += ld * ld;
-            double e = ((double)xv - (double)cv) - s;
-            sE += e * e;
+            float lf = __bfloat162float(l);
+            float sv = hf + lf;                // exact
+            float p = sv * sv;
+            float pe = fmaf(sv, sv, -p);       // exact error of the square
+            two_sum_acc(nh, nl, p);
+            nl += pe;
+            sH = fmaf(hf, hf, sH);
+            sL = fmaf(lf, lf, sL);
+            float e = fabsf(dc) + fabsf(r - lf);   // |(x - c) - (hi + lo)|, bounded
+            sE = fmaf(e, e, sE);
         }
         hi[i * dp + t] = h;
         lo[i * dp + t] = l;
     }
-    __shared__ double red[4][32];
+    __shared__ float red[5][32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        sN += __shfl_xor_sync(0xffffffffu, sN, o);
+        // combine (hi, lo) pairs error-free across lanes
+        float oh = __shfl_xor_sync(0xffffffffu, nh, o), ol = __shfl_xor_sync(0xffffffffu, nl, o);
+        two_sum_acc(nh, nl, oh);
+        nl += ol;
         sH += __shfl_xor_sync(0xffffffffu, sH, o);
         sL += __shfl_xor_sync(0xffffffffu, sL, o);
         sE += __shfl_xor_sync(0xffffffffu, sE, o);
     }
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { red[0][warp] = sN; red[1][warp] = sH; red[2][warp] = sL; red[3][warp] = sE; }
+    if (lane == 0) { red[0][warp] = nh; red[1][warp] = nl; red[2][warp] = sH; red[3][warp] = sL; red[4][warp] = sE; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0, b = 0, c = 0, e = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; c += red[2][w]; e += red[3][w]; }
-        // FP64 sums of d non-negative terms: relative error below d*2^-53;
-        // inflate so the recorded values are upper bounds where needed.
-        double infl = 1.0 + (double)(dp + 8) * 2.3e-16;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += (double)red[0][w] + (double)red[1][w];
+            b += red[2][w]; c += red[3][w]; e += red[4][w];
+        }
+        // FP32 sums of at most dp non-negative terms: relative error below
+        // dp * 2^-23; inflate the bounds by that much (and 1e-6 more).
+        double infl = 1.0 + (double)(dp + 64) * 1.2e-7 + 1e-6;
         Nn[i] = a;
-        Hn[i] = (sqrt(b) + sqrt(c)) * infl;
-        Ln[i] = sqrt(c) * infl;
-        En[i] = sqrt(e) * infl * (1.0 + 1e-12) + 1e-300;
+        Hn[i] = (sqrt(b * infl) + sqrt(c * infl)) * (1.0 + 1e-12);
+        Ln[i] = sqrt(c * infl) * (1.0 + 1e-12);
+        En[i] = sqrt(e * infl) * (1.0 + 1e-12) + 1e-300;
     }
 }
 
@@ -243,8 +278,9 @@ __device__ __forceinline__ void approx_and_bound(const CilWork &w, int64_t i, in
     const int64_t a = i, b = w.n1 + j;
     const double Ni = w.N[a], Nj = w.N[b];
     A = (Ni + Nj) - 2.0 * P;
+    // N_i, N_j carry <= (dp + 64) 2^-44 relative error (compensated FP32)
     double eg = 2.0 * (gam * w.H[a] * w.H[b] + w.L[a] * w.L[b]) +
-                4.0 * (double)(w.dp + 8) * 1.1102230246251565e-16 * (Ni + Nj + 2.0 * fabs(P));
+                4.0 * (double)(w.dp + 64) * 5.684341886080802e-14 * (Ni + Nj + 2.0 * fabs(P));
     double up = fmax(A + eg, 0.0);
     double D = w.E[a] + w.E[b];
     double er = D * (2.0 * sqrt(up) + D);
@@ -258,8 +294,9 @@ __global__ void d2_bound_kernel(CilWork w, double gam) {
     double lb = 0.0, ub = 0.0;
     if (q < np) {
         int64_t i = q / w.n2, j = q - i * w.n2;
-        double P = 0.0;
-        for (int64_t c = 0; c < w.nchunk; ++c) P += (double)w.Ppart[c * np + q];
+        float ph = 0.f, pl = 0.f;
+        for (int64_t c = 0; c < w.nchunk; ++c) two_sum_acc(ph, pl, w.Ppart[c * np + q]);
+        double P = (double)ph + (double)pl;
         double A, m;
         approx_and_bound(w, i, j, P, gam, A, m);
         w.A[q] = A;
@@ -279,45 +316,58 @@ __global__ void d2_bound_kernel(CilWork w, double gam) {
     }
 }
 
-// 3b. exact pass: the canonical sum for every pair that could hold the
+// 3b. exact pass.  classify_kernel enqueues every pair that could hold the
 //     maximum (upper bound >= the largest lower bound) or whose interval
 //     could contain a threshold.  Before R0 is known exactly, R0^2 lies in
 //     [lbmax, ubmax], so T_k = (R0 b^-k)^2 lies in [lbmax b^-2k, ubmax b^-2k]
 //     up to the rounding of the radius recursion (relative 1e-13 margin).
-//     Exact values overwrite A with Mg = -1 as the flag.
-__global__ void exact_pass_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
-                                  const float *__restrict__ X2, int64_t ld2, const double *__restrict__ radii_in,
-                                  double b, int M) {
+//     canonical_kernel then evaluates the queued pairs (one block each) and
+//     overwrites A with the exact value, Mg = -1 as the flag.
+__global__ void classify_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M, int all) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t np = w.n1 * w.n2;
     if (q >= np) return;
-    const double A = w.A[q], m = w.Mg[q];
-    const double lo = A - m, hi = A + m;
-    bool need = false;
+    bool need = all != 0, maxc = false;
     if (!radii_in) {
         const double lbmax = __longlong_as_double((long long)w.scal[0]);
         const double ubmax = __longlong_as_double((long long)w.scal[1]);
-        need = hi >= lbmax;
+        const double lo = all ? 0.0 : w.A[q] - w.Mg[q], hi = all ? 1.0 : w.A[q] + w.Mg[q];
+        maxc = all || hi >= lbmax;
+        need = need || maxc;
         double f = 1.0;
         for (int k = 0; k < M && !need; ++k) {
             f = f / (b * b);
             double tlo = lbmax * f * (1.0 - 1e-13), thi = ubmax * f * (1.0 + 1e-13);
             need = !(hi < tlo || lo > thi);
         }
-    } else {
+    } else if (!need) {
+        const double lo = w.A[q] - w.Mg[q], hi = w.A[q] + w.Mg[q];
         for (int k = 0; k < M && !need; ++k) {
             double T = __dmul_rn(radii_in[k], radii_in[k]);
             need = !(hi < T || lo >= T);
         }
     }
     if (!need) return;
-    int64_t i = q / w.n2, j = q - i * w.n2;
-    double e = canonical_d2(X1 + i * ld1, X2 + j * ld2, w.d);
-    w.A[q] = e;
-    w.Mg[q] = -1.0;
-    if (!radii_in && hi >= __longlong_as_double((long long)w.scal[0]))
-        atomicMax(&w.scal[2], (unsigned long long)__double_as_longlong(e));
-    atomicAdd(&w.scal[3], 1ull);
+    unsigned long long slot = atomicAdd(&w.scal[4], 1ull);
+    w.queue[slot] = (unsigned long long)q | (maxc ? (1ull << 63) : 0ull);
+}
+
+__global__ void __launch_bounds__(256) canonical_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
+                                                        const float *__restrict__ X2, int64_t ld2, int count) {
+    __shared__ double sw[8];
+    const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[4];
+    for (unsigned long long qi = blockIdx.x; qi < qlen; qi += gridDim.x) {
+        const unsigned long long ent = w.queue[qi];
+        const int64_t q = (int64_t)(ent & ~(1ull << 63));
+        const int64_t i = q / w.n2, j = q - i * w.n2;
+        double e = canonical_block(X1 + i * ld1, X2 + j * ld2, w.d, sw);
+        if (threadIdx.x == 0) {
+            w.A[q] = e;
+            w.Mg[q] = -1.0;
+            if (ent >> 63) atomicMax(&w.scal[2], (unsigned long long)__double_as_longlong(e));
+            if (count) atomicAdd(&w.scal[3], 1ull);
+        }
+    }
 }
 
 // 3c. radii: R0 = sqrt(max), R_k = R_{k-1}/b  (or copy the given radii)
@@ -339,9 +389,7 @@ __global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, dou
 
 // 3d. bins and counts.  A pair is classified from [A - m, A + m] when no
 //     threshold T_k = R_k*R_k falls inside; otherwise from the canonical sum.
-__global__ void bins_counts_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
-                                   const float *__restrict__ X2, int64_t ld2,
-                                   const double *__restrict__ radii_out, int M, int exact_all,
+__global__ void bins_counts_kernel(CilWork w, const double *__restrict__ radii_out, int M,
                                    uint8_t *__restrict__ bins, unsigned long long *__restrict__ counts) {
     __shared__ double Tk[32];
     __shared__ unsigned long long cnt[32];
@@ -357,8 +405,8 @@ __global__ void bins_counts_kernel(CilWork w, const float *__restrict__ X1, int6
     int64_t np = w.n1 * w.n2;
     int K = 0;
     if (q < np) {
-        bool amb = exact_all != 0;
-        if (!amb) {
+        bool amb = false;
+        {
             const double A = w.A[q], m = w.Mg[q];
             if (m < 0.0) {
                 for (int k = 0; k < M; ++k) K += (A < Tk[k]) ? 1 : 0;
@@ -370,17 +418,16 @@ __global__ void bins_counts_kernel(CilWork w, const float *__restrict__ X1, int6
                 }
             }
         }
+        // A pair the exact pass did not foresee cannot occur (its interval would
+        // straddle a threshold inside the predicted range); flag it loudly.
         if (amb) {
-            // exact path, or a pair the exact pass did not foresee (defensive)
-            int64_t i = q / w.n2, j = q - i * w.n2;
-            double e = canonical_d2(X1 + i * ld1, X2 + j * ld2, w.d);
-            K = 0;
-            for (int k = 0; k < M; ++k) K += (e < Tk[k]) ? 1 : 0;
-            if (!exact_all) atomicAdd(&w.scal[3], 1ull);
+            K = 0xFF;
+            atomicOr(&w.scal[5], 1ull);
         }
         bins[q] = (uint8_t)K;
     }
     const int lane = threadIdx.x & 31;
+    if (K == 0xFF) K = 0;
     for (int k = 0; k < M; ++k) {
         unsigned bal = __ballot_sync(0xffffffffu, K >= k + 1);
         if (lane == 0 && bal) atomicAdd(&cnt[k], (unsigned long long)__popc(bal));
@@ -389,20 +436,10 @@ __global__ void bins_counts_kernel(CilWork w, const float *__restrict__ X1, int6
     if ((int)threadIdx.x < M && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], cnt[threadIdx.x]);
 }
 
-// exact path: canonical sum for every pair into A (used for the maximum)
-__global__ void exact_all_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
-                                 const float *__restrict__ X2, int64_t ld2) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t np = w.n1 * w.n2;
-    if (q >= np) return;
-    int64_t i = q / w.n2, j = q - i * w.n2;
-    double e = canonical_d2(X1 + i * ld1, X2 + j * ld2, w.d);
-    atomicMax(&w.scal[2], (unsigned long long)__double_as_longlong(e));
-}
-
 __global__ void finish_kernel(CilWork w, int64_t *n_rechecked, const int64_t *counts, int M, double *Cv) {
     if (blockIdx.x != 0) return;
-    if (threadIdx.x == 0 && n_rechecked) *n_rechecked = (int64_t)w.scal[3];
+    // a set scal[5] (unforeseen ambiguous pair) reports -1 rechecks
+    if (threadIdx.x == 0 && n_rechecked) *n_rechecked = w.scal[5] ? -1 : (int64_t)w.scal[3];
     if (Cv && (int)threadIdx.x < M)
         Cv[threadIdx.x] = __ddiv_rn((double)counts[threadIdx.x], (double)w.n1 * (double)w.n2);
 }
@@ -443,12 +480,9 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
     cudaStream_t s = (cudaStream_t)stream;
     int64_t np = n1 * n2;
     unsigned gp = (unsigned)((np + 255) / 256);
-    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 4 * sizeof(unsigned long long), s));
+    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 8 * sizeof(unsigned long long), s));
     RD_CUDA_TRY(cudaMemsetAsync(counts, 0, M * sizeof(int64_t), s));
-    if (exact) {
-        if (!radii_in) exact_all_kernel<<<gp, 256, 0, s>>>(w, X1, ld1, X2, ld2);
-        note_launch();
-    } else {
+    if (!exact) {
         centre_kernel<<<(unsigned)((w.dp + 255) / 256), 256, 0, s>>>(X1, ld1, n1, X2, ld2, n2, d, w.dp, w.centre);
         note_launch();
         pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(X1, ld1, n1, X2, ld2, d, w.dp, w.centre, w.hi, w.lo, w.N,
@@ -457,18 +491,25 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
         dim3 gg((unsigned)((n2 + 63) / 64), (unsigned)((n1 + 63) / 64), (unsigned)w.nchunk);
         gram_simt_kernel<<<gg, 256, 0, s>>>(w.hi, w.lo, n1, n2, w.dp, w.kc, w.Ppart);
         note_launch();
-        // SIMT Gram: 3*kc fused multiply-adds per accumulator, each
-        // rounding to nearest (2^-24), plus margin for the chunk bookkeeping.
-        const double gam = (3.0 * (double)w.kc + 64.0) * 5.9604644775390625e-8;
+        // SIMT Gram: 3*kc fused multiply-adds per accumulator, each rounding
+        // to nearest (2^-24), plus margin; the chunk partials are summed by a
+        // compensated FP32 sum ((nchunk + 4) 2^-45 of the magnitudes).
+        const double gam = (3.0 * (double)w.kc + 64.0) * 5.9604644775390625e-8 +
+                           (double)(w.nchunk + 4) * 2.842170943040401e-14;
         d2_bound_kernel<<<gp, 256, 0, s>>>(w, gam);
         note_launch();
-        exact_pass_kernel<<<gp, 256, 0, s>>>(w, X1, ld1, X2, ld2, radii_in, b, M);
+    }
+    classify_kernel<<<gp, 256, 0, s>>>(w, radii_in, b, M, exact ? 1 : 0);
+    note_launch();
+    {
+        int64_t ncta = 2 * 148;
+        if (ncta > np) ncta = np;
+        canonical_kernel<<<(unsigned)ncta, 256, 0, s>>>(w, X1, ld1, X2, ld2, exact ? 0 : 1);
         note_launch();
     }
     radii_kernel<<<1, 32, 0, s>>>(w, radii_in, b, M, radii_out);
     note_launch();
-    bins_counts_kernel<<<gp, 256, 0, s>>>(w, X1, ld1, X2, ld2, radii_out, M, exact ? 1 : 0, bins,
-                                          (unsigned long long *)counts);
+    bins_counts_kernel<<<gp, 256, 0, s>>>(w, radii_out, M, bins, (unsigned long long *)counts);
     note_launch();
     finish_kernel<<<1, 32, 0, s>>>(w, n_rechecked, counts, M, Cv);
     note_launch();

@@ -30,6 +30,9 @@ def run_both(p, X1, X2, b=1.3, M=16, radii=None, exact=False):
     r = torch.from_numpy(np.asarray(radii, np.float64)) if radii is not None else None
     g = fn(t1, t2, b=b, M=M, radii=r)
     o = oracle.cil(X1, X2, b=b, M=M, radii_=radii)
+    # -1 would mean a pair whose bound straddled a threshold the exact pass
+    # did not foresee
+    assert int(g["n_rechecked"]) >= 0
     return g, o
 
 
