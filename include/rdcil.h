@@ -213,6 +213,26 @@ rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1,
                        double *d_C, int64_t *d_n_rechecked, void *d_work, size_t work_bytes,
                        void *stream);
 
+/* cil_features_static — cil_features for callers that cannot allocate
+ * device memory on their hot path (cudaMalloc may synchronise the whole
+ * device; some host applications own all device memory through their own
+ * pool and forbid plug-in allocations).  The paper has no counterpart: this
+ * is a deployment variant.  Same arguments, definitions and outputs as
+ * cil_features, but no workspace: the scratch is one 16 MiB file-scope
+ * device array that every GPU loading the library holds until the process
+ * exits.  Limits: n1, n2 <= 128, d <= 8192 (RD_ERR_INVALID_ARG otherwise).
+ * The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the one array: calls whose GPU work overlaps (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The call allocates nothing (no cudaMalloc/cudaFree, no allocating
+ * library routine); it clears what it needs cleared itself. */
+rd_status cil_features_static(const float *d_X1, int64_t ld1, int64_t n1,
+                              const float *d_X2, int64_t ld2, int64_t n2, int64_t d,
+                              const double *d_radii_in, double b, int32_t M,
+                              double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
+                              double *d_C, int64_t *d_n_rechecked, void *stream);
+
 /* cil_features_exact — the same outputs with every pair evaluated by the
  * exact sequential FP64 sum (no Gram product).  Slow; for checking. */
 rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1,

@@ -531,3 +531,59 @@ extern "C" rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t 
     return cil_run(d_X1, ld1, n1, d_X2, ld2, n2, d, d_radii_in, b, M, d_radii_out, d_bins, d_counts, d_C,
                    nullptr, d_work, work_bytes, stream, true);
 }
+
+// ===========================================================================
+// Allocation-free variant of cil_features.
+//
+// Some callers cannot call cudaMalloc on the hot path: cudaMalloc may
+// synchronise the whole device (stalling every other stream of a sampler
+// that overlaps model runs with likelihood evaluations), and hosts that own
+// a fixed device-memory budget through their own pool allocator do not let
+// plug-in code allocate outside it.  This entry point needs no workspace
+// from the caller: its scratch is one file-scope device array of
+// CIL_STATIC_BYTES, held by every GPU that loads the library until the
+// process exits.
+// ===========================================================================
+#include <mutex>
+
+namespace rdcil {
+static constexpr size_t CIL_STATIC_BYTES = 16u << 20;     // 16 MiB per device
+static constexpr int64_t CIL_STATIC_MAX_N = 128;          // patterns per set
+static constexpr int64_t CIL_STATIC_MAX_D = 8192;         // pattern length
+static __device__ __align__(256) unsigned char g_cil_static_scratch[CIL_STATIC_BYTES];
+
+// Device address of the array, looked up once per device with that device
+// current (in host code the array's name is only a host-side stand-in).
+static void *static_scratch_ptr(int device, rd_status &st) {
+    static std::mutex mu;
+    static void *ptrs[64] = {nullptr};
+    st = RD_OK;
+    if (device < 0 || device >= 64) { st = RD_ERR_UNSUPPORTED; return nullptr; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_cil_static_scratch) != cudaSuccess || !p) {
+            st = RD_ERR_CUDA;
+            return nullptr;
+        }
+        ptrs[device] = p;
+    }
+    return ptrs[device];
+}
+}  // namespace rdcil
+
+extern "C" rd_status cil_features_static(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                         int64_t ld2, int64_t n2, int64_t d, const double *d_radii_in, double b,
+                                         int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
+                                         double *d_C, int64_t *d_n_rechecked, void *stream) {
+    if (n1 > CIL_STATIC_MAX_N || n2 > CIL_STATIC_MAX_N || d > CIL_STATIC_MAX_D) return RD_ERR_INVALID_ARG;
+    if (n1 < 1 || n2 < 1 || d < 1) return RD_ERR_INVALID_ARG;
+    if (layout(n1, n2, d, nullptr).bytes > CIL_STATIC_BYTES) return RD_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RD_ERR_CUDA;
+    rd_status st;
+    void *scratch = static_scratch_ptr(dev, st);
+    if (st) return st;
+    return cil_features(d_X1, ld1, n1, d_X2, ld2, n2, d, d_radii_in, b, M, d_radii_out, d_bins, d_counts, d_C,
+                        d_n_rechecked, scratch, CIL_STATIC_BYTES, stream);
+}
