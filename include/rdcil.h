@@ -195,7 +195,10 @@ const char *rd_status_str(rd_status s);
  *   (row i, column j); d_counts[M] int64; d_C (nullable) float64[M], the
  *   correlation integral vector C(R_k) = counts[k-1] / (n1 n2) (eq. CIL);
  *   d_n_rechecked (nullable) int64: pairs whose distance had to be
- *   evaluated exactly.
+ *   evaluated exactly; -2 if the tensor-core stage timed out (a bounded
+ *   wait expired; outputs invalid), -1 if an approximate interval
+ *   straddled a threshold that the exact pass did not foresee (outputs
+ *   invalid; not expected to occur).
  *
  * Method: the patterns are centred and split into bf16 hi + lo parts; a
  * tensor-core Gram product (FP32 accumulation) gives
@@ -232,6 +235,15 @@ rd_status cil_features_static(const float *d_X1, int64_t ld1, int64_t n1,
                               const double *d_radii_in, double b, int32_t M,
                               double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
                               double *d_C, int64_t *d_n_rechecked, void *stream);
+
+/* cil_debug_approx — checking entry point: for every pair, the approximate
+ * d2 (A, from the centred bf16 hi/lo tensor-core Gram) and the rigorous
+ * bound m with |A - d2| <= m that cil_features relies on, before any exact
+ * evaluation.  d_A, d_m: float64 [n1*n2].  Same workspace as cil_features. */
+rd_status cil_debug_approx(const float *d_X1, int64_t ld1, int64_t n1,
+                           const float *d_X2, int64_t ld2, int64_t n2, int64_t d,
+                           double *d_A, double *d_m, void *d_work, size_t work_bytes,
+                           void *stream);
 
 /* cil_features_exact — the same outputs with every pair evaluated by the
  * exact sequential FP64 sum (no Gram product).  Slow; for checking. */

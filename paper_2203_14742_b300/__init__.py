@@ -51,6 +51,7 @@ _SIGS = {
                             _vp, _vp, _vp, _sz, _vp]),
     "cil_features_exact": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _dbl, _i32, _vp, _vp,
                                   _vp, _vp, _vp, _sz, _vp]),
+    "cil_debug_approx": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _sz, _vp]),
     "synlik_stats": (_i32, [_vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                             _vp, _vp, _vp]),
     "rd_kernel_launches": (_u64, []),
@@ -277,6 +278,18 @@ def _cil_call(fn, X1, X2, b, M, radii, work=None):
     _check(fn, getattr(lib(), fn)(*args))
     return {"R0": radii_out[0], "radii": radii_out[1:], "bins": bins, "counts": counts, "C": Cvec,
             "n_rechecked": nre}
+
+
+def cil_approx(X1, X2):
+    """(A, m): approximate squared distances and their error bounds (checking)."""
+    X1, ld1, n1, d = _as_rows(X1)
+    X2, ld2, n2, _ = _as_rows(X2)
+    A = torch.empty((n1, n2), dtype=torch.float64, device=X1.device)
+    m = torch.empty_like(A)
+    w, wb = _workspace(n1, n2, d, X1.device)
+    _check("cil_debug_approx", lib().cil_debug_approx(_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, d, _ptr(A),
+                                                      _ptr(m), _ptr(w), wb, _stream()))
+    return A, m
 
 
 def cil(X1, X2, b=1.3, M=16, radii=None, work=None):

@@ -23,7 +23,10 @@
 
 namespace rdcil {
 
-static constexpr int KCHUNK_MAX = 2048;  // longest split-K chunk (bounds FP32 accumulation error)
+rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2, int64_t dp, int64_t kc,
+                         int64_t nchunk, float *Ppart, uint32_t *status, cudaStream_t s);
+
+static constexpr int KCHUNK_MAX = 512;   // longest split-K chunk (bounds FP32 accumulation error)
 static constexpr int PAD = 64;           // padded pattern length granularity
 static constexpr int TILE = 64;          // Gram output tile (pairs per side)
 
@@ -207,63 +210,8 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
 }
 
 // ---------------------------------------------------------------------------
-// 2. Gram product on CUDA cores (bf16 operands, FP32 accumulation, split-K)
-//    tile 64x64 pairs, K step 32, 256 threads, 4x4 outputs per thread
+// 2. Gram product: tensor cores (gram_tc.cu), split-K chunks of kc.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) gram_simt_kernel(const __nv_bfloat16 *__restrict__ hi,
-                                                        const __nv_bfloat16 *__restrict__ lo, int64_t n1,
-                                                        int64_t n2, int64_t dp, int64_t kc,
-                                                        float *__restrict__ Ppart) {
-    __shared__ float sAh[32][65], sAl[32][65], sBh[32][65], sBl[32][65];
-    const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
-    const int64_t k_begin = (int64_t)blockIdx.z * kc;
-    const int64_t k_end = min(dp, k_begin + kc);
-    const int tid = threadIdx.x;
-    const int ti = tid / 16, tj = tid % 16;
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    const __nv_bfloat16 *Bh = hi + n1 * dp, *Bl = lo + n1 * dp;
-    for (int64_t k0 = k_begin; k0 < k_end; k0 += 32) {
-        for (int q = tid; q < 64 * 32; q += 256) {
-            int r = q / 32, c = q % 32;
-            int64_t ia = i0 + r, jb = j0 + r;
-            sAh[c][r] = ia < n1 ? __bfloat162float(hi[ia * dp + k0 + c]) : 0.f;
-            sAl[c][r] = ia < n1 ? __bfloat162float(lo[ia * dp + k0 + c]) : 0.f;
-            sBh[c][r] = jb < n2 ? __bfloat162float(Bh[jb * dp + k0 + c]) : 0.f;
-            sBl[c][r] = jb < n2 ? __bfloat162float(Bl[jb * dp + k0 + c]) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int c = 0; c < 32; ++c) {
-            float ah[4], al[4], bh[4], bl[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                ah[a] = sAh[c][ti * 4 + a]; al[a] = sAl[c][ti * 4 + a];
-                bh[a] = sBh[c][tj * 4 + a]; bl[a] = sBl[c][tj * 4 + a];
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    acc[a][b] = fmaf(ah[a], bh[b], acc[a][b]);
-                    acc[a][b] = fmaf(ah[a], bl[b], acc[a][b]);
-                    acc[a][b] = fmaf(al[a], bh[b], acc[a][b]);
-                }
-        }
-        __syncthreads();
-    }
-    float *out = Ppart + (int64_t)blockIdx.z * n1 * n2;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            int64_t i = i0 + ti * 4 + a, j = j0 + tj * 4 + b;
-            if (i < n1 && j < n2) out[i * n2 + j] = acc[a][b];
-        }
-}
 
 // ---------------------------------------------------------------------------
 // 3a. approximate d2 and its rigorous error bound; running max lower bound
@@ -438,8 +386,10 @@ __global__ void bins_counts_kernel(CilWork w, const double *__restrict__ radii_o
 
 __global__ void finish_kernel(CilWork w, int64_t *n_rechecked, const int64_t *counts, int M, double *Cv) {
     if (blockIdx.x != 0) return;
-    // a set scal[5] (unforeseen ambiguous pair) reports -1 rechecks
-    if (threadIdx.x == 0 && n_rechecked) *n_rechecked = w.scal[5] ? -1 : (int64_t)w.scal[3];
+    // a set scal[5] (unforeseen ambiguous pair) reports -1 rechecks, a Gram
+    // timeout (scal[6]) -2
+    if (threadIdx.x == 0 && n_rechecked)
+        *n_rechecked = w.scal[6] ? -2 : (w.scal[5] ? -1 : (int64_t)w.scal[3]);
     if (Cv && (int)threadIdx.x < M)
         Cv[threadIdx.x] = __ddiv_rn((double)counts[threadIdx.x], (double)w.n1 * (double)w.n2);
 }
@@ -488,13 +438,15 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
         pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(X1, ld1, n1, X2, ld2, d, w.dp, w.centre, w.hi, w.lo, w.N,
                                                         w.H, w.L, w.E);
         note_launch();
-        dim3 gg((unsigned)((n2 + 63) / 64), (unsigned)((n1 + 63) / 64), (unsigned)w.nchunk);
-        gram_simt_kernel<<<gg, 256, 0, s>>>(w.hi, w.lo, n1, n2, w.dp, w.kc, w.Ppart);
-        note_launch();
-        // SIMT Gram: 3*kc fused multiply-adds per accumulator, each rounding
-        // to nearest (2^-24), plus margin; the chunk partials are summed by a
+        st = launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.kc, w.nchunk, w.Ppart,
+                            reinterpret_cast<uint32_t *>(&w.scal[6]), s);
+        if (st) return st;
+        // Tensor-core accumulation model: per chunk 3*kc/16 instructions add
+        // into the FP32 accumulator; each adds 16 exact bf16 products and
+        // the accumulator with at most 17 roundings of 2^-23 relative to the
+        // magnitudes involved.  The chunk partials are summed by a
         // compensated FP32 sum ((nchunk + 4) 2^-45 of the magnitudes).
-        const double gam = (3.0 * (double)w.kc + 64.0) * 5.9604644775390625e-8 +
+        const double gam = (3.0 * (double)w.kc / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
                            (double)(w.nchunk + 4) * 2.842170943040401e-14;
         d2_bound_kernel<<<gp, 256, 0, s>>>(w, gam);
         note_launch();
@@ -513,6 +465,37 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
     note_launch();
     finish_kernel<<<1, 32, 0, s>>>(w, n_rechecked, counts, M, Cv);
     note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+// Checking entry point: the approximate d2 (A) and its error bound (m) of
+// every pair from the pack + tensor-core Gram stages, before any exact
+// evaluation.  |A - canonical d2| <= m must hold for every pair.
+extern "C" rd_status cil_debug_approx(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
+                                      int64_t n2, int64_t d, double *d_A, double *d_m, void *d_work,
+                                      size_t work_bytes, void *stream) {
+    rd_status st = check_args(ld1, n1, ld2, n2, d, nullptr, 2.0, 1);
+    if (st) return st;
+    if (!d_X1 || !d_X2 || !d_A || !d_m || !d_work || (((uintptr_t)d_work) & 255)) return RD_ERR_INVALID_ARG;
+    CilWork w = layout(n1, n2, d, d_work);
+    if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t np = n1 * n2;
+    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 8 * sizeof(unsigned long long), s));
+    centre_kernel<<<(unsigned)((w.dp + 255) / 256), 256, 0, s>>>(d_X1, ld1, n1, d_X2, ld2, n2, d, w.dp, w.centre);
+    note_launch();
+    pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(d_X1, ld1, n1, d_X2, ld2, d, w.dp, w.centre, w.hi, w.lo, w.N,
+                                                    w.H, w.L, w.E);
+    note_launch();
+    st = launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.kc, w.nchunk, w.Ppart,
+                        reinterpret_cast<uint32_t *>(&w.scal[6]), s);
+    if (st) return st;
+    const double gam = (3.0 * (double)w.kc / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
+                       (double)(w.nchunk + 4) * 2.842170943040401e-14;
+    d2_bound_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(w, gam);
+    note_launch();
+    RD_CUDA_TRY(cudaMemcpyAsync(d_A, w.A, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    RD_CUDA_TRY(cudaMemcpyAsync(d_m, w.Mg, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return cuda_status(cudaGetLastError());
 }
 

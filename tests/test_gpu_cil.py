@@ -144,3 +144,20 @@ def test_bound_holds_against_exact_path(p):
     assert float(a["R0"]) == float(e["R0"])
     assert torch.equal(a["bins"], e["bins"])
     assert torch.equal(a["counts"], e["counts"])
+
+
+@pytest.mark.parametrize("n1,n2,d,off", [(64, 64, 4096, 0.0), (130, 70, 3000, 20.0), (256, 256, 32768, 2.0),
+                                         (5, 300, 128, 0.0)])
+def test_tensor_core_bound_holds_with_slack(p, n1, n2, d, off):
+    """The rigorous error bound of the tensor-core approximation holds for
+    every pair, with room to spare (the model is conservative): the
+    approximation error stays below a quarter of the bound."""
+    X1 = W.clustered_patterns(n1, d, 500 + n1) + off
+    X2 = W.clustered_patterns(n2, d, 600 + n2) + off
+    A, m = p.cil_approx(torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda())
+    ex = oracle.pair_d2(X1, X2)
+    A, m = A.cpu().numpy(), m.cpu().numpy()
+    err = np.abs(A - ex)
+    assert np.all(err <= 0.25 * m), (err / m).max()
+    # and the bound is tight enough to be useful: relative width < 1e-3
+    assert np.all(m <= 1e-3 * ex + 1e-9)
