@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-reference-path", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="fixed stepper tile variant (skips the autotuner; for profiling)")
+    ap.add_argument("--gram-large", action="store_true",
+                    help="also time the tensor-core Gram on 2 x 1024 patterns of d = 32768")
     return ap.parse_args()
 
 
@@ -136,8 +140,12 @@ def run_ours(args, rank, world, local_rank):
     mask = gd["species_mask"]
     d = G * G * (2 if mask == 3 else 1)
     sim = p.Simulation([grp], device=dev)
-    chosen = sim.autotune(steps=300)      # tile shape per (model, G); untimed set-up
-    variant = chosen[gd["model"] * 3 + {32: 0, 64: 1, 128: 2}[G]]
+    if args.variant >= 0:
+        assert p.lib().rd_set_variant(gd["model"], G, args.variant) == 0
+        variant = args.variant
+    else:
+        chosen = sim.autotune(steps=300)      # tile shape per (model, G); untimed set-up
+        variant = chosen[gd["model"] * 3 + {32: 0, 64: 1, 128: 2}[G]]
     fv = sim.group_fields(0).reshape(grp.n_real, 2 * G * G)
     X1, X2 = fv[:n1, :d], fv[n1:n1 + n2, :d]
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -293,7 +301,42 @@ def run_ours(args, rank, world, local_rank):
     cs = clk.summary()
     if cs:
         out["clocks"] = cs
+    if args.gram_large and rank == 0:
+        out["gram_large"] = gram_large(p, torch, dev, stream, pk, src)
     return out
+
+
+def gram_large(p, torch, dev, stream, pk, src):
+    """Tensor-core Gram at the paper's SCIL scale (N_syn = 1000): 2 sets x
+    1024 patterns of d = 32768 (GM 128x128 both species, synthetic cosine
+    fields), plus the whole correlation integral on them."""
+    n, G = 1024, 128
+    X = torch.from_numpy(W.cosine_patterns(2 * n, G, 2, 77, amp=0.8, offset=2.0)).to(dev)
+    X1, X2 = X[:n], X[n:]
+    d = X.shape[1]
+    c = p.cil(X1, X2, b=1.3, M=16)          # packs the workspace (and warms up)
+    torch.cuda.synchronize()
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fl = p.gram_only(n, n, d, dev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_gram = e0.elapsed_time(e1) / reps * 1e-3
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(reps):
+        c = p.cil(X1, X2, b=1.3, M=16)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    t_cil = c0.elapsed_time(c1) / reps * 1e-3
+    tf = fl / t_gram / 1e12
+    return {"pairs": n * n, "d": d, "gram_ms": t_gram * 1e3, "gram_tflops": tf,
+            "peak_bf16_tflops": pk["bf16_tflops"], "frac_of_peak": tf / pk["bf16_tflops"],
+            "peak_note": "bf16 dense burst peak (%s peaks file)" % src,
+            "cil_ms": t_cil * 1e3, "pair_dists_per_s": n * n / t_cil,
+            "rechecked": int(c["n_rechecked"])}
 
 
 # ---------------------------------------------------------------------------

@@ -245,6 +245,13 @@ rd_status cil_debug_approx(const float *d_X1, int64_t ld1, int64_t n1,
                            double *d_A, double *d_m, void *d_work, size_t work_bytes,
                            void *stream);
 
+/* cil_gram_only — benchmarking entry point: re-run only the tensor-core Gram
+ * stage on a workspace already packed by cil_features or cil_debug_approx
+ * with the same (n1, n2, d).  *flops (host, nullable) receives the FLOPs of
+ * the launch: 3 bf16 products x 2 x n1 x n2 x d_padded. */
+rd_status cil_gram_only(int64_t n1, int64_t n2, int64_t d, void *d_work, size_t work_bytes,
+                        double *flops, void *stream);
+
 /* cil_features_exact — the same outputs with every pair evaluated by the
  * exact sequential FP64 sum (no Gram product).  Slow; for checking. */
 rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1,

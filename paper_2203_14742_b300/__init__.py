@@ -51,6 +51,7 @@ _SIGS = {
                             _vp, _vp, _vp, _sz, _vp]),
     "cil_features_exact": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _dbl, _i32, _vp, _vp,
                                   _vp, _vp, _vp, _sz, _vp]),
+    "cil_gram_only": (_i32, [_i64, _i64, _i64, _vp, _sz, C.POINTER(_dbl), _vp]),
     "cil_debug_approx": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _sz, _vp]),
     "synlik_stats": (_i32, [_vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                             _vp, _vp, _vp]),
@@ -290,6 +291,15 @@ def cil_approx(X1, X2):
     _check("cil_debug_approx", lib().cil_debug_approx(_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, d, _ptr(A),
                                                       _ptr(m), _ptr(w), wb, _stream()))
     return A, m
+
+
+def gram_only(n1, n2, d, device=None):
+    """Re-run the tensor-core Gram stage on the cached workspace (benchmarking);
+    returns the FLOPs of the launch."""
+    w, wb = _workspace(n1, n2, d, torch.device(device or "cuda"))
+    fl = C.c_double()
+    _check("cil_gram_only", lib().cil_gram_only(n1, n2, d, _ptr(w), wb, C.byref(fl), _stream()))
+    return fl.value
 
 
 def cil(X1, X2, b=1.3, M=16, radii=None, work=None):

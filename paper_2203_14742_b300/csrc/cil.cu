@@ -499,6 +499,20 @@ extern "C" rd_status cil_debug_approx(const float *d_X1, int64_t ld1, int64_t n1
     return cuda_status(cudaGetLastError());
 }
 
+// Benchmarking entry point: re-run only the tensor-core Gram stage on a
+// workspace that a previous cil_features / cil_debug_approx call with the
+// same (n1, n2, d) has packed.  Returns the FLOP count of the launch in
+// *flops (3 bf16 products per element pair, 2 flops each).
+extern "C" rd_status cil_gram_only(int64_t n1, int64_t n2, int64_t d, void *d_work, size_t work_bytes,
+                                   double *flops, void *stream) {
+    if (n1 < 1 || n2 < 1 || d < 1 || !d_work || (((uintptr_t)d_work) & 255)) return RD_ERR_INVALID_ARG;
+    CilWork w = layout(n1, n2, d, d_work);
+    if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
+    if (flops) *flops = 3.0 * 2.0 * (double)n1 * (double)n2 * (double)w.dp;
+    return launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.kc, w.nchunk, w.Ppart,
+                          reinterpret_cast<uint32_t *>(&w.scal[6]), (cudaStream_t)stream);
+}
+
 extern "C" rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
                                   int64_t n2, int64_t d, const double *d_radii_in, double b, int32_t M,
                                   double *d_radii_out, uint8_t *d_bins, int64_t *d_counts, double *d_C,
