@@ -34,6 +34,23 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 FP32_INST_PER_CELL = {W.FHN: 16, W.GM: 17}   # minimal FP32 pipe instructions per cell-update
+
+# DRAM bytes (read + write) of one stepper launch on this workload, from the
+# ncu capture summarised in profiles/rd_resident_scalar_kernel_fhn64_c2.md,
+# keyed by a hash of the stepper sources: reported only while the kernel is
+# the one that was measured.
+STEPPER_TRAFFIC = {"71b8f7bde4d08c1c": 4249856}
+STEPPER_SOURCES = ["paper_2203_14742_b300/csrc/stepper.cu", "paper_2203_14742_b300/csrc/tile.cuh",
+                   "paper_2203_14742_b300/csrc/common.cuh"]
+
+
+def stepper_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in STEPPER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return STEPPER_TRAFFIC.get(h.hexdigest()[:16])
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -291,7 +308,8 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tinst/s",
-                     "frac": achieved / peak_alu, "traffic": None,
+                     "frac": achieved / peak_alu,
+                     "traffic": stepper_traffic() if variant == 0 and args.config == "c2" else None,
                      "kernel": "rd_resident_kernel<FHN,64,4,4>",
                      "note": "FP32 pipe instructions: %d per cell-update x cell-updates / kernel time; "
                              "peak = 148 SM x 128 FP32 lanes x max SM clock (%s peaks file)" % (inst, src)},

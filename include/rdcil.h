@@ -126,6 +126,16 @@ rd_status rd_reinit(rd_handle *h, float *d_fields, void *stream);
 rd_status rd_integrate_batch(rd_handle *h, float *d_fields, int64_t steps_override,
                              double *d_residual, void *stream);
 
+/* rd_set_schedule — how rd_integrate_batch launches the batch:
+ *   0 (default) automatic: one persistent launch when the handle holds more
+ *     than one group, otherwise one launch of the autotuned tile variant;
+ *   1 one launch per group (tile variant per (model, G));
+ *   2 one persistent launch for all groups: 256-thread CTAs, one per SM,
+ *     pulling (group, realisation) items longest first from a device queue,
+ *     so mixed models, grid sizes and step counts share the GPU.
+ * All schedules give bit-identical fields. */
+rd_status rd_set_schedule(rd_handle *h, int32_t mode);
+
 /* rd_integrate_reference — the plain path the batched stepper is measured
  * against: one realisation per launch, one Euler step per launch, state
  * round-tripping through global memory.  Same arithmetic contract as

@@ -57,6 +57,7 @@ _SIGS = {
                             _vp, _vp, _vp]),
     "rd_kernel_launches": (_u64, []),
     "rd_n_variants": (_i32, []),
+    "rd_set_schedule": (_i32, [_vp, _i32]),
     "rd_set_variant": (_i32, [_i32, _i32, _i32]),
     "rd_get_variant": (_i32, [_i32, _i32]),
     "rd_autotune": (_i32, [_vp, _vp, _i64, _vp, C.POINTER(_i32)]),
@@ -203,6 +204,10 @@ class Simulation:
         _check("rd_integrate_f64", lib().rd_integrate_f64(self.handle, _ptr(fields64), _ptr(tmp),
                                                           int(steps), _stream()))
         return fields64
+
+    def set_schedule(self, mode):
+        """0 automatic, 1 one launch per group, 2 one persistent launch."""
+        _check("rd_set_schedule", lib().rd_set_schedule(self.handle, int(mode)))
 
     def autotune(self, steps=200):
         """Pick the fastest tile shape per (model, G); re-initialises the fields."""

@@ -79,6 +79,8 @@ extern "C" rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_
     }
     st = adjoint_reserve(h);
     if (st) { rd_free(hh); return st; }
+    st = batch_plan_create(h.h_groups, n_groups, &h.batch);
+    if (st) { rd_free(hh); return st; }
     for (int32_t i = 0; i < n_groups; ++i) {
         st = launch_init_fields(h.h_groups[i], d_fields, s);
         if (st) { rd_free(hh); return st; }
@@ -99,10 +101,19 @@ extern "C" rd_status rd_reinit(rd_handle *hh, float *d_fields, void *stream) {
     return RD_OK;
 }
 
+extern "C" rd_status rd_set_schedule(rd_handle *hh, int32_t mode) {
+    if (!hh || mode < 0 || mode > 2) return RD_ERR_INVALID_ARG;
+    hh->h.schedule = mode;
+    return RD_OK;
+}
+
 extern "C" rd_status rd_integrate_batch(rd_handle *hh, float *d_fields, int64_t steps_override, double *d_residual,
                                         void *stream) {
     if (!hh || !d_fields || ((uintptr_t)d_fields & 15)) return RD_ERR_INVALID_ARG;
     Handle &h = hh->h;
+    const bool persistent = h.schedule == 2 || (h.schedule == 0 && h.n_groups > 1);
+    if (persistent)
+        return launch_batch(h.batch, d_fields, steps_override, d_residual, h.d_status, (cudaStream_t)stream);
     for (int32_t i = 0; i < h.n_groups; ++i) {
         const GroupDev &g = h.h_groups[i];
         int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
@@ -157,6 +168,7 @@ extern "C" void rd_free(rd_handle *hh) {
     if (!hh) return;
     Handle &h = hh->h;
     adjoint_release(h);
+    batch_plan_free(h.batch);
     if (h.d_groups) cudaFree(h.d_groups);
     if (h.d_status) cudaFree(h.d_status);
     delete[] h.h_groups;

@@ -46,8 +46,10 @@ struct Handle {
     size_t ckpt_floats;
     double *d_adj_scratch;
     size_t adj_scratch_doubles;
-    // cached launch plan
+    // adjoint scratch (adjoint.cu) and the persistent batch plan (stepper.cu)
     void *plan;
+    void *batch;
+    int32_t schedule;         // 0 auto, 1 one launch per group, 2 one persistent launch
 };
 
 inline rd_status cuda_status(cudaError_t e) {
@@ -75,6 +77,10 @@ rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int
                               cudaStream_t s);
 rd_status launch_integrate_variant(const GroupDev &g, float *fields, int64_t steps, double *residual,
                                    uint32_t *status, cudaStream_t s, int vi);
+rd_status batch_plan_create(const GroupDev *groups, int n_groups, void **out);
+void batch_plan_free(void *plan);
+rd_status launch_batch(void *plan, float *fields, int64_t steps_override, double *residual, uint32_t *status,
+                       cudaStream_t s);
 void set_variant_choice(int model, int G, int vi);
 int get_variant_choice(int model, int G);
 int n_variants();

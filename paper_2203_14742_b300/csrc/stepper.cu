@@ -17,7 +17,9 @@
 //   rd_reference_step_kernel one cell per thread, one step and one realisation
 //                            per launch (the plain path for comparison)
 //   rd_f64_step_kernel       FP64 in the paper's operation order, no FMA
+#include <algorithm>
 #include <cstdio>
+#include <vector>
 #include "tile.cuh"
 
 namespace rdcil {
@@ -222,18 +224,17 @@ rd_resident_kernel(float *__restrict__ fields, int64_t field_offset, int64_t ste
 // dependency latency (packed f32x2 instructions occupy the FMA pipe for two
 // cycles on this GPU).
 // ---------------------------------------------------------------------------
+// One realisation r of a group, by a whole CTA of Tiling<G,TY,TX>::NT
+// threads; sm = the halo ring (Tiling::SMEM bytes).
 template <int MODEL, int G, int TY, int TX>
-__global__ void __launch_bounds__(Tiling<G, TY, TX>::NT, 1)
-rd_resident_scalar_kernel(float *__restrict__ fields, int64_t field_offset, int64_t steps, CoefF cf,
-                          double p0, double p1, double p2, double p3, double *__restrict__ residual,
-                          uint32_t *__restrict__ status) {
+__device__ __forceinline__ void run_scalar(float *__restrict__ fields, int64_t field_offset, int r, int64_t steps,
+                                           const CoefF &cf, double p0, double p1, double p2, double p3,
+                                           double *__restrict__ residual, uint32_t *__restrict__ status,
+                                           float *sm) {
     using T = Tiling<G, TY, TX>;
     constexpr int NX = T::NX;
-    extern __shared__ float4 smem_f4[];
-    float *sm = reinterpret_cast<float *>(smem_f4);
     const int tid = threadIdx.x;
     const int tx = tid % NX, ty = tid / NX;
-    const int r = blockIdx.x;
     float *base = fields + field_offset + (int64_t)r * 2 * G * G;
     float u[TY][TX], v[TY][TX];
     tile_load<G, TY, TX>(base, tx, ty, u, v);
@@ -300,6 +301,16 @@ rd_resident_scalar_kernel(float *__restrict__ fields, int64_t field_offset, int6
             residual[2 * r + 1] = sqrt(s / (double)(2 * G * G));
         }
     }
+}
+
+template <int MODEL, int G, int TY, int TX>
+__global__ void __launch_bounds__(Tiling<G, TY, TX>::NT, 1)
+rd_resident_scalar_kernel(float *__restrict__ fields, int64_t field_offset, int64_t steps, CoefF cf,
+                          double p0, double p1, double p2, double p3, double *__restrict__ residual,
+                          uint32_t *__restrict__ status) {
+    extern __shared__ float4 smem_f4[];
+    run_scalar<MODEL, G, TY, TX>(fields, field_offset, (int)blockIdx.x, steps, cf, p0, p1, p2, p3, residual, status,
+                                 reinterpret_cast<float *>(smem_f4));
 }
 
 // ---------------------------------------------------------------------------
@@ -407,6 +418,145 @@ int n_variants() { return NVAR; }
 // traj holds, per realisation, `steps` states of 2*G*G floats back to back.
 rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int64_t steps, cudaStream_t s) {
     return dispatch_model<true>(g, fields, steps, nullptr, nullptr, traj, steps * 2 * (int64_t)g.G * g.G, s, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batched stepper: one launch for a whole mixed batch (several
+// parameter groups, models and grid sizes).  Every CTA has 256 threads and
+// loops: take the next (group, realisation) item from a global queue
+// (items ordered longest first), integrate it to the end, repeat.  The tile
+// shape per grid size keeps 256 threads for every item type (G = 32: 2x2,
+// 64: 4x4, 128: 8x8), and the per-node arithmetic is the same as in the
+// per-group kernels, so results are bit-identical to them.
+// ---------------------------------------------------------------------------
+struct BatchGroup {
+    CoefF cf;
+    double p[4];
+    int64_t field_offset, n_steps, real_base;
+    int32_t model, G, n_real, pad;
+};
+struct BatchItem {
+    int32_t group, real;
+};
+
+constexpr int BATCH_THREADS = 256;
+constexpr size_t BATCH_SMEM = Tiling<128, 8, 8>::SMEM;   // largest halo ring of the three shapes
+static_assert(Tiling<32, 2, 2>::NT == BATCH_THREADS && Tiling<64, 4, 4>::NT == BATCH_THREADS &&
+                  Tiling<128, 8, 8>::NT == BATCH_THREADS, "batch tile shapes must use 256 threads");
+static_assert(Tiling<32, 2, 2>::SMEM <= BATCH_SMEM && Tiling<64, 4, 4>::SMEM <= BATCH_SMEM, "halo ring");
+
+template <int MODEL>
+__device__ __forceinline__ void batch_item(float *fields, const BatchGroup &g, int r, int64_t steps, double *res,
+                                           uint32_t *status, float *sm) {
+    switch (g.G) {
+        case 32: run_scalar<MODEL, 32, 2, 2>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2], g.p[3],
+                                             res, status, sm); break;
+        case 64: run_scalar<MODEL, 64, 4, 4>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2], g.p[3],
+                                             res, status, sm); break;
+        default: run_scalar<MODEL, 128, 8, 8>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2],
+                                              g.p[3], res, status, sm); break;
+    }
+}
+
+__global__ void __launch_bounds__(BATCH_THREADS, 1)
+rd_batch_kernel(float *__restrict__ fields, const BatchGroup *__restrict__ groups, const BatchItem *__restrict__ items,
+                int n_items, unsigned int *__restrict__ head, int64_t steps_override, double *__restrict__ residual,
+                uint32_t *__restrict__ status) {
+    extern __shared__ float4 smem_f4[];
+    float *sm = reinterpret_cast<float *>(smem_f4);
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        const BatchGroup g = groups[w.group];
+        const int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
+        double *res = residual ? residual + 2 * g.real_base : nullptr;
+        switch (g.model) {
+            case RD_FHN: batch_item<RD_FHN>(fields, g, w.real, steps, res, status, sm); break;
+            case RD_GM: batch_item<RD_GM>(fields, g, w.real, steps, res, status, sm); break;
+            default: batch_item<RD_DIFF>(fields, g, w.real, steps, res, status, sm); break;
+        }
+        __syncthreads();
+    }
+}
+
+struct BatchPlan {
+    BatchGroup *d_groups = nullptr;
+    BatchItem *d_items = nullptr;
+    unsigned int *d_head = nullptr;
+    int n_items = 0;
+    int n_sm = 148;
+};
+
+rd_status batch_plan_create(const GroupDev *groups, int n_groups, void **out) {
+    *out = nullptr;
+    std::vector<BatchGroup> bg((size_t)n_groups);
+    std::vector<BatchItem> items;
+    std::vector<double> cost;
+    for (int i = 0; i < n_groups; ++i) {
+        const GroupDev &g = groups[i];
+        BatchGroup &b = bg[(size_t)i];
+        b.cf = make_coef(g);
+        for (int k = 0; k < 4; ++k) b.p[k] = g.p[k];
+        b.field_offset = g.field_offset;
+        b.n_steps = g.n_steps;
+        b.real_base = g.real_base;
+        b.model = g.model;
+        b.G = g.G;
+        b.n_real = g.n_real;
+        b.pad = 0;
+        for (int r = 0; r < g.n_real; ++r) items.push_back(BatchItem{i, r});
+    }
+    // longest first: cost ~ G^2 * steps
+    std::stable_sort(items.begin(), items.end(), [&](const BatchItem &a, const BatchItem &b) {
+        const GroupDev &ga = groups[a.group], &gb = groups[b.group];
+        return (double)ga.G * ga.G * (double)ga.n_steps > (double)gb.G * gb.G * (double)gb.n_steps;
+    });
+    BatchPlan *p = new BatchPlan();
+    p->n_items = (int)items.size();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    bool ok = cudaMalloc(&p->d_groups, sizeof(BatchGroup) * bg.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_items, sizeof(BatchItem) * items.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_head, sizeof(unsigned int)) == cudaSuccess &&
+              cudaMemcpy(p->d_groups, bg.data(), sizeof(BatchGroup) * bg.size(), cudaMemcpyHostToDevice) ==
+                  cudaSuccess &&
+              cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice) ==
+                  cudaSuccess;
+    *out = p;
+    return ok ? RD_OK : RD_ERR_OOM;
+}
+
+void batch_plan_free(void *pp) {
+    BatchPlan *p = (BatchPlan *)pp;
+    if (!p) return;
+    cudaFree(p->d_groups);
+    cudaFree(p->d_items);
+    cudaFree(p->d_head);
+    delete p;
+}
+
+rd_status launch_batch(void *pp, float *fields, int64_t steps_override, double *residual, uint32_t *status,
+                       cudaStream_t s) {
+    BatchPlan *p = (BatchPlan *)pp;
+    if (!p) return RD_ERR_INVALID_ARG;
+    static bool attr = false;
+    if (!attr) {
+        RD_CUDA_TRY(cudaFuncSetAttribute(rd_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)BATCH_SMEM));
+        attr = true;
+    }
+    RD_CUDA_TRY(cudaMemsetAsync(p->d_head, 0, sizeof(unsigned int), s));
+    int grid = p->n_sm < p->n_items ? p->n_sm : p->n_items;
+    rd_batch_kernel<<<grid, BATCH_THREADS, BATCH_SMEM, s>>>(fields, p->d_groups, p->d_items, p->n_items, p->d_head,
+                                                           steps_override, residual, status);
+    note_launch();
+    return cuda_status(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------

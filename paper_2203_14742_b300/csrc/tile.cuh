@@ -24,8 +24,10 @@ struct Tiling {
 
 template <int TX>
 __device__ __forceinline__ void st_row(float *dst, const float (&a)[TX]) {
-    if constexpr (TX == 4) {
-        *reinterpret_cast<float4 *>(dst) = make_float4(a[0], a[1], a[2], a[3]);
+    if constexpr (TX % 4 == 0) {
+#pragma unroll
+        for (int c = 0; c < TX; c += 4)
+            *reinterpret_cast<float4 *>(dst + c) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
     } else if constexpr (TX == 2) {
         *reinterpret_cast<float2 *>(dst) = make_float2(a[0], a[1]);
     } else {
@@ -36,9 +38,12 @@ __device__ __forceinline__ void st_row(float *dst, const float (&a)[TX]) {
 
 template <int TX>
 __device__ __forceinline__ void ld_row(const float *src, float (&a)[TX]) {
-    if constexpr (TX == 4) {
-        float4 t = *reinterpret_cast<const float4 *>(src);
-        a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+    if constexpr (TX % 4 == 0) {
+#pragma unroll
+        for (int c = 0; c < TX; c += 4) {
+            float4 t = *reinterpret_cast<const float4 *>(src + c);
+            a[c] = t.x; a[c + 1] = t.y; a[c + 2] = t.z; a[c + 3] = t.w;
+        }
     } else if constexpr (TX == 2) {
         float2 t = *reinterpret_cast<const float2 *>(src);
         a[0] = t.x; a[1] = t.y;

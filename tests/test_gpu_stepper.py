@@ -231,3 +231,55 @@ def test_c3_sample_gm128_full_horizon(p):
     err = rel_err(sim.group_fields(0).cpu().numpy(), ref)
     print("c3 GM 128 full-horizon field error", err)
     assert err <= FIELD_TOL
+
+
+def mixed_groups(p, steps_scale=1.0):
+    def st(n):
+        return max(1, int(n * steps_scale))
+    return [mkgroup(p, W.FHN, 64, 5, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -10, st(300), (-0.05, 0.05), 101),
+            mkgroup(p, W.GM, 128, 3, (2.5e-4, 0.01, 1.0, 0.52), 2 ** -10, st(200), (0.0, 0.01), 102),
+            mkgroup(p, W.FHN, 32, 7, (2.9e-4, 0.05, 9.5, 0.93), 2 ** -8, st(400), (-0.05, 0.05), 103),
+            mkgroup(p, W.GM, 64, 4, (2.5e-4, 0.01, 1.0, 0.47), 2 ** -8, st(250), (0.0, 0.01), 104),
+            mkgroup(p, W.FHN, 128, 2, (2.8e-4, 0.05, 10.0, 0.97), 2 ** -12, st(150), (-0.05, 0.05), 105),
+            mkgroup(p, W.DIFF, 64, 2, (3e-3, 1e-3), 2 ** -12, st(100), (-1.0, 1.0), 106)]
+
+
+def test_persistent_batch_bit_identical_to_per_group(p):
+    gs = mixed_groups(p)
+    a = p.Simulation(gs)
+    b = p.Simulation(gs)
+    a.set_schedule(1)          # one launch per group
+    b.set_schedule(2)          # one persistent launch
+    ra = a.integrate()
+    rb = b.integrate()
+    assert a.sync_status() == 0 and b.sync_status() == 0
+    assert torch.equal(a.fields, b.fields)
+    assert torch.equal(ra, rb)
+
+
+def test_persistent_batch_against_oracle(p):
+    gs = mixed_groups(p)
+    sim = p.Simulation(gs)     # more than one group: automatic schedule is persistent
+    f0 = [sim.group_fields(i).cpu().numpy().astype(np.float64) for i in range(len(gs))]
+    sim.integrate()
+    for i, g in enumerate(gs):
+        ref = oracle.step(g.model, g.params, g.dt, g.n_steps, f0[i])
+        assert rel_err(sim.group_fields(i).cpu().numpy(), ref) <= FIELD_TOL, i
+
+
+def test_c4_mixed_batch_slice(p):
+    """c4: 64 parameter vectors x 128 realisations, FHN and GM at 64^2 and
+    128^2 in one persistent launch (steps shortened to 2 %); one realisation
+    of every eighth group checked against the oracle."""
+    cfg = W.config("c4", steps_scale=0.02)
+    gs = [p.Group.from_dict(g) for g in cfg["groups"]]
+    sim = p.Simulation(gs)
+    picks = list(range(0, len(gs), 8))
+    f0 = {i: sim.group_fields(i)[:1].cpu().numpy().astype(np.float64) for i in picks}
+    res = sim.integrate()
+    assert sim.sync_status() == 0
+    assert torch.isfinite(res).all()
+    for i in picks:
+        g = gs[i]
+        ref = oracle.step(g.model, g.params, g.dt, g.n_steps, f0[i])
+        assert rel_err(sim.group_fields(i)[:1].cpu().numpy(), ref) <= FIELD_TOL, i
