@@ -33,7 +33,11 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
-FP32_INST_PER_CELL = {W.FHN: 16, W.GM: 17}   # minimal FP32 pipe instructions per cell-update
+# FP32-pipe instructions of the implemented update per cell-update: FHN 8
+# (two 5-point sums) + 8 (kinetics and update); GM 8 + 13 (deviation form;
+# the division's reciprocal runs on the MUFU pipe and is not counted);
+# DIFF 8 + 2.
+FP32_INST_PER_CELL = {W.FHN: 16, W.GM: 21, W.DIFF: 10}
 
 # DRAM bytes (read + write) of one stepper launch on this workload, from the
 # ncu capture summarised in profiles/rd_resident_scalar_kernel_fhn64_c2.md,
@@ -65,6 +69,8 @@ def parse():
     ap.add_argument("--no-reference-path", action="store_true")
     ap.add_argument("--variant", type=int, default=-1,
                     help="fixed stepper tile variant (skips the autotuner; for profiling)")
+    ap.add_argument("--graph", action="store_true",
+                    help="also time the pass captured in a CUDA graph and replayed")
     ap.add_argument("--gram-large", action="store_true",
                     help="also time the tensor-core Gram on 2 x 1024 patterns of d = 32768")
     return ap.parse_args()
@@ -149,55 +155,42 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     cfg = W.config(args.config)
-    gd = dict(cfg["groups"][0])
-    gd["seed"] = gd["seed"] + 7919 * rank          # weak scaling: one independent batch per rank
-    grp = p.Group.from_dict(gd)
+    gds = []
+    for gd in cfg["groups"]:
+        gd = dict(gd)
+        gd["seed"] = gd["seed"] + 7919 * rank      # weak scaling: one independent batch per rank
+        gds.append(gd)
+    groups = [p.Group.from_dict(gd) for gd in gds]
     n1, n2, M, b, T = cfg["n1"], cfg["n2"], cfg["M"], cfg["b"], cfg["T_res"]
-    G = grp.G
-    mask = gd["species_mask"]
-    d = G * G * (2 if mask == 3 else 1)
-    sim = p.Simulation([grp], device=dev)
+    sets = [(n1, n2, gd["species_mask"]) for gd in gds]
+    pipe = p.Pipeline(groups, sets, M, b, T, cfg["seed"] + rank, device=dev)
+    sim = pipe.sim
+    multi = len(groups) > 1
     if args.variant >= 0:
-        assert p.lib().rd_set_variant(gd["model"], G, args.variant) == 0
+        for g in groups:
+            assert p.lib().rd_set_variant(g.model, g.G, args.variant) == 0
         variant = args.variant
-    else:
+    elif not multi:
         chosen = sim.autotune(steps=300)      # tile shape per (model, G); untimed set-up
-        variant = chosen[gd["model"] * 3 + {32: 0, 64: 1, 128: 2}[G]]
-    fv = sim.group_fields(0).reshape(grp.n_real, 2 * G * G)
-    X1, X2 = fv[:n1, :d], fv[n1:n1 + n2, :d]
+        variant = chosen[groups[0].model * 3 + {32: 0, 64: 1, 128: 2}[groups[0].G]]
+    else:
+        variant = "persistent"
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    cell_updates = grp.n_real * G * G * grp.n_steps
+    cell_updates = sum(g.n_real * g.G * g.G * g.n_steps for g in groups)
+    inst = sum(g.n_real * g.G * g.G * g.n_steps * FP32_INST_PER_CELL[g.model] for g in groups)
+    pairs = n1 * n2 * len(groups)
 
-    def step(host=None):
-        if host is None:
-            sim.reinit()
-        else:
-            sim.fields.copy_(host["fields"], non_blocking=True)
-        res = sim.integrate()
-        c = p.cil(X1, X2, b=b, M=M)
-        s = p.synlik(c["bins"], M, T, cfg["seed"] + rank, y_obs=c["C"])
-        if host is not None:
-            for k in ("mu", "cov", "chol"):
-                host[k].copy_(s[k], non_blocking=True)
-            host["scal"].copy_(s["scalars"], non_blocking=True)
-            host["counts"].copy_(c["counts"], non_blocking=True)
-            host["residual"].copy_(res, non_blocking=True)
-        return res, c, s
-
-    # ---- warm-up and a correctness glance ------------------------------------
+    # ---- warm-up -------------------------------------------------------------
     for _ in range(args.warmup):
-        res, c, s = step()
+        pipe.run()
     torch.cuda.synchronize()
     assert sim.sync_status() == 0, "non-finite field during warm-up"
 
     # ---- device-timed whole steps (L2 flushed between steps) -----------------
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+    def evs():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    marks = [evs() for _ in range(args.steps)]
     launches0 = p.lib().rd_kernel_launches()
     if world > 1:
         torch.distributed.barrier()
@@ -205,21 +198,23 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         for i in range(args.steps):
             flush.fill_(float(i))
-            ev[i][0].record(stream)
+            e = marks[i]
+            e[0].record(stream)
             sim.reinit()
-            kev[i][0].record(stream)
-            res = sim.integrate()
-            kev[i][1].record(stream)
-            cev[i][0].record(stream)
-            c = p.cil(X1, X2, b=b, M=M)
-            cev[i][1].record(stream)
-            s = p.synlik(c["bins"], M, T, cfg["seed"] + rank, y_obs=c["C"])
-            ev[i][1].record(stream)
+            e[1].record(stream)
+            _check_int(p, sim, pipe)
+            e[2].record(stream)
+            for (X1, X2), out in zip(pipe.views, pipe.cil_out):
+                p.cil(X1, X2, b=b, M=M, work=pipe.work, out=out)
+            e[3].record(stream)
+            p.synlik(pipe.bins, M, T, pipe.seed, y_obs=pipe.C, out=pipe.stats)
+            e[4].record(stream)
         torch.cuda.synchronize()
     launches = p.lib().rd_kernel_launches() - launches0
-    step_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
-    k_ms = [a.elapsed_time(b_) for a, b_ in kev]
-    cil_ms = [a.elapsed_time(b_) for a, b_ in cev]
+    step_ms = sum(m[0].elapsed_time(m[4]) for m in marks)
+    k_ms = [m[1].elapsed_time(m[2]) for m in marks]
+    cil_ms = [m[2].elapsed_time(m[3]) for m in marks]
+    syn_ms = [m[3].elapsed_time(m[4]) for m in marks]
     if world > 1:
         t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -227,26 +222,47 @@ def run_ours(args, rank, world, local_rank):
     assert sim.sync_status() == 0
     ms_per_step = step_ms / args.steps
     value = cell_updates * world / (ms_per_step * 1e-3)
+    nre = int(sum(int(o["n_rechecked"]) for o in pipe.cil_out))
+
+    # ---- the same pass captured in a CUDA graph and replayed -----------------
+    graph_ms = None
+    if args.graph:
+        pipe.capture()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pipe.replay()
+        torch.cuda.synchronize()
+        g0.record(stream)
+        for _ in range(args.steps):
+            pipe.replay()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = g0.elapsed_time(g1) / args.steps
+        pipe.graph = None
 
     # ---- end to end through the public API with host buffers -----------------
     host = {"fields": torch.empty(sim.fields.shape, dtype=torch.float32, pin_memory=True)}
     sim.reinit()
     host["fields"].copy_(sim.fields)
-    for k, shape, dt in (("mu", (M,), torch.float64), ("cov", (M, M), torch.float64),
-                         ("chol", (M, M), torch.float64), ("scal", (4,), torch.float64),
-                         ("counts", (M,), torch.int64), ("residual", (grp.n_real, 2), torch.float64)):
-        host[k] = torch.empty(shape, dtype=dt, pin_memory=True)
-    step(host)
+    outs = {"mu": pipe.stats["mu"], "cov": pipe.stats["cov"], "chol": pipe.stats["chol"],
+            "scalars": pipe.stats["scalars"], "status": pipe.stats["status"], "C": pipe.C,
+            "residual": pipe.residual}
+    for k, t in outs.items():
+        host[k] = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+
+    def e2e_step():
+        sim.fields.copy_(host["fields"], non_blocking=True)
+        pipe.run(reinit=False)
+        for k, t in outs.items():
+            host[k].copy_(t, non_blocking=True)
+
+    e2e_step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
-    e0.record(stream)
     for _ in range(e2e_steps):
-        step(host)
-    e1.record(stream)
+        e2e_step()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     if world > 1:
@@ -254,12 +270,12 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t)
     h2d = host["fields"].numel() * 4
-    d2h = sum(host[k].numel() * host[k].element_size() for k in host if k != "fields")
+    d2h = sum(host[k].numel() * host[k].element_size() for k in outs)
 
     # ---- plain single-realisation FP32 path on a slice (same GPU) ------------
     ref_rate = None
     if not args.no_reference_path and rank == 0:
-        gsl = dict(gd)
+        gsl = dict(gds[0])
         gsl["n_real"] = 2
         ssl = p.Simulation([p.Group.from_dict(gsl)], device=dev)
         nsl = 500
@@ -270,17 +286,25 @@ def run_ours(args, rank, world, local_rank):
         ssl.integrate_reference(steps=nsl)
         r1.record(stream)
         torch.cuda.synchronize()
-        ref_rate = 2 * G * G * nsl / (r0.elapsed_time(r1) * 1e-3)
+        ref_rate = 2 * gsl["G"] ** 2 * nsl / (r0.elapsed_time(r1) * 1e-3)
 
-    # ---- roofline of the dominant kernel (the resident stepper) -------------
+    # ---- roofline of the dominant kernel (the stepper) ----------------------
     pk, src = peaks()
     k_avg_ms = sum(k_ms) / len(k_ms)
-    inst = FP32_INST_PER_CELL[gd["model"]]
-    achieved = cell_updates * inst / (k_avg_ms * 1e-3) / 1e12          # Tinst/s
+    achieved = inst / (k_avg_ms * 1e-3) / 1e12                          # T FP32 instructions / s
     peak_alu = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12   # FP32 lanes x clock
     cil_avg = sum(cil_ms) / len(cil_ms)
-    pair_rate = n1 * n2 / (cil_avg * 1e-3)
-
+    kname = "rd_batch_kernel (persistent)" if multi else (
+        "rd_resident_%s_kernel<%s,%d> variant %s" % ("scalar" if variant in (0, 2) else "packed",
+                                                      {0: "FHN", 1: "GM", 2: "DIFF"}[groups[0].model],
+                                                      groups[0].G, variant))
+    workload = {"c2": "c2: FHN 64x64, 2 sets x 64 realisations, 10^4 Euler steps, u-only d=4096, M=16, "
+                      "b=1.3, 200 resamples",
+                "c4": "c4: 64 parameter vectors x 128 realisations, FHN+GM at 64^2 (10^4 steps) and 128^2 "
+                      "(2x10^4 steps) in one persistent launch, 2 x 64 sets per vector, M=16, 200 resamples",
+                "c1": "c1: FHN 32x32, 2 x 16, 2000 steps, d=2048, M=8, 50 resamples",
+                "c3": "c3: GM 128x128, 2 x 256, 2x10^4 steps, d=32768, M=16, 200 resamples",
+                "c5": "c5: FHN 64x64, 32 realisations, 5000 steps"}[args.config]
     out = {
         "metric": "RD cell-updates/s + CIL pair-dists/s at stated tol; % HBM/tensor roofline",
         "value": value,
@@ -294,25 +318,27 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32 stepper, bf16x3 Gram + f64 recheck, f64 statistics",
         "data": "synthetic (seeded counter-based initial noise; the paper's data are simulated too)",
-        "config": {"workload": "c2: FHN 64x64, 2 sets x 64 realisations, 10^4 Euler steps, "
-                               "u-only d=4096, M=16, b=1.3, 200 resamples",
-                   "realisations_per_gpu": grp.n_real, "grid": G, "euler_steps": grp.n_steps,
-                   "pairs": n1 * n2, "pattern_dim": d, "radii": M, "resamples": T,
+        "config": {"workload": workload, "groups": len(groups),
+                   "realisations_per_gpu": sum(g.n_real for g in groups),
+                   "grids": sorted(set(g.G for g in groups)), "pairs": pairs, "radii": M, "resamples": T,
                    "l2": "flushed between timed steps (256 MB write)"},
-        "pair_dists_per_s": pair_rate,
-        "cil_pairs_rechecked_exactly": int(c["n_rechecked"]),
+        "pair_dists_per_s": pairs / (cil_avg * 1e-3),
+        "cil_pairs_rechecked_exactly": nre,
         "stepper_variant": variant,
-        "cil_ms": cil_avg,
         "stepper_ms": k_avg_ms,
+        "cil_ms": cil_avg,
+        "synlik_ms": sum(syn_ms) / len(syn_ms),
+        "graph_replay_ms_per_step": graph_ms,
         "e2e": {"value": cell_updates * world / (e2e_ms * 1e-3), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tinst/s",
                      "frac": achieved / peak_alu,
                      "traffic": stepper_traffic() if variant == 0 and args.config == "c2" else None,
-                     "kernel": "rd_resident_kernel<FHN,64,4,4>",
-                     "note": "FP32 pipe instructions: %d per cell-update x cell-updates / kernel time; "
-                             "peak = 148 SM x 128 FP32 lanes x max SM clock (%s peaks file)" % (inst, src)},
+                     "kernel": kname,
+                     "note": "FP32 pipe instructions of the update (FHN 16, GM 21 per cell-update) x "
+                             "cell-updates / stepper time; peak = 148 SM x 128 FP32 lanes x max SM clock "
+                             "(%s peaks file)" % src},
         "plain_fp32_path_cell_updates_per_s": ref_rate,
         "batched_vs_plain": (cell_updates / (k_avg_ms * 1e-3)) / ref_rate if ref_rate else None,
     }
@@ -322,6 +348,16 @@ def run_ours(args, rank, world, local_rank):
     if args.gram_large and rank == 0:
         out["gram_large"] = gram_large(p, torch, dev, stream, pk, src)
     return out
+
+
+def _check_int(p, sim, pipe):
+    """rd_integrate_batch with the pipeline's residual buffer."""
+    import ctypes
+    st = p.lib().rd_integrate_batch(sim.handle, ctypes.c_void_p(sim.fields.data_ptr()), -1,
+                                    ctypes.c_void_p(pipe.residual.data_ptr()),
+                                    ctypes.c_void_p(__import__("torch").cuda.current_stream().cuda_stream))
+    if st != 0:
+        raise RuntimeError("rd_integrate_batch failed: %d" % st)
 
 
 def gram_large(p, torch, dev, stream, pk, src):

@@ -133,7 +133,8 @@ rd_status rd_integrate_batch(rd_handle *h, float *d_fields, int64_t steps_overri
  *   2 one persistent launch for all groups: 256-thread CTAs, one per SM,
  *     pulling (group, realisation) items longest first from a device queue,
  *     so mixed models, grid sizes and step counts share the GPU.
- * All schedules give bit-identical fields. */
+ * All schedules give bit-identical fields; the residual's RMS is summed in
+ * an order that follows the tiling and agrees to FP64 rounding. */
 rd_status rd_set_schedule(rd_handle *h, int32_t mode);
 
 /* rd_integrate_reference — the plain path the batched stepper is measured

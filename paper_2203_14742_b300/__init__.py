@@ -258,7 +258,7 @@ def _as_rows(X):
     return X, X.stride(0), X.shape[0], X.shape[1]
 
 
-def _cil_call(fn, X1, X2, b, M, radii, work=None):
+def _cil_call(fn, X1, X2, b, M, radii, work=None, out=None):
     X1, ld1, n1, d = _as_rows(X1)
     X2, ld2, n2, d2 = _as_rows(X2)
     if d != d2:
@@ -267,11 +267,14 @@ def _cil_call(fn, X1, X2, b, M, radii, work=None):
     if radii is not None:
         radii = radii.to(device=dev, dtype=torch.float64).contiguous()
         M = radii.numel()
-    radii_out = torch.empty(M + 1, dtype=torch.float64, device=dev)
-    bins = torch.empty((n1, n2), dtype=torch.uint8, device=dev)
-    counts = torch.empty(M, dtype=torch.int64, device=dev)
-    Cvec = torch.empty(M, dtype=torch.float64, device=dev)
-    nre = torch.zeros(1, dtype=torch.int64, device=dev)
+    if out is not None:
+        radii_out, bins, counts, Cvec, nre = out["radii"], out["bins"], out["counts"], out["C"], out["n_rechecked"]
+    else:
+        radii_out = torch.empty(M + 1, dtype=torch.float64, device=dev)
+        bins = torch.empty((n1, n2), dtype=torch.uint8, device=dev)
+        counts = torch.empty(M, dtype=torch.int64, device=dev)
+        Cvec = torch.empty(M, dtype=torch.float64, device=dev)
+        nre = torch.zeros(1, dtype=torch.int64, device=dev)
     if work is None:
         w, wb = _workspace(n1, n2, d, dev)
     else:
@@ -307,9 +310,11 @@ def gram_only(n1, n2, d, device=None):
     return fl.value
 
 
-def cil(X1, X2, b=1.3, M=16, radii=None, work=None):
-    """Correlation integral of two pattern sets (rows of X1, X2)."""
-    return _cil_call("cil_features", X1, X2, b, M, radii, work)
+def cil(X1, X2, b=1.3, M=16, radii=None, work=None, out=None):
+    """Correlation integral of two pattern sets (rows of X1, X2).  `out`
+    (optional) supplies the output tensors: radii [M+1], bins [n1, n2] uint8,
+    counts [M] int64, C [M] float64, n_rechecked [1] int64."""
+    return _cil_call("cil_features", X1, X2, b, M, radii, work, out)
 
 
 def cil_exact(X1, X2, b=1.3, M=16, radii=None, work=None):
@@ -320,24 +325,36 @@ def cil_exact(X1, X2, b=1.3, M=16, radii=None, work=None):
 # ---------------------------------------------------------------------------
 # synthetic likelihood
 # ---------------------------------------------------------------------------
-def synlik(bins, M, T, seed, y_obs=None):
+def synlik_outputs(P, M, T, device):
+    dev = torch.device(device)
+    return {"Y": torch.empty((P, T, M), dtype=torch.int64, device=dev),
+            "mu": torch.empty((P, M), dtype=torch.float64, device=dev),
+            "cov": torch.empty((P, M, M), dtype=torch.float64, device=dev),
+            "chol": torch.empty((P, M, M), dtype=torch.float64, device=dev),
+            "scalars": torch.empty((P, 4), dtype=torch.float64, device=dev),
+            "active": torch.empty((P, M), dtype=torch.uint8, device=dev),
+            "status": torch.empty(P, dtype=torch.int32, device=dev)}
+
+
+def synlik(bins, M, T, seed, y_obs=None, out=None):
     """Bootstrap statistics of bins [P, n1, n2] (or [n1, n2]) uint8."""
     squeeze = bins.dim() == 2
     if squeeze:
         bins = bins.unsqueeze(0)
-    bins = bins.contiguous()
+    if not bins.is_contiguous():
+        raise ValueError("bins must be contiguous")
     P, n1, n2 = bins.shape
     dev = bins.device
-    Y = torch.empty((P, T, M), dtype=torch.int64, device=dev)
-    mu = torch.empty((P, M), dtype=torch.float64, device=dev)
-    cov = torch.empty((P, M, M), dtype=torch.float64, device=dev)
-    chol = torch.empty((P, M, M), dtype=torch.float64, device=dev)
-    sc = torch.empty((P, 4), dtype=torch.float64, device=dev)
-    act = torch.empty((P, M), dtype=torch.uint8, device=dev)
-    st = torch.empty(P, dtype=torch.int32, device=dev)
+    o = out if out is not None else synlik_outputs(P, M, T, dev)
+    Y, mu, cov, chol, sc, act, st = (o["Y"], o["mu"], o["cov"], o["chol"], o["scalars"], o["active"],
+                                     o["status"])
     yo = None
     if y_obs is not None:
-        yo = y_obs.to(device=dev, dtype=torch.float64).reshape(P, M).contiguous()
+        yo = y_obs
+        if yo.dtype != torch.float64 or yo.device != dev or not yo.is_contiguous():
+            yo = yo.to(device=dev, dtype=torch.float64).contiguous()   # marshalling only
+        if yo.numel() != P * M:
+            raise ValueError("y_obs must hold P x M values")
     _check("synlik_stats", lib().synlik_stats(_ptr(bins), n1, n2, int(M), int(T),
                                               int(seed) & 0xFFFFFFFFFFFFFFFF, P, _ptr(yo), _ptr(Y),
                                               _ptr(mu), _ptr(cov), _ptr(chol), _ptr(sc), _ptr(act),
@@ -347,6 +364,73 @@ def synlik(bins, M, T, seed, y_obs=None):
     if squeeze:
         out = {k: v[0] for k, v in out.items()}
     return out
+
+
+# ---------------------------------------------------------------------------
+# one pass of the whole hot path
+# ---------------------------------------------------------------------------
+class Pipeline:
+    """initial state -> integration (+ residual) -> per-group correlation
+    integral of two pattern sets -> bootstrap statistics of every group, with
+    every output buffer allocated once, so that a pass can be captured in a
+    CUDA graph and replayed.  sets[i] = (n1, n2, species_mask) of group i:
+    set 1 = realisations 0..n1-1, set 2 = n1..n1+n2-1.  The cost is
+    evaluated at each group's own correlation vector (y_obs = C)."""
+
+    def __init__(self, groups, sets, M, b, T, seed, device=None):
+        self.sim = Simulation(groups, device=device)
+        self.dev = self.sim.device
+        self.M, self.b, self.T, self.seed = M, b, T, seed
+        self.views = []
+        n1s = set(s[0] for s in sets)
+        n2s = set(s[1] for s in sets)
+        if len(n1s) != 1 or len(n2s) != 1:
+            raise ValueError("all groups need the same set sizes (batched statistics)")
+        self.n1, self.n2 = n1s.pop(), n2s.pop()
+        P = len(groups)
+        for i, (g, (n1, n2, mask)) in enumerate(zip(groups, sets)):
+            G = g.G
+            fv = self.sim.group_fields(i).reshape(g.n_real, 2 * G * G)
+            off = 0 if mask in (1, 3) else G * G
+            d = G * G * (2 if mask == 3 else 1)
+            self.views.append((fv[:n1, off:off + d], fv[n1:n1 + n2, off:off + d]))
+        self.bins = torch.empty((P, self.n1, self.n2), dtype=torch.uint8, device=self.dev)
+        self.C = torch.empty((P, M), dtype=torch.float64, device=self.dev)
+        self.cil_out = [{"radii": torch.empty(M + 1, dtype=torch.float64, device=self.dev),
+                         "bins": self.bins[i], "counts": torch.empty(M, dtype=torch.int64, device=self.dev),
+                         "C": self.C[i], "n_rechecked": torch.zeros(1, dtype=torch.int64, device=self.dev)}
+                        for i in range(P)]
+        self.stats = synlik_outputs(P, M, T, self.dev)
+        self.residual = torch.empty((self.sim.n_real_total, 2), dtype=torch.float64, device=self.dev)
+        dmax = max(x.shape[1] for x, _ in self.views)
+        self.work, self.work_bytes = _workspace(self.n1, self.n2, dmax, self.dev)
+        self.graph = None
+
+    def run(self, reinit=True):
+        if reinit:
+            self.sim.reinit()
+        _check("rd_integrate_batch", lib().rd_integrate_batch(
+            self.sim.handle, _ptr(self.sim.fields), -1, _ptr(self.residual), _stream()))
+        for (X1, X2), out in zip(self.views, self.cil_out):
+            _cil_call("cil_features", X1, X2, self.b, self.M, None, self.work, out)
+        synlik(self.bins, self.M, self.T, self.seed, y_obs=self.C, out=self.stats)
+
+    def capture(self):
+        """Record one pass (from the initial state) as a CUDA graph."""
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream(device=self.dev)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run()            # warm every lazy set-up outside the capture
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
 
 
 # ---------------------------------------------------------------------------
