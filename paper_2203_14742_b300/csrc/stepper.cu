@@ -93,6 +93,57 @@ __device__ __forceinline__ void rhs_f64(double u, double v, double nu, double su
     Fv = p[1] * lv + rv;
 }
 
+// FP64 steady-state residual of the final state of realisation r, read
+// back from global memory after the block stored it (block-visible after
+// the barrier): max |F| and sqrt(mean F^2) over both species, F from the
+// stored FP32 values in the plain operation order.  Thread t takes nodes
+// t, t + NT, ...; the sum is reduced with warp shuffles, then across warps.
+template <int MODEL, int G>
+__device__ __forceinline__ void residual_from_global(const float *__restrict__ base, double p0, double p1, double p2,
+                                                     double p3, double *__restrict__ residual,
+                                                     uint32_t *__restrict__ status, int r, void *smem) {
+    __syncthreads();
+    const double p[4] = {p0, p1, p2, p3};
+    const double h2 = (double)(G - 1) * (double)(G - 1);
+    const float *u = base, *v = base + G * G;
+    double mx = 0.0, ss = 0.0;
+    bool bad = false;
+    for (int k = threadIdx.x; k < G * G; k += blockDim.x) {
+        const int y = k / G, x = k - y * G;
+        const int kn = (y > 0 ? k - G : k), ks = (y < G - 1 ? k + G : k);
+        const int kw = (x > 0 ? k - 1 : k), ke = (x < G - 1 ? k + 1 : k);
+        double Fu, Fv;
+        rhs_f64<MODEL>(u[k], v[k], u[kn], u[ks], u[kw], u[ke], v[kn], v[ks], v[kw], v[ke], p, h2, Fu, Fv);
+        bad |= !isfinite(u[k]) || !isfinite(v[k]) || !isfinite(Fu) || !isfinite(Fv);
+        mx = fmax(mx, fmax(fabs(Fu), fabs(Fv)));
+        ss += Fu * Fu + Fv * Fv;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    }
+    const int anybad = __syncthreads_or(bad ? 1 : 0);
+    double *red = reinterpret_cast<double *>(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) { red[warp] = mx; red[nw + warp] = ss; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0, s = 0.0;
+        for (int wi = 0; wi < nw; ++wi) { m = fmax(m, red[wi]); s += red[nw + wi]; }
+        if (anybad) {
+            atomicOr(status, (unsigned)ST_NONFINITE);
+            m = __longlong_as_double(0x7ff8000000000000ll);
+            s = m;
+        }
+        if (residual) {
+            residual[2 * r] = m;
+            residual[2 * r + 1] = sqrt(s / (double)(2 * G * G));
+        }
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Resident stepper: one realisation per CTA, the field held in registers as
 // packed (u, v) tiles for the whole run.  RECORD = true stores the state
@@ -124,12 +175,15 @@ rd_resident_kernel(float *__restrict__ fields, int64_t field_offset, int64_t ste
 
     for (int64_t n = 0; n < steps; ++n) {
         if (RECORD) {
-            float2 f[TY][TX];
+            // state before this step, as stored fields, one tile row at a time
+            float *dst = traj + (int64_t)r * traj_stride + n * 2 * G * G;
 #pragma unroll
-            for (int i = 0; i < TY; ++i)
+            for (int i = 0; i < TY; ++i) {
+                float2 f[TX];
 #pragma unroll
-                for (int c = 0; c < TX; ++c) f[i][c] = from_state2<MODEL>(w[i][c], cf);
-            tile2_store<G, TY, TX>(traj + (int64_t)r * traj_stride + n * 2 * G * G, tx, ty, f);
+                for (int c = 0; c < TX; ++c) f[c] = from_state2<MODEL>(w[i][c], cf);
+                st_row_g<G, TX>(dst, ty * TY + i, tx * TX, f);
+            }
         }
         float2 *hb = sm + (int)(n & 1) * (T::HALO_F2 / 2);
         halo2_put<G, TY, TX>(hb, tx, ty, w);
@@ -144,77 +198,7 @@ rd_resident_kernel(float *__restrict__ fields, int64_t field_offset, int64_t ste
     if (RECORD) return;
 
     // ---- FP64 steady-state residual of the final (stored FP32) state -----
-    float2 *hb = sm + (int)(steps & 1) * (T::HALO_F2 / 2);
-    halo2_put<G, TY, TX>(hb, tx, ty, w);
-    __syncthreads();
-    const double p[4] = {p0, p1, p2, p3};
-    const double h2 = (double)(G - 1) * (double)(G - 1);
-    double mx = 0.0, ss = 0.0;
-    bool bad = false;
-    float2 pw[TX];
-    if (ty > 0) {
-        ld_row2<TX>(hb + (1 * NY + ty - 1) * G + tx * TX, pw);
-    } else {
-#pragma unroll
-        for (int c = 0; c < TX; ++c) pw[c] = w[0][c];
-    }
-#pragma unroll
-    for (int i = 0; i < TY; ++i) {
-        float2 sw[TX];
-        if (i + 1 < TY) {
-#pragma unroll
-            for (int c = 0; c < TX; ++c) sw[c] = w[i + 1][c];
-        } else if (ty < NY - 1) {
-            ld_row2<TX>(hb + (0 * NY + ty + 1) * G + tx * TX, sw);
-        } else {
-#pragma unroll
-            for (int c = 0; c < TX; ++c) sw[c] = w[TY - 1][c];
-        }
-        float2 west, east;
-        west.x = __shfl_up_sync(0xffffffffu, w[i][TX - 1].x, 1, NX);
-        west.y = __shfl_up_sync(0xffffffffu, w[i][TX - 1].y, 1, NX);
-        east.x = __shfl_down_sync(0xffffffffu, w[i][0].x, 1, NX);
-        east.y = __shfl_down_sync(0xffffffffu, w[i][0].y, 1, NX);
-        if (tx == 0) west = w[i][0];
-        if (tx == NX - 1) east = w[i][TX - 1];
-#pragma unroll
-        for (int c = 0; c < TX; ++c) {
-            float2 Wn = c > 0 ? w[i][c - 1] : west, En = c < TX - 1 ? w[i][c + 1] : east;
-            double Fu, Fv;
-            rhs_f64<MODEL>(w[i][c].x, w[i][c].y, pw[c].x, sw[c].x, Wn.x, En.x, pw[c].y, sw[c].y, Wn.y, En.y,
-                           p, h2, Fu, Fv);
-            bad |= !isfinite(w[i][c].x) || !isfinite(w[i][c].y) || !isfinite(Fu) || !isfinite(Fv);
-            mx = fmax(mx, fmax(fabs(Fu), fabs(Fv)));
-            ss += Fu * Fu + Fv * Fv;
-        }
-#pragma unroll
-        for (int c = 0; c < TX; ++c) pw[c] = w[i][c];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    }
-    int anybad = __syncthreads_or(bad ? 1 : 0);
-    // the other halo buffer is free: reuse it for the cross-warp reduction
-    double *red = reinterpret_cast<double *>(sm + (int)((steps + 1) & 1) * (T::HALO_F2 / 2));
-    const int warp = tid >> 5, lane = tid & 31;
-    constexpr int NW = T::NT / 32;
-    if (lane == 0) { red[warp] = mx; red[NW + warp] = ss; }
-    __syncthreads();
-    if (tid == 0) {
-        double m = 0.0, s = 0.0;
-        for (int wi = 0; wi < NW; ++wi) { m = fmax(m, red[wi]); s += red[NW + wi]; }
-        if (anybad) {
-            atomicOr(status, (unsigned)ST_NONFINITE);
-            m = __longlong_as_double(0x7ff8000000000000ll);
-            s = m;
-        }
-        if (residual) {
-            residual[2 * r] = m;
-            residual[2 * r + 1] = sqrt(s / (double)(2 * G * G));
-        }
-    }
+    residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -247,60 +231,7 @@ __device__ __forceinline__ void run_scalar(float *__restrict__ fields, int64_t f
     }
     tile_from_state<MODEL, TY, TX>(u, v, cf);
     tile_store<G, TY, TX>(base, tx, ty, u, v);
-
-    float *hb = sm + (int)(steps & 1) * (T::HALO_FLOATS / 2);
-    halo_put<G, TY, TX>(hb, tx, ty, u, v);
-    __syncthreads();
-    const double p[4] = {p0, p1, p2, p3};
-    const double h2 = (double)(G - 1) * (double)(G - 1);
-    double mx = 0.0, ss = 0.0;
-    bool bad = false;
-    float pu[TX], pv[TX];
-    halo_north<G, TY, TX>(hb, tx, ty, u, v, pu, pv);
-#pragma unroll
-    for (int i = 0; i < TY; ++i) {
-        float su[TX], sv[TX];
-        row_south<G, TY, TX>(hb, tx, ty, i, u, v, su, sv);
-        float wu, eu, wv, ev;
-        row_west_east<NX>(tx, u[i][0], u[i][TX - 1], wu, eu);
-        row_west_east<NX>(tx, v[i][0], v[i][TX - 1], wv, ev);
-#pragma unroll
-        for (int c = 0; c < TX; ++c) {
-            float Wu = c > 0 ? u[i][c - 1] : wu, Eu = c < TX - 1 ? u[i][c + 1] : eu;
-            float Wv = c > 0 ? v[i][c - 1] : wv, Ev = c < TX - 1 ? v[i][c + 1] : ev;
-            double Fu, Fv;
-            rhs_f64<MODEL>(u[i][c], v[i][c], pu[c], su[c], Wu, Eu, pv[c], sv[c], Wv, Ev, p, h2, Fu, Fv);
-            bad |= !isfinite(u[i][c]) || !isfinite(v[i][c]) || !isfinite(Fu) || !isfinite(Fv);
-            mx = fmax(mx, fmax(fabs(Fu), fabs(Fv)));
-            ss += Fu * Fu + Fv * Fv;
-        }
-#pragma unroll
-        for (int c = 0; c < TX; ++c) { pu[c] = u[i][c]; pv[c] = v[i][c]; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    }
-    int anybad = __syncthreads_or(bad ? 1 : 0);
-    double *red = reinterpret_cast<double *>(sm + (int)((steps + 1) & 1) * (T::HALO_FLOATS / 2));
-    const int warp = tid >> 5, lane = tid & 31;
-    constexpr int NW = T::NT / 32;
-    if (lane == 0) { red[warp] = mx; red[NW + warp] = ss; }
-    __syncthreads();
-    if (tid == 0) {
-        double m = 0.0, s = 0.0;
-        for (int wi = 0; wi < NW; ++wi) { m = fmax(m, red[wi]); s += red[NW + wi]; }
-        if (anybad) {
-            atomicOr(status, (unsigned)ST_NONFINITE);
-            m = __longlong_as_double(0x7ff8000000000000ll);
-            s = m;
-        }
-        if (residual) {
-            residual[2 * r] = m;
-            residual[2 * r + 1] = sqrt(s / (double)(2 * G * G));
-        }
-    }
+    residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, sm);
 }
 
 template <int MODEL, int G, int TY, int TX>
@@ -322,10 +253,13 @@ rd_resident_scalar_kernel(float *__restrict__ fields, int64_t field_offset, int6
 struct Variant {
     int packed, TY, TX;
 };
-static constexpr int NVAR = 5;
-static constexpr Variant VAR32[NVAR] = {{0, 4, 4}, {1, 4, 4}, {0, 2, 4}, {1, 2, 4}, {1, 2, 8}};
-static constexpr Variant VAR64[NVAR] = {{0, 4, 4}, {1, 4, 4}, {0, 2, 4}, {1, 2, 4}, {1, 4, 8}};
-static constexpr Variant VAR128[NVAR] = {{0, 8, 4}, {1, 8, 4}, {0, 4, 4}, {1, 4, 8}, {1, 16, 4}};
+static constexpr int NVAR = 8;
+static constexpr Variant VAR32[NVAR] = {{0, 4, 4}, {1, 4, 4}, {0, 2, 4}, {1, 2, 4},
+                                        {1, 2, 8}, {0, 2, 8}, {0, 4, 8}, {0, 2, 2}};
+static constexpr Variant VAR64[NVAR] = {{0, 4, 4}, {1, 4, 4}, {0, 2, 4}, {1, 2, 4},
+                                        {0, 4, 8}, {0, 8, 4}, {0, 2, 8}, {0, 8, 8}};
+static constexpr Variant VAR128[NVAR] = {{0, 8, 4}, {1, 8, 4}, {0, 4, 4}, {1, 4, 8},
+                                         {0, 8, 8}, {0, 16, 4}, {0, 4, 8}, {1, 16, 4}};
 
 template <int G> constexpr Variant var_of(int i) {
     return G == 32 ? VAR32[i] : (G == 64 ? VAR64[i] : VAR128[i]);
@@ -368,13 +302,20 @@ static rd_status launch_variant(const GroupDev &g, float *fields, int64_t steps,
 template <int MODEL, int G, bool RECORD>
 static rd_status launch_resident(const GroupDev &g, float *fields, int64_t steps, double *residual,
                                  uint32_t *status, float *traj, int64_t traj_stride, cudaStream_t s, int vi) {
-    if (RECORD) vi = 1;   // the recording pass always uses the packed default shape
-    switch (vi) {
-        case 1: return launch_variant<MODEL, G, 1, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
-        case 2: return launch_variant<MODEL, G, 2, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
-        case 3: return launch_variant<MODEL, G, 3, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
-        case 4: return launch_variant<MODEL, G, 4, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
-        default: return launch_variant<MODEL, G, 0, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s);
+    if constexpr (RECORD) {
+        // the recording pass always uses the packed shape of variant 1
+        return launch_variant<MODEL, G, 1, true>(g, fields, steps, residual, status, traj, traj_stride, s);
+    } else {
+        switch (vi) {
+            case 1: return launch_variant<MODEL, G, 1, false>(g, fields, steps, residual, status, traj, traj_stride, s);
+            case 2: return launch_variant<MODEL, G, 2, false>(g, fields, steps, residual, status, traj, traj_stride, s);
+            case 3: return launch_variant<MODEL, G, 3, false>(g, fields, steps, residual, status, traj, traj_stride, s);
+            case 4: return launch_variant<MODEL, G, 4, false>(g, fields, steps, residual, status, traj, traj_stride, s);
+            case 5: return launch_variant<MODEL, G, 5, false>(g, fields, steps, residual, status, traj, traj_stride, s);
+            case 6: return launch_variant<MODEL, G, 6, false>(g, fields, steps, residual, status, traj, traj_stride, s);
+            case 7: return launch_variant<MODEL, G, 7, false>(g, fields, steps, residual, status, traj, traj_stride, s);
+            default: return launch_variant<MODEL, G, 0, false>(g, fields, steps, residual, status, traj, traj_stride, s);
+        }
     }
 }
 
