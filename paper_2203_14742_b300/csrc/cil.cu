@@ -11,11 +11,17 @@
 //      representation error E = |(x - c) - (hi + lo)| (all FP64);
 //   2. Gram:  P_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j (bf16 products, FP32
 //      accumulation per K-chunk, chunks summed in FP64);
-//   3. bound: A = N_i + N_j - 2 P_ij approximates d2_ij with a rigorous error
-//      bound built from the FP32 accumulation model, the dropped lo.lo term,
-//      E_i + E_j and the rounding of the canonical sum.  A pair whose interval
-//      [A - m, A + m] contains a threshold (or could hold the maximum that
-//      defines R0) is re-evaluated with the canonical sum.
+//   3. tier 1: A = N_i + N_j - 2 P_ij approximates d2_ij with a rigorous
+//      error bound (FP32 accumulation model, dropped lo.lo term, E_i + E_j,
+//      rounding of the canonical sum), kept as an FP32 interval rounded
+//      outwards;
+//   4. tier 2: pairs whose interval could hold the maximum (which defines R0)
+//      or contain a threshold get an FP32 error-free evaluation of the exact
+//      sum of squares (TwoSum / exact products, double-float accumulation)
+//      with a ~1e-12 relative bound;
+//   5. tier 3: the few pairs still undecided (in practice the maximum) are
+//      evaluated in the canonical FP64 order, one warp per group of 32
+//      partial sums so that the 8 groups of a pair run on different SMs.
 // Counts per radius are reduced with warp ballot + popc.
 #include <cstdio>
 #include <cuda_bf16.h>
@@ -28,9 +34,23 @@ rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2,
 
 static constexpr int KCHUNK_MAX = 512;   // longest split-K chunk (bounds FP32 accumulation error)
 static constexpr int PAD = 64;           // padded pattern length granularity
-static constexpr int TILE = 64;          // Gram output tile (pairs per side)
+static constexpr int TILE = 128;         // Gram output tile (pairs per side)
+static constexpr int MAX_CHUNKS = 64;    // at most this many split-K partials per pair
 
 static inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// scalar slots of the workspace
+enum : int {
+    SC_LB1 = 0,    // max over pairs of the tier-1 lower bound (float bits)
+    SC_UB1 = 1,    // max over pairs of the tier-1 upper bound (float bits)
+    SC_LB2 = 2,    // max over maximum candidates of the tier-2 lower bound (double bits)
+    SC_UB2 = 3,    // max over maximum candidates of the tier-2 upper bound (double bits)
+    SC_MAX = 4,    // exact maximum (double bits)
+    SC_Q1 = 5,     // tier-2 queue length
+    SC_Q2 = 6,     // tier-3 queue length
+    SC_UNDECIDED = 7,
+    SC_TIMEOUT = 8,
+};
 
 struct CilWork {
     int64_t n1, n2, d, dp, kc, nchunk;
@@ -38,11 +58,16 @@ struct CilWork {
     __nv_bfloat16 *hi;      // [(n1+n2)][dp]
     __nv_bfloat16 *lo;      // [(n1+n2)][dp]
     double *N, *H, *L, *E;  // [(n1+n2)]
+    float *Hf, *Lf, *Ef;    // [(n1+n2)] the same bounds as FP32, rounded up
     float *Ppart;           // [nchunk][n1][n2]
-    double *A, *Mg;         // [n1*n2] approximate d2 and its error bound (Mg < 0: A is exact)
-    unsigned long long *queue; // [n1*n2] pairs to evaluate exactly (bit 63: may hold the maximum)
-    unsigned long long *scal;  // [0] max lower bound, [1] max upper bound, [2] exact max (FP64 bits),
-                               // [3] n_rechecked, [4] queue length
+    float *lo32, *hi32;     // [n1*n2] tier-1 interval of d2 (rounded outwards)
+    double *lo2, *hi2;      // [n1*n2] tier-2 interval (valid where flag >= 1)
+    double *ex;             // [n1*n2] canonical d2 (valid where flag == 2)
+    uint8_t *flag;          // [n1*n2] 0: tier 1 decides, 1: tier 2, 2: canonical
+    unsigned long long *q1, *q2;  // [n1*n2] tier-2 / tier-3 queues (bit 63: may hold the maximum)
+    double *grp;            // [n1*n2][8] canonical group sums by tier-3 slot
+    unsigned int *arrive;   // [n1*n2] groups finished, by tier-3 slot
+    unsigned long long *scal;  // see SC_* below
     size_t bytes;
 };
 
@@ -55,6 +80,8 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     int64_t want = (2 * 148 + tiles - 1) / tiles;
     int64_t kc = round_up((w.dp + want - 1) / want, PAD);
     if (kc > KCHUNK_MAX) kc = KCHUNK_MAX;
+    int64_t kmin = round_up((w.dp + MAX_CHUNKS - 1) / MAX_CHUNKS, PAD);
+    if (kc < kmin) kc = kmin;
     w.kc = kc;
     w.nchunk = (w.dp + kc - 1) / kc;
     int64_t n = n1 + n2;
@@ -71,11 +98,22 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     w.H = (double *)take(sizeof(double) * n);
     w.L = (double *)take(sizeof(double) * n);
     w.E = (double *)take(sizeof(double) * n);
-    w.Ppart = (float *)take(sizeof(float) * w.nchunk * n1 * n2);
-    w.A = (double *)take(sizeof(double) * n1 * n2);
-    w.Mg = (double *)take(sizeof(double) * n1 * n2);
-    w.queue = (unsigned long long *)take(sizeof(unsigned long long) * n1 * n2);
-    w.scal = (unsigned long long *)take(sizeof(unsigned long long) * 8);
+    w.Hf = (float *)take(sizeof(float) * n);
+    w.Lf = (float *)take(sizeof(float) * n);
+    w.Ef = (float *)take(sizeof(float) * n);
+    const int64_t np = n1 * n2;
+    w.Ppart = (float *)take(sizeof(float) * w.nchunk * np);
+    w.lo32 = (float *)take(sizeof(float) * np);
+    w.hi32 = (float *)take(sizeof(float) * np);
+    w.lo2 = (double *)take(sizeof(double) * np);
+    w.hi2 = (double *)take(sizeof(double) * np);
+    w.ex = (double *)take(sizeof(double) * np);
+    w.flag = (uint8_t *)take(sizeof(uint8_t) * np);
+    w.q1 = (unsigned long long *)take(sizeof(unsigned long long) * np);
+    w.q2 = (unsigned long long *)take(sizeof(unsigned long long) * np);
+    w.grp = (double *)take(sizeof(double) * 8 * np);
+    w.arrive = (unsigned int *)take(sizeof(unsigned int) * np);
+    w.scal = (unsigned long long *)take(sizeof(unsigned long long) * 16);
     w.bytes = off;
     return w;
 }
@@ -147,7 +185,8 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
                             const float *__restrict__ X2, int64_t ld2, int64_t d, int64_t dp,
                             const float *__restrict__ centre, __nv_bfloat16 *__restrict__ hi,
                             __nv_bfloat16 *__restrict__ lo, double *__restrict__ Nn, double *__restrict__ Hn,
-                            double *__restrict__ Ln, double *__restrict__ En) {
+                            double *__restrict__ Ln, double *__restrict__ En, float *__restrict__ Hf,
+                            float *__restrict__ Lf, float *__restrict__ Ef) {
     const int64_t i = blockIdx.x;
     const float *x = i < n1 ? X1 + i * ld1 : X2 + (i - n1) * ld2;
     // N = |hi + lo|^2 to ~2^-44 relative (compensated FP32); H, L, E are
@@ -206,6 +245,9 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
         Hn[i] = (sqrt(b * infl) + sqrt(c * infl)) * (1.0 + 1e-12);
         Ln[i] = sqrt(c * infl) * (1.0 + 1e-12);
         En[i] = sqrt(e * infl) * (1.0 + 1e-12) + 1e-300;
+        Hf[i] = __double2float_ru(Hn[i]);
+        Lf[i] = __double2float_ru(Ln[i]);
+        Ef[i] = __double2float_ru(En[i]) + 1e-30f;
     }
 }
 
@@ -214,111 +256,239 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
-// 3a. approximate d2 and its rigorous error bound; running max lower bound
+// 3. tier 1: approximate d2 and a rigorous bound, as an FP32 interval
 // ---------------------------------------------------------------------------
 // Accumulation model for the Gram: a sequence of n roundings into one FP32
 // accumulator errs by at most n * u * S, S = sum of the magnitudes of the
 // products, u the unit roundoff of one accumulation step (gam = n * u is
 // passed in per Gram kernel).  Here S = sum |hi||hi'| + |hi||lo'| + |lo||hi'|
-// <= H_i H_j.  The dropped lo.lo' term is bounded by L_i L_j.
-__device__ __forceinline__ void approx_and_bound(const CilWork &w, int64_t i, int64_t j, double P,
-                                                 double gam, double &A, double &m) {
-    const int64_t a = i, b = w.n1 + j;
-    const double Ni = w.N[a], Nj = w.N[b];
-    A = (Ni + Nj) - 2.0 * P;
-    // N_i, N_j carry <= (dp + 64) 2^-44 relative error (compensated FP32)
-    double eg = 2.0 * (gam * w.H[a] * w.H[b] + w.L[a] * w.L[b]) +
-                4.0 * (double)(w.dp + 64) * 5.684341886080802e-14 * (Ni + Nj + 2.0 * fabs(P));
-    double up = fmax(A + eg, 0.0);
-    double D = w.E[a] + w.E[b];
-    double er = D * (2.0 * sqrt(up) + D);
-    double ec = (double)(w.d + 8) * 2.220446049250313e-16 * (up + er);
-    m = 2.0 * (eg + er + ec) + 1e-300;
-}
-
-__global__ void d2_bound_kernel(CilWork w, double gam) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t np = w.n1 * w.n2;
-    double lb = 0.0, ub = 0.0;
+// <= H_i H_j.  The dropped lo.lo' term is bounded by L_i L_j.  The interval
+// arithmetic below rounds every bound upwards (FP32 _ru intrinsics).
+__global__ void d2_bound_kernel(CilWork w, float gam) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t np = w.n1 * w.n2;
+    float lb = 0.f, ub = 0.f;
     if (q < np) {
-        int64_t i = q / w.n2, j = q - i * w.n2;
+        const int64_t i = q / w.n2, j = q - i * w.n2;
+        const int64_t a = i, bb = w.n1 + j;
         float ph = 0.f, pl = 0.f;
         for (int64_t c = 0; c < w.nchunk; ++c) two_sum_acc(ph, pl, w.Ppart[c * np + q]);
-        double P = (double)ph + (double)pl;
-        double A, m;
-        approx_and_bound(w, i, j, P, gam, A, m);
-        w.A[q] = A;
-        w.Mg[q] = m;
-        lb = fmax(A - m, 0.0);
-        ub = fmax(A + m, 0.0);
+        const double P = (double)ph + (double)pl;
+        const double Ni = w.N[a], Nj = w.N[bb];
+        const double A = (Ni + Nj) - 2.0 * P;
+        const float Af = fabsf((float)A);
+        const float Ns = __fadd_ru(__fadd_ru(__double2float_ru(Ni), __double2float_ru(Nj)),
+                                   __fmul_ru(2.f, fabsf(__double2float_ru(fabs(P)))));
+        // Gram accumulation, dropped lo.lo, norms' compensated sums (2^-44),
+        // the double rounding of A above (2^-52 of the terms)
+        float eg = __fmul_ru(2.f, __fadd_ru(__fmul_ru(__fmul_ru(gam, w.Hf[a]), w.Hf[bb]),
+                                            __fmul_ru(w.Lf[a], w.Lf[bb])));
+        eg = __fadd_ru(eg, __fmul_ru((float)(w.dp + 64) * 5.7e-14f + 4.5e-16f, Ns));
+        const float up = __fadd_ru(__double2float_ru(A), eg);
+        const float D = __fadd_ru(w.Ef[a], w.Ef[bb]);
+        const float er = __fmul_ru(D, __fadd_ru(__fmul_ru(2.f, __fsqrt_ru(fmaxf(up, 0.f))), D));
+        // canonical order vs the exact value: (d/256 + 10) 2^-52 relative
+        const float ec = __fmul_ru((float)(w.d / 256 + 10) * 2.3e-16f, __fadd_ru(fmaxf(up, 0.f), er));
+        float m = __fmul_ru(2.f, __fadd_ru(__fadd_ru(eg, er), ec));
+        m = __fadd_ru(m, __fmul_ru(1.2e-7f, Af)) + 1e-30f;   // FP32 rounding of A
+        const float lo = __fsub_rd(__double2float_rd(A), m);
+        const float hi = __fadd_ru(__double2float_ru(A), m);
+        w.lo32[q] = lo;
+        w.hi32[q] = hi;
+        lb = fmaxf(lo, 0.f);
+        ub = fmaxf(hi, 0.f);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        lb = fmax(lb, __shfl_xor_sync(0xffffffffu, lb, o));
-        ub = fmax(ub, __shfl_xor_sync(0xffffffffu, ub, o));
+        lb = fmaxf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+        ub = fmaxf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
     }
     if ((threadIdx.x & 31) == 0) {
-        // non-negative doubles order like their bit patterns
-        atomicMax(&w.scal[0], (unsigned long long)__double_as_longlong(lb));
-        atomicMax(&w.scal[1], (unsigned long long)__double_as_longlong(ub));
+        // non-negative floats order like their bit patterns
+        atomicMax(&w.scal[SC_LB1], (unsigned long long)__float_as_uint(lb));
+        atomicMax(&w.scal[SC_UB1], (unsigned long long)__float_as_uint(ub));
     }
 }
 
-// 3b. exact pass.  classify_kernel enqueues every pair that could hold the
-//     maximum (upper bound >= the largest lower bound) or whose interval
-//     could contain a threshold.  Before R0 is known exactly, R0^2 lies in
-//     [lbmax, ubmax], so T_k = (R0 b^-k)^2 lies in [lbmax b^-2k, ubmax b^-2k]
-//     up to the rounding of the radius recursion (relative 1e-13 margin).
-//     canonical_kernel then evaluates the queued pairs (one block each) and
-//     overwrites A with the exact value, Mg = -1 as the flag.
-__global__ void classify_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M, int all) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t np = w.n1 * w.n2;
+// Threshold ranges.  Before R0 is known exactly, R0^2 lies in [lb, ub] and
+// T_k = (R0 b^-k)^2 in [lb b^-2k, ub b^-2k] up to the rounding of the radius
+// recursion; rel is the relative margin that covers it.
+__device__ __forceinline__ void threshold_ranges(double lb, double ub, double b, int M, double rel, double *tlo,
+                                                 double *thi) {
+    double f = 1.0;
+    for (int k = 0; k < M; ++k) {
+        f = f / (b * b);
+        tlo[k] = lb * f * (1.0 - rel);
+        thi[k] = ub * f * (1.0 + rel);
+    }
+}
+
+// 4a. classify: tier 1 decides, or the pair goes to tier 2 (or straight to
+//     tier 3 for the exact path).
+__global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M, int all) {
+    __shared__ float tlo[32], thi[32];
+    if (threadIdx.x == 0) {
+        double dlo[32], dhi[32];
+        if (radii_in) {
+            for (int k = 0; k < M; ++k) dlo[k] = dhi[k] = __dmul_rn(radii_in[k], radii_in[k]);
+        } else {
+            const double lb = (double)__uint_as_float((unsigned)w.scal[SC_LB1]);
+            const double ub = (double)__uint_as_float((unsigned)w.scal[SC_UB1]);
+            threshold_ranges(lb, ub, b, M, 1e-6, dlo, dhi);
+        }
+        for (int k = 0; k < M; ++k) {
+            tlo[k] = __double2float_rd(dlo[k]);
+            thi[k] = __double2float_ru(dhi[k]);
+        }
+    }
+    __syncthreads();
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t np = w.n1 * w.n2;
     if (q >= np) return;
-    bool need = all != 0, maxc = false;
-    if (!radii_in) {
-        const double lbmax = __longlong_as_double((long long)w.scal[0]);
-        const double ubmax = __longlong_as_double((long long)w.scal[1]);
-        const double lo = all ? 0.0 : w.A[q] - w.Mg[q], hi = all ? 1.0 : w.A[q] + w.Mg[q];
-        maxc = all || hi >= lbmax;
-        need = need || maxc;
-        double f = 1.0;
-        for (int k = 0; k < M && !need; ++k) {
-            f = f / (b * b);
-            double tlo = lbmax * f * (1.0 - 1e-13), thi = ubmax * f * (1.0 + 1e-13);
-            need = !(hi < tlo || lo > thi);
-        }
-    } else if (!need) {
-        const double lo = w.A[q] - w.Mg[q], hi = w.A[q] + w.Mg[q];
-        for (int k = 0; k < M && !need; ++k) {
-            double T = __dmul_rn(radii_in[k], radii_in[k]);
-            need = !(hi < T || lo >= T);
-        }
+    w.flag[q] = 0;
+    if (all) {   // exact path: every pair to tier 3; all may hold the maximum
+        unsigned long long slot = atomicAdd(&w.scal[SC_Q2], 1ull);
+        w.q2[slot] = (unsigned long long)q | (radii_in ? 0ull : (1ull << 63));
+        w.arrive[slot] = 0u;
+        return;
     }
-    if (!need) return;
-    unsigned long long slot = atomicAdd(&w.scal[4], 1ull);
-    w.queue[slot] = (unsigned long long)q | (maxc ? (1ull << 63) : 0ull);
+    const float lo = w.lo32[q], hi = w.hi32[q];
+    const bool maxc = !radii_in && hi >= __uint_as_float((unsigned)w.scal[SC_LB1]);
+    bool amb = false;
+    for (int k = 0; k < M && !amb; ++k) amb = !(hi < tlo[k] || lo >= thi[k]);
+    if (!(maxc || amb)) return;
+    unsigned long long slot = atomicAdd(&w.scal[SC_Q1], 1ull);
+    w.q1[slot] = (unsigned long long)q | (maxc ? (1ull << 63) : 0ull);
 }
 
-__global__ void __launch_bounds__(256) canonical_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
-                                                        const float *__restrict__ X2, int64_t ld2, int count) {
-    __shared__ double sw[8];
-    const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[4];
+// 4b. tier 2: d2 = sum (x - y)^2 from FP32 error-free transformations.
+//     Per element: s = fl(x - y) and e with s + e = x - y exactly (TwoSum);
+//     s^2 = p + pe exactly (product and its FMA error); 2 s e rounded
+//     (error <= 2^-47 s^2); e^2 <= 2^-48 s^2 dropped.  Each thread keeps a
+//     (H, L) pair: H += p error-free (TwoSum), L collects the rest in FP32:
+//     |L| <= (n + 3) 2^-24 S for n terms per thread and S = sum p, so its
+//     2n roundings cost at most 2 n (n + 4) 2^-48 S.  The 256
+//     thread pairs are combined in FP64 (error <= 300 2^-53).  The interval
+//     finally includes the distance of the canonical FP64 order from the
+//     exact value, (d/256 + 10) 2^-52 relative.
+__global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
+                                                    const float *__restrict__ X2, int64_t ld2) {
+    __shared__ double red[2][8];
+    const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[SC_Q1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (unsigned long long qi = blockIdx.x; qi < qlen; qi += gridDim.x) {
-        const unsigned long long ent = w.queue[qi];
+        const unsigned long long ent = w.q1[qi];
         const int64_t q = (int64_t)(ent & ~(1ull << 63));
         const int64_t i = q / w.n2, j = q - i * w.n2;
-        double e = canonical_block(X1 + i * ld1, X2 + j * ld2, w.d, sw);
+        const float *x = X1 + i * ld1, *y = X2 + j * ld2;
+        float H = 0.f, L = 0.f;
+        for (int64_t t = threadIdx.x; t < w.d; t += 256) {
+            const float a = __ldg(x + t), bv = __ldg(y + t);
+            const float sd = a - bv;
+            const float bb = sd - a;
+            const float e = (a - (sd - bb)) + (-bv - bb);
+            const float p = sd * sd;
+            const float pe = fmaf(sd, sd, -p);
+            const float cr = (2.f * sd) * e;
+            two_sum_acc(H, L, p);
+            L += pe + cr;
+        }
+        double v = (double)H + (double)L;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[0][warp] = v;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            w.A[q] = e;
-            w.Mg[q] = -1.0;
-            if (ent >> 63) atomicMax(&w.scal[2], (unsigned long long)__double_as_longlong(e));
-            if (count) atomicAdd(&w.scal[3], 1ull);
+            double D2 = 0.0;
+            for (int g = 0; g < 8; ++g) D2 += red[0][g];
+            const double n = (double)((w.d + 255) / 256);
+            const double rel = 2.0 * (2.9e-14 + 2.0 * n * (n + 4.0) * 3.56e-15 + 300.0 * 1.12e-16 +
+                                      (double)(w.d / 256 + 10) * 2.23e-16);
+            const double err = rel * fabs(D2) + 1e-300;
+            const double lo = D2 - err, hi = D2 + err;
+            w.lo2[q] = lo;
+            w.hi2[q] = hi;
+            w.flag[q] = 1;
+            if (ent >> 63) {
+                atomicMax(&w.scal[SC_LB2], (unsigned long long)__double_as_longlong(fmax(lo, 0.0)));
+                atomicMax(&w.scal[SC_UB2], (unsigned long long)__double_as_longlong(fmax(hi, 0.0)));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// 4c. classify tier-2 pairs: those that may still hold the maximum or whose
+//     tier-2 interval meets a threshold range go to tier 3.
+__global__ void classify2_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M) {
+    __shared__ double tlo[32], thi[32];
+    if (threadIdx.x == 0) {
+        if (radii_in) {
+            for (int k = 0; k < M; ++k) tlo[k] = thi[k] = __dmul_rn(radii_in[k], radii_in[k]);
+        } else {
+            threshold_ranges(__longlong_as_double((long long)w.scal[SC_LB2]),
+                             __longlong_as_double((long long)w.scal[SC_UB2]), b, M, 1e-13, tlo, thi);
+        }
+    }
+    __syncthreads();
+    const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[SC_Q1];
+    const unsigned long long qi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= qlen) return;
+    const unsigned long long ent = w.q1[qi];
+    const int64_t q = (int64_t)(ent & ~(1ull << 63));
+    const double lo = w.lo2[q], hi = w.hi2[q];
+    const bool maxc = (ent >> 63) && hi >= __longlong_as_double((long long)w.scal[SC_LB2]);
+    bool amb = false;
+    for (int k = 0; k < M && !amb; ++k) amb = !(hi < tlo[k] || lo >= thi[k]);
+    if (!(maxc || amb)) return;
+    unsigned long long slot = atomicAdd(&w.scal[SC_Q2], 1ull);
+    w.q2[slot] = (unsigned long long)q | (maxc ? (1ull << 63) : 0ull);
+    w.arrive[slot] = 0u;
+}
+
+// 5. tier 3: the canonical FP64 order.  One warp per (pair, group of 32
+//    partials): lane l of group g sums t = 32 g + l (mod 256) in increasing
+//    t, the warp combines its 32 partials by the halving tree; the last of
+//    the 8 warps of a pair to finish combines the 8 group sums by the same
+//    tree.  Spreading the 8 groups over SMs multiplies the FP64 pipes a pair
+//    can use.
+__global__ void __launch_bounds__(32) canonical_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
+                                                       const float *__restrict__ X2, int64_t ld2) {
+    const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[SC_Q2];
+    const int lane = threadIdx.x;
+    for (unsigned long long it = blockIdx.x; it < qlen * 8ull; it += gridDim.x) {
+        const unsigned long long slot = it >> 3;
+        const int g = (int)(it & 7ull);
+        const unsigned long long ent = w.q2[slot];
+        const int64_t q = (int64_t)(ent & ~(1ull << 63));
+        const int64_t i = q / w.n2, j = q - i * w.n2;
+        const float *x = X1 + i * ld1, *y = X2 + j * ld2;
+        double acc = 0.0;
+        for (int64_t t = 32 * g + lane; t < w.d; t += 256) acc = __dadd_rn(acc, sq_diff(__ldg(x + t), __ldg(y + t)));
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(0xffffffffu, acc, s));
+        if (lane == 0) {
+            w.grp[slot * 8 + g] = acc;
+            __threadfence();
+            const unsigned prev = atomicAdd(&w.arrive[slot], 1u);
+            if (prev == 7u) {
+                __threadfence();
+                double v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = *(volatile double *)&w.grp[slot * 8 + k];
+#pragma unroll
+                for (int s = 4; s >= 1; s >>= 1)
+#pragma unroll
+                    for (int k = 0; k < s; ++k) v[k] = __dadd_rn(v[k], v[k + s]);
+                w.ex[q] = v[0];
+                w.flag[q] = 2;
+                if (ent >> 63) atomicMax(&w.scal[SC_MAX], (unsigned long long)__double_as_longlong(v[0]));
+            }
         }
     }
 }
 
-// 3c. radii: R0 = sqrt(max), R_k = R_{k-1}/b  (or copy the given radii)
+// radii: R0 = sqrt(max), R_k = R_{k-1}/b  (or copy the given radii)
 __global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M,
                              double *__restrict__ radii_out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -327,7 +497,7 @@ __global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, dou
         for (int k = 0; k < M; ++k) radii_out[k + 1] = radii_in[k];
         return;
     }
-    double R = __dsqrt_rn(__longlong_as_double((long long)w.scal[2]));
+    double R = __dsqrt_rn(__longlong_as_double((long long)w.scal[SC_MAX]));
     radii_out[0] = R;
     for (int k = 0; k < M; ++k) {
         R = __ddiv_rn(R, b);
@@ -335,47 +505,54 @@ __global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, dou
     }
 }
 
-// 3d. bins and counts.  A pair is classified from [A - m, A + m] when no
-//     threshold T_k = R_k*R_k falls inside; otherwise from the canonical sum.
+// bins and counts: each pair is decided by the highest tier it reached.
 __global__ void bins_counts_kernel(CilWork w, const double *__restrict__ radii_out, int M,
                                    uint8_t *__restrict__ bins, unsigned long long *__restrict__ counts) {
     __shared__ double Tk[32];
+    __shared__ float Tlo[32], Thi[32];
     __shared__ unsigned long long cnt[32];
     if (threadIdx.x < 32) {
         cnt[threadIdx.x] = 0ull;
         if ((int)threadIdx.x < M) {
-            double r = radii_out[threadIdx.x + 1];
-            Tk[threadIdx.x] = __dmul_rn(r, r);
+            const double r = radii_out[threadIdx.x + 1];
+            const double T = __dmul_rn(r, r);
+            Tk[threadIdx.x] = T;
+            Tlo[threadIdx.x] = __double2float_rd(T);
+            Thi[threadIdx.x] = __double2float_ru(T);
         }
     }
     __syncthreads();
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t np = w.n1 * w.n2;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t np = w.n1 * w.n2;
     int K = 0;
     if (q < np) {
-        bool amb = false;
-        {
-            const double A = w.A[q], m = w.Mg[q];
-            if (m < 0.0) {
-                for (int k = 0; k < M; ++k) K += (A < Tk[k]) ? 1 : 0;
-            } else {
-                for (int k = 0; k < M; ++k) {
-                    double T = Tk[k];
-                    if (A + m < T) K++;
-                    else if (!(A - m >= T)) amb = true;
-                }
+        const int f = w.flag[q];
+        bool und = false;
+        if (f == 2) {
+            const double e = w.ex[q];
+            for (int k = 0; k < M; ++k) K += (e < Tk[k]) ? 1 : 0;
+        } else if (f == 1) {
+            const double lo = w.lo2[q], hi = w.hi2[q];
+            for (int k = 0; k < M; ++k) {
+                if (hi < Tk[k]) K++;
+                else if (!(lo >= Tk[k])) und = true;
+            }
+        } else {
+            const float lo = w.lo32[q], hi = w.hi32[q];
+            for (int k = 0; k < M; ++k) {
+                if (hi < Tlo[k]) K++;
+                else if (!(lo >= Thi[k])) und = true;
             }
         }
-        // A pair the exact pass did not foresee cannot occur (its interval would
-        // straddle a threshold inside the predicted range); flag it loudly.
-        if (amb) {
-            K = 0xFF;
-            atomicOr(&w.scal[5], 1ull);
+        // cannot happen: an interval that meets a threshold was sent to the
+        // next tier by the classify kernels; reported loudly if it does
+        if (und) {
+            atomicOr(&w.scal[SC_UNDECIDED], 1ull);
+            K = 0;
         }
         bins[q] = (uint8_t)K;
     }
     const int lane = threadIdx.x & 31;
-    if (K == 0xFF) K = 0;
     for (int k = 0; k < M; ++k) {
         unsigned bal = __ballot_sync(0xffffffffu, K >= k + 1);
         if (lane == 0 && bal) atomicAdd(&cnt[k], (unsigned long long)__popc(bal));
@@ -386,12 +563,21 @@ __global__ void bins_counts_kernel(CilWork w, const double *__restrict__ radii_o
 
 __global__ void finish_kernel(CilWork w, int64_t *n_rechecked, const int64_t *counts, int M, double *Cv) {
     if (blockIdx.x != 0) return;
-    // a set scal[5] (unforeseen ambiguous pair) reports -1 rechecks, a Gram
-    // timeout (scal[6]) -2
+    // -2: a Gram wait timed out; -1: a pair was left undecided; else the
+    // number of pairs evaluated in the canonical FP64 order
     if (threadIdx.x == 0 && n_rechecked)
-        *n_rechecked = w.scal[6] ? -2 : (w.scal[5] ? -1 : (int64_t)w.scal[3]);
+        *n_rechecked = w.scal[SC_TIMEOUT] ? -2 : (w.scal[SC_UNDECIDED] ? -1 : (int64_t)w.scal[SC_Q2]);
     if (Cv && (int)threadIdx.x < M)
         Cv[threadIdx.x] = __ddiv_rn((double)counts[threadIdx.x], (double)w.n1 * (double)w.n2);
+}
+
+// midpoints and half-widths of the tier-1 intervals (checking entry point)
+__global__ void export_approx_kernel(CilWork w, double *__restrict__ A, double *__restrict__ m) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= w.n1 * w.n2) return;
+    const double lo = w.lo32[q], hi = w.hi32[q];
+    A[q] = 0.5 * (lo + hi);
+    m[q] = 0.5 * (hi - lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,6 +603,34 @@ extern "C" rd_status cil_workspace_size(int64_t n1, int64_t n2, int64_t d, size_
     return RD_OK;
 }
 
+// Tensor-core accumulation model (tier 1): per chunk 3*kc/16 instructions
+// add into the FP32 accumulator; each adds 16 exact bf16 products and the
+// accumulator with at most 17 roundings of 2^-23 relative to the magnitudes
+// involved.  The chunk partials are summed by a compensated FP32 sum
+// ((nchunk + 4) 2^-45 of the magnitudes).
+static float gram_gamma(const CilWork &w) {
+    const double g = (3.0 * (double)w.kc / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
+                     (double)(w.nchunk + 4) * 2.842170943040401e-14;
+    return (float)(g * (1.0 + 1e-6));
+}
+
+// pack + tensor-core Gram + tier-1 intervals
+static rd_status tier1(const CilWork &w, const float *X1, int64_t ld1, const float *X2, int64_t ld2,
+                       cudaStream_t s) {
+    const int64_t n1 = w.n1, n2 = w.n2, np = n1 * n2;
+    centre_kernel<<<(unsigned)((w.dp + 255) / 256), 256, 0, s>>>(X1, ld1, n1, X2, ld2, n2, w.d, w.dp, w.centre);
+    note_launch();
+    pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(X1, ld1, n1, X2, ld2, w.d, w.dp, w.centre, w.hi, w.lo, w.N,
+                                                    w.H, w.L, w.E, w.Hf, w.Lf, w.Ef);
+    note_launch();
+    rd_status st = launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.kc, w.nchunk, w.Ppart,
+                                  reinterpret_cast<uint32_t *>(&w.scal[SC_TIMEOUT]), s);
+    if (st) return st;
+    d2_bound_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(w, gram_gamma(w));
+    note_launch();
+    return RD_OK;
+}
+
 static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *X2, int64_t ld2, int64_t n2,
                          int64_t d, const double *radii_in, double b, int32_t M, double *radii_out,
                          uint8_t *bins, int64_t *counts, double *Cv, int64_t *n_rechecked, void *work,
@@ -428,35 +642,27 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
     CilWork w = layout(n1, n2, d, work);
     if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t np = n1 * n2;
-    unsigned gp = (unsigned)((np + 255) / 256);
-    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 8 * sizeof(unsigned long long), s));
+    const int64_t np = n1 * n2;
+    const unsigned gp = (unsigned)((np + 255) / 256);
+    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 16 * sizeof(unsigned long long), s));
     RD_CUDA_TRY(cudaMemsetAsync(counts, 0, M * sizeof(int64_t), s));
     if (!exact) {
-        centre_kernel<<<(unsigned)((w.dp + 255) / 256), 256, 0, s>>>(X1, ld1, n1, X2, ld2, n2, d, w.dp, w.centre);
-        note_launch();
-        pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(X1, ld1, n1, X2, ld2, d, w.dp, w.centre, w.hi, w.lo, w.N,
-                                                        w.H, w.L, w.E);
-        note_launch();
-        st = launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.kc, w.nchunk, w.Ppart,
-                            reinterpret_cast<uint32_t *>(&w.scal[6]), s);
+        st = tier1(w, X1, ld1, X2, ld2, s);
         if (st) return st;
-        // Tensor-core accumulation model: per chunk 3*kc/16 instructions add
-        // into the FP32 accumulator; each adds 16 exact bf16 products and
-        // the accumulator with at most 17 roundings of 2^-23 relative to the
-        // magnitudes involved.  The chunk partials are summed by a
-        // compensated FP32 sum ((nchunk + 4) 2^-45 of the magnitudes).
-        const double gam = (3.0 * (double)w.kc / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
-                           (double)(w.nchunk + 4) * 2.842170943040401e-14;
-        d2_bound_kernel<<<gp, 256, 0, s>>>(w, gam);
+    }
+    classify1_kernel<<<gp, 256, 0, s>>>(w, radii_in, b, M, exact ? 1 : 0);
+    note_launch();
+    if (!exact) {
+        const unsigned g2 = (unsigned)(np < 2 * 148 ? np : 2 * 148);
+        tier2_kernel<<<g2, 256, 0, s>>>(w, X1, ld1, X2, ld2);
+        note_launch();
+        classify2_kernel<<<gp, 256, 0, s>>>(w, radii_in, b, M);
         note_launch();
     }
-    classify_kernel<<<gp, 256, 0, s>>>(w, radii_in, b, M, exact ? 1 : 0);
-    note_launch();
     {
-        int64_t ncta = 2 * 148;
-        if (ncta > np) ncta = np;
-        canonical_kernel<<<(unsigned)ncta, 256, 0, s>>>(w, X1, ld1, X2, ld2, exact ? 0 : 1);
+        const int64_t items = 8 * np;
+        const unsigned g3 = (unsigned)(items < 16 * 148 ? items : 16 * 148);
+        canonical_kernel<<<g3, 32, 0, s>>>(w, X1, ld1, X2, ld2);
         note_launch();
     }
     radii_kernel<<<1, 32, 0, s>>>(w, radii_in, b, M, radii_out);
@@ -468,9 +674,9 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
     return cuda_status(cudaGetLastError());
 }
 
-// Checking entry point: the approximate d2 (A) and its error bound (m) of
-// every pair from the pack + tensor-core Gram stages, before any exact
-// evaluation.  |A - canonical d2| <= m must hold for every pair.
+// Checking entry point: the tier-1 approximation of every pair as midpoint A
+// and half-width m of its interval (pack + tensor-core Gram + bound, before
+// any exact evaluation).  |A - canonical d2| <= m must hold for every pair.
 extern "C" rd_status cil_debug_approx(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
                                       int64_t n2, int64_t d, double *d_A, double *d_m, void *d_work,
                                       size_t work_bytes, void *stream) {
@@ -480,22 +686,12 @@ extern "C" rd_status cil_debug_approx(const float *d_X1, int64_t ld1, int64_t n1
     CilWork w = layout(n1, n2, d, d_work);
     if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t np = n1 * n2;
-    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 8 * sizeof(unsigned long long), s));
-    centre_kernel<<<(unsigned)((w.dp + 255) / 256), 256, 0, s>>>(d_X1, ld1, n1, d_X2, ld2, n2, d, w.dp, w.centre);
-    note_launch();
-    pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(d_X1, ld1, n1, d_X2, ld2, d, w.dp, w.centre, w.hi, w.lo, w.N,
-                                                    w.H, w.L, w.E);
-    note_launch();
-    st = launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.kc, w.nchunk, w.Ppart,
-                        reinterpret_cast<uint32_t *>(&w.scal[6]), s);
+    const int64_t np = n1 * n2;
+    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 16 * sizeof(unsigned long long), s));
+    st = tier1(w, d_X1, ld1, d_X2, ld2, s);
     if (st) return st;
-    const double gam = (3.0 * (double)w.kc / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
-                       (double)(w.nchunk + 4) * 2.842170943040401e-14;
-    d2_bound_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(w, gam);
+    export_approx_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(w, d_A, d_m);
     note_launch();
-    RD_CUDA_TRY(cudaMemcpyAsync(d_A, w.A, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    RD_CUDA_TRY(cudaMemcpyAsync(d_m, w.Mg, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return cuda_status(cudaGetLastError());
 }
 
@@ -510,7 +706,7 @@ extern "C" rd_status cil_gram_only(int64_t n1, int64_t n2, int64_t d, void *d_wo
     if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
     if (flops) *flops = 3.0 * 2.0 * (double)n1 * (double)n2 * (double)w.dp;
     return launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.kc, w.nchunk, w.Ppart,
-                          reinterpret_cast<uint32_t *>(&w.scal[6]), (cudaStream_t)stream);
+                          reinterpret_cast<uint32_t *>(&w.scal[SC_TIMEOUT]), (cudaStream_t)stream);
 }
 
 extern "C" rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
