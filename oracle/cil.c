@@ -153,39 +153,44 @@ void orc_resample_counts(const uint8_t *bins, int64_t n1, int64_t n2, int M,
 }
 
 /* Synthetic-likelihood statistics (Alg. 1 step 3, eq. cil:CF, eq.
-   cil:CF_synth).  y_t = Y_t / (n1*n2).  mu = mean over t; Sigma = sample
-   covariance with 1/(T-1); active[k] = 1 unless all Y[t][k] are equal;
+   cil:CF_synth).  y_t = Y_t / n_pairs, n_pairs = n1*n2.  The mean and the
+   sample covariance (normaliser 1/(T-1)) of the y_t are rational numbers of
+   the integer counts; they are formed exactly from S_k = sum_t Y[t][k] and
+   P_kl = sum_t Y[t][k] Y[t][l] and rounded at the end:
+     mu_k     = S_k / (T n_pairs),
+     Sigma_kl = (T P_kl - S_k S_l) / (T (T-1) n_pairs^2)
+   (numerator and denominator exact 64-bit integers, each converted to FP64
+   with rounding to nearest, then one FP64 division).
+   active[k] = 1 unless all Y[t][k] are equal;
    L = lower Cholesky factor of the active block (Cholesky-Banachiewicz);
    logdet = 2*sum log L_ii; f = || L^-1 (y_obs - mu)_act ||^2;
    loglik = -(f + logdet + M_act*log(2*pi))/2.
    cov and chol are M x M; chol holds the factor of the active block packed
    into its leading M_act x M_act corner.  Returns 0, or 3 when the active
-   block is not positive definite. */
+   block is not positive definite.  Requires T^2 n_pairs^2 < 2^62. */
 int orc_stats(const int64_t *Y, int T, int M, int64_t n_pairs,
               const double *y_obs, double *mu, double *cov, double *chol,
               double *logdet, double *f, double *loglik, uint8_t *active,
               int *m_act_out)
 {
-    double *y = (double *)malloc(sizeof(double) * (size_t)T * (size_t)M);
-    for (int64_t q = 0; q < (int64_t)T * M; ++q) y[q] = (double)Y[q] / (double)n_pairs;
+    int64_t S[256];
     for (int k = 0; k < M; ++k) {
-        double s = 0.0;
-        for (int t = 0; t < T; ++t) s = s + y[(int64_t)t * M + k];
-        mu[k] = s / (double)T;
+        int64_t s = 0;
+        for (int t = 0; t < T; ++t) s += Y[(int64_t)t * M + k];
+        S[k] = s;
+        mu[k] = (double)s / ((double)T * (double)n_pairs);
         int same = 1;
         for (int t = 1; t < T; ++t)
             if (Y[(int64_t)t * M + k] != Y[k]) same = 0;
         active[k] = (uint8_t)(same ? 0 : 1);
     }
+    const int64_t den = (int64_t)T * (int64_t)(T - 1) * n_pairs * n_pairs;
     for (int k = 0; k < M; ++k)
         for (int l = 0; l < M; ++l) {
-            double s = 0.0;
-            for (int t = 0; t < T; ++t) {
-                double a = y[(int64_t)t * M + k] - mu[k];
-                double b = y[(int64_t)t * M + l] - mu[l];
-                s = s + a * b;
-            }
-            cov[k * M + l] = s / (double)(T - 1);
+            int64_t P = 0;
+            for (int t = 0; t < T; ++t) P += Y[(int64_t)t * M + k] * Y[(int64_t)t * M + l];
+            const int64_t num = (int64_t)T * P - S[k] * S[l];
+            cov[k * M + l] = (double)num / (double)den;
         }
     int idx[256];
     int ma = 0;
@@ -225,7 +230,6 @@ int orc_stats(const int64_t *Y, int T, int M, int64_t n_pairs,
         *f = NAN;
         *loglik = NAN;
     }
-    free(y);
     return status;
 }
 

@@ -250,3 +250,21 @@ def test_canonical_order_matches_written_out_tree():
                 w[i] = w[i] + w[i + s]
             s //= 2
         assert oracle.pair_d2(x[None], y[None])[0, 0] == w[0]
+
+
+def test_stats_mean_cov_are_exactly_rounded_rationals():
+    """Mean and covariance of y_t = Y_t / n_pairs are the exact rationals of
+    the integer counts, rounded once (Python's float(Fraction) is correctly
+    rounded), for counts whose numerators stay below 2^53."""
+    from fractions import Fraction
+    rng = np.random.default_rng(4)
+    T, M, npairs = 37, 5, 1000
+    Y = rng.integers(0, npairs + 1, size=(T, M)).astype(np.int64)
+    s = oracle.stats(Y, npairs)
+    for k in range(M):
+        assert s["mu"][k] == float(Fraction(int(Y[:, k].sum()), T * npairs))
+        for l in range(M):
+            ex = sum((Fraction(int(Y[t, k]), npairs) - Fraction(int(Y[:, k].sum()), T * npairs)) *
+                     (Fraction(int(Y[t, l]), npairs) - Fraction(int(Y[:, l].sum()), T * npairs))
+                     for t in range(T)) / (T - 1)
+            assert s["cov"][k, l] == float(ex)
