@@ -39,6 +39,12 @@ static constexpr int MAX_CHUNKS = 64;    // at most this many split-K partials p
 
 static inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// b^-2k, k = 1..M, evaluated on the host (only used for the threshold
+// ranges, which carry a relative margin)
+struct Beta {
+    double v[32];
+};
+
 // scalar slots of the workspace
 enum : int {
     SC_LB1 = 0,    // max over pairs of the tier-1 lower bound (float bits)
@@ -67,6 +73,8 @@ struct CilWork {
     unsigned long long *q1, *q2;  // [n1*n2] tier-2 / tier-3 queues (bit 63: may hold the maximum)
     double *grp;            // [n1*n2][8] canonical group sums by tier-3 slot
     unsigned int *arrive;   // [n1*n2] groups finished, by tier-3 slot
+    float *t1lo, *t1hi;     // [32] tier-1 threshold ranges (FP32, outward)
+    double *t2lo, *t2hi;    // [32] tier-2 threshold ranges
     unsigned long long *scal;  // see SC_* below
     size_t bytes;
 };
@@ -113,6 +121,10 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     w.q2 = (unsigned long long *)take(sizeof(unsigned long long) * np);
     w.grp = (double *)take(sizeof(double) * 8 * np);
     w.arrive = (unsigned int *)take(sizeof(unsigned int) * np);
+    w.t1lo = (float *)take(sizeof(float) * 32);
+    w.t1hi = (float *)take(sizeof(float) * 32);
+    w.t2lo = (double *)take(sizeof(double) * 32);
+    w.t2hi = (double *)take(sizeof(double) * 32);
     w.scal = (unsigned long long *)take(sizeof(unsigned long long) * 16);
     w.bytes = off;
     return w;
@@ -174,11 +186,13 @@ __global__ void centre_kernel(const float *__restrict__ X1, int64_t ld1, int64_t
     if (t >= dp) return;
     if (t >= d) { centre[t] = 0.f; return; }
     // any centre is valid (distances are translation invariant); a good one
-    // keeps |x - c| small so the bf16 split loses little
+    // keeps |x - c| small so the bf16 split loses little.  The mean of up to
+    // 16 patterns evenly spread over each set is plenty for that.
+    const int64_t s1 = n1 < 16 ? n1 : 16, s2 = n2 < 16 ? n2 : 16;
     float s = 0.f;
-    for (int64_t i = 0; i < n1; ++i) s += X1[i * ld1 + t];
-    for (int64_t j = 0; j < n2; ++j) s += X2[j * ld2 + t];
-    centre[t] = s / (float)(n1 + n2);
+    for (int64_t a = 0; a < s1; ++a) s += X1[(a * n1 / s1) * ld1 + t];
+    for (int64_t a = 0; a < s2; ++a) s += X2[(a * n2 / s2) * ld2 + t];
+    centre[t] = s / (float)(s1 + s2);
 }
 
 __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n1,
@@ -312,34 +326,43 @@ __global__ void d2_bound_kernel(CilWork w, float gam) {
 
 // Threshold ranges.  Before R0 is known exactly, R0^2 lies in [lb, ub] and
 // T_k = (R0 b^-k)^2 in [lb b^-2k, ub b^-2k] up to the rounding of the radius
-// recursion; rel is the relative margin that covers it.
-__device__ __forceinline__ void threshold_ranges(double lb, double ub, double b, int M, double rel, double *tlo,
-                                                 double *thi) {
-    double f = 1.0;
-    for (int k = 0; k < M; ++k) {
-        f = f / (b * b);
-        tlo[k] = lb * f * (1.0 - rel);
-        thi[k] = ub * f * (1.0 + rel);
+// recursion; rel is the relative margin that covers it.  One thread per k
+// (beta[k] = b^-2k from the host).  tier 1 writes FP32 ranges rounded
+// outwards, tier 2 FP64 ranges.  With given radii the ranges are the exact
+// thresholds.
+__global__ void ranges_kernel(CilWork w, const double *__restrict__ radii_in, Beta beta, int M, int tier) {
+    const int k = threadIdx.x;
+    if (k >= M) return;
+    double lo, hi;
+    if (radii_in) {
+        lo = hi = __dmul_rn(radii_in[k], radii_in[k]);
+    } else if (tier == 1) {
+        const double lb = (double)__uint_as_float((unsigned)w.scal[SC_LB1]);
+        const double ub = (double)__uint_as_float((unsigned)w.scal[SC_UB1]);
+        lo = lb * beta.v[k] * (1.0 - 1e-6);
+        hi = ub * beta.v[k] * (1.0 + 1e-6);
+    } else {
+        const double lb = __longlong_as_double((long long)w.scal[SC_LB2]);
+        const double ub = __longlong_as_double((long long)w.scal[SC_UB2]);
+        lo = lb * beta.v[k] * (1.0 - 1e-13);
+        hi = ub * beta.v[k] * (1.0 + 1e-13);
+    }
+    if (tier == 1) {
+        w.t1lo[k] = __double2float_rd(lo);
+        w.t1hi[k] = __double2float_ru(hi);
+    } else {
+        w.t2lo[k] = lo;
+        w.t2hi[k] = hi;
     }
 }
 
 // 4a. classify: tier 1 decides, or the pair goes to tier 2 (or straight to
 //     tier 3 for the exact path).
-__global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M, int all) {
+__global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in, int M, int all) {
     __shared__ float tlo[32], thi[32];
-    if (threadIdx.x == 0) {
-        double dlo[32], dhi[32];
-        if (radii_in) {
-            for (int k = 0; k < M; ++k) dlo[k] = dhi[k] = __dmul_rn(radii_in[k], radii_in[k]);
-        } else {
-            const double lb = (double)__uint_as_float((unsigned)w.scal[SC_LB1]);
-            const double ub = (double)__uint_as_float((unsigned)w.scal[SC_UB1]);
-            threshold_ranges(lb, ub, b, M, 1e-6, dlo, dhi);
-        }
-        for (int k = 0; k < M; ++k) {
-            tlo[k] = __double2float_rd(dlo[k]);
-            thi[k] = __double2float_ru(dhi[k]);
-        }
+    if ((int)threadIdx.x < M) {
+        tlo[threadIdx.x] = w.t1lo[threadIdx.x];
+        thi[threadIdx.x] = w.t1hi[threadIdx.x];
     }
     __syncthreads();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -420,15 +443,11 @@ __global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__re
 
 // 4c. classify tier-2 pairs: those that may still hold the maximum or whose
 //     tier-2 interval meets a threshold range go to tier 3.
-__global__ void classify2_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M) {
+__global__ void classify2_kernel(CilWork w, int M) {
     __shared__ double tlo[32], thi[32];
-    if (threadIdx.x == 0) {
-        if (radii_in) {
-            for (int k = 0; k < M; ++k) tlo[k] = thi[k] = __dmul_rn(radii_in[k], radii_in[k]);
-        } else {
-            threshold_ranges(__longlong_as_double((long long)w.scal[SC_LB2]),
-                             __longlong_as_double((long long)w.scal[SC_UB2]), b, M, 1e-13, tlo, thi);
-        }
+    if ((int)threadIdx.x < M) {
+        tlo[threadIdx.x] = w.t2lo[threadIdx.x];
+        thi[threadIdx.x] = w.t2hi[threadIdx.x];
     }
     __syncthreads();
     const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[SC_Q1];
@@ -650,13 +669,27 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
         st = tier1(w, X1, ld1, X2, ld2, s);
         if (st) return st;
     }
-    classify1_kernel<<<gp, 256, 0, s>>>(w, radii_in, b, M, exact ? 1 : 0);
+    Beta beta{};
+    {
+        double f = 1.0;
+        for (int k = 0; k < M; ++k) {
+            f = f / (b * b);
+            beta.v[k] = radii_in ? 0.0 : f;
+        }
+    }
+    if (!exact) {
+        ranges_kernel<<<1, 32, 0, s>>>(w, radii_in, beta, M, 1);
+        note_launch();
+    }
+    classify1_kernel<<<gp, 256, 0, s>>>(w, radii_in, M, exact ? 1 : 0);
     note_launch();
     if (!exact) {
         const unsigned g2 = (unsigned)(np < 2 * 148 ? np : 2 * 148);
         tier2_kernel<<<g2, 256, 0, s>>>(w, X1, ld1, X2, ld2);
         note_launch();
-        classify2_kernel<<<gp, 256, 0, s>>>(w, radii_in, b, M);
+        ranges_kernel<<<1, 32, 0, s>>>(w, radii_in, beta, M, 2);
+        note_launch();
+        classify2_kernel<<<gp, 256, 0, s>>>(w, M);
         note_launch();
     }
     {
