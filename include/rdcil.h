@@ -287,7 +287,12 @@ rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1,
  * (Lemire's multiply-shift), set-2 index b with ((t*2+1) << 32) | b.
  * Y[t][k-1] = sum_a sum_b [K_{I_a J_b} >= k]   (int64)
  * y_t = Y_t / (n1 n2);  mu = (1/T) sum_t y_t;
- * cov = (1/(T-1)) sum_t (y_t - mu)(y_t - mu)^T;
+ * cov = (1/(T-1)) sum_t (y_t - mu)(y_t - mu)^T,
+ * both formed exactly from the integer counts and rounded once:
+ *   mu_k = S_k / (T n1 n2),  cov_kl = (T P_kl - S_k S_l) / (T (T-1) (n1 n2)^2)
+ *   with S_k = sum_t Y[t][k], P_kl = sum_t Y[t][k] Y[t][l] (64-bit integers;
+ *   numerator and denominator each converted to FP64 with rounding to
+ *   nearest, then one FP64 division);
  * active[k] = 0 iff Y[t][k] is the same for every t;
  * chol = lower Cholesky factor of the active block of cov, packed into the
  *   leading M_act x M_act corner (rest zero);
@@ -295,10 +300,8 @@ rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1,
  *   f = |L^-1 (y_obs - mu)_act|^2, loglik = -(f + logdet + M_act log 2pi)/2
  *   (f and loglik NaN when d_y_obs is NULL);
  * status[p] = RD_OK or RD_ERR_NOT_PD (active block not positive definite).
- * mu and cov follow the plain sequential definition in t order, so they
- * match a plain FP64 evaluation bit for bit.
- * Limits: n1 + n2 <= 49152; 1 <= M <= 32; 2 <= T; T*M <= 24576;
- * T*(n1*n2)^2 < 4.6e18.  Violations return RD_ERR_INVALID_ARG. */
+ * Limits: n1 + n2 <= 49152; 1 <= M <= 32; 2 <= T;
+ * (T n1 n2)^2 < 4.6e18.  Violations return RD_ERR_INVALID_ARG. */
 rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2, int32_t M,
                        int32_t T, uint64_t seed, int32_t n_problems,
                        const double *d_y_obs, int64_t *d_Y, double *d_mu,

@@ -9,10 +9,10 @@
 //   counter-based SplitMix64 stream, are staged in shared memory, and the
 //   per-radius counts of the resampled pair set are accumulated with warp
 //   ballot + popc over the stored bin indices K_ij.
-// stats_kernel: one CTA per problem.  Mean and covariance follow the plain
-//   sequential definition in t order without FMA (so they equal a plain FP64
-//   evaluation bit for bit); Cholesky of the active block, log-determinant,
-//   Mahalanobis term and log-likelihood on one thread (M <= 32).
+// stats_kernel: one CTA per problem.  Mean and covariance are the exact
+//   rationals of the integer counts, formed with integer sums and rounded
+//   once; Cholesky of the active block column by column (rows of a column in
+//   parallel); log-determinant, Mahalanobis term and log-likelihood (M <= 32).
 #include "common.cuh"
 
 namespace rdcil {
@@ -68,62 +68,73 @@ __global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int
                              int32_t *__restrict__ status_all) {
     const int p = blockIdx.x;
     const int64_t *Y = Yall + (int64_t)p * T * M;
-    extern __shared__ double ys[];   // [T][M]: y_t = Y_t / (n1 n2), one division each
+    __shared__ long long S[32];
     __shared__ double mu[32], cov[32 * 32], L[32 * 32];
-    __shared__ int act[32];
-    const double dnp = (double)np;
+    __shared__ int act[32], idx[32], s_ma, s_st;
     const int tid = threadIdx.x;
-    for (int e = tid; e < T * M; e += blockDim.x) ys[e] = __ddiv_rn((double)Y[e], dnp);
-    __syncthreads();
+    // mean: S_k / (T n_pairs), S_k an exact integer sum
     if (tid < M) {
-        double s = 0.0;
+        long long sum = 0;
         int same = 1;
-        const int64_t y0 = Y[tid];
+        const long long y0 = Y[tid];
         for (int t = 0; t < T; ++t) {
-            s = __dadd_rn(s, ys[t * M + tid]);
-            same &= (Y[(int64_t)t * M + tid] == y0);
+            const long long yy = Y[(int64_t)t * M + tid];
+            sum += yy;
+            same &= (yy == y0);
         }
-        mu[tid] = __ddiv_rn(s, (double)T);
+        S[tid] = sum;
+        mu[tid] = __ddiv_rn(__ll2double_rn(sum), __dmul_rn((double)T, (double)np));
         act[tid] = same ? 0 : 1;
     }
     __syncthreads();
+    // covariance: (T P_kl - S_k S_l) / (T (T-1) n_pairs^2), exact integers,
+    // each rounded to FP64 once, then one division
+    const double dden = __ll2double_rn((long long)T * (long long)(T - 1) * np * np);
     for (int e = tid; e < M * M; e += blockDim.x) {
-        int k = e / M, l = e - k * M;
-        double s = 0.0;
-        if (l >= k) {   // symmetric: the (l, k) entry is the same sequence of operations
-            for (int t = 0; t < T; ++t) {
-                double a = __dsub_rn(ys[t * M + k], mu[k]);
-                double b = __dsub_rn(ys[t * M + l], mu[l]);
-                s = __dadd_rn(s, __dmul_rn(a, b));
-            }
-            cov[e] = __ddiv_rn(s, (double)(T - 1));
+        const int k = e / M, l = e - k * M;
+        if (l >= k) {
+            long long P = 0;
+            for (int t = 0; t < T; ++t) P += Y[(int64_t)t * M + k] * Y[(int64_t)t * M + l];
+            const long long num = (long long)T * P - S[k] * S[l];
+            cov[e] = __ddiv_rn(__ll2double_rn(num), dden);
         }
         L[e] = 0.0;
     }
     __syncthreads();
     for (int e = tid; e < M * M; e += blockDim.x) {
-        int k = e / M, l = e - k * M;
+        const int k = e / M, l = e - k * M;
         if (l < k) cov[e] = cov[l * M + k];
     }
-    __syncthreads();
     if (tid == 0) {
-        int idx[32];
         int ma = 0;
         for (int k = 0; k < M; ++k)
             if (act[k]) idx[ma++] = k;
-        int st = RD_OK;
-        for (int i = 0; i < ma && st == RD_OK; ++i) {
-            for (int j = 0; j <= i; ++j) {
-                double s = cov[idx[i] * M + idx[j]];
-                for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(L[i * M + k], L[j * M + k]));
-                if (i == j) {
-                    if (!(s > 0.0)) { st = RD_ERR_NOT_PD; break; }
-                    L[i * M + i] = __dsqrt_rn(s);
-                } else {
-                    L[i * M + j] = __ddiv_rn(s, L[j * M + j]);
-                }
-            }
+        s_ma = ma;
+        s_st = RD_OK;
+    }
+    __syncthreads();
+    const int ma = s_ma;
+    // Cholesky of the active block, column by column; every entry is the
+    // same sequence of operations as row-by-row Cholesky-Banachiewicz
+    // (inner sums in increasing k), so the factor is identical
+    for (int j = 0; j < ma; ++j) {
+        if (tid == 0) {
+            double s = cov[idx[j] * M + idx[j]];
+            for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(L[j * M + k], L[j * M + k]));
+            if (!(s > 0.0)) s_st = RD_ERR_NOT_PD;
+            else L[j * M + j] = __dsqrt_rn(s);
         }
+        __syncthreads();
+        if (s_st != RD_OK) break;
+        for (int i = j + 1 + tid; i < ma; i += blockDim.x) {
+            double s = cov[idx[i] * M + idx[j]];
+            for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(L[i * M + k], L[j * M + k]));
+            L[i * M + j] = __ddiv_rn(s, L[j * M + j]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int st = s_st;
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
         double logdet = nan, f = nan, ll = nan;
         if (st == RD_OK) {
@@ -173,9 +184,9 @@ extern "C" rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2,
     if (n1 < 1 || n2 < 1 || n1 + n2 > 49152 || M < 1 || M > 32 || T < 2 || n_problems < 1 ||
         n_problems > 65535)
         return RD_ERR_INVALID_ARG;
+    // the exact covariance numerators T P_kl - S_k S_l stay in 64 bits
     double np = (double)n1 * (double)n2;
-    if ((double)T * np * np >= 4.6e18) return RD_ERR_INVALID_ARG;
-    if ((int64_t)T * M > 24576) return RD_ERR_INVALID_ARG;   // y_t staged in shared memory
+    if ((double)T * (double)T * np * np >= 4.6e18) return RD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     size_t smem = (size_t)(n1 + n2) * sizeof(int32_t);
     if (smem > 48 * 1024) {
@@ -189,16 +200,7 @@ extern "C" rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2,
     dim3 g((unsigned)T, (unsigned)n_problems);
     bootstrap_kernel<<<g, 256, smem, s>>>(d_bins, (int)n1, (int)n2, M, T, seed, d_Y);
     note_launch();
-    size_t smem2 = (size_t)T * M * sizeof(double);
-    if (smem2 > 48 * 1024) {
-        static size_t set2 = 0;
-        if (smem2 > set2) {
-            RD_CUDA_TRY(cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem2));
-            set2 = smem2;
-        }
-    }
-    stats_kernel<<<(unsigned)n_problems, 256, smem2, s>>>(d_Y, M, T, n1 * n2, d_y_obs, d_mu, d_cov, d_chol,
+    stats_kernel<<<(unsigned)n_problems, 256, 0, s>>>(d_Y, M, T, n1 * n2, d_y_obs, d_mu, d_cov, d_chol,
                                                       d_scalars, d_active, d_status);
     note_launch();
     return cuda_status(cudaGetLastError());

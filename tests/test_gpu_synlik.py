@@ -1,8 +1,8 @@
 """GPU parity of the bootstrap counts and synthetic-likelihood statistics.
 
-Resampled counts are integers: bit-exact.  Mean, covariance and the
-Cholesky factor follow the same sequential operation order with every
-operation rounded separately on both sides: bit-exact.  log() is the only
+Resampled counts are integers: bit-exact.  Mean and covariance are exact
+rationals of the counts rounded once on both sides, and the Cholesky factor
+is the same sequence of rounded operations: bit-exact.  log() is the only
 library function involved (log-determinant, log-likelihood): relative 1e-13.
 """
 import math
