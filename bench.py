@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -33,11 +34,11 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
-# FP32-pipe instructions of the implemented update per cell-update: FHN 8
-# (two 5-point sums) + 8 (kinetics and update); GM 8 + 13 (deviation form;
+# FP32-pipe instructions of the implemented update per cell-update: two
+# neighbour sums (3 + 3), then FHN u 6, v 3; GM u 9, v 5 (deviation form;
 # the division's reciprocal runs on the MUFU pipe and is not counted);
-# DIFF 8 + 2.
-FP32_INST_PER_CELL = {W.FHN: 16, W.GM: 21, W.DIFF: 10}
+# DIFF 2 + 2.
+FP32_INST_PER_CELL = {W.FHN: 15, W.GM: 20, W.DIFF: 10}
 
 # DRAM bytes (read + write) of one stepper launch on this workload, from the
 # ncu capture summarised in profiles/rd_resident_scalar_kernel_fhn64_c2.md,
@@ -87,60 +88,77 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled through NVML (the
+    driver library nvidia-smi reads, called through ctypes) every few
+    milliseconds on a thread, so that even a timed region of a few tens of
+    milliseconds has samples.  Call begin() and end() around the timed
+    region; summary() keeps the samples taken between them."""
 
-    def __init__(self, index):
+    # nvmlClocksEventReason* bits of the NVML API
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, index, interval_s=0.005):
         self.index = index
-        self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        self.interval = interval_s
+        self.samples = []
+        self.t_begin = self.t_end = None
+        self.thread = None
+        self.stop = threading.Event()
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index),
-                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=self.f, stderr=subprocess.DEVNULL)
+            import ctypes as C
+            nv = C.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return self
+            h = C.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.index), C.byref(h)) != 0:
+                return self
+            mx = C.c_uint(0)
+            nv.nvmlDeviceGetMaxClockInfo(h, C.c_int(self.NVML_CLOCK_SM), C.byref(mx))
+            self.max_mhz = int(mx.value)
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+
+            def loop():
+                clk, rs = C.c_uint(0), C.c_ulonglong(0)
+                while not self.stop.is_set():
+                    if nv.nvmlDeviceGetClockInfo(h, C.c_int(self.NVML_CLOCK_SM), C.byref(clk)) == 0 and \
+                            get_reasons(h, C.byref(rs)) == 0:
+                        self.samples.append((time.perf_counter(), int(clk.value),
+                                             [n for n, m in self.REASONS if rs.value & m]))
+                    self.stop.wait(self.interval)
+
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            time.sleep(0.05)
         except Exception:
-            self.proc = None
+            self.thread = None
         return self
 
+    def begin(self):
+        self.t_begin = time.perf_counter()
+
+    def end(self):
+        self.t_end = time.perf_counter()
+
     def __exit__(self, *a):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
-            self.f.close()
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=2)
 
     def summary(self):
-        if self.proc is None:
+        if self.thread is None or self.t_begin is None:
             return None
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        try:
-            for line in open(self.path):
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 7:
-                    continue
-                try:
-                    sm.append(float(parts[0]))
-                    mx.append(float(parts[1]))
-                except ValueError:
-                    continue
-                for n, v in zip(names, parts[3:7]):
-                    if v.lower() == "active":
-                        reasons.add(n)
-        except OSError:
+        t1 = self.t_end if self.t_end is not None else float("inf")
+        inside = [s for s in self.samples if self.t_begin <= s[0] <= t1]
+        if not inside:
             return None
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = sorted(set(r for s in inside for r in s[2]))
+        return {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(inside), "source": "NVML every 5 ms in the timed region"}
 
 
 # ---------------------------------------------------------------------------
@@ -196,6 +214,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
+        clk.begin()
         for i in range(args.steps):
             flush.fill_(float(i))
             e = marks[i]
@@ -210,6 +229,7 @@ def run_ours(args, rank, world, local_rank):
             p.synlik(pipe.bins, M, T, pipe.seed, y_obs=pipe.C, out=pipe.stats)
             e[4].record(stream)
         torch.cuda.synchronize()
+        clk.end()
     launches = p.lib().rd_kernel_launches() - launches0
     step_ms = sum(m[0].elapsed_time(m[4]) for m in marks)
     k_ms = [m[1].elapsed_time(m[2]) for m in marks]
@@ -336,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak_alu,
                      "traffic": stepper_traffic() if variant == 0 and args.config == "c2" else None,
                      "kernel": kname,
-                     "note": "FP32 pipe instructions of the update (FHN 16, GM 21 per cell-update) x "
+                     "note": "FP32 pipe instructions of the update (FHN 15, GM 20 per cell-update) x "
                              "cell-updates / stepper time; peak = 148 SM x 128 FP32 lanes x max SM clock "
                              "(%s peaks file)" % src},
         "plain_fp32_path_cell_updates_per_s": ref_rate,

@@ -514,10 +514,10 @@ __global__ void rd_reference_step_kernel(const float *__restrict__ src, float *_
     int k = y * G + x;
     int kn = (y > 0 ? y - 1 : y) * G + x, ks = (y < G - 1 ? y + 1 : y) * G + x;
     int kw = y * G + (x > 0 ? x - 1 : x), ke = y * G + (x < G - 1 ? x + 1 : x);
-    float lu = fmaf(-4.f, u[k], (u[kn] + u[ks]) + (u[kw] + u[ke]));
-    float lv = fmaf(-4.f, v[k], (v[kn] + v[ks]) + (v[kw] + v[ke]));
+    float nu = (u[kn] + u[ks]) + (u[kw] + u[ke]);
+    float nv = (v[kn] + v[ks]) + (v[kw] + v[ke]);
     float un, vn;
-    euler_cell<MODEL>(u[k], v[k], lu, lv, cf, un, vn);
+    euler_cell<MODEL>(u[k], v[k], nu, nv, cf, un, vn);
     dst[k] = un;
     dst[G * G + k] = vn;
 }

@@ -6,6 +6,9 @@
 // the east/west neighbours of a tile edge are shuffle lanes), NY = G/TY
 // along y.  North/south tile edges go through a double-buffered shared
 // memory ring halo[buf 2][species 2][edge 2][NY][G] (one barrier per step).
+// (Extra ring slots holding the mirror ghosts, which make the north/south
+// reads unconditional, measured 9 % slower on FHN 64x64: the edge tiles'
+// extra stores cost more than the tests they remove.)
 #pragma once
 #include "common.cuh"
 
@@ -114,31 +117,43 @@ __device__ __forceinline__ void row_west_east(int tx, float first, float last, f
 // GM is stepped in deviation form (see euler_cell): u0, v0 = the FP32
 // equilibrium (1/mu, 1/mu^2), tu0 = 2 u0, e0 = u0 - mu v0 and e1 = u0^2 - v0
 // (evaluated in FP64, rounded once; both are 0 when 1/mu is exact).
+// The v update folds the node's own weight with the -4 of the 5-point
+// stencil (FP64 on the host, rounded once):
+//   FHN: be = 1 - 4 cv - k2 k3;   GM: be = 1 - 4 cv - k2, k2e1 = k2 e1.
+// (v relaxes quickly, so the rounding of be does not accumulate; u keeps
+// the form u + increments, because a rounded weight near 1 on u itself
+// would bias every step the same way.)
 struct CoefF {
     float cu, cv, k1, k2, k3;
     float u0, v0, tu0, e0, e1;
+    float be, k2e1;
 };
 
 inline CoefF make_coef(const GroupDev &g) {
     double g1 = (double)(g.G - 1);
     double h2 = g1 * g1;
     CoefF c{};
-    c.cu = (float)(g.p[0] * g.dt * h2);
-    c.cv = (float)(g.p[1] * g.dt * h2);
+    const double cu = g.p[0] * g.dt * h2, cv = g.p[1] * g.dt * h2;
+    c.cu = (float)cu;
+    c.cv = (float)cv;
     c.k1 = (float)g.dt;
     if (g.model == RD_FHN || g.model == RD_GM) {
         c.k2 = (float)(g.p[2] * g.dt);
         c.k3 = (float)g.p[3];
     }
+    if (g.model == RD_FHN) c.be = (float)(1.0 - 4.0 * cv - g.p[2] * g.dt * g.p[3]);
     if (g.model == RD_GM) {
-        double mu = g.p[3];
+        double mu = g.p[3], k2 = g.p[2] * g.dt;
         float u0 = (float)(1.0 / mu);
         float v0 = (float)((double)u0 * (double)u0);
         c.u0 = u0;
         c.v0 = v0;
         c.tu0 = 2.0f * u0;
-        c.e0 = (float)((double)u0 - mu * (double)v0);
-        c.e1 = (float)((double)u0 * (double)u0 - (double)v0);
+        const double e0 = (double)u0 - mu * (double)v0, e1 = (double)u0 * (double)u0 - (double)v0;
+        c.e0 = (float)e0;
+        c.e1 = (float)e1;
+        c.be = (float)(1.0 - 4.0 * cv - k2);
+        c.k2e1 = (float)(k2 * e1);
     }
     return c;
 }
@@ -154,32 +169,34 @@ __device__ __forceinline__ void from_state(float &u, float &v, const CoefF &c) {
     if (MODEL == RD_GM) { u += c.u0; v += c.v0; }
 }
 
-// One explicit Euler update of a node given the unscaled 5-point sums
-// lu = (N + S + W + E - 4 c) for both species (of the state registers;
-// the Laplacian of a deviation equals that of the field).
+// One explicit Euler update of a node given the neighbour sums
+// su = (N + S) + (W + E) of both species (of the state registers; the
+// Laplacian of a deviation equals that of the field):
+//   FHN: u' = u + cu (su - 4u) + k1 (u - u^3 - v),   v' = be v + k2 u + cv sv
+// (= v + dt (Dv Lap v + eps (u - a v)) with the folded weight be).
 template <int MODEL>
-__device__ __forceinline__ void euler_cell(float u, float v, float lu, float lv, const CoefF &c, float &un,
+__device__ __forceinline__ void euler_cell(float u, float v, float su, float sv, const CoefF &c, float &un,
                                            float &vn) {
     if (MODEL == RD_FHN) {
-        // u + dt (Du Lap u + u - u^3 - v),  v + dt (Dv Lap v + eps (u - a v))
         float ru = fmaf(-u * u, u, u - v);
-        un = fmaf(c.cu, lu, fmaf(c.k1, ru, u));
-        vn = fmaf(c.cv, lv, fmaf(c.k2, fmaf(-c.k3, v, u), v));
+        un = fmaf(c.cu, fmaf(-4.f, u, su), fmaf(c.k1, ru, u));
+        vn = fmaf(c.be, v, fmaf(c.k2, u, c.cv * sv));
     } else if (MODEL == RD_GM) {
         // Deviation form, exact in real arithmetic for U = u0 + a, V = v0 + b:
         //   U^2/V - mu U = U (a - mu b + e0) / V,   U^2 - V = a (2 u0 + a) - b + e1
         // so the increments carry the relative precision of the deviation
-        // rather than of the equilibrium value.
+        // rather than of the equilibrium value:
+        //   a' = a + cu (sa - 4a) + k2 U (a - mu b + e0) / V
+        //   b' = be b + cv sb + k2 a (a + 2 u0) + k2 e1
         const float a = u, b = v;
         float U = a + c.u0, V = b + c.v0;
         float t = fmaf(-c.k3, b, a + c.e0);
         float f = __fdividef(U * t, V);
-        float g = fmaf(a, a + c.tu0, c.e1 - b);
-        un = fmaf(c.cu, lu, fmaf(c.k2, f, a));
-        vn = fmaf(c.cv, lv, fmaf(c.k2, g, b));
+        un = fmaf(c.cu, fmaf(-4.f, a, su), fmaf(c.k2, f, a));
+        vn = fmaf(c.be, b, fmaf(c.k2 * a, a + c.tu0, fmaf(c.cv, sv, c.k2e1)));
     } else {
-        un = fmaf(c.cu, lu, u);
-        vn = fmaf(c.cv, lv, v);
+        un = fmaf(c.cu, fmaf(-4.f, u, su), u);
+        vn = fmaf(c.cv, fmaf(-4.f, v, sv), v);
     }
 }
 
@@ -205,9 +222,9 @@ __device__ __forceinline__ void tile_step(const float *hb, int tx, int ty, float
         for (int c = 0; c < TX; ++c) {
             float Wu = c > 0 ? cu_[c - 1] : wu, Eu = c < TX - 1 ? cu_[c + 1] : eu;
             float Wv = c > 0 ? cv_[c - 1] : wv, Ev = c < TX - 1 ? cv_[c + 1] : ev;
-            float lu = fmaf(-4.f, cu_[c], (pu[c] + su[c]) + (Wu + Eu));
-            float lv = fmaf(-4.f, cv_[c], (pv[c] + sv[c]) + (Wv + Ev));
-            euler_cell<MODEL>(cu_[c], cv_[c], lu, lv, cf, u[i][c], v[i][c]);
+            float nu = (pu[c] + su[c]) + (Wu + Eu);
+            float nv = (pv[c] + sv[c]) + (Wv + Ev);
+            euler_cell<MODEL>(cu_[c], cv_[c], nu, nv, cf, u[i][c], v[i][c]);
         }
 #pragma unroll
         for (int c = 0; c < TX; ++c) { pu[c] = cu_[c]; pv[c] = cv_[c]; }
@@ -347,26 +364,25 @@ __device__ __forceinline__ float2 from_state2(float2 w, const CoefF &c) {
 }
 
 // One Euler update of a node: C = (u, v) (or the GM deviation (a, b)),
-// L = packed unscaled 5-point sums of both species.
+// S = packed neighbour sums of both species.  Per species it performs the
+// operations of euler_cell in the same order.
 template <int MODEL>
-__device__ __forceinline__ float2 euler2(float2 C, float2 L, const CoefF &c) {
-    const float2 cd = make_float2(c.cu, c.cv);
+__device__ __forceinline__ float2 euler2(float2 C, float2 S, const CoefF &c) {
     if (MODEL == RD_FHN) {
-        // (u - u^3 - v, u - a v) = (-u^2, -a) * (u, v) + (u - v, u)
         const float u = C.x, v = C.y;
-        float2 R = __ffma2_rn(make_float2(-u * u, -c.k3), C, make_float2(u - v, u));
-        float2 in = __ffma2_rn(make_float2(c.k1, c.k2), R, C);
-        return __ffma2_rn(cd, L, in);
+        float ru = fmaf(-u * u, u, u - v);
+        return make_float2(fmaf(c.cu, fmaf(-4.f, u, S.x), fmaf(c.k1, ru, u)),
+                           fmaf(c.be, v, fmaf(c.k2, u, c.cv * S.y)));
     } else if (MODEL == RD_GM) {
         const float a = C.x, b = C.y;
-        float2 UV = __fadd2_rn(C, make_float2(c.u0, c.v0));
+        float U = a + c.u0, V = b + c.v0;
         float t = fmaf(-c.k3, b, a + c.e0);
-        float f = __fdividef(UV.x * t, UV.y);
-        float g = fmaf(a, a + c.tu0, c.e1 - b);
-        float2 in = __ffma2_rn(make_float2(c.k2, c.k2), make_float2(f, g), C);
-        return __ffma2_rn(cd, L, in);
+        float f = __fdividef(U * t, V);
+        return make_float2(fmaf(c.cu, fmaf(-4.f, a, S.x), fmaf(c.k2, f, a)),
+                           fmaf(c.be, b, fmaf(c.k2 * a, a + c.tu0, fmaf(c.cv, S.y, c.k2e1))));
     } else {
-        return __ffma2_rn(cd, L, C);
+        const float2 L = __ffma2_rn(make_float2(-4.f, -4.f), C, S);
+        return __ffma2_rn(make_float2(c.cu, c.cv), L, C);
     }
 }
 
@@ -381,7 +397,6 @@ __device__ __forceinline__ void halo2_put(float2 *hb, int tx, int ty, const floa
 template <int MODEL, int G, int TY, int TX>
 __device__ __forceinline__ void tile2_step(const float2 *hb, int tx, int ty, float2 (&w)[TY][TX], const CoefF &cf) {
     constexpr int NX = Tiling2<G, TY, TX>::NX, NY = Tiling2<G, TY, TX>::NY;
-    const float2 m4 = make_float2(-4.f, -4.f);
     float2 pw[TX];
     if (ty > 0) {
         ld_row2<TX>(hb + (1 * NY + ty - 1) * G + tx * TX, pw);
@@ -415,9 +430,8 @@ __device__ __forceinline__ void tile2_step(const float2 *hb, int tx, int ty, flo
         for (int c = 0; c < TX; ++c) {
             float2 Wn = c > 0 ? cw[c - 1] : west;
             float2 En = c < TX - 1 ? cw[c + 1] : east;
-            float2 L = __fadd2_rn(__fadd2_rn(pw[c], sw[c]), __fadd2_rn(Wn, En));
-            L = __ffma2_rn(m4, cw[c], L);
-            w[i][c] = euler2<MODEL>(cw[c], L, cf);
+            float2 S = __fadd2_rn(__fadd2_rn(pw[c], sw[c]), __fadd2_rn(Wn, En));
+            w[i][c] = euler2<MODEL>(cw[c], S, cf);
         }
 #pragma unroll
         for (int c = 0; c < TX; ++c) pw[c] = cw[c];
