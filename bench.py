@@ -314,10 +314,13 @@ def run_ours(args, rank, world, local_rank):
     achieved = inst / (k_avg_ms * 1e-3) / 1e12                          # T FP32 instructions / s
     peak_alu = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12   # FP32 lanes x clock
     cil_avg = sum(cil_ms) / len(cil_ms)
-    kname = "rd_batch_kernel (persistent)" if multi else (
-        "rd_resident_%s_kernel<%s,%d> variant %s" % ("scalar" if variant in (0, 2) else "packed",
-                                                      {0: "FHN", 1: "GM", 2: "DIFF"}[groups[0].model],
-                                                      groups[0].G, variant))
+    if multi:
+        kname = "rd_batch_kernel (persistent)"
+    else:
+        pk_, ty_, tx_ = p.variant_shape(groups[0].G, variant)
+        kname = "%s<%s,%d,%dx%d> variant %s" % ("rd_resident_kernel" if pk_ else "rd_resident_scalar_kernel",
+                                               {0: "FHN", 1: "GM", 2: "DIFF"}[groups[0].model],
+                                               groups[0].G, ty_, tx_, variant)
     workload = {"c2": "c2: FHN 64x64, 2 sets x 64 realisations, 10^4 Euler steps, u-only d=4096, M=16, "
                       "b=1.3, 200 resamples",
                 "c4": "c4: 64 parameter vectors x 128 realisations, FHN+GM at 64^2 (10^4 steps) and 128^2 "

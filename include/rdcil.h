@@ -161,6 +161,10 @@ rd_status rd_integrate_f64(rd_handle *h, double *d_fields64, double *d_tmp64,
  * fields; the choice (per model and G, process-wide) only affects speed.
  * rd_n_variants: number of variants (indices 0..n-1, 0 = default).
  * rd_set_variant / rd_get_variant: choose / read the variant of (model, G).
+ * rd_variant_shape: the tile shape of variant `variant` at grid side G
+ *   (32, 64 or 128): shape = host int32[3] receiving {packed (1 = float2
+ *   (u, v) tiles, 0 = separate u and v tiles), TY, TX}.  RD_ERR_INVALID_ARG
+ *   for an unknown G or variant or a null shape.
  * rd_autotune: time every variant on the largest group of each (model, G)
  *   class present in h for `steps` Euler steps, keep the fastest, then
  *   re-initialise d_fields (rd_reinit).  Synchronous.  chosen (nullable,
@@ -168,6 +172,7 @@ rd_status rd_integrate_f64(rd_handle *h, double *d_fields64, double *d_tmp64,
 int32_t rd_n_variants(void);
 rd_status rd_set_variant(int32_t model, int32_t G, int32_t variant);
 int32_t rd_get_variant(int32_t model, int32_t G);
+rd_status rd_variant_shape(int32_t G, int32_t variant, int32_t *shape);
 rd_status rd_autotune(rd_handle *h, float *d_fields, int64_t steps, void *stream, int32_t *chosen);
 
 /* rd_sync_status — synchronise `stream`, read and clear the handle's device

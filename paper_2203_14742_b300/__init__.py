@@ -60,6 +60,7 @@ _SIGS = {
     "rd_set_schedule": (_i32, [_vp, _i32]),
     "rd_set_variant": (_i32, [_i32, _i32, _i32]),
     "rd_get_variant": (_i32, [_i32, _i32]),
+    "rd_variant_shape": (_i32, [_i32, _i32, C.POINTER(_i32)]),
     "rd_autotune": (_i32, [_vp, _vp, _i64, _vp, C.POINTER(_i32)]),
     "rd_adjoint": (_i32, [_vp, _i32, _vp, _i32, C.POINTER(_i32), _i64, C.POINTER(_i32), _i64, _vp,
                           _i32, _dbl, _vp, _vp, _vp, _vp]),
@@ -238,6 +239,13 @@ class Simulation:
 # correlation integral
 # ---------------------------------------------------------------------------
 _work_cache = {}
+
+
+def variant_shape(G, variant):
+    """(packed, TY, TX) of stepper tile variant `variant` at grid side G."""
+    sh = (_i32 * 3)()
+    _check("rd_variant_shape", lib().rd_variant_shape(int(G), int(variant), sh))
+    return int(sh[0]), int(sh[1]), int(sh[2])
 
 
 def _workspace(n1, n2, d, device):

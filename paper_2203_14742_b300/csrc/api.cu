@@ -200,6 +200,15 @@ extern "C" uint64_t rd_kernel_launches(void) { return g_launches.load(); }
 // ---------------------------------------------------------------------------
 extern "C" int32_t rd_n_variants(void) { return n_variants(); }
 
+extern "C" rd_status rd_variant_shape(int32_t G, int32_t variant, int32_t *shape) {
+    int pk, ty, tx;
+    if (!shape || !variant_shape(G, variant, &pk, &ty, &tx)) return RD_ERR_INVALID_ARG;
+    shape[0] = pk;
+    shape[1] = ty;
+    shape[2] = tx;
+    return RD_OK;
+}
+
 extern "C" rd_status rd_set_variant(int32_t model, int32_t G, int32_t variant) {
     if (model < 0 || model > 2 || (G != 32 && G != 64 && G != 128) || variant < 0 || variant >= n_variants())
         return RD_ERR_INVALID_ARG;

@@ -12,7 +12,8 @@
 //                            registers as TYxTX tiles per thread for the whole
 //                            run; north/south tile edges exchanged through a
 //                            double-buffered shared-memory ring (one barrier
-//                            per step), east/west edges through warp shuffles;
+//                            per step), east/west edges through warp shuffles
+//                            (serpentine column order, see tile.cuh);
 //                            FP64 residual reduced with warp shuffles at exit
 //   rd_reference_step_kernel one cell per thread, one step and one realisation
 //                            per launch (the plain path for comparison)
@@ -221,16 +222,17 @@ __device__ __forceinline__ void run_scalar(float *__restrict__ fields, int64_t f
     const int tx = tid % NX, ty = tid / NX;
     float *base = fields + field_offset + (int64_t)r * 2 * G * G;
     float u[TY][TX], v[TY][TX];
-    tile_load<G, TY, TX>(base, tx, ty, u, v);
+    tile_load_s<G, TY, TX>(base, tx, ty, u, v);
     tile_to_state<MODEL, TY, TX>(u, v, cf);
+    const int src = serp_src<NX>(tx);
     for (int64_t n = 0; n < steps; ++n) {
         float *hb = sm + (int)(n & 1) * (T::HALO_FLOATS / 2);
         halo_put<G, TY, TX>(hb, tx, ty, u, v);
         __syncthreads();
-        tile_step<MODEL, G, TY, TX>(hb, tx, ty, u, v, cf);
+        tile_step_s<MODEL, G, TY, TX>(hb, tx, ty, src, u, v, cf);
     }
     tile_from_state<MODEL, TY, TX>(u, v, cf);
-    tile_store<G, TY, TX>(base, tx, ty, u, v);
+    tile_store_s<G, TY, TX>(base, tx, ty, u, v);
     residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, sm);
 }
 
@@ -355,6 +357,14 @@ rd_status launch_integrate_variant(const GroupDev &g, float *fields, int64_t ste
 void set_variant_choice(int model, int G, int vi) { g_choice[model][gidx(G)] = vi; }
 int get_variant_choice(int model, int G) { return g_choice[model][gidx(G)]; }
 int n_variants() { return NVAR; }
+bool variant_shape(int G, int vi, int *packed, int *TY, int *TX) {
+    if (vi < 0 || vi >= NVAR || (G != 32 && G != 64 && G != 128)) return false;
+    const Variant V = G == 32 ? VAR32[vi] : (G == 64 ? VAR64[vi] : VAR128[vi]);
+    *packed = V.packed;
+    *TY = V.TY;
+    *TX = V.TX;
+    return true;
+}
 
 // traj holds, per realisation, `steps` states of 2*G*G floats back to back.
 rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int64_t steps, cudaStream_t s) {

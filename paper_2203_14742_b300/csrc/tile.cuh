@@ -200,37 +200,6 @@ __device__ __forceinline__ void euler_cell(float u, float v, float su, float sv,
     }
 }
 
-// One explicit Euler step of a whole register tile (reads halo buffer hb
-// after the barrier that follows halo_put).
-template <int MODEL, int G, int TY, int TX>
-__device__ __forceinline__ void tile_step(const float *hb, int tx, int ty, float (&u)[TY][TX], float (&v)[TY][TX],
-                                          const CoefF &cf) {
-    constexpr int NX = Tiling<G, TY, TX>::NX;
-    float pu[TX], pv[TX];
-    halo_north<G, TY, TX>(hb, tx, ty, u, v, pu, pv);
-#pragma unroll
-    for (int i = 0; i < TY; ++i) {
-        float su[TX], sv[TX];
-        row_south<G, TY, TX>(hb, tx, ty, i, u, v, su, sv);
-        float wu, eu, wv, ev;
-        row_west_east<NX>(tx, u[i][0], u[i][TX - 1], wu, eu);
-        row_west_east<NX>(tx, v[i][0], v[i][TX - 1], wv, ev);
-        float cu_[TX], cv_[TX];
-#pragma unroll
-        for (int c = 0; c < TX; ++c) { cu_[c] = u[i][c]; cv_[c] = v[i][c]; }
-#pragma unroll
-        for (int c = 0; c < TX; ++c) {
-            float Wu = c > 0 ? cu_[c - 1] : wu, Eu = c < TX - 1 ? cu_[c + 1] : eu;
-            float Wv = c > 0 ? cv_[c - 1] : wv, Ev = c < TX - 1 ? cv_[c + 1] : ev;
-            float nu = (pu[c] + su[c]) + (Wu + Eu);
-            float nv = (pv[c] + sv[c]) + (Wv + Ev);
-            euler_cell<MODEL>(cu_[c], cv_[c], nu, nv, cf, u[i][c], v[i][c]);
-        }
-#pragma unroll
-        for (int c = 0; c < TX; ++c) { pu[c] = cu_[c]; pv[c] = cv_[c]; }
-    }
-}
-
 template <int MODEL, int TY, int TX>
 __device__ __forceinline__ void tile_to_state(float (&u)[TY][TX], float (&v)[TY][TX], const CoefF &c) {
 #pragma unroll
@@ -264,6 +233,92 @@ __device__ __forceinline__ void tile_store(float *base, int tx, int ty, const fl
     for (int i = 0; i < TY; ++i) {
         st_row<TX>(base + (y0 + i) * G + x0, u[i]);
         st_row<TX>(base + G * G + (y0 + i) * G + x0, v[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Serpentine tiles for the forward stepper.  Lanes with even tx hold their
+// tile columns in reverse order (register c = column x0 + TX-1-c), lanes
+// with odd tx in natural order.  Then across the boundary between tx = 2k
+// and 2k+1 both lanes hold the boundary column in register 0, and across
+// the boundary between 2k+1 and 2k+2 both hold it in register TX-1: one
+// xor-shuffle of register 0 and one indexed shuffle of register TX-1 (the
+// source lane fixed for the whole run) give every lane both outside
+// neighbours.  A lane at the domain edge names itself as the source and so
+// receives its own edge column, which is the mirror ghost.  The Laplacian
+// needs only W + E, which does not depend on the column order (addition
+// is commutative), so every node's arithmetic is the same as in the
+// natural-order tiles of the packed and adjoint kernels.
+// Vertically adjacent tiles share tx and so share the column order, which
+// keeps the north/south halo ring in register order.
+// ---------------------------------------------------------------------------
+template <int NX>
+__device__ __forceinline__ int serp_src(int tx) {
+    const int lane = threadIdx.x & 31;
+    if (tx & 1) return tx == NX - 1 ? lane : lane + 1;
+    return tx == 0 ? lane : lane - 1;
+}
+
+template <int G, int TY, int TX>
+__device__ __forceinline__ void tile_load_s(const float *base, int tx, int ty, float (&u)[TY][TX],
+                                            float (&v)[TY][TX]) {
+    float a[TY][TX], b[TY][TX];
+    tile_load<G, TY, TX>(base, tx, ty, a, b);
+    const bool rev = !(tx & 1);
+#pragma unroll
+    for (int i = 0; i < TY; ++i)
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            u[i][c] = rev ? a[i][TX - 1 - c] : a[i][c];
+            v[i][c] = rev ? b[i][TX - 1 - c] : b[i][c];
+        }
+}
+
+template <int G, int TY, int TX>
+__device__ __forceinline__ void tile_store_s(float *base, int tx, int ty, const float (&u)[TY][TX],
+                                             const float (&v)[TY][TX]) {
+    float a[TY][TX], b[TY][TX];
+    const bool rev = !(tx & 1);
+#pragma unroll
+    for (int i = 0; i < TY; ++i)
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            a[i][c] = rev ? u[i][TX - 1 - c] : u[i][c];
+            b[i][c] = rev ? v[i][TX - 1 - c] : v[i][c];
+        }
+    tile_store<G, TY, TX>(base, tx, ty, a, b);
+}
+
+// One Euler step of a serpentine tile (reads halo buffer hb after the
+// barrier that follows halo_put; mirror ghosts at the top/bottom edge).  (A second, test-free copy of this body for the
+// warps away from the top and bottom edges measured 29 % slower on FHN
+// 64x64: two unrolled bodies in one loop cost more than the tests.)
+template <int MODEL, int G, int TY, int TX>
+__device__ __forceinline__ void tile_step_s(const float *hb, int tx, int ty, int src, float (&u)[TY][TX],
+                                            float (&v)[TY][TX], const CoefF &cf) {
+    float pu[TX], pv[TX];
+    halo_north<G, TY, TX>(hb, tx, ty, u, v, pu, pv);
+#pragma unroll
+    for (int i = 0; i < TY; ++i) {
+        float su[TX], sv[TX];
+        row_south<G, TY, TX>(hb, tx, ty, i, u, v, su, sv);
+        const float xu0 = __shfl_xor_sync(0xffffffffu, u[i][0], 1);
+        const float xv0 = __shfl_xor_sync(0xffffffffu, v[i][0], 1);
+        const float xu1 = __shfl_sync(0xffffffffu, u[i][TX - 1], src);
+        const float xv1 = __shfl_sync(0xffffffffu, v[i][TX - 1], src);
+        float cu_[TX], cv_[TX];
+#pragma unroll
+        for (int c = 0; c < TX; ++c) { cu_[c] = u[i][c]; cv_[c] = v[i][c]; }
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            float Lu = c > 0 ? cu_[c - 1] : xu0, Ru = c < TX - 1 ? cu_[c + 1] : xu1;
+            float Lv = c > 0 ? cv_[c - 1] : xv0, Rv = c < TX - 1 ? cv_[c + 1] : xv1;
+            float nu = (pu[c] + su[c]) + (Lu + Ru);
+            float nv = (pv[c] + sv[c]) + (Lv + Rv);
+            euler_cell<MODEL>(cu_[c], cv_[c], nu, nv, cf, u[i][c], v[i][c]);
+        }
+#pragma unroll
+        for (int c = 0; c < TX; ++c) { pu[c] = cu_[c]; pv[c] = cv_[c]; }
     }
 }
 

@@ -80,3 +80,20 @@ def test_argument_errors_before_any_launch(libpath):
     assert L.cil_features(w, 8, 4, w, 8, 4, 8, None, 1.0, 8, w, w, w, None, None, w, 1 << 20, None) == 1
     # synlik: T < 2
     assert L.synlik_stats(w, 4, 4, 8, 1, 0, 1, None, w, w, w, w, w, w, w, None) == 1
+
+
+def test_variant_shapes_are_valid_tilings(libpath):
+    """Every stepper tile variant tiles its grid with whole warps, and keeps
+    a tile row inside one warp (the east/west shuffles assume it)."""
+    import paper_2203_14742_b300 as p
+    for G in (32, 64, 128):
+        for v in range(p.lib().rd_n_variants()):
+            packed, TY, TX = p.variant_shape(G, v)
+            assert packed in (0, 1) and G % TY == 0 and G % TX == 0
+            NX, NY = G // TX, G // TY
+            assert NX <= 32 and NX & (NX - 1) == 0 and NX % 2 == 0
+            assert (NX * NY) % 32 == 0 and NX * NY <= 1024
+        assert p.variant_shape(G, 0)[0] == 0
+    sh = (ctypes.c_int32 * 3)()
+    assert p.lib().rd_variant_shape(48, 0, sh) == 1
+    assert p.lib().rd_variant_shape(64, p.lib().rd_n_variants(), sh) == 1
