@@ -29,13 +29,13 @@
 
 namespace rdcil {
 
-rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2, int64_t dp, int64_t kc,
-                         int64_t nchunk, float *Ppart, uint32_t *status, cudaStream_t s);
+rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2, int64_t dp, int64_t S,
+                         int64_t cs, float *Ppart, uint32_t *status, cudaStream_t s);
 
-static constexpr int KCHUNK_MAX = 512;   // longest split-K chunk (bounds FP32 accumulation error)
+static constexpr int KSTEPS_MAX = 4;     // longest accumulator chunk, in K steps of 64 (bounds FP32 error)
 static constexpr int PAD = 64;           // padded pattern length granularity
 static constexpr int TILE = 128;         // Gram output tile (pairs per side)
-static constexpr int MAX_CHUNKS = 64;    // at most this many split-K partials per pair
+static constexpr int N_SM = 148;
 
 static inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -59,13 +59,15 @@ enum : int {
 };
 
 struct CilWork {
-    int64_t n1, n2, d, dp, kc, nchunk;
+    int64_t n1, n2, d, dp;
+    int64_t ntj, S, cs;     // Gram: tiles along set 2, K segments per tile, K steps per chunk
+    int64_t nchunk;         // upper bound on the chunk partials summed per pair
     float *centre;          // [dp]
     __nv_bfloat16 *hi;      // [(n1+n2)][dp]
     __nv_bfloat16 *lo;      // [(n1+n2)][dp]
     double *N, *H, *L, *E;  // [(n1+n2)]
     float *Hf, *Lf, *Ef;    // [(n1+n2)] the same bounds as FP32, rounded up
-    float *Ppart;           // [nchunk][n1][n2]
+    float *Ppart;           // [S][hi, lo][n1][n2] compensated segment sums
     float *lo32, *hi32;     // [n1*n2] tier-1 interval of d2 (rounded outwards)
     double *lo2, *hi2;      // [n1*n2] tier-2 interval (valid where flag >= 1)
     double *ex;             // [n1*n2] canonical d2 (valid where flag == 2)
@@ -83,15 +85,23 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     CilWork w{};
     w.n1 = n1; w.n2 = n2; w.d = d;
     w.dp = round_up(d, PAD);
-    // split-K chunk: enough CTAs to cover the GPU twice, at most KCHUNK_MAX
-    int64_t tiles = ((n1 + TILE - 1) / TILE) * ((n2 + TILE - 1) / TILE);
-    int64_t want = (2 * 148 + tiles - 1) / tiles;
-    int64_t kc = round_up((w.dp + want - 1) / want, PAD);
-    if (kc > KCHUNK_MAX) kc = KCHUNK_MAX;
-    int64_t kmin = round_up((w.dp + MAX_CHUNKS - 1) / MAX_CHUNKS, PAD);
-    if (kc < kmin) kc = kmin;
-    w.kc = kc;
-    w.nchunk = (w.dp + kc - 1) / kc;
+    // Gram work split: one CTA per (128 x 128 output tile, K segment), with
+    // enough segments to give every SM a CTA (at most 32 for a single tile,
+    // which keeps the partials of small problems small).  Accumulator
+    // chunks of one K step (64 columns) while the whole product is small,
+    // else of up to KSTEPS_MAX steps: the chunk length sets the FP32
+    // accumulation bound, and the drain of a chunk must keep pace with the
+    // tensor core.
+    const int64_t nti = (n1 + TILE - 1) / TILE, ntj = (n2 + TILE - 1) / TILE, tiles = nti * ntj;
+    const int64_t n64 = w.dp / PAD;
+    int64_t S = tiles == 1 ? 32 : N_SM / tiles;
+    if (S < 1) S = 1;
+    if (S > n64) S = n64;
+    const int64_t seg_max = (n64 + S - 1) / S;
+    w.ntj = ntj;
+    w.S = S;
+    w.cs = tiles * n64 <= 4096 ? 1 : (seg_max < KSTEPS_MAX ? seg_max : KSTEPS_MAX);
+    w.nchunk = S * ((seg_max + w.cs - 1) / w.cs);
     int64_t n = n1 + n2;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -110,7 +120,7 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     w.Lf = (float *)take(sizeof(float) * n);
     w.Ef = (float *)take(sizeof(float) * n);
     const int64_t np = n1 * n2;
-    w.Ppart = (float *)take(sizeof(float) * w.nchunk * np);
+    w.Ppart = (float *)take(sizeof(float) * S * 2 * np);
     w.lo32 = (float *)take(sizeof(float) * np);
     w.hi32 = (float *)take(sizeof(float) * np);
     w.lo2 = (double *)take(sizeof(double) * np);
@@ -266,7 +276,7 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
 }
 
 // ---------------------------------------------------------------------------
-// 2. Gram product: tensor cores (gram_tc.cu), split-K chunks of kc.
+// 2. Gram product: tensor cores (gram_tc.cu), K segments of compensated chunks.
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
@@ -285,8 +295,12 @@ __global__ void d2_bound_kernel(CilWork w, float gam) {
     if (q < np) {
         const int64_t i = q / w.n2, j = q - i * w.n2;
         const int64_t a = i, bb = w.n1 + j;
+        // segment sums (hi, lo) of this pair, in segment order
         float ph = 0.f, pl = 0.f;
-        for (int64_t c = 0; c < w.nchunk; ++c) two_sum_acc(ph, pl, w.Ppart[c * np + q]);
+        for (int64_t sg = 0; sg < w.S; ++sg) {
+            two_sum_acc(ph, pl, w.Ppart[(2 * sg) * np + q]);
+            pl += w.Ppart[(2 * sg + 1) * np + q];
+        }
         const double P = (double)ph + (double)pl;
         const double Ni = w.N[a], Nj = w.N[bb];
         const double A = (Ni + Nj) - 2.0 * P;
@@ -622,14 +636,17 @@ extern "C" rd_status cil_workspace_size(int64_t n1, int64_t n2, int64_t d, size_
     return RD_OK;
 }
 
-// Tensor-core accumulation model (tier 1): per chunk 3*kc/16 instructions
-// add into the FP32 accumulator; each adds 16 exact bf16 products and the
-// accumulator with at most 17 roundings of 2^-23 relative to the magnitudes
-// involved.  The chunk partials are summed by a compensated FP32 sum
-// ((nchunk + 4) 2^-45 of the magnitudes).
+// Tensor-core accumulation model (tier 1): per chunk of cs K steps,
+// 3*64*cs/16 instructions add into the FP32 accumulator; each adds 16 exact
+// bf16 products and the accumulator with at most 17 roundings of 2^-23
+// relative to the magnitudes involved.  The chunk partials are summed with
+// TwoSum into an FP32 hi/lo pair, in the kernel within a segment and then
+// across segments: for n terms that errs by at most about (n u)^2 of their
+// magnitudes (u = 2^-24), taken here as (nchunk + S + 4)^2 2^-47.
 static float gram_gamma(const CilWork &w) {
-    const double g = (3.0 * (double)w.kc / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
-                     (double)(w.nchunk + 4) * 2.842170943040401e-14;
+    const double n = (double)(w.nchunk + w.S + 4);
+    const double g = (3.0 * 64.0 * (double)w.cs / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
+                     n * n * 7.105427357601002e-15;
     return (float)(g * (1.0 + 1e-6));
 }
 
@@ -642,7 +659,7 @@ static rd_status tier1(const CilWork &w, const float *X1, int64_t ld1, const flo
     pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(X1, ld1, n1, X2, ld2, w.d, w.dp, w.centre, w.hi, w.lo, w.N,
                                                     w.H, w.L, w.E, w.Hf, w.Lf, w.Ef);
     note_launch();
-    rd_status st = launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.kc, w.nchunk, w.Ppart,
+    rd_status st = launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.S, w.cs, w.Ppart,
                                   reinterpret_cast<uint32_t *>(&w.scal[SC_TIMEOUT]), s);
     if (st) return st;
     d2_bound_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(w, gram_gamma(w));
@@ -738,7 +755,7 @@ extern "C" rd_status cil_gram_only(int64_t n1, int64_t n2, int64_t d, void *d_wo
     CilWork w = layout(n1, n2, d, d_work);
     if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
     if (flops) *flops = 3.0 * 2.0 * (double)n1 * (double)n2 * (double)w.dp;
-    return launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.kc, w.nchunk, w.Ppart,
+    return launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.S, w.cs, w.Ppart,
                           reinterpret_cast<uint32_t *>(&w.scal[SC_TIMEOUT]), (cudaStream_t)stream);
 }
 

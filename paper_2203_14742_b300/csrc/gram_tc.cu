@@ -1,16 +1,23 @@
 // Tensor-core Gram product for the correlation integral (the one dense
-// contraction of the path): P_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j over one
-// K-chunk, bf16 operands, FP32 accumulation in tensor memory.
+// contraction of the path): P_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j, bf16
+// operands, FP32 accumulation in tensor memory, accumulated over K chunks
+// whose partials are summed with compensation.
 //
 // Blackwell (sm_100 family) structure, written with inline PTX:
 //   * TMA (cp.async.bulk.tensor) loads 128-row x 64-column bf16 tiles of the
 //     hi and lo parts of both pattern sets into 128-byte-swizzled shared
 //     memory, three stages deep, completion tracked by mbarriers;
 //   * one elected thread issues tcgen05.mma (M = N = 128, K = 16, kind::f16
-//     with bf16 inputs, FP32 accumulator in TMEM) and frees each stage with
-//     tcgen05.commit;
-//   * four warps read the 128 x 128 FP32 accumulator back with tcgen05.ld
-//     (warp w owns TMEM lanes 32w..32w+31) and store the chunk partials.
+//     with bf16 inputs, FP32 accumulator in TMEM) into two alternating TMEM
+//     accumulators, one K chunk each (the chunk length bounds the FP32
+//     accumulation error), and frees each stage with tcgen05.commit;
+//   * four drain warps read each finished chunk back with tcgen05.ld and add
+//     it into a compensated (TwoSum hi + lo) FP32 sum that stays in TMEM
+//     (tcgen05.st), while the tensor core fills the other accumulator;
+//     after the segment's last chunk they store hi and lo once.
+// One CTA per (output tile, K segment); the segments of all tiles run
+// concurrently and in step along K, so each bf16 tile is fetched from HBM
+// about once and re-read from L2 by the CTAs that share it.
 // Every mbarrier wait is bounded: on timeout the kernel raises ST_TIMEOUT in
 // the status word, skips its epilogue, frees its TMEM and returns.
 #include <cuda.h>
@@ -25,6 +32,7 @@ static constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
 static constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;              // 16 KiB
 static constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;             // A hi, A lo, B hi, B lo
 static constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
+static_assert((2 * TC_STAGES + 4) * 8 + 4 <= 256, "barrier area");
 static constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;                  // bounded spin (~seconds)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -119,37 +127,92 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// grid: (ceil(n2/128), ceil(n1/128), nchunk); block: 128 threads.
-// Rows 0..n1-1 of the hi/lo arrays are set 1, rows n1..n1+n2-1 set 2.
-__global__ void __launch_bounds__(128, 1)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+        "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+        "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+        "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+        "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+        "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One CTA per (output tile t, K segment s): grid = ntiles * S, block = 192
+// threads.  Tile t covers set-1 rows 128*(t / ntj) and set-2 rows
+// 128*(t % ntj) (rows 0..n1-1 of the hi/lo arrays are set 1, rows
+// n1..n1+n2-1 set 2).  Segment s covers the 64-column K steps
+// [s*n64/S, (s+1)*n64/S).
+//   warp 0    TMA producer (one lane)
+//   warp 1    MMA issuer (one lane): K chunks of at most cs steps, each
+//             accumulated from zero into TMEM accumulator (chunk & 1)
+//   warps 2-5 drain: add each finished chunk into a compensated FP32 sum
+//             (TwoSum, hi and lo parts kept in TMEM), and after the last
+//             chunk of the segment store hi and lo of the valid pairs to
+//             Ppart[(s * 2 + {0, 1}) * n1 * n2 + i * n2 + j].
+// TMEM columns: [0,128) and [128,256) accumulators, [256,384) sum hi,
+// [384,512) sum lo; warp w may access TMEM lanes 32 (w % 4) .. +31 (rows).
+__global__ void __launch_bounds__(192, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int n1, int n2,
-               int dp, int kc, float *__restrict__ Ppart, uint32_t *__restrict__ status) {
+               int dp, int ntj, int S, int cs, float *__restrict__ Ppart, uint32_t *__restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + TC_STAGES * TC_STAGE_BYTES);
     uint64_t *empty = full + TC_STAGES;
-    uint64_t *done = empty + TC_STAGES;
-    uint32_t *tslot = (uint32_t *)(done + 1);
+    uint64_t *accf = empty + TC_STAGES;     // [2] chunk accumulated (MMA commit)
+    uint64_t *acce = accf + 2;              // [2] accumulator drained (4 drain warps)
+    uint32_t *tslot = (uint32_t *)(acce + 2);
     __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i0 = blockIdx.y * TC_BM, j0 = blockIdx.x * TC_BN;
-    const int k_begin = blockIdx.z * kc;
-    const int k_end = min(dp, k_begin + kc);
-    const int nk = (k_end - k_begin) / TC_BK;
+    const int t = blockIdx.x / S, sgm = blockIdx.x - (blockIdx.x / S) * S;
+    const int i0 = (t / ntj) * TC_BM, j0 = (t % ntj) * TC_BN;
+    const int n64 = dp / TC_BK;
+    const int k_lo = (int)((int64_t)sgm * n64 / S), k_hi = (int)((int64_t)(sgm + 1) * n64 / S);
+    const int nst = k_hi - k_lo;                           // K steps of this segment (>= 1)
+    const int nch = (nst + cs - 1) / cs;                   // chunks of this segment
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int q = 0; q < TC_STAGES; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
         }
-        mbar_init(done, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&accf[q], 1);
+            mbar_init(&acce[q], 4);
+        }
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(TC_BN)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -160,78 +223,131 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
     int issued = 0;   // stages handed to TMA by the producer
 
     if (threadIdx.x == 0) {
-        // ---- producer: TMA loads ----
-        for (int it = 0; it < nk; ++it) {
-            const int s = it % TC_STAGES;
+        // ---- producer: TMA loads of the whole segment ----
+        for (int it = 0; it < nst; ++it) {
+            const int q = it % TC_STAGES;
             const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u)) { s_fail = 1; break; }
-            uint8_t *st = smem + s * TC_STAGE_BYTES;
-            mbar_expect_tx(&full[s], TC_STAGE_BYTES);
-            const int k = k_begin + it * TC_BK;
-            tma_load_2d(st, &tm_hi, k, i0, &full[s]);
-            tma_load_2d(st + TC_TILE_BYTES, &tm_lo, k, i0, &full[s]);
-            tma_load_2d(st + 2 * TC_TILE_BYTES, &tm_hi, k, n1 + j0, &full[s]);
-            tma_load_2d(st + 3 * TC_TILE_BYTES, &tm_lo, k, n1 + j0, &full[s]);
+            if (!mbar_wait(&empty[q], ph ^ 1u)) { s_fail = 1; break; }
+            uint8_t *st = smem + q * TC_STAGE_BYTES;
+            mbar_expect_tx(&full[q], TC_STAGE_BYTES);
+            const int k = (k_lo + it) * TC_BK;
+            tma_load_2d(st, &tm_hi, k, i0, &full[q]);
+            tma_load_2d(st + TC_TILE_BYTES, &tm_lo, k, i0, &full[q]);
+            tma_load_2d(st + 2 * TC_TILE_BYTES, &tm_hi, k, n1 + j0, &full[q]);
+            tma_load_2d(st + 3 * TC_TILE_BYTES, &tm_lo, k, n1 + j0, &full[q]);
             issued = it + 1;
         }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer ----
         constexpr uint32_t idesc = idesc_bf16_f32(TC_BM, TC_BN);
         bool ok = true;
-        for (int it = 0; it < nk && ok; ++it) {
-            const int s = it % TC_STAGES;
-            const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph)) { s_fail = 1; ok = false; break; }
+        int it = 0;
+        for (int c = 0; c < nch && ok; ++c) {
+            const int buf = c & 1;
+            if (c >= 2 && !mbar_wait(&acce[buf], (uint32_t)((c >> 1) - 1) & 1u)) { s_fail = 1; break; }
             fence_after();
-            const uint32_t base = smem_u32(smem + s * TC_STAGE_BYTES);
+            const uint32_t dacc = tmem + (uint32_t)(buf * TC_BN);
+            const int it_end = min(nst, (c + 1) * cs);
+            for (int first = 1; it < it_end; ++it, first = 0) {
+                const int q = it % TC_STAGES;
+                const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+                if (!mbar_wait(&full[q], ph)) { s_fail = 1; ok = false; break; }
+                fence_after();
+                const uint32_t base = smem_u32(smem + q * TC_STAGE_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                const uint32_t off = kk * 32;   // 16 bf16 = 32 bytes along K inside the swizzle atom
-                const uint64_t ah = smem_desc_sw128(base + off);
-                const uint64_t al = smem_desc_sw128(base + TC_TILE_BYTES + off);
-                const uint64_t bh = smem_desc_sw128(base + 2 * TC_TILE_BYTES + off);
-                const uint64_t bl = smem_desc_sw128(base + 3 * TC_TILE_BYTES + off);
-                mma_bf16(tmem, ah, bh, idesc, (it | kk) ? 1u : 0u);
-                mma_bf16(tmem, ah, bl, idesc, 1u);
-                mma_bf16(tmem, al, bh, idesc, 1u);
+                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                    const uint32_t off = kk * 32;   // 16 bf16 = 32 bytes along K inside the swizzle atom
+                    const uint64_t ah = smem_desc_sw128(base + off);
+                    const uint64_t al = smem_desc_sw128(base + TC_TILE_BYTES + off);
+                    const uint64_t bh = smem_desc_sw128(base + 2 * TC_TILE_BYTES + off);
+                    const uint64_t bl = smem_desc_sw128(base + 3 * TC_TILE_BYTES + off);
+                    mma_bf16(dacc, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
+                    mma_bf16(dacc, ah, bl, idesc, 1u);
+                    mma_bf16(dacc, al, bh, idesc, 1u);
+                }
+                mma_commit(&empty[q]);   // stage free once these MMAs have read it
             }
-            mma_commit(&empty[s]);   // stage free once these MMAs have read it
+            if (ok) mma_commit(&accf[buf]);   // chunk complete in accumulator buf
         }
-        mma_commit(done);            // accumulator complete
+    } else if (warp >= 2) {
+        // ---- drain: compensated sum of the chunk partials ----
+        const int qd = warp & 3;                                   // TMEM lane quarter
+        const uint32_t lrow = (uint32_t)(qd * 32) << 16;
+        const int row = qd * 32 + lane;
+        for (int c = 0; c < nch; ++c) {
+            const int buf = c & 1;
+            const bool got = mbar_wait(&accf[buf], (uint32_t)(c >> 1) & 1u);
+            // warp-uniform: tcgen05.ld/st below are warp-collective
+            if (!__all_sync(0xffffffffu, got)) { s_fail = 1; break; }
+            fence_after();
+            const bool last = (c == nch - 1);
+            const int64_t np = (int64_t)n1 * n2;
+            const int i = i0 + row;
+            float *out_h = Ppart + (int64_t)(sgm * 2) * np + (int64_t)i * n2 + j0;
+            float *out_l = out_h + np;
+#pragma unroll 1
+            for (int cb = 0; cb < TC_BN; cb += 32) {
+                float a[32], h[32], l[32];
+                tmem_ld32(tmem + lrow + (uint32_t)(buf * TC_BN + cb), a);
+                if (c == 0) {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) { h[k] = a[k]; l[k] = 0.f; }
+                } else {
+                    tmem_ld32(tmem + lrow + (uint32_t)(2 * TC_BN + cb), h);
+                    tmem_ld32(tmem + lrow + (uint32_t)(3 * TC_BN + cb), l);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const float sum = h[k] + a[k];
+                        const float bb = sum - h[k];
+                        const float e = (h[k] - (sum - bb)) + (a[k] - bb);
+                        h[k] = sum;
+                        l[k] += e;
+                    }
+                }
+                if (last) {
+                    if (i < n1) {
+                        if ((n2 & 3) == 0 && j0 + cb + 32 <= n2) {
+#pragma unroll
+                            for (int k = 0; k < 32; k += 4) {
+                                *reinterpret_cast<float4 *>(out_h + cb + k) =
+                                    make_float4(h[k], h[k + 1], h[k + 2], h[k + 3]);
+                                *reinterpret_cast<float4 *>(out_l + cb + k) =
+                                    make_float4(l[k], l[k + 1], l[k + 2], l[k + 3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 32; ++k)
+                                if (j0 + cb + k < n2) {
+                                    out_h[cb + k] = h[k];
+                                    out_l[cb + k] = l[k];
+                                }
+                        }
+                    }
+                } else {
+                    tmem_st32(tmem + lrow + (uint32_t)(2 * TC_BN + cb), h);
+                    tmem_st32(tmem + lrow + (uint32_t)(3 * TC_BN + cb), l);
+                }
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);   // accumulator buf may be overwritten
+        }
     }
     __syncwarp();
 
-    // ---- epilogue: TMEM -> registers -> partials ----
-    const bool ok = mbar_wait(done, 0);
-    fence_after();
-    // block-uniform decision: tcgen05.ld below is warp-collective
-    const int good = __syncthreads_and(ok ? 1 : 0) && !s_fail;
-    if (good) {
-        const int i = i0 + warp * 32 + lane;
-        float *out = Ppart + (int64_t)blockIdx.z * n1 * n2;
-#pragma unroll 1
-        for (int c = 0; c < TC_BN; c += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (i < n1) {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int j = j0 + c + q;
-                    if (j < n2) out[(int64_t)i * n2 + j] = v[q];
-                }
-            }
-        }
-    }
-    if (threadIdx.x == 0 && !good) {
+    fence_before();
+    const int bad = __syncthreads_or(s_fail);
+    if (threadIdx.x == 0 && bad) {
         atomicOr(status, (unsigned)ST_TIMEOUT);
         // let the copies already in flight land before the block's shared
         // memory is released (bounded)
         for (int it = 0; it < issued; ++it) mbar_wait(&full[it % TC_STAGES], (uint32_t)(it / TC_STAGES) & 1u);
     }
-    fence_before();
     __syncthreads();
+    fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -264,13 +380,17 @@ static bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t dp)
     return r == CUDA_SUCCESS;
 }
 
-// Preconditions (checked): hi/lo 16-byte aligned, dp a multiple of 64, kc a
-// multiple of 64.
-rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2, int64_t dp, int64_t kc,
-                         int64_t nchunk, float *Ppart, uint32_t *status, cudaStream_t s) {
-    if ((((uintptr_t)hi | (uintptr_t)lo) & 15) || (dp % TC_BK) || (kc % TC_BK) || n1 < 1 || n2 < 1)
+// Preconditions (checked): hi/lo 16-byte aligned, dp a multiple of 64,
+// 1 <= S <= dp / 64, cs >= 1 (K steps of 64 per accumulator chunk).
+// Ppart holds S * 2 * n1 * n2 floats (16-byte aligned).
+rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2, int64_t dp, int64_t S, int64_t cs,
+                         float *Ppart, uint32_t *status, cudaStream_t s) {
+    if ((((uintptr_t)hi | (uintptr_t)lo | (uintptr_t)Ppart) & 15) || (dp % TC_BK) || n1 < 1 || n2 < 1 || S < 1 ||
+        S > dp / TC_BK || cs < 1 || cs > dp / TC_BK)
         return RD_ERR_INVALID_ARG;
     if (n1 + n2 > 0x7FFFFFFF || dp > 0x7FFFFFFF) return RD_ERR_UNSUPPORTED;
+    const int64_t nti = (n1 + TC_BM - 1) / TC_BM, ntj = (n2 + TC_BN - 1) / TC_BN;
+    if (nti * ntj * S > 0x7FFFFFFF) return RD_ERR_UNSUPPORTED;
     CUtensorMap mh, ml;
     if (!make_map(&mh, hi, n1 + n2, dp) || !make_map(&ml, lo, n1 + n2, dp)) return RD_ERR_CUDA;
     static bool attr = false;
@@ -278,8 +398,8 @@ rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2,
         RD_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
         attr = true;
     }
-    dim3 grid((unsigned)((n2 + TC_BN - 1) / TC_BN), (unsigned)((n1 + TC_BM - 1) / TC_BM), (unsigned)nchunk);
-    gram_tc_kernel<<<grid, 128, TC_SMEM, s>>>(mh, ml, (int)n1, (int)n2, (int)dp, (int)kc, Ppart, status);
+    gram_tc_kernel<<<(unsigned)(nti * ntj * S), 192, TC_SMEM, s>>>(mh, ml, (int)n1, (int)n2, (int)dp, (int)ntj,
+                                                                   (int)S, (int)cs, Ppart, status);
     note_launch();
     return cuda_status(cudaGetLastError());
 }
