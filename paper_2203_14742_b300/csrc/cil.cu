@@ -198,13 +198,48 @@ __global__ void centre_kernel(const float *__restrict__ X1, int64_t ld1, int64_t
     // any centre is valid (distances are translation invariant); a good one
     // keeps |x - c| small so the bf16 split loses little.  The mean of up to
     // 16 patterns evenly spread over each set is plenty for that.
+    // (all samples are loaded before they are summed, so the loads overlap)
     const int64_t s1 = n1 < 16 ? n1 : 16, s2 = n2 < 16 ? n2 : 16;
+    float v1[16], v2[16];
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {
+        v1[a] = a < s1 ? X1[(a * n1 / s1) * ld1 + t] : 0.f;
+        v2[a] = a < s2 ? X2[(a * n2 / s2) * ld2 + t] : 0.f;
+    }
     float s = 0.f;
-    for (int64_t a = 0; a < s1; ++a) s += X1[(a * n1 / s1) * ld1 + t];
-    for (int64_t a = 0; a < s2; ++a) s += X2[(a * n2 / s2) * ld2 + t];
+#pragma unroll
+    for (int a = 0; a < 16; ++a) s += v1[a] + v2[a];
     centre[t] = s / (float)(s1 + s2);
 }
 
+// One element of the pack: x - c split into bf16 hi + lo, with the
+// compensated square sum of hi + lo and the bound sums.
+struct PackAcc {
+    float nh = 0.f, nl = 0.f, sH = 0.f, sL = 0.f, sE = 0.f;
+};
+__device__ __forceinline__ void pack_elem(float xv, float cv, __nv_bfloat16 &h, __nv_bfloat16 &l, PackAcc &A) {
+    float xc = xv - cv;
+    // exact rounding error of x - c (TwoSum of x and -c)
+    float bb = xc - xv;
+    float dc = (xv - (xc - bb)) - (cv + bb);
+    h = __float2bfloat16_rn(xc);
+    float hf = __bfloat162float(h);
+    float r = xc - hf;                 // exact
+    l = __float2bfloat16_rn(r);
+    float lf = __bfloat162float(l);
+    float sv = hf + lf;                // exact
+    float p = sv * sv;
+    float pe = fmaf(sv, sv, -p);       // exact error of the square
+    two_sum_acc(A.nh, A.nl, p);
+    A.nl += pe;
+    A.sH = fmaf(hf, hf, A.sH);
+    A.sL = fmaf(lf, lf, A.sL);
+    float e = fabsf(dc) + fabsf(r - lf);   // |(x - c) - (hi + lo)|, bounded
+    A.sE = fmaf(e, e, A.sE);
+}
+
+// One block per pattern; each thread takes groups of 8 elements (float4
+// loads, 16-byte bf16 stores when the pattern row is 16-byte aligned).
 __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n1,
                             const float *__restrict__ X2, int64_t ld2, int64_t d, int64_t dp,
                             const float *__restrict__ centre, __nv_bfloat16 *__restrict__ hi,
@@ -213,35 +248,37 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
                             float *__restrict__ Lf, float *__restrict__ Ef) {
     const int64_t i = blockIdx.x;
     const float *x = i < n1 ? X1 + i * ld1 : X2 + (i - n1) * ld2;
+    const bool vec = ((uintptr_t)x & 15) == 0;
     // N = |hi + lo|^2 to ~2^-44 relative (compensated FP32); H, L, E are
     // upper bounds (plain FP32 sums, inflated below)
-    float nh = 0.f, nl = 0.f, sH = 0.f, sL = 0.f, sE = 0.f;
-    for (int64_t t = threadIdx.x; t < dp; t += blockDim.x) {
-        __nv_bfloat16 h = __float2bfloat16_rn(0.f), l = __float2bfloat16_rn(0.f);
-        if (t < d) {
-            float xv = x[t], cv = centre[t];
-            float xc = xv - cv;
-            // exact rounding error of x - c (TwoSum of x and -c)
-            float bb = xc - xv;
-            float dc = (xv - (xc - bb)) - (cv + bb);
-            h = __float2bfloat16_rn(xc);
-            float hf = __bfloat162float(h);
-            float r = xc - hf;                 // exact
-            l = __float2bfloat16_rn(r);
-            float lf = __bfloat162float(l);
-            float sv = hf + lf;                // exact
-            float p = sv * sv;
-            float pe = fmaf(sv, sv, -p);       // exact error of the square
-            two_sum_acc(nh, nl, p);
-            nl += pe;
-            sH = fmaf(hf, hf, sH);
-            sL = fmaf(lf, lf, sL);
-            float e = fabsf(dc) + fabsf(r - lf);   // |(x - c) - (hi + lo)|, bounded
-            sE = fmaf(e, e, sE);
+    PackAcc A;
+    for (int64_t t0 = (int64_t)threadIdx.x * 8; t0 < dp; t0 += (int64_t)blockDim.x * 8) {
+        __align__(16) __nv_bfloat16 h[8];
+        __align__(16) __nv_bfloat16 l[8];
+        if (vec && t0 + 8 <= d) {
+            const float4 xa = *reinterpret_cast<const float4 *>(x + t0);
+            const float4 xb = *reinterpret_cast<const float4 *>(x + t0 + 4);
+            const float4 ca = *reinterpret_cast<const float4 *>(centre + t0);
+            const float4 cb = *reinterpret_cast<const float4 *>(centre + t0 + 4);
+            pack_elem(xa.x, ca.x, h[0], l[0], A);
+            pack_elem(xa.y, ca.y, h[1], l[1], A);
+            pack_elem(xa.z, ca.z, h[2], l[2], A);
+            pack_elem(xa.w, ca.w, h[3], l[3], A);
+            pack_elem(xb.x, cb.x, h[4], l[4], A);
+            pack_elem(xb.y, cb.y, h[5], l[5], A);
+            pack_elem(xb.z, cb.z, h[6], l[6], A);
+            pack_elem(xb.w, cb.w, h[7], l[7], A);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                h[k] = l[k] = __float2bfloat16_rn(0.f);
+                if (t0 + k < d) pack_elem(x[t0 + k], centre[t0 + k], h[k], l[k], A);
+            }
         }
-        hi[i * dp + t] = h;
-        lo[i * dp + t] = l;
+        *reinterpret_cast<uint4 *>(hi + i * dp + t0) = *reinterpret_cast<const uint4 *>(h);
+        *reinterpret_cast<uint4 *>(lo + i * dp + t0) = *reinterpret_cast<const uint4 *>(l);
     }
+    float nh = A.nh, nl = A.nl, sH = A.sH, sL = A.sL, sE = A.sE;
     __shared__ float red[5][32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
