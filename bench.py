@@ -74,6 +74,9 @@ def parse():
                     help="also time the pass captured in a CUDA graph and replayed")
     ap.add_argument("--gram-large", action="store_true",
                     help="also time the tensor-core Gram on 2 x 1024 patterns of d = 32768")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="also time the adjoint (smoothed-CIL gradient) on the FHN 64x64 adjoint workload "
+                         "(32 realisations, 5000 steps)")
     ap.add_argument("--gram-large-only", action="store_true",
                     help="time only the tensor-core Gram and correlation integral on 2 x 1024 patterns of "
                          "d = 32768 (for profiling); prints that object alone")
@@ -373,6 +376,8 @@ def run_ours(args, rank, world, local_rank):
         out["clocks"] = cs
     if args.gram_large and rank == 0:
         out["gram_large"] = gram_large(p, torch, dev, stream, pk, src)
+    if args.adjoint and rank == 0:
+        out["adjoint"] = adjoint_c5(p, torch, dev, stream)
     return out
 
 
@@ -422,6 +427,43 @@ def gram_large(p, torch, dev, stream, pk, src):
                          "products (3 x 2 n1 n2 d flops), algorithmic = 2 n1 n2 d" % src,
             "cil_ms": t_cil * 1e3, "pair_dists_per_s": n * n / t_cil,
             "rechecked": int(c["n_rechecked"])}
+
+
+def adjoint_c5(p, torch, dev, stream):
+    """Smoothed-CIL gradient (discrete adjoint with sqrt(N) checkpoints) on
+    the FHN 64x64 adjoint workload: 32 realisations (2 x 16), 5000 steps,
+    M = 16 radii from the unperturbed run, tau_k = 0.05 R_k, cotangent 1/M."""
+    cfg = W.config("c5")
+    gd = dict(cfg["groups"][0])
+    sim = p.Simulation([p.Group.from_dict(gd, adjoint=True)], device=dev)
+    f0 = sim.fields.clone()
+    n, G, N = gd["n_real"], gd["G"], gd["n_steps"]
+    sim.integrate()
+    X = sim.fields.view(n, 2 * G * G)[:, :G * G] if gd["species_mask"] == 1 else sim.fields.view(n, 2 * G * G)
+    half = n // 2
+    c = p.cil(X[:half], X[half:], b=cfg["b"], M=cfg["M"])
+    radii = c["radii"].clone()
+    cot = torch.full((cfg["M"],), 1.0 / cfg["M"], dtype=torch.float64, device=dev)
+    s1, s2 = list(range(half)), list(range(half, n))
+    sim.adjoint(0, f0, gd["species_mask"], s1, s2, radii, cfg["tau_frac"], cot)   # warm-up
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        Cv, g = sim.adjoint(0, f0, gd["species_mask"], s1, s2, radii, cfg["tau_frac"], cot)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / reps * 1e-3
+    C = math.ceil(math.sqrt(N))
+    cells = n * G * G * N
+    ckpt = (math.ceil(N / C) * n + C * n) * 2 * G * G * 4
+    return {"workload": "FHN 64x64, 32 realisations, 5000 steps, M=16, tau=0.05 R_k",
+            "ms": t * 1e3, "trajectory_cell_updates_per_s": cells / t,
+            "executed_cell_updates_per_s": 3 * cells / t,
+            "note": "one trajectory = n G^2 N cell-updates; the adjoint executes 3 passes of it (recording "
+                    "forward, segment recompute, reverse)",
+            "checkpoint_bytes": ckpt, "segment": C, "grad": [float(x) for x in g.cpu()]}
 
 
 # ---------------------------------------------------------------------------

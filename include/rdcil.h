@@ -189,6 +189,17 @@ void rd_free(rd_handle *h);
  * this process so far (its own kernels only; memset/memcpy not counted). */
 uint64_t rd_kernel_launches(void);
 
+/* rd_set_spin_limit — testing hook for the failure path (the paper has no
+ * counterpart).  The tensor-core Gram kernel's pipeline waits on its
+ * mbarriers poll at most `polls` times before the kernel gives up, flags a
+ * timeout (cil_features then reports *d_n_rechecked = -2) and returns with
+ * its copies and tensor-core work drained; 0 restores the default (about
+ * 4 million polls, seconds).  A tiny limit makes the waits run out on
+ * purpose, so a test can check that the timeout is reported and that the
+ * context stays usable.  Process-wide; not thread-safe against concurrent
+ * CIL calls. */
+void rd_set_spin_limit(uint32_t polls);
+
 const char *rd_status_str(rd_status s);
 
 /* ------------------------------------------------------------------------

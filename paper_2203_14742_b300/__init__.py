@@ -56,6 +56,7 @@ _SIGS = {
     "synlik_stats": (_i32, [_vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                             _vp, _vp, _vp]),
     "rd_kernel_launches": (_u64, []),
+    "rd_set_spin_limit": (None, [C.c_uint32]),
     "rd_n_variants": (_i32, []),
     "rd_set_schedule": (_i32, [_vp, _i32]),
     "rd_set_variant": (_i32, [_i32, _i32, _i32]),

@@ -195,6 +195,8 @@ void rdcil::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); 
 
 extern "C" uint64_t rd_kernel_launches(void) { return g_launches.load(); }
 
+extern "C" void rd_set_spin_limit(uint32_t polls) { set_gram_spin_limit(polls); }
+
 // ---------------------------------------------------------------------------
 // tile-shape variants and the autotuner
 // ---------------------------------------------------------------------------

@@ -84,6 +84,7 @@ rd_status launch_batch(void *plan, float *fields, int64_t steps_override, double
 void set_variant_choice(int model, int G, int vi);
 int get_variant_choice(int model, int G);
 int n_variants();
+void set_gram_spin_limit(uint32_t n);
 bool variant_shape(int G, int vi, int *packed, int *TY, int *TX);
 
 }  // namespace rdcil

@@ -32,7 +32,7 @@ static constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
 static constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;              // 16 KiB
 static constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;             // A hi, A lo, B hi, B lo
 static constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
-static_assert((2 * TC_STAGES + 4) * 8 + 4 <= 256, "barrier area");
+static_assert((2 * TC_STAGES + 5) * 8 + 4 <= 256, "barrier area");
 static constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;                  // bounded spin (~seconds)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -60,9 +60,11 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it)
+// Bounded wait for the phase with the given parity to complete (at most
+// `limit` polls; the pipeline waits take the limit from the launch, the
+// clean-up waits for work already issued always use TC_WAIT_LIMIT).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = TC_WAIT_LIMIT) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try(bar, parity)) return true;
     return false;
 }
@@ -180,14 +182,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // [384,512) sum lo; warp w may access TMEM lanes 32 (w % 4) .. +31 (rows).
 __global__ void __launch_bounds__(192, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int n1, int n2,
-               int dp, int ntj, int S, int cs, float *__restrict__ Ppart, uint32_t *__restrict__ status) {
+               int dp, int ntj, int S, int cs, float *__restrict__ Ppart, uint32_t *__restrict__ status,
+               uint32_t spin) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + TC_STAGES * TC_STAGE_BYTES);
     uint64_t *empty = full + TC_STAGES;
     uint64_t *accf = empty + TC_STAGES;     // [2] chunk accumulated (MMA commit)
     uint64_t *acce = accf + 2;              // [2] accumulator drained (4 drain warps)
-    uint32_t *tslot = (uint32_t *)(acce + 2);
+    uint64_t *mdone = acce + 2;             // every MMA issued by this CTA has completed
+    uint32_t *tslot = (uint32_t *)(mdone + 1);
     __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -207,6 +211,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
             mbar_init(&accf[q], 1);
             mbar_init(&acce[q], 4);
         }
+        mbar_init(mdone, 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -227,7 +232,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         for (int it = 0; it < nst; ++it) {
             const int q = it % TC_STAGES;
             const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
-            if (!mbar_wait(&empty[q], ph ^ 1u)) { s_fail = 1; break; }
+            if (!mbar_wait(&empty[q], ph ^ 1u, spin)) { s_fail = 1; break; }
             uint8_t *st = smem + q * TC_STAGE_BYTES;
             mbar_expect_tx(&full[q], TC_STAGE_BYTES);
             const int k = (k_lo + it) * TC_BK;
@@ -244,14 +249,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         int it = 0;
         for (int c = 0; c < nch && ok; ++c) {
             const int buf = c & 1;
-            if (c >= 2 && !mbar_wait(&acce[buf], (uint32_t)((c >> 1) - 1) & 1u)) { s_fail = 1; break; }
+            if (c >= 2 && !mbar_wait(&acce[buf], (uint32_t)((c >> 1) - 1) & 1u, spin)) { s_fail = 1; break; }
             fence_after();
             const uint32_t dacc = tmem + (uint32_t)(buf * TC_BN);
             const int it_end = min(nst, (c + 1) * cs);
             for (int first = 1; it < it_end; ++it, first = 0) {
                 const int q = it % TC_STAGES;
                 const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
-                if (!mbar_wait(&full[q], ph)) { s_fail = 1; ok = false; break; }
+                if (!mbar_wait(&full[q], ph, spin)) { s_fail = 1; ok = false; break; }
                 fence_after();
                 const uint32_t base = smem_u32(smem + q * TC_STAGE_BYTES);
 #pragma unroll
@@ -269,6 +274,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
             }
             if (ok) mma_commit(&accf[buf]);   // chunk complete in accumulator buf
         }
+        // whatever happened above, let every MMA this CTA issued finish before
+        // its shared memory and tensor memory are released
+        mma_commit(mdone);
+        if (!mbar_wait(mdone, 0)) s_fail = 1;
     } else if (warp >= 2) {
         // ---- drain: compensated sum of the chunk partials ----
         const int qd = warp & 3;                                   // TMEM lane quarter
@@ -276,7 +285,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         const int row = qd * 32 + lane;
         for (int c = 0; c < nch; ++c) {
             const int buf = c & 1;
-            const bool got = mbar_wait(&accf[buf], (uint32_t)(c >> 1) & 1u);
+            const bool got = mbar_wait(&accf[buf], (uint32_t)(c >> 1) & 1u, spin);
             // warp-uniform: tcgen05.ld/st below are warp-collective
             if (!__all_sync(0xffffffffu, got)) { s_fail = 1; break; }
             fence_after();
@@ -340,9 +349,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
     const int bad = __syncthreads_or(s_fail);
     if (threadIdx.x == 0 && bad) {
         atomicOr(status, (unsigned)ST_TIMEOUT);
-        // let the copies already in flight land before the block's shared
-        // memory is released (bounded)
-        for (int it = 0; it < issued; ++it) mbar_wait(&full[it % TC_STAGES], (uint32_t)(it / TC_STAGES) & 1u);
+        // let the copies still in flight (at most the last TC_STAGES issued;
+        // earlier ones were waited for by the MMA issuer before their stage
+        // was refilled) land before the block's shared memory is released
+        for (int it = issued > TC_STAGES ? issued - TC_STAGES : 0; it < issued; ++it)
+            mbar_wait(&full[it % TC_STAGES], (uint32_t)(it / TC_STAGES) & 1u);
     }
     __syncthreads();
     fence_after();
@@ -383,6 +394,9 @@ static bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t dp)
 // Preconditions (checked): hi/lo 16-byte aligned, dp a multiple of 64,
 // 1 <= S <= dp / 64, cs >= 1 (K steps of 64 per accumulator chunk).
 // Ppart holds S * 2 * n1 * n2 floats (16-byte aligned).
+static uint32_t g_spin_limit = TC_WAIT_LIMIT;
+void set_gram_spin_limit(uint32_t n) { g_spin_limit = n ? n : TC_WAIT_LIMIT; }
+
 rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2, int64_t dp, int64_t S, int64_t cs,
                          float *Ppart, uint32_t *status, cudaStream_t s) {
     if ((((uintptr_t)hi | (uintptr_t)lo | (uintptr_t)Ppart) & 15) || (dp % TC_BK) || n1 < 1 || n2 < 1 || S < 1 ||
@@ -399,7 +413,7 @@ rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2,
         attr = true;
     }
     gram_tc_kernel<<<(unsigned)(nti * ntj * S), 192, TC_SMEM, s>>>(mh, ml, (int)n1, (int)n2, (int)dp, (int)ntj,
-                                                                   (int)S, (int)cs, Ppart, status);
+                                                                   (int)S, (int)cs, Ppart, status, g_spin_limit);
     note_launch();
     return cuda_status(cudaGetLastError());
 }
