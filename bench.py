@@ -170,6 +170,39 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# multi-rank host logic (weak scaling: every rank runs its own independent
+# batch; no collective on the data path, only the timing is reduced)
+# ---------------------------------------------------------------------------
+RANK_SEED_STRIDE = 7919
+
+
+def rank_groups(cfg, rank):
+    """The workload's groups for one rank: the same shapes, seeds offset by
+    rank so that every rank integrates an independent batch."""
+    out = []
+    for gd in cfg["groups"]:
+        gd = dict(gd)
+        gd["seed"] = gd["seed"] + RANK_SEED_STRIDE * rank
+        out.append(gd)
+    return out
+
+
+def max_over_ranks(x, device, world):
+    """The largest value of x over all ranks (x itself when world == 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second, over the slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2203_14742_b300 as p
@@ -179,11 +212,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     cfg = W.config(args.config)
-    gds = []
-    for gd in cfg["groups"]:
-        gd = dict(gd)
-        gd["seed"] = gd["seed"] + 7919 * rank      # weak scaling: one independent batch per rank
-        gds.append(gd)
+    gds = rank_groups(cfg, rank)
     groups = [p.Group.from_dict(gd) for gd in gds]
     n1, n2, M, b, T = cfg["n1"], cfg["n2"], cfg["M"], cfg["b"], cfg["T_res"]
     sets = [(n1, n2, gd["species_mask"]) for gd in gds]
@@ -241,13 +270,10 @@ def run_ours(args, rank, world, local_rank):
     k_ms = [m[1].elapsed_time(m[2]) for m in marks]
     cil_ms = [m[2].elapsed_time(m[3]) for m in marks]
     syn_ms = [m[3].elapsed_time(m[4]) for m in marks]
-    if world > 1:
-        t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t)
+    step_ms = max_over_ranks(step_ms, dev, world)
     assert sim.sync_status() == 0
     ms_per_step = step_ms / args.steps
-    value = cell_updates * world / (ms_per_step * 1e-3)
+    value = whole_job_rate(cell_updates, world, ms_per_step)
     nre = int(sum(int(o["n_rechecked"]) for o in pipe.cil_out))
 
     # ---- the same pass captured in a CUDA graph and replayed -----------------
@@ -291,10 +317,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t)
+    e2e_ms = max_over_ranks(e2e_ms, dev, world)
     h2d = host["fields"].numel() * 4
     d2h = sum(host[k].numel() * host[k].element_size() for k in outs)
 
@@ -358,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
         "cil_ms": cil_avg,
         "synlik_ms": sum(syn_ms) / len(syn_ms),
         "graph_replay_ms_per_step": graph_ms,
-        "e2e": {"value": cell_updates * world / (e2e_ms * 1e-3), "unit": "cell-updates/s",
+        "e2e": {"value": whole_job_rate(cell_updates, world, e2e_ms), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tinst/s",

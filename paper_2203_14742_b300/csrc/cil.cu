@@ -5,12 +5,16 @@
 // evaluated in FP64 in one fixed order (term t into partial t mod 256, each
 // partial in increasing t, partials combined by a halving tree within groups
 // of 32 and then across the 8 groups; no FMA).  It does so in three stages:
-//   1. pack:  centre every pattern by the set mean c (translation does not
-//      change distances), split x - c into bf16 hi + lo, and record per
+//   1. pack:  centre every pattern by c = the mean of up to 16 patterns
+//      sampled from each set (translation does not change distances; any c
+//      is valid, a central one keeps the bf16 split accurate), split x - c
+//      into bf16 hi + lo, and record per
 //      pattern N = |hi+lo|^2, H = |hi| + |lo|, L = |lo| and the
 //      representation error E = |(x - c) - (hi + lo)| (all FP64);
 //   2. Gram:  P_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j (bf16 products, FP32
-//      accumulation per K-chunk, chunks summed in FP64);
+//      accumulation per K chunk in tensor memory, chunk partials summed with
+//      TwoSum into FP32 hi/lo pairs per K segment, segments combined the
+//      same way);
 //   3. tier 1: A = N_i + N_j - 2 P_ij approximates d2_ij with a rigorous
 //      error bound (FP32 accumulation model, dropped lo.lo term, E_i + E_j,
 //      rounding of the canonical sum), kept as an FP32 interval rounded
