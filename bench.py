@@ -511,15 +511,22 @@ def oracle_sample(cfg, n_steps_sample):
     t_cil = time.perf_counter() - t1
     full_cells = n * G * G * g["n_steps"]
     t_full = t_step * (g["n_steps"] / n_steps_sample) + t_cil
-    note = ("all %d realisations x %d of %d Euler steps (stepping time scaled by %.0fx) + full CIL "
-            "and bootstrap statistics" % (n, n_steps_sample, g["n_steps"], g["n_steps"] / n_steps_sample))
+    if n_steps_sample >= g["n_steps"]:
+        note = ("the whole workload: all %d realisations x %d Euler steps + CIL + bootstrap statistics"
+                % (n, g["n_steps"]))
+    else:
+        note = ("all %d realisations x %d of %d Euler steps (stepping time scaled by %.0fx) + full CIL "
+                "and bootstrap statistics" % (n, n_steps_sample, g["n_steps"], g["n_steps"] / n_steps_sample))
     return full_cells / t_full, t_step + t_cil, note
 
 
 def run_reference(args):
+    import oracle
     cfg = W.config(args.config)
-    cores = os.cpu_count()
-    n_sample = 500
+    # each step is the whole workload (about 5 s on 16 cores) while the run
+    # stays within a few minutes; beyond 20 steps a proportional sample
+    n_full = cfg["groups"][0]["n_steps"]
+    n_sample = n_full if args.steps + args.warmup <= 20 else max(1000, n_full * 20 // (args.steps + args.warmup))
     oracle_sample(cfg, 10)           # warm (builds the library)
     vals, secs = [], 0.0
     for _ in range(args.warmup):
@@ -529,6 +536,7 @@ def run_reference(args):
         vals.append(v)
         secs += s
     value = statistics.mean(vals)
+    cores = oracle.threads()
     g = cfg["groups"][0]
     return {
         "impl": "reference",
@@ -573,8 +581,9 @@ def main():
     out = run_ours(args, rank, world, local_rank)
     if rank == 0 and not args.no_cpu_baseline:
         cfg = W.config(args.config)
-        v, secs, note = oracle_sample(cfg, 1000)
-        out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": os.cpu_count(),
+        v, secs, note = oracle_sample(cfg, cfg["groups"][0]["n_steps"])
+        import oracle
+        out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": oracle.threads(),
                                "kind": "oracle", "sample": note + " (%.1f s of CPU work)" % secs}
     if rank == 0:
         print(json.dumps(out))

@@ -20,6 +20,11 @@ FHN, GM, DIFF = 0, 1, 2
 _lib = None
 
 
+def threads():
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(lib().orc_threads())
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -28,6 +33,7 @@ def lib():
         dp, fp, i64p, i32p, u8p = (C.POINTER(C.c_double), C.POINTER(C.c_float),
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_uint8))
+        L.orc_threads.restype = C.c_int
         L.orc_sm64.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_sm64.restype = C.c_uint64
         L.orc_equilibrium.argtypes = [C.c_int, dp, dp, dp]

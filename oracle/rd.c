@@ -36,6 +36,19 @@
 #include <string.h>
 #include <math.h>
 #include "sm64.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the OpenMP loops below use (1 without OpenMP); reported with the
+   CPU timings. */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define ORC_FHN 0
 #define ORC_GM 1
