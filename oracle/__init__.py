@@ -34,6 +34,17 @@ def lib():
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_uint8))
         L.orc_threads.restype = C.c_int
+        L.orc_minmax.argtypes = [fp, C.c_int64, C.c_int, C.c_int, fp]
+        L.orc_fd.argtypes = [fp, C.c_int64, C.c_int, C.c_int, fp, fp]
+        L.orc_maxabs.argtypes = [fp, fp, C.c_int64]
+        L.orc_maxabs.restype = C.c_double
+        L.orc_d2_canon.argtypes = [fp, fp, C.c_int64]
+        L.orc_d2_canon.restype = C.c_double
+        L.orc_mcil_values.argtypes = [fp, fp, fp, C.c_int64, fp, fp, fp, C.c_int64, C.c_int, C.c_int,
+                                      C.c_int, dp]
+        L.orc_mcil_bins.argtypes = [dp, C.c_int64, C.c_int, C.c_double, C.c_int, dp, u8p, i64p]
+        L.orc_mcil_squared.argtypes = [C.c_int]
+        L.orc_mcil_squared.restype = C.c_int
         L.orc_sm64.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_sm64.restype = C.c_uint64
         L.orc_equilibrium.argtypes = [C.c_int, dp, dp, dp]
@@ -311,3 +322,91 @@ def smooth_cil_loss(model, p, dt, n_steps, w0, species_mask, set1, set2, radii_,
                                   s1.size, _p(s2, C.c_int32), s2.size, _p(r, C.c_double), M,
                                   float(tau_frac), _p(c, C.c_double), _p(Cv, C.c_double))
     return L, Cv
+
+
+# ---------------------------------------------------------------------------
+# multi-feature correlation integral (Sec. 3.1, Alg. 2; min-max scaling,
+# Sec. 4) -- see mcil.c for the definitions and readings
+# ---------------------------------------------------------------------------
+FEATURES = ("L2", "Linf", "W12", "W12p", "W1inf", "W1infp")
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, np.float32)
+
+
+def minmax(X, G, nsp):
+    """Min-max scaled copy of patterns X [n, nsp*G*G] (per species)."""
+    X = _f32(X)
+    out = np.empty_like(X)
+    lib().orc_minmax(_p(X, C.c_float), X.shape[0], G, nsp, _p(out, C.c_float))
+    return out
+
+
+def fd(X, G, nsp):
+    """Forward-difference patterns (Ax, Ay), each [n, nsp*G*(G-1)] float32."""
+    X = _f32(X)
+    n = X.shape[0]
+    Ax = np.empty((n, nsp * G * (G - 1)), np.float32)
+    Ay = np.empty((n, nsp * G * (G - 1)), np.float32)
+    lib().orc_fd(_p(X, C.c_float), n, G, nsp, _p(Ax, C.c_float), _p(Ay, C.c_float))
+    return Ax, Ay
+
+
+def maxabs(x, y):
+    x, y = _f32(x), _f32(y)
+    return lib().orc_maxabs(_p(x, C.c_float), _p(y, C.c_float), x.size)
+
+
+def d2_canon(x, y):
+    x, y = _f32(x), _f32(y)
+    return lib().orc_d2_canon(_p(x, C.c_float), _p(y, C.c_float), x.size)
+
+
+def mcil_values(X1, X2, G, nsp, mask=63):
+    """Feature values V[6, n1, n2] of every cross-set pair (NaN where the
+    feature is not in mask): squared for L2 and W12, plain otherwise."""
+    X1, X2 = _f32(X1), _f32(X2)
+    Ax1, Ay1 = fd(X1, G, nsp)
+    Ax2, Ay2 = fd(X2, G, nsp)
+    n1, n2 = X1.shape[0], X2.shape[0]
+    V = np.full((6, n1, n2), np.nan)
+    lib().orc_mcil_values(_p(X1, C.c_float), _p(Ax1, C.c_float), _p(Ay1, C.c_float), n1,
+                          _p(X2, C.c_float), _p(Ax2, C.c_float), _p(Ay2, C.c_float), n2,
+                          G, nsp, int(mask), _p(V, C.c_double))
+    return V
+
+
+def mcil(X1, X2, G, nsp, b, M, mask=63, scale=False):
+    """Multi-feature correlation integral (Alg. 2 step 2.2): per feature in
+    mask (ascending), radii [K, M+1] (R0 first), bins [K, n1, n2], counts
+    [K, M]; C = the concatenated vector (K*M) of eq. (CIL)."""
+    if scale:
+        X1, X2 = minmax(X1, G, nsp), minmax(X2, G, nsp)
+    V = mcil_values(X1, X2, G, nsp, mask)
+    feats = [f for f in range(6) if mask & (1 << f)]
+    n1, n2 = V.shape[1], V.shape[2]
+    K = len(feats)
+    radii = np.empty((K, M + 1))
+    bins = np.empty((K, n1, n2), np.uint8)
+    counts = np.empty((K, M), np.int64)
+    for a, f in enumerate(feats):
+        v = np.ascontiguousarray(V[f])
+        lib().orc_mcil_bins(_p(v, C.c_double), n1 * n2, lib().orc_mcil_squared(f), float(b), M,
+                            _p(radii[a], C.c_double), _p(bins[a], C.c_uint8), _p(counts[a], C.c_int64))
+    return {"features": feats, "values": V, "radii": radii, "bins": bins, "counts": counts,
+            "C": counts.reshape(-1) / float(n1 * n2)}
+
+
+def synlik_multi(bins, M, T, seed, y_obs=None):
+    """Bootstrap statistics of a concatenated feature vector (Alg. 5 with
+    the multi-feature vector of Alg. 2): every resample draws one pair of
+    index sets and counts it under every feature; Y[t] = (Y_feature0[t],
+    Y_feature1[t], ...)."""
+    bins = np.asarray(bins, np.uint8)
+    K, n1, n2 = bins.shape
+    I, J = bootstrap_indices(seed, T, n1, n2)
+    Y = np.concatenate([resample_counts(bins[a], M, I, J) for a in range(K)], axis=1)
+    out = stats(Y, n1 * n2, y_obs)
+    out["Y"] = Y
+    return out

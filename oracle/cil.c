@@ -62,6 +62,12 @@ static double d2_f32(const float *x, const float *y, int64_t d)
     return w[0];
 }
 
+/* The canonical squared distance, for the other oracle files. */
+double orc_d2_canon(const float *x, const float *y, int64_t d)
+{
+    return d2_f32(x, y, d);
+}
+
 static double d2_f64(const double *x, const double *y, int64_t d)
 {
     double acc = 0.0;
