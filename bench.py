@@ -77,6 +77,11 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="also time the adjoint (smoothed-CIL gradient) on the FHN 64x64 adjoint workload "
                          "(32 realisations, 5000 steps)")
+    ap.add_argument("--mcil", action="store_true",
+                    help="also time the multi-feature correlation integral (six distances) at the FHN 64x64 "
+                         "and GM 128x128 set shapes")
+    ap.add_argument("--mcil-only", action="store_true",
+                    help="time only the multi-feature correlation integral (for profiling)")
     ap.add_argument("--gram-large-only", action="store_true",
                     help="time only the tensor-core Gram and correlation integral on 2 x 1024 patterns of "
                          "d = 32768 (for profiling); prints that object alone")
@@ -401,6 +406,8 @@ def run_ours(args, rank, world, local_rank):
         out["gram_large"] = gram_large(p, torch, dev, stream, pk, src)
     if args.adjoint and rank == 0:
         out["adjoint"] = adjoint_c5(p, torch, dev, stream)
+    if args.mcil and rank == 0:
+        out["mcil"] = mcil_bench(p, torch, dev, stream)
     return out
 
 
@@ -450,6 +457,32 @@ def gram_large(p, torch, dev, stream, pk, src):
                          "products (3 x 2 n1 n2 d flops), algorithmic = 2 n1 n2 d" % src,
             "cil_ms": t_cil * 1e3, "pair_dists_per_s": n * n / t_cil,
             "rechecked": int(c["n_rechecked"])}
+
+
+def mcil_bench(p, torch, dev, stream):
+    """Multi-feature correlation integral (L2, Linf, W12, W12', W1inf,
+    W1inf'; Sec. 3.1) on synthetic cosine-mode fields of two set shapes:
+    2 x 64 patterns of one 64x64 species and 2 x 256 of two 128x128
+    species; raw and min-max scaled."""
+    res = []
+    for (n, G, nsp) in ((64, 64, 1), (256, 128, 2)):
+        X = torch.from_numpy(W.cosine_patterns(2 * n, G, nsp, 91, amp=0.8, offset=1.0)).to(dev)
+        for scale in (False, True):
+            work = p.mcil_workspace(n, n, G, nsp, 63, scale, 16, dev)
+            r = p.mcil(X[:n], X[n:], G, nsp, b=1.3, M=16, scale=scale, work=work)
+            torch.cuda.synchronize()
+            reps = 5
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                r = p.mcil(X[:n], X[n:], G, nsp, b=1.3, M=16, scale=scale, work=work)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / reps * 1e-3
+            res.append({"pairs": n * n, "G": G, "species": nsp, "d": nsp * G * G, "scaled": scale,
+                        "features": 6, "ms": t * 1e3, "pair_features_per_s": 6 * n * n / t,
+                        "exact_pairs": int(r["n_exact"])})
+    return res
 
 
 def adjoint_c5(p, torch, dev, stream):
@@ -563,6 +596,15 @@ def main():
         if rank != 0:
             return
         print(json.dumps(run_reference(args)))
+        return
+    if args.mcil_only:
+        import torch
+        import paper_2203_14742_b300 as p
+        from paper_2203_14742_b300 import build as B
+        B.build()
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        print(json.dumps(mcil_bench(p, torch, dev, torch.cuda.current_stream(dev))))
         return
     if args.gram_large_only:
         import torch

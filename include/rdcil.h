@@ -324,6 +324,69 @@ rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2, int32_t M,
                        double *d_cov, double *d_chol, double *d_scalars,
                        uint8_t *d_active, int32_t *d_status, void *stream);
 
+/* synlik_stats_multi — the same statistics of a concatenated feature
+ * vector (the multi-feature CIL of Sec. 3.1 / Alg. 2 with the bootstrap of
+ * Alg. 5): d_bins is uint8 [n_problems][n_feat][n1][n2] (one bin matrix
+ * per feature, e.g. from mcil_features); every resample draws one pair of
+ * index sets (as above, stream seed + p) and counts it under every
+ * feature, so d_Y is [n_problems][T][n_feat*M] with component f*M + k-1
+ * the count of feature f at radius k; all other outputs as above with
+ * n_feat*M components.  synlik_stats is the case n_feat = 1.
+ * Limits as above and 1 <= n_feat*M <= 96. */
+rd_status synlik_stats_multi(const uint8_t *d_bins, int32_t n_feat, int64_t n1, int64_t n2,
+                             int32_t M, int32_t T, uint64_t seed, int32_t n_problems,
+                             const double *d_y_obs, int64_t *d_Y, double *d_mu, double *d_cov,
+                             double *d_chol, double *d_scalars, uint8_t *d_active,
+                             int32_t *d_status, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Multi-feature correlation integral (Sec. 3.1, Alg. 2 step 2.2; min-max
+ * scaled data, Sec. 4).
+ *
+ * Patterns are n_species (1 or 2) fields of G x G floats, contiguous per
+ * pattern: pattern i of set 1 starts at d_X1 + i*ld1 (likewise set 2), so
+ * one or both species of a realisation are read in place from the field
+ * array.  h = 1/(G-1), g = G-1.  The derivative patterns are forward
+ * differences of each field, rounded to FP32 once (Dx: G x (G-1) values
+ * s[y][x+1] - s[y][x], Dy: (G-1) x G values s[y+1][x] - s[y][x]).  With
+ * q0, qx, qy the squared distances of the patterns and of their Dx and Dy
+ * patterns in the canonical FP64 order of cil_features, and m0, mx, my the
+ * exact maxima of |difference|, feature f (bit f of `features`) is the FP64
+ * expression (every operation rounded to nearest, no FMA)
+ *   0 L2      (eq. norm:L2)         squared value  q0
+ *   1 Linf    (eq. norm:Linf)       value          m0
+ *   2 W12     (eq. norm:W12)        squared value  (h^2 q0 + qx) + qy
+ *   3 W12'    (eq. norm:W12prime)   value          (h sqrt(q0) + sqrt(qx)) + sqrt(qy)
+ *   4 W1inf   (eq. norm:W1inf)      value          max(m0, max(g mx, g my))
+ *   5 W1inf'  (eq. norm:W1infprime) value          (m0 + g mx) + g my
+ * (h = 1/g and h^2 = 1/(g*g) rounded to nearest).  The L2 feature is the
+ * plain Euclidean distance of cil_features (same bins and counts).  A
+ * squared feature is decided like cil_features (R0 = sqrt(max), K = #{k :
+ * V < R_k * R_k}); a value feature directly (R0 = max V, K = #{k : V <
+ * R_k}); R_k = R_{k-1} / b, all in FP64.
+ * scale != 0: every species of every pattern is first min-max scaled,
+ *   s -> fl32(((double)s - min) / (max - min)) in FP64 (0 where max == min).
+ * Outputs, for the K = popcount(features) selected features in ascending
+ * order: d_radii_out [K][M+1] (R0, R_1..R_M); d_bins uint8 [K][n1][n2];
+ * d_counts int64 [K][M]; d_C (nullable) float64 [K*M], the concatenated
+ * correlation integral vector (counts / (n1 n2)); d_n_exact (nullable)
+ * int64: pairs evaluated in the canonical order (-2 if a tensor-core stage
+ * timed out; outputs invalid).  Bins and counts equal the definition bit
+ * for bit: squared distances come from the tensor-core Gram with rigorous
+ * intervals, maxima from an FP32 pass (whose rounding is within 2^-23 of
+ * the exact maximum), and every pair whose interval may hold a maximum or
+ * meets a threshold is evaluated exactly.
+ * Workspace: d_work (256-byte aligned) of mcil_workspace_size bytes.
+ * Limits: 1 <= n1, n2 <= 65535; 2 <= G <= 4096; 1 <= M <= 32; b > 1;
+ * 1 <= features <= 63. */
+rd_status mcil_workspace_size(int64_t n1, int64_t n2, int32_t G, int32_t n_species,
+                              int32_t features, int32_t scale, int32_t M, size_t *bytes);
+rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                        int64_t ld2, int64_t n2, int32_t G, int32_t n_species, int32_t features,
+                        int32_t scale, double b, int32_t M, double *d_radii_out, uint8_t *d_bins,
+                        int64_t *d_counts, double *d_C, int64_t *d_n_exact, void *d_work,
+                        size_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Adjoint: gradient of a sigmoid-smoothed correlation integral with respect
  * to the four parameters of one group (the paper itself is gradient-free;

@@ -55,6 +55,11 @@ _SIGS = {
     "cil_debug_approx": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _sz, _vp]),
     "synlik_stats": (_i32, [_vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                             _vp, _vp, _vp]),
+    "synlik_stats_multi": (_i32, [_vp, _i32, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, _vp, _vp]),
+    "mcil_workspace_size": (_i32, [_i64, _i64, _i32, _i32, _i32, _i32, _i32, C.POINTER(_sz)]),
+    "mcil_features": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _dbl, _i32, _vp, _vp,
+                             _vp, _vp, _vp, _vp, _sz, _vp]),
     "rd_kernel_launches": (_u64, []),
     "rd_set_spin_limit": (None, [C.c_uint32]),
     "rd_n_variants": (_i32, []),
@@ -345,16 +350,19 @@ def synlik_outputs(P, M, T, device):
             "status": torch.empty(P, dtype=torch.int32, device=dev)}
 
 
-def synlik(bins, M, T, seed, y_obs=None, out=None):
-    """Bootstrap statistics of bins [P, n1, n2] (or [n1, n2]) uint8."""
-    squeeze = bins.dim() == 2
+def synlik(bins, M, T, seed, y_obs=None, out=None, n_feat=1):
+    """Bootstrap statistics of bins [P, n1, n2] (or [n1, n2]) uint8; with
+    n_feat > 1, bins [P, n_feat, n1, n2] (or [n_feat, n1, n2]) of a
+    concatenated feature vector (n_feat * M components)."""
+    squeeze = bins.dim() == (2 if n_feat == 1 else 3)
     if squeeze:
         bins = bins.unsqueeze(0)
     if not bins.is_contiguous():
         raise ValueError("bins must be contiguous")
-    P, n1, n2 = bins.shape
+    P, n1, n2 = bins.shape[0], bins.shape[-2], bins.shape[-1]
+    Mt = n_feat * M
     dev = bins.device
-    o = out if out is not None else synlik_outputs(P, M, T, dev)
+    o = out if out is not None else synlik_outputs(P, Mt, T, dev)
     Y, mu, cov, chol, sc, act, st = (o["Y"], o["mu"], o["cov"], o["chol"], o["scalars"], o["active"],
                                      o["status"])
     yo = None
@@ -362,17 +370,56 @@ def synlik(bins, M, T, seed, y_obs=None, out=None):
         yo = y_obs
         if yo.dtype != torch.float64 or yo.device != dev or not yo.is_contiguous():
             yo = yo.to(device=dev, dtype=torch.float64).contiguous()   # marshalling only
-        if yo.numel() != P * M:
-            raise ValueError("y_obs must hold P x M values")
-    _check("synlik_stats", lib().synlik_stats(_ptr(bins), n1, n2, int(M), int(T),
-                                              int(seed) & 0xFFFFFFFFFFFFFFFF, P, _ptr(yo), _ptr(Y),
-                                              _ptr(mu), _ptr(cov), _ptr(chol), _ptr(sc), _ptr(act),
-                                              _ptr(st), _stream()))
+        if yo.numel() != P * Mt:
+            raise ValueError("y_obs must hold P x n_feat*M values")
+    _check("synlik_stats_multi", lib().synlik_stats_multi(_ptr(bins), int(n_feat), n1, n2, int(M), int(T),
+                                                          int(seed) & 0xFFFFFFFFFFFFFFFF, P, _ptr(yo), _ptr(Y),
+                                                          _ptr(mu), _ptr(cov), _ptr(chol), _ptr(sc), _ptr(act),
+                                                          _ptr(st), _stream()))
     out = {"Y": Y, "mu": mu, "cov": cov, "chol": chol, "scalars": sc, "logdet": sc[:, 0], "f": sc[:, 1],
            "loglik": sc[:, 2], "m_active": sc[:, 3], "active": act, "status": st}
     if squeeze:
         out = {k: v[0] for k, v in out.items()}
     return out
+
+
+# ---------------------------------------------------------------------------
+# multi-feature correlation integral
+# ---------------------------------------------------------------------------
+FEATURES = ("L2", "Linf", "W12", "W12p", "W1inf", "W1infp")
+
+
+def mcil_workspace(n1, n2, G, n_species, features=63, scale=False, M=16, device=None):
+    """A device workspace for mcil() with these sizes (reusable across calls)."""
+    sz = _sz()
+    _check("mcil_workspace_size", lib().mcil_workspace_size(int(n1), int(n2), int(G), int(n_species),
+                                                            int(features), 1 if scale else 0, int(M),
+                                                            C.byref(sz)))
+    return torch.empty(sz.value, dtype=torch.uint8, device=device)
+
+
+def mcil(X1, X2, G, n_species, b=1.3, M=16, features=63, scale=False, work=None):
+    """Multi-feature correlation integral of two pattern sets (rows of n_species
+    G x G fields, read in place).  Returns radii [K, M+1], bins [K, n1, n2],
+    counts [K, M], C [K*M] and n_exact for the K selected features."""
+    X1, ld1, n1, d = _as_rows(X1)
+    X2, ld2, n2, d2 = _as_rows(X2)
+    if d != d2 or d != n_species * G * G:
+        raise ValueError("pattern length must be n_species * G * G")
+    dev = X1.device
+    K = bin(int(features)).count("1")
+    if work is None:
+        work = mcil_workspace(n1, n2, G, n_species, features, scale, M, dev)
+    radii = torch.empty((K, M + 1), dtype=torch.float64, device=dev)
+    bins = torch.empty((K, n1, n2), dtype=torch.uint8, device=dev)
+    counts = torch.empty((K, M), dtype=torch.int64, device=dev)
+    Cv = torch.empty(K * M, dtype=torch.float64, device=dev)
+    nex = torch.zeros(1, dtype=torch.int64, device=dev)
+    _check("mcil_features", lib().mcil_features(_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, int(G), int(n_species),
+                                                int(features), 1 if scale else 0, float(b), int(M), _ptr(radii),
+                                                _ptr(bins), _ptr(counts), _ptr(Cv), _ptr(nex), _ptr(work),
+                                                work.numel(), _stream()))
+    return {"radii": radii, "bins": bins, "counts": counts, "C": Cv, "n_exact": nex}
 
 
 # ---------------------------------------------------------------------------

@@ -708,6 +708,26 @@ static rd_status tier1(const CilWork &w, const float *X1, int64_t ld1, const flo
     return RD_OK;
 }
 
+// Internal entry for the multi-feature correlation integral: tier-1
+// intervals [lo, hi] (FP32, outward) of the canonical squared distance of
+// every pair of two pattern arrays, left in the workspace; *timeout points
+// at the word the tensor-core stage raises on a timeout.
+rd_status cil_tier1_intervals(const float *X1, int64_t ld1, int64_t n1, const float *X2, int64_t ld2, int64_t n2,
+                              int64_t d, void *work, size_t work_bytes, const float **lo, const float **hi,
+                              const unsigned long long **timeout, cudaStream_t s) {
+    if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535 || d < 1 || ld1 < d || ld2 < d) return RD_ERR_INVALID_ARG;
+    if (!X1 || !X2 || !work || (((uintptr_t)work & 255) != 0)) return RD_ERR_INVALID_ARG;
+    CilWork w = layout(n1, n2, d, work);
+    if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
+    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 16 * sizeof(unsigned long long), s));
+    rd_status st = tier1(w, X1, ld1, X2, ld2, s);
+    if (st) return st;
+    *lo = w.lo32;
+    *hi = w.hi32;
+    *timeout = &w.scal[SC_TIMEOUT];
+    return RD_OK;
+}
+
 static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *X2, int64_t ld2, int64_t n2,
                          int64_t d, const double *radii_in, double b, int32_t M, double *radii_out,
                          uint8_t *bins, int64_t *counts, double *Cv, int64_t *n_rechecked, void *work,

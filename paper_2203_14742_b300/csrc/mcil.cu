@@ -1,0 +1,572 @@
+// Multi-feature correlation integral (MCIL): the correlation integral
+// vector of eq. (CIL) under six distances of the pattern difference
+// u = s_i - s_j, concatenated (Sec. 3.1, Alg. 2), optionally on min-max
+// scaled patterns (Sec. 4, "scaled pattern data").
+//
+// A pattern is n_species fields of G x G nodes; h = 1/(G-1), g = G-1.  The
+// derivative patterns are forward differences of each field rounded to FP32
+// once (Dx: G x (G-1), Dy: (G-1) x G per species).  With q0, qx, qy the
+// canonical squared distances (the fixed FP64 order of the CIL: partial
+// t mod 256, halving trees) of the patterns and of their Dx and Dy patterns,
+// and m0, mx, my the exact maxima of |difference|, the features are
+//   0 L2      squared  q0                                  (eq. norm:L2)
+//   1 Linf    value    m0                                  (eq. norm:Linf)
+//   2 W12     squared  (h^2 q0 + qx) + qy                  (eq. norm:W12)
+//   3 W12'    value    (h sqrt(q0) + sqrt(qx)) + sqrt(qy)   (eq. norm:W12prime)
+//   4 W1inf   value    max(m0, max(g mx, g my))            (eq. norm:W1inf)
+//   5 W1inf'  value    (m0 + g mx) + g my                  (eq. norm:W1infprime)
+// each one FP64 expression with every operation rounded to nearest.  A
+// squared feature is decided like the CIL (R0 = sqrt(max), V < R_k * R_k),
+// a value feature directly (R0 = max, V < R_k); R_k = R_{k-1} / b.
+//
+// Exactness contract: bins and counts equal that definition bit for bit.
+//   1. q0, qx, qy: tier-1 intervals of the CIL (centred bf16 hi/lo split,
+//      tensor-core Gram, rigorous bound), one run per pattern array;
+//   2. m0, mx, my: a tiled SIMT pass (split over K, partial maxima met by
+//      atomicMax) takes max |fl32(a - b)|; rounding to
+//      nearest is monotone, so that is fl32 of the exact maximum M, and
+//      M lies within m32 (1 -+ 2^-23);
+//   3. per pair and feature, an FP64 interval of the feature value by
+//      outward-rounded (_rd / _ru) evaluation of its expression (every
+//      operation is monotone on the non-negative inputs);
+//   4. pairs whose interval may hold a feature's maximum are evaluated
+//      exactly (the canonical FP64 order, one CTA per pair), which fixes R0
+//      and the radii; then pairs whose interval meets a threshold are
+//      evaluated exactly too; everything else is decided by its interval.
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+rd_status cil_tier1_intervals(const float *X1, int64_t ld1, int64_t n1, const float *X2, int64_t ld2, int64_t n2,
+                              int64_t d, void *work, size_t work_bytes, const float **lo, const float **hi,
+                              const unsigned long long **timeout, cudaStream_t s);
+extern "C" rd_status cil_workspace_size(int64_t n1, int64_t n2, int64_t d, size_t *bytes);
+
+namespace rdcil {
+
+static constexpr int NF = 6;
+__host__ __device__ constexpr bool feat_squared(int f) { return f == 0 || f == 2; }
+
+struct McilWork {
+    int64_t n1, n2, np, d0, de;
+    int G, nsp, mask, M;
+    float *S1, *S2;                 // min-max scaled patterns (scale only)
+    float *Ax1, *Ay1, *Ax2, *Ay2;   // forward-difference patterns
+    void *cw[3];                    // CIL workspaces for the pattern, Dx, Dy arrays
+    size_t cw_bytes[3];
+    float *mabs;                    // [3][np] FP32 max |difference| of the three arrays
+    double *vlo, *vhi;              // [NF][np] feature intervals
+    double *vex;                    // [NF][np] exact feature values (where flag == 2)
+    uint8_t *flag;                  // [np] 0 interval, 1 queued, 2 exact
+    int64_t *queue;                 // [np] pairs to evaluate exactly
+    unsigned long long *scal;       // [0] queue length, [1] pass-A length, [2 + f] max lower bound (bits)
+    double *thr;                    // [NF][32] thresholds of the decision (R_k^2 or R_k)
+    size_t bytes;
+};
+
+static inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+static McilWork mlayout(int64_t n1, int64_t n2, int G, int nsp, int mask, int scale, int M, void *base) {
+    McilWork w{};
+    w.n1 = n1; w.n2 = n2; w.np = n1 * n2; w.G = G; w.nsp = nsp; w.mask = mask; w.M = M;
+    w.d0 = (int64_t)nsp * G * G;
+    w.de = (int64_t)nsp * G * (G - 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = (size_t)rup((int64_t)(off + bytes), 256);
+        return (char *)base + o;
+    };
+    const int64_t n = n1 + n2;
+    if (scale) {
+        w.S1 = (float *)take(sizeof(float) * n1 * w.d0);
+        w.S2 = (float *)take(sizeof(float) * n2 * w.d0);
+    }
+    const bool deriv = (mask & 0x3C) != 0;
+    if (deriv) {
+        w.Ax1 = (float *)take(sizeof(float) * n1 * w.de);
+        w.Ay1 = (float *)take(sizeof(float) * n1 * w.de);
+        w.Ax2 = (float *)take(sizeof(float) * n2 * w.de);
+        w.Ay2 = (float *)take(sizeof(float) * n2 * w.de);
+    }
+    (void)n;
+    const bool need_q0 = (mask & 0x0D) != 0, need_qd = (mask & 0x0C) != 0;
+    for (int a = 0; a < 3; ++a) {
+        const bool need = a == 0 ? need_q0 : need_qd;
+        w.cw[a] = nullptr;
+        w.cw_bytes[a] = 0;
+        if (need) {
+            size_t sz = 0;
+            cil_workspace_size(n1, n2, a == 0 ? w.d0 : w.de, &sz);
+            w.cw_bytes[a] = sz;
+            w.cw[a] = take(sz);
+        }
+    }
+    w.mabs = (float *)take(sizeof(float) * 3 * w.np);
+    w.vlo = (double *)take(sizeof(double) * NF * w.np);
+    w.vhi = (double *)take(sizeof(double) * NF * w.np);
+    w.vex = (double *)take(sizeof(double) * NF * w.np);
+    w.flag = (uint8_t *)take(w.np);
+    w.queue = (int64_t *)take(sizeof(int64_t) * w.np);
+    w.scal = (unsigned long long *)take(sizeof(unsigned long long) * 16);
+    w.thr = (double *)take(sizeof(double) * NF * 32);
+    w.bytes = off;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// 0. min-max scaling: one CTA per (pattern, species)
+// ---------------------------------------------------------------------------
+__global__ void minmax_kernel(const float *__restrict__ X, int64_t ld, int G, int nsp, float *__restrict__ out) {
+    const int64_t i = blockIdx.x / nsp;
+    const int sp = blockIdx.x % nsp;
+    const int64_t cells = (int64_t)G * G;
+    const float *x = X + i * ld + sp * cells;
+    float *o = out + (i * nsp + sp) * cells;
+    float mn = x[0], mx = x[0];
+    for (int64_t c = threadIdx.x; c < cells; c += blockDim.x) {
+        mn = fminf(mn, x[c]);
+        mx = fmaxf(mx, x[c]);
+    }
+    __shared__ float smn[32], smx[32];
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o2));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { smn[warp] = mn; smx[warp] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) { smn[0] = fminf(smn[0], smn[q]); smx[0] = fmaxf(smx[0], smx[q]); }
+    }
+    __syncthreads();
+    mn = smn[0];
+    mx = smx[0];
+    const double span = __dsub_rn((double)mx, (double)mn);
+    for (int64_t c = threadIdx.x; c < cells; c += blockDim.x)
+        o[c] = mx > mn ? __double2float_rn(__ddiv_rn(__dsub_rn((double)x[c], (double)mn), span)) : 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// 1. forward-difference patterns (FP32 subtraction = the exact difference
+//    rounded once)
+// ---------------------------------------------------------------------------
+__global__ void fd_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int G, int nsp, float *__restrict__ Ax,
+                          float *__restrict__ Ay) {
+    const int64_t ce = (int64_t)G * (G - 1);
+    const int64_t total = n * nsp * ce;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t is = e / ce, c = e - is * ce;
+        const int64_t i = is / nsp;
+        const int sp = (int)(is - i * nsp);
+        const float *x = X + i * ld + (int64_t)sp * G * G;
+        // Dx: row y, column c2 < G-1
+        {
+            const int y = (int)(c / (G - 1)), c2 = (int)(c - (int64_t)y * (G - 1));
+            Ax[e] = x[(int64_t)y * G + c2 + 1] - x[(int64_t)y * G + c2];
+        }
+        // Dy: row y < G-1, column c2
+        {
+            const int y = (int)(c / G), c2 = (int)(c - (int64_t)y * G);
+            Ay[e] = x[(int64_t)(y + 1) * G + c2] - x[(int64_t)y * G + c2];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. max |a - b| of every pair, FP32: 128 x 128 pairs per CTA, 8 x 8 per
+//    thread (rows ty + 16a, columns tx + 16c, so the shared-memory reads of
+//    a warp are broadcasts or 16 consecutive words), 32-column slices of
+//    both sets in shared memory, and a split of K over blockIdx.z whose
+//    partial maxima meet in atomicMax on the FP32 bit patterns (non-negative
+//    floats order like their bits; max is exact in any order)
+// ---------------------------------------------------------------------------
+constexpr int MX_T = 128, MX_K = 32;
+__global__ void __launch_bounds__(256) maxabs_kernel(const float *__restrict__ A, int64_t lda, int64_t n1,
+                                                     const float *__restrict__ B, int64_t ldb, int64_t n2, int64_t d,
+                                                     int64_t kch, float *__restrict__ out) {
+    __shared__ float sa[MX_K][MX_T + 1], sb[MX_K][MX_T + 1];
+    const int64_t i0 = (int64_t)blockIdx.y * MX_T, j0 = (int64_t)blockIdx.x * MX_T;
+    const int64_t k_lo = (int64_t)blockIdx.z * kch, k_hi = min(d, k_lo + kch);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float m[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) m[a][c] = 0.f;
+    for (int64_t k0 = k_lo; k0 < k_hi; k0 += MX_K) {
+        // 128 rows x 32 columns of each set, 16 values per thread; a warp
+        // reads 32 consecutive columns of one row
+        for (int e = threadIdx.x; e < MX_T * MX_K; e += 256) {
+            const int r = e / MX_K, kk = e - r * MX_K;
+            const int64_t k = k0 + kk;
+            const int64_t ia = i0 + r, jb = j0 + r;
+            sa[kk][r] = (ia < n1 && k < k_hi) ? A[ia * lda + k] : 0.f;
+            sb[kk][r] = (jb < n2 && k < k_hi) ? B[jb * ldb + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < MX_K; ++kk) {
+            float av[8], bv[8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) av[a] = sa[kk][ty + 16 * a];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) bv[c] = sb[kk][tx + 16 * c];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) m[a][c] = fmaxf(m[a][c], fabsf(av[a] - bv[c]));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int64_t i = i0 + ty + 16 * a, j = j0 + tx + 16 * c;
+            if (i < n1 && j < n2 && m[a][c] > 0.f)
+                atomicMax(reinterpret_cast<unsigned int *>(out) + i * n2 + j, __float_as_uint(m[a][c]));
+        }
+}
+
+// ---------------------------------------------------------------------------
+// 3. feature intervals (outward rounding) and the largest lower bound
+// ---------------------------------------------------------------------------
+struct QIv {
+    const float *lo[3], *hi[3];
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *a, double v) {
+    atomicMax(a, (unsigned long long)__double_as_longlong(fmax(v, 0.0)));
+}
+
+__global__ void intervals_kernel(McilWork w, QIv qi, double h, double h2, double g) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t np = w.np;
+    double lb[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) lb[f] = 0.0;
+    if (q < np) {
+        double ql[3] = {0, 0, 0}, qh[3] = {0, 0, 0}, ml[3] = {0, 0, 0}, mh[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (qi.lo[a]) {
+                ql[a] = fmax((double)qi.lo[a][q], 0.0);
+                qh[a] = fmax((double)qi.hi[a][q], 0.0);
+            }
+            // |m32 - M| <= 2^-24 M for the exact maximum M, so M lies in
+            // [m32 / (1 + 2^-24), m32 / (1 - 2^-24)], inside m32 (1 -+ 2^-23)
+            const double m32 = (double)w.mabs[a * np + q];
+            ml[a] = __dmul_rd(m32, 1.0 - 1.1920928955078125e-7);
+            mh[a] = __dmul_ru(m32, 1.0 + 1.1920928955078125e-7);
+        }
+        double lo[NF], hi[NF];
+        lo[0] = ql[0];
+        hi[0] = qh[0];
+        lo[1] = ml[0];
+        hi[1] = mh[0];
+        lo[2] = __dadd_rd(__dadd_rd(__dmul_rd(h2, ql[0]), ql[1]), ql[2]);
+        hi[2] = __dadd_ru(__dadd_ru(__dmul_ru(h2, qh[0]), qh[1]), qh[2]);
+        lo[3] = __dadd_rd(__dadd_rd(__dmul_rd(h, __dsqrt_rd(ql[0])), __dsqrt_rd(ql[1])), __dsqrt_rd(ql[2]));
+        hi[3] = __dadd_ru(__dadd_ru(__dmul_ru(h, __dsqrt_ru(qh[0])), __dsqrt_ru(qh[1])), __dsqrt_ru(qh[2]));
+        lo[4] = fmax(ml[0], fmax(__dmul_rd(g, ml[1]), __dmul_rd(g, ml[2])));
+        hi[4] = fmax(mh[0], fmax(__dmul_ru(g, mh[1]), __dmul_ru(g, mh[2])));
+        lo[5] = __dadd_rd(__dadd_rd(ml[0], __dmul_rd(g, ml[1])), __dmul_rd(g, ml[2]));
+        hi[5] = __dadd_ru(__dadd_ru(mh[0], __dmul_ru(g, mh[1])), __dmul_ru(g, mh[2]));
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (w.mask & (1 << f)) {
+                w.vlo[f * np + q] = lo[f];
+                w.vhi[f * np + q] = hi[f];
+                lb[f] = lo[f];
+            }
+        }
+        w.flag[q] = 0;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        double v = lb[f];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0 && (w.mask & (1 << f))) atomic_max_nonneg(&w.scal[2 + f], v);
+    }
+}
+
+// pairs whose interval may hold a feature's maximum go to the exact queue
+__global__ void candidates_kernel(McilWork w) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= w.np) return;
+    bool cand = false;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        if (w.mask & (1 << f)) cand |= w.vhi[f * w.np + q] >= __longlong_as_double((long long)w.scal[2 + f]);
+    if (cand) {
+        w.flag[q] = 1;
+        const unsigned long long slot = atomicAdd(&w.scal[0], 1ull);
+        w.queue[slot] = q;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4. exact evaluation: one CTA (256 threads) per queued pair
+// ---------------------------------------------------------------------------
+struct Arr3 {
+    const float *a1[3], *a2[3];
+    int64_t ld1[3], ld2[3], d[3];
+};
+
+// canonical squared distance (thread p = partial p) and exact max |x - y|
+__device__ void exact_q_m(const float *x, const float *y, int64_t d, double *sred, double &q, double &m) {
+    double acc = 0.0, mx = 0.0;
+    for (int64_t t = threadIdx.x; t < d; t += 256) {
+        const double df = __dsub_rn((double)x[t], (double)y[t]);
+        acc = __dadd_rn(acc, __dmul_rn(df, df));
+        mx = fmax(mx, fabs(df));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, acc, s);
+        if (lane < s) acc = __dadd_rn(acc, o);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+    }
+    __syncthreads();
+    if (lane == 0) { sred[warp] = acc; sred[8 + warp] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double wv[8];
+        for (int gi = 0; gi < 8; ++gi) wv[gi] = sred[gi];
+        for (int s = 4; s >= 1; s >>= 1)
+            for (int i = 0; i < s; ++i) wv[i] = __dadd_rn(wv[i], wv[i + s]);
+        double mm = 0.0;
+        for (int gi = 0; gi < 8; ++gi) mm = fmax(mm, sred[8 + gi]);
+        sred[16] = wv[0];
+        sred[17] = mm;
+    }
+    __syncthreads();
+    q = sred[16];
+    m = sred[17];
+}
+
+__global__ void __launch_bounds__(256) exact_kernel(McilWork w, Arr3 A, double h, double h2, double g, int pass) {
+    __shared__ double sred[18];
+    const unsigned long long nq = w.scal[0];
+    const unsigned long long first = pass == 0 ? 0ull : w.scal[1];
+    for (unsigned long long e = first + blockIdx.x; e < nq; e += gridDim.x) {
+        const int64_t q = w.queue[e];
+        const int64_t i = q / w.n2, j = q - i * w.n2;
+        double qv[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+        const bool need[3] = {true, (w.mask & 0x3C) != 0, (w.mask & 0x3C) != 0};
+        for (int a = 0; a < 3; ++a)
+            if (need[a]) exact_q_m(A.a1[a] + i * A.ld1[a], A.a2[a] + j * A.ld2[a], A.d[a], sred, qv[a], mv[a]);
+        if (threadIdx.x == 0) {
+            const int64_t np = w.np;
+            double v[NF];
+            v[0] = qv[0];
+            v[1] = mv[0];
+            v[2] = __dadd_rn(__dadd_rn(__dmul_rn(h2, qv[0]), qv[1]), qv[2]);
+            v[3] = __dadd_rn(__dadd_rn(__dmul_rn(h, __dsqrt_rn(qv[0])), __dsqrt_rn(qv[1])), __dsqrt_rn(qv[2]));
+            {
+                const double bx = __dmul_rn(g, mv[1]), by = __dmul_rn(g, mv[2]);
+                const double b = bx > by ? bx : by;
+                v[4] = mv[0] > b ? mv[0] : b;
+            }
+            v[5] = __dadd_rn(__dadd_rn(mv[0], __dmul_rn(g, mv[1])), __dmul_rn(g, mv[2]));
+            for (int f = 0; f < NF; ++f)
+                if (w.mask & (1 << f)) w.vex[f * np + q] = v[f];
+            w.flag[q] = 2;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 5. radii from the exact maxima; thresholds
+// ---------------------------------------------------------------------------
+__global__ void radii_kernel_m(McilWork w, double b, double *radii_out) {
+    // one warp per feature; the maximum is among the queued candidates
+    const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long nq = w.scal[0];
+    if (threadIdx.x == 0) w.scal[1] = nq;   // pass A covers the queue so far
+    if (f >= NF || !(w.mask & (1 << f))) return;
+    double mx = 0.0;
+    for (unsigned long long e = lane; e < nq; e += 32) mx = fmax(mx, w.vex[f * w.np + w.queue[e]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        int slot = 0;
+        for (int f2 = 0; f2 < f; ++f2) slot += (w.mask >> f2) & 1;
+        double *R = radii_out + (int64_t)slot * (w.M + 1);
+        double r = feat_squared(f) ? __dsqrt_rn(mx) : mx;
+        R[0] = r;
+        for (int k = 1; k <= w.M; ++k) {
+            r = __ddiv_rn(r, b);
+            R[k] = r;
+            w.thr[f * 32 + k - 1] = feat_squared(f) ? __dmul_rn(r, r) : r;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 6. classify by interval; undecided pairs join the exact queue
+// ---------------------------------------------------------------------------
+__global__ void classify_kernel_m(McilWork w) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= w.np || w.flag[q] != 0) return;
+    bool undecided = false;
+    for (int f = 0; f < NF && !undecided; ++f) {
+        if (!(w.mask & (1 << f))) continue;
+        const double lo = w.vlo[f * w.np + q], hi = w.vhi[f * w.np + q];
+        for (int k = 0; k < w.M; ++k) {
+            const double T = w.thr[f * 32 + k];
+            if (!(hi < T) && !(lo >= T)) { undecided = true; break; }
+        }
+    }
+    if (undecided) {
+        w.flag[q] = 1;
+        const unsigned long long slot = atomicAdd(&w.scal[0], 1ull);
+        w.queue[slot] = q;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 7. bins (exact value where evaluated, else the interval) and counts
+// ---------------------------------------------------------------------------
+__global__ void bins_kernel_m(McilWork w, uint8_t *__restrict__ bins, int64_t *__restrict__ counts) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int slot = 0;
+    for (int f = 0; f < NF; ++f) {
+        if (!(w.mask & (1 << f))) continue;
+        int K = 0;
+        if (q < w.np) {
+            const bool ex = w.flag[q] == 2;
+            const double v = ex ? w.vex[f * w.np + q] : w.vhi[f * w.np + q];
+            for (int k = 0; k < w.M; ++k)
+                if (v < w.thr[f * 32 + k]) K = k + 1;
+            bins[(int64_t)slot * w.np + q] = (uint8_t)K;
+        }
+        for (int k = 0; k < w.M; ++k) {
+            const unsigned c = __popc(__ballot_sync(0xffffffffu, K > k));
+            if (lane == 0 && c) atomicAdd((unsigned long long *)&counts[(int64_t)slot * w.M + k], (unsigned long long)c);
+        }
+        ++slot;
+    }
+}
+
+__global__ void finish_kernel_m(McilWork w, const unsigned long long *t0, const unsigned long long *t1,
+                                const unsigned long long *t2, int64_t *counts, double *Cv, int K,
+                                int64_t *n_exact) {
+    const bool to = (t0 && *t0) || (t1 && *t1) || (t2 && *t2);
+    if (threadIdx.x == 0 && n_exact) *n_exact = to ? -2 : (int64_t)w.scal[0];
+    if (Cv)
+        for (int e = threadIdx.x; e < K * w.M; e += blockDim.x)
+            Cv[e] = __ddiv_rn((double)counts[e], (double)w.np);
+}
+
+static rd_status mcil_check(int64_t n1, int64_t n2, int G, int nsp, int mask, int M, double b) {
+    if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535) return RD_ERR_INVALID_ARG;
+    if (G < 2 || G > 4096 || nsp < 1 || nsp > 2) return RD_ERR_INVALID_ARG;
+    if (mask < 1 || mask > 63 || M < 1 || M > 32 || !(b > 1.0)) return RD_ERR_INVALID_ARG;
+    return RD_OK;
+}
+
+}  // namespace rdcil
+
+using namespace rdcil;
+
+extern "C" rd_status mcil_workspace_size(int64_t n1, int64_t n2, int32_t G, int32_t n_species, int32_t features,
+                                         int32_t scale, int32_t M, size_t *bytes) {
+    if (!bytes) return RD_ERR_INVALID_ARG;
+    rd_status st = mcil_check(n1, n2, G, n_species, features, M, 2.0);
+    if (st) return st;
+    *bytes = mlayout(n1, n2, G, n_species, features, scale, M, nullptr).bytes;
+    return RD_OK;
+}
+
+extern "C" rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
+                                   int64_t n2, int32_t G, int32_t n_species, int32_t features, int32_t scale,
+                                   double b, int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
+                                   double *d_C, int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream) {
+    rd_status st = mcil_check(n1, n2, G, n_species, features, M, b);
+    if (st) return st;
+    const int64_t d0 = (int64_t)n_species * G * G;
+    if (!d_X1 || !d_X2 || !d_radii_out || !d_bins || !d_counts || !d_work) return RD_ERR_INVALID_ARG;
+    if (ld1 < d0 || ld2 < d0 || (((uintptr_t)d_work) & 255)) return RD_ERR_INVALID_ARG;
+    McilWork w = mlayout(n1, n2, G, n_species, features, scale, M, d_work);
+    if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = __builtin_popcount((unsigned)features);
+    const int64_t np = w.np;
+    const unsigned gp = (unsigned)((np + 255) / 256);
+    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 16 * sizeof(unsigned long long), s));
+    RD_CUDA_TRY(cudaMemsetAsync(d_counts, 0, (size_t)K * M * sizeof(int64_t), s));
+
+    // patterns (scaled copies when asked)
+    const float *P1 = d_X1, *P2 = d_X2;
+    int64_t l1 = ld1, l2 = ld2;
+    if (scale) {
+        minmax_kernel<<<(unsigned)(n1 * n_species), 256, 0, s>>>(d_X1, ld1, G, n_species, w.S1);
+        note_launch();
+        minmax_kernel<<<(unsigned)(n2 * n_species), 256, 0, s>>>(d_X2, ld2, G, n_species, w.S2);
+        note_launch();
+        P1 = w.S1; P2 = w.S2; l1 = l2 = d0;
+    }
+    const bool deriv = (features & 0x3C) != 0;
+    if (deriv) {
+        fd_kernel<<<4 * 148, 256, 0, s>>>(P1, l1, n1, G, n_species, w.Ax1, w.Ay1);
+        note_launch();
+        fd_kernel<<<4 * 148, 256, 0, s>>>(P2, l2, n2, G, n_species, w.Ax2, w.Ay2);
+        note_launch();
+    }
+    Arr3 A{};
+    A.a1[0] = P1; A.a2[0] = P2; A.ld1[0] = l1; A.ld2[0] = l2; A.d[0] = d0;
+    A.a1[1] = w.Ax1; A.a2[1] = w.Ax2; A.a1[2] = w.Ay1; A.a2[2] = w.Ay2;
+    for (int a = 1; a < 3; ++a) { A.ld1[a] = A.ld2[a] = w.de; A.d[a] = w.de; }
+
+    // squared distances: tier-1 intervals
+    QIv qi{};
+    const unsigned long long *tmo[3] = {nullptr, nullptr, nullptr};
+    for (int a = 0; a < 3; ++a) {
+        if (!w.cw[a]) continue;
+        st = cil_tier1_intervals(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2, A.d[a], w.cw[a], w.cw_bytes[a],
+                                 &qi.lo[a], &qi.hi[a], &tmo[a], s);
+        if (st) return st;
+    }
+    // maxima
+    RD_CUDA_TRY(cudaMemsetAsync(w.mabs, 0, sizeof(float) * 3 * np, s));
+    const bool need_m0 = (features & 0x32) != 0, need_md = (features & 0x30) != 0;
+    for (int a = 0; a < 3; ++a) {
+        if (a == 0 ? !need_m0 : !need_md) continue;
+        // K chunks (multiples of 32, at least 64) for about two CTAs per SM
+        const int64_t tiles = ((n1 + MX_T - 1) / MX_T) * ((n2 + MX_T - 1) / MX_T);
+        const int64_t want = (2 * 148 + tiles - 1) / tiles;
+        int64_t kch = (A.d[a] + want - 1) / want;
+        kch = (kch + MX_K - 1) / MX_K * MX_K;
+        if (kch < 2 * MX_K) kch = 2 * MX_K;
+        const int64_t nk = (A.d[a] + kch - 1) / kch;
+        dim3 grid((unsigned)((n2 + MX_T - 1) / MX_T), (unsigned)((n1 + MX_T - 1) / MX_T), (unsigned)nk);
+        maxabs_kernel<<<grid, 256, 0, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2, A.d[a], kch,
+                                           w.mabs + a * np);
+        note_launch();
+    }
+    const double g = (double)(G - 1), h = 1.0 / g, h2 = 1.0 / (g * g);
+    intervals_kernel<<<gp, 256, 0, s>>>(w, qi, h, h2, g);
+    note_launch();
+    candidates_kernel<<<gp, 256, 0, s>>>(w);
+    note_launch();
+    const unsigned ge = 4 * 148;
+    exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 0);
+    note_launch();
+    radii_kernel_m<<<1, 32 * NF, 0, s>>>(w, b, d_radii_out);
+    note_launch();
+    classify_kernel_m<<<gp, 256, 0, s>>>(w);
+    note_launch();
+    exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 1);
+    note_launch();
+    bins_kernel_m<<<gp, 256, 0, s>>>(w, d_bins, d_counts);
+    note_launch();
+    finish_kernel_m<<<1, 256, 0, s>>>(w, tmo[0], tmo[1], tmo[2], d_counts, d_C, K, d_n_exact);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}

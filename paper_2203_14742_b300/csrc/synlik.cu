@@ -17,11 +17,13 @@
 
 namespace rdcil {
 
+static constexpr int SYN_MAX_M = 96;   // components of the (concatenated) CIL vector
+
 __device__ __forceinline__ uint32_t lemire_index(uint64_t seed, uint64_t ctr, uint32_t n) {
     return (uint32_t)__umul64hi(splitmix64_at(seed, ctr), (uint64_t)n);
 }
 
-__global__ void bootstrap_kernel(const uint8_t *__restrict__ bins, int n1, int n2, int M, int T,
+__global__ void bootstrap_kernel(const uint8_t *__restrict__ bins, int nf, int n1, int n2, int M, int T,
                                  uint64_t seed, int64_t *__restrict__ Y) {
     extern __shared__ int32_t sidx[];
     __shared__ unsigned long long cnt[32];
@@ -32,33 +34,38 @@ __global__ void bootstrap_kernel(const uint8_t *__restrict__ bins, int n1, int n
         I[a] = (int32_t)lemire_index(sp, (((uint64_t)t * 2u + 0u) << 32) | (uint64_t)a, (uint32_t)n1);
     for (int b = threadIdx.x; b < n2; b += blockDim.x)
         J[b] = (int32_t)lemire_index(sp, (((uint64_t)t * 2u + 1u) << 32) | (uint64_t)b, (uint32_t)n2);
-    if (threadIdx.x < 32) cnt[threadIdx.x] = 0ull;
-    __syncthreads();
-    const uint8_t *B = bins + (int64_t)p * n1 * n2;
     const int64_t np = (int64_t)n1 * n2;
-    unsigned long long c[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) c[k] = 0ull;
     const int lane = threadIdx.x & 31;
-    // stride so that every warp iteration is uniform (full-warp ballots)
-    for (int64_t base = (int64_t)(threadIdx.x & ~31); base < np; base += blockDim.x) {
-        int64_t q = base + lane;
-        int K = 0;
-        if (q < np) {
-            int a = (int)(q / n2), b = (int)(q - (int64_t)a * n2);
-            K = B[(int64_t)I[a] * n2 + J[b]];
+    const int Mt = nf * M;
+    // one resampled pair of index sets, counted under every feature
+    for (int f = 0; f < nf; ++f) {
+        if (threadIdx.x < 32) cnt[threadIdx.x] = 0ull;
+        __syncthreads();
+        const uint8_t *B = bins + ((int64_t)p * nf + f) * np;
+        unsigned long long c[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) c[k] = 0ull;
+        // stride so that every warp iteration is uniform (full-warp ballots)
+        for (int64_t base = (int64_t)(threadIdx.x & ~31); base < np; base += blockDim.x) {
+            int64_t q = base + lane;
+            int K = 0;
+            if (q < np) {
+                int a = (int)(q / n2), b = (int)(q - (int64_t)a * n2);
+                K = B[(int64_t)I[a] * n2 + J[b]];
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+                if (k < M) c[k] += (unsigned long long)__popc(__ballot_sync(0xffffffffu, K > k));
         }
+        if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k)
-            if (k < M) c[k] += (unsigned long long)__popc(__ballot_sync(0xffffffffu, K > k));
+            for (int k = 0; k < 32; ++k)
+                if (k < M && c[k]) atomicAdd(&cnt[k], c[k]);
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < M) Y[((int64_t)p * T + t) * Mt + f * M + threadIdx.x] = (int64_t)cnt[threadIdx.x];
+        __syncthreads();
     }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-            if (k < M && c[k]) atomicAdd(&cnt[k], c[k]);
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < M) Y[((int64_t)p * T + t) * M + threadIdx.x] = (int64_t)cnt[threadIdx.x];
 }
 
 __global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int64_t np,
@@ -68,23 +75,26 @@ __global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int
                              int32_t *__restrict__ status_all) {
     const int p = blockIdx.x;
     const int64_t *Y = Yall + (int64_t)p * T * M;
-    __shared__ long long S[32];
-    __shared__ double mu[32], cov[32 * 32], L[32 * 32];
-    __shared__ int act[32], idx[32], s_ma, s_st;
+    // M components: S, mu, cov, L, act, idx in dynamic shared memory
+    extern __shared__ double smem_d[];
+    double *mu = smem_d, *cov = mu + M, *L = cov + M * M;
+    long long *S = reinterpret_cast<long long *>(L + M * M);
+    int *act = reinterpret_cast<int *>(S + M), *idx = act + M;
+    __shared__ int s_ma, s_st;
     const int tid = threadIdx.x;
     // mean: S_k / (T n_pairs), S_k an exact integer sum
-    if (tid < M) {
+    for (int k = tid; k < M; k += blockDim.x) {
         long long sum = 0;
         int same = 1;
-        const long long y0 = Y[tid];
+        const long long y0 = Y[k];
         for (int t = 0; t < T; ++t) {
-            const long long yy = Y[(int64_t)t * M + tid];
+            const long long yy = Y[(int64_t)t * M + k];
             sum += yy;
             same &= (yy == y0);
         }
-        S[tid] = sum;
-        mu[tid] = __ddiv_rn(__ll2double_rn(sum), __dmul_rn((double)T, (double)np));
-        act[tid] = same ? 0 : 1;
+        S[k] = sum;
+        mu[k] = __ddiv_rn(__ll2double_rn(sum), __dmul_rn((double)T, (double)np));
+        act[k] = same ? 0 : 1;
     }
     __syncthreads();
     // covariance: (T P_kl - S_k S_l) / (T (T-1) n_pairs^2), exact integers,
@@ -143,7 +153,7 @@ __global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int
             logdet = 2.0 * ld;
             if (y_obs_all) {
                 const double *yo = y_obs_all + (int64_t)p * M;
-                double z[32];
+                double z[SYN_MAX_M];
                 double ff = 0.0;
                 for (int i = 0; i < ma; ++i) {
                     double s = __dsub_rn(yo[idx[i]], mu[idx[i]]);
@@ -165,9 +175,9 @@ __global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int
         cov_all[(int64_t)p * M * M + e] = cov[e];
         chol_all[(int64_t)p * M * M + e] = L[e];
     }
-    if (tid < M) {
-        mu_all[(int64_t)p * M + tid] = mu[tid];
-        active_all[(int64_t)p * M + tid] = (uint8_t)act[tid];
+    for (int k = tid; k < M; k += blockDim.x) {
+        mu_all[(int64_t)p * M + k] = mu[k];
+        active_all[(int64_t)p * M + k] = (uint8_t)act[k];
     }
 }
 
@@ -175,14 +185,14 @@ __global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int
 
 using namespace rdcil;
 
-extern "C" rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2, int32_t M, int32_t T,
-                                  uint64_t seed, int32_t n_problems, const double *d_y_obs, int64_t *d_Y,
-                                  double *d_mu, double *d_cov, double *d_chol, double *d_scalars,
-                                  uint8_t *d_active, int32_t *d_status, void *stream) {
+extern "C" rd_status synlik_stats_multi(const uint8_t *d_bins, int32_t n_feat, int64_t n1, int64_t n2, int32_t M,
+                                        int32_t T, uint64_t seed, int32_t n_problems, const double *d_y_obs,
+                                        int64_t *d_Y, double *d_mu, double *d_cov, double *d_chol, double *d_scalars,
+                                        uint8_t *d_active, int32_t *d_status, void *stream) {
     if (!d_bins || !d_Y || !d_mu || !d_cov || !d_chol || !d_scalars || !d_active || !d_status)
         return RD_ERR_INVALID_ARG;
     if (n1 < 1 || n2 < 1 || n1 + n2 > 49152 || M < 1 || M > 32 || T < 2 || n_problems < 1 ||
-        n_problems > 65535)
+        n_problems > 65535 || n_feat < 1 || n_feat * M > SYN_MAX_M)
         return RD_ERR_INVALID_ARG;
     // the exact covariance numerators T P_kl - S_k S_l stay in 64 bits
     double np = (double)n1 * (double)n2;
@@ -198,10 +208,29 @@ extern "C" rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2,
         }
     }
     dim3 g((unsigned)T, (unsigned)n_problems);
-    bootstrap_kernel<<<g, 256, smem, s>>>(d_bins, (int)n1, (int)n2, M, T, seed, d_Y);
+    bootstrap_kernel<<<g, 256, smem, s>>>(d_bins, n_feat, (int)n1, (int)n2, M, T, seed, d_Y);
     note_launch();
-    stats_kernel<<<(unsigned)n_problems, 256, 0, s>>>(d_Y, M, T, n1 * n2, d_y_obs, d_mu, d_cov, d_chol,
-                                                      d_scalars, d_active, d_status);
+    const int Mt = n_feat * M;
+    const size_t smem2 = sizeof(double) * ((size_t)Mt + 2 * (size_t)Mt * Mt) + sizeof(long long) * Mt +
+                         2 * sizeof(int) * Mt;
+    if (smem2 > 48 * 1024) {
+        static size_t set2 = 0;
+        if (smem2 > set2) {
+            RD_CUDA_TRY(cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem2));
+            set2 = smem2;
+        }
+    }
+    stats_kernel<<<(unsigned)n_problems, 256, smem2, s>>>(d_Y, Mt, T, n1 * n2, d_y_obs, d_mu, d_cov, d_chol,
+                                                          d_scalars, d_active, d_status);
     note_launch();
     return cuda_status(cudaGetLastError());
+}
+
+extern "C" rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2, int32_t M, int32_t T,
+                                  uint64_t seed, int32_t n_problems, const double *d_y_obs, int64_t *d_Y,
+                                  double *d_mu, double *d_cov, double *d_chol, double *d_scalars,
+                                  uint8_t *d_active, int32_t *d_status, void *stream) {
+    return synlik_stats_multi(d_bins, 1, n1, n2, M, T, seed, n_problems, d_y_obs, d_Y, d_mu, d_cov, d_chol,
+                              d_scalars, d_active, d_status, stream);
 }
