@@ -351,7 +351,8 @@ rd_status synlik_stats_multi(const uint8_t *d_bins, int32_t n_feat, int64_t n1, 
  * s[y][x+1] - s[y][x], Dy: (G-1) x G values s[y+1][x] - s[y][x]).  With
  * q0, qx, qy the squared distances of the patterns and of their Dx and Dy
  * patterns in the canonical FP64 order of cil_features, and m0, mx, my the
- * exact maxima of |difference|, feature f (bit f of `features`) is the FP64
+ * maxima of |difference| with each difference in FP64 (rounded to nearest,
+ * as in the squared distance), feature f (bit f of `features`) is the FP64
  * expression (every operation rounded to nearest, no FMA)
  *   0 L2      (eq. norm:L2)         squared value  q0
  *   1 Linf    (eq. norm:Linf)       value          m0
@@ -374,8 +375,9 @@ rd_status synlik_stats_multi(const uint8_t *d_bins, int32_t n_feat, int64_t n1, 
  * timed out; outputs invalid).  Bins and counts equal the definition bit
  * for bit: squared distances come from the tensor-core Gram with rigorous
  * intervals, maxima from an FP32 pass (whose rounding is within 2^-23 of
- * the exact maximum), and every pair whose interval may hold a maximum or
- * meets a threshold is evaluated exactly.
+ * the maximum), and every pair whose interval may hold a maximum or meets
+ * a threshold is re-bounded (FP32 error-free sums, exact maxima) and if
+ * still undecided evaluated in the canonical order.
  * Workspace: d_work (256-byte aligned) of mcil_workspace_size bytes.
  * Limits: 1 <= n1, n2 <= 65535; 2 <= G <= 4096; 1 <= M <= 32; b > 1;
  * 1 <= features <= 63. */

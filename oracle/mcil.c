@@ -31,7 +31,10 @@
  *     rescales its radii), so it equals the single-norm CIL exactly;
  *   - with q0, qx, qy the canonical squared distances (the fixed FP64
  *     order of the CIL) of the patterns and of their Dx and Dy patterns, and
- *     m0, mx, my the exact maxima of |difference|, every feature is one
+ *     m0, mx, my the maxima of |difference| with every difference taken in
+ *     FP64 (the same rounded difference as the squared distance uses: exact
+ *     unless the two numbers' exponents differ by more than 29), every
+ *     feature is one
  *     FP64 expression with each operation rounded:
  *       0 L2        squared value  q0
  *       1 Linf      value          m0
@@ -102,8 +105,8 @@ void orc_fd(const float *X, int64_t n, int G, int nsp, float *Ax, float *Ay)
         }
 }
 
-/* Exact max_t |x_t - y_t| of two FP32 vectors (FP64 differences of FP32
-   numbers are exact). */
+/* max_t |x_t - y_t| of two FP32 vectors, each difference in FP64 (rounded
+   to nearest; exact unless the exponents differ by more than 29). */
 double orc_maxabs(const float *x, const float *y, int64_t d)
 {
     double m = 0.0;

@@ -8,7 +8,8 @@
 // once (Dx: G x (G-1), Dy: (G-1) x G per species).  With q0, qx, qy the
 // canonical squared distances (the fixed FP64 order of the CIL: partial
 // t mod 256, halving trees) of the patterns and of their Dx and Dy patterns,
-// and m0, mx, my the exact maxima of |difference|, the features are
+// and m0, mx, my the maxima of |difference| with each difference in FP64
+// (rounded to nearest, like the squared distance's), the features are
 //   0 L2      squared  q0                                  (eq. norm:L2)
 //   1 Linf    value    m0                                  (eq. norm:Linf)
 //   2 W12     squared  (h^2 q0 + qx) + qy                  (eq. norm:W12)
@@ -23,16 +24,18 @@
 //   1. q0, qx, qy: tier-1 intervals of the CIL (centred bf16 hi/lo split,
 //      tensor-core Gram, rigorous bound), one run per pattern array;
 //   2. m0, mx, my: a tiled SIMT pass (split over K, partial maxima met by
-//      atomicMax) takes max |fl32(a - b)|; rounding to
-//      nearest is monotone, so that is fl32 of the exact maximum M, and
-//      M lies within m32 (1 -+ 2^-23);
+//      atomicMax) takes max |fl32(a - b)|; rounding to nearest is monotone,
+//      so that is fl32 of the exact maximum M, and M (and its FP64 rounding,
+//      the defined value) lies within m32 (1 -+ 2^-23);
 //   3. per pair and feature, an FP64 interval of the feature value by
 //      outward-rounded (_rd / _ru) evaluation of its expression (every
 //      operation is monotone on the non-negative inputs);
 //   4. pairs whose interval may hold a feature's maximum are evaluated
 //      exactly (the canonical FP64 order, one CTA per pair), which fixes R0
-//      and the radii; then pairs whose interval meets a threshold are
-//      evaluated exactly too; everything else is decided by its interval.
+//      and the radii; pairs whose interval meets a threshold get tier 2
+//      (FP32 error-free squared distances with a ~1e-12 bound, exact
+//      maxima) and, if still undecided, the canonical evaluation; every
+//      other pair is decided by its interval.
 #include <cuda_runtime.h>
 #include "common.cuh"
 
@@ -58,7 +61,10 @@ struct McilWork {
     double *vex;                    // [NF][np] exact feature values (where flag == 2)
     uint8_t *flag;                  // [np] 0 interval, 1 queued, 2 exact
     int64_t *queue;                 // [np] pairs to evaluate exactly
-    unsigned long long *scal;       // [0] queue length, [1] pass-A length, [2 + f] max lower bound (bits)
+    unsigned long long *scal;       // [0] queue length; [1] end of the maximum-candidate phase; [2 + f]
+                                    // largest lower bound of feature f (bits); [8] start of the final
+                                    // canonical segment; [9] number of maximum candidates; [10] pairs
+                                    // evaluated in the canonical order
     double *thr;                    // [NF][32] thresholds of the decision (R_k^2 or R_k)
     size_t bytes;
 };
@@ -315,7 +321,8 @@ struct Arr3 {
     int64_t ld1[3], ld2[3], d[3];
 };
 
-// canonical squared distance (thread p = partial p) and exact max |x - y|
+// canonical squared distance (thread p = partial p) and max |x - y| of the
+// FP64 differences
 __device__ void exact_q_m(const float *x, const float *y, int64_t d, double *sred, double &q, double &m) {
     double acc = 0.0, mx = 0.0;
     for (int64_t t = threadIdx.x; t < d; t += 256) {
@@ -348,10 +355,12 @@ __device__ void exact_q_m(const float *x, const float *y, int64_t d, double *sre
     m = sred[17];
 }
 
-__global__ void __launch_bounds__(256) exact_kernel(McilWork w, Arr3 A, double h, double h2, double g, int pass) {
+// queued pairs from scal[start_slot] (0: from the start) to the end
+__global__ void __launch_bounds__(256) exact_kernel(McilWork w, Arr3 A, double h, double h2, double g,
+                                                    int start_slot) {
     __shared__ double sred[18];
     const unsigned long long nq = w.scal[0];
-    const unsigned long long first = pass == 0 ? 0ull : w.scal[1];
+    const unsigned long long first = start_slot == 0 ? 0ull : w.scal[start_slot];
     for (unsigned long long e = first + blockIdx.x; e < nq; e += gridDim.x) {
         const int64_t q = w.queue[e];
         const int64_t i = q / w.n2, j = q - i * w.n2;
@@ -375,8 +384,160 @@ __global__ void __launch_bounds__(256) exact_kernel(McilWork w, Arr3 A, double h
             for (int f = 0; f < NF; ++f)
                 if (w.mask & (1 << f)) w.vex[f * np + q] = v[f];
             w.flag[q] = 2;
+            atomicAdd(&w.scal[10], 1ull);
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4b. tier 2 for the pairs classification left open: per pattern array, the
+//     squared distance from FP32 error-free transformations (s = fl(x - y)
+//     and e with s + e = x - y exactly; s^2 = p + pe exactly; 2 s e rounded;
+//     e^2 dropped; per thread an error-free (H, L) accumulation), as an
+//     interval that also covers the canonical order (the bound of the
+//     single-norm tier 2), and the maximum of |x - y| without FP64 work per
+//     element: |x - y| = |s| + sign(s) e orders like the pair
+//     (|s|, sign(s) e), compared lexicographically in FP32; the winner's
+//     |s| + sign(s) e rounded to FP64 is the defined value (FP64 rounding
+//     is monotone, so it is the maximum of the rounded differences).
+// ---------------------------------------------------------------------------
+struct MaxKey {
+    float a, b;   // |s|, sign(s) e
+};
+__device__ __forceinline__ MaxKey mk_max(MaxKey u, MaxKey v) {
+    return (v.a > u.a || (v.a == u.a && v.b > u.b)) ? v : u;
+}
+
+__device__ void t2_q_m(const float *x, const float *y, int64_t d, double *sred, double &qlo, double &qhi,
+                       double &m) {
+    float H = 0.f, L = 0.f;
+    MaxKey key{0.f, 0.f};
+    for (int64_t t = threadIdx.x; t < d; t += 256) {
+        const float a = __ldg(x + t), bv = __ldg(y + t);
+        const float sd = a - bv;
+        const float bb = sd - a;
+        const float e = (a - (sd - bb)) + (-bv - bb);
+        const float p = sd * sd;
+        const float pe = fmaf(sd, sd, -p);
+        const float cr = (2.f * sd) * e;
+        const float sH = H + p;                  // H += p without error, into (H, L)
+        const float b2 = sH - H;
+        L += (H - (sH - b2)) + (p - b2);
+        H = sH;
+        L += pe + cr;
+        const MaxKey k{fabsf(sd), sd < 0.f ? -e : e};
+        key = mk_max(key, k);
+    }
+    double v = (double)H + (double)L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        const MaxKey k{__shfl_xor_sync(0xffffffffu, key.a, o), __shfl_xor_sync(0xffffffffu, key.b, o)};
+        key = mk_max(key, k);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sred[warp] = v;
+        sred[8 + warp] = (double)key.a + (double)key.b;   // |x - y| of that element, rounded to FP64
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double D2 = 0.0, mm = 0.0;
+        for (int gi = 0; gi < 8; ++gi) {
+            D2 += sred[gi];
+            mm = fmax(mm, sred[8 + gi]);
+        }
+        const double n = (double)((d + 255) / 256);
+        const double rel = 2.0 * (2.9e-14 + 2.0 * n * (n + 4.0) * 3.56e-15 + 300.0 * 1.12e-16 +
+                                  (double)(d / 256 + 10) * 2.23e-16);
+        const double err = rel * fabs(D2) + 1e-300;
+        sred[16] = fmax(D2 - err, 0.0);
+        sred[17] = D2 + err;
+        sred[18] = mm;
+    }
+    __syncthreads();
+    qlo = sred[16];
+    qhi = sred[17];
+    m = sred[18];
+}
+
+// queued pairs from scal[start_slot] (0: from the start) to the end
+__global__ void __launch_bounds__(256) tier2_kernel_m(McilWork w, Arr3 A, double h, double h2, double g,
+                                                      int start_slot) {
+    __shared__ double sred[19];
+    const unsigned long long nq = w.scal[0], first = start_slot == 0 ? 0ull : w.scal[start_slot];
+    const bool deriv = (w.mask & 0x3C) != 0;
+    for (unsigned long long e = first + blockIdx.x; e < nq; e += gridDim.x) {
+        const int64_t q = w.queue[e];
+        const int64_t i = q / w.n2, j = q - i * w.n2;
+        double ql[3] = {0, 0, 0}, qh[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a)
+            if (a == 0 || deriv) t2_q_m(A.a1[a] + i * A.ld1[a], A.a2[a] + j * A.ld2[a], A.d[a], sred, ql[a], qh[a], mv[a]);
+        if (threadIdx.x == 0) {
+            const int64_t np = w.np;
+            double lo[NF], hi[NF];
+            lo[0] = ql[0];
+            hi[0] = qh[0];
+            lo[1] = hi[1] = mv[0];
+            lo[2] = __dadd_rd(__dadd_rd(__dmul_rd(h2, ql[0]), ql[1]), ql[2]);
+            hi[2] = __dadd_ru(__dadd_ru(__dmul_ru(h2, qh[0]), qh[1]), qh[2]);
+            lo[3] = __dadd_rd(__dadd_rd(__dmul_rd(h, __dsqrt_rd(ql[0])), __dsqrt_rd(ql[1])), __dsqrt_rd(ql[2]));
+            hi[3] = __dadd_ru(__dadd_ru(__dmul_ru(h, __dsqrt_ru(qh[0])), __dsqrt_ru(qh[1])), __dsqrt_ru(qh[2]));
+            // the maxima are exact: the max features are evaluated exactly as
+            // in the canonical expression
+            {
+                const double bx = __dmul_rn(g, mv[1]), by = __dmul_rn(g, mv[2]);
+                const double b = bx > by ? bx : by;
+                lo[4] = hi[4] = mv[0] > b ? mv[0] : b;
+            }
+            lo[5] = hi[5] = __dadd_rn(__dadd_rn(mv[0], __dmul_rn(g, mv[1])), __dmul_rn(g, mv[2]));
+            for (int f = 0; f < NF; ++f)
+                if (w.mask & (1 << f)) {
+                    w.vlo[f * np + q] = lo[f];
+                    w.vhi[f * np + q] = hi[f];
+                }
+            w.flag[q] = 3;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void mark_kernel_m(McilWork w, int slot) {
+    if (threadIdx.x == 0) w.scal[slot] = w.scal[0];
+}
+
+// after tier 2 on the maximum candidates: raise each feature's largest
+// lower bound with their tighter intervals
+__global__ void lb2_kernel_m(McilWork w) {
+    const unsigned long long nA = w.scal[9];
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < nA;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        const int64_t q = w.queue[e];
+        for (int f = 0; f < NF; ++f)
+            if (w.mask & (1 << f)) atomic_max_nonneg(&w.scal[2 + f], w.vlo[f * w.np + q]);
+    }
+}
+
+// candidates whose interval of some feature is not a single value and may
+// still hold that feature's maximum are evaluated in the canonical order
+__global__ void cand2_kernel_m(McilWork w) {
+    const unsigned long long nA = w.scal[9];
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < nA;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        const int64_t q = w.queue[e];
+        bool need = false;
+        for (int f = 0; f < NF; ++f) {
+            if (!(w.mask & (1 << f))) continue;
+            const double lo = w.vlo[f * w.np + q], hi = w.vhi[f * w.np + q];
+            need |= (lo < hi) && hi >= __longlong_as_double((long long)w.scal[2 + f]);
+        }
+        if (need) {
+            w.flag[q] = 1;
+            const unsigned long long slot = atomicAdd(&w.scal[0], 1ull);
+            w.queue[slot] = q;
+        }
     }
 }
 
@@ -386,11 +547,18 @@ __global__ void __launch_bounds__(256) exact_kernel(McilWork w, Arr3 A, double h
 __global__ void radii_kernel_m(McilWork w, double b, double *radii_out) {
     // one warp per feature; the maximum is among the queued candidates
     const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned long long nq = w.scal[0];
-    if (threadIdx.x == 0) w.scal[1] = nq;   // pass A covers the queue so far
+    const unsigned long long nq = w.scal[0], nA = w.scal[9];
+    if (threadIdx.x == 0) w.scal[1] = nq;   // end of the candidate phase
     if (f >= NF || !(w.mask & (1 << f))) return;
+    // every pair that may hold the maximum now has its value exactly: from
+    // the canonical pass (flag 2) or a single-value tier-2 interval
     double mx = 0.0;
-    for (unsigned long long e = lane; e < nq; e += 32) mx = fmax(mx, w.vex[f * w.np + w.queue[e]]);
+    for (unsigned long long e = lane; e < nA; e += 32) {
+        const int64_t q = w.queue[e];
+        const double lo = w.vlo[f * w.np + q], hi = w.vhi[f * w.np + q];
+        if (w.flag[q] == 2) mx = fmax(mx, w.vex[f * w.np + q]);
+        else if (lo == hi) mx = fmax(mx, lo);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) {
@@ -410,9 +578,11 @@ __global__ void radii_kernel_m(McilWork w, double b, double *radii_out) {
 // ---------------------------------------------------------------------------
 // 6. classify by interval; undecided pairs join the exact queue
 // ---------------------------------------------------------------------------
-__global__ void classify_kernel_m(McilWork w) {
+// first = 0: pairs still on their tier-1 interval (flag 0); first = 1:
+// pairs tier 2 re-bounded (flag 3).  Undecided ones join the queue.
+__global__ void classify_kernel_m(McilWork w, int second) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= w.np || w.flag[q] != 0) return;
+    if (q >= w.np || w.flag[q] != (second ? 3 : 0)) return;
     bool undecided = false;
     for (int f = 0; f < NF && !undecided; ++f) {
         if (!(w.mask & (1 << f))) continue;
@@ -458,7 +628,7 @@ __global__ void finish_kernel_m(McilWork w, const unsigned long long *t0, const 
                                 const unsigned long long *t2, int64_t *counts, double *Cv, int K,
                                 int64_t *n_exact) {
     const bool to = (t0 && *t0) || (t1 && *t1) || (t2 && *t2);
-    if (threadIdx.x == 0 && n_exact) *n_exact = to ? -2 : (int64_t)w.scal[0];
+    if (threadIdx.x == 0 && n_exact) *n_exact = to ? -2 : (int64_t)w.scal[10];
     if (Cv)
         for (int e = threadIdx.x; e < K * w.M; e += blockDim.x)
             Cv[e] = __ddiv_rn((double)counts[e], (double)w.np);
@@ -555,14 +725,28 @@ extern "C" rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, c
     note_launch();
     candidates_kernel<<<gp, 256, 0, s>>>(w);
     note_launch();
+    mark_kernel_m<<<1, 32, 0, s>>>(w, 9);
+    note_launch();
     const unsigned ge = 4 * 148;
-    exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 0);
+    tier2_kernel_m<<<ge, 256, 0, s>>>(w, A, h, h2, g, 0);
+    note_launch();
+    lb2_kernel_m<<<148, 256, 0, s>>>(w);
+    note_launch();
+    cand2_kernel_m<<<148, 256, 0, s>>>(w);
+    note_launch();
+    exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 9);
     note_launch();
     radii_kernel_m<<<1, 32 * NF, 0, s>>>(w, b, d_radii_out);
     note_launch();
-    classify_kernel_m<<<gp, 256, 0, s>>>(w);
+    classify_kernel_m<<<gp, 256, 0, s>>>(w, 0);
     note_launch();
-    exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 1);
+    tier2_kernel_m<<<ge, 256, 0, s>>>(w, A, h, h2, g, 1);
+    note_launch();
+    mark_kernel_m<<<1, 32, 0, s>>>(w, 8);
+    note_launch();
+    classify_kernel_m<<<gp, 256, 0, s>>>(w, 1);
+    note_launch();
+    exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 8);
     note_launch();
     bins_kernel_m<<<gp, 256, 0, s>>>(w, d_bins, d_counts);
     note_launch();
