@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-FHN, GM, DIFF = 0, 1, 2
+FHN, GM, DIFF, BZ = 0, 1, 2, 3
 
 _lib = None
 

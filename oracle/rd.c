@@ -22,8 +22,11 @@
  *         F_u = Du*Lap(u) + rho*(u^2/v - mu*u),  F_v = Dv*Lap(v) + rho*(u^2 - v).
  *   DIFF: pure diffusion (reaction switched off), a degenerate case used to
  *         pin the discrete Laplacian.
+ *   BZ:   the Brusselator ("BZ" in the paper's Table 1), u = v, v = w,
+ *         Du = nu_1, Dv = nu_2:
+ *         F_u = Du*Lap(u) + A - (B+1)*u + u^2*v,  F_v = Dv*Lap(v) + B*u - u^2*v.
  * Parameter vectors p[4]: FHN (Du, Dv, eps, a); GM (Du, Dv, rho, mu);
- * DIFF (Du, Dv, -, -).
+ * DIFF (Du, Dv, -, -); BZ (Du, Dv, A, B).
  *
  * Grid: G x G nodes, h = 1/(G-1); field layout [species][y][x], row-major.
  * Discrete Laplacian (App. B.1.1):
@@ -53,15 +56,19 @@ int orc_threads(void) {
 #define ORC_FHN 0
 #define ORC_GM 1
 #define ORC_DIFF 2
+#define ORC_BZ 3
 
 /* Homogeneous steady state (Sec. 4.1): FHN (0,0); GM (1/mu, 1/mu^2) with
-   mu_w = 1, evaluated as u0 = 1/mu, v0 = u0*u0; DIFF (0,0). */
+   mu_w = 1, evaluated as u0 = 1/mu, v0 = u0*u0; BZ (A, B/A); DIFF (0,0). */
 void orc_equilibrium(int model, const double *p, double *u0, double *v0)
 {
     if (model == ORC_GM) {
         double a = 1.0 / p[3];
         *u0 = a;
         *v0 = a * a;
+    } else if (model == ORC_BZ) {
+        *u0 = p[2];
+        *v0 = p[3] / p[2];
     } else {
         *u0 = 0.0;
         *v0 = 0.0;
@@ -132,6 +139,11 @@ void orc_rhs(int model, int G, const double *p, const double *w, double *F)
                 double mu_u = p[3] * uk;
                 ru = p[2] * (q - mu_u);
                 rv = p[2] * (uu - vk);
+            } else if (model == ORC_BZ) {
+                double uuv = (uk * uk) * vk;
+                double bu = (p[3] + 1.0) * uk;
+                ru = (p[2] - bu) + uuv;
+                rv = p[3] * uk - uuv;
             } else {
                 ru = 0.0;
                 rv = 0.0;
@@ -233,6 +245,16 @@ static void jt_vec(int model, int G, const double *p, const double *w,
                 sv = dfu_dv * a + dfv_dv * b;
                 g2 = g2 + ((uk * uk) / vk - mu * uk) * a + (uk * uk - vk) * b;
                 g3 = g3 + (-(rho * uk)) * a;
+            } else if (model == ORC_BZ) {
+                double B = p[3];
+                double dfu_du = -(B + 1.0) + 2.0 * uk * vk;
+                double dfu_dv = uk * uk;
+                double dfv_du = B - 2.0 * uk * vk;
+                double dfv_dv = -(uk * uk);
+                su = dfu_du * a + dfv_du * b;
+                sv = dfu_dv * a + dfv_dv * b;
+                g2 = g2 + a;                          /* dF_u/dA = 1, dF_v/dA = 0 */
+                g3 = g3 + (-uk) * a + uk * b;         /* dF_u/dB = -u, dF_v/dB = u */
             } else {
                 su = 0.0;
                 sv = 0.0;
@@ -298,6 +320,10 @@ void orc_jvp(int model, int G, const double *p, const double *w,
                 ou += rho * (2.0 * uk / vk - mu) * a - rho * (uk * uk) / (vk * vk) * b
                       + dtheta[2] * ((uk * uk) / vk - mu * uk) + dtheta[3] * (-(rho * uk));
                 ov += 2.0 * rho * uk * a - rho * b + dtheta[2] * (uk * uk - vk);
+            } else if (model == ORC_BZ) {
+                double B = p[3];
+                ou += (-(B + 1.0) + 2.0 * uk * vk) * a + (uk * uk) * b + dtheta[2] - dtheta[3] * uk;
+                ov += (B - 2.0 * uk * vk) * a - (uk * uk) * b + dtheta[3] * uk;
             }
             out[k] = ou;
             out[cells + k] = ov;

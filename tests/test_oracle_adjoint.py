@@ -12,7 +12,7 @@ import pytest
 import oracle
 import workloads as W
 
-FHN, GM = oracle.FHN, oracle.GM
+FHN, GM, BZ = oracle.FHN, oracle.GM, oracle.BZ
 
 
 def small_problem(model):
@@ -20,9 +20,12 @@ def small_problem(model):
     if model == FHN:
         p = np.array([2.8e-3, 0.05, 10.0, 0.95])
         dt, lo, hi = 2.0 ** -12, -0.05, 0.05
-    else:
+    elif model == GM:
         p = np.array([2.5e-3, 0.05, 1.0, 0.5])
         dt, lo, hi = 2.0 ** -10, 0.0, 0.01
+    else:
+        p = np.array([1.6e-3, 1.32e-2, 4.5, 6.96])
+        dt, lo, hi = 2.0 ** -9, 0.0, 0.01
     w0 = oracle.init_fields(model, G, n_real, p, lo, hi, 4242).astype(np.float64)
     set1, set2 = np.arange(0, 3), np.arange(3, 6)
     wN = oracle.step(model, p, dt, steps, w0)
@@ -36,7 +39,7 @@ def small_problem(model):
                 radii=radii, cot=cot, mask=3)
 
 
-@pytest.mark.parametrize("model", [FHN, GM])
+@pytest.mark.parametrize("model", [FHN, GM, BZ])
 def test_adjoint_matches_central_differences(model):
     P = small_problem(model)
     C, g = oracle.smooth_cil_grad(P["model"], P["p"], P["dt"], P["steps"], P["w0"], P["mask"],
@@ -71,7 +74,7 @@ def test_adjoint_taylor_remainder_is_second_order():
     assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0, rem
 
 
-@pytest.mark.parametrize("model", [FHN, GM])
+@pytest.mark.parametrize("model", [FHN, GM, BZ])
 def test_jvp_vjp_dot_product(model):
     rng = np.random.default_rng(3)
     G = 9

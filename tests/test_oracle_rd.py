@@ -13,7 +13,7 @@ import pytest
 import oracle
 import workloads as W
 
-FHN, GM, DIFF = oracle.FHN, oracle.GM, oracle.DIFF
+FHN, GM, DIFF, BZ = oracle.FHN, oracle.GM, oracle.DIFF, oracle.BZ
 
 
 def dct_mode(G, k, l):
@@ -137,6 +137,26 @@ def test_gm_equilibrium_is_exact_fixed_point():
     assert np.array_equal(w, w0)
 
 
+def test_bz_equilibrium_is_exact_fixed_point():
+    # A = 2, B = 3: the equilibrium (A, B/A) = (2, 1.5) is exact in FP64
+    p = (1.6e-3, 1.32e-2, 2.0, 3.0)
+    u0, v0 = oracle.equilibrium(BZ, p)
+    assert (u0, v0) == (2.0, 1.5)   # (A, B/A), Sec. 4.1
+    w0 = np.stack([np.full((16, 16), u0), np.full((16, 16), v0)])[None]
+    assert np.all(oracle.rhs(BZ, p, w0[0]) == 0.0)
+    w = oracle.step(BZ, p, 2 ** -8, 300, w0)
+    assert np.array_equal(w, w0)
+
+
+def test_bz_kinetics_at_a_worked_point():
+    """F at u = 1, v = 2 with A = 4.5, B = 6.96 and no diffusion: by hand
+    A - (B+1) u + u^2 v = 4.5 - 7.96 + 2 = -1.46 and B u - u^2 v = 4.96."""
+    p = (0.0, 0.0, 4.5, 6.96)
+    w = np.stack([np.ones((4, 4)), np.full((4, 4), 2.0)])
+    F = oracle.rhs(BZ, p, w)
+    assert np.allclose(F[0], -1.46, rtol=1e-15) and np.allclose(F[1], 4.96, rtol=1e-15)
+
+
 def test_residual_zero_at_equilibrium_and_matches_one_step():
     p = W.FHN_THETA0
     assert np.all(oracle.residual(FHN, p, np.zeros((2, 2, 8, 8))) == 0.0)
@@ -159,8 +179,13 @@ def jac(model, p):
     if model == FHN:
         eps, a = a3, a4
         return np.array([[1.0, -1.0], [eps, -eps * a]])
-    rho, mu = a3, a4
-    return rho * np.array([[mu, -mu * mu], [2.0 / mu, -1.0]])
+    if model == GM:
+        rho, mu = a3, a4
+        return rho * np.array([[mu, -mu * mu], [2.0 / mu, -1.0]])
+    # Brusselator at (A, B/A): d/du (A - (B+1) u + u^2 v) = -(B+1) + 2 u v = B - 1,
+    # d/dv = u^2 = A^2; d/du (B u - u^2 v) = B - 2 u v = -B, d/dv = -A^2
+    A, B = a3, a4
+    return np.array([[B - 1.0, A * A], [-B, -A * A]])
 
 
 @pytest.mark.parametrize("model,p,G,k,l,dt", [
@@ -168,6 +193,8 @@ def jac(model, p):
     (FHN, (2.6e-4, 0.052, 9.5, 0.93), 32, 5, 0, 2 ** -9),
     (GM, (2.5e-4, 0.01, 1.0, 0.5), 32, 4, 1, 2 ** -8),
     (GM, (2.5e-4, 0.01, 1.0, 0.53), 16, 2, 2, 2 ** -8),
+    (BZ, W.BZ_THETA0, 32, 3, 1, 2 ** -8),
+    (BZ, (1.6e-3, 1.32e-2, 4.4, 7.1), 16, 1, 1, 2 ** -8),
 ])
 def test_linear_dispersion(model, p, G, k, l, dt):
     """A small perturbation along DCT mode (k,l) evolves by the matrix power
@@ -188,7 +215,7 @@ def test_linear_dispersion(model, p, G, k, l, dt):
     assert np.abs(got - cn).max() < 1e-5 * max(1.0, scale) + 1e-7 * scale
 
 
-@pytest.mark.parametrize("cfg", ["c1", "c2", "c3", "c4", "c5"])
+@pytest.mark.parametrize("cfg", ["c1", "c2", "c3", "c4", "c5", "c6"])
 def test_drawn_parameters_are_turing_unstable(cfg):
     """Every drawn parameter vector has some non-constant discrete mode with
     Re lambda > 0 and a stable (or, at a = 1, marginal) constant mode: the
@@ -210,7 +237,7 @@ def test_drawn_parameters_are_turing_unstable(cfg):
 
 
 def test_explicit_time_step_below_diffusion_limit():
-    for cfg in ("c1", "c2", "c3", "c4", "c5"):
+    for cfg in ("c1", "c2", "c3", "c4", "c5", "c6"):
         for g in W.config(cfg, steps_scale=1e-6)["groups"]:
             h2 = 1.0 / (g["G"] - 1) ** 2
             assert g["dt"] < h2 / (4 * max(g["params"][0], g["params"][1]))

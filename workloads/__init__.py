@@ -24,6 +24,8 @@ Workloads (sizes follow the paper's Table 1 models and the hot-path configs):
       2^-12 (128^2); GM 2^-8 (64^2), 2^-10 (128^2).
   c5  FHN 64x64, 32 realisations (2 x 16), dt 2^-10, 5000 steps, M = 16,
       smoothed CIL with tau_k = 0.05 R_k, cotangent 1/M.
+  c6  Brusselator ("BZ", Table 1) 64x64, 2 sets x 64, dt 2^-8, 25600 steps
+      (T = 100), both species (d = 8192), noise U(0, 0.01), M = 16.
   glarge  the paper's SCIL scale (N_syn = 1000, Sec. 5.3): 2 sets x 1024
       patterns of d = 32768 for the Gram kernel alone.
 """
@@ -31,7 +33,7 @@ import math
 
 import numpy as np
 
-FHN, GM, DIFF = 0, 1, 2
+FHN, GM, DIFF, BZ = 0, 1, 2, 3
 
 SEED_BASE = 0x2203147420000000
 
@@ -39,6 +41,7 @@ SEED_BASE = 0x2203147420000000
 # species order (u, v); see the model mapping in oracle/rd.c.
 FHN_THETA0 = (2.8e-4, 0.05, 10.0, 1.0)      # Du = nu_2, Dv = nu_1, eps, a = alpha
 GM_THETA0 = (2.5e-4, 0.01, 1.0, 0.5)        # Du = nu_1, Dv = nu_2, rho, mu = mu_v
+BZ_THETA0 = (1.6e-3, 1.32e-2, 4.5, 6.96)    # Brusselator: Du = nu_1, Dv = nu_2, A, B
 
 
 def seed_of(cfg_index: int) -> int:
@@ -51,6 +54,8 @@ def draw_params(model: int, seed: int, n: int = 1):
     FHN: Du, Dv, eps within +-10 % of Table 1; a in [0.9, 1.0] (a < 1 makes
     the equilibrium strictly stable to homogeneous perturbations).
     GM:  mu within +-10 % of 0.5; rho = 1; Table 1 diffusions.
+    BZ:  A in [4.3, 4.6], B in [6.9, 7.2] around Table 1's (4.5, 6.96);
+         Table 1 diffusions.
     The oracle test suite checks every drawn vector for a diffusion-driven
     instability on the discrete grid.
     """
@@ -66,6 +71,12 @@ def draw_params(model: int, seed: int, n: int = 1):
         elif model == GM:
             mu = GM_THETA0[3] * rng.uniform(0.9, 1.1)
             out.append((GM_THETA0[0], GM_THETA0[1], 1.0, mu))
+        elif model == BZ:
+            # A in [4.3, 4.6], B in [6.9, 7.2]: above the Turing threshold
+            # (1 + A sqrt(Du/Dv))^2 <= 6.77 and below the Hopf value 1 + A^2
+            A = rng.uniform(4.3, 4.6)
+            B = rng.uniform(6.9, 7.2)
+            out.append((BZ_THETA0[0], BZ_THETA0[1], A, B))
         else:
             raise ValueError("model")
     return out
@@ -118,6 +129,13 @@ def config(name: str, steps_scale: float = 1.0):
                                         s + 1000 * (k + 1) + j, mask))
                 k += 1
         return {"name": name, "groups": groups, "n1": 64, "n2": 64, "M": 16, "b": 1.3,
+                "T_res": 200, "seed": s}
+    if name == "c6":
+        s = seed_of(6)
+        p = draw_params(BZ, s)[0]
+        # Table 1: T = 100 on 64 x 64; h^2 / (4 Dv) = 4.8e-3, so dt = 2^-8
+        g = group(BZ, 64, 128, p, 2.0 ** -8, steps(25600), (0.0, 0.01), s, 3)
+        return {"name": name, "groups": [g], "n1": 64, "n2": 64, "M": 16, "b": 1.3,
                 "T_res": 200, "seed": s}
     if name == "c5":
         s = seed_of(5)
