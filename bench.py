@@ -37,8 +37,9 @@ import workloads as W  # noqa: E402
 # FP32-pipe instructions of the implemented update per cell-update: two
 # neighbour sums (3 + 3), then FHN u 6, v 3; GM u 9, v 5 (deviation form;
 # the division's reciprocal runs on the MUFU pipe and is not counted);
-# DIFF 2 + 2.
-FP32_INST_PER_CELL = {W.FHN: 15, W.GM: 20, W.DIFF: 10}
+# BZ u 8 (a + u0, U*U, *b, fma P, e0 + P, fma f, fma, fma), v 6 (-e0 - P,
+# fma g, fma, fma, fma -4, ...); DIFF 2 + 2.
+FP32_INST_PER_CELL = {W.FHN: 15, W.GM: 20, W.DIFF: 10, W.BZ: 22}
 
 # DRAM bytes (read + write) of one stepper launch on this workload, from the
 # ncu capture summarised in profiles/rd_resident_scalar_kernel_fhn64_c2.md,
@@ -361,7 +362,9 @@ def run_ours(args, rank, world, local_rank):
                       "(2x10^4 steps) in one persistent launch, 2 x 64 sets per vector, M=16, 200 resamples",
                 "c1": "c1: FHN 32x32, 2 x 16, 2000 steps, d=2048, M=8, 50 resamples",
                 "c3": "c3: GM 128x128, 2 x 256, 2x10^4 steps, d=32768, M=16, 200 resamples",
-                "c5": "c5: FHN 64x64, 32 realisations, 5000 steps"}[args.config]
+                "c5": "c5: FHN 64x64, 32 realisations, 5000 steps",
+                "c6": "c6: Brusselator 64x64, 2 sets x 64 realisations, 25600 Euler steps (T = 100), both "
+                      "species d=8192, M=16, b=1.3, 200 resamples"}[args.config]
     out = {
         "metric": "RD cell-updates/s + CIL pair-dists/s at stated tol; % HBM/tensor roofline",
         "value": value,

@@ -54,10 +54,15 @@ typedef int32_t rd_status;
  *            u_t = Du Lap u + rho (u^2/v - mu u),  v_t = Dv Lap v + rho (u^2 - v)
  *          params = (Du, Dv, rho, mu); equilibrium (1/mu, 1/mu^2).
  *  RD_DIFF pure diffusion (reaction off), params = (Du, Dv, -, -); a
- *          degenerate case with closed-form solutions, used for checks. */
+ *          degenerate case with closed-form solutions, used for checks.
+ *  RD_BZ   the Brusselator ("BZ" in the paper's Table 1), eq. (bzSystem)
+ *          with u = v, v = w:
+ *            u_t = Du Lap u + A - (B+1) u + u^2 v,  v_t = Dv Lap v + B u - u^2 v
+ *          params = (Du, Dv, A, B); equilibrium (A, B/A). */
 #define RD_FHN 0
 #define RD_GM 1
 #define RD_DIFF 2
+#define RD_BZ 3
 
 /* group flags */
 #define RD_GROUP_ADJOINT 1   /* reserve checkpoint memory for rd_adjoint */
@@ -71,7 +76,7 @@ typedef int32_t rd_status;
  * library does not check stability, but a blow-up is reported as
  * RD_ERR_NONFINITE. */
 typedef struct rd_group {
-    int32_t model;          /* RD_FHN / RD_GM / RD_DIFF */
+    int32_t model;          /* RD_FHN / RD_GM / RD_DIFF / RD_BZ */
     int32_t G;              /* grid side */
     int32_t n_real;         /* realisations in this group (>= 1) */
     int32_t flags;          /* RD_GROUP_* */
@@ -168,7 +173,7 @@ rd_status rd_integrate_f64(rd_handle *h, double *d_fields64, double *d_tmp64,
  * rd_autotune: time every variant on the largest group of each (model, G)
  *   class present in h for `steps` Euler steps, keep the fastest, then
  *   re-initialise d_fields (rd_reinit).  Synchronous.  chosen (nullable,
- *   host int32[9]) receives the choice per [model][G index 32/64/128]. */
+ *   host int32[12]) receives the choice per [model][G index 32/64/128]. */
 int32_t rd_n_variants(void);
 rd_status rd_set_variant(int32_t model, int32_t G, int32_t variant);
 int32_t rd_get_variant(int32_t model, int32_t G);

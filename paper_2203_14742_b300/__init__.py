@@ -218,7 +218,7 @@ class Simulation:
 
     def autotune(self, steps=200):
         """Pick the fastest tile shape per (model, G); re-initialises the fields."""
-        chosen = (C.c_int32 * 9)(*([-1] * 9))
+        chosen = (C.c_int32 * 12)(*([-1] * 12))
         _check("rd_autotune", lib().rd_autotune(self.handle, _ptr(self.fields), int(steps), _stream(),
                                                 chosen))
         return list(chosen)

@@ -173,6 +173,15 @@ __device__ __forceinline__ void adj_cell(float u, float v, float lu, float lv, f
         lvn = fmaf(c.cv, Llv, fmaf(c.k2, fmaf(-q * q, lu, -lv), lv));
         s[2] = fmaf(fmaf(u, q, -c.k3 * u), lu, fmaf(fmaf(u, u, -v), lv, s[2]));
         s[3] = fmaf(u, lu, s[3]);                    // u lambda_u   (x -rho dt)
+    } else if (MODEL == RD_BZ) {
+        // J^T: [2uv - (B+1), B - 2uv; u^2, -u^2]; with dl = lambda_u - lambda_v
+        // the u row is (2uv - B) dl - lambda_u and the v row u^2 dl
+        const float dl = lu - lv;
+        const float t = fmaf(2.f * u, v, -c.k3);
+        lun = fmaf(c.cu, Llu, fmaf(c.k1, fmaf(t, dl, -lu), lu));
+        lvn = fmaf(c.cv, Llv, fmaf(c.k1, (u * u) * dl, lv));
+        s[2] = s[2] + lu;                            // dF/dA = (1, 0)       (x dt)
+        s[3] = fmaf(-u, dl, s[3]);                   // dF/dB = (-u, u)      (x dt)
     } else {
         lun = fmaf(c.cu, Llu, lu);
         lvn = fmaf(c.cv, Llv, lv);
@@ -357,6 +366,7 @@ extern "C" rd_status rd_adjoint(rd_handle *hh, int32_t group, const float *d_fie
     cf.sc[1] = g.dt * h2;
     if (g.model == RD_FHN) { cf.sc[2] = g.dt; cf.sc[3] = -g.p[2] * g.dt; }
     else if (g.model == RD_GM) { cf.sc[2] = g.dt; cf.sc[3] = -g.p[2] * g.dt; }
+    else if (g.model == RD_BZ) { cf.sc[2] = g.dt; cf.sc[3] = g.dt; }
     else { cf.sc[2] = 0.0; cf.sc[3] = 0.0; }
     for (int64_t q = nseg - 1; q >= 0; --q) {
         int64_t len = std::min(C, N - q * C);
@@ -367,6 +377,7 @@ extern "C" rd_status rd_adjoint(rd_handle *hh, int32_t group, const float *d_fie
         switch (g.model) {
             case RD_FHN: st = reverse_G<RD_FHN>(g, a.traj, ts, len, a.lam, cf, d_grad, active, s); break;
             case RD_GM: st = reverse_G<RD_GM>(g, a.traj, ts, len, a.lam, cf, d_grad, active, s); break;
+            case RD_BZ: st = reverse_G<RD_BZ>(g, a.traj, ts, len, a.lam, cf, d_grad, active, s); break;
             default: st = reverse_G<RD_DIFF>(g, a.traj, ts, len, a.lam, cf, d_grad, active, s); break;
         }
         if (st) return st;

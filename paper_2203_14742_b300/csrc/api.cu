@@ -23,13 +23,14 @@ static rd_status validate_groups(const rd_group *groups, int32_t n_groups) {
     std::vector<std::pair<int64_t, int64_t>> iv;
     for (int32_t i = 0; i < n_groups; ++i) {
         const rd_group &g = groups[i];
-        if (g.model != RD_FHN && g.model != RD_GM && g.model != RD_DIFF) return RD_ERR_INVALID_ARG;
+        if (g.model != RD_FHN && g.model != RD_GM && g.model != RD_DIFF && g.model != RD_BZ) return RD_ERR_INVALID_ARG;
         if (g.G != 32 && g.G != 64 && g.G != 128) return RD_ERR_INVALID_ARG;
         if (g.n_real < 1 || g.n_steps < 0 || g.field_offset < 0 || (g.field_offset & 3)) return RD_ERR_INVALID_ARG;
         if (!(g.dt > 0.0) || !std::isfinite(g.dt)) return RD_ERR_INVALID_ARG;
         for (double p : g.params)
             if (!std::isfinite(p)) return RD_ERR_INVALID_ARG;
         if (g.model == RD_GM && !(g.params[3] != 0.0)) return RD_ERR_INVALID_ARG;
+        if (g.model == RD_BZ && !(g.params[2] != 0.0)) return RD_ERR_INVALID_ARG;
         if (!(g.noise_lo <= g.noise_hi)) return RD_ERR_INVALID_ARG;
         int64_t len = (int64_t)g.n_real * 2 * g.G * g.G;
         iv.emplace_back(g.field_offset, g.field_offset + len);
@@ -212,14 +213,14 @@ extern "C" rd_status rd_variant_shape(int32_t G, int32_t variant, int32_t *shape
 }
 
 extern "C" rd_status rd_set_variant(int32_t model, int32_t G, int32_t variant) {
-    if (model < 0 || model > 2 || (G != 32 && G != 64 && G != 128) || variant < 0 || variant >= n_variants())
+    if (model < 0 || model > 3 || (G != 32 && G != 64 && G != 128) || variant < 0 || variant >= n_variants())
         return RD_ERR_INVALID_ARG;
     set_variant_choice(model, G, variant);
     return RD_OK;
 }
 
 extern "C" int32_t rd_get_variant(int32_t model, int32_t G) {
-    if (model < 0 || model > 2 || (G != 32 && G != 64 && G != 128)) return -1;
+    if (model < 0 || model > 3 || (G != 32 && G != 64 && G != 128)) return -1;
     return get_variant_choice(model, G);
 }
 
@@ -231,7 +232,7 @@ extern "C" rd_status rd_autotune(rd_handle *hh, float *d_fields, int64_t steps, 
     RD_CUDA_TRY(cudaEventCreate(&e0));
     RD_CUDA_TRY(cudaEventCreate(&e1));
     rd_status st = RD_OK;
-    for (int model = 0; model < 3 && st == RD_OK; ++model)
+    for (int model = 0; model < 4 && st == RD_OK; ++model)
         for (int G : {32, 64, 128}) {
             // the largest group of this (model, G) class stands for the class
             int best_g = -1;

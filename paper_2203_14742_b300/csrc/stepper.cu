@@ -50,6 +50,10 @@ static void equilibrium(const GroupDev &g, double &u0, double &v0) {
         volatile double a = 1.0 / g.p[3];
         u0 = a;
         v0 = a * a;
+    } else if (g.model == RD_BZ) {
+        volatile double q = g.p[3] / g.p[2];
+        u0 = g.p[2];
+        v0 = q;
     } else {
         u0 = 0.0;
         v0 = 0.0;
@@ -86,6 +90,10 @@ __device__ __forceinline__ void rhs_f64(double u, double v, double nu, double su
         double uu = u * u;
         ru = p[2] * (uu / v - p[3] * u);
         rv = p[2] * (uu - v);
+    } else if (MODEL == RD_BZ) {
+        double uuv = (u * u) * v;
+        ru = (p[2] - (p[3] + 1.0) * u) + uuv;
+        rv = p[3] * u - uuv;
     } else {
         ru = 0.0;
         rv = 0.0;
@@ -267,7 +275,7 @@ template <int G> constexpr Variant var_of(int i) {
     return G == 32 ? VAR32[i] : (G == 64 ? VAR64[i] : VAR128[i]);
 }
 
-static int g_choice[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // [model][G index]
+static int g_choice[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // [model][G index]
 static inline int gidx(int G) { return G == 32 ? 0 : (G == 64 ? 1 : 2); }
 
 template <int MODEL, int G, int VI, bool RECORD>
@@ -339,6 +347,7 @@ static rd_status dispatch_model(const GroupDev &g, float *fields, int64_t steps,
         case RD_FHN: return dispatch_G<RD_FHN, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
         case RD_GM: return dispatch_G<RD_GM, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
         case RD_DIFF: return dispatch_G<RD_DIFF, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
+        case RD_BZ: return dispatch_G<RD_BZ, RECORD>(g, fields, steps, residual, status, traj, traj_stride, s, vi);
         default: return RD_ERR_UNSUPPORTED;
     }
 }
@@ -429,6 +438,7 @@ rd_batch_kernel(float *__restrict__ fields, const BatchGroup *__restrict__ group
         switch (g.model) {
             case RD_FHN: batch_item<RD_FHN>(fields, g, w.real, steps, res, status, sm); break;
             case RD_GM: batch_item<RD_GM>(fields, g, w.real, steps, res, status, sm); break;
+            case RD_BZ: batch_item<RD_BZ>(fields, g, w.real, steps, res, status, sm); break;
             default: batch_item<RD_DIFF>(fields, g, w.real, steps, res, status, sm); break;
         }
         __syncthreads();
@@ -545,6 +555,7 @@ rd_status launch_integrate_reference(const GroupDev &g, float *fields, float *tm
             switch (g.model) {
                 case RD_FHN: rd_reference_step_kernel<RD_FHN><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
                 case RD_GM: rd_reference_step_kernel<RD_GM><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
+                case RD_BZ: rd_reference_step_kernel<RD_BZ><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
                 default: rd_reference_step_kernel<RD_DIFF><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
             }
         }
@@ -591,6 +602,11 @@ __global__ void rd_f64_step_kernel(const double *__restrict__ src, double *__res
         double q = __ddiv_rn(uu, vk);
         ru = __dmul_rn(p2, __dsub_rn(q, __dmul_rn(p3, uk)));
         rv = __dmul_rn(p2, __dsub_rn(uu, vk));
+    } else if (model == RD_BZ) {
+        double uuv = __dmul_rn(__dmul_rn(uk, uk), vk);
+        double bu = __dmul_rn(__dadd_rn(p3, 1.0), uk);
+        ru = __dadd_rn(__dsub_rn(p2, bu), uuv);
+        rv = __dsub_rn(__dmul_rn(p3, uk), uuv);
     } else {
         ru = 0.0;
         rv = 0.0;

@@ -113,7 +113,7 @@ __device__ __forceinline__ void row_west_east(int tx, float first, float last, f
 
 // FP32 kinetics with coefficients folded with dt and (G-1)^2 on the host:
 //   cu = Du dt (G-1)^2, cv = Dv dt (G-1)^2, k1 = dt,
-//   FHN: k2 = eps dt, k3 = a;   GM: k2 = rho dt, k3 = mu.
+//   FHN: k2 = eps dt, k3 = a;   GM: k2 = rho dt, k3 = mu;   BZ: k3 = B.
 // GM is stepped in deviation form (see euler_cell): u0, v0 = the FP32
 // equilibrium (1/mu, 1/mu^2), tu0 = 2 u0, e0 = u0 - mu v0 and e1 = u0^2 - v0
 // (evaluated in FP64, rounded once; both are 0 when 1/mu is exact).
@@ -123,10 +123,16 @@ __device__ __forceinline__ void row_west_east(int tx, float first, float last, f
 // (v relaxes quickly, so the rounding of be does not accumulate; u keeps
 // the form u + increments, because a rounded weight near 1 on u itself
 // would bias every step the same way.)
+// BZ (Brusselator) is stepped in deviation form too: u0 = A, v0 = the FP32
+// B/A, and with a = u - u0, b = v - v0, P = v0 a^2 + (u0 + a)^2 b:
+//   f = e0 + c1 a + P,   g = -e0 + c2 a - P,
+//   e0 = A (A v0 - B), c1 = 2 A v0 - (B + 1), c2 = B - 2 A v0   (FP64, rounded once)
+// (exact in real arithmetic; e0 = 0 and c1 = B - 1, c2 = -B when B/A is exact).
 struct CoefF {
     float cu, cv, k1, k2, k3;
     float u0, v0, tu0, e0, e1;
     float be, k2e1;
+    float c1, c2;
 };
 
 inline CoefF make_coef(const GroupDev &g) {
@@ -137,11 +143,20 @@ inline CoefF make_coef(const GroupDev &g) {
     c.cu = (float)cu;
     c.cv = (float)cv;
     c.k1 = (float)g.dt;
-    if (g.model == RD_FHN || g.model == RD_GM) {
+    if (g.model == RD_FHN || g.model == RD_GM || g.model == RD_BZ) {
         c.k2 = (float)(g.p[2] * g.dt);
         c.k3 = (float)g.p[3];
     }
     if (g.model == RD_FHN) c.be = (float)(1.0 - 4.0 * cv - g.p[2] * g.dt * g.p[3]);
+    if (g.model == RD_BZ) {
+        const double A = g.p[2], B = g.p[3];
+        const float v0 = (float)(B / A);
+        c.u0 = (float)A;
+        c.v0 = v0;
+        c.e0 = (float)(A * (A * (double)v0 - B));
+        c.c1 = (float)(2.0 * A * (double)v0 - (B + 1.0));
+        c.c2 = (float)(B - 2.0 * A * (double)v0);
+    }
     if (g.model == RD_GM) {
         double mu = g.p[3], k2 = g.p[2] * g.dt;
         float u0 = (float)(1.0 / mu);
@@ -162,11 +177,11 @@ inline CoefF make_coef(const GroupDev &g) {
 // (u - u0, v - v0) from the FP32 equilibrium for GM.  These convert.
 template <int MODEL>
 __device__ __forceinline__ void to_state(float &u, float &v, const CoefF &c) {
-    if (MODEL == RD_GM) { u -= c.u0; v -= c.v0; }
+    if (MODEL == RD_GM || MODEL == RD_BZ) { u -= c.u0; v -= c.v0; }
 }
 template <int MODEL>
 __device__ __forceinline__ void from_state(float &u, float &v, const CoefF &c) {
-    if (MODEL == RD_GM) { u += c.u0; v += c.v0; }
+    if (MODEL == RD_GM || MODEL == RD_BZ) { u += c.u0; v += c.v0; }
 }
 
 // One explicit Euler update of a node given the neighbour sums
@@ -194,6 +209,15 @@ __device__ __forceinline__ void euler_cell(float u, float v, float su, float sv,
         float f = __fdividef(U * t, V);
         un = fmaf(c.cu, fmaf(-4.f, a, su), fmaf(c.k2, f, a));
         vn = fmaf(c.be, b, fmaf(c.k2 * a, a + c.tu0, fmaf(c.cv, sv, c.k2e1)));
+    } else if (MODEL == RD_BZ) {
+        // deviation form (see CoefF): f = e0 + c1 a + P, g = -e0 + c2 a - P
+        const float a = u, b = v;
+        const float U = a + c.u0;
+        const float P = fmaf(c.v0 * a, a, (U * U) * b);
+        const float f = fmaf(c.c1, a, c.e0 + P);
+        const float g = fmaf(c.c2, a, -c.e0 - P);
+        un = fmaf(c.cu, fmaf(-4.f, a, su), fmaf(c.k1, f, a));
+        vn = fmaf(c.cv, fmaf(-4.f, b, sv), fmaf(c.k1, g, b));
     } else {
         un = fmaf(c.cu, fmaf(-4.f, u, su), u);
         vn = fmaf(c.cv, fmaf(-4.f, v, sv), v);
@@ -409,12 +433,12 @@ __device__ __forceinline__ void tile2_store(float *base, int tx, int ty, const f
 
 template <int MODEL>
 __device__ __forceinline__ float2 to_state2(float2 w, const CoefF &c) {
-    if (MODEL == RD_GM) return __fadd2_rn(w, make_float2(-c.u0, -c.v0));
+    if (MODEL == RD_GM || MODEL == RD_BZ) return __fadd2_rn(w, make_float2(-c.u0, -c.v0));
     return w;
 }
 template <int MODEL>
 __device__ __forceinline__ float2 from_state2(float2 w, const CoefF &c) {
-    if (MODEL == RD_GM) return __fadd2_rn(w, make_float2(c.u0, c.v0));
+    if (MODEL == RD_GM || MODEL == RD_BZ) return __fadd2_rn(w, make_float2(c.u0, c.v0));
     return w;
 }
 
@@ -435,6 +459,10 @@ __device__ __forceinline__ float2 euler2(float2 C, float2 S, const CoefF &c) {
         float f = __fdividef(U * t, V);
         return make_float2(fmaf(c.cu, fmaf(-4.f, a, S.x), fmaf(c.k2, f, a)),
                            fmaf(c.be, b, fmaf(c.k2 * a, a + c.tu0, fmaf(c.cv, S.y, c.k2e1))));
+    } else if (MODEL == RD_BZ) {
+        float un, vn;
+        euler_cell<RD_BZ>(C.x, C.y, S.x, S.y, c, un, vn);
+        return make_float2(un, vn);
     } else {
         const float2 L = __ffma2_rn(make_float2(-4.f, -4.f), C, S);
         return __ffma2_rn(make_float2(c.cu, c.cv), L, C);

@@ -56,6 +56,7 @@ def compare(sim, f0, w0, set1, set2, radii, cot, model, par, dt, steps, mask, ta
 @pytest.mark.parametrize("model,par,dt,noise", [
     (W.FHN, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -8, (-0.05, 0.05)),
     (W.GM, (2.5e-4, 0.01, 1.0, 0.5), 2 ** -8, (0.0, 0.01)),
+    (W.BZ, W.BZ_THETA0, 2 ** -8, (0.0, 0.01)),
 ])
 def test_adjoint_small_matches_oracle(p, model, par, dt, noise):
     steps = 300

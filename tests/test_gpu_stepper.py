@@ -45,6 +45,8 @@ CASES = [
     (W.GM, 128, 2, (2.5e-4, 0.01, 1.0, 0.48), 2 ** -10, (0.0, 0.01)),
     (W.FHN, 128, 2, (2.8e-4, 0.05, 10.0, 0.97), 2 ** -12, (-0.05, 0.05)),
     (W.DIFF, 64, 2, (3e-3, 1e-3), 2 ** -12, (-1.0, 1.0)),
+    (W.BZ, 64, 3, W.BZ_THETA0, 2 ** -8, (0.0, 0.01)),
+    (W.BZ, 32, 4, (1.6e-3, 1.32e-2, 4.4, 7.1), 2 ** -8, (0.0, 0.01)),
 ]
 
 
@@ -142,7 +144,8 @@ def test_split_integration_is_bit_identical(p):
 
 
 @pytest.mark.parametrize("model,par,x0", [(W.FHN, (2.8e-4, 0.05, 10.0, 1.0), (0.0, 0.0)),
-                                          (W.GM, (2.5e-4, 0.01, 1.0, 0.5), (2.0, 4.0))])
+                                          (W.GM, (2.5e-4, 0.01, 1.0, 0.5), (2.0, 4.0)),
+                                          (W.BZ, (1.6e-3, 1.32e-2, 2.0, 3.0), (2.0, 1.5))])
 def test_equilibrium_fixed_point(p, model, par, x0):
     sim = p.Simulation([mkgroup(p, model, 64, 2, par, 2 ** -10, 500, (0.0, 0.0), 1)])
     f0 = sim.fields.clone()
@@ -191,6 +194,7 @@ def test_c2_full_size_error_curve(p):
     (W.FHN, 64, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -10, (-0.05, 0.05)),
     (W.GM, 128, (2.5e-4, 0.01, 1.0, 0.47), 2 ** -10, (0.0, 0.01)),
     (W.FHN, 32, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -8, (-0.05, 0.05)),
+    (W.BZ, 64, W.BZ_THETA0, 2 ** -8, (0.0, 0.01)),
 ])
 def test_tile_variants_bit_identical(p, model, G, par, dt, noise):
     """Tile shape only changes data movement: every variant gives the same bits."""
@@ -233,6 +237,22 @@ def test_c3_sample_gm128_full_horizon(p):
     assert err <= FIELD_TOL
 
 
+def test_c6_sample_bz64_full_horizon(p):
+    """c6 (Brusselator 64x64, 25600 steps of 2^-8, T = 100 as in Table 1): two
+    realisations against the FP64 oracle over the full horizon."""
+    cfg = W.config("c6")
+    g = dict(cfg["groups"][0])
+    g["n_real"] = 2
+    sim = p.Simulation([p.Group.from_dict(g)])
+    f0 = sim.group_fields(0).cpu().numpy().astype(np.float64)
+    res = sim.integrate()
+    assert sim.sync_status() == 0
+    ref = oracle.step(g["model"], g["params"], g["dt"], g["n_steps"], f0)
+    err = rel_err(sim.group_fields(0).cpu().numpy(), ref)
+    print("c6 BZ 64 full-horizon field error", err, "residual", res.cpu().numpy())
+    assert err <= FIELD_TOL
+
+
 def mixed_groups(p, steps_scale=1.0):
     def st(n):
         return max(1, int(n * steps_scale))
@@ -241,7 +261,8 @@ def mixed_groups(p, steps_scale=1.0):
             mkgroup(p, W.FHN, 32, 7, (2.9e-4, 0.05, 9.5, 0.93), 2 ** -8, st(400), (-0.05, 0.05), 103),
             mkgroup(p, W.GM, 64, 4, (2.5e-4, 0.01, 1.0, 0.47), 2 ** -8, st(250), (0.0, 0.01), 104),
             mkgroup(p, W.FHN, 128, 2, (2.8e-4, 0.05, 10.0, 0.97), 2 ** -12, st(150), (-0.05, 0.05), 105),
-            mkgroup(p, W.DIFF, 64, 2, (3e-3, 1e-3), 2 ** -12, st(100), (-1.0, 1.0), 106)]
+            mkgroup(p, W.DIFF, 64, 2, (3e-3, 1e-3), 2 ** -12, st(100), (-1.0, 1.0), 106),
+            mkgroup(p, W.BZ, 64, 3, W.BZ_THETA0, 2 ** -8, st(300), (0.0, 0.01), 107)]
 
 
 def test_persistent_batch_bit_identical_to_per_group(p):
