@@ -354,7 +354,7 @@ def run_ours(args, rank, world, local_rank):
     else:
         pk_, ty_, tx_ = p.variant_shape(groups[0].G, variant)
         kname = "%s<%s,%d,%dx%d> variant %s" % ("rd_resident_kernel" if pk_ else "rd_resident_scalar_kernel",
-                                               {0: "FHN", 1: "GM", 2: "DIFF"}[groups[0].model],
+                                               {0: "FHN", 1: "GM", 2: "DIFF", 3: "BZ"}[groups[0].model],
                                                groups[0].G, ty_, tx_, variant)
     workload = {"c2": "c2: FHN 64x64, 2 sets x 64 realisations, 10^4 Euler steps, u-only d=4096, M=16, "
                       "b=1.3, 200 resamples",
@@ -396,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak_alu,
                      "traffic": stepper_traffic() if variant == 0 and args.config == "c2" else None,
                      "kernel": kname,
-                     "note": "FP32 pipe instructions of the update (FHN 15, GM 20 per cell-update) x "
+                     "note": "FP32 pipe instructions of the update (FHN 15, GM 20, BZ 22 per cell-update) x "
                              "cell-updates / stepper time; peak = 148 SM x 128 FP32 lanes x max SM clock "
                              "(%s peaks file)" % src},
         "plain_fp32_path_cell_updates_per_s": ref_rate,
