@@ -2,6 +2,7 @@
 indices and counts must be bit-exact (integer results of an exact
 definition), on shapes that span several tiles and ragged tails."""
 import json
+import math
 import os
 
 import numpy as np
@@ -161,3 +162,37 @@ def test_tensor_core_bound_holds_with_slack(p, n1, n2, d, off):
     assert np.all(err <= 0.25 * m), (err / m).max()
     # and the bound is tight enough to be useful: relative width < 1e-3
     assert np.all(m <= 1e-3 * ex + 1e-9)
+
+
+def test_paper_scale_sampled_pairs(p):
+    """2 x 1024 patterns of d = 32768 (the SCIL scale, as timed by bench.py
+    --gram-large): too many pairs for the brute-force oracle, so the bins of
+    2000 random pairs are recomputed from the oracle's canonical distance
+    and the GPU's radii, R0 is checked against the oracle's distance of the
+    pair the approximate stage ranks largest (and bounds every sampled
+    distance), and the counts are checked against the bin matrix."""
+    n, G = 1024, 128
+    X = W.cosine_patterns(2 * n, G, 2, 77, amp=0.8, offset=2.0)
+    X1, X2 = X[:n], X[n:]
+    t1, t2 = torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda()
+    g = p.cil(t1, t2, b=1.3, M=16)
+    torch.cuda.synchronize()
+    assert int(g["n_rechecked"]) >= 0
+    R0 = float(g["R0"])
+    radii = g["radii"].cpu().numpy()
+    bins = g["bins"].cpu().numpy()
+    counts = g["counts"].cpu().numpy()
+    for k in range(1, 17):
+        assert counts[k - 1] == int((bins >= k).sum())
+    # the largest distance is among the 16 pairs the approximate stage
+    # ranks largest (its error bound is ~1e-4 relative)
+    A, _ = p.cil_approx(t1, t2)
+    top = torch.topk(A.reshape(-1), 16).indices.cpu().numpy()
+    best = max(oracle.d2_canon(X1[q // n], X2[q % n]) for q in top)
+    assert math.sqrt(best) == R0
+    rng = np.random.default_rng(5)
+    for i, j in zip(rng.integers(0, n, 2000), rng.integers(0, n, 2000)):
+        d2 = oracle.d2_canon(X1[i], X2[j])
+        assert math.sqrt(d2) <= R0
+        K = sum(1 for r in radii if d2 < r * r)
+        assert bins[i, j] == K, (i, j)
