@@ -78,6 +78,11 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="also time the adjoint (smoothed-CIL gradient) on the FHN 64x64 adjoint workload "
                          "(32 realisations, 5000 steps)")
+    ap.add_argument("--stream", action="store_true",
+                    help="also time the streaming stepper (TMA tiles, temporal blocking) on FHN 512x512 x 128 "
+                         "realisations, against the HBM roofline")
+    ap.add_argument("--stream-only", action="store_true",
+                    help="time only the streaming stepper (for profiling)")
     ap.add_argument("--mcil", action="store_true",
                     help="also time the multi-feature correlation integral (six distances) at the FHN 64x64 "
                          "and GM 128x128 set shapes")
@@ -411,6 +416,8 @@ def run_ours(args, rank, world, local_rank):
         out["adjoint"] = adjoint_c5(p, torch, dev, stream)
     if args.mcil and rank == 0:
         out["mcil"] = mcil_bench(p, torch, dev, stream)
+    if args.stream and rank == 0:
+        out["stream"] = stream_bench(p, torch, dev, stream, pk, src)
     return out
 
 
@@ -460,6 +467,39 @@ def gram_large(p, torch, dev, stream, pk, src):
                          "products (3 x 2 n1 n2 d flops), algorithmic = 2 n1 n2 d" % src,
             "cil_ms": t_cil * 1e3, "pair_dists_per_s": n * n / t_cil,
             "rechecked": int(c["n_rechecked"])}
+
+
+def stream_bench(p, torch, dev, stream, pk, src, depths=(1, 2, 4, 8)):
+    """Streaming stepper on FHN 512x512, 128 realisations (268 MB of fields,
+    above L2): 64 Euler steps per depth.  Algorithmic HBM bytes per launch =
+    the fields read and written once (16 B per cell), so 16/S B per
+    cell-update at depth S."""
+    G, n, steps = 512, 128, 64
+    g = p.Group(W.FHN, G, n, (2.8e-4, 0.05, 10.0, 0.95), 2.0 ** -16, steps, (-0.05, 0.05), 4242)
+    sim = p.Simulation([g], device=dev)
+    cells = n * G * G
+    out = []
+    for S in depths:
+        sim.set_stream_depth(S)
+        sim.reinit()
+        sim.integrate(residual=False)
+        torch.cuda.synchronize()
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            sim.integrate(residual=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps * 1e-3
+        launches = (steps + S - 1) // S
+        gbs = 16.0 * cells * launches / t / 1e9
+        out.append({"depth": S, "ms": t * 1e3, "cell_updates_per_s": cells * steps / t,
+                    "hbm_algorithmic_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"],
+                    "bytes_per_cell_update": 16.0 / S})
+    assert sim.sync_status() == 0
+    return {"workload": "FHN 512x512, 128 realisations, 64 Euler steps (dt 2^-16)", "peak_hbm_gbs": pk["hbm_gbs"],
+            "peak_note": "%s peaks file; achieved = 16 B per cell per launch / time" % src, "depths": out}
 
 
 def mcil_bench(p, torch, dev, stream):
@@ -599,6 +639,16 @@ def main():
         if rank != 0:
             return
         print(json.dumps(run_reference(args)))
+        return
+    if args.stream_only:
+        import torch
+        import paper_2203_14742_b300 as p
+        from paper_2203_14742_b300 import build as B
+        B.build()
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        pk, src = peaks()
+        print(json.dumps(stream_bench(p, torch, dev, torch.cuda.current_stream(dev), pk, src)))
         return
     if args.mcil_only:
         import torch

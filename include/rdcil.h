@@ -66,12 +66,15 @@ typedef int32_t rd_status;
 
 /* group flags */
 #define RD_GROUP_ADJOINT 1   /* reserve checkpoint memory for rd_adjoint */
+#define RD_GROUP_STREAM 2    /* use the streaming stepper even where the resident one fits */
 
 /* One parameter group: n_real realisations of one model on one G x G grid
  * with one parameter vector and one step count (a theta of Alg. 3/6 step 1).
  * Fields of realisation r live at d_fields + field_offset + r*2*G*G as
  * [species u, v][y][x] float32, row-major.  field_offset must be a multiple
- * of 4 floats (16-byte rows).  Supported G: 32, 64, 128.  dt must be below
+ * of 4 floats (16-byte rows).  G: a multiple of 4 from 8 to 4096 (32, 64
+ * and 128 run on the resident stepper, others on the streaming stepper, see
+ * rd_set_stream_depth).  dt must be below
  * the explicit stability limit (h^2 / (4 max(Du, Dv)), h = 1/(G-1)); the
  * library does not check stability, but a blow-up is reported as
  * RD_ERR_NONFINITE. */
@@ -142,6 +145,19 @@ rd_status rd_integrate_batch(rd_handle *h, float *d_fields, int64_t steps_overri
  * an order that follows the tiling and agrees to FP64 rounding. */
 rd_status rd_set_schedule(rd_handle *h, int32_t mode);
 
+/* Groups whose grid is not 32, 64 or 128 (or that carry RD_GROUP_STREAM)
+ * run on the streaming stepper: one CTA per (32 x 64 tile, realisation)
+ * loads the tile and a halo by TMA, advances it `depth` Euler steps in
+ * shared memory (temporal blocking) and writes it back, ping-ponging
+ * between d_fields and a handle-owned buffer (the result always ends in
+ * d_fields).  Per node the arithmetic equals the resident stepper's, so a
+ * group gives bit-identical fields on either.  They are not in the
+ * persistent launch, and rd_adjoint does not support them.
+ * rd_set_stream_depth: steps fused per launch, 1, 2, 4 (default) or 8.
+ * rd_get_stream_depth: the current depth (-1 for a null handle). */
+rd_status rd_set_stream_depth(rd_handle *h, int32_t depth);
+int32_t rd_get_stream_depth(const rd_handle *h);
+
 /* rd_integrate_reference — the plain path the batched stepper is measured
  * against: one realisation per launch, one Euler step per launch, state
  * round-tripping through global memory.  Same arithmetic contract as
@@ -171,8 +187,9 @@ rd_status rd_integrate_f64(rd_handle *h, double *d_fields64, double *d_tmp64,
  *   (u, v) tiles, 0 = separate u and v tiles), TY, TX}.  RD_ERR_INVALID_ARG
  *   for an unknown G or variant or a null shape.
  * rd_autotune: time every variant on the largest group of each (model, G)
- *   class present in h for `steps` Euler steps, keep the fastest, then
- *   re-initialise d_fields (rd_reinit).  Synchronous.  chosen (nullable,
+ *   class present in h for `steps` Euler steps, keep the fastest (and, if
+ *   h holds streaming groups, the fastest temporal depth on the largest of
+ *   them), then re-initialise d_fields (rd_reinit).  Synchronous.  chosen (nullable,
  *   host int32[12]) receives the choice per [model][G index 32/64/128]. */
 int32_t rd_n_variants(void);
 rd_status rd_set_variant(int32_t model, int32_t G, int32_t variant);

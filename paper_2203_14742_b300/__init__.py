@@ -23,6 +23,7 @@ __all__ = ["FHN", "GM", "DIFF", "Group", "Simulation", "cil", "cil_exact", "synl
 
 FHN, GM, DIFF = 0, 1, 2
 GROUP_ADJOINT = 1
+GROUP_STREAM = 2
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librdcil.so")
 
@@ -64,6 +65,8 @@ _SIGS = {
     "rd_set_spin_limit": (None, [C.c_uint32]),
     "rd_n_variants": (_i32, []),
     "rd_set_schedule": (_i32, [_vp, _i32]),
+    "rd_set_stream_depth": (_i32, [_vp, _i32]),
+    "rd_get_stream_depth": (_i32, [_vp]),
     "rd_set_variant": (_i32, [_i32, _i32, _i32]),
     "rd_get_variant": (_i32, [_i32, _i32]),
     "rd_variant_shape": (_i32, [_i32, _i32, C.POINTER(_i32)]),
@@ -119,25 +122,28 @@ def _stream():
 
 class Group:
     """One parameter group (a theta): n_real realisations of `model` on a
-    G x G grid.  params: FHN (Du, Dv, eps, a); GM (Du, Dv, rho, mu)."""
+    G x G grid.  params: FHN (Du, Dv, eps, a); GM (Du, Dv, rho, mu); BZ (Du,
+    Dv, A, B).  stream=True runs it on the streaming stepper even where the
+    resident one fits."""
 
     def __init__(self, model, G, n_real, params, dt, n_steps, noise=(-0.05, 0.05), seed=0,
-                 adjoint=False):
+                 adjoint=False, stream=False):
         self.model, self.G, self.n_real = int(model), int(G), int(n_real)
         self.params = tuple(float(p) for p in params) + (0.0,) * (4 - len(params))
         self.dt, self.n_steps = float(dt), int(n_steps)
         self.noise = (float(noise[0]), float(noise[1]))
         self.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
         self.adjoint = bool(adjoint)
+        self.stream = bool(stream)
 
     @property
     def floats(self):
         return self.n_real * 2 * self.G * self.G
 
     @classmethod
-    def from_dict(cls, d, adjoint=False):
+    def from_dict(cls, d, adjoint=False, stream=False):
         return cls(d["model"], d["G"], d["n_real"], d["params"], d["dt"], d["n_steps"],
-                   d["noise"], d["seed"], adjoint=adjoint)
+                   d["noise"], d["seed"], adjoint=adjoint, stream=stream)
 
 
 class Simulation:
@@ -161,7 +167,7 @@ class Simulation:
         for i, g in enumerate(self.groups):
             a = arr[i]
             a.model, a.G, a.n_real = g.model, g.G, g.n_real
-            a.flags = GROUP_ADJOINT if g.adjoint else 0
+            a.flags = (GROUP_ADJOINT if g.adjoint else 0) | (GROUP_STREAM if g.stream else 0)
             a.n_steps, a.field_offset, a.dt = g.n_steps, offs[i], g.dt
             for k in range(4):
                 a.params[k] = g.params[k]
@@ -211,6 +217,10 @@ class Simulation:
         _check("rd_integrate_f64", lib().rd_integrate_f64(self.handle, _ptr(fields64), _ptr(tmp),
                                                           int(steps), _stream()))
         return fields64
+
+    def set_stream_depth(self, depth):
+        """Euler steps fused per launch of the streaming stepper (1, 2, 4, 8)."""
+        _check("rd_set_stream_depth", lib().rd_set_stream_depth(self.handle, int(depth)))
 
     def set_schedule(self, mode):
         """0 automatic, 1 one launch per group, 2 one persistent launch."""

@@ -24,7 +24,12 @@ static rd_status validate_groups(const rd_group *groups, int32_t n_groups) {
     for (int32_t i = 0; i < n_groups; ++i) {
         const rd_group &g = groups[i];
         if (g.model != RD_FHN && g.model != RD_GM && g.model != RD_DIFF && g.model != RD_BZ) return RD_ERR_INVALID_ARG;
-        if (g.G != 32 && g.G != 64 && g.G != 128) return RD_ERR_INVALID_ARG;
+        // resident stepper: G = 32, 64, 128; streaming stepper: any multiple of
+        // 4 from 8 to 4096
+        if (g.G < 8 || g.G > 4096 || (g.G & 3)) return RD_ERR_INVALID_ARG;
+        const bool resident = !(g.flags & RD_GROUP_STREAM) && (g.G == 32 || g.G == 64 || g.G == 128);
+        if ((g.flags & RD_GROUP_ADJOINT) && !resident) return RD_ERR_UNSUPPORTED;
+        if (g.flags & ~(RD_GROUP_ADJOINT | RD_GROUP_STREAM)) return RD_ERR_INVALID_ARG;
         if (g.n_real < 1 || g.n_steps < 0 || g.field_offset < 0 || (g.field_offset & 3)) return RD_ERR_INVALID_ARG;
         if (!(g.dt > 0.0) || !std::isfinite(g.dt)) return RD_ERR_INVALID_ARG;
         for (double p : g.params)
@@ -80,6 +85,8 @@ extern "C" rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_
     }
     st = adjoint_reserve(h);
     if (st) { rd_free(hh); return st; }
+    st = stream_reserve(h);
+    if (st) { rd_free(hh); return st; }
     st = batch_plan_create(h.h_groups, n_groups, &h.batch);
     if (st) { rd_free(hh); return st; }
     for (int32_t i = 0; i < n_groups; ++i) {
@@ -102,6 +109,14 @@ extern "C" rd_status rd_reinit(rd_handle *hh, float *d_fields, void *stream) {
     return RD_OK;
 }
 
+extern "C" rd_status rd_set_stream_depth(rd_handle *hh, int32_t depth) {
+    if (!hh || (depth != 1 && depth != 2 && depth != 4 && depth != 8)) return RD_ERR_INVALID_ARG;
+    hh->h.stream_depth = depth;
+    return RD_OK;
+}
+
+extern "C" int32_t rd_get_stream_depth(const rd_handle *hh) { return hh ? hh->h.stream_depth : -1; }
+
 extern "C" rd_status rd_set_schedule(rd_handle *hh, int32_t mode) {
     if (!hh || mode < 0 || mode > 2) return RD_ERR_INVALID_ARG;
     hh->h.schedule = mode;
@@ -112,13 +127,22 @@ extern "C" rd_status rd_integrate_batch(rd_handle *hh, float *d_fields, int64_t 
                                         void *stream) {
     if (!hh || !d_fields || ((uintptr_t)d_fields & 15)) return RD_ERR_INVALID_ARG;
     Handle &h = hh->h;
-    const bool persistent = h.schedule == 2 || (h.schedule == 0 && h.n_groups > 1);
-    if (persistent)
-        return launch_batch(h.batch, d_fields, steps_override, d_residual, h.d_status, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    int n_res = 0;
+    for (int32_t i = 0; i < h.n_groups; ++i) n_res += group_is_resident(h.h_groups[i]) ? 1 : 0;
+    const bool persistent = h.schedule == 2 || (h.schedule == 0 && n_res > 1);
+    if (persistent && n_res > 0) {
+        rd_status st = launch_batch(h.batch, d_fields, steps_override, d_residual, h.d_status, s);
+        if (st) return st;
+    }
     for (int32_t i = 0; i < h.n_groups; ++i) {
         const GroupDev &g = h.h_groups[i];
         int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
-        rd_status st = launch_integrate_group(g, d_fields, steps, d_residual, h.d_status, (cudaStream_t)stream);
+        rd_status st = RD_OK;
+        if (!group_is_resident(g))
+            st = launch_stream_group(h, g, d_fields, steps, d_residual, s);
+        else if (!persistent)
+            st = launch_integrate_group(g, d_fields, steps, d_residual, h.d_status, s);
         if (st) return st;
     }
     return RD_OK;
@@ -169,6 +193,7 @@ extern "C" void rd_free(rd_handle *hh) {
     if (!hh) return;
     Handle &h = hh->h;
     adjoint_release(h);
+    stream_release(h);
     batch_plan_free(h.batch);
     if (h.d_groups) cudaFree(h.d_groups);
     if (h.d_status) cudaFree(h.d_status);
@@ -237,7 +262,7 @@ extern "C" rd_status rd_autotune(rd_handle *hh, float *d_fields, int64_t steps, 
             // the largest group of this (model, G) class stands for the class
             int best_g = -1;
             for (int i = 0; i < h.n_groups; ++i)
-                if (h.h_groups[i].model == model && h.h_groups[i].G == G &&
+                if (h.h_groups[i].model == model && h.h_groups[i].G == G && group_is_resident(h.h_groups[i]) &&
                     (best_g < 0 || h.h_groups[i].n_real > h.h_groups[best_g].n_real))
                     best_g = i;
             if (best_g < 0) continue;
@@ -262,6 +287,31 @@ extern "C" rd_status rd_autotune(rd_handle *hh, float *d_fields, int64_t steps, 
             set_variant_choice(model, G, best_v);
             if (chosen) chosen[model * 3 + (G == 32 ? 0 : G == 64 ? 1 : 2)] = best_v;
         }
+    // streaming groups: the temporal depth, timed on the largest of them
+    int best_s = -1;
+    for (int i = 0; i < h.n_groups; ++i)
+        if (!group_is_resident(h.h_groups[i]) &&
+            (best_s < 0 || (double)h.h_groups[i].n_real * h.h_groups[i].G * h.h_groups[i].G >
+                               (double)h.h_groups[best_s].n_real * h.h_groups[best_s].G * h.h_groups[best_s].G))
+            best_s = i;
+    if (best_s >= 0 && st == RD_OK) {
+        const GroupDev &g = h.h_groups[best_s];
+        float best_ms = 1e30f;
+        int best_d = h.stream_depth;
+        for (int d : {1, 2, 4, 8}) {
+            h.stream_depth = d;
+            st = launch_stream_group(h, g, d_fields, steps, nullptr, s);   // warm
+            if (st) break;
+            cudaEventRecord(e0, s);
+            st = launch_stream_group(h, g, d_fields, steps, nullptr, s);
+            cudaEventRecord(e1, s);
+            if (st || cudaEventSynchronize(e1) != cudaSuccess) { st = st ? st : RD_ERR_CUDA; break; }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (t < best_ms) { best_ms = t; best_d = d; }
+        }
+        h.stream_depth = best_d;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st;

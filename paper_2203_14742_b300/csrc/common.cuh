@@ -50,6 +50,10 @@ struct Handle {
     void *plan;
     void *batch;
     int32_t schedule;         // 0 auto, 1 one launch per group, 2 one persistent launch
+    // streaming stepper (groups that are not resident, stream.cu)
+    float *d_stream_tmp;      // the other HBM buffer of the ping-pong
+    double *d_stream_part;    // residual partial sums
+    int32_t stream_depth;     // Euler steps fused per launch (1, 2, 4 or 8)
 };
 
 inline rd_status cuda_status(cudaError_t e) {
@@ -84,6 +88,11 @@ rd_status launch_batch(void *plan, float *fields, int64_t steps_override, double
 void set_variant_choice(int model, int G, int vi);
 int get_variant_choice(int model, int G);
 int n_variants();
+bool group_is_resident(const GroupDev &g);
+rd_status stream_reserve(Handle &h);
+void stream_release(Handle &h);
+rd_status launch_stream_group(const Handle &h, const GroupDev &g, float *fields, int64_t steps, double *residual,
+                              cudaStream_t s);
 void set_gram_spin_limit(uint32_t n);
 bool variant_shape(int G, int vi, int *packed, int *TY, int *TX);
 

@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <mutex>
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace rdcil {
 
@@ -33,49 +34,7 @@ static constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;              // 16 KiB
 static constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;             // A hi, A lo, B hi, B lo
 static constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
 static_assert((2 * TC_STAGES + 5) * 8 + 4 <= 256, "barrier area");
-static constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;                  // bounded spin (~seconds)
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity to complete (at most
-// `limit` polls; the pipeline waits take the limit from the launch, the
-// clean-up waits for work already issued always use TC_WAIT_LIMIT).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = TC_WAIT_LIMIT) {
-    for (uint32_t it = 0; it < limit; ++it)
-        if (mbar_try(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int c0, int c1, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)tm), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
-}
+static constexpr uint32_t TC_WAIT_LIMIT = MBAR_WAIT_LIMIT;           // bounded spin (~seconds)
 
 // Shared-memory matrix descriptor, K-major operand in the 128-byte swizzle
 // layout: start address >> 4 (bits 0-13), leading byte offset (unused for

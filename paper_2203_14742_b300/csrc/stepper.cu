@@ -74,34 +74,6 @@ rd_status launch_init_fields(const GroupDev &g, float *fields, cudaStream_t s) {
     return cuda_status(cudaGetLastError());
 }
 
-// FP64 right-hand side at one node from FP32 neighbours (used for the
-// residual; operation order of the plain definition).
-template <int MODEL>
-__device__ __forceinline__ void rhs_f64(double u, double v, double nu, double su, double wu, double eu,
-                                        double nv, double sv, double wv, double ev, const double *p,
-                                        double h2, double &Fu, double &Fv) {
-    double lu = ((((eu + wu) + su) + nu) - 4.0 * u) * h2;
-    double lv = ((((ev + wv) + sv) + nv) - 4.0 * v) * h2;
-    double ru, rv;
-    if (MODEL == RD_FHN) {
-        ru = (u - (u * u) * u) - v;
-        rv = p[2] * (u - p[3] * v);
-    } else if (MODEL == RD_GM) {
-        double uu = u * u;
-        ru = p[2] * (uu / v - p[3] * u);
-        rv = p[2] * (uu - v);
-    } else if (MODEL == RD_BZ) {
-        double uuv = (u * u) * v;
-        ru = (p[2] - (p[3] + 1.0) * u) + uuv;
-        rv = p[3] * u - uuv;
-    } else {
-        ru = 0.0;
-        rv = 0.0;
-    }
-    Fu = p[0] * lu + ru;
-    Fv = p[1] * lv + rv;
-}
-
 // FP64 steady-state residual of the final state of realisation r, read
 // back from global memory after the block stored it (block-visible after
 // the barrier): max |F| and sqrt(mean F^2) over both species, F from the
@@ -470,6 +442,7 @@ rd_status batch_plan_create(const GroupDev *groups, int n_groups, void **out) {
         b.G = g.G;
         b.n_real = g.n_real;
         b.pad = 0;
+        if (!group_is_resident(g)) continue;   // streaming groups run on their own launches
         for (int r = 0; r < g.n_real; ++r) items.push_back(BatchItem{i, r});
     }
     // longest first: cost ~ G^2 * steps
@@ -506,6 +479,7 @@ rd_status launch_batch(void *pp, float *fields, int64_t steps_override, double *
                        cudaStream_t s) {
     BatchPlan *p = (BatchPlan *)pp;
     if (!p) return RD_ERR_INVALID_ARG;
+    if (p->n_items == 0) return RD_OK;
     static bool attr = false;
     if (!attr) {
         RD_CUDA_TRY(cudaFuncSetAttribute(rd_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -224,6 +224,34 @@ __device__ __forceinline__ void euler_cell(float u, float v, float su, float sv,
     }
 }
 
+// FP64 right-hand side at one node from FP32 neighbours (used for the
+// residual; operation order of the plain definition).
+template <int MODEL>
+__device__ __forceinline__ void rhs_f64(double u, double v, double nu, double su, double wu, double eu,
+                                        double nv, double sv, double wv, double ev, const double *p,
+                                        double h2, double &Fu, double &Fv) {
+    double lu = ((((eu + wu) + su) + nu) - 4.0 * u) * h2;
+    double lv = ((((ev + wv) + sv) + nv) - 4.0 * v) * h2;
+    double ru, rv;
+    if (MODEL == RD_FHN) {
+        ru = (u - (u * u) * u) - v;
+        rv = p[2] * (u - p[3] * v);
+    } else if (MODEL == RD_GM) {
+        double uu = u * u;
+        ru = p[2] * (uu / v - p[3] * u);
+        rv = p[2] * (uu - v);
+    } else if (MODEL == RD_BZ) {
+        double uuv = (u * u) * v;
+        ru = (p[2] - (p[3] + 1.0) * u) + uuv;
+        rv = p[3] * u - uuv;
+    } else {
+        ru = 0.0;
+        rv = 0.0;
+    }
+    Fu = p[0] * lu + ru;
+    Fv = p[1] * lv + rv;
+}
+
 template <int MODEL, int TY, int TX>
 __device__ __forceinline__ void tile_to_state(float (&u)[TY][TX], float (&v)[TY][TX], const CoefF &c) {
 #pragma unroll

@@ -65,8 +65,15 @@ def test_argument_errors_before_any_launch(libpath):
     L = p.lib()
     h = ctypes.c_void_p()
     g = (p.RdGroup * 1)()
-    g[0].model, g[0].G, g[0].n_real, g[0].dt = 0, 48, 1, 1e-3     # unsupported G
+    g[0].model, g[0].n_real, g[0].dt = 0, 1, 1e-3
+    for G in (50, 4, 8192):                                           # unsupported G
+        g[0].G = G
+        assert L.rd_init(g, 1, ctypes.c_void_p(256), None, ctypes.byref(h)) == 1
+    g[0].G, g[0].flags = 48, 4                                        # unknown flag
     assert L.rd_init(g, 1, ctypes.c_void_p(256), None, ctypes.byref(h)) == 1
+    g[0].flags = 1                                                    # adjoint needs a resident grid
+    assert L.rd_init(g, 1, ctypes.c_void_p(256), None, ctypes.byref(h)) == 6
+    g[0].flags = 0
     g[0].G = 64
     g[0].field_offset = 2                                             # misaligned
     assert L.rd_init(g, 1, ctypes.c_void_p(256), None, ctypes.byref(h)) == 1
@@ -97,3 +104,10 @@ def test_variant_shapes_are_valid_tilings(libpath):
     sh = (ctypes.c_int32 * 3)()
     assert p.lib().rd_variant_shape(48, 0, sh) == 1
     assert p.lib().rd_variant_shape(64, p.lib().rd_n_variants(), sh) == 1
+
+
+def test_stream_depth_argument_checks(libpath):
+    import paper_2203_14742_b300 as p
+    L = p.lib()
+    assert L.rd_set_stream_depth(None, 4) == 1
+    assert L.rd_get_stream_depth(None) == -1
