@@ -34,6 +34,15 @@ def lib():
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_uint8))
         L.orc_threads.restype = C.c_int
+        L.orc_rkc_coef.argtypes = [C.c_int, dp, dp, dp, dp, dp]
+        L.orc_rkc_beta.argtypes = [C.c_int]
+        L.orc_rkc_beta.restype = C.c_double
+        L.orc_gershgorin.argtypes = [C.c_int, C.c_int, dp, dp]
+        L.orc_gershgorin.restype = C.c_double
+        L.orc_rkc_fixed.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_int, C.c_int64, dp]
+        L.orc_rkc_adaptive.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_double,
+                                       C.c_double, C.c_double, C.c_int, C.c_int64, dp, i64p]
+        L.orc_rkc_adaptive.restype = C.c_int
         L.orc_minmax.argtypes = [fp, C.c_int64, C.c_int, C.c_int, fp]
         L.orc_fd.argtypes = [fp, C.c_int64, C.c_int, C.c_int, fp, fp]
         L.orc_maxabs.argtypes = [fp, fp, C.c_int64]
@@ -410,3 +419,53 @@ def synlik_multi(bins, M, T, seed, y_obs=None):
     out = stats(Y, n1 * n2, y_obs)
     out["Y"] = Y
     return out
+
+
+# ---------------------------------------------------------------------------
+# Stabilised explicit second-order Runge-Kutta (App. B.2; Chebyshev
+# coefficients, see rkc.c for the readings).
+
+def rkc_coef(s):
+    """Coefficients of the s-stage method: dict of arrays mu, nu, mt, gt
+    (index = stage j) and scalars w0, w1, b_s, a_s, beta."""
+    mu, nu, mt, gt = (np.zeros(s + 1) for _ in range(4))
+    ex = np.zeros(5)
+    lib().orc_rkc_coef(int(s), _p(mu, C.c_double), _p(nu, C.c_double), _p(mt, C.c_double),
+                       _p(gt, C.c_double), _p(ex, C.c_double))
+    return dict(mu=mu, nu=nu, mt=mt, gt=gt, w0=ex[0], w1=ex[1], b_s=ex[2], a_s=ex[3], beta=ex[4])
+
+
+def rkc_beta(s):
+    """Length of the real stability interval of the s-stage method."""
+    return float(lib().orc_rkc_beta(int(s)))
+
+
+def gershgorin(model, p, w):
+    """Gershgorin bound of the spectral radius of dF/dw at w[2, G, G]."""
+    p = _params(p)
+    w = _d(w)
+    return float(lib().orc_gershgorin(model, w.shape[-1], _p(p, C.c_double), _p(w, C.c_double)))
+
+
+def rkc_fixed(model, p, h, s, n_steps, w):
+    """n_steps steps of size h with s stages on w[n_real, 2, G, G] (float64 copy)."""
+    p = _params(p)
+    w = np.array(w, dtype=np.float64, order="C", copy=True)
+    n_real, G = w.shape[0], w.shape[-1]
+    lib().orc_rkc_fixed(model, G, n_real, _p(p, C.c_double), float(h), int(s), int(n_steps),
+                        _p(w, C.c_double))
+    return w
+
+
+def rkc_adaptive(model, p, t_end, h0, rtol, atol, w, s_max=256, max_attempts=100000):
+    """Adaptive integration of w[n_real, 2, G, G] from 0 to t_end.
+    Returns (w float64, stats int64 [n_real, 4] = accepted, rejected, RHS
+    evaluations, largest s; number of failed realisations)."""
+    p = _params(p)
+    w = np.array(w, dtype=np.float64, order="C", copy=True)
+    n_real, G = w.shape[0], w.shape[-1]
+    stats = np.zeros((n_real, 4), np.int64)
+    failed = lib().orc_rkc_adaptive(model, G, n_real, _p(p, C.c_double), float(t_end), float(h0),
+                                    float(rtol), float(atol), int(s_max), int(max_attempts),
+                                    _p(w, C.c_double), _p(stats, C.c_int64))
+    return w, stats, int(failed)
