@@ -43,6 +43,7 @@ typedef int32_t rd_status;
 #define RD_ERR_NONFINITE 5
 #define RD_ERR_UNSUPPORTED 6
 #define RD_ERR_OOM 7
+#define RD_ERR_STEPSIZE 8   /* adaptive step control gave up (rd_integrate_rkc) */
 
 /* Reaction kinetics (Sec. 4.1), species order (u, v):
  *  RD_FHN  FitzHugh-Nagumo, eq. (introduction:0) with u = membrane potential
@@ -176,6 +177,71 @@ rd_status rd_integrate_reference(rd_handle *h, float *d_fields, float *d_tmp,
  * is slow on this GPU). */
 rd_status rd_integrate_f64(rd_handle *h, double *d_fields64, double *d_tmp64,
                            int64_t steps_override, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Stabilised explicit second-order Runge-Kutta integration (App. B.2).
+ *
+ * The paper integrates the RD systems with ROCK2: stages by a three-term
+ * recurrence, the stage number s from h times a Gershgorin bound of the
+ * Jacobian's spectral radius, a weighted RMS error norm and a predictive
+ * step-size controller with eta = 0.8.  ROCK2's recurrence coefficients are
+ * not printed in the paper; this library uses the same family's member with
+ * closed-form coefficients, the second-order Runge-Kutta-Chebyshev method
+ * (damping 2/13), with T_j the Chebyshev polynomials of the first kind:
+ *   w0 = 1 + (2/13)/s^2,  w1 = T_s'(w0)/T_s''(w0),
+ *   b_j = T_j''(w0)/T_j'(w0)^2 (b_0 = b_1 = b_2),  a_j = 1 - b_j T_j(w0),
+ *   Y_0 = w_n,  Y_1 = Y_0 + b_1 w1 h F(Y_0),
+ *   Y_j = (1-mu_j-nu_j) Y_0 + mu_j Y_{j-1} + nu_j Y_{j-2}
+ *         + mt_j h F(Y_{j-1}) + gt_j h F(Y_0),   j = 2..s,
+ *   mu_j = 2 b_j w0/b_{j-1}, nu_j = -b_j/b_{j-2}, mt_j = 2 b_j w1/b_{j-1},
+ *   gt_j = -a_{j-1} mt_j,   w_{n+1} = Y_s,
+ * stable for h rho <= beta(s) = (1 + w0)/w1 (about 0.65 s^2).
+ * Step control (adaptive mode), per realisation:
+ *   rho   = max over nodes of the Gershgorin row sums of dF/dw at w_n (a node
+ *           with n in-domain neighbours: |-n D (G-1)^2 + df/du| +
+ *           n D (G-1)^2 + |df/dv|, likewise the v row);
+ *   s     = the smallest s >= 2 with h rho <= beta(s); above s_max the step
+ *           is cut to beta(s_max)/rho;
+ *   est   = (12 (w_n - w_{n+1}) + 6 h (F(w_n) + F(w_{n+1}))) / 15;
+ *   err   = sqrt(mean (est / (atol + rtol max(|w_n|, |w_{n+1}|)))^2), accept
+ *           when err <= 1;
+ *   h_new = fac h, fac = 0.8 err^(-1/3) (h_n/h_{n-1}) (err_{n-1}/err)^(1/3)
+ *           after two consecutive accepted steps, 0.8 err^(-1/3) otherwise,
+ *           err floored at 1e-10, fac in [0.1, 10] and <= 1 right after a
+ *           rejection; the last step ends exactly at t_end.
+ * FP32 state, FP64 control.  Groups must have G = 32 or 64
+ * (RD_ERR_UNSUPPORTED otherwise; nothing is launched).
+ */
+#define RD_RKC_S_MAX 256
+
+typedef struct rd_rkc_opts {
+    double t_end;          /* > 0: every group integrates from 0 to t_end;
+                              <= 0: each group to its own dt * n_steps */
+    double h0;             /* first trial step (adaptive) / the step (fixed), > 0 */
+    double rtol, atol;     /* error weights (adaptive), >= 0, not both 0 */
+    int32_t s_max;         /* stage limit, 2 .. RD_RKC_S_MAX (adaptive) */
+    int32_t s_fixed;       /* 0: adaptive; 2 .. RD_RKC_S_MAX: fixed mode, n_fixed
+                              steps of size h0 with s_fixed stages, no error
+                              control (t_end, rtol, atol, s_max ignored) */
+    int64_t n_fixed;       /* steps of the fixed mode, >= 0 */
+    int64_t max_attempts;  /* attempted steps per realisation before giving up, >= 1 */
+} rd_rkc_opts;
+
+/* rd_integrate_rkc — integrate every realisation of every group in place
+ * (d_fields as for rd_integrate_batch), one CTA per realisation running its
+ * own step control on the device, groups launched in order on `stream`.
+ * opts: host struct, read during the call.
+ * d_stats (nullable): device int64 [n_real_total][4] = accepted steps,
+ *   rejected steps, RHS evaluations (1 + the sum of s over all attempts),
+ *   largest s used.
+ * d_residual (nullable): as for rd_integrate_batch.
+ * A realisation whose control gives up (more than max_attempts attempts, or
+ * h below 1e-12 t_end) sets RD_ERR_STEPSIZE, one whose error or state turns
+ * non-finite RD_ERR_NONFINITE, in the status word (rd_sync_status); its
+ * state is left where it stopped.  Returns RD_ERR_INVALID_ARG for a bad
+ * option, RD_ERR_UNSUPPORTED for a group it cannot run. */
+rd_status rd_integrate_rkc(rd_handle *h, float *d_fields, const rd_rkc_opts *opts, int64_t *d_stats,
+                           double *d_residual, void *stream);
 
 /* Tile-shape variants of the resident stepper.  Every variant performs the
  * same per-node arithmetic in the same order, so all give bit-identical

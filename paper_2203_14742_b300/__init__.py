@@ -35,6 +35,14 @@ class RdGroup(C.Structure):
                 ("seed", C.c_uint64)]
 
 
+class RdRkcOpts(C.Structure):
+    _fields_ = [("t_end", C.c_double), ("h0", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
+                ("s_max", C.c_int32), ("s_fixed", C.c_int32), ("n_fixed", C.c_int64),
+                ("max_attempts", C.c_int64)]
+
+
+RKC_S_MAX = 256
+
 _vp, _i64, _i32, _dbl, _u64, _sz = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_uint64, C.c_size_t
 
 _SIGS = {
@@ -43,6 +51,7 @@ _SIGS = {
     "rd_integrate_batch": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "rd_integrate_reference": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "rd_integrate_f64": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+    "rd_integrate_rkc": (_i32, [_vp, _vp, C.POINTER(RdRkcOpts), _vp, _vp, _vp]),
     "rd_sync_status": (_i32, [_vp, _vp]),
     "rd_n_real_total": (_i64, [_vp]),
     "rd_free": (None, [_vp]),
@@ -217,6 +226,23 @@ class Simulation:
         _check("rd_integrate_f64", lib().rd_integrate_f64(self.handle, _ptr(fields64), _ptr(tmp),
                                                           int(steps), _stream()))
         return fields64
+
+    def integrate_rkc(self, h0, t_end=0.0, rtol=1e-5, atol=1e-5, s_max=RKC_S_MAX, max_attempts=100000,
+                      s_fixed=0, n_fixed=0, stats=True, residual=False):
+        """Stabilised second-order Runge-Kutta (App. B.2, Chebyshev
+        coefficients) in place.  Adaptive by default: every realisation from
+        0 to t_end (<= 0: each group's dt * n_steps) with its own step
+        control; s_fixed >= 2: n_fixed steps of size h0 with s_fixed stages.
+        Returns (stats int64 [n_real, 4] = accepted, rejected, RHS
+        evaluations, largest s; residual or None)."""
+        o = RdRkcOpts(float(t_end), float(h0), float(rtol), float(atol), int(s_max), int(s_fixed),
+                      int(n_fixed), int(max_attempts))
+        st = torch.empty((self.n_real_total, 4), dtype=torch.int64, device=self.device) if stats else None
+        res = (torch.empty((self.n_real_total, 2), dtype=torch.float64, device=self.device)
+               if residual else None)
+        _check("rd_integrate_rkc", lib().rd_integrate_rkc(self.handle, _ptr(self.fields), C.byref(o),
+                                                          _ptr(st), _ptr(res), _stream()))
+        return st, res
 
     def set_stream_depth(self, depth):
         """Euler steps fused per launch of the streaming stepper (1, 2, 4, 8)."""

@@ -174,6 +174,30 @@ extern "C" rd_status rd_integrate_f64(rd_handle *hh, double *d_fields64, double 
     return RD_OK;
 }
 
+extern "C" rd_status rd_integrate_rkc(rd_handle *hh, float *d_fields, const rd_rkc_opts *opts, int64_t *d_stats,
+                                      double *d_residual, void *stream) {
+    if (!hh || !d_fields || !opts) return RD_ERR_INVALID_ARG;
+    const rd_rkc_opts &o = *opts;
+    if (!(o.h0 > 0.0) || !std::isfinite(o.h0)) return RD_ERR_INVALID_ARG;
+    if (o.s_fixed != 0 && (o.s_fixed < 2 || o.s_fixed > RD_RKC_S_MAX)) return RD_ERR_INVALID_ARG;
+    if (o.s_fixed == 0) {
+        if (!(o.rtol >= 0.0) || !(o.atol >= 0.0) || !(o.rtol + o.atol > 0.0)) return RD_ERR_INVALID_ARG;
+        if (o.s_max < 2 || o.s_max > RD_RKC_S_MAX || o.max_attempts < 1) return RD_ERR_INVALID_ARG;
+        if (!std::isfinite(o.t_end)) return RD_ERR_INVALID_ARG;
+    } else if (o.n_fixed < 0) {
+        return RD_ERR_INVALID_ARG;
+    }
+    Handle &h = hh->h;
+    for (int gi = 0; gi < h.n_groups; ++gi)
+        if (!rkc_supported(h.h_groups[gi])) return RD_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int gi = 0; gi < h.n_groups; ++gi) {
+        rd_status st = launch_rkc_group(h.h_groups[gi], d_fields, o, d_stats, d_residual, h.d_status, s);
+        if (st != RD_OK) return st;
+    }
+    return RD_OK;
+}
+
 extern "C" rd_status rd_sync_status(rd_handle *hh, void *stream) {
     if (!hh) return RD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -184,6 +208,7 @@ extern "C" rd_status rd_sync_status(rd_handle *hh, void *stream) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return RD_ERR_CUDA;
     if (v & ST_TIMEOUT) return RD_ERR_TIMEOUT;
     if (v & ST_NONFINITE) return RD_ERR_NONFINITE;
+    if (v & ST_STEPFAIL) return RD_ERR_STEPSIZE;
     return RD_OK;
 }
 
@@ -211,6 +236,7 @@ extern "C" const char *rd_status_str(rd_status s) {
         case RD_ERR_NONFINITE: return "non-finite field";
         case RD_ERR_UNSUPPORTED: return "unsupported configuration";
         case RD_ERR_OOM: return "out of device memory";
+        case RD_ERR_STEPSIZE: return "adaptive step control gave up";
         default: return "unknown status";
     }
 }

@@ -11,6 +11,7 @@ namespace rdcil {
 enum : uint32_t {
     ST_NONFINITE = 1u,
     ST_TIMEOUT = 2u,
+    ST_STEPFAIL = 4u,
 };
 
 // SplitMix64 (Steele, Lea & Flood 2014): output number i of the stream that
@@ -95,5 +96,8 @@ rd_status launch_stream_group(const Handle &h, const GroupDev &g, float *fields,
                               cudaStream_t s);
 void set_gram_spin_limit(uint32_t n);
 bool variant_shape(int G, int vi, int *packed, int *TY, int *TX);
+bool rkc_supported(const GroupDev &g);
+rd_status launch_rkc_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats, double *residual,
+                           uint32_t *status, cudaStream_t s);
 
 }  // namespace rdcil

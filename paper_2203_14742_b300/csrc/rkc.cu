@@ -1,0 +1,543 @@
+// Stabilised explicit second-order Runge-Kutta integration of the batched
+// reaction-diffusion systems (App. B.2): stages by a three-term recurrence,
+// stage number from a Gershgorin bound of the Jacobian's spectral radius,
+// weighted RMS error estimate and a predictive step-size controller
+// (eta = 0.8), all on the GPU.  The coefficients are those of the
+// second-order Runge-Kutta-Chebyshev method (damping eps = 2/13), the member
+// of the family with closed-form coefficients, since the paper does not
+// print ROCK2's:
+//   w0 = 1 + eps/s^2,  w1 = T_s'(w0)/T_s''(w0),  b_j = T_j''(w0)/T_j'(w0)^2
+//   (b_0 = b_1 = b_2),  a_j = 1 - b_j T_j(w0),
+//   Y_1 = Y_0 + mt_1 h F(Y_0),  mt_1 = b_1 w1,
+//   Y_j = (1-mu_j-nu_j) Y_0 + mu_j Y_{j-1} + nu_j Y_{j-2} + mt_j h F(Y_{j-1}) + gt_j h F(Y_0),
+//   mu_j = 2 b_j w0/b_{j-1}, nu_j = -b_j/b_{j-2}, mt_j = 2 b_j w1/b_{j-1}, gt_j = -a_{j-1} mt_j,
+//   stable for h rho <= beta(s) = (1 + w0)/w1.
+//
+// B300 design.  One CTA integrates one realisation for its whole adaptive
+// run, with no host round trip: the state lives in register tiles (the
+// natural-order tiles of tile.cuh), each stage is one halo exchange
+// through the shared-memory ring and one barrier, and thread 0 takes the
+// step-control decisions in FP64 from block reductions.  (The paper's GPU
+// solver kept the vectors in global memory and synchronised with the host
+// after every stage.)
+//
+// Precision.  The recurrence is carried on the increments D_j = Y_j - Y_0,
+//   D_1 = mt_1 h F_0,  D_j = mu_j D_{j-1} + nu_j D_{j-2} + mt_j h F(Y_0 + D_{j-1}) + gt_j h F_0,
+// which is the same recurrence (the stage weights sum to one), so the FP32
+// rounding of the stages is relative to the small increments rather than to
+// the state (with the plain form, mu_j ~ 2 and nu_j ~ -1 amplify the
+// state's rounding through the stages).  GM and BZ states are kept as the
+// deviation from the FP32 equilibrium, as in the Euler stepper.  The error
+// estimate uses Y_0 - Y_s = -D_s, free of cancellation.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+#include "common.cuh"
+#include "tile.cuh"
+
+namespace rdcil {
+
+constexpr int RKC_SMAX = RD_RKC_S_MAX;
+constexpr int RKC_STRIDE = RKC_SMAX + 1;
+
+// ---------------------------------------------------------------------------
+// Coefficient table: tab[s][j] = (mu_j, nu_j, mt_j, gt_j) in FP32 for
+// s = 2..RKC_SMAX, j = 1..s; beta[s] in FP64.  One thread per s.
+// ---------------------------------------------------------------------------
+__global__ void rkc_table_kernel(float4 *__restrict__ tab, double *__restrict__ beta) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < 2 || s > RKC_SMAX) return;
+    const double w0 = 1.0 + (2.0 / 13.0) / ((double)s * (double)s);
+    // first pass: T_s', T_s'' at w0 -> w1
+    double T0 = 1.0, T1v = w0, d0 = 0.0, d1 = 1.0, e0 = 0.0, e1 = 0.0;
+    for (int j = 2; j <= s; ++j) {
+        const double T2v = 2.0 * w0 * T1v - T0;
+        const double d2 = 2.0 * T1v + 2.0 * w0 * d1 - d0;
+        const double e2 = 4.0 * d1 + 2.0 * w0 * e1 - e0;
+        T0 = T1v; T1v = T2v; d0 = d1; d1 = d2; e0 = e1; e1 = e2;
+    }
+    const double w1 = d1 / e1;
+    beta[s] = (1.0 + w0) / w1;
+    // second pass: b_j, a_j and the stage coefficients
+    T0 = 1.0; T1v = w0; d0 = 0.0; d1 = 1.0; e0 = 0.0; e1 = 0.0;
+    // b_2 = T_2''/T_2'^2 = 4 / (4 w0)^2 first (b_0 = b_1 = b_2)
+    const double b2 = 4.0 / ((4.0 * w0) * (4.0 * w0));
+    double bjm2 = b2, bjm1 = b2;                 // b_{j-2}, b_{j-1}
+    double ajm1 = 1.0 - b2 * w0;                 // a_1
+    float4 *row = tab + (size_t)s * RKC_STRIDE;
+    row[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    row[1] = make_float4(0.f, 0.f, (float)(b2 * w1), 0.f);
+    for (int j = 2; j <= s; ++j) {
+        const double T2v = 2.0 * w0 * T1v - T0;
+        const double d2 = 2.0 * T1v + 2.0 * w0 * d1 - d0;
+        const double e2 = 4.0 * d1 + 2.0 * w0 * e1 - e0;
+        const double bj = e2 / (d2 * d2);
+        const double mu = 2.0 * bj * w0 / bjm1;
+        const double nu = -bj / bjm2;
+        const double mt = 2.0 * bj * w1 / bjm1;
+        const double gt = -ajm1 * mt;
+        row[j] = make_float4((float)mu, (float)nu, (float)mt, (float)gt);
+        ajm1 = 1.0 - bj * T2v;
+        bjm2 = bjm1;
+        bjm1 = bj;
+        T0 = T1v; T1v = T2v; d0 = d1; d1 = d2; e0 = e1; e1 = e2;
+    }
+}
+
+static float4 *g_tab = nullptr;
+static double *g_beta = nullptr;
+static std::once_flag g_tab_once;
+static rd_status g_tab_status = RD_OK;
+
+static rd_status rkc_tables(cudaStream_t s) {
+    std::call_once(g_tab_once, [s]() {
+        if (cudaMalloc(&g_tab, sizeof(float4) * (size_t)RKC_STRIDE * RKC_STRIDE) != cudaSuccess ||
+            cudaMalloc(&g_beta, sizeof(double) * RKC_STRIDE) != cudaSuccess) {
+            g_tab_status = RD_ERR_OOM;
+            return;
+        }
+        cudaMemsetAsync(g_beta, 0, sizeof(double) * RKC_STRIDE, s);
+        rkc_table_kernel<<<(RKC_STRIDE + 127) / 128, 128, 0, s>>>(g_tab, g_beta);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) g_tab_status = RD_ERR_CUDA;
+    });
+    return g_tab_status;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 right-hand side without time-step folding.
+//   du = Du (G-1)^2, dv = Dv (G-1)^2;  FHN p2 = eps, p3 = a;  GM p2 = rho,
+//   p3 = mu, deviation form with u0, v0, tu0 = 2 u0, e0 = u0 - mu v0,
+//   e1 = u0^2 - v0;  BZ p2 = A, p3 = B, deviation form with u0 = A, v0 = B/A,
+//   e0 = A (A v0 - B), c1 = 2 A v0 - (B+1), c2 = B - 2 A v0.
+// ---------------------------------------------------------------------------
+struct RkcK {
+    float du, dv, p2, p3;
+    float u0, v0, tu0, e0, e1, c1, c2;
+};
+
+static RkcK make_rkc_k(const GroupDev &g) {
+    RkcK k{};
+    const double g2 = (double)(g.G - 1) * (double)(g.G - 1);
+    k.du = (float)(g.p[0] * g2);
+    k.dv = (float)(g.p[1] * g2);
+    k.p2 = (float)g.p[2];
+    k.p3 = (float)g.p[3];
+    if (g.model == RD_GM) {
+        const double mu = g.p[3];
+        const float u0 = (float)(1.0 / mu);
+        const float v0 = (float)((double)u0 * (double)u0);
+        k.u0 = u0;
+        k.v0 = v0;
+        k.tu0 = 2.0f * u0;
+        k.e0 = (float)((double)u0 - mu * (double)v0);
+        k.e1 = (float)((double)u0 * (double)u0 - (double)v0);
+    } else if (g.model == RD_BZ) {
+        const double A = g.p[2], B = g.p[3];
+        const float v0 = (float)(B / A);
+        k.u0 = (float)A;
+        k.v0 = v0;
+        k.e0 = (float)(A * (A * (double)v0 - B));
+        k.c1 = (float)(2.0 * A * (double)v0 - (B + 1.0));
+        k.c2 = (float)(B - 2.0 * A * (double)v0);
+    }
+    return k;
+}
+
+// F at one node from its state (a, b) and the neighbour sums su, sv.
+template <int MODEL>
+__device__ __forceinline__ void rhs_cell(float a, float b, float su, float sv, const RkcK &k, float &Fu, float &Fv) {
+    const float lu = k.du * fmaf(-4.f, a, su), lv = k.dv * fmaf(-4.f, b, sv);
+    if (MODEL == RD_FHN) {
+        Fu = lu + fmaf(-a * a, a, a - b);
+        Fv = fmaf(k.p2, fmaf(-k.p3, b, a), lv);
+    } else if (MODEL == RD_GM) {
+        // U^2/V - mu U = U (a - mu b + e0) / V,  U^2 - V = a (a + 2 u0) - b + e1
+        const float U = a + k.u0, V = b + k.v0;
+        const float t = fmaf(-k.p3, b, a + k.e0);
+        Fu = fmaf(k.p2, (U * t) / V, lu);
+        Fv = fmaf(k.p2, fmaf(a, a + k.tu0, k.e1) - b, lv);
+    } else if (MODEL == RD_BZ) {
+        const float U = a + k.u0;
+        const float P = fmaf(k.v0 * a, a, (U * U) * b);
+        Fu = fmaf(k.c1, a, k.e0 + P) + lu;
+        Fv = fmaf(k.c2, a, -k.e0 - P) + lv;
+    } else {
+        Fu = lu;
+        Fv = lv;
+    }
+}
+
+// Gershgorin row sums of the Jacobian at one node (field values U, V; n =
+// in-domain neighbours), the larger of the u and v rows.
+template <int MODEL>
+__device__ __forceinline__ float gersh_cell(float U, float V, float n, const RkcK &k) {
+    float fu, fv, gu, gv;
+    if (MODEL == RD_FHN) {
+        fu = fmaf(-3.f * U, U, 1.f); fv = -1.f; gu = k.p2; gv = -k.p2 * k.p3;
+    } else if (MODEL == RD_GM) {
+        const float q = U / V;
+        fu = k.p2 * fmaf(2.f, q, -k.p3); fv = -k.p2 * q * q; gu = 2.f * k.p2 * U; gv = -k.p2;
+    } else if (MODEL == RD_BZ) {
+        const float uv = U * V;
+        fu = fmaf(2.f, uv, -(k.p3 + 1.f)); fv = U * U; gu = fmaf(-2.f, uv, k.p3); gv = -U * U;
+    } else {
+        fu = 0.f; fv = 0.f; gu = 0.f; gv = 0.f;
+    }
+    const float nu = n * k.du, nv = n * k.dv;
+    const float ru = fabsf(fu - nu) + nu + fabsf(fv);
+    const float rv = fabsf(gv - nv) + nv + fabsf(gu);
+    return fmaxf(ru, rv);
+}
+
+// Evaluate the RHS of the tile state (yu, yv) after exchanging its edge rows
+// through ring buffer hb, calling body(i, c, Fu, Fv) for every node.
+template <int MODEL, int G, int TY, int TX, class Body>
+__device__ __forceinline__ void tile_eval(float *hb, int tx, int ty, const float (&yu)[TY][TX],
+                                          const float (&yv)[TY][TX], const RkcK &k, Body body) {
+    constexpr int NX = Tiling<G, TY, TX>::NX;
+    halo_put<G, TY, TX>(hb, tx, ty, yu, yv);
+    __syncthreads();
+    float pu[TX], pv[TX];
+    halo_north<G, TY, TX>(hb, tx, ty, yu, yv, pu, pv);
+#pragma unroll
+    for (int i = 0; i < TY; ++i) {
+        float su[TX], sv[TX];
+        row_south<G, TY, TX>(hb, tx, ty, i, yu, yv, su, sv);
+        float wu, eu, wv, ev;
+        row_west_east<NX>(tx, yu[i][0], yu[i][TX - 1], wu, eu);
+        row_west_east<NX>(tx, yv[i][0], yv[i][TX - 1], wv, ev);
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            const float Lu = c > 0 ? yu[i][c - 1] : wu, Ru = c < TX - 1 ? yu[i][c + 1] : eu;
+            const float Lv = c > 0 ? yv[i][c - 1] : wv, Rv = c < TX - 1 ? yv[i][c + 1] : ev;
+            const float nu = (pu[c] + su[c]) + (Lu + Ru);
+            const float nv = (pv[c] + sv[c]) + (Lv + Rv);
+            float Fu, Fv;
+            rhs_cell<MODEL>(yu[i][c], yv[i][c], nu, nv, k, Fu, Fv);
+            body(i, c, Fu, Fv);
+        }
+#pragma unroll
+        for (int c = 0; c < TX; ++c) { pu[c] = yu[i][c]; pv[c] = yv[i][c]; }
+    }
+}
+
+// Step control state, owned by thread 0 (shared memory).
+struct RkcCtl {
+    double t, t_end, h, h_prev, err_prev;
+    int64_t attempts, n_acc, n_rej, n_rhs;
+    float hf, rho, rho_new;
+    int s, s_used, last, have_prev, after_reject, accept, done, fail;
+};
+
+struct RkcRun {
+    double t_end, h0, rtol, atol;
+    int32_t s_max, s_fixed;
+    int64_t n_fixed, max_attempts;
+};
+
+// Plan the next attempt (thread 0): clip to t_end, pick s from rho.
+__device__ __forceinline__ void rkc_plan(RkcCtl &c, const RkcRun &run, const double *__restrict__ beta) {
+    if (run.s_fixed >= 2) {
+        if (c.n_acc >= run.n_fixed) { c.done = 1; return; }
+        c.h = run.h0;
+        c.s = run.s_fixed;
+    } else {
+        if (!(c.t < c.t_end)) { c.done = 1; return; }
+        if (c.attempts >= run.max_attempts || c.h < 1e-12 * c.t_end) { c.done = 1; c.fail = 1; return; }
+        c.last = 0;
+        if (c.h >= c.t_end - c.t) { c.h = c.t_end - c.t; c.last = 1; }
+        const double hr = c.h * (double)c.rho;
+        int s = 2;
+        while (s < run.s_max && hr > beta[s]) ++s;
+        if (hr > beta[s]) { c.h = beta[run.s_max] / (double)c.rho; c.last = 0; }
+        c.s = s;
+    }
+    c.attempts += 1;
+    c.hf = (float)c.h;
+    c.n_rhs += c.s;
+    if (c.s > c.s_used) c.s_used = c.s;
+}
+
+// Accept or reject the attempt just made (thread 0), then plan the next.
+__device__ __forceinline__ void rkc_decide(RkcCtl &c, const RkcRun &run, const double *__restrict__ beta,
+                                           double sumsq, int m) {
+    if (run.s_fixed >= 2) {
+        c.accept = 1;
+        c.n_acc += 1;
+        rkc_plan(c, run, beta);
+        return;
+    }
+    const double err = sqrt(sumsq / (double)m);
+    if (!isfinite(err)) { c.accept = 0; c.done = 1; c.fail = 2; return; }
+    const double ef = err > 1e-10 ? err : 1e-10;
+    double fac;
+    if (err <= 1.0) {
+        c.accept = 1;
+        c.t = c.last ? c.t_end : c.t + c.h;
+        c.n_acc += 1;
+        c.rho = c.rho_new;
+        fac = 0.8 * pow(ef, -1.0 / 3.0);
+        if (c.have_prev) fac = fac * (c.h / c.h_prev) * pow(c.err_prev / ef, 1.0 / 3.0);
+        fac = fmin(fmax(fac, 0.1), 10.0);
+        if (c.after_reject && fac > 1.0) fac = 1.0;
+        c.h_prev = c.h;
+        c.err_prev = ef;
+        c.have_prev = 1;
+        c.after_reject = 0;
+    } else {
+        c.accept = 0;
+        c.n_rej += 1;
+        fac = fmin(fmax(0.8 * pow(ef, -1.0 / 3.0), 0.1), 10.0);
+        c.after_reject = 1;
+    }
+    c.h = fac * c.h;
+    rkc_plan(c, run, beta);
+}
+
+// Block reduction of (sum of squares, max rho) to thread 0.  red: 64 doubles.
+__device__ __forceinline__ void block_reduce2(double &ss, float &mx, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) { red[warp] = ss; red[32 + warp] = (double)mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < nw; ++w) { a += red[w]; b = fmax(b, red[32 + w]); }
+        ss = a;
+        mx = (float)b;
+    }
+}
+
+template <int MODEL, int G, int TY, int TX>
+__global__ void __launch_bounds__(Tiling<G, TY, TX>::NT, 1)
+rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun run, double t_end,
+              const float4 *__restrict__ tab, const double *__restrict__ beta, int64_t *__restrict__ stats,
+              double p0, double p1, double p2, double p3, double *__restrict__ residual,
+              uint32_t *__restrict__ status) {
+    using T = Tiling<G, TY, TX>;
+    constexpr int NX = T::NX;
+    constexpr int M = 2 * G * G;
+    extern __shared__ float4 smem_f4[];
+    float *ring = reinterpret_cast<float *>(smem_f4);
+    double *red = reinterpret_cast<double *>(ring + T::HALO_FLOATS);
+    RkcCtl &c = *reinterpret_cast<RkcCtl *>(red + 64);
+    const int tid = threadIdx.x, tx = tid % NX, ty = tid / NX;
+    const int r = blockIdx.x;
+    float *base = fields + field_offset + (int64_t)r * M;
+    const bool adaptive = run.s_fixed < 2;
+
+    float y0u[TY][TX], y0v[TY][TX], f0u[TY][TX], f0v[TY][TX];
+    float d1u[TY][TX], d1v[TY][TX], d2u[TY][TX], d2v[TY][TX];
+    float yu[TY][TX], yv[TY][TX];
+    tile_load<G, TY, TX>(base, tx, ty, y0u, y0v);
+    {
+        CoefF cf{};
+        cf.u0 = k.u0;
+        cf.v0 = k.v0;
+        tile_to_state<MODEL, TY, TX>(y0u, y0v, cf);
+    }
+    // in-domain neighbour count of each node (Gershgorin row weights)
+    auto ncount = [&](int i, int cc) {
+        const int y = ty * TY + i, x = tx * TX + cc;
+        return (float)((x > 0) + (x < G - 1) + (y > 0) + (y < G - 1));
+    };
+
+    int hk = 0;
+    // F(Y_0) and rho(Y_0)
+    float rmax = 0.f;
+    tile_eval<MODEL, G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, y0u, y0v, k,
+                                [&](int i, int cc, float Fu, float Fv) {
+                                    f0u[i][cc] = Fu;
+                                    f0v[i][cc] = Fv;
+                                    if (adaptive)
+                                        rmax = fmaxf(rmax, gersh_cell<MODEL>(y0u[i][cc] + k.u0, y0v[i][cc] + k.v0,
+                                                                             ncount(i, cc), k));
+                                });
+    hk ^= 1;
+    {
+        double dummy = 0.0;
+        block_reduce2(dummy, rmax, red);
+    }
+    if (tid == 0) {
+        c.t = 0.0;
+        c.t_end = t_end;
+        c.h = run.h0;
+        c.h_prev = 0.0;
+        c.err_prev = 0.0;
+        c.attempts = 0;
+        c.n_acc = 0;
+        c.n_rej = 0;
+        c.n_rhs = 1;
+        c.rho = rmax;
+        c.s = 0;
+        c.s_used = 0;
+        c.have_prev = 0;
+        c.after_reject = 0;
+        c.accept = 0;
+        c.done = 0;
+        c.fail = 0;
+        rkc_plan(c, run, beta);
+    }
+    __syncthreads();
+
+    while (!c.done) {
+        const int s = c.s;
+        const float h = c.hf;
+        const float4 *row = tab + (size_t)s * RKC_STRIDE;
+        // stage 1
+        {
+            const float m1 = row[1].z * h;
+#pragma unroll
+            for (int i = 0; i < TY; ++i)
+#pragma unroll
+                for (int cc = 0; cc < TX; ++cc) {
+                    d1u[i][cc] = m1 * f0u[i][cc];
+                    d1v[i][cc] = m1 * f0v[i][cc];
+                    d2u[i][cc] = 0.f;
+                    d2v[i][cc] = 0.f;
+                }
+        }
+        // stages 2..s
+        for (int j = 2; j <= s; ++j) {
+            const float4 cj = row[j];
+            const float mth = cj.z * h, gth = cj.w * h;
+#pragma unroll
+            for (int i = 0; i < TY; ++i)
+#pragma unroll
+                for (int cc = 0; cc < TX; ++cc) {
+                    yu[i][cc] = y0u[i][cc] + d1u[i][cc];
+                    yv[i][cc] = y0v[i][cc] + d1v[i][cc];
+                }
+            tile_eval<MODEL, G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, yu, yv, k,
+                                        [&](int i, int cc, float Fu, float Fv) {
+                                            const float nu_ = fmaf(cj.x, d1u[i][cc],
+                                                                   fmaf(cj.y, d2u[i][cc],
+                                                                        fmaf(mth, Fu, gth * f0u[i][cc])));
+                                            const float nv_ = fmaf(cj.x, d1v[i][cc],
+                                                                   fmaf(cj.y, d2v[i][cc],
+                                                                        fmaf(mth, Fv, gth * f0v[i][cc])));
+                                            d2u[i][cc] = d1u[i][cc];
+                                            d2v[i][cc] = d1v[i][cc];
+                                            d1u[i][cc] = nu_;
+                                            d1v[i][cc] = nv_;
+                                        });
+            hk ^= 1;
+        }
+        // Y_s, F(Y_s) (kept in d2), error estimate and rho(Y_s)
+#pragma unroll
+        for (int i = 0; i < TY; ++i)
+#pragma unroll
+            for (int cc = 0; cc < TX; ++cc) {
+                yu[i][cc] = y0u[i][cc] + d1u[i][cc];
+                yv[i][cc] = y0v[i][cc] + d1v[i][cc];
+            }
+        float acc = 0.f;
+        rmax = 0.f;
+        const float rtol = (float)run.rtol, atol = (float)run.atol, h04 = 0.4f * h;
+        tile_eval<MODEL, G, TY, TX>(
+            ring + hk * (T::HALO_FLOATS / 2), tx, ty, yu, yv, k, [&](int i, int cc, float Fu, float Fv) {
+                d2u[i][cc] = Fu;
+                d2v[i][cc] = Fv;
+                if (adaptive) {
+                    // est = (12 (Y_0 - Y_s) + 6 h (F_0 + F_s)) / 15,  Y_0 - Y_s = -D_s
+                    const float eu = fmaf(-0.8f, d1u[i][cc], h04 * (f0u[i][cc] + Fu));
+                    const float ev = fmaf(-0.8f, d1v[i][cc], h04 * (f0v[i][cc] + Fv));
+                    const float U0 = y0u[i][cc] + k.u0, V0 = y0v[i][cc] + k.v0;
+                    const float Us = yu[i][cc] + k.u0, Vs = yv[i][cc] + k.v0;
+                    const float qu = eu / fmaf(rtol, fmaxf(fabsf(U0), fabsf(Us)), atol);
+                    const float qv = ev / fmaf(rtol, fmaxf(fabsf(V0), fabsf(Vs)), atol);
+                    acc = fmaf(qu, qu, fmaf(qv, qv, acc));
+                    rmax = fmaxf(rmax, gersh_cell<MODEL>(Us, Vs, ncount(i, cc), k));
+                }
+            });
+        hk ^= 1;
+        double ss = (double)acc;
+        block_reduce2(ss, rmax, red);
+        if (tid == 0) {
+            c.rho_new = rmax;
+            rkc_decide(c, run, beta, ss, M);
+        }
+        __syncthreads();
+        if (c.accept) {
+#pragma unroll
+            for (int i = 0; i < TY; ++i)
+#pragma unroll
+                for (int cc = 0; cc < TX; ++cc) {
+                    y0u[i][cc] = yu[i][cc];
+                    y0v[i][cc] = yv[i][cc];
+                    f0u[i][cc] = d2u[i][cc];
+                    f0v[i][cc] = d2v[i][cc];
+                }
+        }
+    }
+    {
+        CoefF cf{};
+        cf.u0 = k.u0;
+        cf.v0 = k.v0;
+        tile_from_state<MODEL, TY, TX>(y0u, y0v, cf);
+    }
+    tile_store<G, TY, TX>(base, tx, ty, y0u, y0v);
+    if (tid == 0) {
+        if (stats) {
+            int64_t *st = stats + 4 * (int64_t)r;
+            st[0] = c.n_acc;
+            st[1] = c.n_rej;
+            st[2] = c.n_rhs;
+            st[3] = c.s_used;
+        }
+        if (c.fail == 1) atomicOr(status, (unsigned)ST_STEPFAIL);
+        if (c.fail == 2) atomicOr(status, (unsigned)ST_NONFINITE);
+    }
+    residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, ring);
+}
+
+template <int G> struct RkcShape;
+template <> struct RkcShape<32> { static constexpr int TY = 2, TX = 1; };
+template <> struct RkcShape<64> { static constexpr int TY = 4, TX = 2; };
+
+template <int MODEL, int G>
+static rd_status launch_rkc_mg(const GroupDev &g, float *fields, const RkcRun &run, int64_t *stats,
+                               double *residual, uint32_t *status, cudaStream_t s) {
+    constexpr int TY = RkcShape<G>::TY, TX = RkcShape<G>::TX;
+    using T = Tiling<G, TY, TX>;
+    const size_t smem = T::SMEM + 64 * sizeof(double) + sizeof(RkcCtl);
+    auto kern = rd_rkc_kernel<MODEL, G, TY, TX>;
+    RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const double t_end = run.t_end > 0.0 ? run.t_end : g.dt * (double)g.n_steps;
+    kern<<<g.n_real, T::NT, smem, s>>>(fields, g.field_offset, make_rkc_k(g), run, t_end, g_tab, g_beta,
+                                       stats ? stats + 4 * g.real_base : nullptr, g.p[0], g.p[1], g.p[2], g.p[3],
+                                       residual ? residual + 2 * g.real_base : nullptr, status);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+template <int MODEL>
+static rd_status launch_rkc_m(const GroupDev &g, float *fields, const RkcRun &run, int64_t *stats, double *residual,
+                              uint32_t *status, cudaStream_t s) {
+    if (g.G == 32) return launch_rkc_mg<MODEL, 32>(g, fields, run, stats, residual, status, s);
+    if (g.G == 64) return launch_rkc_mg<MODEL, 64>(g, fields, run, stats, residual, status, s);
+    return RD_ERR_UNSUPPORTED;
+}
+
+bool rkc_supported(const GroupDev &g) { return g.G == 32 || g.G == 64; }
+
+rd_status launch_rkc_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats, double *residual,
+                           uint32_t *status, cudaStream_t s) {
+    rd_status st = rkc_tables(s);
+    if (st != RD_OK) return st;
+    RkcRun run{o.t_end, o.h0, o.rtol, o.atol, o.s_max, o.s_fixed, o.n_fixed, o.max_attempts};
+    switch (g.model) {
+        case RD_FHN: return launch_rkc_m<RD_FHN>(g, fields, run, stats, residual, status, s);
+        case RD_GM: return launch_rkc_m<RD_GM>(g, fields, run, stats, residual, status, s);
+        case RD_DIFF: return launch_rkc_m<RD_DIFF>(g, fields, run, stats, residual, status, s);
+        case RD_BZ: return launch_rkc_m<RD_BZ>(g, fields, run, stats, residual, status, s);
+        default: return RD_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace rdcil

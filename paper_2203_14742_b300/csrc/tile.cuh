@@ -252,6 +252,57 @@ __device__ __forceinline__ void rhs_f64(double u, double v, double nu, double su
     Fv = p[1] * lv + rv;
 }
 
+// FP64 steady-state residual of the final state of realisation r, read
+// back from global memory after the block stored it (block-visible after
+// the barrier): max |F| and sqrt(mean F^2) over both species, F from the
+// stored FP32 values in the plain operation order.  Thread t takes nodes
+// t, t + NT, ...; the sum is reduced with warp shuffles, then across warps.
+template <int MODEL, int G>
+__device__ __forceinline__ void residual_from_global(const float *__restrict__ base, double p0, double p1, double p2,
+                                                     double p3, double *__restrict__ residual,
+                                                     uint32_t *__restrict__ status, int r, void *smem) {
+    __syncthreads();
+    const double p[4] = {p0, p1, p2, p3};
+    const double h2 = (double)(G - 1) * (double)(G - 1);
+    const float *u = base, *v = base + G * G;
+    double mx = 0.0, ss = 0.0;
+    bool bad = false;
+    for (int k = threadIdx.x; k < G * G; k += blockDim.x) {
+        const int y = k / G, x = k - y * G;
+        const int kn = (y > 0 ? k - G : k), ks = (y < G - 1 ? k + G : k);
+        const int kw = (x > 0 ? k - 1 : k), ke = (x < G - 1 ? k + 1 : k);
+        double Fu, Fv;
+        rhs_f64<MODEL>(u[k], v[k], u[kn], u[ks], u[kw], u[ke], v[kn], v[ks], v[kw], v[ke], p, h2, Fu, Fv);
+        bad |= !isfinite(u[k]) || !isfinite(v[k]) || !isfinite(Fu) || !isfinite(Fv);
+        mx = fmax(mx, fmax(fabs(Fu), fabs(Fv)));
+        ss += Fu * Fu + Fv * Fv;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    }
+    const int anybad = __syncthreads_or(bad ? 1 : 0);
+    double *red = reinterpret_cast<double *>(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) { red[warp] = mx; red[nw + warp] = ss; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0, s = 0.0;
+        for (int wi = 0; wi < nw; ++wi) { m = fmax(m, red[wi]); s += red[nw + wi]; }
+        if (anybad) {
+            atomicOr(status, (unsigned)ST_NONFINITE);
+            m = __longlong_as_double(0x7ff8000000000000ll);
+            s = m;
+        }
+        if (residual) {
+            residual[2 * r] = m;
+            residual[2 * r + 1] = sqrt(s / (double)(2 * G * G));
+        }
+    }
+    __syncthreads();
+}
+
 template <int MODEL, int TY, int TX>
 __device__ __forceinline__ void tile_to_state(float (&u)[TY][TX], float (&v)[TY][TX], const CoefF &c) {
 #pragma unroll
