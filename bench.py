@@ -88,6 +88,10 @@ def parse():
                          "and GM 128x128 set shapes")
     ap.add_argument("--mcil-only", action="store_true",
                     help="time only the multi-feature correlation integral (for profiling)")
+    ap.add_argument("--rkc", action="store_true",
+                    help="add the adaptive stabilised RK2 (App. B.2) against the Euler stepper on c2")
+    ap.add_argument("--rkc-only", action="store_true",
+                    help="run only the adaptive stabilised RK2 comparison and print it")
     ap.add_argument("--gram-large-only", action="store_true",
                     help="time only the tensor-core Gram and correlation integral on 2 x 1024 patterns of "
                          "d = 32768 (for profiling); prints that object alone")
@@ -418,6 +422,8 @@ def run_ours(args, rank, world, local_rank):
         out["mcil"] = mcil_bench(p, torch, dev, stream)
     if args.stream and rank == 0:
         out["stream"] = stream_bench(p, torch, dev, stream, pk, src)
+    if args.rkc and rank == 0:
+        out["rkc"] = rkc_bench(p, torch, dev, stream, pk, src)
     return out
 
 
@@ -500,6 +506,82 @@ def stream_bench(p, torch, dev, stream, pk, src, depths=(1, 2, 4, 8)):
     assert sim.sync_status() == 0
     return {"workload": "FHN 512x512, 128 realisations, 64 Euler steps (dt 2^-16)", "peak_hbm_gbs": pk["hbm_gbs"],
             "peak_note": "%s peaks file; achieved = 16 B per cell per launch / time" % src, "depths": out}
+
+
+# FP32 instructions per cell per RHS stage of the adaptive RK2 kernel (FHN):
+# 5-point sums and Laplacian 10, kinetics 5, stage state Y_0 + D 2,
+# increment recurrence 8, sum 1.
+RKC_FP32_INST_PER_CELL_STAGE = {W.FHN: 26}
+
+
+def rkc_bench(p, torch, dev, stream, pk, src, tols=(1e-5, 1e-6, 1e-7)):
+    """Adaptive stabilised second-order RK (App. B.2, Chebyshev
+    coefficients) against the explicit Euler stepper on the FHN 64x64
+    workload (2 x 64 realisations, integrated to T = 10^4 x 2^-10): time to
+    T on the GPU, RHS evaluations, and the accuracy of both on a sample of
+    two realisations against an accurate oracle reference (adaptive,
+    tolerance 1e-9)."""
+    import oracle
+    cfg = W.config("c2")
+    gd = cfg["groups"][0]
+    G, n = gd["G"], gd["n_real"]
+    T = gd["dt"] * gd["n_steps"]
+    sim = p.Simulation([p.Group.from_dict(gd)], device=dev)
+    w0 = sim.group_fields(0)[:2].cpu().numpy()
+    ref, _, failed = oracle.rkc_adaptive(gd["model"], gd["params"], T, 1e-3, 1e-9, 1e-9, w0)
+    assert failed == 0
+
+    def rel(a):
+        a = np.asarray(a, np.float64)
+        num = np.abs(a - ref).reshape(2, 2, -1).max(-1)
+        return float((num / np.abs(ref).reshape(2, 2, -1).max(-1)).max())
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps + 1):
+            sim.reinit()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return min(ts[1:]), r
+
+    t_eul, _ = timed(lambda: sim.integrate(residual=False))
+    assert sim.sync_status() == 0
+    err_eul = rel(sim.group_fields(0)[:2].cpu().numpy())
+    peak_alu = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    rows = []
+    for tol in tols:
+        t, (st, _) = timed(lambda: sim.integrate_rkc(1e-3, rtol=tol, atol=tol))
+        assert sim.sync_status() == 0
+        st = st.cpu().numpy()
+        err = rel(sim.group_fields(0)[:2].cpu().numpy())
+        n_rhs = int(st[:, 2].sum())
+        inst = n_rhs * G * G * RKC_FP32_INST_PER_CELL_STAGE[gd["model"]]
+        rows.append({"tol": tol, "ms": t * 1e3, "steps_mean": float(st[:, 0].mean()),
+                     "rejected_mean": float(st[:, 1].mean()), "rhs_mean": float(st[:, 2].mean()),
+                     "s_max_used": int(st[:, 3].max()), "rel_err_sample": err,
+                     "cell_stage_updates_per_s": n_rhs * G * G / t,
+                     "alu_tinst_per_s": inst / t / 1e12, "alu_frac": inst / t / 1e12 / peak_alu,
+                     "speedup_vs_euler": t_eul / t, "as_accurate_as_euler": err <= err_eul})
+    # fixed schedule (no step control): the pure per-stage cost
+    s_fix, n_fix = 16, 128
+    t_fix, _ = timed(lambda: sim.integrate_rkc(0.1, s_fixed=s_fix, n_fixed=n_fix))
+    assert sim.sync_status() == 0
+    n_rhs = n * (1 + s_fix * n_fix)
+    inst = n_rhs * G * G * RKC_FP32_INST_PER_CELL_STAGE[gd["model"]]
+    fixed = {"s": s_fix, "steps": n_fix, "h": 0.1, "ms": t_fix * 1e3, "us_per_stage": t_fix * 1e6 / (1 + s_fix * n_fix),
+             "cell_stage_updates_per_s": n_rhs * G * G / t_fix, "alu_tinst_per_s": inst / t_fix / 1e12,
+             "alu_frac": inst / t_fix / 1e12 / peak_alu}
+    return {"workload": "FHN 64x64, 2 x 64 realisations, 0 -> T = 10^4 x 2^-10 (the c2 horizon)",
+            "fixed_schedule": fixed,
+            "euler": {"ms": t_eul * 1e3, "steps": gd["n_steps"], "rel_err_sample": err_eul},
+            "reference": "oracle adaptive, tolerance 1e-9, realisations 0 and 1",
+            "peak_note": "alu peak = 148 SM x 128 FP32 lanes x max SM clock (%s peaks file); "
+                         "%d FP32 instructions per cell per RHS stage" % (src, RKC_FP32_INST_PER_CELL_STAGE[gd["model"]]),
+            "tolerances": rows}
 
 
 def mcil_bench(p, torch, dev, stream):
@@ -658,6 +740,16 @@ def main():
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)
         print(json.dumps(mcil_bench(p, torch, dev, torch.cuda.current_stream(dev))))
+        return
+    if args.rkc_only:
+        import torch
+        import paper_2203_14742_b300 as p
+        from paper_2203_14742_b300 import build as B
+        B.build()
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        pk, src = peaks()
+        print(json.dumps(rkc_bench(p, torch, dev, torch.cuda.current_stream(dev), pk, src)))
         return
     if args.gram_large_only:
         import torch

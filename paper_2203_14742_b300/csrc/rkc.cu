@@ -190,14 +190,20 @@ __device__ __forceinline__ float gersh_cell(float U, float V, float n, const Rkc
     return fmaxf(ru, rv);
 }
 
-// Evaluate the RHS of the tile state (yu, yv) after exchanging its edge rows
-// through ring buffer hb, calling body(i, c, Fu, Fv) for every node.
-template <int MODEL, int G, int TY, int TX, class Body>
-__device__ __forceinline__ void tile_eval(float *hb, int tx, int ty, const float (&yu)[TY][TX],
-                                          const float (&yv)[TY][TX], const RkcK &k, Body body) {
-    constexpr int NX = Tiling<G, TY, TX>::NX;
+// Exchange the edge rows of the tile state (yu, yv) through ring buffer hb
+// (one barrier), then evaluate its RHS, calling body(i, c, Fu, Fv) for
+// every node.
+template <int G, int TY, int TX>
+__device__ __forceinline__ void tile_exchange(float *hb, int tx, int ty, const float (&yu)[TY][TX],
+                                              const float (&yv)[TY][TX]) {
     halo_put<G, TY, TX>(hb, tx, ty, yu, yv);
     __syncthreads();
+}
+
+template <int MODEL, int G, int TY, int TX, class Body>
+__device__ __forceinline__ void tile_apply(const float *hb, int tx, int ty, const float (&yu)[TY][TX],
+                                           const float (&yv)[TY][TX], const RkcK &k, Body body) {
+    constexpr int NX = Tiling<G, TY, TX>::NX;
     float pu[TX], pv[TX];
     halo_north<G, TY, TX>(hb, tx, ty, yu, yv, pu, pv);
 #pragma unroll
@@ -222,11 +228,45 @@ __device__ __forceinline__ void tile_eval(float *hb, int tx, int ty, const float
     }
 }
 
+template <int MODEL, int G, int TY, int TX, class Body>
+__device__ __forceinline__ void tile_eval(float *hb, int tx, int ty, const float (&yu)[TY][TX],
+                                          const float (&yv)[TY][TX], const RkcK &k, Body body) {
+    tile_exchange<G, TY, TX>(hb, tx, ty, yu, yv);
+    tile_apply<MODEL, G, TY, TX>(hb, tx, ty, yu, yv, k, body);
+}
+
+// One stage j >= 2 of the increment recurrence: Y = Y_0 + D_{j-1} (dl),
+// D_j = mu_j D_{j-1} + nu_j D_{j-2} + mt_j h F(Y) + gt_j h F_0, written over
+// D_{j-2} (dp).  Coefficients from crow[j] (shared memory, read after the
+// exchange barrier).
+template <int MODEL, int G, int TY, int TX>
+__device__ __forceinline__ void rkc_stage(float *hb, int tx, int ty, const float (&y0u)[TY][TX],
+                                          const float (&y0v)[TY][TX], const float (&f0u)[TY][TX],
+                                          const float (&f0v)[TY][TX], const float (&dlu)[TY][TX],
+                                          const float (&dlv)[TY][TX], float (&dpu)[TY][TX], float (&dpv)[TY][TX],
+                                          float (&yu)[TY][TX], float (&yv)[TY][TX], const float4 *crow, int j,
+                                          float h, const RkcK &k) {
+#pragma unroll
+    for (int i = 0; i < TY; ++i)
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            yu[i][c] = y0u[i][c] + dlu[i][c];
+            yv[i][c] = y0v[i][c] + dlv[i][c];
+        }
+    tile_exchange<G, TY, TX>(hb, tx, ty, yu, yv);
+    const float4 cj = crow[j];
+    const float mth = cj.z * h, gth = cj.w * h;
+    tile_apply<MODEL, G, TY, TX>(hb, tx, ty, yu, yv, k, [&](int i, int c, float Fu, float Fv) {
+        dpu[i][c] = fmaf(cj.x, dlu[i][c], fmaf(cj.y, dpu[i][c], fmaf(mth, Fu, gth * f0u[i][c])));
+        dpv[i][c] = fmaf(cj.x, dlv[i][c], fmaf(cj.y, dpv[i][c], fmaf(mth, Fv, gth * f0v[i][c])));
+    });
+}
+
 // Step control state, owned by thread 0 (shared memory).
 struct RkcCtl {
-    double t, t_end, h, h_prev, err_prev;
+    double t, t_end, h, h_prev;
     int64_t attempts, n_acc, n_rej, n_rhs;
-    float hf, rho, rho_new;
+    float err_prev, hf, rho, rho_new;
     int s, s_used, last, have_prev, after_reject, accept, done, fail;
 };
 
@@ -248,7 +288,10 @@ __device__ __forceinline__ void rkc_plan(RkcCtl &c, const RkcRun &run, const dou
         c.last = 0;
         if (c.h >= c.t_end - c.t) { c.h = c.t_end - c.t; c.last = 1; }
         const double hr = c.h * (double)c.rho;
-        int s = 2;
+        // beta(s) < 0.66 s^2 for every s, so no s below sqrt(hr / 0.66)
+        // qualifies: start the search for the smallest s there
+        int s = (int)sqrtf((float)hr / 0.66f);
+        s = s < 2 ? 2 : (s > run.s_max ? run.s_max : s);
         while (s < run.s_max && hr > beta[s]) ++s;
         if (hr > beta[s]) { c.h = beta[run.s_max] / (double)c.rho; c.last = 0; }
         c.s = s;
@@ -260,27 +303,29 @@ __device__ __forceinline__ void rkc_plan(RkcCtl &c, const RkcRun &run, const dou
 }
 
 // Accept or reject the attempt just made (thread 0), then plan the next.
+// The step-size factor is computed in FP32 (the FP32 error estimate it
+// comes from is far less precise than that); t and h stay FP64.
 __device__ __forceinline__ void rkc_decide(RkcCtl &c, const RkcRun &run, const double *__restrict__ beta,
-                                           double sumsq, int m) {
+                                           float sumsq, int m) {
     if (run.s_fixed >= 2) {
         c.accept = 1;
         c.n_acc += 1;
         rkc_plan(c, run, beta);
         return;
     }
-    const double err = sqrt(sumsq / (double)m);
+    const float err = sqrtf(sumsq / (float)m);
     if (!isfinite(err)) { c.accept = 0; c.done = 1; c.fail = 2; return; }
-    const double ef = err > 1e-10 ? err : 1e-10;
-    double fac;
-    if (err <= 1.0) {
+    const float ef = fmaxf(err, 1e-10f);
+    float fac;
+    if (err <= 1.f) {
         c.accept = 1;
         c.t = c.last ? c.t_end : c.t + c.h;
         c.n_acc += 1;
         c.rho = c.rho_new;
-        fac = 0.8 * pow(ef, -1.0 / 3.0);
-        if (c.have_prev) fac = fac * (c.h / c.h_prev) * pow(c.err_prev / ef, 1.0 / 3.0);
-        fac = fmin(fmax(fac, 0.1), 10.0);
-        if (c.after_reject && fac > 1.0) fac = 1.0;
+        fac = 0.8f / cbrtf(ef);
+        if (c.have_prev) fac = fac * ((float)c.h / (float)c.h_prev) * cbrtf(c.err_prev / ef);
+        fac = fminf(fmaxf(fac, 0.1f), 10.f);
+        if (c.after_reject && fac > 1.f) fac = 1.f;
         c.h_prev = c.h;
         c.err_prev = ef;
         c.have_prev = 1;
@@ -288,29 +333,58 @@ __device__ __forceinline__ void rkc_decide(RkcCtl &c, const RkcRun &run, const d
     } else {
         c.accept = 0;
         c.n_rej += 1;
-        fac = fmin(fmax(0.8 * pow(ef, -1.0 / 3.0), 0.1), 10.0);
+        fac = fminf(fmaxf(0.8f / cbrtf(ef), 0.1f), 10.f);
         c.after_reject = 1;
     }
-    c.h = fac * c.h;
+    c.h = (double)fac * c.h;
     rkc_plan(c, run, beta);
 }
 
-// Block reduction of (sum of squares, max rho) to thread 0.  red: 64 doubles.
-__device__ __forceinline__ void block_reduce2(double &ss, float &mx, double *red) {
+// Block reduction of (sum of squares, max rho): warp shuffles, then warp 0
+// combines the per-warp partials (every lane of warp 0 ends with the
+// result).  red: 64 floats.
+__device__ __forceinline__ void block_reduce2(float &ss, float &mx, float *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ss += __shfl_xor_sync(0xffffffffu, ss, o);
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0) { red[warp] = ss; red[32 + warp] = (double)mx; }
+    if (lane == 0) { red[warp] = ss; red[32 + warp] = mx; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < nw; ++w) { a += red[w]; b = fmax(b, red[32 + w]); }
-        ss = a;
-        mx = (float)b;
+    if (warp == 0) {
+        ss = lane < nw ? red[lane] : 0.f;
+        mx = lane < nw ? red[32 + lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
     }
+}
+
+// Shared memory (byte offsets): halo ring at 0 | 64 doubles of reduction
+// scratch | RkcCtl | coefficient row float4[RKC_STRIDE] at a 16-byte
+// boundary | beta[RKC_STRIDE] doubles.
+template <int G, int TY, int TX>
+__host__ __device__ constexpr size_t rkc_red_off() {
+    return Tiling<G, TY, TX>::SMEM;
+}
+template <int G, int TY, int TX>
+__host__ __device__ constexpr size_t rkc_ctl_off() {
+    return rkc_red_off<G, TY, TX>() + 64 * sizeof(double);
+}
+template <int G, int TY, int TX>
+__host__ __device__ constexpr size_t rkc_crow_off() {
+    return (rkc_ctl_off<G, TY, TX>() + sizeof(RkcCtl) + 15) / 16 * 16;
+}
+template <int G, int TY, int TX>
+__host__ __device__ constexpr size_t rkc_beta_off() {
+    return rkc_crow_off<G, TY, TX>() + RKC_STRIDE * sizeof(float4);
+}
+template <int G, int TY, int TX>
+__host__ __device__ constexpr size_t rkc_smem() {
+    return rkc_beta_off<G, TY, TX>() + RKC_STRIDE * sizeof(double);
 }
 
 template <int MODEL, int G, int TY, int TX>
@@ -323,10 +397,17 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
     constexpr int NX = T::NX;
     constexpr int M = 2 * G * G;
     extern __shared__ float4 smem_f4[];
-    float *ring = reinterpret_cast<float *>(smem_f4);
-    double *red = reinterpret_cast<double *>(ring + T::HALO_FLOATS);
-    RkcCtl &c = *reinterpret_cast<RkcCtl *>(red + 64);
+    static_assert(rkc_red_off<G, TY, TX>() % 16 == 0 && rkc_ctl_off<G, TY, TX>() % 16 == 0 &&
+                      rkc_crow_off<G, TY, TX>() % 16 == 0 && rkc_beta_off<G, TY, TX>() % 16 == 0,
+                  "shared-memory regions must start on 16-byte boundaries");
+    char *sb = reinterpret_cast<char *>(smem_f4);
+    float *ring = reinterpret_cast<float *>(sb);
+    double *red = reinterpret_cast<double *>(sb + rkc_red_off<G, TY, TX>());
+    RkcCtl &c = *reinterpret_cast<RkcCtl *>(sb + rkc_ctl_off<G, TY, TX>());
+    float4 *crow = reinterpret_cast<float4 *>(sb + rkc_crow_off<G, TY, TX>());
+    double *betaS = reinterpret_cast<double *>(sb + rkc_beta_off<G, TY, TX>());
     const int tid = threadIdx.x, tx = tid % NX, ty = tid / NX;
+    for (int i = tid; i < RKC_STRIDE; i += blockDim.x) betaS[i] = beta[i];
     const int r = blockIdx.x;
     float *base = fields + field_offset + (int64_t)r * M;
     const bool adaptive = run.s_fixed < 2;
@@ -360,15 +441,15 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
                                 });
     hk ^= 1;
     {
-        double dummy = 0.0;
-        block_reduce2(dummy, rmax, red);
+        float dummy = 0.f;
+        block_reduce2(dummy, rmax, reinterpret_cast<float *>(red));
     }
     if (tid == 0) {
         c.t = 0.0;
         c.t_end = t_end;
         c.h = run.h0;
         c.h_prev = 0.0;
-        c.err_prev = 0.0;
+        c.err_prev = 0.f;
         c.attempts = 0;
         c.n_acc = 0;
         c.n_rej = 0;
@@ -381,7 +462,7 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
         c.accept = 0;
         c.done = 0;
         c.fail = 0;
-        rkc_plan(c, run, beta);
+        rkc_plan(c, run, betaS);
     }
     __syncthreads();
 
@@ -389,6 +470,9 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
         const int s = c.s;
         const float h = c.hf;
         const float4 *row = tab + (size_t)s * RKC_STRIDE;
+        // coefficient row of this s into shared memory (first read after the
+        // exchange barrier of stage 2)
+        for (int i = tid; i <= s; i += blockDim.x) crow[i] = row[i];
         // stage 1
         {
             const float m1 = row[1].z * h;
@@ -402,30 +486,24 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
                     d2v[i][cc] = 0.f;
                 }
         }
-        // stages 2..s
-        for (int j = 2; j <= s; ++j) {
-            const float4 cj = row[j];
-            const float mth = cj.z * h, gth = cj.w * h;
+        // stages 2..s, two per iteration so that the roles of the latest and
+        // previous increments alternate without register moves
+        for (int j = 2; j <= s; j += 2) {
+            rkc_stage<MODEL, G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, y0u, y0v, f0u, f0v, d1u, d1v, d2u,
+                                        d2v, yu, yv, crow, j, h, k);
+            hk ^= 1;
+            if (j + 1 > s) {
 #pragma unroll
-            for (int i = 0; i < TY; ++i)
+                for (int i = 0; i < TY; ++i)
 #pragma unroll
-                for (int cc = 0; cc < TX; ++cc) {
-                    yu[i][cc] = y0u[i][cc] + d1u[i][cc];
-                    yv[i][cc] = y0v[i][cc] + d1v[i][cc];
-                }
-            tile_eval<MODEL, G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, yu, yv, k,
-                                        [&](int i, int cc, float Fu, float Fv) {
-                                            const float nu_ = fmaf(cj.x, d1u[i][cc],
-                                                                   fmaf(cj.y, d2u[i][cc],
-                                                                        fmaf(mth, Fu, gth * f0u[i][cc])));
-                                            const float nv_ = fmaf(cj.x, d1v[i][cc],
-                                                                   fmaf(cj.y, d2v[i][cc],
-                                                                        fmaf(mth, Fv, gth * f0v[i][cc])));
-                                            d2u[i][cc] = d1u[i][cc];
-                                            d2v[i][cc] = d1v[i][cc];
-                                            d1u[i][cc] = nu_;
-                                            d1v[i][cc] = nv_;
-                                        });
+                    for (int cc = 0; cc < TX; ++cc) {
+                        d1u[i][cc] = d2u[i][cc];
+                        d1v[i][cc] = d2v[i][cc];
+                    }
+                break;
+            }
+            rkc_stage<MODEL, G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, y0u, y0v, f0u, f0v, d2u, d2v, d1u,
+                                        d1v, yu, yv, crow, j + 1, h, k);
             hk ^= 1;
         }
         // Y_s, F(Y_s) (kept in d2), error estimate and rho(Y_s)
@@ -449,18 +527,18 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
                     const float ev = fmaf(-0.8f, d1v[i][cc], h04 * (f0v[i][cc] + Fv));
                     const float U0 = y0u[i][cc] + k.u0, V0 = y0v[i][cc] + k.v0;
                     const float Us = yu[i][cc] + k.u0, Vs = yv[i][cc] + k.v0;
-                    const float qu = eu / fmaf(rtol, fmaxf(fabsf(U0), fabsf(Us)), atol);
-                    const float qv = ev / fmaf(rtol, fmaxf(fabsf(V0), fabsf(Vs)), atol);
+                    const float qu = __fdividef(eu, fmaf(rtol, fmaxf(fabsf(U0), fabsf(Us)), atol));
+                    const float qv = __fdividef(ev, fmaf(rtol, fmaxf(fabsf(V0), fabsf(Vs)), atol));
                     acc = fmaf(qu, qu, fmaf(qv, qv, acc));
                     rmax = fmaxf(rmax, gersh_cell<MODEL>(Us, Vs, ncount(i, cc), k));
                 }
             });
         hk ^= 1;
-        double ss = (double)acc;
-        block_reduce2(ss, rmax, red);
+        float ss = acc;
+        block_reduce2(ss, rmax, reinterpret_cast<float *>(red));
         if (tid == 0) {
             c.rho_new = rmax;
-            rkc_decide(c, run, beta, ss, M);
+            rkc_decide(c, run, betaS, ss, M);
         }
         __syncthreads();
         if (c.accept) {
@@ -505,7 +583,7 @@ static rd_status launch_rkc_mg(const GroupDev &g, float *fields, const RkcRun &r
                                double *residual, uint32_t *status, cudaStream_t s) {
     constexpr int TY = RkcShape<G>::TY, TX = RkcShape<G>::TX;
     using T = Tiling<G, TY, TX>;
-    const size_t smem = T::SMEM + 64 * sizeof(double) + sizeof(RkcCtl);
+    const size_t smem = rkc_smem<G, TY, TX>();
     auto kern = rd_rkc_kernel<MODEL, G, TY, TX>;
     RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const double t_end = run.t_end > 0.0 ? run.t_end : g.dt * (double)g.n_steps;
