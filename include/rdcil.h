@@ -243,6 +243,20 @@ typedef struct rd_rkc_opts {
 rd_status rd_integrate_rkc(rd_handle *h, float *d_fields, const rd_rkc_opts *opts, int64_t *d_stats,
                            double *d_residual, void *stream);
 
+/* Tile shapes of the rd_integrate_rkc kernel (nodes per thread, TY x TX):
+ * G = 32: 0 = 2x1 (512 threads, default), 1 = 4x1 (256), 2 = 2x2 (256);
+ * G = 64: 0 = 4x2 (512 threads), 1 = 4x4 (256, default), 2 = 2x4 (512).
+ * Per node every shape runs the same arithmetic, so a fixed schedule gives
+ * bit-identical fields; in adaptive mode the error norm is summed in an
+ * order that follows the tiling, so its last bits, and through the step
+ * sizes the fields, may differ between shapes (a given shape is
+ * deterministic).  The choice (per G, process-wide) is a speed knob.  rd_rkc_set_variant returns RD_ERR_INVALID_ARG for
+ * another G or an unknown variant; rd_rkc_get_variant returns -1 for
+ * another G. */
+int32_t rd_rkc_n_variants(void);
+rd_status rd_rkc_set_variant(int32_t G, int32_t variant);
+int32_t rd_rkc_get_variant(int32_t G);
+
 /* Tile-shape variants of the resident stepper.  Every variant performs the
  * same per-node arithmetic in the same order, so all give bit-identical
  * fields; the choice (per model and G, process-wide) only affects speed.

@@ -52,6 +52,9 @@ _SIGS = {
     "rd_integrate_reference": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "rd_integrate_f64": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "rd_integrate_rkc": (_i32, [_vp, _vp, C.POINTER(RdRkcOpts), _vp, _vp, _vp]),
+    "rd_rkc_n_variants": (_i32, []),
+    "rd_rkc_set_variant": (_i32, [_i32, _i32]),
+    "rd_rkc_get_variant": (_i32, [_i32]),
     "rd_sync_status": (_i32, [_vp, _vp]),
     "rd_n_real_total": (_i64, [_vp]),
     "rd_free": (None, [_vp]),
@@ -281,6 +284,15 @@ class Simulation:
 # correlation integral
 # ---------------------------------------------------------------------------
 _work_cache = {}
+
+
+def rkc_set_variant(G, variant):
+    """Tile shape of the adaptive RK2 kernel for grid side G (32 or 64)."""
+    _check("rd_rkc_set_variant", lib().rd_rkc_set_variant(int(G), int(variant)))
+
+
+def rkc_get_variant(G):
+    return int(lib().rd_rkc_get_variant(int(G)))
 
 
 def variant_shape(G, variant):

@@ -198,6 +198,12 @@ extern "C" rd_status rd_integrate_rkc(rd_handle *hh, float *d_fields, const rd_r
     return RD_OK;
 }
 
+extern "C" int32_t rd_rkc_n_variants(void) { return rkc_n_variants(); }
+extern "C" rd_status rd_rkc_set_variant(int32_t G, int32_t variant) {
+    return rkc_set_variant(G, variant) ? RD_OK : RD_ERR_INVALID_ARG;
+}
+extern "C" int32_t rd_rkc_get_variant(int32_t G) { return rkc_get_variant(G); }
+
 extern "C" rd_status rd_sync_status(rd_handle *hh, void *stream) {
     if (!hh) return RD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -97,6 +97,9 @@ rd_status launch_stream_group(const Handle &h, const GroupDev &g, float *fields,
 void set_gram_spin_limit(uint32_t n);
 bool variant_shape(int G, int vi, int *packed, int *TY, int *TX);
 bool rkc_supported(const GroupDev &g);
+int rkc_n_variants();
+bool rkc_set_variant(int G, int v);
+int rkc_get_variant(int G);
 rd_status launch_rkc_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats, double *residual,
                            uint32_t *status, cudaStream_t s);
 

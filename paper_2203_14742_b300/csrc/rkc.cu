@@ -168,6 +168,37 @@ __device__ __forceinline__ void rhs_cell(float a, float b, float su, float sv, c
     }
 }
 
+// The RHS split for the stages: F_u = du Lu + ku Ru, F_v = dv Lv + kv Rv
+// with the unscaled 5-point sums Lu, Lv and the kinetics' scale factors
+// (ku, kv) = FHN (1, eps), GM (rho, rho), BZ (1, 1), DIFF (0, 0), so a
+// stage folds du, dv, ku, kv into its per-stage weights.
+template <int MODEL>
+__device__ __forceinline__ void react_scale(const RkcK &k, float &ku, float &kv) {
+    if (MODEL == RD_FHN) { ku = 1.f; kv = k.p2; }
+    else if (MODEL == RD_GM) { ku = k.p2; kv = k.p2; }
+    else if (MODEL == RD_BZ) { ku = 1.f; kv = 1.f; }
+    else { ku = 0.f; kv = 0.f; }
+}
+template <int MODEL>
+__device__ __forceinline__ void rhs_parts(float a, float b, const RkcK &k, float &Ru, float &Rv) {
+    if (MODEL == RD_FHN) {
+        Ru = fmaf(-a * a, a, a - b);
+        Rv = fmaf(-k.p3, b, a);
+    } else if (MODEL == RD_GM) {
+        const float U = a + k.u0, V = b + k.v0;
+        Ru = (U * fmaf(-k.p3, b, a + k.e0)) / V;
+        Rv = fmaf(a, a + k.tu0, k.e1) - b;
+    } else if (MODEL == RD_BZ) {
+        const float U = a + k.u0;
+        const float P = fmaf(k.v0 * a, a, (U * U) * b);
+        Ru = fmaf(k.c1, a, k.e0 + P);
+        Rv = fmaf(k.c2, a, -k.e0 - P);
+    } else {
+        Ru = 0.f;
+        Rv = 0.f;
+    }
+}
+
 // Gershgorin row sums of the Jacobian at one node (field values U, V; n =
 // in-domain neighbours), the larger of the u and v rows.
 template <int MODEL>
@@ -191,8 +222,8 @@ __device__ __forceinline__ float gersh_cell(float U, float V, float n, const Rkc
 }
 
 // Exchange the edge rows of the tile state (yu, yv) through ring buffer hb
-// (one barrier), then evaluate its RHS, calling body(i, c, Fu, Fv) for
-// every node.
+// (one barrier); tile_apply then calls body(i, c, su, sv) with the
+// neighbour sums of every node, tile_eval body(i, c, Fu, Fv) with its RHS.
 template <int G, int TY, int TX>
 __device__ __forceinline__ void tile_exchange(float *hb, int tx, int ty, const float (&yu)[TY][TX],
                                               const float (&yv)[TY][TX]) {
@@ -200,9 +231,9 @@ __device__ __forceinline__ void tile_exchange(float *hb, int tx, int ty, const f
     __syncthreads();
 }
 
-template <int MODEL, int G, int TY, int TX, class Body>
+template <int G, int TY, int TX, class Body>
 __device__ __forceinline__ void tile_apply(const float *hb, int tx, int ty, const float (&yu)[TY][TX],
-                                           const float (&yv)[TY][TX], const RkcK &k, Body body) {
+                                           const float (&yv)[TY][TX], Body body) {
     constexpr int NX = Tiling<G, TY, TX>::NX;
     float pu[TX], pv[TX];
     halo_north<G, TY, TX>(hb, tx, ty, yu, yv, pu, pv);
@@ -219,9 +250,7 @@ __device__ __forceinline__ void tile_apply(const float *hb, int tx, int ty, cons
             const float Lv = c > 0 ? yv[i][c - 1] : wv, Rv = c < TX - 1 ? yv[i][c + 1] : ev;
             const float nu = (pu[c] + su[c]) + (Lu + Ru);
             const float nv = (pv[c] + sv[c]) + (Lv + Rv);
-            float Fu, Fv;
-            rhs_cell<MODEL>(yu[i][c], yv[i][c], nu, nv, k, Fu, Fv);
-            body(i, c, Fu, Fv);
+            body(i, c, nu, nv);
         }
 #pragma unroll
         for (int c = 0; c < TX; ++c) { pu[c] = yu[i][c]; pv[c] = yv[i][c]; }
@@ -232,13 +261,18 @@ template <int MODEL, int G, int TY, int TX, class Body>
 __device__ __forceinline__ void tile_eval(float *hb, int tx, int ty, const float (&yu)[TY][TX],
                                           const float (&yv)[TY][TX], const RkcK &k, Body body) {
     tile_exchange<G, TY, TX>(hb, tx, ty, yu, yv);
-    tile_apply<MODEL, G, TY, TX>(hb, tx, ty, yu, yv, k, body);
+    tile_apply<G, TY, TX>(hb, tx, ty, yu, yv, [&](int i, int c, float su, float sv) {
+        float Fu, Fv;
+        rhs_cell<MODEL>(yu[i][c], yv[i][c], su, sv, k, Fu, Fv);
+        body(i, c, Fu, Fv);
+    });
 }
 
 // One stage j >= 2 of the increment recurrence: Y = Y_0 + D_{j-1} (dl),
 // D_j = mu_j D_{j-1} + nu_j D_{j-2} + mt_j h F(Y) + gt_j h F_0, written over
-// D_{j-2} (dp).  Coefficients from crow[j] (shared memory, read after the
-// exchange barrier).
+// D_{j-2} (dp), with mt_j h F(Y) = (mt_j h du) Lu + (mt_j h ku) Ru (likewise
+// v).  Coefficients from crow[j] (shared memory, read after the exchange
+// barrier).
 template <int MODEL, int G, int TY, int TX>
 __device__ __forceinline__ void rkc_stage(float *hb, int tx, int ty, const float (&y0u)[TY][TX],
                                           const float (&y0v)[TY][TX], const float (&f0u)[TY][TX],
@@ -256,9 +290,21 @@ __device__ __forceinline__ void rkc_stage(float *hb, int tx, int ty, const float
     tile_exchange<G, TY, TX>(hb, tx, ty, yu, yv);
     const float4 cj = crow[j];
     const float mth = cj.z * h, gth = cj.w * h;
-    tile_apply<MODEL, G, TY, TX>(hb, tx, ty, yu, yv, k, [&](int i, int c, float Fu, float Fv) {
-        dpu[i][c] = fmaf(cj.x, dlu[i][c], fmaf(cj.y, dpu[i][c], fmaf(mth, Fu, gth * f0u[i][c])));
-        dpv[i][c] = fmaf(cj.x, dlv[i][c], fmaf(cj.y, dpv[i][c], fmaf(mth, Fv, gth * f0v[i][c])));
+    float ku, kv;
+    react_scale<MODEL>(k, ku, kv);
+    const float mdu = mth * k.du, mdv = mth * k.dv, mru = mth * ku, mrv = mth * kv;
+    tile_apply<G, TY, TX>(hb, tx, ty, yu, yv, [&](int i, int c, float su, float sv) {
+        const float a = yu[i][c], b = yv[i][c];
+        const float Lu = fmaf(-4.f, a, su), Lv = fmaf(-4.f, b, sv);
+        float gu = gth * f0u[i][c], gv = gth * f0v[i][c];
+        if (MODEL != RD_DIFF) {
+            float Ru, Rv;
+            rhs_parts<MODEL>(a, b, k, Ru, Rv);
+            gu = fmaf(mru, Ru, gu);
+            gv = fmaf(mrv, Rv, gv);
+        }
+        dpu[i][c] = fmaf(cj.x, dlu[i][c], fmaf(cj.y, dpu[i][c], fmaf(mdu, Lu, gu)));
+        dpv[i][c] = fmaf(cj.x, dlv[i][c], fmaf(cj.y, dpv[i][c], fmaf(mdv, Lv, gv)));
     });
 }
 
@@ -574,14 +620,34 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
     residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, ring);
 }
 
-template <int G> struct RkcShape;
-template <> struct RkcShape<32> { static constexpr int TY = 2, TX = 1; };
-template <> struct RkcShape<64> { static constexpr int TY = 4, TX = 2; };
+// Tile shapes (TY x TX nodes per thread), per grid side; every shape runs
+// the same per-node arithmetic, so all give bit-identical fields.
+//   G = 32: 0 = 2 x 1 (512 threads), 1 = 4 x 1 (256), 2 = 2 x 2 (256)
+//   G = 64: 0 = 4 x 2 (512 threads), 1 = 4 x 4 (256, default), 2 = 2 x 4 (512)
+constexpr int RKC_NVAR = 3;
+template <int G, int V> struct RkcShape;
+template <> struct RkcShape<32, 0> { static constexpr int TY = 2, TX = 1; };
+template <> struct RkcShape<32, 1> { static constexpr int TY = 4, TX = 1; };
+template <> struct RkcShape<32, 2> { static constexpr int TY = 2, TX = 2; };
+template <> struct RkcShape<64, 0> { static constexpr int TY = 4, TX = 2; };
+template <> struct RkcShape<64, 1> { static constexpr int TY = 4, TX = 4; };
+template <> struct RkcShape<64, 2> { static constexpr int TY = 2, TX = 4; };
+// defaults: FHN 64x64 x 128, fixed 16-stage schedule on B300: 4 x 4 took
+// 0.668 us per stage, 4 x 2 0.705, 2 x 4 0.736
+static int g_rkc_var[2] = {0, 1};   // [G == 64]
 
-template <int MODEL, int G>
+int rkc_n_variants() { return RKC_NVAR; }
+bool rkc_set_variant(int G, int v) {
+    if ((G != 32 && G != 64) || v < 0 || v >= RKC_NVAR) return false;
+    g_rkc_var[G == 64] = v;
+    return true;
+}
+int rkc_get_variant(int G) { return (G == 32 || G == 64) ? g_rkc_var[G == 64] : -1; }
+
+template <int MODEL, int G, int V>
 static rd_status launch_rkc_mg(const GroupDev &g, float *fields, const RkcRun &run, int64_t *stats,
                                double *residual, uint32_t *status, cudaStream_t s) {
-    constexpr int TY = RkcShape<G>::TY, TX = RkcShape<G>::TX;
+    constexpr int TY = RkcShape<G, V>::TY, TX = RkcShape<G, V>::TX;
     using T = Tiling<G, TY, TX>;
     const size_t smem = rkc_smem<G, TY, TX>();
     auto kern = rd_rkc_kernel<MODEL, G, TY, TX>;
@@ -597,8 +663,17 @@ static rd_status launch_rkc_mg(const GroupDev &g, float *fields, const RkcRun &r
 template <int MODEL>
 static rd_status launch_rkc_m(const GroupDev &g, float *fields, const RkcRun &run, int64_t *stats, double *residual,
                               uint32_t *status, cudaStream_t s) {
-    if (g.G == 32) return launch_rkc_mg<MODEL, 32>(g, fields, run, stats, residual, status, s);
-    if (g.G == 64) return launch_rkc_mg<MODEL, 64>(g, fields, run, stats, residual, status, s);
+    const int v = rkc_get_variant(g.G);
+    if (g.G == 32) {
+        if (v == 1) return launch_rkc_mg<MODEL, 32, 1>(g, fields, run, stats, residual, status, s);
+        if (v == 2) return launch_rkc_mg<MODEL, 32, 2>(g, fields, run, stats, residual, status, s);
+        return launch_rkc_mg<MODEL, 32, 0>(g, fields, run, stats, residual, status, s);
+    }
+    if (g.G == 64) {
+        if (v == 1) return launch_rkc_mg<MODEL, 64, 1>(g, fields, run, stats, residual, status, s);
+        if (v == 2) return launch_rkc_mg<MODEL, 64, 2>(g, fields, run, stats, residual, status, s);
+        return launch_rkc_mg<MODEL, 64, 0>(g, fields, run, stats, residual, status, s);
+    }
     return RD_ERR_UNSUPPORTED;
 }
 

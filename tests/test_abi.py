@@ -111,3 +111,19 @@ def test_stream_depth_argument_checks(libpath):
     L = p.lib()
     assert L.rd_set_stream_depth(None, 4) == 1
     assert L.rd_get_stream_depth(None) == -1
+
+
+def test_rkc_argument_checks_without_gpu(libpath):
+    # null handle / options, and the tile-shape setters, need no device
+    import paper_2203_14742_b300 as p
+    L = p.lib()
+    o = p.RdRkcOpts(0.0, 1e-3, 1e-5, 1e-5, 256, 0, 0, 1000)
+    assert L.rd_integrate_rkc(None, ctypes.c_void_p(256), ctypes.byref(o), None, None, None) == 1
+    assert ctypes.sizeof(p.RdRkcOpts) == 56
+    assert L.rd_rkc_n_variants() == 3
+    assert L.rd_rkc_get_variant(64) == 1 and L.rd_rkc_get_variant(32) == 0
+    assert L.rd_rkc_get_variant(128) == -1
+    assert L.rd_rkc_set_variant(128, 0) == 1 and L.rd_rkc_set_variant(64, 3) == 1
+    assert L.rd_rkc_set_variant(64, 0) == 0 and L.rd_rkc_get_variant(64) == 0
+    assert L.rd_rkc_set_variant(64, 1) == 0
+    assert L.rd_status_str(8) == b"adaptive step control gave up"

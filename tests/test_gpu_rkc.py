@@ -246,3 +246,34 @@ def test_argument_checks(p):
     with pytest.raises(p.RdError) as e:
         big.integrate_rkc(1e-3)
     assert e.value.status == 6
+
+
+@pytest.mark.parametrize("model,G,par,noise", [
+    (W.FHN, 64, W.FHN_THETA0, (-0.05, 0.05)),
+    (W.GM, 32, W.GM_THETA0, (0.0, 0.01)),
+    (W.BZ, 64, W.BZ_THETA0, (0.0, 0.01)),
+])
+def test_tile_shapes(p, model, G, par, noise):
+    # Per node every shape runs the same arithmetic: a fixed schedule gives
+    # bit-identical fields.  The adaptive error norm is summed in an order
+    # that follows the tiling, so its last bits (and through h the fields)
+    # may differ; the runs must still agree to the field tolerance.
+    fixed, adaptive = [], []
+    try:
+        for v in range(p.lib().rd_rkc_n_variants()):
+            p.rkc_set_variant(G, v)
+            assert p.rkc_get_variant(G) == v
+            sim = sim_of(p, model, G, 3, par, noise, 31)
+            sim.integrate_rkc(0.05, s_fixed=12, n_fixed=20)
+            fixed.append(sim.group_fields(0).clone())
+            sim.reinit()
+            st, _ = sim.integrate_rkc(1e-3, t_end=2.0, rtol=1e-5, atol=1e-5)
+            assert sim.sync_status() == 0
+            adaptive.append((sim.group_fields(0).cpu().numpy(), st.cpu().numpy()))
+    finally:
+        p.rkc_set_variant(G, 1 if G == 64 else 0)
+    for f in fixed[1:]:
+        assert torch.equal(f, fixed[0])
+    for f, st in adaptive[1:]:
+        assert rel_err(f, adaptive[0][0]) <= 1e-4
+        assert np.abs(st[:, 0] - adaptive[0][1][:, 0]).max() <= 2
