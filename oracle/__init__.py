@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-FHN, GM, DIFF, BZ = 0, 1, 2, 3
+FHN, GM, DIFF, BZ, RDODE = 0, 1, 2, 3, 4
 
 _lib = None
 
@@ -34,6 +34,10 @@ def lib():
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_uint8))
         L.orc_threads.restype = C.c_int
+        L.orc_rdode_init.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_int, fp]
+        L.orc_rdode_rhs.argtypes = [C.c_int, dp, dp, dp]
+        L.orc_rdode_gershgorin.argtypes = [C.c_int, dp, dp]
+        L.orc_rdode_gershgorin.restype = C.c_double
         L.orc_rkc_coef.argtypes = [C.c_int, dp, dp, dp, dp, dp]
         L.orc_rkc_beta.argtypes = [C.c_int]
         L.orc_rkc_beta.restype = C.c_double
@@ -98,8 +102,8 @@ def _d(a):
 
 
 def _params(p):
-    p = np.zeros(4, np.float64) if p is None else np.asarray(p, np.float64)
-    out = np.zeros(4, np.float64)
+    p = np.zeros(6, np.float64) if p is None else np.asarray(p, np.float64)
+    out = np.zeros(6, np.float64)
     out[:len(p)] = p
     return out
 
@@ -441,10 +445,32 @@ def rkc_beta(s):
 
 
 def gershgorin(model, p, w):
-    """Gershgorin bound of the spectral radius of dF/dw at w[2, G, G]."""
+    """Gershgorin bound of the spectral radius of dF/dw at w[2, G, G]
+    (w[2, N] for RDODE)."""
     p = _params(p)
     w = _d(w)
     return float(lib().orc_gershgorin(model, w.shape[-1], _p(p, C.c_double), _p(w, C.c_double)))
+
+
+# ---------------------------------------------------------------------------
+# Reaction-diffusion-ODE model (Sec. 4.3, eq. rdode), 1-D, [2][N] per
+# realisation, p = (unused, D, m1, m2, m3, k).
+
+def rdode_init(N, n_real, lo, hi, seed, n_smooth):
+    """[n_real, 2, N] float32: u = smoothed U(lo, hi) noise, w = 0."""
+    out = np.empty((n_real, 2, N), np.float32)
+    lib().orc_rdode_init(int(N), int(n_real), float(lo), float(hi),
+                         C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(n_smooth), _p(out, C.c_float))
+    return out
+
+
+def rdode_rhs(p, w):
+    """F(w) of one realisation w[2, N] (float64)."""
+    p = _params(p)
+    w = _d(w)
+    F = np.empty_like(w)
+    lib().orc_rdode_rhs(w.shape[-1], _p(p, C.c_double), _p(w, C.c_double), _p(F, C.c_double))
+    return F
 
 
 def rkc_fixed(model, p, h, s, n_steps, w):

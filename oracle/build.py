@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["rd.c", "cil.c", "mcil.c", "rkc.c"]
+SOURCES = ["rd.c", "cil.c", "mcil.c", "rkc.c", "rdode.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

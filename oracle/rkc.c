@@ -59,6 +59,8 @@
  *   - the last step is cut to end exactly at t_end;
  *   - a realisation fails when it needs more than max_attempts attempts or
  *     h drops below 1e-12 t_end.
+ * The same driver integrates the 1-D reaction-diffusion-ODE system of
+ * rdode.c (model 4), whose realisations are [2][N].
  * RHS evaluations per attempt: s (F(Y_1)..F(Y_{s-1}) and F(Y_s), which is
  * F(w_{n+1}) of the estimate and the next step's F(Y_0)), plus one for the
  * initial F(w_0).
@@ -69,6 +71,22 @@
 #include <math.h>
 
 void orc_rhs(int model, int G, const double *p, const double *w, double *F);
+void orc_rdode_rhs(int N, const double *p, const double *w, double *F);
+double orc_rdode_gershgorin(int N, const double *p, const double *w);
+
+/* Model 4 is the 1-D reaction-diffusion-ODE system of rdode.c (G = its
+   node count N, a realisation is [2][N]); the others are the 2-D systems
+   of rd.c ([2][G][G]). */
+#define ORC_RDODE 4
+static int64_t m_of(int model, int G)
+{
+    return model == ORC_RDODE ? 2 * (int64_t)G : 2 * (int64_t)G * G;
+}
+static void rhs_any(int model, int G, const double *p, const double *w, double *F)
+{
+    if (model == ORC_RDODE) orc_rdode_rhs(G, p, w, F);
+    else orc_rhs(model, G, p, w, F);
+}
 
 #define RKC_EPS (2.0 / 13.0)
 
@@ -157,6 +175,7 @@ static void kinetics_jac(int model, const double *p, double u, double v, double 
 /* Gershgorin bound of the spectral radius of dF/dw at w ([2][G][G]). */
 double orc_gershgorin(int model, int G, const double *p, const double *w)
 {
+    if (model == ORC_RDODE) return orc_rdode_gershgorin(G, p, w);
     const int64_t cells = (int64_t)G * G;
     const double g2 = (double)(G - 1) * (double)(G - 1);
     const double du = p[0] * g2, dv = p[1] * g2;
@@ -182,13 +201,13 @@ static void rkc_step_one(int model, int G, const double *p, double h, int s,
                          const double *mu, const double *nu, const double *mt, const double *gt,
                          double *w, const double *F0, double *Fs, double *Ym2, double *Ym1, double *Fj)
 {
-    const int64_t m = 2 * (int64_t)G * G;
+    const int64_t m = m_of(model, G);
     for (int64_t k = 0; k < m; ++k) {
         Ym2[k] = w[k];
         Ym1[k] = w[k] + (mt[1] * h) * F0[k];
     }
     for (int j = 2; j <= s; ++j) {
-        orc_rhs(model, G, p, Ym1, Fj);
+        rhs_any(model, G, p, Ym1, Fj);
         const double c0 = (1.0 - mu[j]) - nu[j];
         const double cf = mt[j] * h, c0f = gt[j] * h;
         for (int64_t k = 0; k < m; ++k) {
@@ -202,7 +221,7 @@ static void rkc_step_one(int model, int G, const double *p, double h, int s,
         }
     }
     memcpy(w, Ym1, sizeof(double) * (size_t)m);
-    if (Fs) orc_rhs(model, G, p, w, Fs);
+    if (Fs) rhs_any(model, G, p, w, Fs);
 }
 
 /* Fixed schedule: n_steps steps of size h with s stages each, for n_real
@@ -210,7 +229,7 @@ static void rkc_step_one(int model, int G, const double *p, double h, int s,
 void orc_rkc_fixed(int model, int G, int n_real, const double *p, double h, int s,
                    int64_t n_steps, double *w)
 {
-    const int64_t m = 2 * (int64_t)G * G;
+    const int64_t m = m_of(model, G);
     double *mu = malloc(sizeof(double) * (size_t)(s + 1)), *nu = malloc(sizeof(double) * (size_t)(s + 1));
     double *mt = malloc(sizeof(double) * (size_t)(s + 1)), *gt = malloc(sizeof(double) * (size_t)(s + 1));
     double ex[5];
@@ -220,7 +239,7 @@ void orc_rkc_fixed(int model, int G, int n_real, const double *p, double h, int 
         double *buf = malloc(sizeof(double) * (size_t)(5 * m));
         double *F0 = buf, *Fs = buf + m, *a = buf + 2 * m, *b = buf + 3 * m, *c = buf + 4 * m;
         double *wr = w + (int64_t)r * m;
-        orc_rhs(model, G, p, wr, F0);
+        rhs_any(model, G, p, wr, F0);
         for (int64_t n = 0; n < n_steps; ++n) {
             rkc_step_one(model, G, p, h, s, mu, nu, mt, gt, wr, F0, Fs, a, b, c);
             memcpy(F0, Fs, sizeof(double) * (size_t)m);
@@ -239,7 +258,7 @@ int orc_rkc_adaptive(int model, int G, int n_real, const double *p, double t_end
                      double rtol, double atol, int s_max, int64_t max_attempts, double *w,
                      int64_t *stats)
 {
-    const int64_t m = 2 * (int64_t)G * G;
+    const int64_t m = m_of(model, G);
     const double eta = 0.8;
     int failed = 0;
     /* coefficient tables for every s = 2..s_max, and beta(s) */
@@ -260,7 +279,7 @@ int orc_rkc_adaptive(int model, int G, int n_real, const double *p, double t_end
         double *wr = w + (int64_t)r * m;
         int64_t *st = stats + 4 * (int64_t)r;
         st[0] = 0; st[1] = 0; st[2] = 1; st[3] = 0;
-        orc_rhs(model, G, p, wr, F0);
+        rhs_any(model, G, p, wr, F0);
         double t = 0.0, h = h0, h_prev = 0.0, err_prev = 0.0;
         int have_prev = 0, after_reject = 0, ok = 1;
         int64_t attempts = 0;

@@ -26,6 +26,11 @@ Workloads (sizes follow the paper's Table 1 models and the hot-path configs):
       smoothed CIL with tau_k = 0.05 R_k, cotangent 1/M.
   c6  Brusselator ("BZ", Table 1) 64x64, 2 sets x 64, dt 2^-8, 25600 steps
       (T = 100), both species (d = 8192), noise U(0, 0.01), M = 16.
+  c7  reaction-diffusion-ODE model (Sec. 4.3, Table 1 "RD"), 64 nodes, 2 sets
+      x 100 realisations (the 100 model runs per cost evaluation of Sec. 5),
+      t in [0, 50] by the adaptive stabilised RK2 (rtol = atol = 1e-6),
+      initial u = U(0, 2) noise smoothed by 10 moving-average passes, w = 0;
+      (m1, m2) within +-5 % of (1.44, 4.1); both species (d = 128), M = 13.
   glarge  the paper's SCIL scale (N_syn = 1000, Sec. 5.3): 2 sets x 1024
       patterns of d = 32768 for the Gram kernel alone.
 """
@@ -33,7 +38,7 @@ import math
 
 import numpy as np
 
-FHN, GM, DIFF, BZ = 0, 1, 2, 3
+FHN, GM, DIFF, BZ, RDODE = 0, 1, 2, 3, 4
 
 SEED_BASE = 0x2203147420000000
 
@@ -42,6 +47,8 @@ SEED_BASE = 0x2203147420000000
 FHN_THETA0 = (2.8e-4, 0.05, 10.0, 1.0)      # Du = nu_2, Dv = nu_1, eps, a = alpha
 GM_THETA0 = (2.5e-4, 0.01, 1.0, 0.5)        # Du = nu_1, Dv = nu_2, rho, mu = mu_v
 BZ_THETA0 = (1.6e-3, 1.32e-2, 4.5, 6.96)    # Brusselator: Du = nu_1, Dv = nu_2, A, B
+# 1-D reaction-diffusion-ODE model (Sec. 4.3): (unused, D, m1, m2, m3, k)
+RDODE_THETA0 = (0.0, 1.0, 1.44, 4.1, 4.1, 0.01)
 
 
 def seed_of(cfg_index: int) -> int:
@@ -56,6 +63,7 @@ def draw_params(model: int, seed: int, n: int = 1):
     GM:  mu within +-10 % of 0.5; rho = 1; Table 1 diffusions.
     BZ:  A in [4.3, 4.6], B in [6.9, 7.2] around Table 1's (4.5, 6.96);
          Table 1 diffusions.
+    RDODE: m1, m2 within +-5 % of Table 1's (1.44, 4.1); D, m3, k fixed.
     The oracle test suite checks every drawn vector for a diffusion-driven
     instability on the discrete grid.
     """
@@ -77,6 +85,10 @@ def draw_params(model: int, seed: int, n: int = 1):
             A = rng.uniform(4.3, 4.6)
             B = rng.uniform(6.9, 7.2)
             out.append((BZ_THETA0[0], BZ_THETA0[1], A, B))
+        elif model == RDODE:
+            m1 = RDODE_THETA0[2] * rng.uniform(0.95, 1.05)
+            m2 = RDODE_THETA0[3] * rng.uniform(0.95, 1.05)
+            out.append((0.0, RDODE_THETA0[1], m1, m2, RDODE_THETA0[4], RDODE_THETA0[5]))
         else:
             raise ValueError("model")
     return out
@@ -137,6 +149,13 @@ def config(name: str, steps_scale: float = 1.0):
         g = group(BZ, 64, 128, p, 2.0 ** -8, steps(25600), (0.0, 0.01), s, 3)
         return {"name": name, "groups": [g], "n1": 64, "n2": 64, "M": 16, "b": 1.3,
                 "T_res": 200, "seed": s}
+    if name == "c7":
+        s = seed_of(7)
+        p = draw_params(RDODE, s)[0]
+        # Table 1: t in [0, 50] on 64 nodes; dt * n_steps is only the horizon
+        g = group(RDODE, 64, 200, p, 2.0 ** -10, steps(51200), (0.0, 2.0), s, 3)
+        return {"name": name, "groups": [g], "n1": 100, "n2": 100, "M": 13, "b": 1.3,
+                "T_res": 200, "seed": s, "rkc_tol": 1e-6}
     if name == "c5":
         s = seed_of(5)
         p = draw_params(FHN, s)[0]
