@@ -59,11 +59,27 @@ typedef int32_t rd_status;
  *  RD_BZ   the Brusselator ("BZ" in the paper's Table 1), eq. (bzSystem)
  *          with u = v, v = w:
  *            u_t = Du Lap u + A - (B+1) u + u^2 v,  v_t = Dv Lap v + B u - u^2 v
- *          params = (Du, Dv, A, B); equilibrium (A, B/A). */
+ *          params = (Du, Dv, A, B); equilibrium (A, B/A).
+ *  RD_RDODE the 1-D reaction-diffusion-ODE model, Sec. 4.3 eq. (rdode), a
+ *          non-diffusing u coupled to a diffusing w on G nodes of (0, 1),
+ *          h = 1/(G-1), zero flux:
+ *            u_t = -u - u w + m1 u^2/(1 + k u^2),
+ *            w_t = D w_xx - m3 w - u w + m2 u^2/(1 + k u^2)
+ *          params = (unused, D, m1, m2, m3, k); a realisation is
+ *          [species u, w][x] (2*G floats); G = 32, 64, 128 or 256.
+ *          Initial state (Sec. 4.3): u = uniform noise U(noise_lo, noise_hi)
+ *          per node (SplitMix64 output number (r*2)*G + x of the group's
+ *          stream, FP64 lo + (hi - lo) U), smoothed by RD_RDODE_SMOOTH passes
+ *          of the 3-node moving average ((u_{x-1} + u_x) + u_{x+1}) / 3 with
+ *          ghost = edge node, in FP64, rounded once to FP32; w = 0.  Only
+ *          rd_integrate_rkc integrates it (explicit Euler would need
+ *          dt < h^2/(2D), the paper integrates it with ROCK2). */
 #define RD_FHN 0
 #define RD_GM 1
 #define RD_DIFF 2
 #define RD_BZ 3
+#define RD_RDODE 4
+#define RD_RDODE_SMOOTH 10
 
 /* group flags */
 #define RD_GROUP_ADJOINT 1   /* reserve checkpoint memory for rd_adjoint */
@@ -78,16 +94,20 @@ typedef int32_t rd_status;
  * rd_set_stream_depth).  dt must be below
  * the explicit stability limit (h^2 / (4 max(Du, Dv)), h = 1/(G-1)); the
  * library does not check stability, but a blow-up is reported as
- * RD_ERR_NONFINITE. */
+ * RD_ERR_NONFINITE.  RD_RDODE groups are 1-D: G nodes, realisation r at
+ * d_fields + field_offset + r*2*G as [species u, w][x]; flags must be 0;
+ * rd_integrate_batch, rd_integrate_reference, rd_integrate_f64,
+ * rd_autotune and rd_adjoint return RD_ERR_UNSUPPORTED for a handle that
+ * holds one. */
 typedef struct rd_group {
-    int32_t model;          /* RD_FHN / RD_GM / RD_DIFF / RD_BZ */
-    int32_t G;              /* grid side */
+    int32_t model;          /* RD_FHN / RD_GM / RD_DIFF / RD_BZ / RD_RDODE */
+    int32_t G;              /* grid side (RD_RDODE: node count) */
     int32_t n_real;         /* realisations in this group (>= 1) */
     int32_t flags;          /* RD_GROUP_* */
     int64_t n_steps;        /* explicit Euler steps for rd_integrate_batch */
     int64_t field_offset;   /* floats from d_fields to realisation 0 */
     double dt;              /* time step */
-    double params[4];       /* see the model list above */
+    double params[6];       /* see the model list above (unused slots 0) */
     double noise_lo;        /* initial state = equilibrium + U(noise_lo, noise_hi) */
     double noise_hi;
     uint64_t seed;          /* counter-based noise stream of this group */

@@ -18,10 +18,10 @@ import os
 
 import torch
 
-__all__ = ["FHN", "GM", "DIFF", "Group", "Simulation", "cil", "cil_exact", "synlik",
+__all__ = ["FHN", "GM", "DIFF", "BZ", "RDODE", "Group", "Simulation", "cil", "cil_exact", "synlik",
            "SmoothCIL", "lib", "status_str"]
 
-FHN, GM, DIFF = 0, 1, 2
+FHN, GM, DIFF, BZ, RDODE = 0, 1, 2, 3, 4
 GROUP_ADJOINT = 1
 GROUP_STREAM = 2
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -31,7 +31,7 @@ LIB_PATH = os.path.join(_HERE, "librdcil.so")
 class RdGroup(C.Structure):
     _fields_ = [("model", C.c_int32), ("G", C.c_int32), ("n_real", C.c_int32), ("flags", C.c_int32),
                 ("n_steps", C.c_int64), ("field_offset", C.c_int64), ("dt", C.c_double),
-                ("params", C.c_double * 4), ("noise_lo", C.c_double), ("noise_hi", C.c_double),
+                ("params", C.c_double * 6), ("noise_lo", C.c_double), ("noise_hi", C.c_double),
                 ("seed", C.c_uint64)]
 
 
@@ -141,7 +141,7 @@ class Group:
     def __init__(self, model, G, n_real, params, dt, n_steps, noise=(-0.05, 0.05), seed=0,
                  adjoint=False, stream=False):
         self.model, self.G, self.n_real = int(model), int(G), int(n_real)
-        self.params = tuple(float(p) for p in params) + (0.0,) * (4 - len(params))
+        self.params = tuple(float(p) for p in params) + (0.0,) * (6 - len(params))
         self.dt, self.n_steps = float(dt), int(n_steps)
         self.noise = (float(noise[0]), float(noise[1]))
         self.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
@@ -149,8 +149,17 @@ class Group:
         self.stream = bool(stream)
 
     @property
+    def cells(self):
+        """Nodes per species: G x G, or G for the 1-D RDODE model."""
+        return self.G if self.model == RDODE else self.G * self.G
+
+    @property
+    def shape(self):
+        return (self.n_real, 2, self.G) if self.model == RDODE else (self.n_real, 2, self.G, self.G)
+
+    @property
     def floats(self):
-        return self.n_real * 2 * self.G * self.G
+        return self.n_real * 2 * self.cells
 
     @classmethod
     def from_dict(cls, d, adjoint=False, stream=False):
@@ -181,7 +190,7 @@ class Simulation:
             a.model, a.G, a.n_real = g.model, g.G, g.n_real
             a.flags = (GROUP_ADJOINT if g.adjoint else 0) | (GROUP_STREAM if g.stream else 0)
             a.n_steps, a.field_offset, a.dt = g.n_steps, offs[i], g.dt
-            for k in range(4):
+            for k in range(6):
                 a.params[k] = g.params[k]
             a.noise_lo, a.noise_hi, a.seed = g.noise[0], g.noise[1], g.seed
         self._arr = arr
@@ -203,7 +212,7 @@ class Simulation:
         g = self.groups[i]
         f = self.fields if fields is None else fields
         o = self.offsets[i]
-        return f[o:o + g.floats].view(g.n_real, 2, g.G, g.G)
+        return f[o:o + g.floats].view(*g.shape)
 
     # -- calls -------------------------------------------------------------
     def reinit(self):

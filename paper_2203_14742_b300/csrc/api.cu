@@ -18,12 +18,25 @@ rd_status adjoint_reserve(Handle &h);
 void adjoint_release(Handle &h);
 }  // namespace rdcil
 
+// True if the handle holds a group of the 1-D model, which only
+// rd_integrate_rkc integrates.
+static bool has_rdode(const Handle &h) {
+    for (int32_t i = 0; i < h.n_groups; ++i)
+        if (h.h_groups[i].model == RD_RDODE) return true;
+    return false;
+}
+
 static rd_status validate_groups(const rd_group *groups, int32_t n_groups) {
     if (!groups || n_groups < 1) return RD_ERR_INVALID_ARG;
     std::vector<std::pair<int64_t, int64_t>> iv;
     for (int32_t i = 0; i < n_groups; ++i) {
         const rd_group &g = groups[i];
-        if (g.model != RD_FHN && g.model != RD_GM && g.model != RD_DIFF && g.model != RD_BZ) return RD_ERR_INVALID_ARG;
+        if (g.model != RD_FHN && g.model != RD_GM && g.model != RD_DIFF && g.model != RD_BZ && g.model != RD_RDODE)
+            return RD_ERR_INVALID_ARG;
+        if (g.model == RD_RDODE) {
+            // 1-D: 32, 64, 128 or 256 nodes, no flags
+            if ((g.G != 32 && g.G != 64 && g.G != 128 && g.G != 256) || g.flags) return RD_ERR_INVALID_ARG;
+        }
         // resident stepper: G = 32, 64, 128; streaming stepper: any multiple of
         // 4 from 8 to 4096
         if (g.G < 8 || g.G > 4096 || (g.G & 3)) return RD_ERR_INVALID_ARG;
@@ -37,7 +50,7 @@ static rd_status validate_groups(const rd_group *groups, int32_t n_groups) {
         if (g.model == RD_GM && !(g.params[3] != 0.0)) return RD_ERR_INVALID_ARG;
         if (g.model == RD_BZ && !(g.params[2] != 0.0)) return RD_ERR_INVALID_ARG;
         if (!(g.noise_lo <= g.noise_hi)) return RD_ERR_INVALID_ARG;
-        int64_t len = (int64_t)g.n_real * 2 * g.G * g.G;
+        int64_t len = (int64_t)g.n_real * 2 * g.G * (g.model == RD_RDODE ? 1 : g.G);
         iv.emplace_back(g.field_offset, g.field_offset + len);
     }
     std::sort(iv.begin(), iv.end());
@@ -65,7 +78,7 @@ extern "C" rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_
         GroupDev &d = h.h_groups[i];
         d.model = g.model; d.G = g.G; d.n_real = g.n_real; d.flags = g.flags;
         d.n_steps = g.n_steps; d.field_offset = g.field_offset; d.dt = g.dt;
-        for (int k = 0; k < 4; ++k) d.p[k] = g.params[k];
+        for (int k = 0; k < 6; ++k) d.p[k] = g.params[k];
         d.noise_lo = g.noise_lo; d.noise_hi = g.noise_hi; d.seed = g.seed;
         d.real_base = base;
         base += g.n_real;
@@ -127,6 +140,7 @@ extern "C" rd_status rd_integrate_batch(rd_handle *hh, float *d_fields, int64_t 
                                         void *stream) {
     if (!hh || !d_fields || ((uintptr_t)d_fields & 15)) return RD_ERR_INVALID_ARG;
     Handle &h = hh->h;
+    if (has_rdode(h)) return RD_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     int n_res = 0;
     for (int32_t i = 0; i < h.n_groups; ++i) n_res += group_is_resident(h.h_groups[i]) ? 1 : 0;
@@ -152,6 +166,7 @@ extern "C" rd_status rd_integrate_reference(rd_handle *hh, float *d_fields, floa
                                             void *stream) {
     if (!hh || !d_fields || !d_tmp) return RD_ERR_INVALID_ARG;
     Handle &h = hh->h;
+    if (has_rdode(h)) return RD_ERR_UNSUPPORTED;
     for (int32_t i = 0; i < h.n_groups; ++i) {
         const GroupDev &g = h.h_groups[i];
         int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
@@ -165,6 +180,7 @@ extern "C" rd_status rd_integrate_f64(rd_handle *hh, double *d_fields64, double 
                                       void *stream) {
     if (!hh || !d_fields64 || !d_tmp64) return RD_ERR_INVALID_ARG;
     Handle &h = hh->h;
+    if (has_rdode(h)) return RD_ERR_UNSUPPORTED;
     for (int32_t i = 0; i < h.n_groups; ++i) {
         const GroupDev &g = h.h_groups[i];
         int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
@@ -284,6 +300,7 @@ extern "C" int32_t rd_get_variant(int32_t model, int32_t G) {
 extern "C" rd_status rd_autotune(rd_handle *hh, float *d_fields, int64_t steps, void *stream, int32_t *chosen) {
     if (!hh || !d_fields || steps < 1) return RD_ERR_INVALID_ARG;
     Handle &h = hh->h;
+    if (has_rdode(h)) return RD_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     RD_CUDA_TRY(cudaEventCreate(&e0));

@@ -29,7 +29,7 @@ struct GroupDev {
     int32_t model, G, n_real, flags;
     int64_t n_steps, field_offset;
     double dt;
-    double p[4];
+    double p[6];
     double noise_lo, noise_hi;
     uint64_t seed;
     int64_t real_base;   // index of this group's first realisation overall
@@ -97,6 +97,10 @@ rd_status launch_stream_group(const Handle &h, const GroupDev &g, float *fields,
 void set_gram_spin_limit(uint32_t n);
 bool variant_shape(int G, int vi, int *packed, int *TY, int *TX);
 bool rkc_supported(const GroupDev &g);
+bool rkc1d_supported(const GroupDev &g);
+rd_status launch_rkc1d_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats,
+                             double *residual, uint32_t *status, cudaStream_t s);
+rd_status launch_rdode_init(const GroupDev &g, float *fields, cudaStream_t s);
 int rkc_n_variants();
 bool rkc_set_variant(int G, int v);
 int rkc_get_variant(int G);

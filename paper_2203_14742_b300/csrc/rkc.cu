@@ -34,11 +34,10 @@
 #include <mutex>
 #include "common.cuh"
 #include "tile.cuh"
+#include "rkc.cuh"
 
 namespace rdcil {
 
-constexpr int RKC_SMAX = RD_RKC_S_MAX;
-constexpr int RKC_STRIDE = RKC_SMAX + 1;
 
 // ---------------------------------------------------------------------------
 // Coefficient table: tab[s][j] = (mu_j, nu_j, mt_j, gt_j) in FP32 for
@@ -89,7 +88,7 @@ static double *g_beta = nullptr;
 static std::once_flag g_tab_once;
 static rd_status g_tab_status = RD_OK;
 
-static rd_status rkc_tables(cudaStream_t s) {
+rd_status rkc_tables(cudaStream_t s, const float4 **tab, const double **beta) {
     std::call_once(g_tab_once, [s]() {
         if (cudaMalloc(&g_tab, sizeof(float4) * (size_t)RKC_STRIDE * RKC_STRIDE) != cudaSuccess ||
             cudaMalloc(&g_beta, sizeof(double) * RKC_STRIDE) != cudaSuccess) {
@@ -101,6 +100,8 @@ static rd_status rkc_tables(cudaStream_t s) {
         note_launch();
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) g_tab_status = RD_ERR_CUDA;
     });
+    *tab = g_tab;
+    *beta = g_beta;
     return g_tab_status;
 }
 
@@ -306,84 +307,6 @@ __device__ __forceinline__ void rkc_stage(float *hb, int tx, int ty, const float
         dpu[i][c] = fmaf(cj.x, dlu[i][c], fmaf(cj.y, dpu[i][c], fmaf(mdu, Lu, gu)));
         dpv[i][c] = fmaf(cj.x, dlv[i][c], fmaf(cj.y, dpv[i][c], fmaf(mdv, Lv, gv)));
     });
-}
-
-// Step control state, owned by thread 0 (shared memory).
-struct RkcCtl {
-    double t, t_end, h, h_prev;
-    int64_t attempts, n_acc, n_rej, n_rhs;
-    float err_prev, hf, rho, rho_new;
-    int s, s_used, last, have_prev, after_reject, accept, done, fail;
-};
-
-struct RkcRun {
-    double t_end, h0, rtol, atol;
-    int32_t s_max, s_fixed;
-    int64_t n_fixed, max_attempts;
-};
-
-// Plan the next attempt (thread 0): clip to t_end, pick s from rho.
-__device__ __forceinline__ void rkc_plan(RkcCtl &c, const RkcRun &run, const double *__restrict__ beta) {
-    if (run.s_fixed >= 2) {
-        if (c.n_acc >= run.n_fixed) { c.done = 1; return; }
-        c.h = run.h0;
-        c.s = run.s_fixed;
-    } else {
-        if (!(c.t < c.t_end)) { c.done = 1; return; }
-        if (c.attempts >= run.max_attempts || c.h < 1e-12 * c.t_end) { c.done = 1; c.fail = 1; return; }
-        c.last = 0;
-        if (c.h >= c.t_end - c.t) { c.h = c.t_end - c.t; c.last = 1; }
-        const double hr = c.h * (double)c.rho;
-        // beta(s) < 0.66 s^2 for every s, so no s below sqrt(hr / 0.66)
-        // qualifies: start the search for the smallest s there
-        int s = (int)sqrtf((float)hr / 0.66f);
-        s = s < 2 ? 2 : (s > run.s_max ? run.s_max : s);
-        while (s < run.s_max && hr > beta[s]) ++s;
-        if (hr > beta[s]) { c.h = beta[run.s_max] / (double)c.rho; c.last = 0; }
-        c.s = s;
-    }
-    c.attempts += 1;
-    c.hf = (float)c.h;
-    c.n_rhs += c.s;
-    if (c.s > c.s_used) c.s_used = c.s;
-}
-
-// Accept or reject the attempt just made (thread 0), then plan the next.
-// The step-size factor is computed in FP32 (the FP32 error estimate it
-// comes from is far less precise than that); t and h stay FP64.
-__device__ __forceinline__ void rkc_decide(RkcCtl &c, const RkcRun &run, const double *__restrict__ beta,
-                                           float sumsq, int m) {
-    if (run.s_fixed >= 2) {
-        c.accept = 1;
-        c.n_acc += 1;
-        rkc_plan(c, run, beta);
-        return;
-    }
-    const float err = sqrtf(sumsq / (float)m);
-    if (!isfinite(err)) { c.accept = 0; c.done = 1; c.fail = 2; return; }
-    const float ef = fmaxf(err, 1e-10f);
-    float fac;
-    if (err <= 1.f) {
-        c.accept = 1;
-        c.t = c.last ? c.t_end : c.t + c.h;
-        c.n_acc += 1;
-        c.rho = c.rho_new;
-        fac = 0.8f / cbrtf(ef);
-        if (c.have_prev) fac = fac * ((float)c.h / (float)c.h_prev) * cbrtf(c.err_prev / ef);
-        fac = fminf(fmaxf(fac, 0.1f), 10.f);
-        if (c.after_reject && fac > 1.f) fac = 1.f;
-        c.h_prev = c.h;
-        c.err_prev = ef;
-        c.have_prev = 1;
-        c.after_reject = 0;
-    } else {
-        c.accept = 0;
-        c.n_rej += 1;
-        fac = fminf(fmaxf(0.8f / cbrtf(ef), 0.1f), 10.f);
-        c.after_reject = 1;
-    }
-    c.h = (double)fac * c.h;
-    rkc_plan(c, run, beta);
 }
 
 // Block reduction of (sum of squares, max rho): warp shuffles, then warp 0
@@ -677,12 +600,18 @@ static rd_status launch_rkc_m(const GroupDev &g, float *fields, const RkcRun &ru
     return RD_ERR_UNSUPPORTED;
 }
 
-bool rkc_supported(const GroupDev &g) { return g.G == 32 || g.G == 64; }
+bool rkc_supported(const GroupDev &g) {
+    if (g.model == RD_RDODE) return rkc1d_supported(g);
+    return g.G == 32 || g.G == 64;
+}
 
 rd_status launch_rkc_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats, double *residual,
                            uint32_t *status, cudaStream_t s) {
-    rd_status st = rkc_tables(s);
+    const float4 *tab = nullptr;
+    const double *beta = nullptr;
+    rd_status st = rkc_tables(s, &tab, &beta);
     if (st != RD_OK) return st;
+    if (g.model == RD_RDODE) return launch_rkc1d_group(g, fields, o, stats, residual, status, s);
     RkcRun run{o.t_end, o.h0, o.rtol, o.atol, o.s_max, o.s_fixed, o.n_fixed, o.max_attempts};
     switch (g.model) {
         case RD_FHN: return launch_rkc_m<RD_FHN>(g, fields, run, stats, residual, status, s);

@@ -61,6 +61,7 @@ static void equilibrium(const GroupDev &g, double &u0, double &v0) {
 }
 
 rd_status launch_init_fields(const GroupDev &g, float *fields, cudaStream_t s) {
+    if (g.model == RD_RDODE) return launch_rdode_init(g, fields, s);
     double u0, v0;
     equilibrium(g, u0, v0);
     int64_t cells = (int64_t)g.G * g.G;
@@ -391,7 +392,8 @@ rd_status batch_plan_create(const GroupDev *groups, int n_groups, void **out) {
         b.G = g.G;
         b.n_real = g.n_real;
         b.pad = 0;
-        if (!group_is_resident(g)) continue;   // streaming groups run on their own launches
+        // streaming groups run on their own launches; the 1-D model is not stepped here
+        if (!group_is_resident(g) || g.model == RD_RDODE) continue;
         for (int r = 0; r < g.n_real; ++r) items.push_back(BatchItem{i, r});
     }
     // longest first: cost ~ G^2 * steps

@@ -335,7 +335,7 @@ rd_status stream_reserve(Handle &h) {
     size_t tmp = 0, part = 0;
     for (int i = 0; i < h.n_groups; ++i) {
         const GroupDev &g = h.h_groups[i];
-        if (group_is_resident(g)) continue;
+        if (group_is_resident(g) || g.model == RD_RDODE) continue;
         tmp = std::max(tmp, (size_t)2 * g.n_real * g.G * g.G);
         part = std::max(part, (size_t)2 * ST_PARTS * g.n_real);
     }

@@ -54,10 +54,10 @@ def test_rd_group_layout_matches_header(libpath):
     import paper_2203_14742_b300 as p
     # offsets written out from the C struct (natural alignment)
     expect = {"model": 0, "G": 4, "n_real": 8, "flags": 12, "n_steps": 16, "field_offset": 24,
-              "dt": 32, "params": 40, "noise_lo": 72, "noise_hi": 80, "seed": 88}
+              "dt": 32, "params": 40, "noise_lo": 88, "noise_hi": 96, "seed": 104}
     for name, off in expect.items():
         assert getattr(p.RdGroup, name).offset == off
-    assert ctypes.sizeof(p.RdGroup) == 96
+    assert ctypes.sizeof(p.RdGroup) == 112
 
 
 def test_argument_errors_before_any_launch(libpath):
