@@ -145,30 +145,6 @@ static RkcK make_rkc_k(const GroupDev &g) {
     return k;
 }
 
-// F at one node from its state (a, b) and the neighbour sums su, sv.
-template <int MODEL>
-__device__ __forceinline__ void rhs_cell(float a, float b, float su, float sv, const RkcK &k, float &Fu, float &Fv) {
-    const float lu = k.du * fmaf(-4.f, a, su), lv = k.dv * fmaf(-4.f, b, sv);
-    if (MODEL == RD_FHN) {
-        Fu = lu + fmaf(-a * a, a, a - b);
-        Fv = fmaf(k.p2, fmaf(-k.p3, b, a), lv);
-    } else if (MODEL == RD_GM) {
-        // U^2/V - mu U = U (a - mu b + e0) / V,  U^2 - V = a (a + 2 u0) - b + e1
-        const float U = a + k.u0, V = b + k.v0;
-        const float t = fmaf(-k.p3, b, a + k.e0);
-        Fu = fmaf(k.p2, (U * t) / V, lu);
-        Fv = fmaf(k.p2, fmaf(a, a + k.tu0, k.e1) - b, lv);
-    } else if (MODEL == RD_BZ) {
-        const float U = a + k.u0;
-        const float P = fmaf(k.v0 * a, a, (U * U) * b);
-        Fu = fmaf(k.c1, a, k.e0 + P) + lu;
-        Fv = fmaf(k.c2, a, -k.e0 - P) + lv;
-    } else {
-        Fu = lu;
-        Fv = lv;
-    }
-}
-
 // The RHS split for the stages: F_u = du Lu + ku Ru, F_v = dv Lv + kv Rv
 // with the unscaled 5-point sums Lu, Lv and the kinetics' scale factors
 // (ku, kv) = FHN (1, eps), GM (rho, rho), BZ (1, 1), DIFF (0, 0), so a
@@ -222,9 +198,44 @@ __device__ __forceinline__ float gersh_cell(float U, float V, float n, const Rkc
     return fmaxf(ru, rv);
 }
 
-// Exchange the edge rows of the tile state (yu, yv) through ring buffer hb
-// (one barrier); tile_apply then calls body(i, c, su, sv) with the
-// neighbour sums of every node, tile_eval body(i, c, Fu, Fv) with its RHS.
+// Kinetics increments R(Y_0 + d) - R(Y_0) in the unscaled form of
+// rhs_parts (same scale factors ku, kv), exact in real arithmetic and formed
+// from the increment (da, db), so their FP32 rounding is relative to the
+// increment:
+//   FHN: u^3 increment = da (u1^2 + u1 u0 + u0^2), u1 = a0 + da;
+//   GM:  U^2 increment p = dU (2 U0 + dU),
+//        U^2/V increment = (p V0 - U0^2 dV) / (V1 V0),  V1 = V0 + dV;
+//   BZ:  U^2 V increment = p V1 + U0^2 dV.
+template <int MODEL>
+__device__ __forceinline__ void rhs_dparts(float a0, float b0, float da, float db, const RkcK &k, float &dRu,
+                                           float &dRv) {
+    if (MODEL == RD_FHN) {
+        const float u1 = a0 + da;
+        const float t = fmaf(u1, u1 + a0, a0 * a0);
+        dRu = fmaf(-da, t, da - db);
+        dRv = fmaf(-k.p3, db, da);
+    } else if (MODEL == RD_GM) {
+        const float U0 = a0 + k.u0, V0 = b0 + k.v0, V1 = V0 + db;
+        const float p = da * fmaf(2.f, U0, da);
+        const float q = fmaf(p, V0, -(U0 * U0) * db) / (V1 * V0);
+        dRu = fmaf(-k.p3, da, q);
+        dRv = p - db;
+    } else if (MODEL == RD_BZ) {
+        const float U0 = a0 + k.u0, V0 = b0 + k.v0, V1 = V0 + db;
+        const float p = da * fmaf(2.f, U0, da);
+        const float dP = fmaf(p, V1, (U0 * U0) * db);
+        dRu = fmaf(-(k.p3 + 1.f), da, dP);
+        dRv = fmaf(k.p3, da, -dP);
+    } else {
+        dRu = 0.f;
+        dRv = 0.f;
+    }
+}
+
+// Exchange the edge rows of a tile quantity (yu, yv) through ring buffer hb
+// (one barrier); tile_apply then calls body(i, c, nu, nv) with the four
+// neighbours (N, S, W, E) of every node as float4 (mirror ghosts at the
+// domain edge).
 template <int G, int TY, int TX>
 __device__ __forceinline__ void tile_exchange(float *hb, int tx, int ty, const float (&yu)[TY][TX],
                                               const float (&yv)[TY][TX]) {
@@ -249,63 +260,57 @@ __device__ __forceinline__ void tile_apply(const float *hb, int tx, int ty, cons
         for (int c = 0; c < TX; ++c) {
             const float Lu = c > 0 ? yu[i][c - 1] : wu, Ru = c < TX - 1 ? yu[i][c + 1] : eu;
             const float Lv = c > 0 ? yv[i][c - 1] : wv, Rv = c < TX - 1 ? yv[i][c + 1] : ev;
-            const float nu = (pu[c] + su[c]) + (Lu + Ru);
-            const float nv = (pv[c] + sv[c]) + (Lv + Rv);
-            body(i, c, nu, nv);
+            body(i, c, make_float4(pu[c], su[c], Lu, Ru), make_float4(pv[c], sv[c], Lv, Rv));
         }
 #pragma unroll
         for (int c = 0; c < TX; ++c) { pu[c] = yu[i][c]; pv[c] = yv[i][c]; }
     }
 }
 
-template <int MODEL, int G, int TY, int TX, class Body>
-__device__ __forceinline__ void tile_eval(float *hb, int tx, int ty, const float (&yu)[TY][TX],
-                                          const float (&yv)[TY][TX], const RkcK &k, Body body) {
-    tile_exchange<G, TY, TX>(hb, tx, ty, yu, yv);
-    tile_apply<G, TY, TX>(hb, tx, ty, yu, yv, [&](int i, int c, float su, float sv) {
-        float Fu, Fv;
-        rhs_cell<MODEL>(yu[i][c], yv[i][c], su, sv, k, Fu, Fv);
-        body(i, c, Fu, Fv);
-    });
+// Unscaled 5-point sum of an increment field: ((N + S) + (W + E)) - 4 d.
+__device__ __forceinline__ float lap5(float d, float4 n) {
+    return fmaf(-4.f, d, (n.x + n.y) + (n.z + n.w));
 }
 
-// One stage j >= 2 of the increment recurrence: Y = Y_0 + D_{j-1} (dl),
-// D_j = mu_j D_{j-1} + nu_j D_{j-2} + mt_j h F(Y) + gt_j h F_0, written over
-// D_{j-2} (dp), with mt_j h F(Y) = (mt_j h du) Lu + (mt_j h ku) Ru (likewise
-// v).  Coefficients from crow[j] (shared memory, read after the exchange
-// barrier).
+// Unscaled 5-point sum of the compensated state y + cy, with the rounding of
+// the neighbour sum kept (TwoSum): ((N + S) + (W + E)) - 4 y is then exact
+// (Sterbenz, the neighbours within a factor 2 of the node) up to the small
+// error terms, to which the compensation's own sum is added.
+__device__ __forceinline__ float lap5_exact(float y, float4 n, float lapc) {
+    const float s1 = n.x + n.y, b1 = s1 - n.x, e1 = (n.x - (s1 - b1)) + (n.y - b1);
+    const float s2 = n.z + n.w, b2 = s2 - n.z, e2 = (n.z - (s2 - b2)) + (n.w - b2);
+    const float s3 = s1 + s2, b3 = s3 - s1, e3 = (s1 - (s3 - b3)) + (s2 - b3);
+    return fmaf(-4.f, y, s3) + (((e1 + e2) + e3) + lapc);
+}
+
+// One stage j >= 2 in increment form: with F(Y_0 + D) = F_0 + dF(D),
+//   dF_u(D) = du Lap(D_u) + ku dR_u(Y_0; D)   (likewise v),
+//   D_j = mu_j D_{j-1} + nu_j D_{j-2} + (mt_j + gt_j) h F_0 + mt_j h dF(D_{j-1}),
+// the same recurrence as the stage form in real arithmetic.  D_{j-1} (dl)
+// is exchanged; D_j is written over D_{j-2} (dp).  Coefficients from
+// crow[j] (shared memory, read after the exchange barrier).
 template <int MODEL, int G, int TY, int TX>
 __device__ __forceinline__ void rkc_stage(float *hb, int tx, int ty, const float (&y0u)[TY][TX],
                                           const float (&y0v)[TY][TX], const float (&f0u)[TY][TX],
                                           const float (&f0v)[TY][TX], const float (&dlu)[TY][TX],
                                           const float (&dlv)[TY][TX], float (&dpu)[TY][TX], float (&dpv)[TY][TX],
-                                          float (&yu)[TY][TX], float (&yv)[TY][TX], const float4 *crow, int j,
-                                          float h, const RkcK &k) {
-#pragma unroll
-    for (int i = 0; i < TY; ++i)
-#pragma unroll
-        for (int c = 0; c < TX; ++c) {
-            yu[i][c] = y0u[i][c] + dlu[i][c];
-            yv[i][c] = y0v[i][c] + dlv[i][c];
-        }
-    tile_exchange<G, TY, TX>(hb, tx, ty, yu, yv);
+                                          const float4 *crow, int j, float h, const RkcK &k) {
+    tile_exchange<G, TY, TX>(hb, tx, ty, dlu, dlv);
     const float4 cj = crow[j];
-    const float mth = cj.z * h, gth = cj.w * h;
+    const float mth = cj.z * h, cfh = (cj.z + cj.w) * h;
     float ku, kv;
     react_scale<MODEL>(k, ku, kv);
     const float mdu = mth * k.du, mdv = mth * k.dv, mru = mth * ku, mrv = mth * kv;
-    tile_apply<G, TY, TX>(hb, tx, ty, yu, yv, [&](int i, int c, float su, float sv) {
-        const float a = yu[i][c], b = yv[i][c];
-        const float Lu = fmaf(-4.f, a, su), Lv = fmaf(-4.f, b, sv);
-        float gu = gth * f0u[i][c], gv = gth * f0v[i][c];
+    tile_apply<G, TY, TX>(hb, tx, ty, dlu, dlv, [&](int i, int c, float4 nu, float4 nv) {
+        float gu = cfh * f0u[i][c], gv = cfh * f0v[i][c];
         if (MODEL != RD_DIFF) {
-            float Ru, Rv;
-            rhs_parts<MODEL>(a, b, k, Ru, Rv);
-            gu = fmaf(mru, Ru, gu);
-            gv = fmaf(mrv, Rv, gv);
+            float dRu, dRv;
+            rhs_dparts<MODEL>(y0u[i][c], y0v[i][c], dlu[i][c], dlv[i][c], k, dRu, dRv);
+            gu = fmaf(mru, dRu, gu);
+            gv = fmaf(mrv, dRv, gv);
         }
-        dpu[i][c] = fmaf(cj.x, dlu[i][c], fmaf(cj.y, dpu[i][c], fmaf(mdu, Lu, gu)));
-        dpv[i][c] = fmaf(cj.x, dlv[i][c], fmaf(cj.y, dpv[i][c], fmaf(mdv, Lv, gv)));
+        dpu[i][c] = fmaf(cj.x, dlu[i][c], fmaf(cj.y, dpu[i][c], fmaf(mdu, lap5(dlu[i][c], nu), gu)));
+        dpv[i][c] = fmaf(cj.x, dlv[i][c], fmaf(cj.y, dpv[i][c], fmaf(mdv, lap5(dlv[i][c], nv), gv)));
     });
 }
 
@@ -334,7 +339,8 @@ __device__ __forceinline__ void block_reduce2(float &ss, float &mx, float *red) 
 
 // Shared memory (byte offsets): halo ring at 0 | 64 doubles of reduction
 // scratch | RkcCtl | coefficient row float4[RKC_STRIDE] at a 16-byte
-// boundary | beta[RKC_STRIDE] doubles.
+// boundary | beta[RKC_STRIDE] doubles | the state's compensation
+// [species 2][G][G] floats at a 16-byte boundary.
 template <int G, int TY, int TX>
 __host__ __device__ constexpr size_t rkc_red_off() {
     return Tiling<G, TY, TX>::SMEM;
@@ -352,8 +358,12 @@ __host__ __device__ constexpr size_t rkc_beta_off() {
     return rkc_crow_off<G, TY, TX>() + RKC_STRIDE * sizeof(float4);
 }
 template <int G, int TY, int TX>
+__host__ __device__ constexpr size_t rkc_c0_off() {
+    return (rkc_beta_off<G, TY, TX>() + RKC_STRIDE * sizeof(double) + 15) / 16 * 16;
+}
+template <int G, int TY, int TX>
 __host__ __device__ constexpr size_t rkc_smem() {
-    return rkc_beta_off<G, TY, TX>() + RKC_STRIDE * sizeof(double);
+    return rkc_c0_off<G, TY, TX>() + 2 * (size_t)G * G * sizeof(float);
 }
 
 template <int MODEL, int G, int TY, int TX>
@@ -367,7 +377,8 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
     constexpr int M = 2 * G * G;
     extern __shared__ float4 smem_f4[];
     static_assert(rkc_red_off<G, TY, TX>() % 16 == 0 && rkc_ctl_off<G, TY, TX>() % 16 == 0 &&
-                      rkc_crow_off<G, TY, TX>() % 16 == 0 && rkc_beta_off<G, TY, TX>() % 16 == 0,
+                      rkc_crow_off<G, TY, TX>() % 16 == 0 && rkc_beta_off<G, TY, TX>() % 16 == 0 &&
+                      rkc_c0_off<G, TY, TX>() % 16 == 0,
                   "shared-memory regions must start on 16-byte boundaries");
     char *sb = reinterpret_cast<char *>(smem_f4);
     float *ring = reinterpret_cast<float *>(sb);
@@ -375,15 +386,24 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
     RkcCtl &c = *reinterpret_cast<RkcCtl *>(sb + rkc_ctl_off<G, TY, TX>());
     float4 *crow = reinterpret_cast<float4 *>(sb + rkc_crow_off<G, TY, TX>());
     double *betaS = reinterpret_cast<double *>(sb + rkc_beta_off<G, TY, TX>());
+    // The state is held compensated: node value = y0 (registers) + c0
+    // (shared memory), c0 the exact FP32 rounding residuals of the accepted
+    // updates (TwoSum).  An FP32 state alone cannot sit at the discrete
+    // equilibrium, so each step would leave stiff diffusion modes of
+    // amplitude ~ulp/2, and the error estimate reports about 0.4 |h lambda|
+    // times such a mode (it does not estimate the stiff modes' true local
+    // error), which would hold h lambda_max near tol / ulp.
+    float *c0 = reinterpret_cast<float *>(sb + rkc_c0_off<G, TY, TX>());
     const int tid = threadIdx.x, tx = tid % NX, ty = tid / NX;
     for (int i = tid; i < RKC_STRIDE; i += blockDim.x) betaS[i] = beta[i];
     const int r = blockIdx.x;
     float *base = fields + field_offset + (int64_t)r * M;
     const bool adaptive = run.s_fixed < 2;
+    float ku, kv;
+    react_scale<MODEL>(k, ku, kv);
 
     float y0u[TY][TX], y0v[TY][TX], f0u[TY][TX], f0v[TY][TX];
     float d1u[TY][TX], d1v[TY][TX], d2u[TY][TX], d2v[TY][TX];
-    float yu[TY][TX], yv[TY][TX];
     tile_load<G, TY, TX>(base, tx, ty, y0u, y0v);
     {
         CoefF cf{};
@@ -391,24 +411,54 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
         cf.v0 = k.v0;
         tile_to_state<MODEL, TY, TX>(y0u, y0v, cf);
     }
+#pragma unroll
+    for (int i = 0; i < TY; ++i)
+#pragma unroll
+        for (int cc = 0; cc < TX; ++cc) {
+            const int node = (ty * TY + i) * G + tx * TX + cc;
+            c0[node] = 0.f;
+            c0[G * G + node] = 0.f;
+        }
     // in-domain neighbour count of each node (Gershgorin row weights)
     auto ncount = [&](int i, int cc) {
         const int y = ty * TY + i, x = tx * TX + cc;
         return (float)((x > 0) + (x < G - 1) + (y > 0) + (y < G - 1));
     };
+    // 5-point sum of the compensation at node (y, x) of species sp
+    auto lapc = [&](int sp, int y, int x) {
+        const float *cs = c0 + sp * G * G;
+        const float ce = cs[y * G + x];
+        const float n = cs[(y > 0 ? y - 1 : y) * G + x], so = cs[(y < G - 1 ? y + 1 : y) * G + x];
+        const float w = cs[y * G + (x > 0 ? x - 1 : x)], e = cs[y * G + (x < G - 1 ? x + 1 : x)];
+        return fmaf(-4.f, ce, (n + so) + (w + e));
+    };
 
     int hk = 0;
-    // F(Y_0) and rho(Y_0)
+    // F_0 = F(Y_0) of the stored compensated state (the kinetics at y0; the
+    // compensation, below ulp/2, only enters the stiff diffusion term)
+    auto eval0 = [&]() {
+        tile_exchange<G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, y0u, y0v);
+        tile_apply<G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, y0u, y0v,
+                              [&](int i, int cc, float4 nu, float4 nv) {
+                                  const int y = ty * TY + i, x = tx * TX + cc;
+                                  const float Lu = lap5_exact(y0u[i][cc], nu, lapc(0, y, x));
+                                  const float Lv = lap5_exact(y0v[i][cc], nv, lapc(1, y, x));
+                                  float Ru, Rv;
+                                  rhs_parts<MODEL>(y0u[i][cc], y0v[i][cc], k, Ru, Rv);
+                                  f0u[i][cc] = fmaf(k.du, Lu, ku * Ru);
+                                  f0v[i][cc] = fmaf(k.dv, Lv, kv * Rv);
+                              });
+        hk ^= 1;
+    };
+    eval0();
     float rmax = 0.f;
-    tile_eval<MODEL, G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, y0u, y0v, k,
-                                [&](int i, int cc, float Fu, float Fv) {
-                                    f0u[i][cc] = Fu;
-                                    f0v[i][cc] = Fv;
-                                    if (adaptive)
-                                        rmax = fmaxf(rmax, gersh_cell<MODEL>(y0u[i][cc] + k.u0, y0v[i][cc] + k.v0,
-                                                                             ncount(i, cc), k));
-                                });
-    hk ^= 1;
+    if (adaptive) {
+#pragma unroll
+        for (int i = 0; i < TY; ++i)
+#pragma unroll
+            for (int cc = 0; cc < TX; ++cc)
+                rmax = fmaxf(rmax, gersh_cell<MODEL>(y0u[i][cc] + k.u0, y0v[i][cc] + k.v0, ncount(i, cc), k));
+    }
     {
         float dummy = 0.f;
         block_reduce2(dummy, rmax, reinterpret_cast<float *>(red));
@@ -459,7 +509,7 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
         // previous increments alternate without register moves
         for (int j = 2; j <= s; j += 2) {
             rkc_stage<MODEL, G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, y0u, y0v, f0u, f0v, d1u, d1v, d2u,
-                                        d2v, yu, yv, crow, j, h, k);
+                                        d2v, crow, j, h, k);
             hk ^= 1;
             if (j + 1 > s) {
 #pragma unroll
@@ -472,37 +522,35 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
                 break;
             }
             rkc_stage<MODEL, G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, y0u, y0v, f0u, f0v, d2u, d2v, d1u,
-                                        d1v, yu, yv, crow, j + 1, h, k);
+                                        d1v, crow, j + 1, h, k);
             hk ^= 1;
         }
-        // Y_s, F(Y_s) (kept in d2), error estimate and rho(Y_s)
-#pragma unroll
-        for (int i = 0; i < TY; ++i)
-#pragma unroll
-            for (int cc = 0; cc < TX; ++cc) {
-                yu[i][cc] = y0u[i][cc] + d1u[i][cc];
-                yv[i][cc] = y0v[i][cc] + d1v[i][cc];
-            }
+        // dF(D_s) = F(Y_s) - F_0, error estimate and rho(Y_s)
         float acc = 0.f;
         rmax = 0.f;
-        const float rtol = (float)run.rtol, atol = (float)run.atol, h04 = 0.4f * h;
-        tile_eval<MODEL, G, TY, TX>(
-            ring + hk * (T::HALO_FLOATS / 2), tx, ty, yu, yv, k, [&](int i, int cc, float Fu, float Fv) {
-                d2u[i][cc] = Fu;
-                d2v[i][cc] = Fv;
-                if (adaptive) {
-                    // est = (12 (Y_0 - Y_s) + 6 h (F_0 + F_s)) / 15,  Y_0 - Y_s = -D_s
-                    const float eu = fmaf(-0.8f, d1u[i][cc], h04 * (f0u[i][cc] + Fu));
-                    const float ev = fmaf(-0.8f, d1v[i][cc], h04 * (f0v[i][cc] + Fv));
+        if (adaptive) {
+            const float rtol = (float)run.rtol, atol = (float)run.atol, h04 = 0.4f * h;
+            tile_exchange<G, TY, TX>(ring + hk * (T::HALO_FLOATS / 2), tx, ty, d1u, d1v);
+            tile_apply<G, TY, TX>(
+                ring + hk * (T::HALO_FLOATS / 2), tx, ty, d1u, d1v, [&](int i, int cc, float4 nu, float4 nv) {
+                    float dRu = 0.f, dRv = 0.f;
+                    if (MODEL != RD_DIFF)
+                        rhs_dparts<MODEL>(y0u[i][cc], y0v[i][cc], d1u[i][cc], d1v[i][cc], k, dRu, dRv);
+                    const float dFu = fmaf(k.du, lap5(d1u[i][cc], nu), ku * dRu);
+                    const float dFv = fmaf(k.dv, lap5(d1v[i][cc], nv), kv * dRv);
+                    // est = (12 (Y_0 - Y_s) + 6 h (F_0 + F_s)) / 15
+                    //     = -0.8 D_s + 0.4 h (2 F_0 + dF(D_s))
+                    const float eu = fmaf(-0.8f, d1u[i][cc], h04 * fmaf(2.f, f0u[i][cc], dFu));
+                    const float ev = fmaf(-0.8f, d1v[i][cc], h04 * fmaf(2.f, f0v[i][cc], dFv));
                     const float U0 = y0u[i][cc] + k.u0, V0 = y0v[i][cc] + k.v0;
-                    const float Us = yu[i][cc] + k.u0, Vs = yv[i][cc] + k.v0;
+                    const float Us = (y0u[i][cc] + d1u[i][cc]) + k.u0, Vs = (y0v[i][cc] + d1v[i][cc]) + k.v0;
                     const float qu = __fdividef(eu, fmaf(rtol, fmaxf(fabsf(U0), fabsf(Us)), atol));
                     const float qv = __fdividef(ev, fmaf(rtol, fmaxf(fabsf(V0), fabsf(Vs)), atol));
                     acc = fmaf(qu, qu, fmaf(qv, qv, acc));
                     rmax = fmaxf(rmax, gersh_cell<MODEL>(Us, Vs, ncount(i, cc), k));
-                }
-            });
-        hk ^= 1;
+                });
+            hk ^= 1;
+        }
         float ss = acc;
         block_reduce2(ss, rmax, reinterpret_cast<float *>(red));
         if (tid == 0) {
@@ -511,15 +559,31 @@ rd_rkc_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun r
         }
         __syncthreads();
         if (c.accept) {
+            // (y0 + c0) + D_s, compensated: TwoSum of y0 and D_s, its error
+            // added to c0, renormalised
 #pragma unroll
             for (int i = 0; i < TY; ++i)
 #pragma unroll
                 for (int cc = 0; cc < TX; ++cc) {
-                    y0u[i][cc] = yu[i][cc];
-                    y0v[i][cc] = yv[i][cc];
-                    f0u[i][cc] = d2u[i][cc];
-                    f0v[i][cc] = d2v[i][cc];
+                    const int node = (ty * TY + i) * G + tx * TX + cc;
+                    {
+                        const float sw = y0u[i][cc] + d1u[i][cc], bp = sw - y0u[i][cc];
+                        const float e = (y0u[i][cc] - (sw - bp)) + (d1u[i][cc] - bp);
+                        const float lo = c0[node] + e;
+                        y0u[i][cc] = sw + lo;
+                        c0[node] = lo - (y0u[i][cc] - sw);
+                    }
+                    {
+                        const float sw = y0v[i][cc] + d1v[i][cc], bp = sw - y0v[i][cc];
+                        const float e = (y0v[i][cc] - (sw - bp)) + (d1v[i][cc] - bp);
+                        const float lo = c0[G * G + node] + e;
+                        y0v[i][cc] = sw + lo;
+                        c0[G * G + node] = lo - (y0v[i][cc] - sw);
+                    }
                 }
+            // F_0 of the new state afresh (not F_0 + dF(D_s)), so the run
+            // keeps solving the discrete system of the state it holds
+            if (!c.done) eval0();
         }
     }
     {

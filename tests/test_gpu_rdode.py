@@ -80,6 +80,8 @@ def test_adaptive_run_to_t50(p):
     assert np.array_equal(got[:, 0] > 1.0, acc[:, 0] > 1.0)
     st = st.cpu().numpy()
     assert np.abs(st[:, 0] - ost[:, 0]).max() <= max(3, 0.05 * ost[:, 0].max())
+    if (st[:, :2] == ost[:, :2]).all():
+        assert rel_err(got, mine) <= 1e-4
     # the stored FP32 state cannot do better than the rounding of w, which
     # the stiff diffusion turns into |F| up to D (N-1)^2 * 4 * ulp(w) / 2
     floor = P0[1] * (N - 1) ** 2 * 4 * np.abs(got[:, 1]).max() * 2.0 ** -24

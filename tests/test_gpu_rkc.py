@@ -7,13 +7,13 @@ stages themselves; held to the field tolerance max|gpu - oracle| /
 max|oracle| <= 1e-5 per realisation and species, and the RHS count exactly.
 
 Adaptive: the step-control decisions (accept, s, h) are taken from FP32
-fields on the GPU and FP64 fields in the oracle; the error estimate is a
-small difference of stage values, so its FP32 value carries a relative
-error of about 1e-3 and the two schedules may part at a decision boundary.
-What is unique is compared exactly where no decision is near a boundary (a
-single step's stage count, a forced rejection); the rest is compared
-through its accuracy: the GPU's final state must be as close to an
-accurate reference as the oracle's own adaptive result at that tolerance.
+fields on the GPU and FP64 fields in the oracle.  The GPU forms every RHS
+evaluation of a step as F(Y_0) + dF(increment) and holds the state
+compensated, so its error estimate is not disturbed by rounding-level
+stiff modes and it takes the oracle's schedule; a decision could still
+part at an exact boundary, so the counts are compared to within one step,
+the fields to the oracle's result when the schedules agree, and the
+accuracy against an accurate reference in every case.
 """
 import numpy as np
 import pytest
@@ -166,8 +166,10 @@ def test_forced_rejection_matches(p):
 
 @pytest.mark.parametrize("model,G,par,noise,T,tol", [
     (W.FHN, 64, W.FHN_THETA0, (-0.05, 0.05), 10000 * 2 ** -10, 1e-5),
-    (W.GM, 64, (2.5e-4, 0.01, 1.0, 0.52), (0.0, 0.01), 40.0, 1e-5),
-    (W.BZ, 64, W.BZ_THETA0, (0.0, 0.01), 10.0, 1e-5),
+    (W.FHN, 64, W.FHN_THETA0, (-0.05, 0.05), 10000 * 2 ** -10, 1e-7),
+    (W.GM, 64, (2.5e-4, 0.01, 1.0, 0.52), (0.0, 0.01), 40.0, 1e-6),
+    (W.BZ, 64, W.BZ_THETA0, (0.0, 0.01), 10.0, 1e-7),
+    (W.FHN, 32, (2.8e-4, 0.05, 10.0, 0.95), (-0.05, 0.05), 2000 * 2 ** -8, 1e-6),
 ])
 def test_adaptive_run_against_oracle(p, model, G, par, noise, T, tol):
     n = 2
@@ -182,11 +184,14 @@ def test_adaptive_run_against_oracle(p, model, G, par, noise, T, tol):
     # accurate reference: the oracle at a 100x tighter tolerance
     acc, _, _ = oracle.rkc_adaptive(model, par, T, 1e-3, tol / 100, tol / 100, w0)
     e_gpu, e_orc = rel_err(got, acc), rel_err(mine, acc)
-    assert e_gpu <= 2.0 * e_orc + 1e-5
-    # the schedules are close: same work within a few steps
-    assert np.abs(st[:, 0] - ost[:, 0]).max() <= max(2, 0.05 * ost[:, 0].max())
-    assert np.abs(st[:, 2] - ost[:, 2]).max() <= 0.1 * ost[:, 2].max()
-    assert np.abs(st[:, 3] - ost[:, 3]).max() <= 2
+    assert e_gpu <= 1.05 * e_orc + 1e-6
+    # the FP32 run takes the FP64 run's schedule (its error estimate is not
+    # disturbed by rounding-level stiff modes) and so lands on its result
+    assert np.abs(st[:, 0] - ost[:, 0]).max() <= 1
+    assert np.abs(st[:, 1] - ost[:, 1]).max() <= 1
+    assert np.abs(st[:, 2] - ost[:, 2]).max() <= 0.02 * ost[:, 2].max()
+    if (st == ost).all():
+        assert rel_err(got, mine) <= FIELD_TOL
 
 
 def test_split_horizon_mixed_groups(p):
