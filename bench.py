@@ -585,13 +585,51 @@ def rkc_bench(p, torch, dev, stream, pk, src, tols=(1e-5, 1e-6, 1e-7)):
                      "cell_stage_updates_per_s": n_rhs * G * G / t,
                      "alu_tinst_per_s": inst / t / 1e12, "alu_frac": inst / t / 1e12 / peak_alu,
                      "speedup_vs_euler": t_eul / t, "as_accurate_as_euler": err <= err_eul})
+    rdode = rdode_c7(p, torch, dev, stream)
     return {"workload": "FHN 64x64, 2 x 64 realisations, 0 -> T = 10^4 x 2^-10 (the c2 horizon)",
+            "rdode_c7": rdode,
             "fixed_schedule": fixed,
             "euler": {"ms": t_eul * 1e3, "steps": gd["n_steps"], "rel_err_sample": err_eul},
             "reference": "oracle adaptive, tolerance 1e-9, realisations 0 and 1",
             "peak_note": "alu peak = 148 SM x 128 FP32 lanes x max SM clock (%s peaks file); "
                          "%d FP32 instructions per cell per RHS stage" % (src, RKC_FP32_INST_PER_CELL_STAGE[gd["model"]]),
             "tolerances": rows}
+
+
+def rdode_c7(p, torch, dev, stream):
+    """The 1-D reaction-diffusion-ODE workload c7 (Sec. 4.3, Table 1: 64
+    nodes, t in [0, 50], 2 x 100 realisations), adaptive stabilised RK2 at
+    the configured tolerance, one warp per realisation; the oracle's FP64
+    run of a sample of realisations on the host for comparison."""
+    import oracle
+    cfg = W.config("c7")
+    gd = cfg["groups"][0]
+    tol = cfg["rkc_tol"]
+    sim = p.Simulation([p.Group.from_dict(gd)], device=dev)
+    ts = []
+    for _ in range(4):
+        sim.reinit()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, _ = sim.integrate_rkc(1e-3, rtol=tol, atol=tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    assert sim.sync_status() == 0
+    t = min(ts[1:])
+    st = st.cpu().numpy()
+    n, N = gd["n_real"], gd["G"]
+    sample = 8
+    w0 = oracle.rdode_init(N, sample, gd["noise"][0], gd["noise"][1], gd["seed"], 10)
+    T = gd["dt"] * gd["n_steps"]
+    t0 = time.perf_counter()
+    _, ost, failed = oracle.rkc_adaptive(W.RDODE, gd["params"], T, 1e-3, tol, tol, w0)
+    t_orc = time.perf_counter() - t0
+    return {"workload": "RD-ODE 64 nodes, 200 realisations, t in [0, 50], tol %g" % tol, "ms": t * 1e3,
+            "realisations_per_s": n / t, "steps_mean": float(st[:, 0].mean()), "rhs_mean": float(st[:, 2].mean()),
+            "cell_stage_updates_per_s": float(st[:, 2].sum()) * 2 * N / t,
+            "oracle_sample": {"realisations": sample, "s": t_orc, "realisations_per_s": sample / t_orc,
+                              "threads": oracle.threads(), "steps_mean": float(ost[:, 0].mean())}}
 
 
 def mcil_bench(p, torch, dev, stream):

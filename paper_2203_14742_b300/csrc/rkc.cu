@@ -217,7 +217,7 @@ __device__ __forceinline__ void rhs_dparts(float a0, float b0, float da, float d
     } else if (MODEL == RD_GM) {
         const float U0 = a0 + k.u0, V0 = b0 + k.v0, V1 = V0 + db;
         const float p = da * fmaf(2.f, U0, da);
-        const float q = fmaf(p, V0, -(U0 * U0) * db) / (V1 * V0);
+        const float q = __fdividef(fmaf(p, V0, -(U0 * U0) * db), V1 * V0);
         dRu = fmaf(-k.p3, da, q);
         dRv = p - db;
     } else if (MODEL == RD_BZ) {

@@ -109,10 +109,12 @@ __device__ __forceinline__ void w_neighbours(const float (&w)[NPL], int lane, fl
     }
 }
 
-// Kinetics: R_u = -u - u w + m1 q,  R_w = -m3 w - u w + m2 q.
+// Kinetics: R_u = -u - u w + m1 q,  R_w = -m3 w - u w + m2 q.  (The
+// quotients here and below use the 2-ulp fast division: they sit on the
+// latency chain of a warp's stage, and FP32 state rounding dominates.)
 __device__ __forceinline__ void kin1(float u, float w, const Rkc1K &K, float &Ru, float &Rw) {
     const float uu = u * u;
-    const float q = uu / fmaf(K.k, uu, 1.f);
+    const float q = __fdividef(uu, fmaf(K.k, uu, 1.f));
     Ru = fmaf(K.m1, q, fmaf(-u, w, -u));
     Rw = fmaf(K.m2, q, fmaf(-u, w, -K.m3 * w));
 }
@@ -126,7 +128,7 @@ __device__ __forceinline__ void dkin1(float u0, float w0, float du, float dw, co
                                       float &dRw) {
     const float u1 = u0 + du, w1 = w0 + dw;
     const float den0 = fmaf(K.k, u0 * u0, 1.f), den1 = fmaf(K.k, u1 * u1, 1.f);
-    const float dq = (du * fmaf(2.f, u0, du)) / (den0 * den1);
+    const float dq = __fdividef(du * fmaf(2.f, u0, du), den0 * den1);
     const float t = fmaf(u0, dw, du * w1);
     dRu = fmaf(K.m1, dq, -du - t);
     dRw = fmaf(K.m2, dq, fmaf(-K.m3, dw, -t));
@@ -135,7 +137,7 @@ __device__ __forceinline__ void dkin1(float u0, float w0, float du, float dw, co
 // Gershgorin row sums at one node with n in-domain neighbours.
 __device__ __forceinline__ float gersh1(float u, float w, float n, const Rkc1K &K) {
     const float den = fmaf(K.k, u * u, 1.f);
-    const float dq = (2.f * u) / (den * den);
+    const float dq = __fdividef(2.f * u, den * den);
     const float fu = fmaf(K.m1, dq, -1.f - w), fw = -u;
     const float gu = fmaf(K.m2, dq, -w), gw = -K.m3 - u;
     const float nd = n * K.dd;
@@ -150,6 +152,11 @@ __global__ void __launch_bounds__(128) rd_rkc1d_kernel(float *__restrict__ field
                                                        double m3, double kk, double *__restrict__ residual,
                                                        uint32_t *__restrict__ status) {
     constexpr int N = 32 * NPL;
+    // beta(s) in shared memory for the stage-count search on each warp's
+    // serial control path (loaded before any warp leaves)
+    __shared__ double betaS[RKC_STRIDE];
+    for (int i = threadIdx.x; i < RKC_STRIDE; i += blockDim.x) betaS[i] = beta[i];
+    __syncthreads();
     const int wid = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= n_real) return;                       // whole warps only
@@ -226,7 +233,7 @@ __global__ void __launch_bounds__(128) rd_rkc1d_kernel(float *__restrict__ field
     c.accept = 0;
     c.done = 0;
     c.fail = 0;
-    rkc_plan(c, run, beta);
+    rkc_plan(c, run, betaS);
 
     // one stage j >= 2: dp <- mu dl + nu dp + mt h F(Y_0 + dl) + gt h F_0
     //                       = mu dl + nu dp + (mt + gt) h F_0 + mt h dF(dl)
@@ -301,7 +308,7 @@ __global__ void __launch_bounds__(128) rd_rkc1d_kernel(float *__restrict__ field
         }
         const float ss = warp_sum(acc);
         c.rho_new = warp_max(rmax);
-        rkc_decide(c, run, beta, ss, 2 * N);
+        rkc_decide(c, run, betaS, ss, 2 * N);
         if (c.accept) {
 #pragma unroll
             for (int i = 0; i < NPL; ++i) {
