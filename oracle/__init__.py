@@ -38,6 +38,8 @@ def lib():
         L.orc_rdode_rhs.argtypes = [C.c_int, dp, dp, dp]
         L.orc_rdode_gershgorin.argtypes = [C.c_int, dp, dp]
         L.orc_rdode_gershgorin.restype = C.c_double
+        L.orc_radii_linear.argtypes = [dp, C.c_int64, C.c_int, dp, dp]
+        L.orc_radii_linear.restype = C.c_double
         L.orc_rkc_coef.argtypes = [C.c_int, dp, dp, dp, dp, dp]
         L.orc_rkc_beta.argtypes = [C.c_int]
         L.orc_rkc_beta.restype = C.c_double
@@ -217,11 +219,24 @@ def bins_counts(d2, radii_):
     return bins, counts
 
 
-def cil(X1, X2, b=None, M=None, radii_=None):
-    """Full CIL of two FP32 pattern sets.  Returns dict with d2, R0, radii,
-    bins, counts."""
+def radii_linear(d2, M):
+    """(R0, radii[M], R_min): the linear law R_k = R0 - k (R0 - R_min) / M
+    with R0 / R_min the largest / smallest distance."""
+    d2 = _d(d2)
+    out = np.empty(M, np.float64)
+    rmin = C.c_double()
+    R0 = lib().orc_radii_linear(_p(d2, C.c_double), d2.size, M, _p(out, C.c_double), C.byref(rmin))
+    return R0, out, rmin.value
+
+
+def cil(X1, X2, b=None, M=None, radii_=None, law="power"):
+    """Full CIL of two FP32 pattern sets (law "power": R_k = R0 b^-k;
+    "linear": R_k = R0 - k (R0 - R_min) / M).  Returns dict with d2, R0,
+    radii, bins, counts."""
     d2 = pair_d2(X1, X2)
-    if radii_ is None:
+    if radii_ is None and law == "linear":
+        R0, r, _ = radii_linear(d2, M)
+    elif radii_ is None:
         R0, r = radii(d2, b, M)
     else:
         r = _d(radii_)

@@ -19,6 +19,9 @@
  *     d2_f32): 256 interleaved partial sums combined by a halving tree;
  *   - R_k = R_{k-1} / b in FP64 (k = 1..M), thresholds T_k = R_k * R_k, and
  *     "d < R_k" is decided as d^2 < T_k;
+ *   - the linear law of Sec. 2.1 (R_k = R0 - k h, h = (R0 - R_M) / M,
+ *     R_M = the smallest cross-set distance, Table 1 for the MC and RD-ODE
+ *     models) as the FP64 expressions h = (R0 - R_M) / M, R_k = R0 - k h;
  *   - covariance normaliser 1/(T-1);
  *   - components whose count is identical across all resamples are
  *     inactive; the Gaussian statistics use the active block only.
@@ -102,6 +105,29 @@ double orc_radii(const double *d2, int64_t n_pairs, double b, int M, double *rad
         R = R / b;
         radii[k] = R;
     }
+    return R0;
+}
+
+/* Linear radii law (Sec. 2.1, Sec. 3.2; Table 1 uses it for the MC and
+   RD-ODE models): R0 = sqrt(max d^2) and R_M = sqrt(min d^2) over the given
+   pairs (the largest and the smallest distance), h = (R0 - R_M) / M,
+   R_k = R0 - k h for k = 1..M (each an FP64 expression, k exact).
+   radii[0..M-1] = R_1..R_M.  Returns R0; *Rmin receives sqrt(min d^2). */
+double orc_radii_linear(const double *d2, int64_t n_pairs, int M, double *radii, double *Rmin)
+{
+    double mx = d2[0], mn = d2[0];
+    for (int64_t k = 1; k < n_pairs; ++k) {
+        if (d2[k] > mx) mx = d2[k];
+        if (d2[k] < mn) mn = d2[k];
+    }
+    const double R0 = sqrt(mx);
+    const double RM = sqrt(mn);
+    const double h = (R0 - RM) / (double)M;
+    for (int k = 1; k <= M; ++k) {
+        const double kh = (double)k * h;
+        radii[k - 1] = R0 - kh;
+    }
+    *Rmin = RM;
     return R0;
 }
 

@@ -268,3 +268,35 @@ def test_stats_mean_cov_are_exactly_rounded_rationals():
                      (Fraction(int(Y[t, l]), npairs) - Fraction(int(Y[:, l].sum()), T * npairs))
                      for t in range(T)) / (T - 1)
             assert s["cov"][k, l] == float(ex)
+
+
+def test_linear_radii_hand_count():
+    # Linear radii law (Sec. 2.1, Sec. 3.2): set 1 = {0, 1}, set 2 = {3, 5, 6}
+    # on a line.  Cross-set distances 3, 5, 6 / 2, 4, 5; R0 = 6 (largest),
+    # R_M = 2 (smallest), M = 4: h = 1, radii 5, 4, 3, 2.  K = #{k : d < R_k}:
+    # d = 3 -> 2, 5 -> 0, 6 -> 0, 2 -> 3, 4 -> 1, 5 -> 0; counts[k-1] =
+    # #{K >= k} = 3, 2, 1, 0.
+    X1 = np.array([[0.0], [1.0]], np.float32)
+    X2 = np.array([[3.0], [5.0], [6.0]], np.float32)
+    o = oracle.cil(X1, X2, M=4, law="linear")
+    assert o["R0"] == 6.0
+    assert list(o["radii"]) == [5.0, 4.0, 3.0, 2.0]
+    assert o["bins"].tolist() == [[2, 0, 0], [3, 1, 0]]
+    assert list(o["counts"]) == [3, 2, 1, 0]
+    R0, r, rmin = oracle.radii_linear(o["d2"], 4)
+    assert rmin == 2.0 and R0 == 6.0
+
+
+def test_linear_radii_span_max_to_min():
+    rng = np.random.default_rng(4)
+    X1 = rng.standard_normal((7, 33)).astype(np.float32)
+    X2 = rng.standard_normal((9, 33)).astype(np.float32)
+    d2 = oracle.pair_d2(X1, X2)
+    for M in (1, 5, 13):
+        R0, r, rmin = oracle.radii_linear(d2, M)
+        assert R0 == np.sqrt(d2.max()) and rmin == np.sqrt(d2.min())
+        assert np.all(np.diff(np.concatenate([[R0], r])) < 0)        # decreasing
+        assert abs(r[-1] - rmin) <= 1e-12 * R0                       # ends at R_min
+        # equal steps
+        steps = -np.diff(np.concatenate([[R0], r]))
+        assert np.allclose(steps, (R0 - rmin) / M, rtol=1e-12)
