@@ -365,6 +365,23 @@ rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1,
                        double *d_C, int64_t *d_n_rechecked, void *d_work, size_t work_bytes,
                        void *stream);
 
+/* cil_features_linear — the same correlation integral with the linear radii
+ * law of Sec. 2.1 / Sec. 3.2 (Table 1 uses it for the MC and RD-ODE models):
+ *   R0 = sqrt(max_ij d2_ij), R_min = sqrt(min_ij d2_ij) (the largest and the
+ *   smallest cross-set distance, both from the canonical d2),
+ *   h = (R0 - R_min) / M,  R_k = R0 - k h  (k = 1..M),
+ * every operation FP64 rounded to nearest.  Bins and counts exactly as for
+ * cil_features (K_ij = #{k : d2_ij < R_k * R_k}); d_radii_out[0] = R0,
+ * d_radii_out[M] = R_M.  The smallest distance is found exactly like the
+ * largest (tier-1 bounds, error-free tier 2, canonical tier 3 for the
+ * candidates left).  Arguments, workspace and limits as for cil_features
+ * (no b). */
+rd_status cil_features_linear(const float *d_X1, int64_t ld1, int64_t n1,
+                              const float *d_X2, int64_t ld2, int64_t n2, int64_t d, int32_t M,
+                              double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
+                              double *d_C, int64_t *d_n_rechecked, void *d_work, size_t work_bytes,
+                              void *stream);
+
 /* cil_features_static — cil_features for callers that cannot allocate
  * device memory on their hot path (cudaMalloc may synchronise the whole
  * device; some host applications own all device memory through their own

@@ -62,6 +62,8 @@ _SIGS = {
     "cil_workspace_size": (_i32, [_i64, _i64, _i64, C.POINTER(_sz)]),
     "cil_features": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _dbl, _i32, _vp, _vp, _vp,
                             _vp, _vp, _vp, _sz, _vp]),
+    "cil_features_linear": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp,
+                                   _vp, _sz, _vp]),
     "cil_features_exact": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _dbl, _i32, _vp, _vp,
                                   _vp, _vp, _vp, _sz, _vp]),
     "cil_gram_only": (_i32, [_i64, _i64, _i64, _vp, _sz, C.POINTER(_dbl), _vp]),
@@ -350,9 +352,12 @@ def _cil_call(fn, X1, X2, b, M, radii, work=None, out=None):
         w, wb = _workspace(n1, n2, d, dev)
     else:
         w, wb = work, work.numel()
-    args = [_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, d, _ptr(radii), float(b or 0.0), int(M),
-            _ptr(radii_out), _ptr(bins), _ptr(counts), _ptr(Cvec)]
-    if fn == "cil_features":
+    if fn == "cil_features_linear":
+        args = [_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, d, int(M)]
+    else:
+        args = [_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, d, _ptr(radii), float(b or 0.0), int(M)]
+    args += [_ptr(radii_out), _ptr(bins), _ptr(counts), _ptr(Cvec)]
+    if fn in ("cil_features", "cil_features_linear"):
         args.append(_ptr(nre))
     args += [_ptr(w), wb, _stream()]
     _check(fn, getattr(lib(), fn)(*args))
@@ -386,6 +391,12 @@ def cil(X1, X2, b=1.3, M=16, radii=None, work=None, out=None):
     (optional) supplies the output tensors: radii [M+1], bins [n1, n2] uint8,
     counts [M] int64, C [M] float64, n_rechecked [1] int64."""
     return _cil_call("cil_features", X1, X2, b, M, radii, work, out)
+
+
+def cil_linear(X1, X2, M=13, work=None, out=None):
+    """Correlation integral with the linear radii law R_k = R0 - k (R0 - R_min)/M
+    (Sec. 2.1; Table 1's law for the MC and RD-ODE models)."""
+    return _cil_call("cil_features_linear", X1, X2, None, M, None, work, out)
 
 
 def cil_exact(X1, X2, b=1.3, M=16, radii=None, work=None):

@@ -60,7 +60,34 @@ enum : int {
     SC_Q2 = 6,     // tier-3 queue length
     SC_UNDECIDED = 7,
     SC_TIMEOUT = 8,
+    // linear radii law: the smallest distance, kept as minima through
+    // atomicMax of complemented bit patterns (the slots start at 0)
+    SC_LBM1 = 9,   // min over pairs of the tier-1 lower bound
+    SC_UBM1 = 10,  // min over pairs of the tier-1 upper bound
+    SC_LBM2 = 11,  // min over minimum candidates of the tier-2 lower bound
+    SC_UBM2 = 12,  // min over minimum candidates of the tier-2 upper bound
+    SC_MIN = 13,   // exact minimum
 };
+
+// queue entries: pair index | bit 63 maximum candidate | bit 62 minimum candidate
+static constexpr unsigned long long Q_MAX = 1ull << 63, Q_MIN = 1ull << 62, Q_IDX = Q_MIN - 1;
+
+// radii laws (Sec. 2.1): R_k = R_{k-1} / b, or R_k = R0 - k (R0 - R_min) / M
+enum : int { LAW_POWER = 0, LAW_LINEAR = 1 };
+
+// minima of non-negative values through atomicMax on complemented bits
+__device__ __forceinline__ void atomic_min_f(unsigned long long *slot, float v) {
+    atomicMax(slot, 0xFFFFFFFFull - (unsigned long long)__float_as_uint(v));
+}
+__device__ __forceinline__ float read_min_f(unsigned long long s) {
+    return s ? __uint_as_float((unsigned)(0xFFFFFFFFull - s)) : __int_as_float(0x7f800000);
+}
+__device__ __forceinline__ void atomic_min_d(unsigned long long *slot, double v) {
+    atomicMax(slot, ~(unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ double read_min_d(unsigned long long s) {
+    return s ? __longlong_as_double((long long)~s) : __longlong_as_double(0x7ff0000000000000ll);
+}
 
 struct CilWork {
     int64_t n1, n2, d, dp;
@@ -333,6 +360,7 @@ __global__ void d2_bound_kernel(CilWork w, float gam) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t np = w.n1 * w.n2;
     float lb = 0.f, ub = 0.f;
+    float lbm = __int_as_float(0x7f800000), ubm = __int_as_float(0x7f800000);
     if (q < np) {
         const int64_t i = q / w.n2, j = q - i * w.n2;
         const int64_t a = i, bb = w.n1 + j;
@@ -366,16 +394,24 @@ __global__ void d2_bound_kernel(CilWork w, float gam) {
         w.hi32[q] = hi;
         lb = fmaxf(lo, 0.f);
         ub = fmaxf(hi, 0.f);
+        lbm = lb;
+        ubm = ub;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lb = fmaxf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
         ub = fmaxf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
+        lbm = fminf(lbm, __shfl_xor_sync(0xffffffffu, lbm, o));
+        ubm = fminf(ubm, __shfl_xor_sync(0xffffffffu, ubm, o));
     }
     if ((threadIdx.x & 31) == 0) {
         // non-negative floats order like their bit patterns
         atomicMax(&w.scal[SC_LB1], (unsigned long long)__float_as_uint(lb));
         atomicMax(&w.scal[SC_UB1], (unsigned long long)__float_as_uint(ub));
+        if (lbm < __int_as_float(0x7f800000)) {
+            atomic_min_f(&w.scal[SC_LBM1], lbm);
+            atomic_min_f(&w.scal[SC_UBM1], ubm);
+        }
     }
 }
 
@@ -385,12 +421,39 @@ __global__ void d2_bound_kernel(CilWork w, float gam) {
 // (beta[k] = b^-2k from the host).  tier 1 writes FP32 ranges rounded
 // outwards, tier 2 FP64 ranges.  With given radii the ranges are the exact
 // thresholds.
-__global__ void ranges_kernel(CilWork w, const double *__restrict__ radii_in, Beta beta, int M, int tier) {
+//
+// Linear law: R_k = (1 - k/M) R0 + (k/M) R_min in real arithmetic, increasing
+// in both; its range follows from the ranges of R0 and R_min, widened by an
+// absolute margin (the FP64 evaluation of h = (R0 - R_min)/M and
+// R_k = R0 - k h errs by a few ulp of R0).
+__global__ void ranges_kernel(CilWork w, const double *__restrict__ radii_in, Beta beta, int M, int tier,
+                              int law) {
     const int k = threadIdx.x;
     if (k >= M) return;
     double lo, hi;
     if (radii_in) {
         lo = hi = __dmul_rn(radii_in[k], radii_in[k]);
+    } else if (law == LAW_LINEAR) {
+        double mxlo, mxhi, mnlo, mnhi;
+        if (tier == 1) {
+            mxlo = (double)__uint_as_float((unsigned)w.scal[SC_LB1]);
+            mxhi = (double)__uint_as_float((unsigned)w.scal[SC_UB1]);
+            mnlo = (double)read_min_f(w.scal[SC_LBM1]);
+            mnhi = (double)read_min_f(w.scal[SC_UBM1]);
+        } else {
+            mxlo = __longlong_as_double((long long)w.scal[SC_LB2]);
+            mxhi = __longlong_as_double((long long)w.scal[SC_UB2]);
+            mnlo = read_min_d(w.scal[SC_LBM2]);
+            mnhi = read_min_d(w.scal[SC_UBM2]);
+        }
+        const double f = (double)(k + 1) / (double)M;
+        const double r0lo = sqrt(fmax(mxlo, 0.0)), r0hi = sqrt(mxhi);
+        const double rmlo = sqrt(fmax(mnlo, 0.0)), rmhi = sqrt(fmax(mnhi, 0.0));
+        const double eta = (tier == 1 ? 1e-6 : 1e-13) * r0hi + 1e-300;
+        const double rlo = fmax((1.0 - f) * r0lo + f * rmlo - eta, 0.0);
+        const double rhi = (1.0 - f) * r0hi + f * rmhi + eta;
+        lo = rlo * rlo * (1.0 - 1e-15);
+        hi = rhi * rhi * (1.0 + 1e-15);
     } else if (tier == 1) {
         const double lb = (double)__uint_as_float((unsigned)w.scal[SC_LB1]);
         const double ub = (double)__uint_as_float((unsigned)w.scal[SC_UB1]);
@@ -413,7 +476,7 @@ __global__ void ranges_kernel(CilWork w, const double *__restrict__ radii_in, Be
 
 // 4a. classify: tier 1 decides, or the pair goes to tier 2 (or straight to
 //     tier 3 for the exact path).
-__global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in, int M, int all) {
+__global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in, int M, int all, int law) {
     __shared__ float tlo[32], thi[32];
     if ((int)threadIdx.x < M) {
         tlo[threadIdx.x] = w.t1lo[threadIdx.x];
@@ -424,19 +487,21 @@ __global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in,
     const int64_t np = w.n1 * w.n2;
     if (q >= np) return;
     w.flag[q] = 0;
-    if (all) {   // exact path: every pair to tier 3; all may hold the maximum
+    const bool lin = !radii_in && law == LAW_LINEAR;
+    if (all) {   // exact path: every pair to tier 3; all may hold the maximum (and minimum)
         unsigned long long slot = atomicAdd(&w.scal[SC_Q2], 1ull);
-        w.q2[slot] = (unsigned long long)q | (radii_in ? 0ull : (1ull << 63));
+        w.q2[slot] = (unsigned long long)q | (radii_in ? 0ull : Q_MAX) | (lin ? Q_MIN : 0ull);
         w.arrive[slot] = 0u;
         return;
     }
     const float lo = w.lo32[q], hi = w.hi32[q];
     const bool maxc = !radii_in && hi >= __uint_as_float((unsigned)w.scal[SC_LB1]);
+    const bool minc = lin && lo <= read_min_f(w.scal[SC_UBM1]);
     bool amb = false;
     for (int k = 0; k < M && !amb; ++k) amb = !(hi < tlo[k] || lo >= thi[k]);
-    if (!(maxc || amb)) return;
+    if (!(maxc || minc || amb)) return;
     unsigned long long slot = atomicAdd(&w.scal[SC_Q1], 1ull);
-    w.q1[slot] = (unsigned long long)q | (maxc ? (1ull << 63) : 0ull);
+    w.q1[slot] = (unsigned long long)q | (maxc ? Q_MAX : 0ull) | (minc ? Q_MIN : 0ull);
 }
 
 // 4b. tier 2: d2 = sum (x - y)^2 from FP32 error-free transformations.
@@ -456,7 +521,7 @@ __global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__re
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (unsigned long long qi = blockIdx.x; qi < qlen; qi += gridDim.x) {
         const unsigned long long ent = w.q1[qi];
-        const int64_t q = (int64_t)(ent & ~(1ull << 63));
+        const int64_t q = (int64_t)(ent & Q_IDX);
         const int64_t i = q / w.n2, j = q - i * w.n2;
         const float *x = X1 + i * ld1, *y = X2 + j * ld2;
         float H = 0.f, L = 0.f;
@@ -487,9 +552,13 @@ __global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__re
             w.lo2[q] = lo;
             w.hi2[q] = hi;
             w.flag[q] = 1;
-            if (ent >> 63) {
+            if (ent & Q_MAX) {
                 atomicMax(&w.scal[SC_LB2], (unsigned long long)__double_as_longlong(fmax(lo, 0.0)));
                 atomicMax(&w.scal[SC_UB2], (unsigned long long)__double_as_longlong(fmax(hi, 0.0)));
+            }
+            if (ent & Q_MIN) {
+                atomic_min_d(&w.scal[SC_LBM2], fmax(lo, 0.0));
+                atomic_min_d(&w.scal[SC_UBM2], fmax(hi, 0.0));
             }
         }
         __syncthreads();
@@ -509,14 +578,15 @@ __global__ void classify2_kernel(CilWork w, int M) {
     const unsigned long long qi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= qlen) return;
     const unsigned long long ent = w.q1[qi];
-    const int64_t q = (int64_t)(ent & ~(1ull << 63));
+    const int64_t q = (int64_t)(ent & Q_IDX);
     const double lo = w.lo2[q], hi = w.hi2[q];
-    const bool maxc = (ent >> 63) && hi >= __longlong_as_double((long long)w.scal[SC_LB2]);
+    const bool maxc = (ent & Q_MAX) && hi >= __longlong_as_double((long long)w.scal[SC_LB2]);
+    const bool minc = (ent & Q_MIN) && lo <= read_min_d(w.scal[SC_UBM2]);
     bool amb = false;
     for (int k = 0; k < M && !amb; ++k) amb = !(hi < tlo[k] || lo >= thi[k]);
-    if (!(maxc || amb)) return;
+    if (!(maxc || minc || amb)) return;
     unsigned long long slot = atomicAdd(&w.scal[SC_Q2], 1ull);
-    w.q2[slot] = (unsigned long long)q | (maxc ? (1ull << 63) : 0ull);
+    w.q2[slot] = (unsigned long long)q | (maxc ? Q_MAX : 0ull) | (minc ? Q_MIN : 0ull);
     w.arrive[slot] = 0u;
 }
 
@@ -534,7 +604,7 @@ __global__ void __launch_bounds__(32) canonical_kernel(CilWork w, const float *_
         const unsigned long long slot = it >> 3;
         const int g = (int)(it & 7ull);
         const unsigned long long ent = w.q2[slot];
-        const int64_t q = (int64_t)(ent & ~(1ull << 63));
+        const int64_t q = (int64_t)(ent & Q_IDX);
         const int64_t i = q / w.n2, j = q - i * w.n2;
         const float *x = X1 + i * ld1, *y = X2 + j * ld2;
         double acc = 0.0;
@@ -556,14 +626,16 @@ __global__ void __launch_bounds__(32) canonical_kernel(CilWork w, const float *_
                     for (int k = 0; k < s; ++k) v[k] = __dadd_rn(v[k], v[k + s]);
                 w.ex[q] = v[0];
                 w.flag[q] = 2;
-                if (ent >> 63) atomicMax(&w.scal[SC_MAX], (unsigned long long)__double_as_longlong(v[0]));
+                if (ent & Q_MAX) atomicMax(&w.scal[SC_MAX], (unsigned long long)__double_as_longlong(v[0]));
+                if (ent & Q_MIN) atomic_min_d(&w.scal[SC_MIN], v[0]);
             }
         }
     }
 }
 
-// radii: R0 = sqrt(max), R_k = R_{k-1}/b  (or copy the given radii)
-__global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M,
+// radii: R0 = sqrt(max), R_k = R_{k-1}/b, or the linear law with R_min =
+// sqrt(min): h = (R0 - R_min)/M, R_k = R0 - k h  (or copy the given radii)
+__global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, double b, int M, int law,
                              double *__restrict__ radii_out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (radii_in) {
@@ -573,6 +645,12 @@ __global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, dou
     }
     double R = __dsqrt_rn(__longlong_as_double((long long)w.scal[SC_MAX]));
     radii_out[0] = R;
+    if (law == LAW_LINEAR) {
+        const double Rm = __dsqrt_rn(read_min_d(w.scal[SC_MIN]));
+        const double h = __ddiv_rn(__dsub_rn(R, Rm), (double)M);
+        for (int k = 1; k <= M; ++k) radii_out[k] = __dsub_rn(R, __dmul_rn((double)k, h));
+        return;
+    }
     for (int k = 0; k < M; ++k) {
         R = __ddiv_rn(R, b);
         radii_out[k + 1] = R;
@@ -658,11 +736,11 @@ __global__ void export_approx_kernel(CilWork w, double *__restrict__ A, double *
 // host side
 // ---------------------------------------------------------------------------
 static rd_status check_args(int64_t ld1, int64_t n1, int64_t ld2, int64_t n2, int64_t d,
-                            const double *radii_in, double b, int M) {
+                            const double *radii_in, double b, int M, int law = LAW_POWER) {
     if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535 || d < 1) return RD_ERR_INVALID_ARG;
     if (ld1 < d || ld2 < d) return RD_ERR_INVALID_ARG;
     if (M < 1 || M > 32) return RD_ERR_INVALID_ARG;
-    if (!radii_in && !(b > 1.0)) return RD_ERR_INVALID_ARG;
+    if (!radii_in && law == LAW_POWER && !(b > 1.0)) return RD_ERR_INVALID_ARG;
     return RD_OK;
 }
 
@@ -731,8 +809,8 @@ rd_status cil_tier1_intervals(const float *X1, int64_t ld1, int64_t n1, const fl
 static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *X2, int64_t ld2, int64_t n2,
                          int64_t d, const double *radii_in, double b, int32_t M, double *radii_out,
                          uint8_t *bins, int64_t *counts, double *Cv, int64_t *n_rechecked, void *work,
-                         size_t work_bytes, void *stream, bool exact) {
-    rd_status st = check_args(ld1, n1, ld2, n2, d, radii_in, b, M);
+                         size_t work_bytes, void *stream, bool exact, int law = LAW_POWER) {
+    rd_status st = check_args(ld1, n1, ld2, n2, d, radii_in, b, M, law);
     if (st) return st;
     if (!X1 || !X2 || !radii_out || !bins || !counts || !work) return RD_ERR_INVALID_ARG;
     if (((uintptr_t)work & 255) != 0) return RD_ERR_INVALID_ARG;
@@ -751,21 +829,21 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
     {
         double f = 1.0;
         for (int k = 0; k < M; ++k) {
-            f = f / (b * b);
+            f = law == LAW_POWER ? f / (b * b) : 0.0;
             beta.v[k] = radii_in ? 0.0 : f;
         }
     }
     if (!exact) {
-        ranges_kernel<<<1, 32, 0, s>>>(w, radii_in, beta, M, 1);
+        ranges_kernel<<<1, 32, 0, s>>>(w, radii_in, beta, M, 1, law);
         note_launch();
     }
-    classify1_kernel<<<gp, 256, 0, s>>>(w, radii_in, M, exact ? 1 : 0);
+    classify1_kernel<<<gp, 256, 0, s>>>(w, radii_in, M, exact ? 1 : 0, law);
     note_launch();
     if (!exact) {
         const unsigned g2 = (unsigned)(np < 2 * 148 ? np : 2 * 148);
         tier2_kernel<<<g2, 256, 0, s>>>(w, X1, ld1, X2, ld2);
         note_launch();
-        ranges_kernel<<<1, 32, 0, s>>>(w, radii_in, beta, M, 2);
+        ranges_kernel<<<1, 32, 0, s>>>(w, radii_in, beta, M, 2, law);
         note_launch();
         classify2_kernel<<<gp, 256, 0, s>>>(w, M);
         note_launch();
@@ -776,7 +854,7 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
         canonical_kernel<<<g3, 32, 0, s>>>(w, X1, ld1, X2, ld2);
         note_launch();
     }
-    radii_kernel<<<1, 32, 0, s>>>(w, radii_in, b, M, radii_out);
+    radii_kernel<<<1, 32, 0, s>>>(w, radii_in, b, M, law, radii_out);
     note_launch();
     bins_counts_kernel<<<gp, 256, 0, s>>>(w, radii_out, M, bins, (unsigned long long *)counts);
     note_launch();
@@ -826,6 +904,14 @@ extern "C" rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1, co
                                   int64_t *d_n_rechecked, void *d_work, size_t work_bytes, void *stream) {
     return cil_run(d_X1, ld1, n1, d_X2, ld2, n2, d, d_radii_in, b, M, d_radii_out, d_bins, d_counts, d_C,
                    d_n_rechecked, d_work, work_bytes, stream, false);
+}
+
+extern "C" rd_status cil_features_linear(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                         int64_t ld2, int64_t n2, int64_t d, int32_t M, double *d_radii_out,
+                                         uint8_t *d_bins, int64_t *d_counts, double *d_C, int64_t *d_n_rechecked,
+                                         void *d_work, size_t work_bytes, void *stream) {
+    return cil_run(d_X1, ld1, n1, d_X2, ld2, n2, d, nullptr, 0.0, M, d_radii_out, d_bins, d_counts, d_C,
+                   d_n_rechecked, d_work, work_bytes, stream, false, LAW_LINEAR);
 }
 
 extern "C" rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
