@@ -619,6 +619,21 @@ def rdode_c7(p, torch, dev, stream):
     t = min(ts[1:])
     st = st.cpu().numpy()
     n, N = gd["n_real"], gd["G"]
+    # the rest of a likelihood evaluation on these patterns (both species,
+    # d = 2N): CIL with Table 1's linear radii law, M = 13, and the
+    # synthetic-likelihood statistics of 200 resampled set pairs
+    X = sim.group_fields(0).reshape(n, 2 * N)
+    half = n // 2
+    tl = []
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c = p.cil_linear(X[:half], X[half:], M=cfg["M"])
+        sl = p.synlik(c["bins"], cfg["M"], cfg["T_res"], cfg["seed"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tl.append(e0.elapsed_time(e1) * 1e-3)
+    t_lik = min(tl[1:])
     sample = 8
     w0 = oracle.rdode_init(N, sample, gd["noise"][0], gd["noise"][1], gd["seed"], 10)
     T = gd["dt"] * gd["n_steps"]
@@ -626,6 +641,7 @@ def rdode_c7(p, torch, dev, stream):
     _, ost, failed = oracle.rkc_adaptive(W.RDODE, gd["params"], T, 1e-3, tol, tol, w0)
     t_orc = time.perf_counter() - t0
     return {"workload": "RD-ODE 64 nodes, 200 realisations, t in [0, 50], tol %g" % tol, "ms": t * 1e3,
+            "cil_linear_synlik_ms": t_lik * 1e3, "counts": c["counts"].cpu().numpy().tolist(),
             "realisations_per_s": n / t, "steps_mean": float(st[:, 0].mean()), "rhs_mean": float(st[:, 2].mean()),
             "cell_stage_updates_per_s": float(st[:, 2].sum()) * 2 * N / t,
             "oracle_sample": {"realisations": sample, "s": t_orc, "realisations_per_s": sample / t_orc,
