@@ -586,13 +586,63 @@ def rkc_bench(p, torch, dev, stream, pk, src, tols=(1e-5, 1e-6, 1e-7)):
                      "alu_tinst_per_s": inst / t / 1e12, "alu_frac": inst / t / 1e12 / peak_alu,
                      "speedup_vs_euler": t_eul / t, "as_accurate_as_euler": err <= err_eul})
     rdode = rdode_c7(p, torch, dev, stream)
+    c3 = rkc_c3(p, torch, dev, stream)
     return {"workload": "FHN 64x64, 2 x 64 realisations, 0 -> T = 10^4 x 2^-10 (the c2 horizon)",
             "rdode_c7": rdode,
+            "gm128_c3": c3,
             "fixed_schedule": fixed,
             "euler": {"ms": t_eul * 1e3, "steps": gd["n_steps"], "rel_err_sample": err_eul},
             "reference": "oracle adaptive, tolerance 1e-9, realisations 0 and 1",
             "peak_note": "alu peak = 148 SM x 128 FP32 lanes x max SM clock (%s peaks file); "
                          "%d FP32 instructions per cell per RHS stage" % (src, RKC_FP32_INST_PER_CELL_STAGE[gd["model"]]),
+            "tolerances": rows}
+
+
+def rkc_c3(p, torch, dev, stream, tols=(1e-5, 1e-6)):
+    """The GM 128x128 workload c3 (2 x 256 realisations, to T = 2*10^4 x
+    2^-10): Euler against the adaptive stabilised RK2 (one 4-CTA cluster
+    per realisation), accuracy of two realisations against an accurate
+    oracle reference (adaptive, tolerance 1e-9)."""
+    import oracle
+    cfg = W.config("c3")
+    gd = cfg["groups"][0]
+    T = gd["dt"] * gd["n_steps"]
+    sim = p.Simulation([p.Group.from_dict(gd)], device=dev)
+    w0 = sim.group_fields(0)[:2].cpu().numpy()
+    ref, _, failed = oracle.rkc_adaptive(gd["model"], gd["params"], T, 1e-3, 1e-9, 1e-9, w0)
+    assert failed == 0
+
+    def rel(a):
+        a = np.asarray(a, np.float64)
+        num = np.abs(a - ref).reshape(2, 2, -1).max(-1)
+        return float((num / np.abs(ref).reshape(2, 2, -1).max(-1)).max())
+
+    def timed(fn, reps=2):
+        ts = []
+        for _ in range(reps + 1):
+            sim.reinit()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return min(ts[1:]), r
+
+    t_eul, _ = timed(lambda: sim.integrate(residual=False))
+    assert sim.sync_status() == 0
+    err_eul = rel(sim.group_fields(0)[:2].cpu().numpy())
+    rows = []
+    for tol in tols:
+        t, (st, _) = timed(lambda: sim.integrate_rkc(1e-3, rtol=tol, atol=tol))
+        assert sim.sync_status() == 0
+        st = st.cpu().numpy()
+        rows.append({"tol": tol, "ms": t * 1e3, "steps_mean": float(st[:, 0].mean()),
+                     "rhs_mean": float(st[:, 2].mean()), "rel_err_sample": rel(sim.group_fields(0)[:2].cpu().numpy()),
+                     "cell_stage_updates_per_s": float(st[:, 2].sum()) * gd["G"] ** 2 / t,
+                     "speedup_vs_euler": t_eul / t})
+    return {"workload": "GM 128x128, 2 x 256 realisations, 0 -> T = 2*10^4 x 2^-10 (c3)",
+            "euler": {"ms": t_eul * 1e3, "steps": gd["n_steps"], "rel_err_sample": err_eul},
             "tolerances": rows}
 
 

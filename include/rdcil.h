@@ -229,8 +229,10 @@ rd_status rd_integrate_f64(rd_handle *h, double *d_fields64, double *d_tmp64,
  *           after two consecutive accepted steps, 0.8 err^(-1/3) otherwise,
  *           err floored at 1e-10, fac in [0.1, 10] and <= 1 right after a
  *           rejection; the last step ends exactly at t_end.
- * FP32 state, FP64 control.  Groups must have G = 32 or 64
- * (RD_ERR_UNSUPPORTED otherwise; nothing is launched).
+ * FP32 state, FP64 control.  Groups must have G = 32, 64 or 128 (or be
+ * RD_RDODE groups; RD_ERR_UNSUPPORTED otherwise, nothing is launched):
+ * one CTA per realisation for G <= 64, one cluster of 4 CTAs for G = 128
+ * (distributed shared memory for the rows between them).
  */
 #define RD_RKC_S_MAX 256
 

@@ -64,6 +64,11 @@ FIXED = [
     (W.BZ, 64, 3, W.BZ_THETA0, (0.0, 0.01), 0.05, 80),
     (W.BZ, 32, 2, (1.6e-3, 1.32e-2, 4.4, 7.1), (0.0, 0.01), 0.05, 60),
     (W.DIFF, 64, 2, (3e-3, 1e-3), (-1.0, 1.0), 0.02, 40),
+    # G = 128: one realisation per 4-CTA cluster
+    (W.FHN, 128, 2, (2.8e-4, 0.05, 10.0, 0.97), (-0.05, 0.05), 0.05, 20),
+    (W.GM, 128, 3, (2.5e-4, 0.01, 1.0, 0.48), (0.0, 0.01), 0.5, 20),
+    (W.BZ, 128, 2, W.BZ_THETA0, (0.0, 0.01), 0.02, 20),
+    (W.DIFF, 128, 2, (3e-3, 1e-3), (-1.0, 1.0), 0.01, 10),
 ]
 
 
@@ -170,6 +175,8 @@ def test_forced_rejection_matches(p):
     (W.GM, 64, (2.5e-4, 0.01, 1.0, 0.52), (0.0, 0.01), 40.0, 1e-6),
     (W.BZ, 64, W.BZ_THETA0, (0.0, 0.01), 10.0, 1e-7),
     (W.FHN, 32, (2.8e-4, 0.05, 10.0, 0.95), (-0.05, 0.05), 2000 * 2 ** -8, 1e-6),
+    (W.GM, 128, (2.5e-4, 0.01, 1.0, 0.48), (0.0, 0.01), 10.0, 1e-5),
+    (W.FHN, 128, (2.8e-4, 0.05, 10.0, 0.97), (-0.05, 0.05), 2.0, 1e-6),
 ])
 def test_adaptive_run_against_oracle(p, model, G, par, noise, T, tol):
     n = 2
@@ -247,7 +254,7 @@ def test_argument_checks(p):
         with pytest.raises(p.RdError) as e:
             sim.integrate_rkc(**kw)
         assert e.value.status == 1
-    big = p.Simulation([p.Group(W.FHN, 128, 1, W.FHN_THETA0, 2 ** -12, 1, (-0.05, 0.05), 1)])
+    big = p.Simulation([p.Group(W.FHN, 256, 1, W.FHN_THETA0, 2 ** -12, 1, (-0.05, 0.05), 1)])
     with pytest.raises(p.RdError) as e:
         big.integrate_rkc(1e-3)
     assert e.value.status == 6
