@@ -499,12 +499,24 @@ class Pipeline:
     every output buffer allocated once, so that a pass can be captured in a
     CUDA graph and replayed.  sets[i] = (n1, n2, species_mask) of group i:
     set 1 = realisations 0..n1-1, set 2 = n1..n1+n2-1.  The cost is
-    evaluated at each group's own correlation vector (y_obs = C)."""
+    evaluated at each group's own correlation vector (y_obs = C).
+    integrator: "euler" (rd_integrate_batch, each group's n_steps) or "rkc"
+    (rd_integrate_rkc to each group's dt * n_steps; `rkc` = dict of h0,
+    rtol, atol, s_max, max_attempts); law: "power" (R0 b^-k) or "linear"
+    (R0 - k (R0 - R_min) / M, b unused).  RDODE groups need "rkc"."""
 
-    def __init__(self, groups, sets, M, b, T, seed, device=None):
+    def __init__(self, groups, sets, M, b, T, seed, device=None, integrator="euler", rkc=None, law="power"):
+        if integrator not in ("euler", "rkc") or law not in ("power", "linear"):
+            raise ValueError("integrator / law")
         self.sim = Simulation(groups, device=device)
         self.dev = self.sim.device
         self.M, self.b, self.T, self.seed = M, b, T, seed
+        self.integrator, self.law = integrator, law
+        r = dict(h0=1e-3, rtol=1e-5, atol=1e-5, s_max=RKC_S_MAX, max_attempts=100000)
+        r.update(rkc or {})
+        self.rkc_opts = RdRkcOpts(0.0, float(r["h0"]), float(r["rtol"]), float(r["atol"]), int(r["s_max"]), 0, 0,
+                                  int(r["max_attempts"]))
+        self.rkc_stats = torch.empty((self.sim.n_real_total, 4), dtype=torch.int64, device=self.dev)
         self.views = []
         n1s = set(s[0] for s in sets)
         n2s = set(s[1] for s in sets)
@@ -513,10 +525,10 @@ class Pipeline:
         self.n1, self.n2 = n1s.pop(), n2s.pop()
         P = len(groups)
         for i, (g, (n1, n2, mask)) in enumerate(zip(groups, sets)):
-            G = g.G
-            fv = self.sim.group_fields(i).reshape(g.n_real, 2 * G * G)
-            off = 0 if mask in (1, 3) else G * G
-            d = G * G * (2 if mask == 3 else 1)
+            cells = g.cells
+            fv = self.sim.group_fields(i).reshape(g.n_real, 2 * cells)
+            off = 0 if mask in (1, 3) else cells
+            d = cells * (2 if mask == 3 else 1)
             self.views.append((fv[:n1, off:off + d], fv[n1:n1 + n2, off:off + d]))
         self.bins = torch.empty((P, self.n1, self.n2), dtype=torch.uint8, device=self.dev)
         self.C = torch.empty((P, M), dtype=torch.float64, device=self.dev)
@@ -533,10 +545,16 @@ class Pipeline:
     def run(self, reinit=True):
         if reinit:
             self.sim.reinit()
-        _check("rd_integrate_batch", lib().rd_integrate_batch(
-            self.sim.handle, _ptr(self.sim.fields), -1, _ptr(self.residual), _stream()))
+        if self.integrator == "euler":
+            _check("rd_integrate_batch", lib().rd_integrate_batch(
+                self.sim.handle, _ptr(self.sim.fields), -1, _ptr(self.residual), _stream()))
+        else:
+            _check("rd_integrate_rkc", lib().rd_integrate_rkc(
+                self.sim.handle, _ptr(self.sim.fields), C.byref(self.rkc_opts), _ptr(self.rkc_stats),
+                _ptr(self.residual), _stream()))
+        fn = "cil_features_linear" if self.law == "linear" else "cil_features"
         for (X1, X2), out in zip(self.views, self.cil_out):
-            _cil_call("cil_features", X1, X2, self.b, self.M, None, self.work, out)
+            _cil_call(fn, X1, X2, self.b, self.M, None, self.work, out)
         synlik(self.bins, self.M, self.T, self.seed, y_obs=self.C, out=self.stats)
 
     def capture(self):

@@ -73,3 +73,33 @@ def test_pipeline_eager_graph_and_separate_calls_agree(p):
         o = oracle.cil(X[:16], X[16:32], b=1.3, M=8)
         assert np.array_equal(eager["bins"][i].cpu().numpy(), o["bins"])
         assert np.array_equal(eager["counts%d" % i].cpu().numpy(), o["counts"])
+
+
+def test_rdode_pipeline_with_rkc_and_linear_law(p):
+    # the RD-ODE likelihood pass of Table 1 (64 nodes, t in [0, 50], linear
+    # radii, M = 13) plus a 2-D group on the adaptive integrator: eager and
+    # graph replay bit-identical, counts equal the oracle's on the same fields
+    gds = [W.group(W.RDODE, 64, 40, W.RDODE_THETA0, 50.0 / 1024, 1024, (0.0, 2.0), 601, 3),
+           W.group(W.FHN, 32, 40, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -8, 512, (-0.05, 0.05), 602, 1)]
+    groups = [p.Group.from_dict(g) for g in gds]
+    sets = [(20, 20, g["species_mask"]) for g in gds]
+    pipe = p.Pipeline(groups, sets, M=13, b=None, T=50, seed=78, integrator="rkc",
+                      rkc=dict(rtol=1e-5, atol=1e-5), law="linear")
+    pipe.run()
+    torch.cuda.synchronize()
+    eager = snapshot(pipe)
+    st = pipe.rkc_stats.cpu().numpy()
+    assert (st[:, 0] > 0).all()
+    pipe.capture()
+    pipe.replay()
+    torch.cuda.synchronize()
+    rep = snapshot(pipe)
+    for k in eager:
+        a, b = eager[k], rep[k]
+        if a.dtype == torch.float64:        # bit patterns (a non-PD group's scalars are NaN)
+            a, b = a.view(torch.int64), b.view(torch.int64)
+        assert torch.equal(a, b), k
+    for i, (X1, X2) in enumerate(pipe.views):
+        o = oracle.cil(X1.cpu().numpy(), X2.cpu().numpy(), M=13, law="linear")
+        assert np.array_equal(pipe.cil_out[i]["counts"].cpu().numpy(), o["counts"])
+        assert np.array_equal(pipe.bins[i].cpu().numpy(), o["bins"])
