@@ -587,9 +587,22 @@ def rkc_bench(p, torch, dev, stream, pk, src, tols=(1e-5, 1e-6, 1e-7)):
                      "speedup_vs_euler": t_eul / t, "as_accurate_as_euler": err <= err_eul})
     rdode = rdode_c7(p, torch, dev, stream)
     c3 = rkc_c3(p, torch, dev, stream)
+    # the FP64 oracle's adaptive run of a sample of c2 realisations on the
+    # host, at the middle tolerance
+    n_s, tol_s = 4, 1e-6
+    w0s = oracle.init_fields(gd["model"], G, n_s, gd["params"], gd["noise"][0], gd["noise"][1], gd["seed"])
+    t0 = time.perf_counter()
+    _, _, failed = oracle.rkc_adaptive(gd["model"], gd["params"], T, 1e-3, tol_s, tol_s, w0s)
+    t_o = time.perf_counter() - t0
+    assert failed == 0
+    row_s = [r for r in rows if r["tol"] == tol_s][0]
+    cpu = {"kind": "oracle", "sample": "%d realisations of c2 to T at tol %g" % (n_s, tol_s), "s": t_o,
+           "cores": oracle.threads(), "realisations_per_s": n_s / t_o,
+           "gpu_realisations_per_s": n / (row_s["ms"] * 1e-3)}
     return {"workload": "FHN 64x64, 2 x 64 realisations, 0 -> T = 10^4 x 2^-10 (the c2 horizon)",
             "rdode_c7": rdode,
             "gm128_c3": c3,
+            "cpu_baseline": cpu,
             "fixed_schedule": fixed,
             "euler": {"ms": t_eul * 1e3, "steps": gd["n_steps"], "rel_err_sample": err_eul},
             "reference": "oracle adaptive, tolerance 1e-9, realisations 0 and 1",
