@@ -777,6 +777,18 @@ def adjoint_c5(p, torch, dev, stream):
 # ---------------------------------------------------------------------------
 # oracle (CPU) arm / baseline
 # ---------------------------------------------------------------------------
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def oracle_sample(cfg, n_steps_sample):
     """Time the oracle on a bounded sample: all realisations for
     n_steps_sample Euler steps (scaled to the full step count), plus the full
@@ -897,8 +909,15 @@ def main():
         cfg = W.config(args.config)
         v, secs, note = oracle_sample(cfg, cfg["groups"][0]["n_steps"])
         import oracle
-        out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": oracle.threads(),
-                               "kind": "oracle", "sample": note + " (%.1f s of CPU work)" % secs}
+        cores = oracle.threads()
+        # one thread, on a sixteenth of the steps (stepping time scaled)
+        oracle.set_threads(1)
+        v1, secs1, note1 = oracle_sample(cfg, max(1, cfg["groups"][0]["n_steps"] // 16))
+        oracle.set_threads(cores)
+        out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": cores,
+                               "kind": "oracle", "sample": note + " (%.1f s of CPU work)" % secs,
+                               "one_thread": {"value": v1, "sample": note1 + " (%.1f s)" % secs1},
+                               "cpu_model": cpu_model()}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -25,6 +25,11 @@ def threads():
     return int(lib().orc_threads())
 
 
+def set_threads(n):
+    """Use n OpenMP threads in the oracle's parallel loops."""
+    lib().orc_set_threads(int(n))
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -34,6 +39,7 @@ def lib():
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_uint8))
         L.orc_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_rdode_init.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_int, fp]
         L.orc_rdode_rhs.argtypes = [C.c_int, dp, dp, dp]
         L.orc_rdode_gershgorin.argtypes = [C.c_int, dp, dp]

@@ -53,6 +53,16 @@ int orc_threads(void) {
 #endif
 }
 
+/* Set the number of OpenMP threads of the oracle's parallel loops (for
+   timing at a given thread count; no effect without OpenMP). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 #define ORC_FHN 0
 #define ORC_GM 1
 #define ORC_DIFF 2
