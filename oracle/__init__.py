@@ -55,13 +55,13 @@ def lib():
         L.orc_rkc_adaptive.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_double,
                                        C.c_double, C.c_double, C.c_int, C.c_int64, dp, i64p]
         L.orc_rkc_adaptive.restype = C.c_int
-        L.orc_minmax.argtypes = [fp, C.c_int64, C.c_int, C.c_int, fp]
-        L.orc_fd.argtypes = [fp, C.c_int64, C.c_int, C.c_int, fp, fp]
+        L.orc_minmax.argtypes = [fp, C.c_int64, C.c_int64, C.c_int, fp]
+        L.orc_fd.argtypes = [fp, C.c_int64, C.c_int, C.c_int, C.c_int, fp, fp]
         L.orc_maxabs.argtypes = [fp, fp, C.c_int64]
         L.orc_maxabs.restype = C.c_double
         L.orc_d2_canon.argtypes = [fp, fp, C.c_int64]
         L.orc_d2_canon.restype = C.c_double
-        L.orc_mcil_values.argtypes = [fp, fp, fp, C.c_int64, fp, fp, fp, C.c_int64, C.c_int, C.c_int,
+        L.orc_mcil_values.argtypes = [fp, fp, fp, C.c_int64, fp, fp, fp, C.c_int64, C.c_int, C.c_int, C.c_int,
                                       C.c_int, dp]
         L.orc_mcil_bins.argtypes = [dp, C.c_int64, C.c_int, C.c_double, C.c_int, dp, u8p, i64p]
         L.orc_mcil_squared.argtypes = [C.c_int]
@@ -369,22 +369,26 @@ def _f32(a):
     return np.ascontiguousarray(a, np.float32)
 
 
-def minmax(X, G, nsp):
-    """Min-max scaled copy of patterns X [n, nsp*G*G] (per species)."""
+def minmax(X, G, nsp, Gy=None):
+    """Min-max scaled copy of patterns X [n, nsp*Gy*G] (per species; Gy = G
+    by default, 1 for 1-D patterns)."""
+    Gy = G if Gy is None else Gy
     X = _f32(X)
     out = np.empty_like(X)
-    lib().orc_minmax(_p(X, C.c_float), X.shape[0], G, nsp, _p(out, C.c_float))
+    lib().orc_minmax(_p(X, C.c_float), X.shape[0], Gy * G, nsp, _p(out, C.c_float))
     return out
 
 
-def fd(X, G, nsp):
-    """Forward-difference patterns (Ax, Ay), each [n, nsp*G*(G-1)] float32."""
+def fd(X, G, nsp, Gy=None):
+    """Forward-difference patterns (Ax [n, nsp*Gy*(G-1)], Ay [n,
+    nsp*(Gy-1)*G]) float32 of Gy x G fields (Gy = G by default)."""
+    Gy = G if Gy is None else Gy
     X = _f32(X)
     n = X.shape[0]
-    Ax = np.empty((n, nsp * G * (G - 1)), np.float32)
-    Ay = np.empty((n, nsp * G * (G - 1)), np.float32)
-    lib().orc_fd(_p(X, C.c_float), n, G, nsp, _p(Ax, C.c_float), _p(Ay, C.c_float))
-    return Ax, Ay
+    Ax = np.empty((n, nsp * Gy * (G - 1)), np.float32)
+    Ay = np.empty((n, max(nsp * (Gy - 1) * G, 1)), np.float32)
+    lib().orc_fd(_p(X, C.c_float), n, Gy, G, nsp, _p(Ax, C.c_float), _p(Ay, C.c_float))
+    return Ax, Ay[:, :nsp * (Gy - 1) * G]
 
 
 def maxabs(x, y):
@@ -397,27 +401,32 @@ def d2_canon(x, y):
     return lib().orc_d2_canon(_p(x, C.c_float), _p(y, C.c_float), x.size)
 
 
-def mcil_values(X1, X2, G, nsp, mask=63):
+def mcil_values(X1, X2, G, nsp, mask=63, Gy=None):
     """Feature values V[6, n1, n2] of every cross-set pair (NaN where the
-    feature is not in mask): squared for L2 and W12, plain otherwise."""
+    feature is not in mask): squared for L2 and W12, plain otherwise.
+    Fields Gy x G (Gy = G by default, 1 for 1-D patterns)."""
+    Gy = G if Gy is None else Gy
     X1, X2 = _f32(X1), _f32(X2)
-    Ax1, Ay1 = fd(X1, G, nsp)
-    Ax2, Ay2 = fd(X2, G, nsp)
+    Ax1, Ay1 = fd(X1, G, nsp, Gy)
+    Ax2, Ay2 = fd(X2, G, nsp, Gy)
+    Ay1 = Ay1 if Ay1.size else np.zeros((X1.shape[0], 1), np.float32)
+    Ay2 = Ay2 if Ay2.size else np.zeros((X2.shape[0], 1), np.float32)
     n1, n2 = X1.shape[0], X2.shape[0]
     V = np.full((6, n1, n2), np.nan)
     lib().orc_mcil_values(_p(X1, C.c_float), _p(Ax1, C.c_float), _p(Ay1, C.c_float), n1,
                           _p(X2, C.c_float), _p(Ax2, C.c_float), _p(Ay2, C.c_float), n2,
-                          G, nsp, int(mask), _p(V, C.c_double))
+                          Gy, G, nsp, int(mask), _p(V, C.c_double))
     return V
 
 
-def mcil(X1, X2, G, nsp, b, M, mask=63, scale=False):
+def mcil(X1, X2, G, nsp, b, M, mask=63, scale=False, Gy=None):
     """Multi-feature correlation integral (Alg. 2 step 2.2): per feature in
     mask (ascending), radii [K, M+1] (R0 first), bins [K, n1, n2], counts
-    [K, M]; C = the concatenated vector (K*M) of eq. (CIL)."""
+    [K, M]; C = the concatenated vector (K*M) of eq. (CIL).  Fields Gy x G
+    (Gy = G by default, 1 for 1-D patterns)."""
     if scale:
-        X1, X2 = minmax(X1, G, nsp), minmax(X2, G, nsp)
-    V = mcil_values(X1, X2, G, nsp, mask)
+        X1, X2 = minmax(X1, G, nsp, Gy), minmax(X2, G, nsp, Gy)
+    V = mcil_values(X1, X2, G, nsp, mask, Gy)
     feats = [f for f in range(6) if mask & (1 << f)]
     n1, n2 = V.shape[1], V.shape[2]
     K = len(feats)

@@ -16,11 +16,14 @@
  * (s - min) / (max - min).
  *
  * Readings of points the paper leaves open:
- *   - a pattern is n_species fields of G x G nodes, h = 1/(G-1);
+ *   - a pattern is n_species fields of Gy x Gx nodes (Gy = Gx = G for the
+ *     2-D models, Gy = 1 for the 1-D reaction-diffusion-ODE model),
+ *     h = 1/(Gx-1);
  *   - derivatives are forward differences of each species field,
- *     Dx s = s[y][x+1] - s[y][x] (G x (G-1) values) and
- *     Dy s = s[y+1][x] - s[y][x] ((G-1) x G values), each rounded to FP32
- *     once (the derivative patterns are FP32 arrays like the patterns);
+ *     Dx s = s[y][x+1] - s[y][x] (Gy x (Gx-1) values) and
+ *     Dy s = s[y+1][x] - s[y][x] ((Gy-1) x Gx values, none in 1-D), each
+ *     rounded to FP32 once (the derivative patterns are FP32 arrays like
+ *     the patterns);
  *   - the derivative of the difference is the difference of the derivative
  *     patterns; discrete norms weight the node sum by h^2 (2-D), so
  *     ||u||_2,h = h ||u||_2, ||Dx u||_2,h = ||Dx s_i - Dx s_j||_2 (the h
@@ -45,7 +48,11 @@
  *     A "squared" feature is decided like the CIL (R0 = sqrt(max),
  *     d^2 < R_k * R_k); a "value" feature directly (R0 = max, F < R_k);
  *   - min-max scaling: out = fl32(((double)s - min) / (max - min)) in FP64,
- *     0 where max == min.
+ *     0 where max == min;
+ *   - in 1-D (Gy = 1) qy = my = 0, and the same expressions are the 1-D
+ *     discrete norms up to a constant factor per feature (W12^2 times h,
+ *     W12' times sqrt(h)), which leaves the radii's ratios and so the bins
+ *     unchanged.
  */
 #include <stdint.h>
 #include <math.h>
@@ -58,10 +65,9 @@ int orc_mcil_squared(int feature)
     return feature == 0 || feature == 2;
 }
 
-/* Min-max scaling of n patterns of n_species G x G fields. */
-void orc_minmax(const float *X, int64_t n, int G, int nsp, float *out)
+/* Min-max scaling of n patterns of n_species fields of `cells` nodes. */
+void orc_minmax(const float *X, int64_t n, int64_t cells, int nsp, float *out)
 {
-    const int64_t cells = (int64_t)G * G;
     for (int64_t i = 0; i < n; ++i)
         for (int s = 0; s < nsp; ++s) {
             const float *x = X + (i * nsp + s) * cells;
@@ -83,25 +89,26 @@ void orc_minmax(const float *X, int64_t n, int G, int nsp, float *out)
         }
 }
 
-/* Forward-difference patterns: Ax[i][s][y][x] = X[i][s][y][x+1] - X[i][s][y][x]
-   (x < G-1), Ay[i][s][y][x] = X[i][s][y+1][x] - X[i][s][y][x] (y < G-1),
-   each the exact difference rounded once to FP32. */
-void orc_fd(const float *X, int64_t n, int G, int nsp, float *Ax, float *Ay)
+/* Forward-difference patterns of Gy x Gx fields: Ax[i][s][y][x] =
+   X[i][s][y][x+1] - X[i][s][y][x] (x < Gx-1), Ay[i][s][y][x] =
+   X[i][s][y+1][x] - X[i][s][y][x] (y < Gy-1), each the exact difference
+   rounded once to FP32. */
+void orc_fd(const float *X, int64_t n, int Gy, int Gx, int nsp, float *Ax, float *Ay)
 {
-    const int64_t cells = (int64_t)G * G, ce = (int64_t)G * (G - 1);
+    const int64_t cells = (int64_t)Gy * Gx, cex = (int64_t)Gy * (Gx - 1), cey = (int64_t)(Gy - 1) * Gx;
     for (int64_t i = 0; i < n; ++i)
         for (int s = 0; s < nsp; ++s) {
             const float *x = X + (i * nsp + s) * cells;
-            float *ax = Ax + (i * nsp + s) * ce;
-            float *ay = Ay + (i * nsp + s) * ce;
-            for (int y = 0; y < G; ++y)
-                for (int c = 0; c + 1 < G; ++c)
-                    ax[(int64_t)y * (G - 1) + c] = (float)((double)x[(int64_t)y * G + c + 1] -
-                                                           (double)x[(int64_t)y * G + c]);
-            for (int y = 0; y + 1 < G; ++y)
-                for (int c = 0; c < G; ++c)
-                    ay[(int64_t)y * G + c] = (float)((double)x[(int64_t)(y + 1) * G + c] -
-                                                     (double)x[(int64_t)y * G + c]);
+            float *ax = Ax + (i * nsp + s) * cex;
+            float *ay = Ay + (i * nsp + s) * cey;
+            for (int y = 0; y < Gy; ++y)
+                for (int c = 0; c + 1 < Gx; ++c)
+                    ax[(int64_t)y * (Gx - 1) + c] = (float)((double)x[(int64_t)y * Gx + c + 1] -
+                                                            (double)x[(int64_t)y * Gx + c]);
+            for (int y = 0; y + 1 < Gy; ++y)
+                for (int c = 0; c < Gx; ++c)
+                    ay[(int64_t)y * Gx + c] = (float)((double)x[(int64_t)(y + 1) * Gx + c] -
+                                                      (double)x[(int64_t)y * Gx + c]);
         }
 }
 
@@ -118,14 +125,15 @@ double orc_maxabs(const float *x, const float *y, int64_t d)
 }
 
 /* The six feature values of every cross-set pair (features not in `mask`
-   are left untouched).  X1, X2: patterns [n][nsp][G][G]; A*1, A*2 their
+   are left untouched).  X1, X2: patterns [n][nsp][Gy][Gx]; A*1, A*2 their
    forward-difference patterns (orc_fd).  V[(f * n1 + i) * n2 + j]. */
 void orc_mcil_values(const float *X1, const float *Ax1, const float *Ay1, int64_t n1,
                      const float *X2, const float *Ax2, const float *Ay2, int64_t n2,
-                     int G, int nsp, int mask, double *V)
+                     int Gy, int Gx, int nsp, int mask, double *V)
 {
-    const int64_t d0 = (int64_t)nsp * G * G, de = (int64_t)nsp * G * (G - 1);
-    const double g = (double)(G - 1);
+    const int64_t d0 = (int64_t)nsp * Gy * Gx;
+    const int64_t dex = (int64_t)nsp * Gy * (Gx - 1), dey = (int64_t)nsp * (Gy - 1) * Gx;
+    const double g = (double)(Gx - 1);
     const double h = 1.0 / g;
     const double h2 = 1.0 / (g * g);
     const int64_t np = n1 * n2;
@@ -137,13 +145,13 @@ void orc_mcil_values(const float *X1, const float *Ax1, const float *Ay1, int64_
             double q0 = 0, qx = 0, qy = 0, m0 = 0, mx = 0, my = 0;
             if (mask & 0x0D) q0 = orc_d2_canon(x, y, d0);
             if (mask & 0x0C) {
-                qx = orc_d2_canon(Ax1 + i * de, Ax2 + j * de, de);
-                qy = orc_d2_canon(Ay1 + i * de, Ay2 + j * de, de);
+                qx = orc_d2_canon(Ax1 + i * dex, Ax2 + j * dex, dex);
+                qy = orc_d2_canon(Ay1 + i * dey, Ay2 + j * dey, dey);
             }
             if (mask & 0x32) m0 = orc_maxabs(x, y, d0);
             if (mask & 0x30) {
-                mx = orc_maxabs(Ax1 + i * de, Ax2 + j * de, de);
-                my = orc_maxabs(Ay1 + i * de, Ay2 + j * de, de);
+                mx = orc_maxabs(Ax1 + i * dex, Ax2 + j * dex, dex);
+                my = orc_maxabs(Ay1 + i * dey, Ay2 + j * dey, dey);
             }
             if (mask & 0x01) V[0 * np + q] = q0;
             if (mask & 0x02) V[1 * np + q] = m0;

@@ -160,3 +160,20 @@ def test_synlik_multi_shares_resamples():
     s1 = oracle.synlik(m["bins"][1], 6, 40, 99)
     assert np.array_equal(s["Y"], np.concatenate([s0["Y"], s1["Y"]], axis=1))
     assert s["mu"].shape == (12,)
+
+
+def test_one_dimensional_features_by_hand():
+    # 1-D patterns (Gy = 1) of Gx = 3 nodes, h = 1/2, g = 2:  x = (0, 1, 3),
+    # y = (1, 1, 1), u = x - y = (-1, 0, 2), Dx u = (1, 2):
+    #   q0 = 1 + 0 + 4 = 5, qx = 1 + 4 = 5, m0 = 2, mx = 2, no y terms;
+    #   L2^2 = 5, Linf = 2, W12^2 = h^2 q0 + qx = 6.25,
+    #   W12' = h sqrt(q0) + sqrt(qx) = 1.5 sqrt(5), W1inf = max(2, 2*2) = 4,
+    #   W1inf' = 2 + 2*2 = 6
+    X1 = np.array([[0.0, 1.0, 3.0]], np.float32)
+    X2 = np.array([[1.0, 1.0, 1.0]], np.float32)
+    V = oracle.mcil_values(X1, X2, 3, 1, 63, Gy=1)[:, 0, 0]
+    assert V[0] == 5.0 and V[1] == 2.0 and V[2] == 6.25
+    assert V[3] == pytest.approx(1.5 * np.sqrt(5.0), rel=1e-15)
+    assert V[4] == 4.0 and V[5] == 6.0
+    Ax, Ay = oracle.fd(X1, 3, 1, Gy=1)
+    assert Ax.tolist() == [[1.0, 2.0]] and Ay.shape == (1, 0)
