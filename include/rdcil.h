@@ -530,6 +530,23 @@ rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, const float 
                         int64_t *d_counts, double *d_C, int64_t *d_n_exact, void *d_work,
                         size_t work_bytes, void *stream);
 
+/* mcil_workspace_size_rect / mcil_features_rect — the same on fields of Gy
+ * x Gx nodes per species (a pattern is n_species * Gy * Gx floats;
+ * 1 <= Gy <= 4096, 2 <= Gx <= 4096), h = 1/(Gx-1), g = Gx-1.  Gy = 1 gives
+ * the 1-D patterns of the reaction-diffusion-ODE model (Sec. 4.3): no y
+ * differences, so qy = my = 0 and the features are the 1-D discrete norms
+ * up to a constant factor per feature (which leaves the bins unchanged).
+ * Sec. 5.2 takes the derivative-based norms of that model on w alone: call
+ * once with both species for L2 and Linf and once with the w rows for the
+ * W features.  mcil_features(G) = mcil_features_rect(Gy = Gx = G). */
+rd_status mcil_workspace_size_rect(int64_t n1, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
+                                   int32_t features, int32_t scale, int32_t M, size_t *bytes);
+rd_status mcil_features_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                             int64_t ld2, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
+                             int32_t features, int32_t scale, double b, int32_t M, double *d_radii_out,
+                             uint8_t *d_bins, int64_t *d_counts, double *d_C, int64_t *d_n_exact,
+                             void *d_work, size_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Adjoint: gradient of a sigmoid-smoothed correlation integral with respect
  * to the four parameters of one group (the paper itself is gradient-free;

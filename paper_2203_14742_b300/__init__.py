@@ -75,6 +75,9 @@ _SIGS = {
     "mcil_workspace_size": (_i32, [_i64, _i64, _i32, _i32, _i32, _i32, _i32, C.POINTER(_sz)]),
     "mcil_features": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _dbl, _i32, _vp, _vp,
                              _vp, _vp, _vp, _vp, _sz, _vp]),
+    "mcil_workspace_size_rect": (_i32, [_i64, _i64, _i32, _i32, _i32, _i32, _i32, _i32, C.POINTER(_sz)]),
+    "mcil_features_rect": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _dbl, _i32,
+                                  _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "rd_kernel_launches": (_u64, []),
     "rd_set_spin_limit": (None, [C.c_uint32]),
     "rd_n_variants": (_i32, []),
@@ -457,37 +460,54 @@ def synlik(bins, M, T, seed, y_obs=None, out=None, n_feat=1):
 FEATURES = ("L2", "Linf", "W12", "W12p", "W1inf", "W1infp")
 
 
-def mcil_workspace(n1, n2, G, n_species, features=63, scale=False, M=16, device=None):
+def mcil_workspace(n1, n2, G, n_species, features=63, scale=False, M=16, device=None, Gy=None):
     """A device workspace for mcil() with these sizes (reusable across calls)."""
+    Gy = G if Gy is None else Gy
     sz = _sz()
-    _check("mcil_workspace_size", lib().mcil_workspace_size(int(n1), int(n2), int(G), int(n_species),
-                                                            int(features), 1 if scale else 0, int(M),
-                                                            C.byref(sz)))
+    _check("mcil_workspace_size_rect", lib().mcil_workspace_size_rect(
+        int(n1), int(n2), int(Gy), int(G), int(n_species), int(features), 1 if scale else 0, int(M), C.byref(sz)))
     return torch.empty(sz.value, dtype=torch.uint8, device=device)
 
 
-def mcil(X1, X2, G, n_species, b=1.3, M=16, features=63, scale=False, work=None):
+def mcil(X1, X2, G, n_species, b=1.3, M=16, features=63, scale=False, work=None, Gy=None):
     """Multi-feature correlation integral of two pattern sets (rows of n_species
-    G x G fields, read in place).  Returns radii [K, M+1], bins [K, n1, n2],
-    counts [K, M], C [K*M] and n_exact for the K selected features."""
+    Gy x G fields, read in place; Gy = G by default, 1 for 1-D patterns).
+    Returns radii [K, M+1], bins [K, n1, n2], counts [K, M], C [K*M] and
+    n_exact for the K selected features."""
+    Gy = G if Gy is None else Gy
     X1, ld1, n1, d = _as_rows(X1)
     X2, ld2, n2, d2 = _as_rows(X2)
-    if d != d2 or d != n_species * G * G:
-        raise ValueError("pattern length must be n_species * G * G")
+    if d != d2 or d != n_species * Gy * G:
+        raise ValueError("pattern length must be n_species * Gy * G")
     dev = X1.device
     K = bin(int(features)).count("1")
     if work is None:
-        work = mcil_workspace(n1, n2, G, n_species, features, scale, M, dev)
+        work = mcil_workspace(n1, n2, G, n_species, features, scale, M, dev, Gy=Gy)
     radii = torch.empty((K, M + 1), dtype=torch.float64, device=dev)
     bins = torch.empty((K, n1, n2), dtype=torch.uint8, device=dev)
     counts = torch.empty((K, M), dtype=torch.int64, device=dev)
     Cv = torch.empty(K * M, dtype=torch.float64, device=dev)
     nex = torch.zeros(1, dtype=torch.int64, device=dev)
-    _check("mcil_features", lib().mcil_features(_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, int(G), int(n_species),
-                                                int(features), 1 if scale else 0, float(b), int(M), _ptr(radii),
-                                                _ptr(bins), _ptr(counts), _ptr(Cv), _ptr(nex), _ptr(work),
-                                                work.numel(), _stream()))
+    _check("mcil_features_rect", lib().mcil_features_rect(
+        _ptr(X1), ld1, n1, _ptr(X2), ld2, n2, int(Gy), int(G), int(n_species), int(features), 1 if scale else 0,
+        float(b), int(M), _ptr(radii), _ptr(bins), _ptr(counts), _ptr(Cv), _ptr(nex), _ptr(work), work.numel(),
+        _stream()))
     return {"radii": radii, "bins": bins, "counts": counts, "C": Cv, "n_exact": nex}
+
+
+def mcil_rdode(fields, n1, b=1.3, M=13, scale=False):
+    """Multi-feature correlation integral of 1-D reaction-diffusion-ODE
+    patterns (Sec. 5.2): fields [n, 2, N] (u, w); set 1 = rows 0..n1-1, set 2
+    the rest.  L2 and Linf of both species, the derivative-based norms
+    (W12, W12', W1inf, W1inf') of w alone (u is discontinuous).  Returns the
+    two mcil() results and the bins [6, n1, n2] concatenated in feature
+    order for synlik(..., n_feat=6)."""
+    n, _, N = fields.shape
+    both = fields.reshape(n, 2 * N)
+    w = fields[:, 1, :]
+    a = mcil(both[:n1], both[n1:], N, 2, b=b, M=M, features=0x03, scale=scale, Gy=1)
+    c = mcil(w[:n1], w[n1:], N, 1, b=b, M=M, features=0x3C, scale=scale, Gy=1)
+    return a, c, torch.cat([a["bins"], c["bins"]], dim=0)
 
 
 # ---------------------------------------------------------------------------

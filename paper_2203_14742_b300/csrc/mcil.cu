@@ -3,9 +3,11 @@
 // u = s_i - s_j, concatenated (Sec. 3.1, Alg. 2), optionally on min-max
 // scaled patterns (Sec. 4, "scaled pattern data").
 //
-// A pattern is n_species fields of G x G nodes; h = 1/(G-1), g = G-1.  The
-// derivative patterns are forward differences of each field rounded to FP32
-// once (Dx: G x (G-1), Dy: (G-1) x G per species).  With q0, qx, qy the
+// A pattern is n_species fields of Gy x Gx nodes (Gy = Gx = G for the 2-D
+// models, Gy = 1 for the 1-D reaction-diffusion-ODE patterns, which have no
+// y differences: qy = my = 0); h = 1/(Gx-1), g = Gx-1.  The derivative
+// patterns are forward differences of each field rounded to FP32 once
+// (Dx: Gy x (Gx-1), Dy: (Gy-1) x Gx per species).  With q0, qx, qy the
 // canonical squared distances (the fixed FP64 order of the CIL: partial
 // t mod 256, halving trees) of the patterns and of their Dx and Dy patterns,
 // and m0, mx, my the maxima of |difference| with each difference in FP64
@@ -50,8 +52,8 @@ static constexpr int NF = 6;
 __host__ __device__ constexpr bool feat_squared(int f) { return f == 0 || f == 2; }
 
 struct McilWork {
-    int64_t n1, n2, np, d0, de;
-    int G, nsp, mask, M;
+    int64_t n1, n2, np, d0, dex, dey;
+    int Gy, Gx, nsp, mask, M;
     float *S1, *S2;                 // min-max scaled patterns (scale only)
     float *Ax1, *Ay1, *Ax2, *Ay2;   // forward-difference patterns
     void *cw[3];                    // CIL workspaces for the pattern, Dx, Dy arrays
@@ -71,11 +73,12 @@ struct McilWork {
 
 static inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-static McilWork mlayout(int64_t n1, int64_t n2, int G, int nsp, int mask, int scale, int M, void *base) {
+static McilWork mlayout(int64_t n1, int64_t n2, int Gy, int Gx, int nsp, int mask, int scale, int M, void *base) {
     McilWork w{};
-    w.n1 = n1; w.n2 = n2; w.np = n1 * n2; w.G = G; w.nsp = nsp; w.mask = mask; w.M = M;
-    w.d0 = (int64_t)nsp * G * G;
-    w.de = (int64_t)nsp * G * (G - 1);
+    w.n1 = n1; w.n2 = n2; w.np = n1 * n2; w.Gy = Gy; w.Gx = Gx; w.nsp = nsp; w.mask = mask; w.M = M;
+    w.d0 = (int64_t)nsp * Gy * Gx;
+    w.dex = (int64_t)nsp * Gy * (Gx - 1);
+    w.dey = (int64_t)nsp * (Gy - 1) * Gx;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -89,20 +92,23 @@ static McilWork mlayout(int64_t n1, int64_t n2, int G, int nsp, int mask, int sc
     }
     const bool deriv = (mask & 0x3C) != 0;
     if (deriv) {
-        w.Ax1 = (float *)take(sizeof(float) * n1 * w.de);
-        w.Ay1 = (float *)take(sizeof(float) * n1 * w.de);
-        w.Ax2 = (float *)take(sizeof(float) * n2 * w.de);
-        w.Ay2 = (float *)take(sizeof(float) * n2 * w.de);
+        w.Ax1 = (float *)take(sizeof(float) * n1 * w.dex);
+        w.Ax2 = (float *)take(sizeof(float) * n2 * w.dex);
+        if (w.dey > 0) {
+            w.Ay1 = (float *)take(sizeof(float) * n1 * w.dey);
+            w.Ay2 = (float *)take(sizeof(float) * n2 * w.dey);
+        }
     }
     (void)n;
     const bool need_q0 = (mask & 0x0D) != 0, need_qd = (mask & 0x0C) != 0;
     for (int a = 0; a < 3; ++a) {
-        const bool need = a == 0 ? need_q0 : need_qd;
+        const int64_t da = a == 0 ? w.d0 : (a == 1 ? w.dex : w.dey);
+        const bool need = (a == 0 ? need_q0 : need_qd) && da > 0;
         w.cw[a] = nullptr;
         w.cw_bytes[a] = 0;
         if (need) {
             size_t sz = 0;
-            cil_workspace_size(n1, n2, a == 0 ? w.d0 : w.de, &sz);
+            cil_workspace_size(n1, n2, da, &sz);
             w.cw_bytes[a] = sz;
             w.cw[a] = take(sz);
         }
@@ -122,10 +128,10 @@ static McilWork mlayout(int64_t n1, int64_t n2, int G, int nsp, int mask, int sc
 // ---------------------------------------------------------------------------
 // 0. min-max scaling: one CTA per (pattern, species)
 // ---------------------------------------------------------------------------
-__global__ void minmax_kernel(const float *__restrict__ X, int64_t ld, int G, int nsp, float *__restrict__ out) {
+__global__ void minmax_kernel(const float *__restrict__ X, int64_t ld, int64_t cells, int nsp,
+                              float *__restrict__ out) {
     const int64_t i = blockIdx.x / nsp;
     const int sp = blockIdx.x % nsp;
-    const int64_t cells = (int64_t)G * G;
     const float *x = X + i * ld + sp * cells;
     float *o = out + (i * nsp + sp) * cells;
     float mn = x[0], mx = x[0];
@@ -157,25 +163,28 @@ __global__ void minmax_kernel(const float *__restrict__ X, int64_t ld, int G, in
 // 1. forward-difference patterns (FP32 subtraction = the exact difference
 //    rounded once)
 // ---------------------------------------------------------------------------
-__global__ void fd_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int G, int nsp, float *__restrict__ Ax,
-                          float *__restrict__ Ay) {
-    const int64_t ce = (int64_t)G * (G - 1);
-    const int64_t total = n * nsp * ce;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t is = e / ce, c = e - is * ce;
+__global__ void fd_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int Gy, int Gx, int nsp,
+                          float *__restrict__ Ax, float *__restrict__ Ay) {
+    const int64_t cex = (int64_t)Gy * (Gx - 1), cey = (int64_t)(Gy - 1) * Gx, cells = (int64_t)Gy * Gx;
+    // Dx: row y, column c2 < Gx-1
+    const int64_t tx_ = n * nsp * cex;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tx_; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t is = e / cex, c = e - is * cex;
         const int64_t i = is / nsp;
         const int sp = (int)(is - i * nsp);
-        const float *x = X + i * ld + (int64_t)sp * G * G;
-        // Dx: row y, column c2 < G-1
-        {
-            const int y = (int)(c / (G - 1)), c2 = (int)(c - (int64_t)y * (G - 1));
-            Ax[e] = x[(int64_t)y * G + c2 + 1] - x[(int64_t)y * G + c2];
-        }
-        // Dy: row y < G-1, column c2
-        {
-            const int y = (int)(c / G), c2 = (int)(c - (int64_t)y * G);
-            Ay[e] = x[(int64_t)(y + 1) * G + c2] - x[(int64_t)y * G + c2];
-        }
+        const float *x = X + i * ld + (int64_t)sp * cells;
+        const int y = (int)(c / (Gx - 1)), c2 = (int)(c - (int64_t)y * (Gx - 1));
+        Ax[e] = x[(int64_t)y * Gx + c2 + 1] - x[(int64_t)y * Gx + c2];
+    }
+    // Dy: row y < Gy-1, column c2
+    const int64_t ty_ = n * nsp * cey;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ty_; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t is = e / cey, c = e - is * cey;
+        const int64_t i = is / nsp;
+        const int sp = (int)(is - i * nsp);
+        const float *x = X + i * ld + (int64_t)sp * cells;
+        const int y = (int)(c / Gx), c2 = (int)(c - (int64_t)y * Gx);
+        Ay[e] = x[(int64_t)(y + 1) * Gx + c2] - x[(int64_t)y * Gx + c2];
     }
 }
 
@@ -634,9 +643,9 @@ __global__ void finish_kernel_m(McilWork w, const unsigned long long *t0, const 
             Cv[e] = __ddiv_rn((double)counts[e], (double)w.np);
 }
 
-static rd_status mcil_check(int64_t n1, int64_t n2, int G, int nsp, int mask, int M, double b) {
+static rd_status mcil_check(int64_t n1, int64_t n2, int Gy, int Gx, int nsp, int mask, int M, double b) {
     if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535) return RD_ERR_INVALID_ARG;
-    if (G < 2 || G > 4096 || nsp < 1 || nsp > 2) return RD_ERR_INVALID_ARG;
+    if (Gx < 2 || Gx > 4096 || Gy < 1 || Gy > 4096 || nsp < 1 || nsp > 2) return RD_ERR_INVALID_ARG;
     if (mask < 1 || mask > 63 || M < 1 || M > 32 || !(b > 1.0)) return RD_ERR_INVALID_ARG;
     return RD_OK;
 }
@@ -645,25 +654,16 @@ static rd_status mcil_check(int64_t n1, int64_t n2, int G, int nsp, int mask, in
 
 using namespace rdcil;
 
-extern "C" rd_status mcil_workspace_size(int64_t n1, int64_t n2, int32_t G, int32_t n_species, int32_t features,
-                                         int32_t scale, int32_t M, size_t *bytes) {
-    if (!bytes) return RD_ERR_INVALID_ARG;
-    rd_status st = mcil_check(n1, n2, G, n_species, features, M, 2.0);
+static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2, int64_t n2,
+                          int32_t Gy, int32_t Gx, int32_t n_species, int32_t features, int32_t scale, double b,
+                          int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts, double *d_C,
+                          int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream) {
+    rd_status st = mcil_check(n1, n2, Gy, Gx, n_species, features, M, b);
     if (st) return st;
-    *bytes = mlayout(n1, n2, G, n_species, features, scale, M, nullptr).bytes;
-    return RD_OK;
-}
-
-extern "C" rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
-                                   int64_t n2, int32_t G, int32_t n_species, int32_t features, int32_t scale,
-                                   double b, int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
-                                   double *d_C, int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream) {
-    rd_status st = mcil_check(n1, n2, G, n_species, features, M, b);
-    if (st) return st;
-    const int64_t d0 = (int64_t)n_species * G * G;
+    const int64_t d0 = (int64_t)n_species * Gy * Gx;
     if (!d_X1 || !d_X2 || !d_radii_out || !d_bins || !d_counts || !d_work) return RD_ERR_INVALID_ARG;
     if (ld1 < d0 || ld2 < d0 || (((uintptr_t)d_work) & 255)) return RD_ERR_INVALID_ARG;
-    McilWork w = mlayout(n1, n2, G, n_species, features, scale, M, d_work);
+    McilWork w = mlayout(n1, n2, Gy, Gx, n_species, features, scale, M, d_work);
     if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int K = __builtin_popcount((unsigned)features);
@@ -676,23 +676,24 @@ extern "C" rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, c
     const float *P1 = d_X1, *P2 = d_X2;
     int64_t l1 = ld1, l2 = ld2;
     if (scale) {
-        minmax_kernel<<<(unsigned)(n1 * n_species), 256, 0, s>>>(d_X1, ld1, G, n_species, w.S1);
+        minmax_kernel<<<(unsigned)(n1 * n_species), 256, 0, s>>>(d_X1, ld1, (int64_t)Gy * Gx, n_species, w.S1);
         note_launch();
-        minmax_kernel<<<(unsigned)(n2 * n_species), 256, 0, s>>>(d_X2, ld2, G, n_species, w.S2);
+        minmax_kernel<<<(unsigned)(n2 * n_species), 256, 0, s>>>(d_X2, ld2, (int64_t)Gy * Gx, n_species, w.S2);
         note_launch();
         P1 = w.S1; P2 = w.S2; l1 = l2 = d0;
     }
     const bool deriv = (features & 0x3C) != 0;
     if (deriv) {
-        fd_kernel<<<4 * 148, 256, 0, s>>>(P1, l1, n1, G, n_species, w.Ax1, w.Ay1);
+        fd_kernel<<<4 * 148, 256, 0, s>>>(P1, l1, n1, Gy, Gx, n_species, w.Ax1, w.Ay1);
         note_launch();
-        fd_kernel<<<4 * 148, 256, 0, s>>>(P2, l2, n2, G, n_species, w.Ax2, w.Ay2);
+        fd_kernel<<<4 * 148, 256, 0, s>>>(P2, l2, n2, Gy, Gx, n_species, w.Ax2, w.Ay2);
         note_launch();
     }
     Arr3 A{};
     A.a1[0] = P1; A.a2[0] = P2; A.ld1[0] = l1; A.ld2[0] = l2; A.d[0] = d0;
     A.a1[1] = w.Ax1; A.a2[1] = w.Ax2; A.a1[2] = w.Ay1; A.a2[2] = w.Ay2;
-    for (int a = 1; a < 3; ++a) { A.ld1[a] = A.ld2[a] = w.de; A.d[a] = w.de; }
+    A.ld1[1] = A.ld2[1] = A.d[1] = w.dex;
+    A.ld1[2] = A.ld2[2] = A.d[2] = w.dey;
 
     // squared distances: tier-1 intervals
     QIv qi{};
@@ -707,7 +708,7 @@ extern "C" rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, c
     RD_CUDA_TRY(cudaMemsetAsync(w.mabs, 0, sizeof(float) * 3 * np, s));
     const bool need_m0 = (features & 0x32) != 0, need_md = (features & 0x30) != 0;
     for (int a = 0; a < 3; ++a) {
-        if (a == 0 ? !need_m0 : !need_md) continue;
+        if ((a == 0 ? !need_m0 : !need_md) || A.d[a] == 0) continue;
         // K chunks (multiples of 32, at least 64) for about two CTAs per SM
         const int64_t tiles = ((n1 + MX_T - 1) / MX_T) * ((n2 + MX_T - 1) / MX_T);
         const int64_t want = (2 * 148 + tiles - 1) / tiles;
@@ -720,7 +721,7 @@ extern "C" rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, c
                                            w.mabs + a * np);
         note_launch();
     }
-    const double g = (double)(G - 1), h = 1.0 / g, h2 = 1.0 / (g * g);
+    const double g = (double)(Gx - 1), h = 1.0 / g, h2 = 1.0 / (g * g);
     intervals_kernel<<<gp, 256, 0, s>>>(w, qi, h, h2, g);
     note_launch();
     candidates_kernel<<<gp, 256, 0, s>>>(w);
@@ -753,4 +754,35 @@ extern "C" rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, c
     finish_kernel_m<<<1, 256, 0, s>>>(w, tmo[0], tmo[1], tmo[2], d_counts, d_C, K, d_n_exact);
     note_launch();
     return cuda_status(cudaGetLastError());
+}
+
+extern "C" rd_status mcil_workspace_size(int64_t n1, int64_t n2, int32_t G, int32_t n_species, int32_t features,
+                                         int32_t scale, int32_t M, size_t *bytes) {
+    return mcil_workspace_size_rect(n1, n2, G, G, n_species, features, scale, M, bytes);
+}
+
+extern "C" rd_status mcil_workspace_size_rect(int64_t n1, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
+                                              int32_t features, int32_t scale, int32_t M, size_t *bytes) {
+    if (!bytes) return RD_ERR_INVALID_ARG;
+    rd_status st = mcil_check(n1, n2, Gy, Gx, n_species, features, M, 2.0);
+    if (st) return st;
+    *bytes = mlayout(n1, n2, Gy, Gx, n_species, features, scale, M, nullptr).bytes;
+    return RD_OK;
+}
+
+extern "C" rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
+                                   int64_t n2, int32_t G, int32_t n_species, int32_t features, int32_t scale,
+                                   double b, int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
+                                   double *d_C, int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream) {
+    return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, G, G, n_species, features, scale, b, M, d_radii_out, d_bins,
+                    d_counts, d_C, d_n_exact, d_work, work_bytes, stream);
+}
+
+extern "C" rd_status mcil_features_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
+                                        int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species, int32_t features,
+                                        int32_t scale, double b, int32_t M, double *d_radii_out, uint8_t *d_bins,
+                                        int64_t *d_counts, double *d_C, int64_t *d_n_exact, void *d_work,
+                                        size_t work_bytes, void *stream) {
+    return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, Gy, Gx, n_species, features, scale, b, M, d_radii_out, d_bins,
+                    d_counts, d_C, d_n_exact, d_work, work_bytes, stream);
 }

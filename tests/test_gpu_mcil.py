@@ -137,3 +137,45 @@ def test_c3_shape(p):
     X = W.cosine_patterns(512, 128, 2, 33, amp=0.8, offset=2.0)
     g, o = run_both(p, X[:256], X[256:], 128, 2, b=1.3, M=16)
     assert_same(g, o)
+
+
+# ---------------------------------------------------------------------------
+# Gy x Gx fields and the 1-D reaction-diffusion-ODE patterns (Sec. 5.2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n1,n2,Gy,Gx,nsp", [(7, 9, 1, 64, 2), (16, 16, 1, 128, 1), (33, 40, 8, 32, 2),
+                                             (3, 4, 1, 3, 1)])
+@pytest.mark.parametrize("scale", [False, True])
+def test_rectangular_fields_bit_exact(p, n1, n2, Gy, Gx, nsp, scale):
+    rng = np.random.default_rng(Gy * 100 + Gx + n1)
+    X = (rng.standard_normal((n1 + n2, nsp * Gy * Gx)) * 0.7 + 1.3).astype(np.float32)
+    t = torch.from_numpy(X).cuda()
+    g = p.mcil(t[:n1], t[n1:], Gx, nsp, b=1.1, M=12, features=63, scale=scale, Gy=Gy)
+    o = oracle.mcil(X[:n1], X[n1:], Gx, nsp, b=1.1, M=12, mask=63, scale=scale, Gy=Gy)
+    torch.cuda.synchronize()
+    assert int(g["n_exact"]) >= 0
+    assert_same(g, o)
+
+
+def test_rdode_patterns_mcil(p):
+    # the RD-ODE workload's patterns at t = 50: L2 and Linf of both species,
+    # the derivative-based norms of w alone, bit-exact with the oracle, and
+    # the concatenated 6-feature bins through the bootstrap statistics
+    cfg = W.config("c7")
+    gd = dict(cfg["groups"][0])
+    gd["n_real"] = 48
+    sim = p.Simulation([p.Group.from_dict(gd)])
+    sim.integrate_rkc(1e-3, rtol=cfg["rkc_tol"], atol=cfg["rkc_tol"])
+    assert sim.sync_status() == 0
+    F = sim.group_fields(0)
+    a, c, bins = p.mcil_rdode(F, 24, b=1.1, M=cfg["M"])
+    Fn = F.cpu().numpy()
+    both = Fn.reshape(48, -1)
+    w = np.ascontiguousarray(Fn[:, 1, :])
+    oa = oracle.mcil(both[:24], both[24:], 64, 2, b=1.1, M=cfg["M"], mask=0x03, Gy=1)
+    oc = oracle.mcil(w[:24], w[24:], 64, 1, b=1.1, M=cfg["M"], mask=0x3C, Gy=1)
+    assert_same(a, oa)
+    assert_same(c, oc)
+    assert bins.shape == (6, 24, 24)
+    s = p.synlik(bins, cfg["M"], 100, cfg["seed"], n_feat=6)
+    so = oracle.synlik_multi(np.concatenate([oa["bins"], oc["bins"]]), cfg["M"], 100, cfg["seed"])
+    assert np.array_equal(s["Y"].cpu().numpy(), so["Y"])
