@@ -63,7 +63,7 @@ def lib():
         L.orc_d2_canon.restype = C.c_double
         L.orc_mcil_values.argtypes = [fp, fp, fp, C.c_int64, fp, fp, fp, C.c_int64, C.c_int, C.c_int, C.c_int,
                                       C.c_int, dp]
-        L.orc_mcil_bins.argtypes = [dp, C.c_int64, C.c_int, C.c_double, C.c_int, dp, u8p, i64p]
+        L.orc_mcil_bins.argtypes = [dp, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_int, dp, u8p, i64p]
         L.orc_mcil_squared.argtypes = [C.c_int]
         L.orc_mcil_squared.restype = C.c_int
         L.orc_sm64.argtypes = [C.c_uint64, C.c_uint64]
@@ -419,11 +419,12 @@ def mcil_values(X1, X2, G, nsp, mask=63, Gy=None):
     return V
 
 
-def mcil(X1, X2, G, nsp, b, M, mask=63, scale=False, Gy=None):
+def mcil(X1, X2, G, nsp, b, M, mask=63, scale=False, Gy=None, law="power"):
     """Multi-feature correlation integral (Alg. 2 step 2.2): per feature in
     mask (ascending), radii [K, M+1] (R0 first), bins [K, n1, n2], counts
     [K, M]; C = the concatenated vector (K*M) of eq. (CIL).  Fields Gy x G
-    (Gy = G by default, 1 for 1-D patterns)."""
+    (Gy = G by default, 1 for 1-D patterns); law "power" (R0 b^-k) or
+    "linear" (R0 - k (R0 - R_min) / M, b unused)."""
     if scale:
         X1, X2 = minmax(X1, G, nsp, Gy), minmax(X2, G, nsp, Gy)
     V = mcil_values(X1, X2, G, nsp, mask, Gy)
@@ -435,7 +436,8 @@ def mcil(X1, X2, G, nsp, b, M, mask=63, scale=False, Gy=None):
     counts = np.empty((K, M), np.int64)
     for a, f in enumerate(feats):
         v = np.ascontiguousarray(V[f])
-        lib().orc_mcil_bins(_p(v, C.c_double), n1 * n2, lib().orc_mcil_squared(f), float(b), M,
+        lib().orc_mcil_bins(_p(v, C.c_double), n1 * n2, lib().orc_mcil_squared(f), 1 if law == "linear" else 0,
+                            float(b or 0.0), M,
                             _p(radii[a], C.c_double), _p(bins[a], C.c_uint8), _p(counts[a], C.c_int64))
     return {"features": feats, "values": V, "radii": radii, "bins": bins, "counts": counts,
             "C": counts.reshape(-1) / float(n1 * n2)}

@@ -182,19 +182,32 @@ void orc_mcil_values(const float *X1, const float *Ax1, const float *Ay1, int64_
 
 /* Radii, bins and counts of one feature (Sec. 2.1 with the feature's
    distance): squared features R0 = sqrt(max V), K = #{k : V < R_k * R_k};
-   value features R0 = max V, K = #{k : V < R_k}; R_k = R_{k-1} / b.
+   value features R0 = max V, K = #{k : V < R_k}.  law 0: R_k = R_{k-1} / b;
+   law 1 (the linear law, Sec. 2.1 / Sec. 3.2): R_min = sqrt(min V) (value
+   features: min V), h = (R0 - R_min) / M, R_k = R0 - k h.
    radii[0] = R0, radii[1..M] = R_1..R_M. */
-void orc_mcil_bins(const double *V, int64_t np, int squared, double b, int M, double *radii,
+void orc_mcil_bins(const double *V, int64_t np, int squared, int law, double b, int M, double *radii,
                    uint8_t *bins, int64_t *counts)
 {
-    double mx = 0.0;
-    for (int64_t q = 0; q < np; ++q)
+    double mx = 0.0, mn = V[0];
+    for (int64_t q = 0; q < np; ++q) {
         if (V[q] > mx) mx = V[q];
+        if (V[q] < mn) mn = V[q];
+    }
     double R = squared ? sqrt(mx) : mx;
     radii[0] = R;
-    for (int k = 1; k <= M; ++k) {
-        R = R / b;
-        radii[k] = R;
+    if (law == 1) {
+        const double Rm = squared ? sqrt(mn) : mn;
+        const double h = (R - Rm) / (double)M;
+        for (int k = 1; k <= M; ++k) {
+            const double kh = (double)k * h;
+            radii[k] = R - kh;
+        }
+    } else {
+        for (int k = 1; k <= M; ++k) {
+            R = R / b;
+            radii[k] = R;
+        }
     }
     for (int k = 0; k < M; ++k) counts[k] = 0;
     for (int64_t q = 0; q < np; ++q) {

@@ -177,3 +177,16 @@ def test_one_dimensional_features_by_hand():
     assert V[4] == 4.0 and V[5] == 6.0
     Ax, Ay = oracle.fd(X1, 3, 1, Gy=1)
     assert Ax.tolist() == [[1.0, 2.0]] and Ay.shape == (1, 0)
+
+
+def test_linear_law_by_hand():
+    # patterns (v, 0) on a line: set 1 = {0, 1}, set 2 = {3, 5, 6}; the L2
+    # and Linf features are both the distance |v - v'| (3, 5, 6 / 2, 4, 5):
+    # R0 = 6, R_min = 2, M = 4, h = 1, radii 5, 4, 3, 2 (worked by hand),
+    # counts 3, 2, 1, 0 for both
+    X1 = np.array([[0.0, 0.0], [1.0, 0.0]], np.float32)
+    X2 = np.array([[3.0, 0.0], [5.0, 0.0], [6.0, 0.0]], np.float32)
+    o = oracle.mcil(X1, X2, 2, 1, None, 4, mask=0x03, Gy=1, law="linear")
+    for a in range(2):
+        assert o["radii"][a].tolist() == [6.0, 5.0, 4.0, 3.0, 2.0]
+        assert o["counts"][a].tolist() == [3, 2, 1, 0]
