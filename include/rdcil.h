@@ -547,6 +547,22 @@ rd_status mcil_features_rect(const float *d_X1, int64_t ld1, int64_t n1, const f
                              uint8_t *d_bins, int64_t *d_counts, double *d_C, int64_t *d_n_exact,
                              void *d_work, size_t work_bytes, void *stream);
 
+/* mcil_features_linear_rect — mcil_features_rect with the linear radii law
+ * of Sec. 2.1 / Sec. 3.2 per feature (Table 1 pairs it with the MC and
+ * RD-ODE models): R0 as above, R_min = sqrt(min V) for a squared feature
+ * and min V for a value feature (min over all n1 n2 pairs), h = (R0 -
+ * R_min) / M, R_k = R0 - k h, every operation FP64 rounded to nearest
+ * (k h first, then the subtraction).  The smallest value of each feature
+ * is found exactly like the largest: the pairs whose interval may hold it
+ * are re-bounded and, if still undecided, evaluated in the canonical
+ * order.  Bins, counts, outputs, workspace (mcil_workspace_size_rect) and
+ * limits as for mcil_features_rect; no b. */
+rd_status mcil_features_linear_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                    int64_t ld2, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
+                                    int32_t features, int32_t scale, int32_t M, double *d_radii_out,
+                                    uint8_t *d_bins, int64_t *d_counts, double *d_C, int64_t *d_n_exact,
+                                    void *d_work, size_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Adjoint: gradient of a sigmoid-smoothed correlation integral with respect
  * to the four parameters of one group (the paper itself is gradient-free;

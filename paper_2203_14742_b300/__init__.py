@@ -78,6 +78,8 @@ _SIGS = {
     "mcil_workspace_size_rect": (_i32, [_i64, _i64, _i32, _i32, _i32, _i32, _i32, _i32, C.POINTER(_sz)]),
     "mcil_features_rect": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _dbl, _i32,
                                   _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "mcil_features_linear_rect": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _i32,
+                                         _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "rd_kernel_launches": (_u64, []),
     "rd_set_spin_limit": (None, [C.c_uint32]),
     "rd_n_variants": (_i32, []),
@@ -469,11 +471,14 @@ def mcil_workspace(n1, n2, G, n_species, features=63, scale=False, M=16, device=
     return torch.empty(sz.value, dtype=torch.uint8, device=device)
 
 
-def mcil(X1, X2, G, n_species, b=1.3, M=16, features=63, scale=False, work=None, Gy=None):
+def mcil(X1, X2, G, n_species, b=1.3, M=16, features=63, scale=False, work=None, Gy=None, law="power"):
     """Multi-feature correlation integral of two pattern sets (rows of n_species
     Gy x G fields, read in place; Gy = G by default, 1 for 1-D patterns).
+    law "power" (R0 b^-k) or "linear" (R0 - k (R0 - R_min) / M, b unused).
     Returns radii [K, M+1], bins [K, n1, n2], counts [K, M], C [K*M] and
     n_exact for the K selected features."""
+    if law not in ("power", "linear"):
+        raise ValueError("law must be 'power' or 'linear'")
     Gy = G if Gy is None else Gy
     X1, ld1, n1, d = _as_rows(X1)
     X2, ld2, n2, d2 = _as_rows(X2)
@@ -488,14 +493,20 @@ def mcil(X1, X2, G, n_species, b=1.3, M=16, features=63, scale=False, work=None,
     counts = torch.empty((K, M), dtype=torch.int64, device=dev)
     Cv = torch.empty(K * M, dtype=torch.float64, device=dev)
     nex = torch.zeros(1, dtype=torch.int64, device=dev)
-    _check("mcil_features_rect", lib().mcil_features_rect(
-        _ptr(X1), ld1, n1, _ptr(X2), ld2, n2, int(Gy), int(G), int(n_species), int(features), 1 if scale else 0,
-        float(b), int(M), _ptr(radii), _ptr(bins), _ptr(counts), _ptr(Cv), _ptr(nex), _ptr(work), work.numel(),
-        _stream()))
+    if law == "linear":
+        _check("mcil_features_linear_rect", lib().mcil_features_linear_rect(
+            _ptr(X1), ld1, n1, _ptr(X2), ld2, n2, int(Gy), int(G), int(n_species), int(features),
+            1 if scale else 0, int(M), _ptr(radii), _ptr(bins), _ptr(counts), _ptr(Cv), _ptr(nex), _ptr(work),
+            work.numel(), _stream()))
+    else:
+        _check("mcil_features_rect", lib().mcil_features_rect(
+            _ptr(X1), ld1, n1, _ptr(X2), ld2, n2, int(Gy), int(G), int(n_species), int(features),
+            1 if scale else 0, float(b), int(M), _ptr(radii), _ptr(bins), _ptr(counts), _ptr(Cv), _ptr(nex),
+            _ptr(work), work.numel(), _stream()))
     return {"radii": radii, "bins": bins, "counts": counts, "C": Cv, "n_exact": nex}
 
 
-def mcil_rdode(fields, n1, b=1.3, M=13, scale=False):
+def mcil_rdode(fields, n1, b=1.3, M=13, scale=False, law="power"):
     """Multi-feature correlation integral of 1-D reaction-diffusion-ODE
     patterns (Sec. 5.2): fields [n, 2, N] (u, w); set 1 = rows 0..n1-1, set 2
     the rest.  L2 and Linf of both species, the derivative-based norms
@@ -505,8 +516,8 @@ def mcil_rdode(fields, n1, b=1.3, M=13, scale=False):
     n, _, N = fields.shape
     both = fields.reshape(n, 2 * N)
     w = fields[:, 1, :]
-    a = mcil(both[:n1], both[n1:], N, 2, b=b, M=M, features=0x03, scale=scale, Gy=1)
-    c = mcil(w[:n1], w[n1:], N, 1, b=b, M=M, features=0x3C, scale=scale, Gy=1)
+    a = mcil(both[:n1], both[n1:], N, 2, b=b, M=M, features=0x03, scale=scale, Gy=1, law=law)
+    c = mcil(w[:n1], w[n1:], N, 1, b=b, M=M, features=0x3C, scale=scale, Gy=1, law=law)
     return a, c, torch.cat([a["bins"], c["bins"]], dim=0)
 
 

@@ -20,7 +20,9 @@
 //   5 W1inf'  value    (m0 + g mx) + g my                  (eq. norm:W1infprime)
 // each one FP64 expression with every operation rounded to nearest.  A
 // squared feature is decided like the CIL (R0 = sqrt(max), V < R_k * R_k),
-// a value feature directly (R0 = max, V < R_k); R_k = R_{k-1} / b.
+// a value feature directly (R0 = max, V < R_k); R_k = R_{k-1} / b (power
+// law) or R_k = R0 - k (R0 - R_min) / M with R_min the smallest value (its
+// sqrt for a squared feature; the linear law of Sec. 2.1 / Sec. 3.2).
 //
 // Exactness contract: bins and counts equal that definition bit for bit.
 //   1. q0, qx, qy: tier-1 intervals of the CIL (centred bf16 hi/lo split,
@@ -32,9 +34,9 @@
 //   3. per pair and feature, an FP64 interval of the feature value by
 //      outward-rounded (_rd / _ru) evaluation of its expression (every
 //      operation is monotone on the non-negative inputs);
-//   4. pairs whose interval may hold a feature's maximum are evaluated
-//      exactly (the canonical FP64 order, one CTA per pair), which fixes R0
-//      and the radii; pairs whose interval meets a threshold get tier 2
+//   4. pairs whose interval may hold a feature's maximum (linear law: or
+//      its minimum) are evaluated exactly (the canonical FP64 order, one
+//      CTA per pair), which fixes R0 (and R_min) and the radii; pairs whose interval meets a threshold get tier 2
 //      (FP32 error-free squared distances with a ~1e-12 bound, exact
 //      maxima) and, if still undecided, the canonical evaluation; every
 //      other pair is decided by its interval.
@@ -49,11 +51,12 @@ extern "C" rd_status cil_workspace_size(int64_t n1, int64_t n2, int64_t d, size_
 namespace rdcil {
 
 static constexpr int NF = 6;
+static constexpr int MC_SCAL = 32;   // control words of one call (see McilWork::scal)
 __host__ __device__ constexpr bool feat_squared(int f) { return f == 0 || f == 2; }
 
 struct McilWork {
     int64_t n1, n2, np, d0, dex, dey;
-    int Gy, Gx, nsp, mask, M;
+    int Gy, Gx, nsp, mask, M, law;   // law 0 power, 1 linear
     float *S1, *S2;                 // min-max scaled patterns (scale only)
     float *Ax1, *Ay1, *Ax2, *Ay2;   // forward-difference patterns
     void *cw[3];                    // CIL workspaces for the pattern, Dx, Dy arrays
@@ -66,7 +69,8 @@ struct McilWork {
     unsigned long long *scal;       // [0] queue length; [1] end of the maximum-candidate phase; [2 + f]
                                     // largest lower bound of feature f (bits); [8] start of the final
                                     // canonical segment; [9] number of maximum candidates; [10] pairs
-                                    // evaluated in the canonical order
+                                    // evaluated in the canonical order; [16 + f] smallest upper
+                                    // bound of feature f (complemented bits, linear law)
     double *thr;                    // [NF][32] thresholds of the decision (R_k^2 or R_k)
     size_t bytes;
 };
@@ -119,7 +123,7 @@ static McilWork mlayout(int64_t n1, int64_t n2, int Gy, int Gx, int nsp, int mas
     w.vex = (double *)take(sizeof(double) * NF * w.np);
     w.flag = (uint8_t *)take(w.np);
     w.queue = (int64_t *)take(sizeof(int64_t) * w.np);
-    w.scal = (unsigned long long *)take(sizeof(unsigned long long) * 16);
+    w.scal = (unsigned long long *)take(sizeof(unsigned long long) * MC_SCAL);
     w.thr = (double *)take(sizeof(double) * NF * 32);
     w.bytes = off;
     return w;
@@ -254,13 +258,24 @@ struct QIv {
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *a, double v) {
     atomicMax(a, (unsigned long long)__double_as_longlong(fmax(v, 0.0)));
 }
+// the minimum through atomicMax on the complemented bits (non-negative
+// doubles order like their bits; the cleared word reads as "none yet")
+__device__ __forceinline__ void atomic_min_nonneg(unsigned long long *a, double v) {
+    atomicMax(a, ~(unsigned long long)__double_as_longlong(fmax(v, 0.0)));
+}
+__device__ __forceinline__ double read_min_nonneg(const unsigned long long *a) {
+    return __longlong_as_double((long long)~*a);
+}
 
 __global__ void intervals_kernel(McilWork w, QIv qi, double h, double h2, double g) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t np = w.np;
-    double lb[NF];
+    double lb[NF], ub[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) lb[f] = 0.0;
+    for (int f = 0; f < NF; ++f) {
+        lb[f] = 0.0;
+        ub[f] = __longlong_as_double(0x7ff0000000000000ll);
+    }
     if (q < np) {
         double ql[3] = {0, 0, 0}, qh[3] = {0, 0, 0}, ml[3] = {0, 0, 0}, mh[3] = {0, 0, 0};
 #pragma unroll
@@ -294,6 +309,7 @@ __global__ void intervals_kernel(McilWork w, QIv qi, double h, double h2, double
                 w.vlo[f * np + q] = lo[f];
                 w.vhi[f * np + q] = hi[f];
                 lb[f] = lo[f];
+                ub[f] = hi[f];
             }
         }
         w.flag[q] = 0;
@@ -304,17 +320,27 @@ __global__ void intervals_kernel(McilWork w, QIv qi, double h, double h2, double
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
         if ((threadIdx.x & 31) == 0 && (w.mask & (1 << f))) atomic_max_nonneg(&w.scal[2 + f], v);
+        if (w.law == 1) {
+            double u = ub[f];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u = fmin(u, __shfl_xor_sync(0xffffffffu, u, o));
+            if ((threadIdx.x & 31) == 0 && (w.mask & (1 << f))) atomic_min_nonneg(&w.scal[16 + f], u);
+        }
     }
 }
 
-// pairs whose interval may hold a feature's maximum go to the exact queue
+// pairs whose interval may hold a feature's maximum (linear law: or its
+// minimum, lo <= the smallest upper bound) go to the exact queue
 __global__ void candidates_kernel(McilWork w) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= w.np) return;
     bool cand = false;
 #pragma unroll
     for (int f = 0; f < NF; ++f)
-        if (w.mask & (1 << f)) cand |= w.vhi[f * w.np + q] >= __longlong_as_double((long long)w.scal[2 + f]);
+        if (w.mask & (1 << f)) {
+            cand |= w.vhi[f * w.np + q] >= __longlong_as_double((long long)w.scal[2 + f]);
+            if (w.law == 1) cand |= w.vlo[f * w.np + q] <= read_min_nonneg(&w.scal[16 + f]);
+        }
     if (cand) {
         w.flag[q] = 1;
         const unsigned long long slot = atomicAdd(&w.scal[0], 1ull);
@@ -517,20 +543,24 @@ __global__ void mark_kernel_m(McilWork w, int slot) {
     if (threadIdx.x == 0) w.scal[slot] = w.scal[0];
 }
 
-// after tier 2 on the maximum candidates: raise each feature's largest
-// lower bound with their tighter intervals
+// after tier 2 on the candidates: raise each feature's largest lower bound
+// (linear law: lower its smallest upper bound) with their tighter intervals
 __global__ void lb2_kernel_m(McilWork w) {
     const unsigned long long nA = w.scal[9];
     for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < nA;
          e += (unsigned long long)gridDim.x * blockDim.x) {
         const int64_t q = w.queue[e];
         for (int f = 0; f < NF; ++f)
-            if (w.mask & (1 << f)) atomic_max_nonneg(&w.scal[2 + f], w.vlo[f * w.np + q]);
+            if (w.mask & (1 << f)) {
+                atomic_max_nonneg(&w.scal[2 + f], w.vlo[f * w.np + q]);
+                if (w.law == 1) atomic_min_nonneg(&w.scal[16 + f], w.vhi[f * w.np + q]);
+            }
     }
 }
 
 // candidates whose interval of some feature is not a single value and may
-// still hold that feature's maximum are evaluated in the canonical order
+// still hold that feature's maximum (or, linear law, its minimum) are
+// evaluated in the canonical order
 __global__ void cand2_kernel_m(McilWork w) {
     const unsigned long long nA = w.scal[9];
     for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < nA;
@@ -541,6 +571,7 @@ __global__ void cand2_kernel_m(McilWork w) {
             if (!(w.mask & (1 << f))) continue;
             const double lo = w.vlo[f * w.np + q], hi = w.vhi[f * w.np + q];
             need |= (lo < hi) && hi >= __longlong_as_double((long long)w.scal[2 + f]);
+            if (w.law == 1) need |= (lo < hi) && lo <= read_min_nonneg(&w.scal[16 + f]);
         }
         if (need) {
             w.flag[q] = 1;
@@ -559,25 +590,37 @@ __global__ void radii_kernel_m(McilWork w, double b, double *radii_out) {
     const unsigned long long nq = w.scal[0], nA = w.scal[9];
     if (threadIdx.x == 0) w.scal[1] = nq;   // end of the candidate phase
     if (f >= NF || !(w.mask & (1 << f))) return;
-    // every pair that may hold the maximum now has its value exactly: from
-    // the canonical pass (flag 2) or a single-value tier-2 interval
-    double mx = 0.0;
+    // every pair that may hold the maximum (or the minimum) now has its
+    // value exactly: from the canonical pass (flag 2) or a single-value
+    // tier-2 interval; every other candidate's value lies strictly inside
+    // (smallest upper bound, largest lower bound)
+    double mx = 0.0, mn = __longlong_as_double(0x7ff0000000000000ll);
     for (unsigned long long e = lane; e < nA; e += 32) {
         const int64_t q = w.queue[e];
         const double lo = w.vlo[f * w.np + q], hi = w.vhi[f * w.np + q];
-        if (w.flag[q] == 2) mx = fmax(mx, w.vex[f * w.np + q]);
-        else if (lo == hi) mx = fmax(mx, lo);
+        double v = -1.0;
+        if (w.flag[q] == 2) v = w.vex[f * w.np + q];
+        else if (lo == hi) v = lo;
+        if (v >= 0.0) {
+            mx = fmax(mx, v);
+            mn = fmin(mn, v);
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
     if (lane == 0) {
         int slot = 0;
         for (int f2 = 0; f2 < f; ++f2) slot += (w.mask >> f2) & 1;
         double *R = radii_out + (int64_t)slot * (w.M + 1);
         double r = feat_squared(f) ? __dsqrt_rn(mx) : mx;
         R[0] = r;
+        const double R0 = r;
+        const double hl = w.law == 1 ? __ddiv_rn(__dsub_rn(R0, feat_squared(f) ? __dsqrt_rn(mn) : mn), (double)w.M) : 0.0;
         for (int k = 1; k <= w.M; ++k) {
-            r = __ddiv_rn(r, b);
+            r = w.law == 1 ? __dsub_rn(R0, __dmul_rn((double)k, hl)) : __ddiv_rn(r, b);
             R[k] = r;
             w.thr[f * 32 + k - 1] = feat_squared(f) ? __dmul_rn(r, r) : r;
         }
@@ -656,7 +699,7 @@ using namespace rdcil;
 
 static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2, int64_t n2,
                           int32_t Gy, int32_t Gx, int32_t n_species, int32_t features, int32_t scale, double b,
-                          int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts, double *d_C,
+                          int law, int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts, double *d_C,
                           int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream) {
     rd_status st = mcil_check(n1, n2, Gy, Gx, n_species, features, M, b);
     if (st) return st;
@@ -665,11 +708,12 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
     if (ld1 < d0 || ld2 < d0 || (((uintptr_t)d_work) & 255)) return RD_ERR_INVALID_ARG;
     McilWork w = mlayout(n1, n2, Gy, Gx, n_species, features, scale, M, d_work);
     if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
+    w.law = law;
     cudaStream_t s = (cudaStream_t)stream;
     const int K = __builtin_popcount((unsigned)features);
     const int64_t np = w.np;
     const unsigned gp = (unsigned)((np + 255) / 256);
-    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, 16 * sizeof(unsigned long long), s));
+    RD_CUDA_TRY(cudaMemsetAsync(w.scal, 0, MC_SCAL * sizeof(unsigned long long), s));
     RD_CUDA_TRY(cudaMemsetAsync(d_counts, 0, (size_t)K * M * sizeof(int64_t), s));
 
     // patterns (scaled copies when asked)
@@ -774,7 +818,7 @@ extern "C" rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, c
                                    int64_t n2, int32_t G, int32_t n_species, int32_t features, int32_t scale,
                                    double b, int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
                                    double *d_C, int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream) {
-    return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, G, G, n_species, features, scale, b, M, d_radii_out, d_bins,
+    return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, G, G, n_species, features, scale, b, 0, M, d_radii_out, d_bins,
                     d_counts, d_C, d_n_exact, d_work, work_bytes, stream);
 }
 
@@ -783,6 +827,15 @@ extern "C" rd_status mcil_features_rect(const float *d_X1, int64_t ld1, int64_t 
                                         int32_t scale, double b, int32_t M, double *d_radii_out, uint8_t *d_bins,
                                         int64_t *d_counts, double *d_C, int64_t *d_n_exact, void *d_work,
                                         size_t work_bytes, void *stream) {
-    return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, Gy, Gx, n_species, features, scale, b, M, d_radii_out, d_bins,
+    return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, Gy, Gx, n_species, features, scale, b, 0, M, d_radii_out, d_bins,
                     d_counts, d_C, d_n_exact, d_work, work_bytes, stream);
+}
+
+extern "C" rd_status mcil_features_linear_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                               int64_t ld2, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
+                                               int32_t features, int32_t scale, int32_t M, double *d_radii_out,
+                                               uint8_t *d_bins, int64_t *d_counts, double *d_C, int64_t *d_n_exact,
+                                               void *d_work, size_t work_bytes, void *stream) {
+    return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, Gy, Gx, n_species, features, scale, 2.0, 1, M, d_radii_out,
+                    d_bins, d_counts, d_C, d_n_exact, d_work, work_bytes, stream);
 }

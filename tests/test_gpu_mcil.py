@@ -179,3 +179,90 @@ def test_rdode_patterns_mcil(p):
     s = p.synlik(bins, cfg["M"], 100, cfg["seed"], n_feat=6)
     so = oracle.synlik_multi(np.concatenate([oa["bins"], oc["bins"]]), cfg["M"], 100, cfg["seed"])
     assert np.array_equal(s["Y"].cpu().numpy(), so["Y"])
+
+
+# ---------------------------------------------------------------------------
+# the linear radii law per feature (Sec. 2.1 / Sec. 3.2)
+# ---------------------------------------------------------------------------
+def run_linear(p, X1, X2, Gx, nsp, M=13, features=63, scale=False, Gy=None):
+    t1 = torch.from_numpy(np.ascontiguousarray(X1)).cuda()
+    t2 = torch.from_numpy(np.ascontiguousarray(X2)).cuda()
+    g = p.mcil(t1, t2, Gx, nsp, M=M, features=features, scale=scale, Gy=Gy, law="linear")
+    o = oracle.mcil(X1, X2, Gx, nsp, None, M, mask=features, scale=scale, Gy=Gy, law="linear")
+    torch.cuda.synchronize()
+    assert int(g["n_exact"]) >= 0
+    assert_same(g, o)
+    return g, o
+
+
+def test_linear_hand_example(p):
+    # on a line: set 1 = {0, 1}, set 2 = {3, 5, 6} -> R0 = 6, R_min = 2,
+    # M = 4: radii 5, 4, 3, 2 and counts 3, 2, 1, 0 for L2 and Linf (by hand)
+    X1 = np.array([[0.0, 0.0], [1.0, 0.0]], np.float32)
+    X2 = np.array([[3.0, 0.0], [5.0, 0.0], [6.0, 0.0]], np.float32)
+    g, _ = run_linear(p, X1, X2, 2, 1, M=4, features=0x03, Gy=1)
+    for a in range(2):
+        assert g["radii"][a].cpu().numpy().tolist() == [6.0, 5.0, 4.0, 3.0, 2.0]
+        assert g["counts"][a].cpu().numpy().tolist() == [3, 2, 1, 0]
+
+
+@pytest.mark.parametrize("n1,n2,Gy,Gx,nsp", [(3, 5, 4, 4, 2), (20, 17, 32, 32, 2), (64, 64, 64, 64, 1),
+                                             (7, 9, 1, 64, 2), (33, 40, 8, 32, 2), (130, 65, 16, 16, 1)])
+@pytest.mark.parametrize("scale", [False, True])
+def test_linear_law_bit_exact(p, n1, n2, Gy, Gx, nsp, scale):
+    X = W.cosine_patterns(n1 + n2, Gx, nsp, 71 + Gx + n1, amp=1.2, offset=0.7)
+    X = np.ascontiguousarray(X.reshape(n1 + n2, nsp, Gx, Gx)[:, :, :Gy, :].reshape(n1 + n2, -1))
+    run_linear(p, X[:n1], X[n1:], Gx, nsp, M=13, scale=scale, Gy=Gy)
+
+
+def test_linear_near_duplicates(p):
+    # set 2 holds slightly perturbed copies of set 1: the smallest values
+    # are tiny differences, where the tensor-core interval is widest, so the
+    # minimum goes through the re-bounding and the canonical order
+    rng = np.random.default_rng(42)
+    G, n = 32, 40
+    X1 = (rng.standard_normal((n, G * G)) * 0.5 + 1.0).astype(np.float32)
+    X2 = X1 + (rng.standard_normal((n, G * G)) * 1e-4).astype(np.float32)
+    g, o = run_linear(p, X1, X2, G, 1, M=16)
+    assert o["radii"][0, -1] < 0.1 * o["radii"][0, 0]
+    assert int(g["n_exact"]) >= 1
+
+
+def test_linear_degenerate_cases(p):
+    rng = np.random.default_rng(9)
+    G = 8
+    # a single pair: R0 = R_min, every radius R0, nothing below it
+    X1 = rng.standard_normal((1, G * G)).astype(np.float32)
+    X2 = rng.standard_normal((1, G * G)).astype(np.float32)
+    g, _ = run_linear(p, X1, X2, G, 1, M=5)
+    assert (g["counts"].cpu().numpy() == 0).all()
+    # a pattern in both sets: every feature's minimum is 0
+    X1 = rng.standard_normal((6, G * G)).astype(np.float32)
+    X2 = np.concatenate([rng.standard_normal((5, G * G)).astype(np.float32), X1[2:3]])
+    g, o = run_linear(p, X1, X2, G, 1, M=13)
+    # ties at the minimum: two pairs at the same smallest values
+    X1 = np.zeros((2, G * G), np.float32)
+    X1[1] += 10.0
+    X2 = np.stack([X1[0] + 1.0, X1[1] + 1.0, X1[0] + 5.0]).astype(np.float32)
+    run_linear(p, X1, X2, G, 1, M=7)
+
+
+def test_linear_rdode_patterns(p):
+    # Table 1's pairing: the RD-ODE patterns at t = 50 with the linear law,
+    # L2/Linf of both species and the W norms of w, bit-exact
+    cfg = W.config("c7")
+    gd = dict(cfg["groups"][0])
+    gd["n_real"] = 48
+    sim = p.Simulation([p.Group.from_dict(gd)])
+    sim.integrate_rkc(1e-3, rtol=cfg["rkc_tol"], atol=cfg["rkc_tol"])
+    assert sim.sync_status() == 0
+    F = sim.group_fields(0)
+    a, c, bins = p.mcil_rdode(F, 24, M=cfg["M"], law="linear")
+    Fn = F.cpu().numpy()
+    both = Fn.reshape(48, -1)
+    w = np.ascontiguousarray(Fn[:, 1, :])
+    oa = oracle.mcil(both[:24], both[24:], 64, 2, None, cfg["M"], mask=0x03, Gy=1, law="linear")
+    oc = oracle.mcil(w[:24], w[24:], 64, 1, None, cfg["M"], mask=0x3C, Gy=1, law="linear")
+    assert_same(a, oa)
+    assert_same(c, oc)
+    assert bins.shape == (6, 24, 24)
