@@ -100,6 +100,9 @@ def test_variant_shapes_are_valid_tilings(libpath):
             NX, NY = G // TX, G // TY
             assert NX <= 32 and NX & (NX - 1) == 0 and NX % 2 == 0
             assert (NX * NY) % 32 == 0 and NX * NY <= 1024
+            # the double-buffered halo ring of the variant fits one CTA
+            ring = {0: 2 * 2 * 2 * NY * G * 4, 1: 2 * 2 * NY * G * 8}[packed]
+            assert ring <= 227 * 1024, (G, v, ring)
         assert p.variant_shape(G, 0)[0] == 0
     sh = (ctypes.c_int32 * 3)()
     assert p.lib().rd_variant_shape(48, 0, sh) == 1
