@@ -457,7 +457,7 @@ rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1,
  *   f = |L^-1 (y_obs - mu)_act|^2, loglik = -(f + logdet + M_act log 2pi)/2
  *   (f and loglik NaN when d_y_obs is NULL);
  * status[p] = RD_OK or RD_ERR_NOT_PD (active block not positive definite).
- * Limits: n1 + n2 <= 49152; 1 <= M <= 32; 2 <= T;
+ * Limits: n1 + n2 <= 49152; 1 <= M <= 32; 2 <= T <= 65535; n_problems <= 65535;
  * (T n1 n2)^2 < 4.6e18.  Violations return RD_ERR_INVALID_ARG. */
 rd_status synlik_stats(const uint8_t *d_bins, int64_t n1, int64_t n2, int32_t M,
                        int32_t T, uint64_t seed, int32_t n_problems,

@@ -5,10 +5,10 @@
 // covariance of the CIL vector, Alg. 1 step 3; cost eq. (cil:CF) and
 // eq. (cil:CF_synth), reported with the Gaussian log-likelihood.
 //
-// bootstrap_kernel: one CTA per (resample, problem).  Indices come from the
-//   counter-based SplitMix64 stream, are staged in shared memory, and the
-//   per-radius counts of the resampled pair set are accumulated with warp
-//   ballot + popc over the stored bin indices K_ij.
+// bootstrap_kernel: one CTA per (row block, resample, problem).  Indices
+//   come from the counter-based SplitMix64 stream; the per-radius counts of
+//   the resampled pair set are accumulated with warp ballot + popc over the
+//   stored bin indices K_ij and summed with integer atomics.
 // stats_kernel: one CTA per problem.  Mean and covariance are the exact
 //   rationals of the integer counts, formed with integer sums and rounded
 //   once; Cholesky of the active block column by column (rows of a column in
@@ -23,49 +23,53 @@ __device__ __forceinline__ uint32_t lemire_index(uint64_t seed, uint64_t ctr, ui
     return (uint32_t)__umul64hi(splitmix64_at(seed, ctr), (uint64_t)n);
 }
 
-__global__ void bootstrap_kernel(const uint8_t *__restrict__ bins, int nf, int n1, int n2, int M, int T,
-                                 uint64_t seed, int64_t *__restrict__ Y) {
-    extern __shared__ int32_t sidx[];
-    __shared__ unsigned long long cnt[32];
-    const int t = blockIdx.x, p = blockIdx.y;
+// One CTA per (row block, resample, problem).  The resampled column indices
+// J (n2 of them, < 65536) are staged in shared memory; each warp walks the
+// resampled rows a of its block (I[a] drawn per row, warp-uniform) and the
+// columns in steps of 32, gathering K = bins[I[a]][J[b]] (the source row is
+// reused from L1) and counting K > k for every radius with one ballot and
+// popc per 32 pairs.  Counts meet in shared memory, then in Y (int64)
+// through integer atomics, so the result does not depend on the order.
+__global__ void __launch_bounds__(256) bootstrap_kernel(const uint8_t *__restrict__ bins, int nf, int n1, int n2,
+                                                        int M, int T, uint64_t seed, int RB,
+                                                        unsigned long long *__restrict__ Y) {
+    extern __shared__ uint16_t sJ[];
+    __shared__ unsigned int cnt[SYN_MAX_M];
+    const int rb = blockIdx.x, t = blockIdx.y, p = blockIdx.z;
     const uint64_t sp = seed + (uint64_t)p;
-    int32_t *I = sidx, *J = sidx + n1;
-    for (int a = threadIdx.x; a < n1; a += blockDim.x)
-        I[a] = (int32_t)lemire_index(sp, (((uint64_t)t * 2u + 0u) << 32) | (uint64_t)a, (uint32_t)n1);
     for (int b = threadIdx.x; b < n2; b += blockDim.x)
-        J[b] = (int32_t)lemire_index(sp, (((uint64_t)t * 2u + 1u) << 32) | (uint64_t)b, (uint32_t)n2);
-    const int64_t np = (int64_t)n1 * n2;
-    const int lane = threadIdx.x & 31;
+        sJ[b] = (uint16_t)lemire_index(sp, (((uint64_t)t * 2u + 1u) << 32) | (uint64_t)b, (uint32_t)n2);
     const int Mt = nf * M;
-    // one resampled pair of index sets, counted under every feature
+    for (int k = threadIdx.x; k < Mt; k += blockDim.x) cnt[k] = 0u;
+    __syncthreads();
+    const int a0 = (int)((int64_t)rb * n1 / RB), a1 = (int)((int64_t)(rb + 1) * n1 / RB);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int64_t np = (int64_t)n1 * n2;
     for (int f = 0; f < nf; ++f) {
-        if (threadIdx.x < 32) cnt[threadIdx.x] = 0ull;
-        __syncthreads();
         const uint8_t *B = bins + ((int64_t)p * nf + f) * np;
-        unsigned long long c[32];
+        unsigned int c[32];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) c[k] = 0ull;
-        // stride so that every warp iteration is uniform (full-warp ballots)
-        for (int64_t base = (int64_t)(threadIdx.x & ~31); base < np; base += blockDim.x) {
-            int64_t q = base + lane;
-            int K = 0;
-            if (q < np) {
-                int a = (int)(q / n2), b = (int)(q - (int64_t)a * n2);
-                K = B[(int64_t)I[a] * n2 + J[b]];
+        for (int k = 0; k < 32; ++k) c[k] = 0u;
+        for (int a = a0 + warp; a < a1; a += nw) {
+            const uint32_t r = lemire_index(sp, (((uint64_t)t * 2u + 0u) << 32) | (uint64_t)a, (uint32_t)n1);
+            const uint8_t *row = B + (int64_t)r * n2;
+            for (int b0 = 0; b0 < n2; b0 += 32) {
+                const int b = b0 + lane;
+                const int K = b < n2 ? (int)__ldg(row + sJ[b]) : 0;
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (k < M) c[k] += (unsigned)__popc(__ballot_sync(0xffffffffu, K > k));
             }
-#pragma unroll
-            for (int k = 0; k < 32; ++k)
-                if (k < M) c[k] += (unsigned long long)__popc(__ballot_sync(0xffffffffu, K > k));
         }
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < 32; ++k)
-                if (k < M && c[k]) atomicAdd(&cnt[k], c[k]);
+                if (k < M && c[k]) atomicAdd(&cnt[f * M + k], c[k]);
         }
-        __syncthreads();
-        if ((int)threadIdx.x < M) Y[((int64_t)p * T + t) * Mt + f * M + threadIdx.x] = (int64_t)cnt[threadIdx.x];
-        __syncthreads();
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < Mt; k += blockDim.x)
+        if (cnt[k]) atomicAdd(&Y[((int64_t)p * T + t) * Mt + k], (unsigned long long)cnt[k]);
 }
 
 __global__ void stats_kernel(const int64_t *__restrict__ Yall, int M, int T, int64_t np,
@@ -191,14 +195,16 @@ extern "C" rd_status synlik_stats_multi(const uint8_t *d_bins, int32_t n_feat, i
                                         uint8_t *d_active, int32_t *d_status, void *stream) {
     if (!d_bins || !d_Y || !d_mu || !d_cov || !d_chol || !d_scalars || !d_active || !d_status)
         return RD_ERR_INVALID_ARG;
-    if (n1 < 1 || n2 < 1 || n1 + n2 > 49152 || M < 1 || M > 32 || T < 2 || n_problems < 1 ||
+    if (n1 < 1 || n2 < 1 || n1 + n2 > 49152 || M < 1 || M > 32 || T < 2 || T > 65535 || n_problems < 1 ||
         n_problems > 65535 || n_feat < 1 || n_feat * M > SYN_MAX_M)
         return RD_ERR_INVALID_ARG;
     // the exact covariance numerators T P_kl - S_k S_l stay in 64 bits
     double np = (double)n1 * (double)n2;
     if ((double)T * (double)T * np * np >= 4.6e18) return RD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    size_t smem = (size_t)(n1 + n2) * sizeof(int32_t);
+    const int Mt0 = n_feat * M;
+    RD_CUDA_TRY(cudaMemsetAsync(d_Y, 0, sizeof(int64_t) * (size_t)n_problems * T * Mt0, s));
+    const size_t smem = (size_t)n2 * sizeof(uint16_t);
     if (smem > 48 * 1024) {
         static size_t set = 0;
         if (smem > set) {
@@ -207,8 +213,14 @@ extern "C" rd_status synlik_stats_multi(const uint8_t *d_bins, int32_t n_feat, i
             set = smem;
         }
     }
-    dim3 g((unsigned)T, (unsigned)n_problems);
-    bootstrap_kernel<<<g, 256, smem, s>>>(d_bins, n_feat, (int)n1, (int)n2, M, T, seed, d_Y);
+    // row blocks per resample: about eight CTAs of 256 threads per SM over
+    // the whole launch, at least one row per warp
+    int64_t RB = (8 * 148 + (int64_t)T * n_problems - 1) / ((int64_t)T * n_problems);
+    if (RB > (n1 + 7) / 8) RB = (n1 + 7) / 8;
+    if (RB < 1) RB = 1;
+    dim3 g((unsigned)RB, (unsigned)T, (unsigned)n_problems);
+    bootstrap_kernel<<<g, 256, smem, s>>>(d_bins, n_feat, (int)n1, (int)n2, M, T, seed, (int)RB,
+                                         reinterpret_cast<unsigned long long *>(d_Y));
     note_launch();
     const int Mt = n_feat * M;
     const size_t smem2 = sizeof(double) * ((size_t)Mt + 2 * (size_t)Mt * Mt) + sizeof(long long) * Mt +

@@ -86,3 +86,17 @@ def test_identity_like_counts_are_resample_invariant_when_constant(p):
     assert int(s["status"]) == 0 and int(s["m_active"]) == 0
     assert float(s["logdet"]) == 0.0 and float(s["f"]) == 0.0
     assert torch.all(s["Y"] == 72)
+
+
+@pytest.mark.parametrize("n1,n2,M,T", [(1000, 1000, 16, 40), (1, 300, 8, 20), (300, 1, 8, 20),
+                                       (1024, 33, 13, 64), (5, 2049, 32, 9)])
+def test_bootstrap_counts_large_and_ragged(p, n1, n2, M, T):
+    # the paper's SCIL scale (N_syn = 1000 patterns, Sec. 4.2) and one-row /
+    # one-column sets; bins drawn directly (every value 0..M), counts exact
+    rng = np.random.default_rng(n1 * 31 + n2)
+    bins = rng.integers(0, M + 1, (n1, n2)).astype(np.uint8)
+    so = oracle.synlik(bins, M, T, 0xB00 + n1)
+    s = p.synlik(torch.from_numpy(bins).cuda(), M, T, 0xB00 + n1)
+    assert np.array_equal(s["Y"].cpu().numpy(), so["Y"])
+    assert np.array_equal(s["mu"].cpu().numpy(), so["mu"])
+    assert np.array_equal(s["cov"].cpu().numpy(), so["cov"])
