@@ -179,7 +179,8 @@ void orc_resample_counts(const uint8_t *bins, int64_t n1, int64_t n2, int M,
         for (int64_t a = 0; a < n1; ++a)
             for (int64_t b = 0; b < n2; ++b) {
                 int K = bins[(int64_t)I[(int64_t)t * n1 + a] * n2 + J[(int64_t)t * n2 + b]];
-                for (int k = 0; k < K; ++k) y[k] += 1;
+                /* y[k-1] counts [K >= k] for k = 1..M only */
+                for (int k = 0; k < K && k < M; ++k) y[k] += 1;
             }
     }
 }

@@ -300,3 +300,15 @@ def test_linear_radii_span_max_to_min():
         # equal steps
         steps = -np.diff(np.concatenate([[R0], r]))
         assert np.allclose(steps, (R0 - rmin) / M, rtol=1e-12)
+
+
+def test_bins_above_M_count_under_every_radius():
+    # Y[t][k-1] = #{pairs : K >= k}, k = 1..M: a bin above M counts under all
+    # M radii and nothing beyond them
+    bins = np.full((3, 4), 9, np.uint8)
+    bins[0, 0] = 2
+    so = oracle.synlik(bins, 4, 5, 11)
+    I, J = oracle.bootstrap_indices(11, 5, 3, 4)
+    for t in range(5):
+        n00 = sum(1 for a in I[t] for b in J[t] if a == 0 and b == 0)
+        assert so["Y"][t].tolist() == [12, 12, 12 - n00, 12 - n00]
