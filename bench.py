@@ -276,7 +276,7 @@ def run_ours(args, rank, world, local_rank):
             for (X1, X2), out in zip(pipe.views, pipe.cil_out):
                 p.cil(X1, X2, b=b, M=M, work=pipe.work, out=out)
             e[3].record(stream)
-            p.synlik(pipe.bins, M, T, pipe.seed, y_obs=pipe.C, out=pipe.stats)
+            p.synlik(pipe.bins, M, T, pipe.seed, y_obs=pipe.C, out=pipe.stats, work=pipe.syn_work)
             e[4].record(stream)
         torch.cuda.synchronize()
         clk.end()

@@ -480,6 +480,32 @@ rd_status synlik_stats_multi(const uint8_t *d_bins, int32_t n_feat, int64_t n1, 
                              double *d_chol, double *d_scalars, uint8_t *d_active,
                              int32_t *d_status, void *stream);
 
+/* synlik_workspace_size / synlik_stats_ws — synlik_stats_multi with a
+ * caller workspace (d_work, 256-byte aligned, synlik_workspace_size bytes),
+ * which lets the bootstrap counts run on the tensor cores.  Same arguments,
+ * definitions, outputs and limits as synlik_stats_multi; Y is identical.
+ * Per resample the counts are the bilinear form
+ *   Y[t][k-1] = sum_i c1[i] sum_j [K_ij >= k] c2[j]
+ * with c1, c2 the multiplicities of the drawn indices (Alg. 5 step 2.1,
+ * Alg. 6 steps 2.1-2.2): a product of the 0/1 matrices [K >= k] with the
+ * multiplicities on tcgen05 (bf16 operands, FP32 accumulation; every value
+ * is an integer below 2^24, so it is exact), then integer sums.  A
+ * multiplicity above 256 (bf16's exact integer range; not expected in
+ * practice) makes the call count with the SIMT kernel of
+ * synlik_stats_multi instead, and so do problems under 2^22 resampled
+ * pairs (n1 n2 T; synlik_set_tc_min_pairs changes the bound, process-wide,
+ * a negative value restores it), where that kernel is faster.  status[p] =
+ * RD_ERR_TIMEOUT if a bounded wait of the tensor-core stage gave up
+ * (outputs invalid). */
+rd_status synlik_workspace_size(int64_t n1, int64_t n2, int32_t M, int32_t T, int32_t n_feat,
+                                int32_t n_problems, size_t *bytes);
+void synlik_set_tc_min_pairs(int64_t n);
+rd_status synlik_stats_ws(const uint8_t *d_bins, int32_t n_feat, int64_t n1, int64_t n2,
+                          int32_t M, int32_t T, uint64_t seed, int32_t n_problems,
+                          const double *d_y_obs, int64_t *d_Y, double *d_mu, double *d_cov,
+                          double *d_chol, double *d_scalars, uint8_t *d_active,
+                          int32_t *d_status, void *d_work, size_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Multi-feature correlation integral (Sec. 3.1, Alg. 2 step 2.2; min-max
  * scaled data, Sec. 4).

@@ -72,6 +72,10 @@ _SIGS = {
                             _vp, _vp, _vp]),
     "synlik_stats_multi": (_i32, [_vp, _i32, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp,
                                   _vp, _vp, _vp, _vp]),
+    "synlik_workspace_size": (_i32, [_i64, _i64, _i32, _i32, _i32, _i32, C.POINTER(_sz)]),
+    "synlik_set_tc_min_pairs": (None, [_i64]),
+    "synlik_stats_ws": (_i32, [_vp, _i32, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
+                               _vp, _vp, _vp, _sz, _vp]),
     "mcil_workspace_size": (_i32, [_i64, _i64, _i32, _i32, _i32, _i32, _i32, C.POINTER(_sz)]),
     "mcil_features": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _dbl, _i32, _vp, _vp,
                              _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -423,10 +427,20 @@ def synlik_outputs(P, M, T, device):
             "status": torch.empty(P, dtype=torch.int32, device=dev)}
 
 
-def synlik(bins, M, T, seed, y_obs=None, out=None, n_feat=1):
+def synlik_workspace(n1, n2, M, T, n_feat=1, n_problems=1, device="cuda"):
+    """Workspace of synlik_stats_ws (tensor-core bootstrap counts)."""
+    sz = _sz(0)
+    _check("synlik_workspace_size", lib().synlik_workspace_size(int(n1), int(n2), int(M), int(T), int(n_feat),
+                                                                int(n_problems), C.byref(sz)))
+    return torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=device)
+
+
+def synlik(bins, M, T, seed, y_obs=None, out=None, n_feat=1, work=None, simt=False):
     """Bootstrap statistics of bins [P, n1, n2] (or [n1, n2]) uint8; with
     n_feat > 1, bins [P, n_feat, n1, n2] (or [n_feat, n1, n2]) of a
-    concatenated feature vector (n_feat * M components)."""
+    concatenated feature vector (n_feat * M components).  The counts run on
+    the tensor cores (synlik_stats_ws, workspace `work` or a fresh one);
+    simt=True takes the SIMT kernel (synlik_stats_multi) instead."""
     squeeze = bins.dim() == (2 if n_feat == 1 else 3)
     if squeeze:
         bins = bins.unsqueeze(0)
@@ -445,10 +459,18 @@ def synlik(bins, M, T, seed, y_obs=None, out=None, n_feat=1):
             yo = yo.to(device=dev, dtype=torch.float64).contiguous()   # marshalling only
         if yo.numel() != P * Mt:
             raise ValueError("y_obs must hold P x n_feat*M values")
-    _check("synlik_stats_multi", lib().synlik_stats_multi(_ptr(bins), int(n_feat), n1, n2, int(M), int(T),
-                                                          int(seed) & 0xFFFFFFFFFFFFFFFF, P, _ptr(yo), _ptr(Y),
-                                                          _ptr(mu), _ptr(cov), _ptr(chol), _ptr(sc), _ptr(act),
-                                                          _ptr(st), _stream()))
+    if simt:
+        _check("synlik_stats_multi", lib().synlik_stats_multi(_ptr(bins), int(n_feat), n1, n2, int(M), int(T),
+                                                              int(seed) & 0xFFFFFFFFFFFFFFFF, P, _ptr(yo),
+                                                              _ptr(Y), _ptr(mu), _ptr(cov), _ptr(chol), _ptr(sc),
+                                                              _ptr(act), _ptr(st), _stream()))
+    else:
+        if work is None:
+            work = synlik_workspace(n1, n2, M, T, n_feat, P, dev)
+        _check("synlik_stats_ws", lib().synlik_stats_ws(_ptr(bins), int(n_feat), n1, n2, int(M), int(T),
+                                                        int(seed) & 0xFFFFFFFFFFFFFFFF, P, _ptr(yo), _ptr(Y),
+                                                        _ptr(mu), _ptr(cov), _ptr(chol), _ptr(sc), _ptr(act),
+                                                        _ptr(st), _ptr(work), work.numel(), _stream()))
     out = {"Y": Y, "mu": mu, "cov": cov, "chol": chol, "scalars": sc, "logdet": sc[:, 0], "f": sc[:, 1],
            "loglik": sc[:, 2], "m_active": sc[:, 3], "active": act, "status": st}
     if squeeze:
@@ -568,6 +590,7 @@ class Pipeline:
                          "C": self.C[i], "n_rechecked": torch.zeros(1, dtype=torch.int64, device=self.dev)}
                         for i in range(P)]
         self.stats = synlik_outputs(P, M, T, self.dev)
+        self.syn_work = synlik_workspace(self.n1, self.n2, M, T, 1, P, self.dev)
         self.residual = torch.empty((self.sim.n_real_total, 2), dtype=torch.float64, device=self.dev)
         dmax = max(x.shape[1] for x, _ in self.views)
         self.work, self.work_bytes = _workspace(self.n1, self.n2, dmax, self.dev)
@@ -586,7 +609,7 @@ class Pipeline:
         fn = "cil_features_linear" if self.law == "linear" else "cil_features"
         for (X1, X2), out in zip(self.views, self.cil_out):
             _cil_call(fn, X1, X2, self.b, self.M, None, self.work, out)
-        synlik(self.bins, self.M, self.T, self.seed, y_obs=self.C, out=self.stats)
+        synlik(self.bins, self.M, self.T, self.seed, y_obs=self.C, out=self.stats, work=self.syn_work)
 
     def capture(self):
         """Record one pass (from the initial state) as a CUDA graph."""

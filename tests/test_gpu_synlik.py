@@ -17,6 +17,14 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture
+def tc_all(p):
+    """Every problem size through the tensor-core bootstrap counts."""
+    p.lib().synlik_set_tc_min_pairs(0)
+    yield
+    p.lib().synlik_set_tc_min_pairs(-1)
+
+
 @pytest.fixture(scope="module")
 def p():
     import __graft_entry__
@@ -33,13 +41,18 @@ def oracle_bins(n1, n2, d, M, b, seed):
 
 @pytest.mark.parametrize("n1,n2,M,T", [(16, 16, 8, 50), (64, 64, 16, 200), (37, 90, 12, 33),
                                        (256, 256, 16, 200)])
-def test_bootstrap_and_stats_match(p, n1, n2, M, T):
+@pytest.mark.parametrize("force_tc", [False, True])
+def test_bootstrap_and_stats_match(p, n1, n2, M, T, force_tc):
     o = oracle_bins(n1, n2, 64, M, 1.08, n1 * 7 + n2)
     seed = 0x5EED + n1
     y_obs = o["counts"] / float(n1 * n2)
     so = oracle.synlik(o["bins"], M, T, seed, y_obs=y_obs)
     bins = torch.from_numpy(o["bins"]).cuda()
-    s = p.synlik(bins, M, T, seed, y_obs=torch.from_numpy(y_obs))
+    p.lib().synlik_set_tc_min_pairs(0 if force_tc else -1)
+    try:
+        s = p.synlik(bins, M, T, seed, y_obs=torch.from_numpy(y_obs))
+    finally:
+        p.lib().synlik_set_tc_min_pairs(-1)
     assert np.array_equal(s["Y"].cpu().numpy(), so["Y"])
     assert np.array_equal(s["mu"].cpu().numpy(), so["mu"])
     assert np.array_equal(s["cov"].cpu().numpy(), so["cov"])
@@ -90,13 +103,43 @@ def test_identity_like_counts_are_resample_invariant_when_constant(p):
 
 @pytest.mark.parametrize("n1,n2,M,T", [(1000, 1000, 16, 40), (1, 300, 8, 20), (300, 1, 8, 20),
                                        (1024, 33, 13, 64), (5, 2049, 32, 9)])
-def test_bootstrap_counts_large_and_ragged(p, n1, n2, M, T):
+@pytest.mark.parametrize("simt", [False, True])
+def test_bootstrap_counts_large_and_ragged(p, tc_all, n1, n2, M, T, simt):
     # the paper's SCIL scale (N_syn = 1000 patterns, Sec. 4.2) and one-row /
     # one-column sets; bins drawn directly (every value 0..M), counts exact
+    # on the tensor cores and with the SIMT kernel
     rng = np.random.default_rng(n1 * 31 + n2)
     bins = rng.integers(0, M + 1, (n1, n2)).astype(np.uint8)
     so = oracle.synlik(bins, M, T, 0xB00 + n1)
-    s = p.synlik(torch.from_numpy(bins).cuda(), M, T, 0xB00 + n1)
+    s = p.synlik(torch.from_numpy(bins).cuda(), M, T, 0xB00 + n1, simt=simt)
     assert np.array_equal(s["Y"].cpu().numpy(), so["Y"])
     assert np.array_equal(s["mu"].cpu().numpy(), so["mu"])
     assert np.array_equal(s["cov"].cpu().numpy(), so["cov"])
+
+
+@pytest.mark.parametrize("n1,n2,M,T,nf", [(50, 950, 13, 1000, 6), (129, 65, 16, 257, 1), (3, 7, 32, 2, 2),
+                                          (200, 200, 5, 33, 3)])
+def test_bootstrap_tensor_core_shapes(p, tc_all, n1, n2, M, T, nf):
+    # Alg. 6 at the paper's SCIL setting (N_set = 50 against the other 950 of
+    # N_syn = 1000, n_CIL = 1000 resamples, six features), more than one
+    # 256-resample tile, tails of every tile dimension; values above M in
+    # the bins count under every radius
+    rng = np.random.default_rng(n1 + 7 * n2 + T)
+    bins = rng.integers(0, M + 3, (nf, n1, n2)).astype(np.uint8)
+    so = oracle.synlik_multi(bins, M, T, 0xC11 + T) if nf > 1 else oracle.synlik(bins[0], M, T, 0xC11 + T)
+    tb = torch.from_numpy(bins).cuda()
+    s = p.synlik(tb if nf > 1 else tb[0], M, T, 0xC11 + T, n_feat=nf)
+    assert np.array_equal(s["Y"].cpu().numpy(), so["Y"])
+    assert np.array_equal(s["cov"].cpu().numpy(), so["cov"])
+    t = p.synlik(tb if nf > 1 else tb[0], M, T, 0xC11 + T, n_feat=nf, simt=True)
+    assert torch.equal(t["Y"], s["Y"])
+
+
+def test_bootstrap_tensor_core_batched_problems(p, tc_all):
+    # several problems in one call (the c4 batch shape), against the SIMT path
+    rng = np.random.default_rng(3)
+    bins = torch.from_numpy(rng.integers(0, 17, (9, 64, 64)).astype(np.uint8)).cuda()
+    s = p.synlik(bins, 16, 200, 12345)
+    t = p.synlik(bins, 16, 200, 12345, simt=True)
+    assert torch.equal(s["Y"], t["Y"])
+    assert torch.equal(s["cov"], t["cov"])
