@@ -420,6 +420,7 @@ def run_ours(args, rank, world, local_rank):
         out["adjoint"] = adjoint_c5(p, torch, dev, stream)
     if args.mcil and rank == 0:
         out["mcil"] = mcil_bench(p, torch, dev, stream)
+        out["scil"] = scil_bench(p, torch, dev, stream)
     if args.stream and rank == 0:
         out["stream"] = stream_bench(p, torch, dev, stream, pk, src)
     if args.rkc and rank == 0:
@@ -737,6 +738,45 @@ def mcil_bench(p, torch, dev, stream):
     return res
 
 
+def scil_bench(p, torch, dev, stream):
+    """The synthetic-likelihood cost after the simulations, at the paper's
+    SCIL scale (Alg. 6 with bootstrapping, Sec. 5.1: N_syn = 1000 patterns,
+    N_set = 50 of them against the other 950, n_CIL = 1000 resampled set
+    pairs, the six features): multi-feature CIL of GM-sized fields (2 species
+    of 128x128, synthetic cosine modes), then bootstrap counts of the
+    96-component vector and its statistics (tensor-core and SIMT counts)."""
+    n_syn, n_set, G, nsp, M, T = 1000, 50, 128, 2, 16, 1000
+    X = torch.from_numpy(W.cosine_patterns(n_syn, G, nsp, 93, amp=0.8, offset=2.0)).to(dev)
+    X1, X2 = X[:n_set], X[n_set:]
+    n2 = n_syn - n_set
+    work = p.mcil_workspace(n_set, n2, G, nsp, 63, False, M, dev)
+    swork = p.synlik_workspace(n_set, n2, M, T, 6, 1, dev)
+    sout = p.synlik_outputs(1, 6 * M, T, dev)
+    r = p.mcil(X1, X2, G, nsp, b=1.3, M=M, work=work)
+    bins = r["bins"].unsqueeze(0).contiguous()
+    yobs = r["C"].unsqueeze(0).contiguous()
+    p.synlik(bins, M, T, 2203, y_obs=yobs, n_feat=6, work=swork, out=sout)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_mcil = timed(lambda: p.mcil(X1, X2, G, nsp, b=1.3, M=M, work=work))
+    t_syn = timed(lambda: p.synlik(bins, M, T, 2203, y_obs=yobs, n_feat=6, work=swork, out=sout))
+    Y_tc = sout["Y"].clone()
+    t_simt = timed(lambda: p.synlik(bins, M, T, 2203, y_obs=yobs, n_feat=6, out=sout, simt=True), reps=2)
+    return {"n_syn": n_syn, "n_set": n_set, "d": nsp * G * G, "features": 6, "M": M, "n_cil": T,
+            "mcil_ms": t_mcil, "bootstrap_stats_ms": t_syn, "bootstrap_stats_simt_ms": t_simt,
+            "same_counts": bool(torch.equal(Y_tc, sout["Y"])), "status": int(sout["status"][0]),
+            "cost_f": float(sout["scalars"][0, 1]), "total_ms": t_mcil + t_syn}
+
+
 def adjoint_c5(p, torch, dev, stream):
     """Smoothed-CIL gradient (discrete adjoint with sqrt(N) checkpoints) on
     the FHN 64x64 adjoint workload: 32 realisations (2 x 16), 5000 steps,
@@ -878,7 +918,8 @@ def main():
         B.build()
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)
-        print(json.dumps(mcil_bench(p, torch, dev, torch.cuda.current_stream(dev))))
+        st_ = torch.cuda.current_stream(dev)
+        print(json.dumps({"mcil": mcil_bench(p, torch, dev, st_), "scil": scil_bench(p, torch, dev, st_)}))
         return
     if args.rkc_only:
         import torch

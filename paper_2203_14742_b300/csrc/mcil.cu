@@ -169,58 +169,62 @@ __global__ void minmax_kernel(const float *__restrict__ X, int64_t ld, int64_t c
 // ---------------------------------------------------------------------------
 __global__ void fd_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int Gy, int Gx, int nsp,
                           float *__restrict__ Ax, float *__restrict__ Ay) {
+    // one grid row r = (pattern i, species sp, row y) at a time; threads
+    // along x (coalesced reads of rows y and y + 1)
     const int64_t cex = (int64_t)Gy * (Gx - 1), cey = (int64_t)(Gy - 1) * Gx, cells = (int64_t)Gy * Gx;
-    // Dx: row y, column c2 < Gx-1
-    const int64_t tx_ = n * nsp * cex;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tx_; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t is = e / cex, c = e - is * cex;
+    const int64_t nrows = n * nsp * Gy;
+    for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int64_t is = r / Gy;
+        const int y = (int)(r - is * Gy);
         const int64_t i = is / nsp;
         const int sp = (int)(is - i * nsp);
-        const float *x = X + i * ld + (int64_t)sp * cells;
-        const int y = (int)(c / (Gx - 1)), c2 = (int)(c - (int64_t)y * (Gx - 1));
-        Ax[e] = x[(int64_t)y * Gx + c2 + 1] - x[(int64_t)y * Gx + c2];
-    }
-    // Dy: row y < Gy-1, column c2
-    const int64_t ty_ = n * nsp * cey;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ty_; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t is = e / cey, c = e - is * cey;
-        const int64_t i = is / nsp;
-        const int sp = (int)(is - i * nsp);
-        const float *x = X + i * ld + (int64_t)sp * cells;
-        const int y = (int)(c / Gx), c2 = (int)(c - (int64_t)y * Gx);
-        Ay[e] = x[(int64_t)(y + 1) * Gx + c2] - x[(int64_t)y * Gx + c2];
+        const float *x = X + i * ld + (int64_t)sp * cells + (int64_t)y * Gx;
+        float *dx = Ax + is * cex + (int64_t)y * (Gx - 1);
+        for (int c = threadIdx.x; c < Gx - 1; c += blockDim.x) dx[c] = x[c + 1] - x[c];
+        if (y < Gy - 1) {
+            float *dy = Ay + is * cey + (int64_t)y * Gx;
+            for (int c = threadIdx.x; c < Gx; c += blockDim.x) dy[c] = x[Gx + c] - x[c];
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// 2. max |a - b| of every pair, FP32: 128 x 128 pairs per CTA, 8 x 8 per
-//    thread (rows ty + 16a, columns tx + 16c, so the shared-memory reads of
-//    a warp are broadcasts or 16 consecutive words), 32-column slices of
-//    both sets in shared memory, and a split of K over blockIdx.z whose
-//    partial maxima meet in atomicMax on the FP32 bit patterns (non-negative
-//    floats order like their bits; max is exact in any order)
+// 2. max |a - b| of every pair, FP32: 128 x 128 (or 64 x 256) pairs per
+//    CTA, 8 x 8 per thread, 32-column slices of both sets in shared memory,
+//    and a split of K over blockIdx.z whose partial maxima meet in atomicMax
+//    on the FP32 bit patterns (non-negative floats order like their bits;
+//    max is exact in any order)
 // ---------------------------------------------------------------------------
-constexpr int MX_T = 128, MX_K = 32;
+constexpr int MX_K = 32;
+// TA x TB pairs per CTA (TA = 128 or 64 set-1 rows; TB = 32768 / TA set-2
+// rows), 8 x 8 per thread: thread (ty, tx) takes rows ty + (TA/8) a and
+// columns tx + (TB/8) c, so the shared-memory reads of a warp are
+// broadcasts (rows) or consecutive words (columns)
+template <int TA>
 __global__ void __launch_bounds__(256) maxabs_kernel(const float *__restrict__ A, int64_t lda, int64_t n1,
                                                      const float *__restrict__ B, int64_t ldb, int64_t n2, int64_t d,
                                                      int64_t kch, float *__restrict__ out) {
-    __shared__ float sa[MX_K][MX_T + 1], sb[MX_K][MX_T + 1];
-    const int64_t i0 = (int64_t)blockIdx.y * MX_T, j0 = (int64_t)blockIdx.x * MX_T;
+    constexpr int TB = 16384 / TA, RY = TA / 8, RX = TB / 8;   // RY x RX = 256 threads
+    static_assert(RY * RX == 256, "thread grid");
+    __shared__ float sa[MX_K][TA + 1], sb[MX_K][TB + 1];
+    const int64_t i0 = (int64_t)blockIdx.y * TA, j0 = (int64_t)blockIdx.x * TB;
     const int64_t k_lo = (int64_t)blockIdx.z * kch, k_hi = min(d, k_lo + kch);
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int tx = threadIdx.x % RX, ty = threadIdx.x / RX;
     float m[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int c = 0; c < 8; ++c) m[a][c] = 0.f;
     for (int64_t k0 = k_lo; k0 < k_hi; k0 += MX_K) {
-        // 128 rows x 32 columns of each set, 16 values per thread; a warp
-        // reads 32 consecutive columns of one row
-        for (int e = threadIdx.x; e < MX_T * MX_K; e += 256) {
+        // a warp reads 32 consecutive columns of one row
+        for (int e = threadIdx.x; e < TA * MX_K; e += 256) {
             const int r = e / MX_K, kk = e - r * MX_K;
-            const int64_t k = k0 + kk;
-            const int64_t ia = i0 + r, jb = j0 + r;
+            const int64_t k = k0 + kk, ia = i0 + r;
             sa[kk][r] = (ia < n1 && k < k_hi) ? A[ia * lda + k] : 0.f;
+        }
+        for (int e = threadIdx.x; e < TB * MX_K; e += 256) {
+            const int r = e / MX_K, kk = e - r * MX_K;
+            const int64_t k = k0 + kk, jb = j0 + r;
             sb[kk][r] = (jb < n2 && k < k_hi) ? B[jb * ldb + k] : 0.f;
         }
         __syncthreads();
@@ -228,9 +232,9 @@ __global__ void __launch_bounds__(256) maxabs_kernel(const float *__restrict__ A
         for (int kk = 0; kk < MX_K; ++kk) {
             float av[8], bv[8];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) av[a] = sa[kk][ty + 16 * a];
+            for (int a = 0; a < 8; ++a) av[a] = sa[kk][ty + RY * a];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) bv[c] = sb[kk][tx + 16 * c];
+            for (int c = 0; c < 8; ++c) bv[c] = sb[kk][tx + RX * c];
 #pragma unroll
             for (int a = 0; a < 8; ++a)
 #pragma unroll
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(256) maxabs_kernel(const float *__restrict__ A
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int64_t i = i0 + ty + 16 * a, j = j0 + tx + 16 * c;
+            const int64_t i = i0 + ty + RY * a, j = j0 + tx + RX * c;
             if (i < n1 && j < n2 && m[a][c] > 0.f)
                 atomicMax(reinterpret_cast<unsigned int *>(out) + i * n2 + j, __float_as_uint(m[a][c]));
         }
@@ -728,9 +732,10 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
     }
     const bool deriv = (features & 0x3C) != 0;
     if (deriv) {
-        fd_kernel<<<4 * 148, 256, 0, s>>>(P1, l1, n1, Gy, Gx, n_species, w.Ax1, w.Ay1);
+        const int fdt = Gx >= 256 ? 256 : (Gx >= 128 ? 128 : 64);
+        fd_kernel<<<16 * 148, fdt, 0, s>>>(P1, l1, n1, Gy, Gx, n_species, w.Ax1, w.Ay1);
         note_launch();
-        fd_kernel<<<4 * 148, 256, 0, s>>>(P2, l2, n2, Gy, Gx, n_species, w.Ax2, w.Ay2);
+        fd_kernel<<<16 * 148, fdt, 0, s>>>(P2, l2, n2, Gy, Gx, n_species, w.Ax2, w.Ay2);
         note_launch();
     }
     Arr3 A{};
@@ -753,16 +758,24 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
     const bool need_m0 = (features & 0x32) != 0, need_md = (features & 0x30) != 0;
     for (int a = 0; a < 3; ++a) {
         if ((a == 0 ? !need_m0 : !need_md) || A.d[a] == 0) continue;
-        // K chunks (multiples of 32, at least 64) for about two CTAs per SM
-        const int64_t tiles = ((n1 + MX_T - 1) / MX_T) * ((n2 + MX_T - 1) / MX_T);
+        // tile shape: 64 x 256 pairs when set 1 is small (less padding),
+        // else 128 x 128; K chunks (multiples of 32, at least 64) for about
+        // two CTAs per SM
+        const bool narrow = n1 <= 64;
+        const int64_t TA = narrow ? 64 : 128, TB = narrow ? 256 : 128;
+        const int64_t tiles = ((n1 + TA - 1) / TA) * ((n2 + TB - 1) / TB);
         const int64_t want = (2 * 148 + tiles - 1) / tiles;
         int64_t kch = (A.d[a] + want - 1) / want;
         kch = (kch + MX_K - 1) / MX_K * MX_K;
         if (kch < 2 * MX_K) kch = 2 * MX_K;
         const int64_t nk = (A.d[a] + kch - 1) / kch;
-        dim3 grid((unsigned)((n2 + MX_T - 1) / MX_T), (unsigned)((n1 + MX_T - 1) / MX_T), (unsigned)nk);
-        maxabs_kernel<<<grid, 256, 0, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2, A.d[a], kch,
-                                           w.mabs + a * np);
+        dim3 grid((unsigned)((n2 + TB - 1) / TB), (unsigned)((n1 + TA - 1) / TA), (unsigned)nk);
+        if (narrow)
+            maxabs_kernel<64><<<grid, 256, 0, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2, A.d[a], kch,
+                                                   w.mabs + a * np);
+        else
+            maxabs_kernel<128><<<grid, 256, 0, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2, A.d[a], kch,
+                                                    w.mabs + a * np);
         note_launch();
     }
     const double g = (double)(Gx - 1), h = 1.0 / g, h2 = 1.0 / (g * g);
