@@ -24,9 +24,10 @@
 //                       [i][t]
 //   bootstrap_tc_kernel one CTA per (problem, feature, 128-row tile,
 //                       N tile of resamples, group of radii, K segment):
-//                       per 64-column chunk the threads build the C2 tile
-//                       and the 0/1 tiles of the CTA's radii in 128-byte
-//                       swizzled shared memory (two stages), one thread
+//                       per 64-column chunk TMA brings the C2 tile (issued
+//                       one chunk ahead) and the threads build the 0/1
+//                       tiles of the CTA's radii, both in 128-byte swizzled
+//                       shared memory (two stages), one thread
 //                       issues tcgen05.mma (M = 128, N = resamples of the
 //                       tile, K = 16) into one TMEM accumulator per radius;
 //                       the epilogue reads Z back with tcgen05.ld,
@@ -36,7 +37,10 @@
 // If a multiplicity exceeds 256 (probability below 1e-500 per resample, but
 // possible) the tensor-core kernel does nothing and the SIMT bootstrap
 // kernel, launched after it, counts instead.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <mutex>
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -99,7 +103,7 @@ static BootWork boot_layout(const BootDims &d, void *base) {
     const int64_t P = d.P;
     w.BP = (uint8_t *)take((size_t)(P * d.nf * d.n1p * d.n2p));
     w.C2 = (uint16_t *)take(sizeof(uint16_t) * (size_t)(P * d.Tp * d.n2p));
-    w.C1T = (uint16_t *)take(sizeof(uint16_t) * (size_t)(P * d.n1p * d.Tp));
+    w.C1T = (uint16_t *)take(sizeof(uint16_t) * (size_t)(P * d.n1p * d.Tp) + 64);   // + the 32-value read past a row
     const size_t c0 = off;
     w.C1cnt = (uint32_t *)take(sizeof(uint32_t) * (size_t)(P * d.Tp * d.n1p));
     w.C2cnt = (uint32_t *)take(sizeof(uint32_t) * (size_t)(P * d.Tp * d.n2p));
@@ -180,14 +184,17 @@ __device__ __forceinline__ uint4 ge_flags(uint32_t w0, uint32_t w1, uint32_t add
 }
 
 __global__ void __launch_bounds__(BT_THREADS, 1)
-bootstrap_tc_kernel(BootWork w, int S, unsigned long long *__restrict__ Y, uint32_t spin) {
+bootstrap_tc_kernel(const __grid_constant__ CUtensorMap tm_c2, BootWork w, int S, unsigned long long *__restrict__ Y,
+                    uint32_t spin) {
     const BootDims &d = w.d;
     if (*(volatile uint32_t *)w.flag) return;   // the SIMT kernel counts instead
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int stage_bytes = d.KG * BT_A_BYTES + d.Tn * 128;
-    uint64_t *bar = (uint64_t *)(smem + 2 * stage_bytes);   // [2] stage consumed, [2] all done
-    uint32_t *tslot = (uint32_t *)(bar + 3);
+    // [0, 1] stage consumed (MMA commit), [2] all MMAs done, [3, 4] the stage's
+    // C2 tile landed (TMA)
+    uint64_t *bar = (uint64_t *)(smem + 2 * stage_bytes);
+    uint32_t *tslot = (uint32_t *)(bar + 5);
     __shared__ int sY[BT_KG_MAX * 256];
     __shared__ int s_fail;
 
@@ -210,9 +217,7 @@ bootstrap_tc_kernel(BootWork w, int S, unsigned long long *__restrict__ Y, uint3
 
     for (int e = tid; e < BT_KG_MAX * 256; e += BT_THREADS) sY[e] = 0;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init(&bar[2], 1);
+        for (int q = 0; q < 5; ++q) mbar_init(&bar[q], 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -229,26 +234,34 @@ bootstrap_tc_kernel(BootWork w, int S, unsigned long long *__restrict__ Y, uint3
 
     const int64_t i = (int64_t)mi * BT_ROWS + tid;   // this thread's row of the tile
     const uint8_t *brow = w.BP + (((int64_t)p * d.nf + f) * d.n1p + i) * d.n2p;
-    const uint16_t *c2t = w.C2 + ((int64_t)p * d.Tp + (int64_t)ni * d.Tn) * d.n2p;
+    const int trow = p * d.Tp + ni * d.Tn;           // first C2 row of the resample tile (TMA y)
     const uint32_t idesc = idesc_bf16_f32(BT_ROWS, d.Tn);
+    const uint32_t c2_bytes = (uint32_t)d.Tn * 128u;
+    const int nloc = c_hi - c_lo;
+    int issued = 0, landed = 0;   // TMA copies issued / seen complete (thread 0)
+    if (tid == 0 && nloc > 0) {
+        mbar_expect_tx(&bar[3], c2_bytes);
+        tma_load_2d(smem + d.KG * BT_A_BYTES, &tm_c2, c_lo * BT_K, trow, &bar[3]);
+        issued = 1;
+    }
+    uint4 bw[4];
+    if (nloc > 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bw[q] = *reinterpret_cast<const uint4 *>(brow + (int64_t)c_lo * BT_K + q * 16);
+    }
     bool failed = false;
-    for (int c = c_lo; c < c_hi; ++c) {
-        const int lc = c - c_lo, st = lc & 1;
-        bool ok = true;
-        if (lc >= 2) ok = mbar_wait(&bar[st], (uint32_t)((lc - 2) >> 1) & 1u, spin);
+    for (int lc = 0; lc < nloc; ++lc) {
+        const int c = c_lo + lc, st = lc & 1;
+        bool ok = s_fail == 0;
+        if (ok && lc >= 2) ok = mbar_wait(&bar[st], (uint32_t)((lc - 2) >> 1) & 1u, spin);
         if (__syncthreads_or(ok ? 0 : 1)) { failed = true; break; }
         uint8_t *sb = smem + st * stage_bytes;
-        uint8_t *sc2 = sb + d.KG * BT_A_BYTES;
-        // C2 tile: Tn rows (resamples) x 64 columns, bf16
-        for (int e = tid; e < d.Tn * 8; e += BT_THREADS) {
-            const int r = e >> 3, ch = e & 7;
-            const uint4 v = *reinterpret_cast<const uint4 *>(c2t + (int64_t)r * d.n2p + (int64_t)c * BT_K + ch * 8);
-            *reinterpret_cast<uint4 *>(sc2 + sw128_off(r, ch)) = v;
-        }
-        // this row's 64 bins bytes, then one 0/1 tile per radius
-        uint4 bw[4];
+        // next chunk's bins, then this chunk's 0/1 tiles, one per radius
+        uint4 bn[4];
+        if (lc + 1 < nloc) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) bw[q] = *reinterpret_cast<const uint4 *>(brow + (int64_t)c * BT_K + q * 16);
+            for (int q = 0; q < 4; ++q) bn[q] = *reinterpret_cast<const uint4 *>(brow + (int64_t)(c + 1) * BT_K + q * 16);
+        }
         for (int kk = 0; kk < kn; ++kk) {
             const uint32_t add = (uint32_t)(0x80 - (k0 + kk)) * 0x01010101u;
             uint8_t *at = sb + kk * BT_A_BYTES;
@@ -262,17 +275,43 @@ bootstrap_tc_kernel(BootWork w, int S, unsigned long long *__restrict__ Y, uint3
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
-            fence_after();
-            const uint32_t bB = smem_u32(sc2);
-            for (int kk = 0; kk < kn; ++kk) {
-                const uint32_t bA = smem_u32(sb + kk * BT_A_BYTES);
+            if (!mbar_wait(&bar[3 + st], (uint32_t)(lc >> 1) & 1u, spin)) {
+                s_fail = 1;
+            } else {
+                landed = lc + 1;
+                fence_after();
+                const uint32_t bB = smem_u32(sb + d.KG * BT_A_BYTES);
+                for (int kk = 0; kk < kn; ++kk) {
+                    const uint32_t bA = smem_u32(sb + kk * BT_A_BYTES);
 #pragma unroll
-                for (int ks = 0; ks < BT_K / 16; ++ks)
-                    mma_bf16(tmem + (uint32_t)(kk * d.TnA), smem_desc_sw128(bA + ks * 32),
-                             smem_desc_sw128(bB + ks * 32), idesc, (lc == 0 && ks == 0) ? 0u : 1u);
+                    for (int ks = 0; ks < BT_K / 16; ++ks)
+                        mma_bf16(tmem + (uint32_t)(kk * d.TnA), smem_desc_sw128(bA + ks * 32),
+                                 smem_desc_sw128(bB + ks * 32), idesc, (lc == 0 && ks == 0) ? 0u : 1u);
+                }
+                mma_commit(&bar[st]);
+                // the next chunk's C2 tile into the other stage, once the MMAs
+                // of the chunk before this one have read it
+                if (lc + 1 < nloc) {
+                    const int sn = (lc + 1) & 1;
+                    if (lc >= 1 && !mbar_wait(&bar[sn], (uint32_t)((lc - 1) >> 1) & 1u, spin)) {
+                        s_fail = 1;
+                    } else {
+                        mbar_expect_tx(&bar[3 + sn], c2_bytes);
+                        tma_load_2d(smem + sn * stage_bytes + d.KG * BT_A_BYTES, &tm_c2, (c + 1) * BT_K, trow,
+                                    &bar[3 + sn]);
+                        issued = lc + 2;
+                    }
+                }
             }
-            mma_commit(&bar[st]);
         }
+        if (lc + 1 < nloc) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bw[q] = bn[q];
+        }
+    }
+    if (tid == 0) {
+        // copies still in flight land before the shared memory is released
+        for (int it = landed; it < issued; ++it) mbar_wait(&bar[3 + (it & 1)], (uint32_t)(it >> 1) & 1u, spin);
     }
     // every MMA issued by this CTA completes before its tensor memory is
     // read or released
@@ -289,12 +328,19 @@ bootstrap_tc_kernel(BootWork w, int S, unsigned long long *__restrict__ Y, uint3
                                 (int64_t)ni * d.Tn;
         for (int kk = 0; kk < kn; ++kk) {
             for (int tb = 0; tb < d.Tn; tb += 32) {
+                // this row's 32 multiplicities (64 bytes, 16-byte aligned)
+                uint32_t cw[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(c1row + tb + 8 * q);
+                    cw[4 * q] = u.x; cw[4 * q + 1] = u.y; cw[4 * q + 2] = u.z; cw[4 * q + 3] = u.w;
+                }
                 float z[32];
                 tmem_ld32(tmem + lrow + (uint32_t)(kk * d.TnA + tb), z);
                 int v[32];
 #pragma unroll
                 for (int l = 0; l < 32; ++l) {
-                    const int c1 = (tb + l < d.Tn) ? (int)c1row[tb + l] : 0;
+                    const int c1 = (tb + l < d.Tn) ? (int)((cw[l >> 1] >> (16 * (l & 1))) & 0xFFFFu) : 0;
                     v[l] = c1 ? __float2int_rn(z[l]) * c1 : 0;
                 }
                 // transpose-reduce: afterwards lane l holds column tb + l summed
@@ -332,6 +378,20 @@ bootstrap_tc_kernel(BootWork w, int S, unsigned long long *__restrict__ Y, uint3
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 boot_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *q = nullptr;
+        cudaDriverEntryPointQueryResult r;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000, cudaEnableDefault, &r) ==
+                cudaSuccess &&
+            r == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)q;
+    });
+    return fn;
+}
+
 size_t boot_workspace_bytes(int64_t n1, int64_t n2, int M, int T, int nf, int P) {
     return boot_layout(boot_dims(n1, n2, M, T, nf, P), nullptr).bytes;
 }
@@ -358,13 +418,26 @@ rd_status launch_bootstrap_tc(const uint8_t *bins, int nf, int64_t n1, int64_t n
     if (S < 1) S = 1;
     if (units * S > 0x7FFFFFFF) return RD_ERR_UNSUPPORTED;
     const size_t smem = 1024 + 2 * (size_t)(d.KG * BT_A_BYTES + d.Tn * 128) + 64;
+    // C2 as a 2-D tensor: n2p bf16 columns (inner) x P Tp rows; boxes of 64
+    // columns (128 bytes, the swizzle span) x Tn resamples
+    auto enc = boot_encode_fn();
+    if (!enc) return RD_ERR_CUDA;
+    CUtensorMap tm;
+    cuuint64_t dims[2] = {(cuuint64_t)d.n2p, (cuuint64_t)((int64_t)P * d.Tp)};
+    cuuint64_t strides[1] = {(cuuint64_t)d.n2p * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BT_K, (cuuint32_t)d.Tn};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, w.C2, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return RD_ERR_CUDA;
     static size_t set = 0;
     if (smem > set) {
         RD_CUDA_TRY(cudaFuncSetAttribute(bootstrap_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         set = smem;
     }
     bootstrap_tc_kernel<<<(unsigned)(units * S), BT_THREADS, smem, s>>>(
-        w, S, reinterpret_cast<unsigned long long *>(Y), MBAR_WAIT_LIMIT);
+        tm, w, S, reinterpret_cast<unsigned long long *>(Y), MBAR_WAIT_LIMIT);
     note_launch();
     *flag_out = w.flag;
     return cuda_status(cudaGetLastError());
