@@ -196,6 +196,12 @@ __global__ void fd_kernel(const float *__restrict__ X, int64_t ld, int64_t n, in
 //    max is exact in any order)
 // ---------------------------------------------------------------------------
 constexpr int MX_K = 32;
+// max(|a|, |b|, |c|): the three-input FP32 max with absolute values
+__device__ __forceinline__ float max3_abs(float a, float b, float c) {
+    float d;
+    asm("max.abs.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
 // TA x TB pairs per CTA (TA = 128 or 64 set-1 rows; TB = 32768 / TA set-2
 // rows), 8 x 8 per thread: thread (ty, tx) takes rows ty + (TA/8) a and
 // columns tx + (TB/8) c, so the shared-memory reads of a warp are
@@ -228,17 +234,25 @@ __global__ void __launch_bounds__(256) maxabs_kernel(const float *__restrict__ A
             sb[kk][r] = (jb < n2 && k < k_hi) ? B[jb * ldb + k] : 0.f;
         }
         __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < MX_K; ++kk) {
-            float av[8], bv[8];
+        // two K columns per step: m = max(|m|, |d1|, |d2|) in one three-input
+        // max (exact in any grouping; m >= 0)
+#pragma unroll 2
+        for (int kk = 0; kk < MX_K; kk += 2) {
+            float av[8], bv[8], aw[8], bw[8];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) av[a] = sa[kk][ty + RY * a];
+            for (int a = 0; a < 8; ++a) {
+                av[a] = sa[kk][ty + RY * a];
+                aw[a] = sa[kk + 1][ty + RY * a];
+            }
 #pragma unroll
-            for (int c = 0; c < 8; ++c) bv[c] = sb[kk][tx + RX * c];
+            for (int c = 0; c < 8; ++c) {
+                bv[c] = sb[kk][tx + RX * c];
+                bw[c] = sb[kk + 1][tx + RX * c];
+            }
 #pragma unroll
             for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) m[a][c] = fmaxf(m[a][c], fabsf(av[a] - bv[c]));
+                for (int c = 0; c < 8; ++c) m[a][c] = max3_abs(m[a][c], av[a] - bv[c], aw[a] - bw[c]);
         }
         __syncthreads();
     }
