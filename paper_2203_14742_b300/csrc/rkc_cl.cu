@@ -6,10 +6,14 @@
 // dF(increment), the state held compensated.
 //
 // B300 design.  Each CTA keeps its rows in registers (4 x 4 nodes per
-// thread, 256 threads) and its compensation in shared memory; a stage's
-// halo exchange writes the tile edges into the CTA's own ring and the CTA's
-// first and last rows into its neighbours' shared memory (distributed
-// shared memory), then one cluster barrier.  The step control is taken by
+// thread, 256 threads) and its compensation in shared memory.  A stage's
+// halo exchange writes the tile edges into the CTA's own ring (a split
+// CTA-scope mbarrier orders them) and sends the CTA's first and last rows
+// into its neighbours' shared memory with st.async, whose bytes complete a
+// transaction mbarrier of the receiving CTA: only the warp that reads a
+// neighbour's row waits for it, and no thread fences at cluster scope.  The
+// exchange of F(Y_0) at the start of a step, which also reads the
+// neighbours' compensation arrays, keeps a cluster barrier.  The step control is taken by
 // CTA 0 alone: every CTA writes its partial error sum and spectral-radius
 // bound into CTA 0's shared memory, CTA 0 decides and writes the control
 // state into every CTA's shared memory, and a cluster barrier later every
@@ -19,6 +23,7 @@
 #include "common.cuh"
 #include "tile.cuh"
 #include "rkc.cuh"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -43,11 +48,12 @@ struct ClShape {
     static constexpr size_t OFF_CTL = OFF_CLP + 16 * 4;
     static constexpr size_t OFF_BETA = (OFF_CTL + sizeof(RkcCtl) + 15) / 16 * 16;
     static constexpr size_t OFF_C0 = (OFF_BETA + RKC_STRIDE * sizeof(double) + 15) / 16 * 16;
-    static constexpr size_t SMEM = OFF_C0 + 2 * (size_t)R * G * 4;
+    static constexpr size_t OFF_MB = OFF_C0 + 2 * (size_t)R * G * 4;   // ClMbar
+    static constexpr size_t SMEM = OFF_MB + 64;
     static_assert(OFF_EXT % 16 == 0 && OFF_RED % 16 == 0 && OFF_CLP % 16 == 0 && OFF_CTL % 16 == 0 &&
-                      OFF_BETA % 16 == 0 && OFF_C0 % 16 == 0,
+                      OFF_BETA % 16 == 0 && OFF_C0 % 16 == 0 && OFF_MB % 16 == 0,
                   "shared-memory regions must start on 16-byte boundaries");
-    static_assert(2 * CL <= 16, "cluster partials");
+    static_assert(3 * CL <= 16, "cluster partials");
 };
 
 // One exchange-and-apply of a tile quantity (yu, yv): the tile edges go into
@@ -137,6 +143,140 @@ __device__ __forceinline__ void cl_exchange_apply(cg::cluster_group &cluster, in
     }
 }
 
+// mbarriers of the stage exchanges: ring (count = threads, one phase per
+// exchange), north[b] / south[b] (count 1, armed with the expected bytes by
+// the lane that waits; the neighbour's st.async bytes complete them) for
+// ext buffer b
+struct ClMbar {
+    uint64_t ring;
+    uint64_t north[2];
+    uint64_t south[2];
+};
+
+__device__ __forceinline__ uint32_t cl_mapa(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+// 16 bytes into another CTA's shared memory; the bytes complete a
+// transaction on that CTA's mbarrier
+__device__ __forceinline__ void cl_st_async(uint32_t raddr, float a, float b, float c, float d, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     raddr),
+                 "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)), "r"(__float_as_uint(d)),
+                 "r"(rbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cl_arrive_cta(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait with acquire at cluster scope (the bytes came from another CTA)
+__device__ __forceinline__ bool cl_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// The stage exchange-and-apply with mbarriers (same data, same body order as
+// cl_exchange_apply).  ex = this exchange's index among the mbarrier
+// exchanges (ring parity), nb[b] = uses of ext buffer b so far (its
+// north/south parity); tmo: a wait gave up (later waits are skipped, the
+// step reports the timeout).
+template <int G, int CL, int TY, int TX, class Body>
+__device__ __forceinline__ void cl_exchange_mb(int cr, float *hb, float *eb, int b, ClMbar *mb, uint32_t ex,
+                                               uint32_t nbb, bool &tmo, uint32_t spin, int tx, int ty,
+                                               const float (&yu)[TY][TX], const float (&yv)[TY][TX], Body body) {
+    using S = ClShape<G, CL, TY, TX>;
+    constexpr int NX = S::NX, NY = S::NY;
+    static_assert(TY >= 3 && TX == 4, "interior rows; one 16-byte send per species");
+    static_assert(NX == 32, "a tile row is one warp");
+    const int x0 = tx * TX;
+    const int lane = threadIdx.x & 31;
+    st_row<TX>(hb + ((0 * 2 + 0) * NY + ty) * G + x0, yu[0]);
+    st_row<TX>(hb + ((0 * 2 + 1) * NY + ty) * G + x0, yu[TY - 1]);
+    st_row<TX>(hb + ((1 * 2 + 0) * NY + ty) * G + x0, yv[0]);
+    st_row<TX>(hb + ((1 * 2 + 1) * NY + ty) * G + x0, yv[TY - 1]);
+    constexpr uint32_t XB = 2 * G * 4;   // bytes of one boundary row, both species
+    if (ty == 0 && cr > 0) {
+        // first row -> the south side of the CTA above
+        const uint32_t rank = (uint32_t)(cr - 1);
+        const uint32_t rbar = cl_mapa(smem_u32(&mb->south[b]), rank);
+        cl_st_async(cl_mapa(smem_u32(eb + (0 * 2 + 1) * G + x0), rank), yu[0][0], yu[0][1], yu[0][2], yu[0][3], rbar);
+        cl_st_async(cl_mapa(smem_u32(eb + (1 * 2 + 1) * G + x0), rank), yv[0][0], yv[0][1], yv[0][2], yv[0][3], rbar);
+        if (lane == 0) mbar_expect_tx(&mb->north[b], XB);   // this warp receives the CTA above's row
+    }
+    if (ty == NY - 1 && cr < CL - 1) {
+        const uint32_t rank = (uint32_t)(cr + 1);
+        const uint32_t rbar = cl_mapa(smem_u32(&mb->north[b]), rank);
+        cl_st_async(cl_mapa(smem_u32(eb + (0 * 2 + 0) * G + x0), rank), yu[TY - 1][0], yu[TY - 1][1], yu[TY - 1][2],
+                    yu[TY - 1][3], rbar);
+        cl_st_async(cl_mapa(smem_u32(eb + (1 * 2 + 0) * G + x0), rank), yv[TY - 1][0], yv[TY - 1][1], yv[TY - 1][2],
+                    yv[TY - 1][3], rbar);
+        if (lane == 0) mbar_expect_tx(&mb->south[b], XB);
+    }
+    cl_arrive_cta(&mb->ring);
+    auto row = [&](int i, const float (&pu)[TX], const float (&pv)[TX], const float (&su)[TX],
+                   const float (&sv)[TX]) {
+        float wu, eu, wv, ev;
+        row_west_east<NX>(tx, yu[i][0], yu[i][TX - 1], wu, eu);
+        row_west_east<NX>(tx, yv[i][0], yv[i][TX - 1], wv, ev);
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            const float Lu = c > 0 ? yu[i][c - 1] : wu, Ru = c < TX - 1 ? yu[i][c + 1] : eu;
+            const float Lv = c > 0 ? yv[i][c - 1] : wv, Rv = c < TX - 1 ? yv[i][c + 1] : ev;
+            body(i, c, make_float4(pu[c], su[c], Lu, Ru), make_float4(pv[c], sv[c], Lv, Rv));
+        }
+    };
+    // interior rows: all neighbours in registers
+#pragma unroll
+    for (int i = 1; i < TY - 1; ++i) row(i, yu[i - 1], yv[i - 1], yu[i + 1], yv[i + 1]);
+    if (!tmo && !mbar_wait(&mb->ring, ex & 1u, spin)) tmo = true;
+    // first row: north from the ring / the CTA above / the mirror ghost
+    {
+        float pu[TX], pv[TX];
+        if (ty > 0) {
+            ld_row<TX>(hb + ((0 * 2 + 1) * NY + ty - 1) * G + x0, pu);
+            ld_row<TX>(hb + ((1 * 2 + 1) * NY + ty - 1) * G + x0, pv);
+        } else if (cr > 0) {
+            if (!tmo && !cl_wait(&mb->north[b], nbb & 1u, spin)) tmo = true;
+            ld_row<TX>(eb + (0 * 2 + 0) * G + x0, pu);
+            ld_row<TX>(eb + (1 * 2 + 0) * G + x0, pv);
+        } else {
+#pragma unroll
+            for (int c = 0; c < TX; ++c) { pu[c] = yu[0][c]; pv[c] = yv[0][c]; }
+        }
+        row(0, pu, pv, yu[1], yv[1]);
+    }
+    // last row: south from the ring / the CTA below / the mirror ghost
+    {
+        float su[TX], sv[TX];
+        if (ty < NY - 1) {
+            ld_row<TX>(hb + ((0 * 2 + 0) * NY + ty + 1) * G + x0, su);
+            ld_row<TX>(hb + ((1 * 2 + 0) * NY + ty + 1) * G + x0, sv);
+        } else if (cr < CL - 1) {
+            if (!tmo && !cl_wait(&mb->south[b], nbb & 1u, spin)) tmo = true;
+            ld_row<TX>(eb + (0 * 2 + 1) * G + x0, su);
+            ld_row<TX>(eb + (1 * 2 + 1) * G + x0, sv);
+        } else {
+#pragma unroll
+            for (int c = 0; c < TX; ++c) { su[c] = yu[TY - 1][c]; sv[c] = yv[TY - 1][c]; }
+        }
+        row(TY - 1, yu[TY - 2], yv[TY - 2], su, sv);
+    }
+}
+
 template <int MODEL, int G, int CL, int TY, int TX>
 __global__ void __launch_bounds__(ClShape<G, CL, TY, TX>::NT, 1)
 rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRun run, double t_end,
@@ -158,7 +298,20 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
     RkcCtl &c = *reinterpret_cast<RkcCtl *>(sb + S::OFF_CTL);
     double *betaS = reinterpret_cast<double *>(sb + S::OFF_BETA);
     float *c0 = reinterpret_cast<float *>(sb + S::OFF_C0);     // [species][R][G], own rows
+    ClMbar *mb = reinterpret_cast<ClMbar *>(sb + S::OFF_MB);
     const int tid = threadIdx.x, tx = tid % NX, ty = tid / NX;
+    if (tid == 0) {
+        // visible to the other CTAs through the cluster barriers that come
+        // before the first stage exchange
+        mbar_init(&mb->ring, S::NT);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&mb->north[q], 1);
+            mbar_init(&mb->south[q], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    bool tmo = false;                 // a stage-exchange wait gave up
+    uint32_t ex = 0, nb0 = 0, nb1 = 0;   // mbarrier exchanges so far; uses of ext buffer 0 / 1
     for (int i = tid; i < RKC_STRIDE; i += blockDim.x) betaS[i] = beta[i];
     float *base = fields + field_offset + (int64_t)r * M;
     float *mine = base + (int64_t)cr * R * G;                  // this CTA's first row
@@ -204,15 +357,24 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
         const float e = c0[sp * R * G + y * G + (x < G - 1 ? x + 1 : x)];
         return fmaf(-4.f, ce, (n + so) + (w + e));
     };
-    // the CTA's partial sums to CTA 0, a cluster barrier (CTA 0 then has all)
+    // the CTA's partial sums (and whether a wait gave up) to CTA 0, a cluster
+    // barrier (CTA 0 then has all)
     auto to_rank0 = [&](float ss, float mx) {
+        const int anyt = __syncthreads_or(tmo ? 1 : 0);
         if (tid == 0) {
             float *dst = cluster.map_shared_rank(clp, 0);
             dst[2 * cr] = ss;
             dst[2 * cr + 1] = mx;
+            dst[2 * CL + cr] = anyt ? 1.f : 0.f;
         }
         cluster.sync();
     };
+    auto timed_out = [&]() {
+        bool t = false;
+        for (int q = 0; q < CL; ++q) t |= clp[2 * CL + q] != 0.f;
+        return t;
+    };
+
     // CTA 0's control state into every CTA, a cluster barrier
     auto broadcast = [&]() {
         if (cr == 0 && tid == 0)
@@ -223,6 +385,16 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
     int hk = 0;
     auto hbuf = [&]() { return ring + hk * S::RING; };
     auto ebuf = [&]() { return ext + hk * S::EXT; };
+    // one stage exchange through the mbarriers (buffer hk), then flip
+    auto xchg = [&](const float (&yu)[TY][TX], const float (&yv)[TY][TX], auto body) {
+        const int b = hk;
+        cl_exchange_mb<G, CL, TY, TX>(cr, hbuf(), ebuf(), b, mb, ex, b ? nb1 : nb0, tmo, MBAR_WAIT_LIMIT, tx, ty,
+                                      yu, yv, body);
+        ++ex;
+        if (b) ++nb1;
+        else ++nb0;
+        hk ^= 1;
+    };
     auto eval0 = [&]() {
         cl_exchange_apply<G, CL, TY, TX>(cluster, cr, hbuf(), ebuf(), tx, ty, y0u, y0v,
                                          [&](int i, int cc, float4 nu, float4 nv) {
@@ -270,6 +442,7 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
             c.done = 0;
             c.fail = 0;
             rkc_plan(c, run, betaS);
+            if (timed_out()) { c.done = 1; c.fail = 3; }
         }
         broadcast();
     }
@@ -299,8 +472,7 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
             const float4 cj = __ldg(&row[j]);
             const float mth = cj.z * h, cfh = (cj.z + cj.w) * h;
             const float mdu = mth * k.du, mdv = mth * k.dv, mru = mth * ku, mrv = mth * kv;
-            cl_exchange_apply<G, CL, TY, TX>(cluster, cr, hbuf(), ebuf(), tx, ty, dlu, dlv,
-                                             [&](int i, int cc, float4 nu, float4 nv) {
+            xchg(dlu, dlv, [&](int i, int cc, float4 nu, float4 nv) {
                 float gu = cfh * f0u[i][cc], gv = cfh * f0v[i][cc];
                 if (MODEL != RD_DIFF) {
                     float dRu, dRv;
@@ -311,7 +483,6 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
                 dpu[i][cc] = fmaf(cj.x, dlu[i][cc], fmaf(cj.y, dpu[i][cc], fmaf(mdu, lap5(dlu[i][cc], nu), gu)));
                 dpv[i][cc] = fmaf(cj.x, dlv[i][cc], fmaf(cj.y, dpv[i][cc], fmaf(mdv, lap5(dlv[i][cc], nv), gv)));
             });
-            hk ^= 1;
         };
         for (int j = 2; j <= s; j += 2) {
             stage(d1u, d1v, d2u, d2v, j);
@@ -330,8 +501,7 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
         float acc = 0.f, rmax = 0.f;
         if (adaptive) {
             const float rtol = (float)run.rtol, atol = (float)run.atol, h04 = 0.4f * h;
-            cl_exchange_apply<G, CL, TY, TX>(cluster, cr, hbuf(), ebuf(), tx, ty, d1u, d1v,
-                                             [&](int i, int cc, float4 nu, float4 nv) {
+            xchg(d1u, d1v, [&](int i, int cc, float4 nu, float4 nv) {
                 float dRu = 0.f, dRv = 0.f;
                 if (MODEL != RD_DIFF) rhs_dparts<MODEL>(y0u[i][cc], y0v[i][cc], d1u[i][cc], d1v[i][cc], k, dRu, dRv);
                 const float dFu = fmaf(k.du, lap5(d1u[i][cc], nu), ku * dRu);
@@ -345,7 +515,6 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
                 acc = fmaf(qu, qu, fmaf(qv, qv, acc));
                 rmax = fmaxf(rmax, gersh_cell<MODEL>(Us, Vs, ncount(i, cc), k));
             });
-            hk ^= 1;
         }
         block_reduce2(acc, rmax, red);
         to_rank0(acc, rmax);
@@ -357,6 +526,7 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
             }
             c.rho_new = rho;
             rkc_decide(c, run, betaS, ss, M);
+            if (timed_out()) { c.accept = 0; c.done = 1; c.fail = 3; }
         }
         broadcast();
         if (c.accept) {
@@ -404,6 +574,7 @@ rd_rkc_cl_kernel(float *__restrict__ fields, int64_t field_offset, RkcK k, RkcRu
         }
         if (c.fail == 1) atomicOr(status, (unsigned)ST_STEPFAIL);
         if (c.fail == 2) atomicOr(status, (unsigned)ST_NONFINITE);
+        if (c.fail == 3) atomicOr(status, (unsigned)ST_TIMEOUT);
     }
     residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, ring);
 }
