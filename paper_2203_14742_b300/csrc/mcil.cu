@@ -188,6 +188,50 @@ __global__ void fd_kernel(const float *__restrict__ X, int64_t ld, int64_t n, in
     }
 }
 
+// The same for Gx a multiple of 4 (and at most 128 x 32 = 4096): a warp
+// covers up to 128 columns of one row with float4 loads, the column right
+// of a lane's four comes from the next lane by shuffle, the next row by a
+// float4 load; eight rows (warps) per block, so every block has eight rows'
+// loads in flight.  Dx rows (Gx - 1 values) are stored value by value, Dy
+// rows as float4.
+__global__ void __launch_bounds__(256) fd4_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int Gy,
+                                                   int Gx, int nsp, float *__restrict__ Ax, float *__restrict__ Ay) {
+    const int64_t cex = (int64_t)Gy * (Gx - 1), cey = (int64_t)(Gy - 1) * Gx, cells = (int64_t)Gy * Gx;
+    const int64_t nrows = n * nsp * Gy;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nq = Gx >> 2;   // float4 per row
+    for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < nrows; r += (int64_t)gridDim.x * 8) {
+        const int64_t is = r / Gy;
+        const int y = (int)(r - is * Gy);
+        const int64_t i = is / nsp;
+        const int sp = (int)(is - i * nsp);
+        const float *x = X + i * ld + (int64_t)sp * cells + (int64_t)y * Gx;
+        float *dx = Ax + is * cex + (int64_t)y * (Gx - 1);
+        float *dy = (y < Gy - 1) ? Ay + is * cey + (int64_t)y * Gx : nullptr;
+        for (int q0 = 0; q0 < nq; q0 += 32) {
+            const int q = q0 + lane;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (q < nq) {
+                a = *reinterpret_cast<const float4 *>(x + 4 * q);
+                if (dy) b = *reinterpret_cast<const float4 *>(x + Gx + 4 * q);
+            }
+            // first value of the next lane's four (the next 32-float4 slice
+            // starts a fresh warp-wide load, read directly)
+            float nx = __shfl_down_sync(0xffffffffu, a.x, 1);
+            if (lane == 31 && q + 1 < nq) nx = x[4 * (q + 1)];
+            if (q < nq) {
+                const int c = 4 * q;
+                dx[c] = a.y - a.x;
+                dx[c + 1] = a.z - a.y;
+                dx[c + 2] = a.w - a.z;
+                if (c + 3 < Gx - 1) dx[c + 3] = nx - a.w;
+                if (dy)
+                    *reinterpret_cast<float4 *>(dy + c) = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 2. max |a - b| of every pair, FP32: 128 x 128 (or 64 x 256) pairs per
 //    CTA, 8 x 8 per thread, 32-column slices of both sets in shared memory,
@@ -746,10 +790,26 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
     }
     const bool deriv = (features & 0x3C) != 0;
     if (deriv) {
-        const int fdt = Gx >= 256 ? 256 : (Gx >= 128 ? 128 : 64);
-        fd_kernel<<<16 * 148, fdt, 0, s>>>(P1, l1, n1, Gy, Gx, n_species, w.Ax1, w.Ay1);
-        note_launch();
-        fd_kernel<<<16 * 148, fdt, 0, s>>>(P2, l2, n2, Gy, Gx, n_species, w.Ax2, w.Ay2);
+        const int64_t r1 = n1 * n_species * Gy, r2 = n2 * n_species * Gy;
+        // float4 rows need 16-byte aligned rows: Gx % 4 == 0 and pattern
+        // strides and bases on 16-byte boundaries
+        const bool vec = (Gx % 4 == 0) && (l1 % 4 == 0) && (l2 % 4 == 0) && ((((uintptr_t)P1) | ((uintptr_t)P2)) % 16 == 0);
+        if (vec) {
+            const int64_t b1 = (r1 + 7) / 8, b2 = (r2 + 7) / 8;
+            fd4_kernel<<<(unsigned)(b1 < 65535 * 16 ? b1 : 65535 * 16), 256, 0, s>>>(P1, l1, n1, Gy, Gx, n_species,
+                                                                                    w.Ax1, w.Ay1);
+            note_launch();
+            fd4_kernel<<<(unsigned)(b2 < 65535 * 16 ? b2 : 65535 * 16), 256, 0, s>>>(P2, l2, n2, Gy, Gx, n_species,
+                                                                                    w.Ax2, w.Ay2);
+        } else {
+            // one block per grid row (every row's loads in flight at once)
+            const int fdt = Gx >= 256 ? 256 : (Gx >= 128 ? 128 : 64);
+            fd_kernel<<<(unsigned)(r1 < 0x7FFFFFFF ? r1 : 0x7FFFFFFF), fdt, 0, s>>>(P1, l1, n1, Gy, Gx, n_species,
+                                                                                   w.Ax1, w.Ay1);
+            note_launch();
+            fd_kernel<<<(unsigned)(r2 < 0x7FFFFFFF ? r2 : 0x7FFFFFFF), fdt, 0, s>>>(P2, l2, n2, Gy, Gx, n_species,
+                                                                                   w.Ax2, w.Ay2);
+        }
         note_launch();
     }
     Arr3 A{};
