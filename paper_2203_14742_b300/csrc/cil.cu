@@ -607,8 +607,20 @@ __global__ void __launch_bounds__(32) canonical_kernel(CilWork w, const float *_
         const int64_t q = (int64_t)(ent & Q_IDX);
         const int64_t i = q / w.n2, j = q - i * w.n2;
         const float *x = X1 + i * ld1, *y = X2 + j * ld2;
+        // increasing t; the loads run eight elements ahead of the sum
         double acc = 0.0;
-        for (int64_t t = 32 * g + lane; t < w.d; t += 256) acc = __dadd_rn(acc, sq_diff(__ldg(x + t), __ldg(y + t)));
+        int64_t t = 32 * g + lane;
+        for (; t + 7 * 256 < w.d; t += 8 * 256) {
+            float xa[8], ya[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                xa[u] = __ldg(x + t + 256 * u);
+                ya[u] = __ldg(y + t + 256 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc = __dadd_rn(acc, sq_diff(xa[u], ya[u]));
+        }
+        for (; t < w.d; t += 256) acc = __dadd_rn(acc, sq_diff(__ldg(x + t), __ldg(y + t)));
 #pragma unroll
         for (int s = 16; s >= 1; s >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(0xffffffffu, acc, s));
         if (lane == 0) {

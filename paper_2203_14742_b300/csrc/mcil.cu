@@ -52,6 +52,7 @@ namespace rdcil {
 
 static constexpr int NF = 6;
 static constexpr int MC_SCAL = 32;   // control words of one call (see McilWork::scal)
+static constexpr int EX_CAP = 4096;  // queued pairs the split canonical evaluation takes per launch
 __host__ __device__ constexpr bool feat_squared(int f) { return f == 0 || f == 2; }
 
 struct McilWork {
@@ -72,6 +73,8 @@ struct McilWork {
                                     // evaluated in the canonical order; [16 + f] smallest upper
                                     // bound of feature f (complemented bits, linear law)
     double *thr;                    // [NF][32] thresholds of the decision (R_k^2 or R_k)
+    double *grp;                    // [EX_CAP][3][8][2] group sums and maxima of the canonical order
+    unsigned int *arrive;           // [EX_CAP] groups finished per queued pair
     size_t bytes;
 };
 
@@ -125,6 +128,8 @@ static McilWork mlayout(int64_t n1, int64_t n2, int Gy, int Gx, int nsp, int mas
     w.queue = (int64_t *)take(sizeof(int64_t) * w.np);
     w.scal = (unsigned long long *)take(sizeof(unsigned long long) * MC_SCAL);
     w.thr = (double *)take(sizeof(double) * NF * 32);
+    w.grp = (double *)take(sizeof(double) * EX_CAP * 48);
+    w.arrive = (unsigned int *)take(sizeof(unsigned int) * EX_CAP);
     w.bytes = off;
     return w;
 }
@@ -452,12 +457,36 @@ __device__ void exact_q_m(const float *x, const float *y, int64_t d, double *sre
     m = sred[17];
 }
 
-// queued pairs from scal[start_slot] (0: from the start) to the end
+// the six features of pair q from its canonical squared distances qv and
+// maxima mv of the three arrays, each one FP64 expression rounded to nearest
+__device__ void exact_store(McilWork &w, int64_t q, const double (&qv)[3], const double (&mv)[3], double h,
+                            double h2, double g) {
+    const int64_t np = w.np;
+    double v[NF];
+    v[0] = qv[0];
+    v[1] = mv[0];
+    v[2] = __dadd_rn(__dadd_rn(__dmul_rn(h2, qv[0]), qv[1]), qv[2]);
+    v[3] = __dadd_rn(__dadd_rn(__dmul_rn(h, __dsqrt_rn(qv[0])), __dsqrt_rn(qv[1])), __dsqrt_rn(qv[2]));
+    {
+        const double bx = __dmul_rn(g, mv[1]), by = __dmul_rn(g, mv[2]);
+        const double b = bx > by ? bx : by;
+        v[4] = mv[0] > b ? mv[0] : b;
+    }
+    v[5] = __dadd_rn(__dadd_rn(mv[0], __dmul_rn(g, mv[1])), __dmul_rn(g, mv[2]));
+    for (int f = 0; f < NF; ++f)
+        if (w.mask & (1 << f)) w.vex[f * np + q] = v[f];
+    w.flag[q] = 2;
+    atomicAdd(&w.scal[10], 1ull);
+}
+
+// queued pairs from scal[start_slot] (0: from the start) to the end, one
+// CTA per pair (queues longer than EX_CAP; exact_grp_kernel takes the rest)
 __global__ void __launch_bounds__(256) exact_kernel(McilWork w, Arr3 A, double h, double h2, double g,
                                                     int start_slot) {
     __shared__ double sred[18];
     const unsigned long long nq = w.scal[0];
     const unsigned long long first = start_slot == 0 ? 0ull : w.scal[start_slot];
+    if (nq <= first + (unsigned long long)EX_CAP) return;
     for (unsigned long long e = first + blockIdx.x; e < nq; e += gridDim.x) {
         const int64_t q = w.queue[e];
         const int64_t i = q / w.n2, j = q - i * w.n2;
@@ -465,25 +494,89 @@ __global__ void __launch_bounds__(256) exact_kernel(McilWork w, Arr3 A, double h
         const bool need[3] = {true, (w.mask & 0x3C) != 0, (w.mask & 0x3C) != 0};
         for (int a = 0; a < 3; ++a)
             if (need[a]) exact_q_m(A.a1[a] + i * A.ld1[a], A.a2[a] + j * A.ld2[a], A.d[a], sred, qv[a], mv[a]);
-        if (threadIdx.x == 0) {
-            const int64_t np = w.np;
-            double v[NF];
-            v[0] = qv[0];
-            v[1] = mv[0];
-            v[2] = __dadd_rn(__dadd_rn(__dmul_rn(h2, qv[0]), qv[1]), qv[2]);
-            v[3] = __dadd_rn(__dadd_rn(__dmul_rn(h, __dsqrt_rn(qv[0])), __dsqrt_rn(qv[1])), __dsqrt_rn(qv[2]));
-            {
-                const double bx = __dmul_rn(g, mv[1]), by = __dmul_rn(g, mv[2]);
-                const double b = bx > by ? bx : by;
-                v[4] = mv[0] > b ? mv[0] : b;
-            }
-            v[5] = __dadd_rn(__dadd_rn(mv[0], __dmul_rn(g, mv[1])), __dmul_rn(g, mv[2]));
-            for (int f = 0; f < NF; ++f)
-                if (w.mask & (1 << f)) w.vex[f * np + q] = v[f];
-            w.flag[q] = 2;
-            atomicAdd(&w.scal[10], 1ull);
-        }
+        if (threadIdx.x == 0) exact_store(w, q, qv, mv, h, h2, g);
         __syncthreads();
+    }
+}
+
+// The same canonical evaluation spread over warps: one warp per (queued
+// pair, pattern array, group g of 32 partials) sums t = 32 g + lane (mod
+// 256) in increasing t and combines its 32 partials by the halving tree of
+// exact_q_m; the last warp of a pair to finish combines the 8 group sums of
+// each array by the same tree and stores the features.  Every sum is the
+// same FP64 operation sequence as in exact_kernel, on up to 24 SMs per pair
+// instead of one.  Takes the queue from scal[start_slot] when it holds at
+// most EX_CAP pairs (exact_kernel takes longer queues); arrive[] cleared by
+// the caller.
+__global__ void __launch_bounds__(32) exact_grp_kernel(McilWork w, Arr3 A, double h, double h2, double g,
+                                                       int start_slot) {
+    const unsigned long long nq = w.scal[0], first = start_slot == 0 ? 0ull : w.scal[start_slot];
+    const unsigned long long cnt = nq > first ? nq - first : 0ull;
+    if (cnt > (unsigned long long)EX_CAP) return;
+    const int na = (w.mask & 0x3C) != 0 ? 3 : 1;
+    const unsigned long long items = cnt * (unsigned long long)(na * 8);
+    const int lane = threadIdx.x;
+    for (unsigned long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const unsigned long long sl = it / (unsigned long long)(na * 8);
+        const int rem = (int)(it - sl * (unsigned long long)(na * 8));
+        const int a = rem >> 3, gi = rem & 7;
+        const int64_t q = w.queue[first + sl];
+        const int64_t i = q / w.n2, j = q - i * w.n2;
+        const float *x = A.a1[a] + i * A.ld1[a], *y = A.a2[a] + j * A.ld2[a];
+        // increasing t; the loads run eight elements ahead of the sum
+        double acc = 0.0, mx = 0.0;
+        const int64_t d = A.d[a];
+        int64_t t = 32 * gi + lane;
+        for (; t + 7 * 256 < d; t += 8 * 256) {
+            float xa[8], ya[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                xa[u] = __ldg(x + t + 256 * u);
+                ya[u] = __ldg(y + t + 256 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const double df = __dsub_rn((double)xa[u], (double)ya[u]);
+                acc = __dadd_rn(acc, __dmul_rn(df, df));
+                mx = fmax(mx, fabs(df));
+            }
+        }
+        for (; t < d; t += 256) {
+            const double df = __dsub_rn((double)x[t], (double)y[t]);
+            acc = __dadd_rn(acc, __dmul_rn(df, df));
+            mx = fmax(mx, fabs(df));
+        }
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            const double o = __shfl_down_sync(0xffffffffu, acc, s);
+            if (lane < s) acc = __dadd_rn(acc, o);
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+        }
+        unsigned last = 0;
+        if (lane == 0) {
+            double *gp = w.grp + (sl * 3 + a) * 16;
+            gp[2 * gi] = acc;
+            gp[2 * gi + 1] = mx;
+            __threadfence();
+            last = atomicAdd(&w.arrive[sl], 1u) == (unsigned)(na * 8 - 1) ? 1u : 0u;
+        }
+        if (lane == 0 && last) {
+            __threadfence();
+            double qv[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+            for (int a2 = 0; a2 < na; ++a2) {
+                const volatile double *gq = w.grp + (sl * 3 + a2) * 16;
+                double wv[8], mm = 0.0;
+                for (int k = 0; k < 8; ++k) {
+                    wv[k] = gq[2 * k];
+                    mm = fmax(mm, gq[2 * k + 1]);
+                }
+                for (int s = 4; s >= 1; s >>= 1)
+                    for (int k = 0; k < s; ++k) wv[k] = __dadd_rn(wv[k], wv[k + s]);
+                qv[a2] = wv[0];
+                mv[a2] = mm;
+            }
+            exact_store(w, q, qv, mv, h, h2, g);
+        }
     }
 }
 
@@ -866,6 +959,9 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
     note_launch();
     cand2_kernel_m<<<148, 256, 0, s>>>(w);
     note_launch();
+    RD_CUDA_TRY(cudaMemsetAsync(w.arrive, 0, sizeof(unsigned int) * EX_CAP, s));
+    exact_grp_kernel<<<16 * 148, 32, 0, s>>>(w, A, h, h2, g, 9);
+    note_launch();
     exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 9);
     note_launch();
     radii_kernel_m<<<1, 32 * NF, 0, s>>>(w, b, d_radii_out);
@@ -877,6 +973,9 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
     mark_kernel_m<<<1, 32, 0, s>>>(w, 8);
     note_launch();
     classify_kernel_m<<<gp, 256, 0, s>>>(w, 1);
+    note_launch();
+    RD_CUDA_TRY(cudaMemsetAsync(w.arrive, 0, sizeof(unsigned int) * EX_CAP, s));
+    exact_grp_kernel<<<16 * 148, 32, 0, s>>>(w, A, h, h2, g, 8);
     note_launch();
     exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 8);
     note_launch();
