@@ -42,6 +42,7 @@
 //      other pair is decided by its interval.
 #include <cuda_runtime.h>
 #include "common.cuh"
+#include "tma.cuh"
 
 rd_status cil_tier1_intervals(const float *X1, int64_t ld1, int64_t n1, const float *X2, int64_t ld2, int64_t n2,
                               int64_t d, void *work, size_t work_bytes, const float **lo, const float **hi,
@@ -256,33 +257,66 @@ __device__ __forceinline__ float max3_abs(float a, float b, float c) {
 // columns tx + (TB/8) c, so the shared-memory reads of a warp are
 // broadcasts (rows) or consecutive words (columns)
 template <int TA>
-__global__ void __launch_bounds__(256) maxabs_kernel(const float *__restrict__ A, int64_t lda, int64_t n1,
-                                                     const float *__restrict__ B, int64_t ldb, int64_t n2, int64_t d,
-                                                     int64_t kch, float *__restrict__ out) {
-    constexpr int TB = 16384 / TA, RY = TA / 8, RX = TB / 8;   // RY x RX = 256 threads
+struct MaxTile {
+    static constexpr int TB = 16384 / TA, RY = TA / 8, RX = TB / 8;   // RY x RX = 256 threads
+    static constexpr int SA = MX_K * (TA + 1), SB = MX_K * (TB + 1);   // floats per buffer
+    static constexpr size_t SMEM = 2 * (size_t)(SA + SB) * sizeof(float);   // two buffers
+};
+
+// 4-byte asynchronous copy global -> shared; src_bytes = 0 writes a zero
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+template <int TA>
+__global__ void __launch_bounds__(256, 2) maxabs_kernel(const float *__restrict__ A, int64_t lda, int64_t n1,
+                                                        const float *__restrict__ B, int64_t ldb, int64_t n2,
+                                                        int64_t d, int64_t kch, float *__restrict__ out) {
+    using MT = MaxTile<TA>;
+    constexpr int TB = MT::TB, RY = MT::RY, RX = MT::RX;
     static_assert(RY * RX == 256, "thread grid");
-    __shared__ float sa[MX_K][TA + 1], sb[MX_K][TB + 1];
+    extern __shared__ float4 mx_smem[];
+    float *sm = reinterpret_cast<float *>(mx_smem);
+    // buffer q: sa = sm + q (SA + SB), sb = sa + SA; element [kk][r]
     const int64_t i0 = (int64_t)blockIdx.y * TA, j0 = (int64_t)blockIdx.x * TB;
     const int64_t k_lo = (int64_t)blockIdx.z * kch, k_hi = min(d, k_lo + kch);
     const int tx = threadIdx.x % RX, ty = threadIdx.x / RX;
+    // K chunk starting at k0 into buffer q (a warp copies 32 consecutive
+    // columns of one row)
+    auto load = [&](int q, int64_t k0) {
+        float *sa = sm + q * (MT::SA + MT::SB), *sb = sa + MT::SA;
+        for (int e = threadIdx.x; e < TA * MX_K; e += 256) {
+            const int r = e / MX_K, kk = e - r * MX_K;
+            const int64_t k = k0 + kk, ia = i0 + r;
+            const bool in = ia < n1 && k < k_hi;
+            cp_async4(sa + kk * (TA + 1) + r, in ? A + ia * lda + k : A, in ? 4 : 0);
+        }
+        for (int e = threadIdx.x; e < TB * MX_K; e += 256) {
+            const int r = e / MX_K, kk = e - r * MX_K;
+            const int64_t k = k0 + kk, jb = j0 + r;
+            const bool in = jb < n2 && k < k_hi;
+            cp_async4(sb + kk * (TB + 1) + r, in ? B + jb * ldb + k : B, in ? 4 : 0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     float m[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int c = 0; c < 8; ++c) m[a][c] = 0.f;
-    for (int64_t k0 = k_lo; k0 < k_hi; k0 += MX_K) {
-        // a warp reads 32 consecutive columns of one row
-        for (int e = threadIdx.x; e < TA * MX_K; e += 256) {
-            const int r = e / MX_K, kk = e - r * MX_K;
-            const int64_t k = k0 + kk, ia = i0 + r;
-            sa[kk][r] = (ia < n1 && k < k_hi) ? A[ia * lda + k] : 0.f;
-        }
-        for (int e = threadIdx.x; e < TB * MX_K; e += 256) {
-            const int r = e / MX_K, kk = e - r * MX_K;
-            const int64_t k = k0 + kk, jb = j0 + r;
-            sb[kk][r] = (jb < n2 && k < k_hi) ? B[jb * ldb + k] : 0.f;
+    if (k_lo < k_hi) load(0, k_lo);
+    int q = 0;
+    for (int64_t k0 = k_lo; k0 < k_hi; k0 += MX_K, q ^= 1) {
+        const bool more = k0 + MX_K < k_hi;
+        if (more) {
+            load(q ^ 1, k0 + MX_K);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
+        const float *sa = sm + q * (MT::SA + MT::SB), *sb = sa + MT::SA;
         // two K columns per step: m = max(|m|, |d1|, |d2|) in one three-input
         // max (exact in any grouping; m >= 0)
 #pragma unroll 2
@@ -290,20 +324,20 @@ __global__ void __launch_bounds__(256) maxabs_kernel(const float *__restrict__ A
             float av[8], bv[8], aw[8], bw[8];
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
-                av[a] = sa[kk][ty + RY * a];
-                aw[a] = sa[kk + 1][ty + RY * a];
+                av[a] = sa[kk * (TA + 1) + ty + RY * a];
+                aw[a] = sa[(kk + 1) * (TA + 1) + ty + RY * a];
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                bv[c] = sb[kk][tx + RX * c];
-                bw[c] = sb[kk + 1][tx + RX * c];
+                bv[c] = sb[kk * (TB + 1) + tx + RX * c];
+                bw[c] = sb[(kk + 1) * (TB + 1) + tx + RX * c];
             }
 #pragma unroll
             for (int a = 0; a < 8; ++a)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) m[a][c] = max3_abs(m[a][c], av[a] - bv[c], aw[a] - bw[c]);
         }
-        __syncthreads();
+        __syncthreads();   // buffer q is refilled two chunks on
     }
 #pragma unroll
     for (int a = 0; a < 8; ++a)
@@ -937,12 +971,25 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
         if (kch < 2 * MX_K) kch = 2 * MX_K;
         const int64_t nk = (A.d[a] + kch - 1) / kch;
         dim3 grid((unsigned)((n2 + TB - 1) / TB), (unsigned)((n1 + TA - 1) / TA), (unsigned)nk);
-        if (narrow)
-            maxabs_kernel<64><<<grid, 256, 0, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2, A.d[a], kch,
-                                                   w.mabs + a * np);
-        else
-            maxabs_kernel<128><<<grid, 256, 0, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2, A.d[a], kch,
-                                                    w.mabs + a * np);
+        if (narrow) {
+            static bool set64 = false;
+            if (!set64) {
+                RD_CUDA_TRY(cudaFuncSetAttribute(maxabs_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)MaxTile<64>::SMEM));
+                set64 = true;
+            }
+            maxabs_kernel<64><<<grid, 256, MaxTile<64>::SMEM, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2,
+                                                                   A.d[a], kch, w.mabs + a * np);
+        } else {
+            static bool set128 = false;
+            if (!set128) {
+                RD_CUDA_TRY(cudaFuncSetAttribute(maxabs_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)MaxTile<128>::SMEM));
+                set128 = true;
+            }
+            maxabs_kernel<128><<<grid, 256, MaxTile<128>::SMEM, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2,
+                                                                     A.d[a], kch, w.mabs + a * np);
+        }
         note_launch();
     }
     const double g = (double)(Gx - 1), h = 1.0 / g, h2 = 1.0 / (g * g);
