@@ -500,6 +500,11 @@ rd_status synlik_stats_multi(const uint8_t *d_bins, int32_t n_feat, int64_t n1, 
 rd_status synlik_workspace_size(int64_t n1, int64_t n2, int32_t M, int32_t T, int32_t n_feat,
                                 int32_t n_problems, size_t *bytes);
 void synlik_set_tc_min_pairs(int64_t n);
+/* synlik_set_tc_mult_limit — the multiplicity above which synlik_stats_ws
+ * counts with the SIMT kernel instead of the tensor cores (process-wide;
+ * default and maximum 256, bf16's exact integer range; values outside
+ * 1..256 restore the default).  A lower limit exercises that path. */
+void synlik_set_tc_mult_limit(int32_t n);
 rd_status synlik_stats_ws(const uint8_t *d_bins, int32_t n_feat, int64_t n1, int64_t n2,
                           int32_t M, int32_t T, uint64_t seed, int32_t n_problems,
                           const double *d_y_obs, int64_t *d_Y, double *d_mu, double *d_cov,

@@ -74,6 +74,7 @@ _SIGS = {
                                   _vp, _vp, _vp, _vp]),
     "synlik_workspace_size": (_i32, [_i64, _i64, _i32, _i32, _i32, _i32, C.POINTER(_sz)]),
     "synlik_set_tc_min_pairs": (None, [_i64]),
+    "synlik_set_tc_mult_limit": (None, [_i32]),
     "synlik_stats_ws": (_i32, [_vp, _i32, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                                _vp, _vp, _vp, _sz, _vp]),
     "mcil_workspace_size": (_i32, [_i64, _i64, _i32, _i32, _i32, _i32, _i32, C.POINTER(_sz)]),

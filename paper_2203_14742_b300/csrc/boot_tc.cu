@@ -129,7 +129,7 @@ __global__ void boot_count_kernel(BootWork w, uint64_t seed) {
         atomicAdd(&c2[boot_index(sp, (((uint64_t)t * 2u + 1u) << 32) | (uint64_t)b, (uint32_t)d.n2)], 1u);
 }
 
-__global__ void boot_prep_kernel(BootWork w, const uint8_t *__restrict__ bins) {
+__global__ void boot_prep_kernel(BootWork w, const uint8_t *__restrict__ bins, uint32_t mult_limit) {
     const BootDims &d = w.d;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x, e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // bins clamped to M (which leaves every [K >= k], k <= M, unchanged and
@@ -146,7 +146,7 @@ __global__ void boot_prep_kernel(BootWork w, const uint8_t *__restrict__ bins) {
     const int64_t nc2 = (int64_t)d.P * d.Tp * d.n2p;
     for (int64_t e = e0; e < nc2; e += stride) {
         const uint32_t v = w.C2cnt[e];
-        if (v > 256u) atomicOr(&w.flag[0], 1u);
+        if (v > mult_limit) atomicOr(&w.flag[0], 1u);
         // an integer up to 256 has at most 8 significant bits: the upper half
         // of its FP32 pattern is its bf16 pattern exactly
         w.C2[e] = (uint16_t)(__float_as_uint((float)v) >> 16);
@@ -392,6 +392,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 boot_encode_fn() {
     return fn;
 }
 
+// multiplicities above this send the counting to the SIMT kernel (256: the
+// largest bf16 holds every integer up to it; lower only to test that path)
+static uint32_t g_mult_limit = 256;
+void boot_set_mult_limit(int n) { g_mult_limit = (n < 1 || n > 256) ? 256u : (uint32_t)n; }
+
 size_t boot_workspace_bytes(int64_t n1, int64_t n2, int M, int T, int nf, int P) {
     return boot_layout(boot_dims(n1, n2, M, T, nf, P), nullptr).bytes;
 }
@@ -408,7 +413,7 @@ rd_status launch_bootstrap_tc(const uint8_t *bins, int nf, int64_t n1, int64_t n
     RD_CUDA_TRY(cudaMemsetAsync(w.C1cnt, 0, w.cnt_bytes, s));
     boot_count_kernel<<<dim3((unsigned)T, (unsigned)P), 256, 0, s>>>(w, seed);
     note_launch();
-    boot_prep_kernel<<<4 * 148, 256, 0, s>>>(w, bins);
+    boot_prep_kernel<<<4 * 148, 256, 0, s>>>(w, bins, g_mult_limit);
     note_launch();
     // units of work; K segments to give every SM about one CTA
     const int64_t units = (int64_t)P * nf * d.MT * d.NT * d.G;

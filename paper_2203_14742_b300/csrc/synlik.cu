@@ -23,6 +23,7 @@ namespace rdcil {
 
 // tensor-core bootstrap counts (boot_tc.cu)
 size_t boot_workspace_bytes(int64_t n1, int64_t n2, int M, int T, int nf, int P);
+void boot_set_mult_limit(int n);
 rd_status launch_bootstrap_tc(const uint8_t *bins, int nf, int64_t n1, int64_t n2, int M, int T, uint64_t seed,
                               int P, int64_t *Y, void *work, size_t work_bytes, const uint32_t **flag_out,
                               cudaStream_t s);
@@ -350,6 +351,8 @@ extern "C" rd_status synlik_stats_multi(const uint8_t *d_bins, int32_t n_feat, i
 static int64_t g_tc_min_pairs = (int64_t)1 << 22;
 
 extern "C" void synlik_set_tc_min_pairs(int64_t n) { g_tc_min_pairs = n < 0 ? ((int64_t)1 << 22) : n; }
+
+extern "C" void synlik_set_tc_mult_limit(int32_t n) { boot_set_mult_limit(n); }
 
 extern "C" rd_status synlik_workspace_size(int64_t n1, int64_t n2, int32_t M, int32_t T, int32_t n_feat,
                                            int32_t n_problems, size_t *bytes) {

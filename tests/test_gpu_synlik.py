@@ -143,3 +143,20 @@ def test_bootstrap_tensor_core_batched_problems(p, tc_all):
     t = p.synlik(bins, 16, 200, 12345, simt=True)
     assert torch.equal(s["Y"], t["Y"])
     assert torch.equal(s["cov"], t["cov"])
+
+
+@pytest.mark.parametrize("limit", [1, 2])
+def test_bootstrap_multiplicity_fallback(p, tc_all, limit):
+    # a multiplicity above the limit (256 in use: bf16's exact integers)
+    # hands the counting to the SIMT kernel on the device; with a limit of
+    # 1 or 2 every resample takes that path, and the counts stay exact
+    rng = np.random.default_rng(77 + limit)
+    bins = rng.integers(0, 14, (300, 200)).astype(np.uint8)
+    so = oracle.synlik(bins, 13, 40, 0xFA11)
+    p.lib().synlik_set_tc_mult_limit(limit)
+    try:
+        s = p.synlik(torch.from_numpy(bins).cuda(), 13, 40, 0xFA11)
+    finally:
+        p.lib().synlik_set_tc_mult_limit(-1)
+    assert np.array_equal(s["Y"].cpu().numpy(), so["Y"])
+    assert np.array_equal(s["cov"].cpu().numpy(), so["cov"])
