@@ -46,6 +46,10 @@ def lib():
         L.orc_rdode_gershgorin.restype = C.c_double
         L.orc_radii_linear.argtypes = [dp, C.c_int64, C.c_int, dp, dp]
         L.orc_radii_linear.restype = C.c_double
+        L.orc_fitted_b.argtypes = [C.c_double, C.c_int]
+        L.orc_fitted_b.restype = C.c_double
+        L.orc_radii_fitted.argtypes = [dp, C.c_int64, C.c_int, dp, dp]
+        L.orc_radii_fitted.restype = C.c_double
         L.orc_rkc_coef.argtypes = [C.c_int, dp, dp, dp, dp, dp]
         L.orc_rkc_beta.argtypes = [C.c_int]
         L.orc_rkc_beta.restype = C.c_double
@@ -235,13 +239,32 @@ def radii_linear(d2, M):
     return R0, out, rmin.value
 
 
+def fitted_b(c, M):
+    """The fitted power-law decay: smallest double b with fl(b^M) >= c (see
+    cil.c)."""
+    return float(lib().orc_fitted_b(float(c), int(M)))
+
+
+def radii_fitted(d2, M):
+    """(R0, radii[M], b): the power law R_k = R0 b^-k with b fitted so that
+    R_M = R_min, the smallest distance."""
+    d2 = _d(d2)
+    out = np.empty(M, np.float64)
+    b = C.c_double()
+    R0 = lib().orc_radii_fitted(_p(d2, C.c_double), d2.size, M, _p(out, C.c_double), C.byref(b))
+    return R0, out, b.value
+
+
 def cil(X1, X2, b=None, M=None, radii_=None, law="power"):
     """Full CIL of two FP32 pattern sets (law "power": R_k = R0 b^-k;
-    "linear": R_k = R0 - k (R0 - R_min) / M).  Returns dict with d2, R0,
-    radii, bins, counts."""
+    "linear": R_k = R0 - k (R0 - R_min) / M; "fitted": the power law with b
+    fitted so that R_M = R_min).  Returns dict with d2, R0, radii, bins,
+    counts."""
     d2 = pair_d2(X1, X2)
     if radii_ is None and law == "linear":
         R0, r, _ = radii_linear(d2, M)
+    elif radii_ is None and law == "fitted":
+        R0, r, _ = radii_fitted(d2, M)
     elif radii_ is None:
         R0, r = radii(d2, b, M)
     else:

@@ -131,6 +131,51 @@ double orc_radii_linear(const double *d2, int64_t n_pairs, int M, double *radii,
     return R0;
 }
 
+/* Power law with the decay fitted to the range of the distances (Sec. 2.1,
+   Sec. 3.2; Table 1 uses it for the FHN, GM and BZ models): R0 = sqrt(max
+   d^2), R_min = sqrt(min d^2), b > 1 with R_M / R0 = b^-M, R_k = R_{k-1} / b.
+   Reading (the paper gives the condition, not how b is computed): b is the
+   smallest double whose M-th power, formed as M - 1 sequential products
+   each rounded to nearest, reaches c = R0 / R_min, found by halving
+   [1, c] (mid = lo + (hi - lo) * 0.5, every operation rounded to nearest)
+   until lo and hi are adjacent; b = 1 when c <= 1 (R_min = R0) and b = +inf
+   when c is not finite (R_min = 0), where every R_k = R0 / b^k is 0. */
+double orc_fitted_b(double c, int M)
+{
+    if (!(c < INFINITY)) return INFINITY;
+    if (!(c > 1.0)) return 1.0;
+    double lo = 1.0, hi = c;
+    for (int it = 0; it < 400; ++it) {
+        const double half = (hi - lo) * 0.5;
+        const double mid = lo + half;
+        if (!(mid > lo) || !(mid < hi)) break;
+        double p = mid;
+        for (int k = 1; k < M; ++k) p = p * mid;
+        if (p < c) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+/* radii[0..M-1] = R_1..R_M of the fitted power law; returns R0, *b_out = b */
+double orc_radii_fitted(const double *d2, int64_t n_pairs, int M, double *radii, double *b_out)
+{
+    double mx = d2[0], mn = d2[0];
+    for (int64_t k = 1; k < n_pairs; ++k) {
+        if (d2[k] > mx) mx = d2[k];
+        if (d2[k] < mn) mn = d2[k];
+    }
+    const double R0 = sqrt(mx), Rm = sqrt(mn);
+    const double b = orc_fitted_b(R0 / Rm, M);
+    double R = R0;
+    for (int k = 0; k < M; ++k) {
+        R = R / b;
+        radii[k] = R;
+    }
+    *b_out = b;
+    return R0;
+}
+
 /* Bin index K_ij = #{k in 1..M : d_ij < R_k} (strict, eq. eCDF), and
    counts[k-1] = #{(i,j) : K_ij >= k} = N1*N2 * C(R_k). */
 void orc_bins_counts(const double *d2, int64_t n_pairs, const double *radii,

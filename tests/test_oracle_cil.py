@@ -312,3 +312,41 @@ def test_bins_above_M_count_under_every_radius():
     for t in range(5):
         n00 = sum(1 for a in I[t] for b in J[t] if a == 0 and b == 0)
         assert so["Y"][t].tolist() == [12, 12, 12 - n00, 12 - n00]
+
+
+def test_fitted_b_definition():
+    # b is the smallest double whose M-th power (sequential products rounded
+    # to nearest) reaches c: checked against its neighbours by brute force
+    def powM(x, M):
+        p = x
+        for _ in range(M - 1):
+            p = p * x
+        return p
+    for c, M in ((8.0, 3), (10.0, 16), (1.0000001, 13), (123.456, 7), (2.0, 1), (1e6, 32)):
+        b = oracle.fitted_b(c, M)
+        assert powM(b, M) >= c
+        assert powM(np.nextafter(b, 0.0), M) < c
+    assert oracle.fitted_b(8.0, 3) == 2.0            # 2^3 = 8 exactly
+    assert oracle.fitted_b(1.0, 5) == 1.0            # R_min = R0
+    assert oracle.fitted_b(0.5, 5) == 1.0
+    assert oracle.fitted_b(np.inf, 5) == np.inf      # R_min = 0
+
+
+def test_fitted_law_by_hand():
+    # on a line: set 1 = {0}, set 2 = {1, 2, 8}: R0 = 8, R_min = 1, M = 3
+    # -> b = 2, radii 4, 2, 1; counts #{d < R_k} = 2, 1, 0 (worked by hand)
+    X1 = np.array([[0.0]], np.float32)
+    X2 = np.array([[1.0], [2.0], [8.0]], np.float32)
+    o = oracle.cil(X1, X2, M=3, law="fitted")
+    assert o["R0"] == 8.0
+    assert o["radii"].tolist() == [4.0, 2.0, 1.0]
+    assert o["counts"].tolist() == [2, 1, 0]
+    # R_M equals R_min up to the rounding of b: the recursion ends within a
+    # few ulp of the smallest distance
+    rng = np.random.default_rng(3)
+    X1 = rng.standard_normal((9, 40)).astype(np.float32)
+    X2 = rng.standard_normal((11, 40)).astype(np.float32)
+    o = oracle.cil(X1, X2, M=13, law="fitted")
+    rmin = math.sqrt(o["d2"].min())
+    assert abs(o["radii"][-1] - rmin) <= 64 * np.spacing(rmin)
+    assert np.all(np.diff(o["radii"]) < 0)
