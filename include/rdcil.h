@@ -384,6 +384,24 @@ rd_status cil_features_linear(const float *d_X1, int64_t ld1, int64_t n1,
                               double *d_C, int64_t *d_n_rechecked, void *d_work, size_t work_bytes,
                               void *stream);
 
+/* cil_features_fitted — the same correlation integral with the power law
+ * whose decay is fitted to the range of the distances (Sec. 2.1, Sec. 3.2;
+ * Table 1 uses it for the FHN, GM and BZ models): R0 and R_min the largest
+ * and the smallest cross-set distance (from the canonical d2), b > 1 with
+ * R_M / R0 = b^-M, R_k = R_{k-1} / b.  The paper gives the condition, not
+ * how b is computed; here b is the smallest double whose M-th power, formed
+ * as M - 1 sequential products rounded to nearest, reaches R0 / R_min,
+ * found by halving [1, R0 / R_min] (mid = lo + (hi - lo) * 0.5, every
+ * operation rounded to nearest) until the ends are adjacent doubles; b = 1
+ * when R_min = R0 and b = +inf (every R_k = 0) when R_min = 0.  Bins and
+ * counts as for cil_features; d_radii_out[0] = R0.  Arguments, workspace
+ * and limits as for cil_features (no b). */
+rd_status cil_features_fitted(const float *d_X1, int64_t ld1, int64_t n1,
+                              const float *d_X2, int64_t ld2, int64_t n2, int64_t d, int32_t M,
+                              double *d_radii_out, uint8_t *d_bins, int64_t *d_counts,
+                              double *d_C, int64_t *d_n_rechecked, void *d_work, size_t work_bytes,
+                              void *stream);
+
 /* cil_features_static — cil_features for callers that cannot allocate
  * device memory on their hot path (cudaMalloc may synchronise the whole
  * device; some host applications own all device memory through their own

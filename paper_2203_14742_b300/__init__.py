@@ -64,6 +64,8 @@ _SIGS = {
                             _vp, _vp, _vp, _sz, _vp]),
     "cil_features_linear": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp,
                                    _vp, _sz, _vp]),
+    "cil_features_fitted": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp,
+                                   _vp, _sz, _vp]),
     "cil_features_exact": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _dbl, _i32, _vp, _vp,
                                   _vp, _vp, _vp, _sz, _vp]),
     "cil_gram_only": (_i32, [_i64, _i64, _i64, _vp, _sz, C.POINTER(_dbl), _vp]),
@@ -362,12 +364,12 @@ def _cil_call(fn, X1, X2, b, M, radii, work=None, out=None):
         w, wb = _workspace(n1, n2, d, dev)
     else:
         w, wb = work, work.numel()
-    if fn == "cil_features_linear":
+    if fn in ("cil_features_linear", "cil_features_fitted"):
         args = [_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, d, int(M)]
     else:
         args = [_ptr(X1), ld1, n1, _ptr(X2), ld2, n2, d, _ptr(radii), float(b or 0.0), int(M)]
     args += [_ptr(radii_out), _ptr(bins), _ptr(counts), _ptr(Cvec)]
-    if fn in ("cil_features", "cil_features_linear"):
+    if fn in ("cil_features", "cil_features_linear", "cil_features_fitted"):
         args.append(_ptr(nre))
     args += [_ptr(w), wb, _stream()]
     _check(fn, getattr(lib(), fn)(*args))
@@ -407,6 +409,13 @@ def cil_linear(X1, X2, M=13, work=None, out=None):
     """Correlation integral with the linear radii law R_k = R0 - k (R0 - R_min)/M
     (Sec. 2.1; Table 1's law for the MC and RD-ODE models)."""
     return _cil_call("cil_features_linear", X1, X2, None, M, None, work, out)
+
+
+def cil_fitted(X1, X2, M=16, work=None, out=None):
+    """Correlation integral with the power law fitted to the distance range:
+    R_k = R0 b^-k, b > 1 with R_M = R_min (Sec. 2.1; Table 1's law for the
+    FHN, GM and BZ models)."""
+    return _cil_call("cil_features_fitted", X1, X2, None, M, None, work, out)
 
 
 def cil_exact(X1, X2, b=1.3, M=16, radii=None, work=None):
@@ -556,11 +565,12 @@ class Pipeline:
     evaluated at each group's own correlation vector (y_obs = C).
     integrator: "euler" (rd_integrate_batch, each group's n_steps) or "rkc"
     (rd_integrate_rkc to each group's dt * n_steps; `rkc` = dict of h0,
-    rtol, atol, s_max, max_attempts); law: "power" (R0 b^-k) or "linear"
-    (R0 - k (R0 - R_min) / M, b unused).  RDODE groups need "rkc"."""
+    rtol, atol, s_max, max_attempts); law: "power" (R0 b^-k), "linear"
+    (R0 - k (R0 - R_min) / M, b unused) or "fitted" (R0 b^-k with b fitted
+    so that R_M = R_min, b unused).  RDODE groups need "rkc"."""
 
     def __init__(self, groups, sets, M, b, T, seed, device=None, integrator="euler", rkc=None, law="power"):
-        if integrator not in ("euler", "rkc") or law not in ("power", "linear"):
+        if integrator not in ("euler", "rkc") or law not in ("power", "linear", "fitted"):
             raise ValueError("integrator / law")
         self.sim = Simulation(groups, device=device)
         self.dev = self.sim.device
@@ -607,7 +617,7 @@ class Pipeline:
             _check("rd_integrate_rkc", lib().rd_integrate_rkc(
                 self.sim.handle, _ptr(self.sim.fields), C.byref(self.rkc_opts), _ptr(self.rkc_stats),
                 _ptr(self.residual), _stream()))
-        fn = "cil_features_linear" if self.law == "linear" else "cil_features"
+        fn = {"linear": "cil_features_linear", "fitted": "cil_features_fitted"}.get(self.law, "cil_features")
         for (X1, X2), out in zip(self.views, self.cil_out):
             _cil_call(fn, X1, X2, self.b, self.M, None, self.work, out)
         synlik(self.bins, self.M, self.T, self.seed, y_obs=self.C, out=self.stats, work=self.syn_work)

@@ -72,8 +72,30 @@ enum : int {
 // queue entries: pair index | bit 63 maximum candidate | bit 62 minimum candidate
 static constexpr unsigned long long Q_MAX = 1ull << 63, Q_MIN = 1ull << 62, Q_IDX = Q_MIN - 1;
 
-// radii laws (Sec. 2.1): R_k = R_{k-1} / b, or R_k = R0 - k (R0 - R_min) / M
-enum : int { LAW_POWER = 0, LAW_LINEAR = 1 };
+// radii laws (Sec. 2.1): R_k = R_{k-1} / b, R_k = R0 - k (R0 - R_min) / M,
+// or R_k = R_{k-1} / b with b fitted so that R_M = R_min (see fitted_b)
+enum : int { LAW_POWER = 0, LAW_LINEAR = 1, LAW_FITTED = 2 };
+__host__ __device__ constexpr bool law_needs_min(int law) { return law == LAW_LINEAR || law == LAW_FITTED; }
+
+// The fitted decay: the smallest double b whose M-th power, formed as M - 1
+// sequential products rounded to nearest, reaches c = R0 / R_min, by halving
+// [1, c] (mid = lo + (hi - lo) * 0.5, each operation rounded to nearest)
+// until lo and hi are adjacent; 1 when c <= 1, +inf when c is not finite.
+__device__ double fitted_b(double c, int M) {
+    if (!(c < __longlong_as_double(0x7ff0000000000000ll))) return __longlong_as_double(0x7ff0000000000000ll);
+    if (!(c > 1.0)) return 1.0;
+    double lo = 1.0, hi = c;
+    for (int it = 0; it < 400; ++it) {
+        const double half = __dmul_rn(__dsub_rn(hi, lo), 0.5);
+        const double mid = __dadd_rn(lo, half);
+        if (!(mid > lo) || !(mid < hi)) break;
+        double pw = mid;
+        for (int k = 1; k < M; ++k) pw = __dmul_rn(pw, mid);
+        if (pw < c) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
 
 // minima of non-negative values through atomicMax on complemented bits
 __device__ __forceinline__ void atomic_min_f(unsigned long long *slot, float v) {
@@ -433,7 +455,7 @@ __global__ void ranges_kernel(CilWork w, const double *__restrict__ radii_in, Be
     double lo, hi;
     if (radii_in) {
         lo = hi = __dmul_rn(radii_in[k], radii_in[k]);
-    } else if (law == LAW_LINEAR) {
+    } else if (law_needs_min(law)) {
         double mxlo, mxhi, mnlo, mnhi;
         if (tier == 1) {
             mxlo = (double)__uint_as_float((unsigned)w.scal[SC_LB1]);
@@ -447,13 +469,22 @@ __global__ void ranges_kernel(CilWork w, const double *__restrict__ radii_in, Be
             mnhi = read_min_d(w.scal[SC_UBM2]);
         }
         const double f = (double)(k + 1) / (double)M;
-        const double r0lo = sqrt(fmax(mxlo, 0.0)), r0hi = sqrt(mxhi);
-        const double rmlo = sqrt(fmax(mnlo, 0.0)), rmhi = sqrt(fmax(mnhi, 0.0));
-        const double eta = (tier == 1 ? 1e-6 : 1e-13) * r0hi + 1e-300;
-        const double rlo = fmax((1.0 - f) * r0lo + f * rmlo - eta, 0.0);
-        const double rhi = (1.0 - f) * r0hi + f * rmhi + eta;
-        lo = rlo * rlo * (1.0 - 1e-15);
-        hi = rhi * rhi * (1.0 + 1e-15);
+        if (law == LAW_LINEAR) {
+            const double r0lo = sqrt(fmax(mxlo, 0.0)), r0hi = sqrt(mxhi);
+            const double rmlo = sqrt(fmax(mnlo, 0.0)), rmhi = sqrt(fmax(mnhi, 0.0));
+            const double eta = (tier == 1 ? 1e-6 : 1e-13) * r0hi + 1e-300;
+            const double rlo = fmax((1.0 - f) * r0lo + f * rmlo - eta, 0.0);
+            const double rhi = (1.0 - f) * r0hi + f * rmhi + eta;
+            lo = rlo * rlo * (1.0 - 1e-15);
+            hi = rhi * rhi * (1.0 + 1e-15);
+        } else {
+            // fitted power law: R_k^2 = (R0^2)^(1 - f) (R_min^2)^f in real
+            // arithmetic, increasing in both; the margin covers pow, the
+            // bisection's b and the k divisions of the recursion
+            const double rel = tier == 1 ? 1e-6 : 1e-11;
+            lo = pow(fmax(mxlo, 0.0), 1.0 - f) * pow(fmax(mnlo, 0.0), f) * (1.0 - rel);
+            hi = pow(fmax(mxhi, 0.0), 1.0 - f) * pow(fmax(mnhi, 0.0), f) * (1.0 + rel) + 1e-300;
+        }
     } else if (tier == 1) {
         const double lb = (double)__uint_as_float((unsigned)w.scal[SC_LB1]);
         const double ub = (double)__uint_as_float((unsigned)w.scal[SC_UB1]);
@@ -487,7 +518,7 @@ __global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in,
     const int64_t np = w.n1 * w.n2;
     if (q >= np) return;
     w.flag[q] = 0;
-    const bool lin = !radii_in && law == LAW_LINEAR;
+    const bool lin = !radii_in && law_needs_min(law);
     if (all) {   // exact path: every pair to tier 3; all may hold the maximum (and minimum)
         unsigned long long slot = atomicAdd(&w.scal[SC_Q2], 1ull);
         w.q2[slot] = (unsigned long long)q | (radii_in ? 0ull : Q_MAX) | (lin ? Q_MIN : 0ull);
@@ -663,6 +694,7 @@ __global__ void radii_kernel(CilWork w, const double *__restrict__ radii_in, dou
         for (int k = 1; k <= M; ++k) radii_out[k] = __dsub_rn(R, __dmul_rn((double)k, h));
         return;
     }
+    if (law == LAW_FITTED) b = fitted_b(__ddiv_rn(R, __dsqrt_rn(read_min_d(w.scal[SC_MIN]))), M);
     for (int k = 0; k < M; ++k) {
         R = __ddiv_rn(R, b);
         radii_out[k + 1] = R;
@@ -924,6 +956,14 @@ extern "C" rd_status cil_features_linear(const float *d_X1, int64_t ld1, int64_t
                                          void *d_work, size_t work_bytes, void *stream) {
     return cil_run(d_X1, ld1, n1, d_X2, ld2, n2, d, nullptr, 0.0, M, d_radii_out, d_bins, d_counts, d_C,
                    d_n_rechecked, d_work, work_bytes, stream, false, LAW_LINEAR);
+}
+
+extern "C" rd_status cil_features_fitted(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                         int64_t ld2, int64_t n2, int64_t d, int32_t M, double *d_radii_out,
+                                         uint8_t *d_bins, int64_t *d_counts, double *d_C, int64_t *d_n_rechecked,
+                                         void *d_work, size_t work_bytes, void *stream) {
+    return cil_run(d_X1, ld1, n1, d_X2, ld2, n2, d, nullptr, 0.0, M, d_radii_out, d_bins, d_counts, d_C,
+                   d_n_rechecked, d_work, work_bytes, stream, false, LAW_FITTED);
 }
 
 extern "C" rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
