@@ -446,8 +446,9 @@ def mcil(X1, X2, G, nsp, b, M, mask=63, scale=False, Gy=None, law="power"):
     """Multi-feature correlation integral (Alg. 2 step 2.2): per feature in
     mask (ascending), radii [K, M+1] (R0 first), bins [K, n1, n2], counts
     [K, M]; C = the concatenated vector (K*M) of eq. (CIL).  Fields Gy x G
-    (Gy = G by default, 1 for 1-D patterns); law "power" (R0 b^-k) or
-    "linear" (R0 - k (R0 - R_min) / M, b unused)."""
+    (Gy = G by default, 1 for 1-D patterns); law "power" (R0 b^-k),
+    "linear" (R0 - k (R0 - R_min) / M, b unused) or "fitted" (R0 b^-k with b
+    fitted so that R_M = R_min, b unused)."""
     if scale:
         X1, X2 = minmax(X1, G, nsp, Gy), minmax(X2, G, nsp, Gy)
     V = mcil_values(X1, X2, G, nsp, mask, Gy)
@@ -459,7 +460,8 @@ def mcil(X1, X2, G, nsp, b, M, mask=63, scale=False, Gy=None, law="power"):
     counts = np.empty((K, M), np.int64)
     for a, f in enumerate(feats):
         v = np.ascontiguousarray(V[f])
-        lib().orc_mcil_bins(_p(v, C.c_double), n1 * n2, lib().orc_mcil_squared(f), 1 if law == "linear" else 0,
+        lib().orc_mcil_bins(_p(v, C.c_double), n1 * n2, lib().orc_mcil_squared(f),
+                            {"power": 0, "linear": 1, "fitted": 2}[law],
                             float(b or 0.0), M,
                             _p(radii[a], C.c_double), _p(bins[a], C.c_uint8), _p(counts[a], C.c_int64))
     return {"features": feats, "values": V, "radii": radii, "bins": bins, "counts": counts,

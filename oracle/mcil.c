@@ -184,8 +184,11 @@ void orc_mcil_values(const float *X1, const float *Ax1, const float *Ay1, int64_
    distance): squared features R0 = sqrt(max V), K = #{k : V < R_k * R_k};
    value features R0 = max V, K = #{k : V < R_k}.  law 0: R_k = R_{k-1} / b;
    law 1 (the linear law, Sec. 2.1 / Sec. 3.2): R_min = sqrt(min V) (value
-   features: min V), h = (R0 - R_min) / M, R_k = R0 - k h.
+   features: min V), h = (R0 - R_min) / M, R_k = R0 - k h; law 2 (the power
+   law with the decay fitted to the range): R_k = R_{k-1} / b with b =
+   orc_fitted_b(R0 / R_min, M) (cil.c).
    radii[0] = R0, radii[1..M] = R_1..R_M. */
+double orc_fitted_b(double c, int M);
 void orc_mcil_bins(const double *V, int64_t np, int squared, int law, double b, int M, double *radii,
                    uint8_t *bins, int64_t *counts)
 {
@@ -204,6 +207,10 @@ void orc_mcil_bins(const double *V, int64_t np, int squared, int law, double b, 
             radii[k] = R - kh;
         }
     } else {
+        if (law == 2) {
+            const double Rm = squared ? sqrt(mn) : mn;
+            b = orc_fitted_b(R / Rm, M);
+        }
         for (int k = 1; k <= M; ++k) {
             R = R / b;
             radii[k] = R;

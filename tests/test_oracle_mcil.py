@@ -190,3 +190,15 @@ def test_linear_law_by_hand():
     for a in range(2):
         assert o["radii"][a].tolist() == [6.0, 5.0, 4.0, 3.0, 2.0]
         assert o["counts"][a].tolist() == [3, 2, 1, 0]
+
+
+def test_fitted_law_by_hand():
+    # patterns (v, 0) on a line: set 1 = {0}, set 2 = {1, 2, 8}: L2 and Linf
+    # are both |v - v'|: R0 = 8, R_min = 1, M = 3 -> b = 2, radii 4, 2, 1,
+    # counts 2, 1, 0 (worked by hand)
+    X1 = np.array([[0.0, 0.0]], np.float32)
+    X2 = np.array([[1.0, 0.0], [2.0, 0.0], [8.0, 0.0]], np.float32)
+    o = oracle.mcil(X1, X2, 2, 1, None, 3, mask=0x03, Gy=1, law="fitted")
+    for a in range(2):
+        assert o["radii"][a].tolist() == [8.0, 4.0, 2.0, 1.0]
+        assert o["counts"][a].tolist() == [2, 1, 0]
