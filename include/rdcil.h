@@ -612,6 +612,18 @@ rd_status mcil_features_linear_rect(const float *d_X1, int64_t ld1, int64_t n1, 
                                     uint8_t *d_bins, int64_t *d_counts, double *d_C, int64_t *d_n_exact,
                                     void *d_work, size_t work_bytes, void *stream);
 
+/* mcil_features_fitted_rect — mcil_features_rect with the power law fitted
+ * to each feature's range (Sec. 2.1 / Sec. 3.2): R0 and R_min as for
+ * mcil_features_linear_rect, b the fitted decay of cil_features_fitted
+ * (the smallest double whose sequentially rounded M-th power reaches
+ * R0 / R_min), R_k = R_{k-1} / b.  Everything else as for
+ * mcil_features_rect; no b. */
+rd_status mcil_features_fitted_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                    int64_t ld2, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
+                                    int32_t features, int32_t scale, int32_t M, double *d_radii_out,
+                                    uint8_t *d_bins, int64_t *d_counts, double *d_C, int64_t *d_n_exact,
+                                    void *d_work, size_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Adjoint: gradient of a sigmoid-smoothed correlation integral with respect
  * to the four parameters of one group (the paper itself is gradient-free;

@@ -87,6 +87,8 @@ _SIGS = {
                                   _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "mcil_features_linear_rect": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _i32,
                                          _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "mcil_features_fitted_rect": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _i32,
+                                         _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "rd_kernel_launches": (_u64, []),
     "rd_set_spin_limit": (None, [C.c_uint32]),
     "rd_n_variants": (_i32, []),
@@ -506,11 +508,12 @@ def mcil_workspace(n1, n2, G, n_species, features=63, scale=False, M=16, device=
 def mcil(X1, X2, G, n_species, b=1.3, M=16, features=63, scale=False, work=None, Gy=None, law="power"):
     """Multi-feature correlation integral of two pattern sets (rows of n_species
     Gy x G fields, read in place; Gy = G by default, 1 for 1-D patterns).
-    law "power" (R0 b^-k) or "linear" (R0 - k (R0 - R_min) / M, b unused).
+    law "power" (R0 b^-k), "linear" (R0 - k (R0 - R_min) / M, b unused) or
+    "fitted" (R0 b^-k with b fitted so that R_M = R_min, b unused).
     Returns radii [K, M+1], bins [K, n1, n2], counts [K, M], C [K*M] and
     n_exact for the K selected features."""
-    if law not in ("power", "linear"):
-        raise ValueError("law must be 'power' or 'linear'")
+    if law not in ("power", "linear", "fitted"):
+        raise ValueError("law must be 'power', 'linear' or 'fitted'")
     Gy = G if Gy is None else Gy
     X1, ld1, n1, d = _as_rows(X1)
     X2, ld2, n2, d2 = _as_rows(X2)
@@ -525,8 +528,9 @@ def mcil(X1, X2, G, n_species, b=1.3, M=16, features=63, scale=False, work=None,
     counts = torch.empty((K, M), dtype=torch.int64, device=dev)
     Cv = torch.empty(K * M, dtype=torch.float64, device=dev)
     nex = torch.zeros(1, dtype=torch.int64, device=dev)
-    if law == "linear":
-        _check("mcil_features_linear_rect", lib().mcil_features_linear_rect(
+    if law in ("linear", "fitted"):
+        fn = "mcil_features_%s_rect" % law
+        _check(fn, getattr(lib(), fn)(
             _ptr(X1), ld1, n1, _ptr(X2), ld2, n2, int(Gy), int(G), int(n_species), int(features),
             1 if scale else 0, int(M), _ptr(radii), _ptr(bins), _ptr(counts), _ptr(Cv), _ptr(nex), _ptr(work),
             work.numel(), _stream()))

@@ -58,7 +58,7 @@ __host__ __device__ constexpr bool feat_squared(int f) { return f == 0 || f == 2
 
 struct McilWork {
     int64_t n1, n2, np, d0, dex, dey;
-    int Gy, Gx, nsp, mask, M, law;   // law 0 power, 1 linear
+    int Gy, Gx, nsp, mask, M, law;   // law 0 power, 1 linear, 2 fitted power (1 and 2 need the minima)
     float *S1, *S2;                 // min-max scaled patterns (scale only)
     float *Ax1, *Ay1, *Ax2, *Ay2;   // forward-difference patterns
     void *cw[3];                    // CIL workspaces for the pattern, Dx, Dy arrays
@@ -421,7 +421,7 @@ __global__ void intervals_kernel(McilWork w, QIv qi, double h, double h2, double
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
         if ((threadIdx.x & 31) == 0 && (w.mask & (1 << f))) atomic_max_nonneg(&w.scal[2 + f], v);
-        if (w.law == 1) {
+        if (w.law >= 1) {
             double u = ub[f];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) u = fmin(u, __shfl_xor_sync(0xffffffffu, u, o));
@@ -440,7 +440,7 @@ __global__ void candidates_kernel(McilWork w) {
     for (int f = 0; f < NF; ++f)
         if (w.mask & (1 << f)) {
             cand |= w.vhi[f * w.np + q] >= __longlong_as_double((long long)w.scal[2 + f]);
-            if (w.law == 1) cand |= w.vlo[f * w.np + q] <= read_min_nonneg(&w.scal[16 + f]);
+            if (w.law >= 1) cand |= w.vlo[f * w.np + q] <= read_min_nonneg(&w.scal[16 + f]);
         }
     if (cand) {
         w.flag[q] = 1;
@@ -742,7 +742,7 @@ __global__ void lb2_kernel_m(McilWork w) {
         for (int f = 0; f < NF; ++f)
             if (w.mask & (1 << f)) {
                 atomic_max_nonneg(&w.scal[2 + f], w.vlo[f * w.np + q]);
-                if (w.law == 1) atomic_min_nonneg(&w.scal[16 + f], w.vhi[f * w.np + q]);
+                if (w.law >= 1) atomic_min_nonneg(&w.scal[16 + f], w.vhi[f * w.np + q]);
             }
     }
 }
@@ -760,7 +760,7 @@ __global__ void cand2_kernel_m(McilWork w) {
             if (!(w.mask & (1 << f))) continue;
             const double lo = w.vlo[f * w.np + q], hi = w.vhi[f * w.np + q];
             need |= (lo < hi) && hi >= __longlong_as_double((long long)w.scal[2 + f]);
-            if (w.law == 1) need |= (lo < hi) && lo <= read_min_nonneg(&w.scal[16 + f]);
+            if (w.law >= 1) need |= (lo < hi) && lo <= read_min_nonneg(&w.scal[16 + f]);
         }
         if (need) {
             w.flag[q] = 1;
@@ -773,6 +773,26 @@ __global__ void cand2_kernel_m(McilWork w) {
 // ---------------------------------------------------------------------------
 // 5. radii from the exact maxima; thresholds
 // ---------------------------------------------------------------------------
+// the fitted decay of the power law (the same definition as the
+// single-feature correlation integral's): the smallest double whose M-th
+// power, M - 1 sequential products rounded to nearest, reaches c, by
+// halving [1, c]; 1 when c <= 1, +inf when c is not finite
+__device__ double fitted_b_m(double c, int M) {
+    if (!(c < __longlong_as_double(0x7ff0000000000000ll))) return __longlong_as_double(0x7ff0000000000000ll);
+    if (!(c > 1.0)) return 1.0;
+    double lo = 1.0, hi = c;
+    for (int it = 0; it < 400; ++it) {
+        const double half = __dmul_rn(__dsub_rn(hi, lo), 0.5);
+        const double mid = __dadd_rn(lo, half);
+        if (!(mid > lo) || !(mid < hi)) break;
+        double pw = mid;
+        for (int k = 1; k < M; ++k) pw = __dmul_rn(pw, mid);
+        if (pw < c) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
 __global__ void radii_kernel_m(McilWork w, double b, double *radii_out) {
     // one warp per feature; the maximum is among the queued candidates
     const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -807,9 +827,11 @@ __global__ void radii_kernel_m(McilWork w, double b, double *radii_out) {
         double r = feat_squared(f) ? __dsqrt_rn(mx) : mx;
         R[0] = r;
         const double R0 = r;
-        const double hl = w.law == 1 ? __ddiv_rn(__dsub_rn(R0, feat_squared(f) ? __dsqrt_rn(mn) : mn), (double)w.M) : 0.0;
+        const double Rm = feat_squared(f) ? __dsqrt_rn(mn) : mn;
+        const double hl = w.law == 1 ? __ddiv_rn(__dsub_rn(R0, Rm), (double)w.M) : 0.0;
+        const double bf = w.law == 2 ? fitted_b_m(__ddiv_rn(R0, Rm), w.M) : b;
         for (int k = 1; k <= w.M; ++k) {
-            r = w.law == 1 ? __dsub_rn(R0, __dmul_rn((double)k, hl)) : __ddiv_rn(r, b);
+            r = w.law == 1 ? __dsub_rn(R0, __dmul_rn((double)k, hl)) : __ddiv_rn(r, bf);
             R[k] = r;
             w.thr[f * 32 + k - 1] = feat_squared(f) ? __dmul_rn(r, r) : r;
         }
@@ -1062,6 +1084,15 @@ extern "C" rd_status mcil_features_rect(const float *d_X1, int64_t ld1, int64_t 
                                         size_t work_bytes, void *stream) {
     return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, Gy, Gx, n_species, features, scale, b, 0, M, d_radii_out, d_bins,
                     d_counts, d_C, d_n_exact, d_work, work_bytes, stream);
+}
+
+extern "C" rd_status mcil_features_fitted_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                               int64_t ld2, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
+                                               int32_t features, int32_t scale, int32_t M, double *d_radii_out,
+                                               uint8_t *d_bins, int64_t *d_counts, double *d_C, int64_t *d_n_exact,
+                                               void *d_work, size_t work_bytes, void *stream) {
+    return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, Gy, Gx, n_species, features, scale, 2.0, 2, M, d_radii_out,
+                    d_bins, d_counts, d_C, d_n_exact, d_work, work_bytes, stream);
 }
 
 extern "C" rd_status mcil_features_linear_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,

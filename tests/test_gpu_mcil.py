@@ -266,3 +266,47 @@ def test_linear_rdode_patterns(p):
     assert_same(a, oa)
     assert_same(c, oc)
     assert bins.shape == (6, 24, 24)
+
+
+# ---------------------------------------------------------------------------
+# the power law fitted to each feature's range (Sec. 2.1 / Sec. 3.2)
+# ---------------------------------------------------------------------------
+def run_fitted(p, X1, X2, Gx, nsp, M=13, features=63, scale=False, Gy=None):
+    t1 = torch.from_numpy(np.ascontiguousarray(X1)).cuda()
+    t2 = torch.from_numpy(np.ascontiguousarray(X2)).cuda()
+    g = p.mcil(t1, t2, Gx, nsp, M=M, features=features, scale=scale, Gy=Gy, law="fitted")
+    o = oracle.mcil(X1, X2, Gx, nsp, None, M, mask=features, scale=scale, Gy=Gy, law="fitted")
+    torch.cuda.synchronize()
+    assert int(g["n_exact"]) >= 0
+    assert_same(g, o)
+    return g, o
+
+
+def test_fitted_hand_example(p):
+    X1 = np.array([[0.0, 0.0]], np.float32)
+    X2 = np.array([[1.0, 0.0], [2.0, 0.0], [8.0, 0.0]], np.float32)
+    g, _ = run_fitted(p, X1, X2, 2, 1, M=3, features=0x03, Gy=1)
+    for a in range(2):
+        assert g["radii"][a].cpu().numpy().tolist() == [8.0, 4.0, 2.0, 1.0]
+        assert g["counts"][a].cpu().numpy().tolist() == [2, 1, 0]
+
+
+@pytest.mark.parametrize("n1,n2,Gy,Gx,nsp", [(3, 5, 4, 4, 2), (20, 17, 32, 32, 2), (64, 64, 64, 64, 1),
+                                             (7, 9, 1, 64, 2), (33, 40, 8, 32, 2)])
+@pytest.mark.parametrize("scale", [False, True])
+def test_fitted_law_bit_exact(p, n1, n2, Gy, Gx, nsp, scale):
+    X = W.cosine_patterns(n1 + n2, Gx, nsp, 171 + Gx + n1, amp=1.2, offset=0.7)
+    X = np.ascontiguousarray(X.reshape(n1 + n2, nsp, Gx, Gx)[:, :, :Gy, :].reshape(n1 + n2, -1))
+    run_fitted(p, X[:n1], X[n1:], Gx, nsp, M=13, scale=scale, Gy=Gy)
+
+
+def test_fitted_degenerate(p):
+    rng = np.random.default_rng(12)
+    G = 8
+    X1 = rng.standard_normal((6, G * G)).astype(np.float32)
+    X2 = np.concatenate([rng.standard_normal((5, G * G)).astype(np.float32), X1[2:3]])
+    g, _ = run_fitted(p, X1, X2, G, 1, M=13)   # R_min = 0 for every feature: b = +inf
+    assert (g["radii"][:, 1:].cpu().numpy() == 0.0).all()
+    X1 = rng.standard_normal((1, G * G)).astype(np.float32)
+    X2 = rng.standard_normal((1, G * G)).astype(np.float32)
+    run_fitted(p, X1, X2, G, 1, M=5)           # one pair: b = 1
