@@ -23,16 +23,25 @@
 
 namespace rdcil {
 
+// The reverse sweep records segment q (re-integrating it from its
+// checkpoint into a trajectory buffer) on an auxiliary stream while the main
+// stream sweeps an earlier-recorded segment backwards; ADJ_NB trajectory
+// buffers let the recordings, which depend only on their checkpoints, run
+// ahead (events order each buffer's reuse after its reverse sweep).
+static constexpr int ADJ_NB = 3;
+
 struct AdjScratch {
     float *ckpt = nullptr;    // [n_seg][n_real][2G^2]
-    float *traj = nullptr;    // [n_real][C][2G^2]
-    float *cur = nullptr;     // [n_real][2G^2]
+    float *traj = nullptr;    // [ADJ_NB][n_real][C][2G^2]
+    float *cur = nullptr;     // [1 + ADJ_NB][n_real][2G^2]: the forward pass, then one per buffer
     float *lam = nullptr;     // [n_real][2G^2]
     double *W = nullptr;      // [n1][n2]
     double *Cbuf = nullptr;   // [32]
     int32_t *sets = nullptr;  // [n1 + n2]
     int32_t *active = nullptr;  // [n_real] realisation appears in a set
     size_t ckpt_f = 0, traj_f = 0, cur_f = 0, W_d = 0, sets_n = 0;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, rec[ADJ_NB] = {}, rev[ADJ_NB] = {};
 };
 
 rd_status adjoint_reserve(Handle &h) {
@@ -54,13 +63,19 @@ rd_status adjoint_reserve(Handle &h) {
     AdjScratch *a = new AdjScratch();
     a->ckpt_f = ck; a->traj_f = tr; a->cur_f = cu; a->W_d = wd; a->sets_n = sn;
     bool ok = cudaMalloc(&a->ckpt, ck * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&a->traj, tr * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&a->cur, cu * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&a->traj, (size_t)ADJ_NB * tr * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&a->cur, (size_t)(1 + ADJ_NB) * cu * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&a->lam, cu * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&a->W, wd * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&a->Cbuf, 32 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&a->sets, sn * sizeof(int32_t)) == cudaSuccess &&
               cudaMalloc(&a->active, (sn / 2 + 1) * sizeof(int32_t)) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&a->aux, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&a->join, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < ADJ_NB && ok; ++b)
+        ok = cudaEventCreateWithFlags(&a->rec[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&a->rev[b], cudaEventDisableTiming) == cudaSuccess;
     h.plan = a;
     return ok ? RD_OK : RD_ERR_OOM;
 }
@@ -70,6 +85,13 @@ void adjoint_release(Handle &h) {
     if (!a) return;
     cudaFree(a->ckpt); cudaFree(a->traj); cudaFree(a->cur); cudaFree(a->lam);
     cudaFree(a->W); cudaFree(a->Cbuf); cudaFree(a->sets); cudaFree(a->active);
+    for (int b = 0; b < ADJ_NB; ++b) {
+        if (a->rec[b]) cudaEventDestroy(a->rec[b]);
+        if (a->rev[b]) cudaEventDestroy(a->rev[b]);
+    }
+    if (a->fork) cudaEventDestroy(a->fork);
+    if (a->join) cudaEventDestroy(a->join);
+    if (a->aux) cudaStreamDestroy(a->aux);
     delete a;
     h.plan = nullptr;
 }
@@ -368,19 +390,33 @@ extern "C" rd_status rd_adjoint(rd_handle *hh, int32_t group, const float *d_fie
     else if (g.model == RD_GM) { cf.sc[2] = g.dt; cf.sc[3] = -g.p[2] * g.dt; }
     else if (g.model == RD_BZ) { cf.sc[2] = g.dt; cf.sc[3] = g.dt; }
     else { cf.sc[2] = 0.0; cf.sc[3] = 0.0; }
-    for (int64_t q = nseg - 1; q >= 0; --q) {
-        int64_t len = std::min(C, N - q * C);
-        RD_CUDA_TRY(cudaMemcpyAsync(a.cur, a.ckpt + q * mall, mall * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        rd_status st = launch_record_group(gl, a.cur, a.traj, len, s);
+    // recordings on the auxiliary stream (after everything above), reverse
+    // sweeps on s, buffer b = k mod ADJ_NB for the k-th segment from the end
+    RD_CUDA_TRY(cudaEventRecord(a.fork, s));
+    RD_CUDA_TRY(cudaStreamWaitEvent(a.aux, a.fork, 0));
+    const size_t trb = a.traj_f;   // floats per trajectory buffer
+    int64_t k = 0;
+    for (int64_t q = nseg - 1; q >= 0; --q, ++k) {
+        const int b = (int)(k % ADJ_NB);
+        const int64_t len = std::min(C, N - q * C);
+        float *traj = a.traj + (size_t)b * trb, *cur = a.cur + (size_t)(1 + b) * a.cur_f;
+        if (k >= ADJ_NB) RD_CUDA_TRY(cudaStreamWaitEvent(a.aux, a.rev[b], 0));   // the buffer's last sweep done
+        RD_CUDA_TRY(cudaMemcpyAsync(cur, a.ckpt + q * mall, mall * sizeof(float), cudaMemcpyDeviceToDevice, a.aux));
+        rd_status st = launch_record_group(gl, cur, traj, len, a.aux);
         if (st) return st;
+        RD_CUDA_TRY(cudaEventRecord(a.rec[b], a.aux));
+        RD_CUDA_TRY(cudaStreamWaitEvent(s, a.rec[b], 0));
         const int64_t ts = len * m;
         switch (g.model) {
-            case RD_FHN: st = reverse_G<RD_FHN>(g, a.traj, ts, len, a.lam, cf, d_grad, active, s); break;
-            case RD_GM: st = reverse_G<RD_GM>(g, a.traj, ts, len, a.lam, cf, d_grad, active, s); break;
-            case RD_BZ: st = reverse_G<RD_BZ>(g, a.traj, ts, len, a.lam, cf, d_grad, active, s); break;
-            default: st = reverse_G<RD_DIFF>(g, a.traj, ts, len, a.lam, cf, d_grad, active, s); break;
+            case RD_FHN: st = reverse_G<RD_FHN>(g, traj, ts, len, a.lam, cf, d_grad, active, s); break;
+            case RD_GM: st = reverse_G<RD_GM>(g, traj, ts, len, a.lam, cf, d_grad, active, s); break;
+            case RD_BZ: st = reverse_G<RD_BZ>(g, traj, ts, len, a.lam, cf, d_grad, active, s); break;
+            default: st = reverse_G<RD_DIFF>(g, traj, ts, len, a.lam, cf, d_grad, active, s); break;
         }
         if (st) return st;
+        RD_CUDA_TRY(cudaEventRecord(a.rev[b], s));
     }
+    RD_CUDA_TRY(cudaEventRecord(a.join, a.aux));
+    RD_CUDA_TRY(cudaStreamWaitEvent(s, a.join, 0));
     return RD_OK;
 }
