@@ -256,10 +256,16 @@ __device__ __forceinline__ float max3_abs(float a, float b, float c) {
 // rows), 8 x 8 per thread: thread (ty, tx) takes rows ty + (TA/8) a and
 // columns tx + (TB/8) c, so the shared-memory reads of a warp are
 // broadcasts (rows) or consecutive words (columns)
+// Thread (ty, tx) of RY x RX takes set-1 rows a4 * TA/2 + 4 ty + q and set-2
+// rows c4 * TB/2 + 4 tx + q (a4, c4 in {0, 1}, q < 4): four consecutive
+// rows per 128-bit shared load (broadcast for set 1, 512 contiguous bytes a
+// warp for set 2).  Each K column of a tile is a row of TA (TB) floats
+// padded by 4 to keep 16-byte alignment.
 template <int TA>
 struct MaxTile {
     static constexpr int TB = 16384 / TA, RY = TA / 8, RX = TB / 8;   // RY x RX = 256 threads
-    static constexpr int SA = MX_K * (TA + 1), SB = MX_K * (TB + 1);   // floats per buffer
+    static constexpr int PA = TA + 4, PB = TB + 4;                     // padded K-column rows
+    static constexpr int SA = MX_K * PA, SB = MX_K * PB;               // floats per buffer
     static constexpr size_t SMEM = 2 * (size_t)(SA + SB) * sizeof(float);   // two buffers
 };
 
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(256, 2) maxabs_kernel(const float *__restrict_
                                                         const float *__restrict__ B, int64_t ldb, int64_t n2,
                                                         int64_t d, int64_t kch, float *__restrict__ out) {
     using MT = MaxTile<TA>;
-    constexpr int TB = MT::TB, RY = MT::RY, RX = MT::RX;
+    constexpr int TB = MT::TB, RY = MT::RY, RX = MT::RX, PA = MT::PA, PB = MT::PB;
     static_assert(RY * RX == 256, "thread grid");
     extern __shared__ float4 mx_smem[];
     float *sm = reinterpret_cast<float *>(mx_smem);
@@ -290,13 +296,13 @@ __global__ void __launch_bounds__(256, 2) maxabs_kernel(const float *__restrict_
             const int r = e / MX_K, kk = e - r * MX_K;
             const int64_t k = k0 + kk, ia = i0 + r;
             const bool in = ia < n1 && k < k_hi;
-            cp_async4(sa + kk * (TA + 1) + r, in ? A + ia * lda + k : A, in ? 4 : 0);
+            cp_async4(sa + kk * PA + r, in ? A + ia * lda + k : A, in ? 4 : 0);
         }
         for (int e = threadIdx.x; e < TB * MX_K; e += 256) {
             const int r = e / MX_K, kk = e - r * MX_K;
             const int64_t k = k0 + kk, jb = j0 + r;
             const bool in = jb < n2 && k < k_hi;
-            cp_async4(sb + kk * (TB + 1) + r, in ? B + jb * ldb + k : B, in ? 4 : 0);
+            cp_async4(sb + kk * PB + r, in ? B + jb * ldb + k : B, in ? 4 : 0);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
@@ -323,14 +329,15 @@ __global__ void __launch_bounds__(256, 2) maxabs_kernel(const float *__restrict_
         for (int kk = 0; kk < MX_K; kk += 2) {
             float av[8], bv[8], aw[8], bw[8];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) {
-                av[a] = sa[kk * (TA + 1) + ty + RY * a];
-                aw[a] = sa[(kk + 1) * (TA + 1) + ty + RY * a];
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                bv[c] = sb[kk * (TB + 1) + tx + RX * c];
-                bw[c] = sb[(kk + 1) * (TB + 1) + tx + RX * c];
+            for (int h = 0; h < 2; ++h) {
+                const float4 x0 = *reinterpret_cast<const float4 *>(sa + kk * PA + h * (TA / 2) + 4 * ty);
+                const float4 x1 = *reinterpret_cast<const float4 *>(sa + (kk + 1) * PA + h * (TA / 2) + 4 * ty);
+                const float4 y0 = *reinterpret_cast<const float4 *>(sb + kk * PB + h * (TB / 2) + 4 * tx);
+                const float4 y1 = *reinterpret_cast<const float4 *>(sb + (kk + 1) * PB + h * (TB / 2) + 4 * tx);
+                av[4 * h] = x0.x; av[4 * h + 1] = x0.y; av[4 * h + 2] = x0.z; av[4 * h + 3] = x0.w;
+                aw[4 * h] = x1.x; aw[4 * h + 1] = x1.y; aw[4 * h + 2] = x1.z; aw[4 * h + 3] = x1.w;
+                bv[4 * h] = y0.x; bv[4 * h + 1] = y0.y; bv[4 * h + 2] = y0.z; bv[4 * h + 3] = y0.w;
+                bw[4 * h] = y1.x; bw[4 * h + 1] = y1.y; bw[4 * h + 2] = y1.z; bw[4 * h + 3] = y1.w;
             }
 #pragma unroll
             for (int a = 0; a < 8; ++a)
@@ -343,7 +350,8 @@ __global__ void __launch_bounds__(256, 2) maxabs_kernel(const float *__restrict_
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int64_t i = i0 + ty + RY * a, j = j0 + tx + RX * c;
+            const int64_t i = i0 + (a >> 2) * (TA / 2) + 4 * ty + (a & 3);
+            const int64_t j = j0 + (c >> 2) * (TB / 2) + 4 * tx + (c & 3);
             if (i < n1 && j < n2 && m[a][c] > 0.f)
                 atomicMax(reinterpret_cast<unsigned int *>(out) + i * n2 + j, __float_as_uint(m[a][c]));
         }
