@@ -265,6 +265,24 @@ typedef struct rd_rkc_opts {
 rd_status rd_integrate_rkc(rd_handle *h, float *d_fields, const rd_rkc_opts *opts, int64_t *d_stats,
                            double *d_residual, void *stream);
 
+/* rd_integrate_imex — semi-implicit (IMEX) Euler in place: every
+ * realisation of every group takes its group's n_steps steps of size dt,
+ *   (I - dt D_s L_h) w_s^{n+1} = w_s^n + dt R_s(u^n, v^n),   s = u, v,
+ * diffusion implicit (L_h the 5-point Laplacian with mirrored Neumann
+ * ghosts, App. B.1.1), reaction explicit (Sec. 4.1 kinetics).  Sec. 5.1 and
+ * App. B.2 contrast explicit stepping with implicit stepping through linear
+ * solves; here the solve is exact up to rounding, through the orthonormal
+ * cosine (DCT-II) basis that diagonalises L_h, so dt is not bound by the
+ * diffusive limit h^2 / (4 D) (the reaction still bounds it).
+ * d_fields as for rd_integrate_batch; d_residual (nullable) as for
+ * rd_integrate_batch, of the final state.  One CTA per realisation, groups
+ * in order on `stream`.  Models RD_FHN, RD_GM, RD_DIFF, RD_BZ on G = 32 or
+ * 64; RD_ERR_UNSUPPORTED (nothing launched) for any other group in h.  A
+ * non-finite final state sets RD_ERR_NONFINITE in the status word when a
+ * residual is asked for.  Precision: FP32 state and products; the
+ * transform tables are formed in FP64 and rounded once. */
+rd_status rd_integrate_imex(rd_handle *h, float *d_fields, double *d_residual, void *stream);
+
 /* Tile shapes of the rd_integrate_rkc kernel (nodes per thread, TY x TX):
  * G = 32: 0 = 2x1 (512 threads, default), 1 = 4x1 (256), 2 = 2x2 (256);
  * G = 64: 0 = 4x2 (512 threads), 1 = 4x4 (256, default), 2 = 2x4 (512).

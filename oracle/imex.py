@@ -71,9 +71,11 @@ def imex_run(model, p, dt, n_steps, w0, factors=None):
     G = w.shape[-1]
     if factors is None:
         factors = imex_matrices(G, (p[0], p[1]), dt)
-    for r in range(w.shape[0]):
-        for _ in range(int(n_steps)):
-            b = reaction_step(model, p, dt, w[r])
-            for s in range(2):
-                w[r, s] = sla.lu_solve(factors[s], b[s].reshape(-1)).reshape(G, G)
+    n = w.shape[0]
+    for _ in range(int(n_steps)):
+        b = np.stack([reaction_step(model, p, dt, w[r]) for r in range(n)])
+        for s in range(2):
+            # all realisations as the columns of one right-hand side
+            x = sla.lu_solve(factors[s], b[:, s].reshape(n, G * G).T)
+            w[:, s] = x.T.reshape(n, G, G)
     return w

@@ -52,6 +52,7 @@ _SIGS = {
     "rd_integrate_reference": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "rd_integrate_f64": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "rd_integrate_rkc": (_i32, [_vp, _vp, C.POINTER(RdRkcOpts), _vp, _vp, _vp]),
+    "rd_integrate_imex": (_i32, [_vp, _vp, _vp, _vp]),
     "rd_rkc_n_variants": (_i32, []),
     "rd_rkc_set_variant": (_i32, [_i32, _i32]),
     "rd_rkc_get_variant": (_i32, [_i32]),
@@ -271,6 +272,16 @@ class Simulation:
         _check("rd_integrate_rkc", lib().rd_integrate_rkc(self.handle, _ptr(self.fields), C.byref(o),
                                                           _ptr(st), _ptr(res), _stream()))
         return st, res
+
+    def integrate_imex(self, residual=False):
+        """Semi-implicit Euler in place: each group's n_steps steps of its dt,
+        diffusion implicit (solved in the cosine basis), reaction explicit.
+        Returns the residual [n_real, 2] or None."""
+        res = (torch.empty((self.n_real_total, 2), dtype=torch.float64, device=self.device)
+               if residual else None)
+        _check("rd_integrate_imex", lib().rd_integrate_imex(self.handle, _ptr(self.fields), _ptr(res),
+                                                            _stream()))
+        return res
 
     def set_stream_depth(self, depth):
         """Euler steps fused per launch of the streaming stepper (1, 2, 4, 8)."""

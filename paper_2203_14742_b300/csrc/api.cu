@@ -214,6 +214,19 @@ extern "C" rd_status rd_integrate_rkc(rd_handle *hh, float *d_fields, const rd_r
     return RD_OK;
 }
 
+extern "C" rd_status rd_integrate_imex(rd_handle *hh, float *d_fields, double *d_residual, void *stream) {
+    if (!hh || !d_fields) return RD_ERR_INVALID_ARG;
+    Handle &h = hh->h;
+    for (int gi = 0; gi < h.n_groups; ++gi)
+        if (!imex_supported(h.h_groups[gi])) return RD_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int gi = 0; gi < h.n_groups; ++gi) {
+        rd_status st = launch_imex_group(h.h_groups[gi], d_fields, d_residual, h.d_status, s);
+        if (st != RD_OK) return st;
+    }
+    return RD_OK;
+}
+
 extern "C" int32_t rd_rkc_n_variants(void) { return rkc_n_variants(); }
 extern "C" rd_status rd_rkc_set_variant(int32_t G, int32_t variant) {
     return rkc_set_variant(G, variant) ? RD_OK : RD_ERR_INVALID_ARG;

@@ -1,0 +1,318 @@
+// Semi-implicit (IMEX) Euler integration of the batched 2-D reaction-
+// diffusion systems: diffusion implicit, reaction explicit,
+//   (I - dt D_s L_h) w_s^{n+1} = w_s^n + dt R_s(u^n, v^n),   s = u, v,
+// with L_h the 5-point Laplacian with mirrored Neumann ghosts (App. B.1.1;
+// Sec. 4.1 kinetics).  Sec. 5.1 and App. B.2 weigh explicit stepping
+// against implicit stepping with linear solves; this is the implicit
+// treatment of the stiff (diffusive) part alone, so the time step is bound
+// by the reaction rather than by h^2 / (4 D).
+//
+// The solve.  With ghost = edge node the 1-D second difference is
+// diagonalised by the orthonormal DCT-II,
+//   C[p][x] = a_p cos(pi p (2x + 1) / (2G)),  a_0 = sqrt(1/G), a_p = sqrt(2/G),
+// with eigenvalue -mu_p, mu_p = 4 sin^2(pi p / (2G)) (times (G-1)^2), so
+//   w^{n+1} = C^T ((C b C^T) o S) C,   S[q][p] = 1 / (1 + dt D (G-1)^2 (mu_p + mu_q)),
+// b the explicit right side: four dense G x G x G products per species and
+// step, exact up to rounding (no iteration).
+//
+// Increment form.  Subtracting (I - dt D L_h) w^n from both sides gives the
+// same step as
+//   (I - dt D_s L_h) d_s = dt F_s(w^n),   w_s^{n+1} = w_s^n + d_s,
+// F = D L_h w + R the explicit right-hand side, so the transforms carry the
+// small increment and their FP32 rounding is relative to it rather than to
+// the field (with b itself the rounding of four products of the whole field
+// per step built up to 2e-5 over 300 FHN steps); at a steady state F = 0
+// and the state stays in place.
+//
+// B300 design.  One CTA per realisation keeps both species, the transform
+// matrices C and C^T, both divisor tables and, per species, an increment
+// and a product buffer in shared memory for the whole run (G = 64: 174 KB); nothing goes to HBM between
+// steps.  The two halves of the block take the two species' products side
+// by side; a thread accumulates a 4 x 4 output tile in FP32 FMAs from one
+// broadcast float4 of the left operand (stored k-major) and one float4 of
+// the right operand per k.  The first and third product store their
+// result transposed, which is the k-major operand the next product wants;
+// the divisors are applied in the second product's epilogue and the
+// increment is added to the state in the fourth's.  The tables
+// are computed once per G in FP64 (cospi, sinpi) and rounded once; the
+// divisors are formed per CTA in FP32 from mu.  GM and BZ states are the
+// deviation from the FP32 equilibrium (the constant lies in mode (0, 0),
+// whose divisor is 1, so the solve commutes with the shift), which keeps
+// the transforms' rounding relative to the pattern rather than to the
+// equilibrium value.
+#include <cmath>
+#include <mutex>
+#include "common.cuh"
+#include "tile.cuh"
+
+namespace rdcil {
+
+// tab = [C (G x G) | C^T (G x G) | mu (G)], row-major, FP32.
+__global__ void imex_table_kernel(int G, float *__restrict__ tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < G * G) {
+        const int p = i / G, x = i - p * G;
+        const double a = p == 0 ? sqrt(1.0 / (double)G) : sqrt(2.0 / (double)G);
+        // p (2x + 1) / (2G) is exact in FP64 for the grid sides used
+        const float c = (float)(a * cospi((double)(p * (2 * x + 1)) / (double)(2 * G)));
+        tab[p * G + x] = c;
+        tab[G * G + x * G + p] = c;
+    }
+    if (i < G) {
+        const double s = sinpi((double)i / (double)(2 * G));
+        tab[2 * G * G + i] = (float)(4.0 * s * s);
+    }
+}
+
+// dt F(w) at one node from the neighbour sums su = (N + S) + (W + E) of the
+// state registers (deviation form for GM and BZ, as in euler_cell; the
+// Laplacian of a deviation is that of the field):
+//   FHN: d_u = cu (su - 4u) + dt (u - u^3 - v),   d_v = cv (sv - 4v) + dt eps (u - a v)
+//   GM:  d_a = cu (sa - 4a) + k2 U (a - mu b + e0) / V,
+//        d_b = cv (sb - 4b) + k2 (a (a + 2 u0) - b + e1)
+//   BZ:  d_a = cu (sa - 4a) + dt (e0 + c1 a + P),  d_b = cv (sb - 4b) + dt (-e0 + c2 a - P)
+// with cu = Du dt (G-1)^2, cv = Dv dt (G-1)^2.
+template <int MODEL>
+__device__ __forceinline__ void incr(float u, float v, float su, float sv, const CoefF &c, float &du, float &dv) {
+    const float lu = c.cu * fmaf(-4.f, u, su), lv = c.cv * fmaf(-4.f, v, sv);
+    if (MODEL == RD_FHN) {
+        const float ru = fmaf(-u * u, u, u - v);
+        const float rv = fmaf(-c.k3, v, u);
+        du = fmaf(c.k1, ru, lu);
+        dv = fmaf(c.k2, rv, lv);
+    } else if (MODEL == RD_GM) {
+        const float a = u, b = v;
+        const float U = a + c.u0, V = b + c.v0;
+        const float t = fmaf(-c.k3, b, a + c.e0);
+        const float f = __fdividef(U * t, V);
+        du = fmaf(c.k2, f, lu);
+        dv = fmaf(c.k2, fmaf(a, a + c.tu0, c.e1 - b), lv);
+    } else if (MODEL == RD_BZ) {
+        const float a = u, b = v;
+        const float U = a + c.u0;
+        const float P = fmaf(c.v0 * a, a, (U * U) * b);
+        const float f = fmaf(c.c1, a, c.e0 + P);
+        const float g = fmaf(c.c2, a, -c.e0 - P);
+        du = fmaf(c.k1, f, lu);
+        dv = fmaf(c.k1, g, lv);
+    } else {
+        du = lu;
+        dv = lv;
+    }
+}
+
+// dt F of the four nodes (y, x..x+3) of both species into Xu, Xv, with
+// mirrored ghosts at the edges.
+template <int MODEL, int G>
+__device__ __forceinline__ void incr4(const float *__restrict__ Wu, const float *__restrict__ Wv,
+                                      float *__restrict__ Xu, float *__restrict__ Xv, int y, int x,
+                                      const CoefF &cf) {
+    constexpr int LD = G + 4;
+    const int o = y * LD + x, on = (y > 0 ? o - LD : o), os = (y < G - 1 ? o + LD : o);
+    float su[4], sv[4], cu[4], cv[4];
+    {
+        const float4 c = *reinterpret_cast<const float4 *>(Wu + o);
+        const float4 n = *reinterpret_cast<const float4 *>(Wu + on);
+        const float4 s = *reinterpret_cast<const float4 *>(Wu + os);
+        const float w = x > 0 ? Wu[o - 1] : c.x, e = x + 4 < G ? Wu[o + 4] : c.w;
+        cu[0] = c.x; cu[1] = c.y; cu[2] = c.z; cu[3] = c.w;
+        su[0] = (n.x + s.x) + (w + c.y);
+        su[1] = (n.y + s.y) + (c.x + c.z);
+        su[2] = (n.z + s.z) + (c.y + c.w);
+        su[3] = (n.w + s.w) + (c.z + e);
+    }
+    {
+        const float4 c = *reinterpret_cast<const float4 *>(Wv + o);
+        const float4 n = *reinterpret_cast<const float4 *>(Wv + on);
+        const float4 s = *reinterpret_cast<const float4 *>(Wv + os);
+        const float w = x > 0 ? Wv[o - 1] : c.x, e = x + 4 < G ? Wv[o + 4] : c.w;
+        cv[0] = c.x; cv[1] = c.y; cv[2] = c.z; cv[3] = c.w;
+        sv[0] = (n.x + s.x) + (w + c.y);
+        sv[1] = (n.y + s.y) + (c.x + c.z);
+        sv[2] = (n.z + s.z) + (c.y + c.w);
+        sv[3] = (n.w + s.w) + (c.z + e);
+    }
+    float du[4], dv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) incr<MODEL>(cu[j], cv[j], su[j], sv[j], cf, du[j], dv[j]);
+    *reinterpret_cast<float4 *>(Xu + o) = make_float4(du[0], du[1], du[2], du[3]);
+    *reinterpret_cast<float4 *>(Xv + o) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+}
+
+// out[r][c] = sum_k At[k][r] B[k][c] over a G x G product in shared memory
+// (leading dimension G + 4).  The calling thread owns rows 4ty..4ty+3 and
+// columns 4tx..4tx+3.  TRANS stores out[c][r] instead; SCALE multiplies by
+// Sc[r][c] on the way out; ADD adds the result to out.
+template <int G, bool TRANS, bool SCALE, bool ADD = false>
+__device__ __forceinline__ void imex_mm(const float *__restrict__ At, const float *__restrict__ B,
+                                        float *__restrict__ out, const float *__restrict__ Sc, int ty, int tx) {
+    constexpr int LD = G + 4;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const float *pa = At + 4 * ty, *pb = B + 4 * tx;
+#pragma unroll 8
+    for (int k = 0; k < G; ++k) {
+        const float4 a = *reinterpret_cast<const float4 *>(pa + k * LD);
+        const float4 b = *reinterpret_cast<const float4 *>(pb + k * LD);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (TRANS) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<float4 *>(out + (4 * tx + j) * LD + 4 * ty) =
+                make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float4 o = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            if (SCALE) {
+                const float4 s = *reinterpret_cast<const float4 *>(Sc + (4 * ty + i) * LD + 4 * tx);
+                o.x *= s.x; o.y *= s.y; o.z *= s.z; o.w *= s.w;
+            }
+            if (ADD) {
+                const float4 w = *reinterpret_cast<const float4 *>(out + (4 * ty + i) * LD + 4 * tx);
+                o.x += w.x; o.y += w.y; o.z += w.z; o.w += w.w;
+            }
+            *reinterpret_cast<float4 *>(out + (4 * ty + i) * LD + 4 * tx) = o;
+        }
+    }
+}
+
+template <int G>
+constexpr size_t imex_smem() { return sizeof(float) * 10 * (size_t)G * (G + 4); }
+
+template <int MODEL, int G>
+__global__ void __launch_bounds__(2 * (G / 4) * (G / 4))
+rd_imex_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, float a_u, float a_v,
+               const float *__restrict__ tab, int64_t steps, double p0, double p1, double p2, double p3,
+               double *__restrict__ residual, uint32_t *__restrict__ status) {
+    constexpr int LD = G + 4, Q = G / 4, NS = Q * Q, NT = 2 * NS, BUF = G * LD;
+    extern __shared__ __align__(16) float sm[];
+    float *sC = sm, *sCT = sC + BUF, *sS = sCT + BUF, *sW = sS + 2 * BUF, *sX = sW + 2 * BUF, *sT = sX + 2 * BUF;
+    const int tid = threadIdx.x, r = blockIdx.x;
+    float *base = fields + field_offset + (int64_t)r * 2 * G * G;
+    const float *mu = tab + 2 * G * G;
+    for (int q = tid; q < G * Q; q += NT) {
+        const int y = q / Q, x = (q - y * Q) * 4;
+        *reinterpret_cast<float4 *>(sC + y * LD + x) = *reinterpret_cast<const float4 *>(tab + y * G + x);
+        *reinterpret_cast<float4 *>(sCT + y * LD + x) = *reinterpret_cast<const float4 *>(tab + G * G + y * G + x);
+        float4 u = *reinterpret_cast<const float4 *>(base + y * G + x);
+        float4 v = *reinterpret_cast<const float4 *>(base + G * G + y * G + x);
+        to_state<MODEL>(u.x, v.x, cf);
+        to_state<MODEL>(u.y, v.y, cf);
+        to_state<MODEL>(u.z, v.z, cf);
+        to_state<MODEL>(u.w, v.w, cf);
+        *reinterpret_cast<float4 *>(sW + y * LD + x) = u;
+        *reinterpret_cast<float4 *>(sW + BUF + y * LD + x) = v;
+        float su[4], sv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float m = mu[y] + mu[x + j];
+            su[j] = 1.f / fmaf(a_u, m, 1.f);
+            sv[j] = 1.f / fmaf(a_v, m, 1.f);
+        }
+        *reinterpret_cast<float4 *>(sS + y * LD + x) = make_float4(su[0], su[1], su[2], su[3]);
+        *reinterpret_cast<float4 *>(sS + BUF + y * LD + x) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+    }
+    __syncthreads();
+    const int sp = tid / NS, l = tid - sp * NS, ty = l / Q, tx = l - ty * Q;
+    float *F = sW + sp * BUF, *X = sX + sp * BUF, *T = sT + sp * BUF;
+    const float *S = sS + sp * BUF;
+    for (int64_t n = 0; n < steps; ++n) {
+        for (int q = tid; q < G * Q; q += NT) {
+            const int y = q / Q, x = (q - y * Q) * 4;
+            incr4<MODEL, G>(sW, sW + BUF, sX, sX + BUF, y, x, cf);   // dt F(w^n)
+        }
+        __syncthreads();
+        imex_mm<G, true, false>(sCT, X, T, nullptr, ty, tx);        // (C dtF)^T
+        __syncthreads();
+        imex_mm<G, false, true>(T, sCT, X, S, ty, tx);              // (C dtF C^T) o S
+        __syncthreads();
+        imex_mm<G, true, false>(sC, X, T, nullptr, ty, tx);         // (C^T .)^T
+        __syncthreads();
+        imex_mm<G, false, false, true>(T, sC, F, nullptr, ty, tx);  // w += C^T . C
+        __syncthreads();
+    }
+    for (int q = tid; q < G * Q; q += NT) {
+        const int y = q / Q, x = (q - y * Q) * 4;
+        float4 u = *reinterpret_cast<const float4 *>(sW + y * LD + x);
+        float4 v = *reinterpret_cast<const float4 *>(sW + BUF + y * LD + x);
+        from_state<MODEL>(u.x, v.x, cf);
+        from_state<MODEL>(u.y, v.y, cf);
+        from_state<MODEL>(u.z, v.z, cf);
+        from_state<MODEL>(u.w, v.w, cf);
+        *reinterpret_cast<float4 *>(base + y * G + x) = u;
+        *reinterpret_cast<float4 *>(base + G * G + y * G + x) = v;
+    }
+    residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, sC);
+}
+
+static float *g_imex_tab[2] = {nullptr, nullptr};   // G = 32, 64
+static std::once_flag g_imex_once[2];
+static rd_status g_imex_status[2] = {RD_OK, RD_OK};
+
+static rd_status imex_table(int G, cudaStream_t s, const float **tab) {
+    const int gi = G == 64;
+    std::call_once(g_imex_once[gi], [G, gi, s]() {
+        if (cudaMalloc(&g_imex_tab[gi], sizeof(float) * (2 * (size_t)G * G + G)) != cudaSuccess) {
+            g_imex_status[gi] = RD_ERR_OOM;
+            return;
+        }
+        imex_table_kernel<<<(G * G + 127) / 128, 128, 0, s>>>(G, g_imex_tab[gi]);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            g_imex_status[gi] = RD_ERR_CUDA;
+    });
+    *tab = g_imex_tab[gi];
+    return g_imex_status[gi];
+}
+
+template <int MODEL, int G>
+static rd_status launch_imex_mg(const GroupDev &g, float *fields, const float *tab, double *residual,
+                                uint32_t *status, cudaStream_t s) {
+    constexpr size_t smem = imex_smem<G>();
+    auto kern = rd_imex_kernel<MODEL, G>;
+    RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const double h2 = (double)(g.G - 1) * (double)(g.G - 1);
+    const float a_u = (float)(g.dt * g.p[0] * h2), a_v = (float)(g.dt * g.p[1] * h2);
+    kern<<<g.n_real, 2 * (G / 4) * (G / 4), smem, s>>>(fields, g.field_offset, make_coef(g), a_u, a_v, tab, g.n_steps,
+                                                      g.p[0], g.p[1], g.p[2], g.p[3],
+                                                      residual ? residual + 2 * g.real_base : nullptr, status);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+template <int G>
+static rd_status launch_imex_g(const GroupDev &g, float *fields, const float *tab, double *residual,
+                               uint32_t *status, cudaStream_t s) {
+    switch (g.model) {
+        case RD_FHN: return launch_imex_mg<RD_FHN, G>(g, fields, tab, residual, status, s);
+        case RD_GM: return launch_imex_mg<RD_GM, G>(g, fields, tab, residual, status, s);
+        case RD_DIFF: return launch_imex_mg<RD_DIFF, G>(g, fields, tab, residual, status, s);
+        case RD_BZ: return launch_imex_mg<RD_BZ, G>(g, fields, tab, residual, status, s);
+        default: return RD_ERR_UNSUPPORTED;
+    }
+}
+
+bool imex_supported(const GroupDev &g) {
+    return g.model != RD_RDODE && (g.G == 32 || g.G == 64);
+}
+
+rd_status launch_imex_group(const GroupDev &g, float *fields, double *residual, uint32_t *status, cudaStream_t s) {
+    if (!imex_supported(g)) return RD_ERR_UNSUPPORTED;
+    const float *tab = nullptr;
+    rd_status st = imex_table(g.G, s, &tab);
+    if (st != RD_OK) return st;
+    if (g.n_steps == 0 && !residual) return RD_OK;
+    return g.G == 32 ? launch_imex_g<32>(g, fields, tab, residual, status, s)
+                     : launch_imex_g<64>(g, fields, tab, residual, status, s);
+}
+
+}  // namespace rdcil

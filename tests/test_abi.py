@@ -130,3 +130,11 @@ def test_rkc_argument_checks_without_gpu(libpath):
     assert L.rd_rkc_set_variant(64, 0) == 0 and L.rd_rkc_get_variant(64) == 0
     assert L.rd_rkc_set_variant(64, 1) == 0
     assert L.rd_status_str(8) == b"adaptive step control gave up"
+
+
+def test_imex_argument_checks_without_gpu(libpath):
+    # a null handle or field pointer is refused before any device work
+    import paper_2203_14742_b300 as p
+    L = p.lib()
+    assert L.rd_integrate_imex(None, ctypes.c_void_p(256), None, None) == 1
+    assert L.rd_integrate_imex(ctypes.c_void_p(256), None, None, None) == 1

@@ -1,0 +1,140 @@
+"""GPU parity of the semi-implicit (IMEX) Euler stepper (implicit diffusion
+solved in the cosine basis, explicit reaction; Sec. 5.1 and App. B.2 on
+implicit stepping, App. B.1.1 discretisation) against the oracle's dense
+LU solve of the same equations in FP64.
+
+Tolerance.  The GPU solves for the increment d = w^{n+1} - w^n, so each
+step's four FP32 products of length G with an orthonormal matrix round
+relative to d (about sqrt(G) 2^-24 of it per product), and the state takes
+one FP32 rounding per step as in explicit Euler; the implicit diffusion
+damps what is carried over.  Measured: 5e-7 after 300 FHN steps at
+G = 32 and 64, 5e-8 for GM and BZ (relative to the field's maximum).  Held to
+max|gpu - oracle| / max|oracle| <= 1e-5 per realisation and species over
+the step counts below (the fields' own tolerance), and bit-exact where the
+arithmetic is exact (zeros and the homogeneous equilibrium of the
+deviation form)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import imex as OI
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def p():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2203_14742_b300 as pk
+    return pk
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    num = np.abs(a - b).reshape(a.shape[0], 2, -1).max(-1)
+    den = np.abs(b).reshape(b.shape[0], 2, -1).max(-1)
+    return float((num / np.maximum(den, 1e-300)).max())
+
+
+def run_gpu(p, model, G, n, par, dt, steps, noise, seed, residual=False):
+    sim = p.Simulation([p.Group(model, G, n, par, dt, steps, noise, seed)])
+    w0 = sim.group_fields(0).cpu().numpy().copy()
+    res = sim.integrate_imex(residual=residual)
+    torch.cuda.synchronize()
+    return w0, sim.group_fields(0).cpu().numpy(), res
+
+
+# (model, G, n_real, params, dt, steps, noise): dt far above the explicit
+# diffusive limit h^2 / (4 max D) (FHN 64: 1.26e-3; GM 64: 6.3e-3)
+CASES = [
+    (W.FHN, 32, 3, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -6, 200, (-0.05, 0.05)),
+    (W.FHN, 64, 2, (2.9e-4, 0.048, 9.7, 0.93), 2 ** -6, 150, (-0.05, 0.05)),
+    (W.GM, 64, 2, (2.5e-4, 0.01, 1.0, 0.52), 2 ** -4, 150, (0.0, 0.01)),
+    (W.GM, 32, 3, (2.5e-4, 0.01, 1.0, 0.48), 2 ** -4, 200, (0.0, 0.01)),
+    (W.BZ, 64, 2, W.BZ_THETA0, 2 ** -6, 150, (0.0, 0.01)),
+    (W.BZ, 32, 3, (1.6e-3, 1.32e-2, 4.4, 7.1), 2 ** -7, 200, (0.0, 0.01)),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_imex_fields_within_tolerance(p, case):
+    model, G, n, par, dt, steps, noise = case
+    w0, got, res = run_gpu(p, model, G, n, par, dt, steps, noise, 0x77 + G, residual=True)
+    want = OI.imex_run(model, par, dt, steps, w0)
+    err = rel_err(got, want)
+    assert err <= FIELD_TOL, err
+    # the residual is the FP64 right-hand side of the final FP32 state
+    ref = oracle.residual(model, par, got.astype(np.float64))
+    np.testing.assert_allclose(res.cpu().numpy(), ref, rtol=1e-9, atol=1e-12)
+
+
+def test_imex_single_step_matches_closely(p):
+    """One step: only the rounding of one right-hand side and four products.
+    On the first step from uniform noise the increment is as large as the
+    field (the diffusion removes most of the noise at once), so the products'
+    rounding, about sqrt(G) 2^-24 of the increment each, is of the field's
+    size: bound 5e-6."""
+    par = (2.9e-4, 0.048, 9.7, 0.93)
+    w0, got, _ = run_gpu(p, W.FHN, 64, 2, par, 2 ** -6, 1, (-0.05, 0.05), 5)
+    want = OI.imex_run(W.FHN, par, 2 ** -6, 1, w0)
+    assert rel_err(got, want) <= 5e-6
+
+
+@pytest.mark.parametrize("G", [32, 64])
+def test_pure_diffusion_mode_decay_and_mass(p, G):
+    """DIFF: a cosine mode decays by the closed-form factor per step (to
+    FP32 rounding of the tables and products), and the mean is kept."""
+    D = (3e-3, 1e-3)
+    dt, steps = 0.01, 20
+    sim = p.Simulation([p.Group(W.DIFF, G, 1, D, dt, steps, (0.0, 0.0), 1)])
+    x = (np.arange(G) + 0.5) * np.pi / G
+    pq = ((1, 2), (3, 0))
+    modes = [np.outer(np.cos(q * x), np.cos(pp * x)) for (pp, q) in pq]
+    f0 = np.stack([0.5 + modes[0], -0.25 + modes[1]])[None].astype(np.float32)
+    sim.group_fields(0).copy_(torch.from_numpy(f0))
+    sim.integrate_imex()
+    got = sim.group_fields(0).cpu().numpy()[0].astype(np.float64)
+    for s, ((pp, q), c) in enumerate(zip(pq, (0.5, -0.25))):
+        lam = (G - 1) ** 2 * (4 * np.sin(np.pi * pp / (2 * G)) ** 2 + 4 * np.sin(np.pi * q / (2 * G)) ** 2)
+        fac = (1.0 / (1.0 + dt * D[s] * lam)) ** steps
+        want = c + fac * modes[s]
+        assert np.abs(got[s] - want).max() <= 2e-6 * (1 + abs(c)), (s, np.abs(got[s] - want).max())
+        assert abs(got[s].mean() - c) <= 2e-6
+
+
+@pytest.mark.parametrize("model,par,noise", [
+    (W.FHN, (2.8e-4, 0.05, 10.0, 0.95), (0.0, 0.0)),
+    (W.GM, (2.5e-4, 0.01, 1.0, 0.52), (0.0, 0.0)),
+    (W.BZ, W.BZ_THETA0, (0.0, 0.0)),
+])
+def test_equilibrium_is_kept_bit_exact(p, model, par, noise):
+    """The homogeneous equilibrium (zero deviation) stays exactly in place."""
+    w0, got, _ = run_gpu(p, model, 64, 1, par, 2 ** -5, 40, noise, 3)
+    np.testing.assert_array_equal(got, w0)
+
+
+def test_imex_refuses_unsupported_groups(p):
+    sim = p.Simulation([p.Group(W.FHN, 128, 1, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -6, 1, (-0.05, 0.05), 1)])
+    with pytest.raises(p.RdError) as e:
+        sim.integrate_imex()
+    assert e.value.status == 6   # RD_ERR_UNSUPPORTED
+
+
+def test_imex_takes_steps_the_explicit_stepper_cannot(p):
+    """At dt = 16 x the explicit diffusive limit the explicit Euler stepper
+    blows up while the semi-implicit one stays bounded and matches the
+    oracle."""
+    par = (2.9e-4, 0.048, 9.7, 0.93)
+    dt = 16 * (1.0 / 63) ** 2 / (4 * par[1])
+    w0, got, _ = run_gpu(p, W.FHN, 64, 1, par, dt, 60, (-0.05, 0.05), 9)
+    assert np.isfinite(got).all() and np.abs(got).max() < 2.0
+    want = OI.imex_run(W.FHN, par, dt, 60, w0)
+    assert rel_err(got, want) <= FIELD_TOL
+    ex = oracle.step(W.FHN, par, dt, 60, w0.astype(np.float64))
+    assert not (np.isfinite(ex).all() and np.abs(ex).max() < 2.0)
