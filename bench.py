@@ -92,6 +92,10 @@ def parse():
                     help="add the adaptive stabilised RK2 (App. B.2) against the Euler stepper on c2")
     ap.add_argument("--rkc-only", action="store_true",
                     help="run only the adaptive stabilised RK2 comparison and print it")
+    ap.add_argument("--imex", action="store_true",
+                    help="add the semi-implicit Euler stepper against the Euler stepper on c2")
+    ap.add_argument("--imex-only", action="store_true",
+                    help="run only the semi-implicit Euler comparison and print it")
     ap.add_argument("--gram-large-only", action="store_true",
                     help="time only the tensor-core Gram and correlation integral on 2 x 1024 patterns of "
                          "d = 32768 (for profiling); prints that object alone")
@@ -425,6 +429,8 @@ def run_ours(args, rank, world, local_rank):
         out["stream"] = stream_bench(p, torch, dev, stream, pk, src)
     if args.rkc and rank == 0:
         out["rkc"] = rkc_bench(p, torch, dev, stream, pk, src)
+    if args.imex and rank == 0:
+        out["imex"] = imex_bench(p, torch, dev, stream, pk, src)
     return out
 
 
@@ -610,6 +616,67 @@ def rkc_bench(p, torch, dev, stream, pk, src, tols=(1e-5, 1e-6, 1e-7)):
             "peak_note": "alu peak = 148 SM x 128 FP32 lanes x max SM clock (%s peaks file); "
                          "%d FP32 instructions per cell per RHS stage" % (src, RKC_FP32_INST_PER_CELL_STAGE[gd["model"]]),
             "tolerances": rows}
+
+
+def imex_bench(p, torch, dev, stream, pk, src, dts=(2 ** -6, 2 ** -5, 2 ** -4)):
+    """Semi-implicit Euler (diffusion implicit through the cosine basis,
+    reaction explicit) against the explicit Euler stepper on the FHN 64x64
+    workload (2 x 64 realisations) to the same horizon T = 10^4 x 2^-10:
+    time on the GPU, FP32 FMA rate of the products against the FP32 peak,
+    and the accuracy of two realisations against an accurate oracle
+    reference (adaptive RK2, tolerance 1e-9)."""
+    import oracle
+    cfg = W.config("c2")
+    gd = cfg["groups"][0]
+    G, n = gd["G"], gd["n_real"]
+    T = gd["dt"] * gd["n_steps"]
+    sim = p.Simulation([p.Group.from_dict(gd)], device=dev)
+    w0 = sim.group_fields(0)[:2].cpu().numpy()
+    ref, _, failed = oracle.rkc_adaptive(gd["model"], gd["params"], T, 1e-3, 1e-9, 1e-9, w0)
+    assert failed == 0
+
+    def rel(a):
+        a = np.asarray(a, np.float64)
+        num = np.abs(a - ref).reshape(2, 2, -1).max(-1)
+        return float((num / np.abs(ref).reshape(2, 2, -1).max(-1)).max())
+
+    def timed(s_, fn, reps=3):
+        ts = []
+        for _ in range(reps + 1):
+            s_.reinit()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return min(ts[1:]), r
+
+    t_eul, _ = timed(sim, lambda: sim.integrate(residual=False))
+    assert sim.sync_status() == 0
+    err_eul = rel(sim.group_fields(0)[:2].cpu().numpy())
+    fma_peak = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12   # T FMA/s
+    rows = []
+    for dt in dts:
+        steps = int(round(T / dt))
+        gi = dict(gd, dt=dt, n_steps=steps)
+        s2 = p.Simulation([p.Group.from_dict(gi)], device=dev)
+        t, res = timed(s2, lambda: s2.integrate_imex(residual=True))
+        assert s2.sync_status() == 0
+        err = rel(s2.group_fields(0)[:2].cpu().numpy())
+        fma = 8.0 * G ** 3 * n * steps   # four G^3 products per species and step
+        rows.append({"dt": dt, "steps": steps, "ms": t * 1e3, "us_per_step": t * 1e6 / steps,
+                     "cell_updates_per_s": n * G * G * steps / t,
+                     "product_tfma_per_s": fma / t / 1e12, "fma_frac": fma / t / 1e12 / fma_peak,
+                     "rel_err_sample": err, "speedup_vs_euler": t_eul / t,
+                     "residual_max": float(res[:, 0].max())})
+    return {"workload": "FHN 64x64, 2 x 64 realisations, 0 -> T = 10^4 x 2^-10 (the c2 horizon)",
+            "variant": p.imex_get_variant(G),
+            "euler": {"ms": t_eul * 1e3, "steps": gd["n_steps"], "dt": gd["dt"], "rel_err_sample": err_eul},
+            "reference": "oracle adaptive RK2, tolerance 1e-9, realisations 0 and 1",
+            "peak_note": "FMA peak = 148 SM x 128 FP32 lanes x max SM clock (%s peaks file); the "
+                         "products take 128 of the 148 SMs (one CTA per realisation)" % src,
+            "rows": rows}
 
 
 def rkc_c3(p, torch, dev, stream, tols=(1e-5, 1e-6)):
@@ -930,6 +997,16 @@ def main():
         torch.cuda.set_device(dev)
         pk, src = peaks()
         print(json.dumps(rkc_bench(p, torch, dev, torch.cuda.current_stream(dev), pk, src)))
+        return
+    if args.imex_only:
+        import torch
+        import paper_2203_14742_b300 as p
+        from paper_2203_14742_b300 import build as B
+        B.build()
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        pk, src = peaks()
+        print(json.dumps(imex_bench(p, torch, dev, torch.cuda.current_stream(dev), pk, src)))
         return
     if args.gram_large_only:
         import torch

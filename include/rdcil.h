@@ -283,6 +283,18 @@ rd_status rd_integrate_rkc(rd_handle *h, float *d_fields, const rd_rkc_opts *opt
  * transform tables are formed in FP64 and rounded once. */
 rd_status rd_integrate_imex(rd_handle *h, float *d_fields, double *d_residual, void *stream);
 
+/* Output tiles of the rd_integrate_imex products (outputs per thread,
+ * TM x TN): 0 = 4x4 (G = 64: 512 threads; default at G = 32), 1 = 8x4
+ * (default at G = 64), 2 = 4x8 (256), 3 = 8x8 (128); G = 32 has a quarter
+ * of the threads.  Every tile runs the same
+ * FMA chains, so the fields are bit-identical; the choice (per G,
+ * process-wide) is a speed knob.  rd_imex_set_variant returns
+ * RD_ERR_INVALID_ARG for another G or an unknown variant;
+ * rd_imex_get_variant returns -1 for another G. */
+int32_t rd_imex_n_variants(void);
+rd_status rd_imex_set_variant(int32_t G, int32_t variant);
+int32_t rd_imex_get_variant(int32_t G);
+
 /* Tile shapes of the rd_integrate_rkc kernel (nodes per thread, TY x TX):
  * G = 32: 0 = 2x1 (512 threads, default), 1 = 4x1 (256), 2 = 2x2 (256);
  * G = 64: 0 = 4x2 (512 threads), 1 = 4x4 (256, default), 2 = 2x4 (512).

@@ -53,6 +53,9 @@ _SIGS = {
     "rd_integrate_f64": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "rd_integrate_rkc": (_i32, [_vp, _vp, C.POINTER(RdRkcOpts), _vp, _vp, _vp]),
     "rd_integrate_imex": (_i32, [_vp, _vp, _vp, _vp]),
+    "rd_imex_n_variants": (_i32, []),
+    "rd_imex_set_variant": (_i32, [_i32, _i32]),
+    "rd_imex_get_variant": (_i32, [_i32]),
     "rd_rkc_n_variants": (_i32, []),
     "rd_rkc_set_variant": (_i32, [_i32, _i32]),
     "rd_rkc_get_variant": (_i32, [_i32]),
@@ -329,6 +332,16 @@ def rkc_set_variant(G, variant):
 
 def rkc_get_variant(G):
     return int(lib().rd_rkc_get_variant(int(G)))
+
+
+def imex_set_variant(G, variant):
+    """Output tile of the semi-implicit stepper's products for grid side G
+    (32 or 64): 0 = 4x4, 1 = 8x4, 2 = 4x8, 3 = 8x8."""
+    _check("rd_imex_set_variant", lib().rd_imex_set_variant(int(G), int(variant)))
+
+
+def imex_get_variant(G):
+    return int(lib().rd_imex_get_variant(int(G)))
 
 
 def variant_shape(G, variant):

@@ -227,6 +227,12 @@ extern "C" rd_status rd_integrate_imex(rd_handle *hh, float *d_fields, double *d
     return RD_OK;
 }
 
+extern "C" int32_t rd_imex_n_variants(void) { return imex_n_variants(); }
+extern "C" rd_status rd_imex_set_variant(int32_t G, int32_t variant) {
+    return imex_set_variant(G, variant) ? RD_OK : RD_ERR_INVALID_ARG;
+}
+extern "C" int32_t rd_imex_get_variant(int32_t G) { return imex_get_variant(G); }
+
 extern "C" int32_t rd_rkc_n_variants(void) { return rkc_n_variants(); }
 extern "C" rd_status rd_rkc_set_variant(int32_t G, int32_t variant) {
     return rkc_set_variant(G, variant) ? RD_OK : RD_ERR_INVALID_ARG;

@@ -107,6 +107,9 @@ int rkc_get_variant(int G);
 rd_status launch_rkc_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats, double *residual,
                            uint32_t *status, cudaStream_t s);
 bool imex_supported(const GroupDev &g);
+int imex_n_variants();
+bool imex_set_variant(int G, int v);
+int imex_get_variant(int G);
 rd_status launch_imex_group(const GroupDev &g, float *fields, double *residual, uint32_t *status, cudaStream_t s);
 
 }  // namespace rdcil

@@ -140,47 +140,68 @@ __device__ __forceinline__ void incr4(const float *__restrict__ Wu, const float 
 }
 
 // out[r][c] = sum_k At[k][r] B[k][c] over a G x G product in shared memory
-// (leading dimension G + 4).  The calling thread owns rows 4ty..4ty+3 and
-// columns 4tx..4tx+3.  TRANS stores out[c][r] instead; SCALE multiplies by
-// Sc[r][c] on the way out; ADD adds the result to out.
-template <int G, bool TRANS, bool SCALE, bool ADD = false>
+// (leading dimension G + 4).  The calling thread owns a TM x TN tile: rows
+// 4ty + (i mod 4) + (i div 4) G/2 and columns 4tx + (j mod 4) + (j div 4) G/2,
+// so each of its 128-bit loads, with its warp's neighbours, covers
+// consecutive banks.  Per k: TM/4 broadcast float4 of the left operand
+// (k-major) and TN/4 float4 of the right one for TM TN FMAs.  TRANS stores
+// out[c][r] instead; SCALE multiplies by Sc[r][c] on the way out; ADD adds
+// the result to out.
+template <int G, int TM, int TN, bool TRANS, bool SCALE, bool ADD = false>
 __device__ __forceinline__ void imex_mm(const float *__restrict__ At, const float *__restrict__ B,
                                         float *__restrict__ out, const float *__restrict__ Sc, int ty, int tx) {
-    constexpr int LD = G + 4;
-    float acc[4][4];
+    constexpr int LD = G + 4, H = G / 2;
+    float acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
     const float *pa = At + 4 * ty, *pb = B + 4 * tx;
-#pragma unroll 8
+#pragma unroll 4
     for (int k = 0; k < G; ++k) {
-        const float4 a = *reinterpret_cast<const float4 *>(pa + k * LD);
-        const float4 b = *reinterpret_cast<const float4 *>(pb + k * LD);
-        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+        float av[TM], bv[TN];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int h = 0; h < TM / 4; ++h) {
+            const float4 a = *reinterpret_cast<const float4 *>(pa + k * LD + h * H);
+            av[4 * h] = a.x; av[4 * h + 1] = a.y; av[4 * h + 2] = a.z; av[4 * h + 3] = a.w;
+        }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int h = 0; h < TN / 4; ++h) {
+            const float4 b = *reinterpret_cast<const float4 *>(pb + k * LD + h * H);
+            bv[4 * h] = b.x; bv[4 * h + 1] = b.y; bv[4 * h + 2] = b.z; bv[4 * h + 3] = b.w;
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     if (TRANS) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            *reinterpret_cast<float4 *>(out + (4 * tx + j) * LD + 4 * ty) =
-                make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        for (int j = 0; j < TN; ++j) {
+            const int c = 4 * tx + (j & 3) + (j >> 2) * H;
+#pragma unroll
+            for (int h = 0; h < TM / 4; ++h)
+                *reinterpret_cast<float4 *>(out + c * LD + 4 * ty + h * H) =
+                    make_float4(acc[4 * h][j], acc[4 * h + 1][j], acc[4 * h + 2][j], acc[4 * h + 3][j]);
+        }
     } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float4 o = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-            if (SCALE) {
-                const float4 s = *reinterpret_cast<const float4 *>(Sc + (4 * ty + i) * LD + 4 * tx);
-                o.x *= s.x; o.y *= s.y; o.z *= s.z; o.w *= s.w;
+        for (int i = 0; i < TM; ++i) {
+            const int r = 4 * ty + (i & 3) + (i >> 2) * H;
+#pragma unroll
+            for (int h = 0; h < TN / 4; ++h) {
+                const int o = r * LD + 4 * tx + h * H;
+                float4 v = make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+                if (SCALE) {
+                    const float4 sc = *reinterpret_cast<const float4 *>(Sc + o);
+                    v.x *= sc.x; v.y *= sc.y; v.z *= sc.z; v.w *= sc.w;
+                }
+                if (ADD) {
+                    const float4 w = *reinterpret_cast<const float4 *>(out + o);
+                    v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+                }
+                *reinterpret_cast<float4 *>(out + o) = v;
             }
-            if (ADD) {
-                const float4 w = *reinterpret_cast<const float4 *>(out + (4 * ty + i) * LD + 4 * tx);
-                o.x += w.x; o.y += w.y; o.z += w.z; o.w += w.w;
-            }
-            *reinterpret_cast<float4 *>(out + (4 * ty + i) * LD + 4 * tx) = o;
         }
     }
 }
@@ -188,12 +209,12 @@ __device__ __forceinline__ void imex_mm(const float *__restrict__ At, const floa
 template <int G>
 constexpr size_t imex_smem() { return sizeof(float) * 10 * (size_t)G * (G + 4); }
 
-template <int MODEL, int G>
-__global__ void __launch_bounds__(2 * (G / 4) * (G / 4))
+template <int MODEL, int G, int TM, int TN>
+__global__ void __launch_bounds__(2 * (G / TM) * (G / TN))
 rd_imex_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, float a_u, float a_v,
                const float *__restrict__ tab, int64_t steps, double p0, double p1, double p2, double p3,
                double *__restrict__ residual, uint32_t *__restrict__ status) {
-    constexpr int LD = G + 4, Q = G / 4, NS = Q * Q, NT = 2 * NS, BUF = G * LD;
+    constexpr int LD = G + 4, Q = G / 4, QX = G / TN, NS = (G / TM) * QX, NT = 2 * NS, BUF = G * LD;
     extern __shared__ __align__(16) float sm[];
     float *sC = sm, *sCT = sC + BUF, *sS = sCT + BUF, *sW = sS + 2 * BUF, *sX = sW + 2 * BUF, *sT = sX + 2 * BUF;
     const int tid = threadIdx.x, r = blockIdx.x;
@@ -222,7 +243,7 @@ rd_imex_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, float
         *reinterpret_cast<float4 *>(sS + BUF + y * LD + x) = make_float4(sv[0], sv[1], sv[2], sv[3]);
     }
     __syncthreads();
-    const int sp = tid / NS, l = tid - sp * NS, ty = l / Q, tx = l - ty * Q;
+    const int sp = tid / NS, l = tid - sp * NS, ty = l / QX, tx = l - ty * QX;
     float *F = sW + sp * BUF, *X = sX + sp * BUF, *T = sT + sp * BUF;
     const float *S = sS + sp * BUF;
     for (int64_t n = 0; n < steps; ++n) {
@@ -231,13 +252,13 @@ rd_imex_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, float
             incr4<MODEL, G>(sW, sW + BUF, sX, sX + BUF, y, x, cf);   // dt F(w^n)
         }
         __syncthreads();
-        imex_mm<G, true, false>(sCT, X, T, nullptr, ty, tx);        // (C dtF)^T
+        imex_mm<G, TM, TN, true, false>(sCT, X, T, nullptr, ty, tx);        // (C dtF)^T
         __syncthreads();
-        imex_mm<G, false, true>(T, sCT, X, S, ty, tx);              // (C dtF C^T) o S
+        imex_mm<G, TM, TN, false, true>(T, sCT, X, S, ty, tx);              // (C dtF C^T) o S
         __syncthreads();
-        imex_mm<G, true, false>(sC, X, T, nullptr, ty, tx);         // (C^T .)^T
+        imex_mm<G, TM, TN, true, false>(sC, X, T, nullptr, ty, tx);         // (C^T .)^T
         __syncthreads();
-        imex_mm<G, false, false, true>(T, sC, F, nullptr, ty, tx);  // w += C^T . C
+        imex_mm<G, TM, TN, false, false, true>(T, sC, F, nullptr, ty, tx);  // w += C^T . C
         __syncthreads();
     }
     for (int q = tid; q < G * Q; q += NT) {
@@ -274,19 +295,46 @@ static rd_status imex_table(int G, cudaStream_t s, const float **tab) {
     return g_imex_status[gi];
 }
 
-template <int MODEL, int G>
-static rd_status launch_imex_mg(const GroupDev &g, float *fields, const float *tab, double *residual,
-                                uint32_t *status, cudaStream_t s) {
+// Output tile per thread (TM x TN): 0 = 4 x 4, 1 = 8 x 4, 2 = 4 x 8, 3 = 8 x 8.
+// Every tile runs the same FMA chains (k ascending per output), so all give
+// bit-identical fields; the choice (per G) is a speed knob.
+// defaults from FHN x 128 realisations, dt = 2^-6, 300 steps on B300 (us
+// per step for 4x4 / 8x4 / 4x8 / 8x8): G = 64: 16.8 / 15.0 / 15.0 / 16.8;
+// G = 32: 4.67 / 6.04 / 6.13 / 9.32
+static int g_imex_var[2] = {0, 1};   // [G == 64]
+
+int imex_n_variants() { return 4; }
+bool imex_set_variant(int G, int v) {
+    if ((G != 32 && G != 64) || v < 0 || v > 3) return false;
+    g_imex_var[G == 64] = v;
+    return true;
+}
+int imex_get_variant(int G) { return (G == 32 || G == 64) ? g_imex_var[G == 64] : -1; }
+
+template <int MODEL, int G, int TM, int TN>
+static rd_status launch_imex_mgt(const GroupDev &g, float *fields, const float *tab, double *residual,
+                                 uint32_t *status, cudaStream_t s) {
     constexpr size_t smem = imex_smem<G>();
-    auto kern = rd_imex_kernel<MODEL, G>;
+    auto kern = rd_imex_kernel<MODEL, G, TM, TN>;
     RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const double h2 = (double)(g.G - 1) * (double)(g.G - 1);
     const float a_u = (float)(g.dt * g.p[0] * h2), a_v = (float)(g.dt * g.p[1] * h2);
-    kern<<<g.n_real, 2 * (G / 4) * (G / 4), smem, s>>>(fields, g.field_offset, make_coef(g), a_u, a_v, tab, g.n_steps,
-                                                      g.p[0], g.p[1], g.p[2], g.p[3],
-                                                      residual ? residual + 2 * g.real_base : nullptr, status);
+    kern<<<g.n_real, 2 * (G / TM) * (G / TN), smem, s>>>(fields, g.field_offset, make_coef(g), a_u, a_v, tab,
+                                                          g.n_steps, g.p[0], g.p[1], g.p[2], g.p[3],
+                                                          residual ? residual + 2 * g.real_base : nullptr, status);
     note_launch();
     return cuda_status(cudaGetLastError());
+}
+
+template <int MODEL, int G>
+static rd_status launch_imex_mg(const GroupDev &g, float *fields, const float *tab, double *residual,
+                                uint32_t *status, cudaStream_t s) {
+    switch (g_imex_var[G == 64]) {
+        case 1: return launch_imex_mgt<MODEL, G, 8, 4>(g, fields, tab, residual, status, s);
+        case 2: return launch_imex_mgt<MODEL, G, 4, 8>(g, fields, tab, residual, status, s);
+        case 3: return launch_imex_mgt<MODEL, G, 8, 8>(g, fields, tab, residual, status, s);
+        default: return launch_imex_mgt<MODEL, G, 4, 4>(g, fields, tab, residual, status, s);
+    }
 }
 
 template <int G>

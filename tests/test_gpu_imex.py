@@ -138,3 +138,21 @@ def test_imex_takes_steps_the_explicit_stepper_cannot(p):
     assert rel_err(got, want) <= FIELD_TOL
     ex = oracle.step(W.FHN, par, dt, 60, w0.astype(np.float64))
     assert not (np.isfinite(ex).all() and np.abs(ex).max() < 2.0)
+
+
+@pytest.mark.parametrize("G", [32, 64])
+def test_imex_tiles_bit_identical(p, G):
+    """The product tile only changes which thread forms an output: every
+    variant gives the same bits."""
+    par = (2.9e-4, 0.048, 9.7, 0.93)
+    keep = p.imex_get_variant(G)
+    outs = []
+    try:
+        for v in range(p.lib().rd_imex_n_variants()):
+            p.imex_set_variant(G, v)
+            _, got, _ = run_gpu(p, W.FHN, G, 2, par, 2 ** -6, 30, (-0.05, 0.05), 21)
+            outs.append(got)
+    finally:
+        p.imex_set_variant(G, keep)
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
