@@ -284,11 +284,14 @@ rd_status rd_integrate_rkc(rd_handle *h, float *d_fields, const rd_rkc_opts *opt
 rd_status rd_integrate_imex(rd_handle *h, float *d_fields, double *d_residual, void *stream);
 
 /* Output tiles of the rd_integrate_imex products (outputs per thread,
- * TM x TN): 0 = 4x4 (G = 64: 512 threads; default at G = 32), 1 = 8x4
- * (default at G = 64), 2 = 4x8 (256), 3 = 8x8 (128); G = 32 has a quarter
- * of the threads.  Every tile runs the same
+ * TM x TN): 0 = 4x4 (G = 64: 512 threads), 1 = 8x4, 2 = 4x8 (256),
+ * 3 = 8x8 (128); G = 32 has a quarter of the threads.  Every tile runs the same
  * FMA chains, so the fields are bit-identical; the choice (per G,
- * process-wide) is a speed knob.  rd_imex_set_variant returns
+ * process-wide) is a speed knob.  4 = the even/odd split: with the spectrum
+ * ordered (even, odd) each product is two half-length sums over
+ * Y[k] +- Y[G-1-k] (the cosine basis's symmetry), half the FMAs, its own
+ * rounding (same tolerance, not bit-identical to 0-3); the default at both
+ * G (256 threads at G = 64).  rd_imex_set_variant returns
  * RD_ERR_INVALID_ARG for another G or an unknown variant;
  * rd_imex_get_variant returns -1 for another G. */
 int32_t rd_imex_n_variants(void);

@@ -335,8 +335,9 @@ def rkc_get_variant(G):
 
 
 def imex_set_variant(G, variant):
-    """Output tile of the semi-implicit stepper's products for grid side G
-    (32 or 64): 0 = 4x4, 1 = 8x4, 2 = 4x8, 3 = 8x8."""
+    """Product variant of the semi-implicit stepper for grid side G (32 or
+    64): output tiles 0 = 4x4, 1 = 8x4, 2 = 4x8, 3 = 8x8; 4 = the even/odd
+    split (half the FMAs; the default)."""
     _check("rd_imex_set_variant", lib().rd_imex_set_variant(int(G), int(variant)))
 
 

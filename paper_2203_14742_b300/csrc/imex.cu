@@ -295,21 +295,327 @@ static rd_status imex_table(int G, cudaStream_t s, const float **tab) {
     return g_imex_status[gi];
 }
 
+// ---------------------------------------------------------------------------
+// Even/odd split.  C[p][G-1-x] = (-1)^p C[p][x], so with the spectrum held in
+// the order m = (even p ascending, odd p ascending), C'[m] = C[p(m)], every
+// product is two half-length sums:
+//   forward (C' Y)[m] = sum_{k<G/2} C'[m][k] (Y[k] +- Y[G-1-k])   (+ for m < G/2)
+//   inverse (C'^T Z)[y], [G-1-y] = A_e +- A_o,  A_e = sum_{k<G/2} C'[k][y] Z[k],
+//                                               A_o = sum_{k<G/2} C'[k+G/2][y] Z[k+G/2]
+// (y < G/2), half the FMAs of the full products; the divisors are applied
+// in the permuted order.  Tables: Ch[k][m] = C'[m][k] (k < G/2, ld G + 4)
+// and Cl[m][y] = C'[m][y] (y < G/2, ld G/2 + 4).  Every product gives each
+// thread 32 outputs from 16 accumulator pairs of float4 loads per k.
+// ---------------------------------------------------------------------------
+__global__ void imex_eo_table_kernel(int G, float *__restrict__ tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int H = G / 2;
+    if (i < G * H) {
+        const int m = i / H, y = i - m * H;
+        const int p = m < H ? 2 * m : 2 * (m - H) + 1;
+        const double a = p == 0 ? sqrt(1.0 / (double)G) : sqrt(2.0 / (double)G);
+        const float c = (float)(a * cospi((double)(p * (2 * y + 1)) / (double)(2 * G)));
+        tab[y * G + m] = c;           // Ch: [k = y < H][m]
+        tab[H * G + m * H + y] = c;   // Cl: [m][y < H]
+    }
+    if (i < G) {
+        const int p = i < H ? 2 * i : 2 * (i - H) + 1;
+        const double s = sinpi((double)p / (double)(2 * G));
+        tab[2 * H * G + i] = (float)(4.0 * s * s);   // mu in the permuted order
+    }
+}
+
+__device__ __forceinline__ void f4a(float (&d)[4], float4 v) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
+
+// forward along the rows' index: T[c][m] = sum_k Ch[k][m] (Y[k][c] +- Y[G-1-k][c])
+// (stored transposed); thread: m = 4ty + i (+ G/2), c = 4tx + j
+template <int G>
+__device__ __forceinline__ void eo_fwd_rows(const float *__restrict__ Ch, const float *__restrict__ Y,
+                                           float *__restrict__ T, int l) {
+    constexpr int LD = G + 4, H = G / 2;
+    const int tx = l % (G / 4), ty = l / (G / 4);
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < H; ++k) {
+        float ae[4], ao[4], y1[4], y2[4];
+        f4a(ae, *reinterpret_cast<const float4 *>(Ch + k * LD + 4 * ty));
+        f4a(ao, *reinterpret_cast<const float4 *>(Ch + k * LD + 4 * ty + H));
+        f4a(y1, *reinterpret_cast<const float4 *>(Y + k * LD + 4 * tx));
+        f4a(y2, *reinterpret_cast<const float4 *>(Y + (G - 1 - k) * LD + 4 * tx));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float e = y1[j] + y2[j], o = y1[j] - y2[j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[i][j] = fmaf(ae[i], e, acc[i][j]);
+                acc[4 + i][j] = fmaf(ao[i], o, acc[4 + i][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float *row = T + (4 * tx + j) * LD + 4 * ty;
+        *reinterpret_cast<float4 *>(row) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        *reinterpret_cast<float4 *>(row + H) = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+    }
+}
+
+// forward along the columns' index, divisors applied:
+// Z[r][m] = S[r][m] sum_k (T[k][r] +- T[G-1-k][r]) Ch[k][m]; thread: r = 4ty + i, m = 4tx + j (+ G/2)
+template <int G>
+__device__ __forceinline__ void eo_fwd_cols(const float *__restrict__ T, const float *__restrict__ Ch,
+                                           float *__restrict__ Z, const float *__restrict__ S, int l) {
+    constexpr int LD = G + 4, H = G / 2;
+    const int tx = l % (G / 8), ty = l / (G / 8);
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < H; ++k) {
+        float t1[4], t2[4], be[4], bo[4];
+        f4a(t1, *reinterpret_cast<const float4 *>(T + k * LD + 4 * ty));
+        f4a(t2, *reinterpret_cast<const float4 *>(T + (G - 1 - k) * LD + 4 * ty));
+        f4a(be, *reinterpret_cast<const float4 *>(Ch + k * LD + 4 * tx));
+        f4a(bo, *reinterpret_cast<const float4 *>(Ch + k * LD + 4 * tx + H));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float e = t1[i] + t2[i], o = t1[i] - t2[i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                acc[i][j] = fmaf(e, be[j], acc[i][j]);
+                acc[i][4 + j] = fmaf(o, bo[j], acc[i][4 + j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int o0 = (4 * ty + i) * LD + 4 * tx;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 sc = *reinterpret_cast<const float4 *>(S + o0 + h * H);
+            *reinterpret_cast<float4 *>(Z + o0 + h * H) =
+                make_float4(acc[i][4 * h] * sc.x, acc[i][4 * h + 1] * sc.y, acc[i][4 * h + 2] * sc.z,
+                            acc[i][4 * h + 3] * sc.w);
+        }
+    }
+}
+
+// inverse along the rows' index: T[c][y], T[c][G-1-y] = A_e +- A_o with
+// A_e = sum_k Cl[k][y] Z[k][c], A_o = sum_k Cl[k+G/2][y] Z[k+G/2][c]
+// (stored transposed); thread: y = 4ty + i (< G/2), c = 4tx + j
+template <int G>
+__device__ __forceinline__ void eo_inv_rows(const float *__restrict__ Cl, const float *__restrict__ Z,
+                                           float *__restrict__ T, int l) {
+    constexpr int LD = G + 4, H = G / 2, LDH = H + 4;
+    const int tx = l % (G / 4), ty = l / (G / 4);
+    float E[4][4], O[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) E[i][j] = O[i][j] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < H; ++k) {
+        float ae[4], ao[4], z1[4], z2[4];
+        f4a(ae, *reinterpret_cast<const float4 *>(Cl + k * LDH + 4 * ty));
+        f4a(ao, *reinterpret_cast<const float4 *>(Cl + (k + H) * LDH + 4 * ty));
+        f4a(z1, *reinterpret_cast<const float4 *>(Z + k * LD + 4 * tx));
+        f4a(z2, *reinterpret_cast<const float4 *>(Z + (k + H) * LD + 4 * tx));
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                E[i][j] = fmaf(ae[i], z1[j], E[i][j]);
+                O[i][j] = fmaf(ao[i], z2[j], O[i][j]);
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float *row = T + (4 * tx + j) * LD;
+        *reinterpret_cast<float4 *>(row + 4 * ty) =
+            make_float4(E[0][j] + O[0][j], E[1][j] + O[1][j], E[2][j] + O[2][j], E[3][j] + O[3][j]);
+        *reinterpret_cast<float4 *>(row + G - 4 - 4 * ty) =
+            make_float4(E[3][j] - O[3][j], E[2][j] - O[2][j], E[1][j] - O[1][j], E[0][j] - O[0][j]);
+    }
+}
+
+// inverse along the columns' index, added to the state: W[r][x], W[r][G-1-x]
+// += B_e +- B_o, B_e = sum_k T[k][r] Cl[k][x], B_o = sum_k T[k+G/2][r] Cl[k+G/2][x];
+// thread: r = 4ty + i, x = 4tx + j (< G/2)
+template <int G>
+__device__ __forceinline__ void eo_inv_cols(const float *__restrict__ T, const float *__restrict__ Cl,
+                                           float *__restrict__ W, int l) {
+    constexpr int LD = G + 4, H = G / 2, LDH = H + 4;
+    const int tx = l % (H / 4), ty = l / (H / 4);
+    float E[4][4], O[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) E[i][j] = O[i][j] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < H; ++k) {
+        float t1[4], t2[4], b1[4], b2[4];
+        f4a(t1, *reinterpret_cast<const float4 *>(T + k * LD + 4 * ty));
+        f4a(t2, *reinterpret_cast<const float4 *>(T + (k + H) * LD + 4 * ty));
+        f4a(b1, *reinterpret_cast<const float4 *>(Cl + k * LDH + 4 * tx));
+        f4a(b2, *reinterpret_cast<const float4 *>(Cl + (k + H) * LDH + 4 * tx));
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                E[i][j] = fmaf(t1[i], b1[j], E[i][j]);
+                O[i][j] = fmaf(t2[i], b2[j], O[i][j]);
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float *row = W + (4 * ty + i) * LD;
+        float4 a = *reinterpret_cast<const float4 *>(row + 4 * tx);
+        a.x += E[i][0] + O[i][0]; a.y += E[i][1] + O[i][1]; a.z += E[i][2] + O[i][2]; a.w += E[i][3] + O[i][3];
+        *reinterpret_cast<float4 *>(row + 4 * tx) = a;
+        float4 b = *reinterpret_cast<const float4 *>(row + G - 4 - 4 * tx);
+        b.x += E[i][3] - O[i][3]; b.y += E[i][2] - O[i][2]; b.z += E[i][1] - O[i][1]; b.w += E[i][0] - O[i][0];
+        *reinterpret_cast<float4 *>(row + G - 4 - 4 * tx) = b;
+    }
+}
+
+template <int G>
+constexpr size_t imex_eo_smem() {
+    return sizeof(float) * ((size_t)(G / 2) * (G + 4) + (size_t)G * (G / 2 + 4) + 8 * (size_t)G * (G + 4));
+}
+
+template <int MODEL, int G>
+__global__ void __launch_bounds__(G * G / 16)
+rd_imex_eo_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, float a_u, float a_v,
+                  const float *__restrict__ tab, int64_t steps, double p0, double p1, double p2, double p3,
+                  double *__restrict__ residual, uint32_t *__restrict__ status) {
+    constexpr int LD = G + 4, H = G / 2, LDH = H + 4, Q = G / 4, NS = G * G / 32, NT = 2 * NS, BUF = G * LD;
+    extern __shared__ __align__(16) float sm[];
+    float *sCh = sm, *sCl = sCh + H * LD, *sS = sCl + G * LDH, *sW = sS + 2 * BUF, *sX = sW + 2 * BUF,
+          *sT = sX + 2 * BUF;
+    const int tid = threadIdx.x, r = blockIdx.x;
+    float *base = fields + field_offset + (int64_t)r * 2 * G * G;
+    const float *mu = tab + 2 * H * G;
+    for (int q = tid; q < H * Q; q += NT) {   // Ch: H rows of G
+        const int y = q / Q, x = (q - y * Q) * 4;
+        *reinterpret_cast<float4 *>(sCh + y * LD + x) = *reinterpret_cast<const float4 *>(tab + y * G + x);
+    }
+    for (int q = tid; q < G * (H / 4); q += NT) {   // Cl: G rows of H
+        const int y = q / (H / 4), x = (q - y * (H / 4)) * 4;
+        *reinterpret_cast<float4 *>(sCl + y * LDH + x) = *reinterpret_cast<const float4 *>(tab + H * G + y * H + x);
+    }
+    for (int q = tid; q < G * Q; q += NT) {
+        const int y = q / Q, x = (q - y * Q) * 4;
+        float4 u = *reinterpret_cast<const float4 *>(base + y * G + x);
+        float4 v = *reinterpret_cast<const float4 *>(base + G * G + y * G + x);
+        to_state<MODEL>(u.x, v.x, cf);
+        to_state<MODEL>(u.y, v.y, cf);
+        to_state<MODEL>(u.z, v.z, cf);
+        to_state<MODEL>(u.w, v.w, cf);
+        *reinterpret_cast<float4 *>(sW + y * LD + x) = u;
+        *reinterpret_cast<float4 *>(sW + BUF + y * LD + x) = v;
+        float su[4], sv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float m = mu[y] + mu[x + j];
+            su[j] = 1.f / fmaf(a_u, m, 1.f);
+            sv[j] = 1.f / fmaf(a_v, m, 1.f);
+        }
+        *reinterpret_cast<float4 *>(sS + y * LD + x) = make_float4(su[0], su[1], su[2], su[3]);
+        *reinterpret_cast<float4 *>(sS + BUF + y * LD + x) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+    }
+    __syncthreads();
+    const int sp = tid / NS, l = tid - sp * NS;
+    float *F = sW + sp * BUF, *X = sX + sp * BUF, *T = sT + sp * BUF;
+    const float *S = sS + sp * BUF;
+    for (int64_t n = 0; n < steps; ++n) {
+        for (int q = tid; q < G * Q; q += NT) {
+            const int y = q / Q, x = (q - y * Q) * 4;
+            incr4<MODEL, G>(sW, sW + BUF, sX, sX + BUF, y, x, cf);   // dt F(w^n)
+        }
+        __syncthreads();
+        eo_fwd_rows<G>(sCh, X, T, l);
+        __syncthreads();
+        eo_fwd_cols<G>(T, sCh, X, S, l);
+        __syncthreads();
+        eo_inv_rows<G>(sCl, X, T, l);
+        __syncthreads();
+        eo_inv_cols<G>(T, sCl, F, l);
+        __syncthreads();
+    }
+    for (int q = tid; q < G * Q; q += NT) {
+        const int y = q / Q, x = (q - y * Q) * 4;
+        float4 u = *reinterpret_cast<const float4 *>(sW + y * LD + x);
+        float4 v = *reinterpret_cast<const float4 *>(sW + BUF + y * LD + x);
+        from_state<MODEL>(u.x, v.x, cf);
+        from_state<MODEL>(u.y, v.y, cf);
+        from_state<MODEL>(u.z, v.z, cf);
+        from_state<MODEL>(u.w, v.w, cf);
+        *reinterpret_cast<float4 *>(base + y * G + x) = u;
+        *reinterpret_cast<float4 *>(base + G * G + y * G + x) = v;
+    }
+    residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, sCh);
+}
+
 // Output tile per thread (TM x TN): 0 = 4 x 4, 1 = 8 x 4, 2 = 4 x 8, 3 = 8 x 8.
 // Every tile runs the same FMA chains (k ascending per output), so all give
-// bit-identical fields; the choice (per G) is a speed knob.
+// bit-identical fields; the choice (per G) is a speed knob.  4 = the
+// even/odd split (half the FMAs, its own rounding).
 // defaults from FHN x 128 realisations, dt = 2^-6, 300 steps on B300 (us
-// per step for 4x4 / 8x4 / 4x8 / 8x8): G = 64: 16.8 / 15.0 / 15.0 / 16.8;
-// G = 32: 4.67 / 6.04 / 6.13 / 9.32
-static int g_imex_var[2] = {0, 1};   // [G == 64]
+// per step for 4x4 / 8x4 / 4x8 / 8x8 / even-odd): G = 64: 16.8 / 15.0 /
+// 15.0 / 16.8 / 10.4; G = 32: 4.67 / 6.04 / 6.13 / 9.32 / 4.09
+static int g_imex_var[2] = {4, 4};   // [G == 64]
 
-int imex_n_variants() { return 4; }
+int imex_n_variants() { return 5; }
 bool imex_set_variant(int G, int v) {
-    if ((G != 32 && G != 64) || v < 0 || v > 3) return false;
+    if ((G != 32 && G != 64) || v < 0 || v > 4) return false;
     g_imex_var[G == 64] = v;
     return true;
 }
 int imex_get_variant(int G) { return (G == 32 || G == 64) ? g_imex_var[G == 64] : -1; }
+
+static float *g_imex_eo_tab[2] = {nullptr, nullptr};   // G = 32, 64
+static std::once_flag g_imex_eo_once[2];
+static rd_status g_imex_eo_status[2] = {RD_OK, RD_OK};
+
+static rd_status imex_eo_table(int G, cudaStream_t s, const float **tab) {
+    const int gi = G == 64;
+    std::call_once(g_imex_eo_once[gi], [G, gi, s]() {
+        if (cudaMalloc(&g_imex_eo_tab[gi], sizeof(float) * ((size_t)G * G + G)) != cudaSuccess) {
+            g_imex_eo_status[gi] = RD_ERR_OOM;
+            return;
+        }
+        imex_eo_table_kernel<<<(G * G / 2 + 127) / 128, 128, 0, s>>>(G, g_imex_eo_tab[gi]);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            g_imex_eo_status[gi] = RD_ERR_CUDA;
+    });
+    *tab = g_imex_eo_tab[gi];
+    return g_imex_eo_status[gi];
+}
+
+template <int MODEL, int G>
+static rd_status launch_imex_eo(const GroupDev &g, float *fields, double *residual, uint32_t *status,
+                                cudaStream_t s) {
+    const float *tab = nullptr;
+    rd_status st = imex_eo_table(G, s, &tab);
+    if (st != RD_OK) return st;
+    constexpr size_t smem = imex_eo_smem<G>();
+    auto kern = rd_imex_eo_kernel<MODEL, G>;
+    RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const double h2 = (double)(g.G - 1) * (double)(g.G - 1);
+    const float a_u = (float)(g.dt * g.p[0] * h2), a_v = (float)(g.dt * g.p[1] * h2);
+    kern<<<g.n_real, G * G / 16, smem, s>>>(fields, g.field_offset, make_coef(g), a_u, a_v, tab, g.n_steps,
+                                            g.p[0], g.p[1], g.p[2], g.p[3],
+                                            residual ? residual + 2 * g.real_base : nullptr, status);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
 
 template <int MODEL, int G, int TM, int TN>
 static rd_status launch_imex_mgt(const GroupDev &g, float *fields, const float *tab, double *residual,
@@ -333,6 +639,7 @@ static rd_status launch_imex_mg(const GroupDev &g, float *fields, const float *t
         case 1: return launch_imex_mgt<MODEL, G, 8, 4>(g, fields, tab, residual, status, s);
         case 2: return launch_imex_mgt<MODEL, G, 4, 8>(g, fields, tab, residual, status, s);
         case 3: return launch_imex_mgt<MODEL, G, 8, 8>(g, fields, tab, residual, status, s);
+        case 4: return launch_imex_eo<MODEL, G>(g, fields, residual, status, s);
         default: return launch_imex_mgt<MODEL, G, 4, 4>(g, fields, tab, residual, status, s);
     }
 }

@@ -138,6 +138,6 @@ def test_imex_argument_checks_without_gpu(libpath):
     L = p.lib()
     assert L.rd_integrate_imex(None, ctypes.c_void_p(256), None, None) == 1
     assert L.rd_integrate_imex(ctypes.c_void_p(256), None, None, None) == 1
-    assert L.rd_imex_n_variants() == 4
+    assert L.rd_imex_n_variants() == 5
     assert L.rd_imex_get_variant(128) == -1
-    assert L.rd_imex_set_variant(128, 0) == 1 and L.rd_imex_set_variant(64, 4) == 1
+    assert L.rd_imex_set_variant(128, 0) == 1 and L.rd_imex_set_variant(64, 5) == 1

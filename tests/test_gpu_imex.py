@@ -148,7 +148,7 @@ def test_imex_tiles_bit_identical(p, G):
     keep = p.imex_get_variant(G)
     outs = []
     try:
-        for v in range(p.lib().rd_imex_n_variants()):
+        for v in range(4):
             p.imex_set_variant(G, v)
             _, got, _ = run_gpu(p, W.FHN, G, 2, par, 2 ** -6, 30, (-0.05, 0.05), 21)
             outs.append(got)
@@ -156,3 +156,31 @@ def test_imex_tiles_bit_identical(p, G):
         p.imex_set_variant(G, keep)
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[4]])
+def test_imex_even_odd_split_within_tolerance(p, case):
+    """Variant 4 forms the same solve from half-length sums (the cosine
+    basis's even/odd symmetry): its own rounding, the same tolerance."""
+    model, G, n, par, dt, steps, noise = case
+    keep = p.imex_get_variant(G)
+    try:
+        p.imex_set_variant(G, 4)
+        w0, got, res = run_gpu(p, model, G, n, par, dt, steps, noise, 0x91 + G, residual=True)
+    finally:
+        p.imex_set_variant(G, keep)
+    want = OI.imex_run(model, par, dt, steps, w0)
+    assert rel_err(got, want) <= FIELD_TOL
+    ref = oracle.residual(model, par, got.astype(np.float64))
+    np.testing.assert_allclose(res.cpu().numpy(), ref, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("G", [32, 64])
+def test_imex_even_odd_mode_decay(p, G):
+    keep = p.imex_get_variant(G)
+    try:
+        p.imex_set_variant(G, 4)
+        test_pure_diffusion_mode_decay_and_mass(p, G)
+        test_equilibrium_is_kept_bit_exact(p, W.GM, (2.5e-4, 0.01, 1.0, 0.52), (0.0, 0.0))
+    finally:
+        p.imex_set_variant(G, keep)
