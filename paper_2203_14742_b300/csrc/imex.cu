@@ -327,6 +327,13 @@ __global__ void imex_eo_table_kernel(int G, float *__restrict__ tab) {
 
 __device__ __forceinline__ void f4a(float (&d)[4], float4 v) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
 
+// The transposed buffer T holds float4 slot s of row c at slot
+// s ^ ((c / 4) mod 8): the forward and inverse row products write rows
+// 4tx + j of a warp's lanes, which with ld = G + 4 would fall on two bank
+// quads; the swizzle spreads eight lanes over eight.  Readers apply the same
+// map.
+__device__ __forceinline__ int swz(int c, int s) { return s ^ ((c >> 2) & 7); }
+
 // forward along the rows' index: T[c][m] = sum_k Ch[k][m] (Y[k][c] +- Y[G-1-k][c])
 // (stored transposed); thread: m = 4ty + i (+ G/2), c = 4tx + j
 template <int G>
@@ -358,9 +365,11 @@ __device__ __forceinline__ void eo_fwd_rows(const float *__restrict__ Ch, const 
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float *row = T + (4 * tx + j) * LD + 4 * ty;
-        *reinterpret_cast<float4 *>(row) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
-        *reinterpret_cast<float4 *>(row + H) = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+        const int c = 4 * tx + j;
+        float *row = T + c * LD;
+        *reinterpret_cast<float4 *>(row + 4 * swz(c, ty)) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        *reinterpret_cast<float4 *>(row + 4 * swz(c, ty + H / 4)) =
+            make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
     }
 }
 
@@ -379,8 +388,8 @@ __device__ __forceinline__ void eo_fwd_cols(const float *__restrict__ T, const f
 #pragma unroll 4
     for (int k = 0; k < H; ++k) {
         float t1[4], t2[4], be[4], bo[4];
-        f4a(t1, *reinterpret_cast<const float4 *>(T + k * LD + 4 * ty));
-        f4a(t2, *reinterpret_cast<const float4 *>(T + (G - 1 - k) * LD + 4 * ty));
+        f4a(t1, *reinterpret_cast<const float4 *>(T + k * LD + 4 * swz(k, ty)));
+        f4a(t2, *reinterpret_cast<const float4 *>(T + (G - 1 - k) * LD + 4 * swz(G - 1 - k, ty)));
         f4a(be, *reinterpret_cast<const float4 *>(Ch + k * LD + 4 * tx));
         f4a(bo, *reinterpret_cast<const float4 *>(Ch + k * LD + 4 * tx + H));
 #pragma unroll
@@ -436,10 +445,11 @@ __device__ __forceinline__ void eo_inv_rows(const float *__restrict__ Cl, const 
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float *row = T + (4 * tx + j) * LD;
-        *reinterpret_cast<float4 *>(row + 4 * ty) =
+        const int c = 4 * tx + j;
+        float *row = T + c * LD;
+        *reinterpret_cast<float4 *>(row + 4 * swz(c, ty)) =
             make_float4(E[0][j] + O[0][j], E[1][j] + O[1][j], E[2][j] + O[2][j], E[3][j] + O[3][j]);
-        *reinterpret_cast<float4 *>(row + G - 4 - 4 * ty) =
+        *reinterpret_cast<float4 *>(row + 4 * swz(c, G / 4 - 1 - ty)) =
             make_float4(E[3][j] - O[3][j], E[2][j] - O[2][j], E[1][j] - O[1][j], E[0][j] - O[0][j]);
     }
 }
@@ -460,8 +470,8 @@ __device__ __forceinline__ void eo_inv_cols(const float *__restrict__ T, const f
 #pragma unroll 4
     for (int k = 0; k < H; ++k) {
         float t1[4], t2[4], b1[4], b2[4];
-        f4a(t1, *reinterpret_cast<const float4 *>(T + k * LD + 4 * ty));
-        f4a(t2, *reinterpret_cast<const float4 *>(T + (k + H) * LD + 4 * ty));
+        f4a(t1, *reinterpret_cast<const float4 *>(T + k * LD + 4 * swz(k, ty)));
+        f4a(t2, *reinterpret_cast<const float4 *>(T + (k + H) * LD + 4 * swz(k + H, ty)));
         f4a(b1, *reinterpret_cast<const float4 *>(Cl + k * LDH + 4 * tx));
         f4a(b2, *reinterpret_cast<const float4 *>(Cl + (k + H) * LDH + 4 * tx));
 #pragma unroll
