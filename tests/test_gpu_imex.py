@@ -184,3 +184,34 @@ def test_imex_even_odd_mode_decay(p, G):
         test_equilibrium_is_kept_bit_exact(p, W.GM, (2.5e-4, 0.01, 1.0, 0.52), (0.0, 0.0))
     finally:
         p.imex_set_variant(G, keep)
+
+
+def test_imex_several_groups_in_one_handle(p):
+    """Groups of different models and grids in one handle: each realisation
+    lands at its own offset and matches the oracle."""
+    gs = [p.Group(W.FHN, 32, 2, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -6, 80, (-0.05, 0.05), 31),
+          p.Group(W.GM, 64, 1, (2.5e-4, 0.01, 1.0, 0.52), 2 ** -4, 60, (0.0, 0.01), 32),
+          p.Group(W.BZ, 32, 2, (1.6e-3, 1.32e-2, 4.4, 7.1), 2 ** -7, 70, (0.0, 0.01), 33)]
+    sim = p.Simulation(gs)
+    w0 = [sim.group_fields(i).cpu().numpy().copy() for i in range(3)]
+    res = sim.integrate_imex(residual=True)
+    torch.cuda.synchronize()
+    assert sim.sync_status() == 0
+    base = 0
+    for i, g in enumerate(gs):
+        got = sim.group_fields(i).cpu().numpy()
+        want = OI.imex_run(g.model, g.params, g.dt, g.n_steps, w0[i])
+        assert rel_err(got, want) <= FIELD_TOL, i
+        ref = oracle.residual(g.model, g.params, got.astype(np.float64))
+        np.testing.assert_allclose(res[base:base + g.n_real].cpu().numpy(), ref, rtol=1e-9, atol=1e-12)
+        base += g.n_real
+
+
+def test_imex_reports_a_blow_up(p):
+    """An explicit reaction step far beyond its limit (FHN, eps dt = 40)
+    diverges: the residual turns NaN and the status word says non-finite."""
+    sim = p.Simulation([p.Group(W.FHN, 32, 1, (2.8e-4, 0.05, 10.0, 0.95), 4.0, 40, (-0.5, 0.5), 3)])
+    res = sim.integrate_imex(residual=True)
+    torch.cuda.synchronize()
+    assert np.isnan(res.cpu().numpy()).all()
+    assert sim.sync_status() == 5   # RD_ERR_NONFINITE
