@@ -592,14 +592,15 @@ class Pipeline:
     CUDA graph and replayed.  sets[i] = (n1, n2, species_mask) of group i:
     set 1 = realisations 0..n1-1, set 2 = n1..n1+n2-1.  The cost is
     evaluated at each group's own correlation vector (y_obs = C).
-    integrator: "euler" (rd_integrate_batch, each group's n_steps) or "rkc"
+    integrator: "euler" (rd_integrate_batch, each group's n_steps), "rkc"
     (rd_integrate_rkc to each group's dt * n_steps; `rkc` = dict of h0,
-    rtol, atol, s_max, max_attempts); law: "power" (R0 b^-k), "linear"
+    rtol, atol, s_max, max_attempts) or "imex" (rd_integrate_imex, each
+    group's n_steps of its dt, diffusion implicit); law: "power" (R0 b^-k), "linear"
     (R0 - k (R0 - R_min) / M, b unused) or "fitted" (R0 b^-k with b fitted
     so that R_M = R_min, b unused).  RDODE groups need "rkc"."""
 
     def __init__(self, groups, sets, M, b, T, seed, device=None, integrator="euler", rkc=None, law="power"):
-        if integrator not in ("euler", "rkc") or law not in ("power", "linear", "fitted"):
+        if integrator not in ("euler", "rkc", "imex") or law not in ("power", "linear", "fitted"):
             raise ValueError("integrator / law")
         self.sim = Simulation(groups, device=device)
         self.dev = self.sim.device
@@ -642,6 +643,9 @@ class Pipeline:
         if self.integrator == "euler":
             _check("rd_integrate_batch", lib().rd_integrate_batch(
                 self.sim.handle, _ptr(self.sim.fields), -1, _ptr(self.residual), _stream()))
+        elif self.integrator == "imex":
+            _check("rd_integrate_imex", lib().rd_integrate_imex(
+                self.sim.handle, _ptr(self.sim.fields), _ptr(self.residual), _stream()))
         else:
             _check("rd_integrate_rkc", lib().rd_integrate_rkc(
                 self.sim.handle, _ptr(self.sim.fields), C.byref(self.rkc_opts), _ptr(self.rkc_stats),
