@@ -346,7 +346,7 @@ __device__ __forceinline__ void eo_fwd_rows(const float *__restrict__ Ch, const 
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 4
+#pragma unroll
     for (int k = 0; k < H; ++k) {
         float ae[4], ao[4], y1[4], y2[4];
         f4a(ae, *reinterpret_cast<const float4 *>(Ch + k * LD + 4 * ty));
@@ -385,7 +385,7 @@ __device__ __forceinline__ void eo_fwd_cols(const float *__restrict__ T, const f
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-#pragma unroll 4
+#pragma unroll
     for (int k = 0; k < H; ++k) {
         float t1[4], t2[4], be[4], bo[4];
         f4a(t1, *reinterpret_cast<const float4 *>(T + k * LD + 4 * swz(k, ty)));
@@ -428,7 +428,7 @@ __device__ __forceinline__ void eo_inv_rows(const float *__restrict__ Cl, const 
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) E[i][j] = O[i][j] = 0.f;
-#pragma unroll 4
+#pragma unroll
     for (int k = 0; k < H; ++k) {
         float ae[4], ao[4], z1[4], z2[4];
         f4a(ae, *reinterpret_cast<const float4 *>(Cl + k * LDH + 4 * ty));
@@ -467,7 +467,7 @@ __device__ __forceinline__ void eo_inv_cols(const float *__restrict__ T, const f
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) E[i][j] = O[i][j] = 0.f;
-#pragma unroll 4
+#pragma unroll
     for (int k = 0; k < H; ++k) {
         float t1[4], t2[4], b1[4], b2[4];
         f4a(t1, *reinterpret_cast<const float4 *>(T + k * LD + 4 * swz(k, ty)));
@@ -578,7 +578,8 @@ rd_imex_eo_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, fl
 // even/odd split (half the FMAs, its own rounding).
 // defaults from FHN x 128 realisations, dt = 2^-6, 300 steps on B300 (us
 // per step for 4x4 / 8x4 / 4x8 / 8x8 / even-odd): G = 64: 16.8 / 15.0 /
-// 15.0 / 16.8 / 10.4; G = 32: 4.67 / 6.04 / 6.13 / 9.32 / 4.09
+// 15.0 / 16.8 / 10.4 (9.1 once its k-loops were fully unrolled); G = 32:
+// 4.67 / 6.04 / 6.13 / 9.32 / 4.09
 static int g_imex_var[2] = {4, 4};   // [G == 64]
 
 int imex_n_variants() { return 5; }
