@@ -672,7 +672,31 @@ def imex_bench(p, torch, dev, stream, pk, src, dts=(2 ** -6, 2 ** -5, 2 ** -4)):
                      "product_tfma_per_s": fma / t / 1e12, "fma_frac": fma / t / 1e12 / fma_peak,
                      "rel_err_sample": err, "speedup_vs_euler": t_eul / t,
                      "residual_max": float(res[:, 0].max())})
+    # the long run (Sec. 5.1: the RD models are integrated to t = 100, by
+    # then at their steady state for the paper's parameters): Euler at its
+    # dt against the semi-implicit step at 2^-4 from the same initial
+    # states, on c2's FHN and on GM 64x64 with c3's parameters
+    T100, dt_i = 100.0, 2 ** -4
+    c3g = W.config("c3")["groups"][0]
+    long_runs = []
+    for name, gl in (("FHN 64x64 (c2)", dict(gd)),
+                     ("GM 64x64 (c3's parameters)", dict(c3g, G=64, n_real=128, dt=2 ** -8))):
+        nl = gl["n_real"]
+        se = p.Simulation([p.Group.from_dict(dict(gl, n_steps=int(round(T100 / gl["dt"]))))], device=dev)
+        t_e, res_e = timed(se, lambda: se.integrate(residual=True), reps=1)
+        fe = se.group_fields(0).cpu().numpy().astype(np.float64)
+        si = p.Simulation([p.Group.from_dict(dict(gl, dt=dt_i, n_steps=int(round(T100 / dt_i))))], device=dev)
+        t_i, res_i = timed(si, lambda: si.integrate_imex(residual=True), reps=1)
+        fi = si.group_fields(0).cpu().numpy().astype(np.float64)
+        dif = (np.abs(fe - fi).reshape(nl, 2, -1).max(-1) / np.abs(fe).reshape(nl, 2, -1).max(-1)).max(-1)
+        long_runs.append({"workload": name, "t_end": T100, "euler_dt": gl["dt"], "euler_ms": t_e * 1e3,
+                          "imex_dt": dt_i, "imex_ms": t_i * 1e3, "speedup": t_e / t_i,
+                          "euler_residual_max": float(res_e[:, 0].max()),
+                          "imex_residual_max": float(res_i[:, 0].max()),
+                          "same_pattern_1e-3": int((dif < 1e-3).sum()), "realisations": nl,
+                          "rel_diff_median": float(np.median(dif))})
     return {"workload": "FHN 64x64, 2 x 64 realisations, 0 -> T = 10^4 x 2^-10 (the c2 horizon)",
+            "t100": long_runs,
             "variant": p.imex_get_variant(G),
             "euler": {"ms": t_eul * 1e3, "steps": gd["n_steps"], "dt": gd["dt"], "rel_err_sample": err_eul},
             "reference": "oracle adaptive RK2, tolerance 1e-9, realisations 0 and 1",
