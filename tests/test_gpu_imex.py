@@ -215,3 +215,20 @@ def test_imex_reports_a_blow_up(p):
     torch.cuda.synchronize()
     assert np.isnan(res.cpu().numpy()).all()
     assert sim.sync_status() == 5   # RD_ERR_NONFINITE
+
+
+def test_imex_c2_full_size_sample(p):
+    """The benchmark's launch: all 128 realisations of the FHN 64x64
+    workload, 625 steps of 2^-6 (the c2 horizon), default kernel; the first
+    and the last realisation against the oracle."""
+    g = W.config("c2")["groups"][0]
+    grp = p.Group(g["model"], g["G"], g["n_real"], g["params"], 2 ** -6, 625, g["noise"], g["seed"])
+    sim = p.Simulation([grp])
+    w0 = sim.group_fields(0).cpu().numpy().copy()
+    sim.integrate_imex()
+    torch.cuda.synchronize()
+    assert sim.sync_status() == 0
+    got = sim.group_fields(0).cpu().numpy()
+    pick = [0, g["n_real"] - 1]
+    want = OI.imex_run(g["model"], g["params"], 2 ** -6, 625, w0[pick])
+    assert rel_err(got[pick], want) <= FIELD_TOL
