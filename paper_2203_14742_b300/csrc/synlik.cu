@@ -325,7 +325,11 @@ static rd_status launch_stats(const int64_t *d_Y, int32_t Mt, int32_t T, int64_t
     moments_kernel<<<dim3((unsigned)((T + MO_T - 1) / MO_T), (unsigned)n_problems), 256, 0, s>>>(
         d_Y, Mt, T, d_mu, d_cov, d_chol);
     note_launch();
-    stats_kernel<<<(unsigned)n_problems, 256, smem2, s>>>(Mt, T, np, d_y_obs, d_mu, d_cov, d_chol, d_scalars,
+    // 512 threads: the FP64 pipe is narrow and long-latency, and more
+    // independent trailing-update products in flight hide it (same-box A/B
+    // at 96 components, 1000 resamples, us per statistics call: 128 threads
+    // 720, 256 540, 512 497, 1024 503)
+    stats_kernel<<<(unsigned)n_problems, 512, smem2, s>>>(Mt, T, np, d_y_obs, d_mu, d_cov, d_chol, d_scalars,
                                                           d_active, d_status, timed_out);
     note_launch();
     return cuda_status(cudaGetLastError());
