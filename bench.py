@@ -45,7 +45,7 @@ FP32_INST_PER_CELL = {W.FHN: 15, W.GM: 20, W.DIFF: 10, W.BZ: 22}
 # ncu capture summarised in profiles/rd_resident_scalar_kernel_fhn64_c2.md,
 # keyed by a hash of the stepper sources: reported only while the kernel is
 # the one that was measured.
-STEPPER_TRAFFIC = {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488}
+STEPPER_TRAFFIC = {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488, "7c8c62601c860730": 4223488}
 STEPPER_SOURCES = ["paper_2203_14742_b300/csrc/stepper.cu", "paper_2203_14742_b300/csrc/tile.cuh",
                    "paper_2203_14742_b300/csrc/common.cuh"]
 
