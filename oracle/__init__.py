@@ -63,8 +63,8 @@ def lib():
         L.orc_fd.argtypes = [fp, C.c_int64, C.c_int, C.c_int, C.c_int, fp, fp]
         L.orc_maxabs.argtypes = [fp, fp, C.c_int64]
         L.orc_maxabs.restype = C.c_double
-        L.orc_d2_canon.argtypes = [fp, fp, C.c_int64]
-        L.orc_d2_canon.restype = C.c_double
+        L.orc_d2_exact.argtypes = [fp, fp, C.c_int64]
+        L.orc_d2_exact.restype = C.c_double
         L.orc_mcil_values.argtypes = [fp, fp, fp, C.c_int64, fp, fp, fp, C.c_int64, C.c_int, C.c_int, C.c_int,
                                       C.c_int, dp]
         L.orc_mcil_bins.argtypes = [dp, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_int, dp, u8p, i64p]
@@ -419,9 +419,9 @@ def maxabs(x, y):
     return lib().orc_maxabs(_p(x, C.c_float), _p(y, C.c_float), x.size)
 
 
-def d2_canon(x, y):
+def d2_exact(x, y):
     x, y = _f32(x), _f32(y)
-    return lib().orc_d2_canon(_p(x, C.c_float), _p(y, C.c_float), x.size)
+    return lib().orc_d2_exact(_p(x, C.c_float), _p(y, C.c_float), x.size)
 
 
 def mcil_values(X1, X2, G, nsp, mask=63, Gy=None):

@@ -14,9 +14,10 @@
  *   eq. (cil:CF_synth).
  *
  * Readings of points the paper leaves open (each stated where used):
- *   - distance = plain Euclidean norm of the difference vector; its FP64
- *     evaluation order, which the paper does not fix, is fixed here (see
- *     d2_f32): 256 interleaved partial sums combined by a halving tree;
+ *   - distance = plain Euclidean norm of the difference vector; its square
+ *     is the exact real sum of squared differences of the FP32 inputs,
+ *     rounded once to the nearest double (see d2_f32), so no evaluation
+ *     order enters;
  *   - R_k = R_{k-1} / b in FP64 (k = 1..M), thresholds T_k = R_k * R_k, and
  *     "d < R_k" is decided as d^2 < T_k;
  *   - the linear law of Sec. 2.1 (R_k = R0 - k h, h = (R0 - R_M) / M,
@@ -38,35 +39,94 @@ int orc_adjoint_one(int model, int G, const double *p, double dt,
 void orc_step(int model, int G, int n_real, const double *p, double dt,
               int64_t n_steps, double *w);
 
-/* Squared distance of two FP32 patterns (eq. eCDF) in one fixed FP64 order:
-   term t = (double(x_t) - double(y_t))^2 goes to partial sum p[t mod 256],
-   each partial accumulated in increasing t; then every group of 32
-   consecutive partials is combined by halving (q[i] = q[i] + q[i + s] for
-   s = 16, 8, 4, 2, 1) and the 8 group results the same way (s = 4, 2, 1).
-   Every operation is rounded separately. */
-static double d2_f32(const float *x, const float *y, int64_t d)
+/* Squared distance of two FP32 patterns (eq. eCDF, Sec. 2.1).  The paper
+   defines the distance on the reals; the value used here is that real
+   number, S = sum_t (x_t - y_t)^2 of the given FP32 values, formed exactly
+   and rounded once to the nearest double (ties to even).  It depends on no
+   evaluation order.
+
+   How it is formed exactly.  A finite float is m 2^e with an integer
+   |m| < 2^24 and e >= -149 (e = -149 for subnormals).  Each term
+   (x - y)^2 = x^2 + y^2 - 2 x y is then three integers below 2^48 times
+   powers of two no smaller than 2^-298.  They are added into one integer N
+   that counts units of 2^-298 (S = N 2^-298 exactly), kept as base-2^64
+   digits in 128-bit signed accumulators so that no carry is lost before
+   the end.  N is then rounded to 53 significant bits.  A non-finite input
+   element gives NaN. */
+#define XD_DIGITS 10            /* 640 bits: N < 2^(48 + 209 + 298 + 33) */
+#define XD_UNIT_EXP (-298)      /* N counts units of 2^-298 */
+
+/* float -> (signed integer significand, exponent); returns 0 if not finite */
+static int float_parts(float f, int64_t *m, int *e)
 {
-    double p[256];
-    for (int j = 0; j < 256; ++j) p[j] = 0.0;
-    for (int64_t t = 0; t < d; ++t) {
-        double df = (double)x[t] - (double)y[t];
-        double sq = df * df;
-        p[t % 256] = p[t % 256] + sq;
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    const int ef = (int)((u >> 23) & 0xffu);
+    int64_t mm = (int64_t)(u & 0x7fffffu);
+    if (ef == 0xff) return 0;
+    if (ef != 0) {
+        mm += (int64_t)1 << 23;
+        *e = ef - 150;
+    } else {
+        *e = -149;
     }
-    for (int g = 0; g < 8; ++g) {
-        double *q = p + 32 * g;
-        for (int s = 16; s >= 1; s /= 2)
-            for (int i = 0; i < s; ++i) q[i] = q[i] + q[i + s];
-    }
-    double w[8];
-    for (int g = 0; g < 8; ++g) w[g] = p[32 * g];
-    for (int s = 4; s >= 1; s /= 2)
-        for (int i = 0; i < s; ++i) w[i] = w[i] + w[i + s];
-    return w[0];
+    *m = (u >> 31) ? -mm : mm;
+    return 1;
 }
 
-/* The canonical squared distance, for the other oracle files. */
-double orc_d2_canon(const float *x, const float *y, int64_t d)
+/* acc += v 2^(pos) in units of 2^-298 (pos >= 0) */
+static void acc_add(__int128 *acc, int64_t v, int pos)
+{
+    const int k = pos / 64, r = pos % 64;
+    const __int128 two64 = (__int128)1 << 64;
+    const __int128 w = (__int128)v * ((__int128)1 << r);   /* |w| < 2^111 */
+    const uint64_t low = (uint64_t)w;                       /* w mod 2^64 */
+    acc[k] += (__int128)low;
+    acc[k + 1] += (w - (__int128)low) / two64;             /* exact */
+}
+
+static double d2_f32(const float *x, const float *y, int64_t d)
+{
+    __int128 acc[XD_DIGITS + 1];
+    for (int k = 0; k <= XD_DIGITS; ++k) acc[k] = 0;
+    for (int64_t t = 0; t < d; ++t) {
+        int64_t mx, my;
+        int ex, ey;
+        if (!float_parts(x[t], &mx, &ex) || !float_parts(y[t], &my, &ey)) return NAN;
+        acc_add(acc, mx * mx, 2 * ex - XD_UNIT_EXP);             /* x^2 */
+        acc_add(acc, my * my, 2 * ey - XD_UNIT_EXP);             /* y^2 */
+        acc_add(acc, -(mx * my), ex + ey + 1 - XD_UNIT_EXP);     /* -2 x y */
+    }
+    /* carries: N = sum dig[k] 2^(64 k) with 0 <= dig[k] < 2^64 */
+    uint64_t dig[XD_DIGITS + 1];
+    __int128 carry = 0;
+    const __int128 two64 = (__int128)1 << 64;
+    for (int k = 0; k <= XD_DIGITS; ++k) {
+        const __int128 t = acc[k] + carry;
+        dig[k] = (uint64_t)t;
+        carry = (t - (__int128)dig[k]) / two64;
+    }
+    if (carry != 0) return NAN;   /* cannot happen: S >= 0 and fits */
+    /* round N to 53 significant bits, ties to even */
+    const int nbits = 64 * (XD_DIGITS + 1);
+    int p = -1;
+    for (int i = nbits - 1; i >= 0 && p < 0; --i)
+        if ((dig[i / 64] >> (i % 64)) & 1u) p = i;
+    if (p < 0) return 0.0;
+    const int low = p > 52 ? p - 52 : 0;   /* lowest kept bit */
+    uint64_t mant = 0;
+    for (int i = p; i >= low; --i) mant = 2 * mant + ((dig[i / 64] >> (i % 64)) & 1u);
+    if (low > 0) {
+        const int half = (int)((dig[(low - 1) / 64] >> ((low - 1) % 64)) & 1u);
+        int sticky = 0;
+        for (int i = low - 2; i >= 0; --i) sticky |= (int)((dig[i / 64] >> (i % 64)) & 1u);
+        if (half && (sticky || (mant & 1u))) mant += 1;   /* may reach 2^53: still exact */
+    }
+    return ldexp((double)mant, low + XD_UNIT_EXP);
+}
+
+/* The squared distance, for the other oracle files. */
+double orc_d2_exact(const float *x, const float *y, int64_t d)
 {
     return d2_f32(x, y, d);
 }

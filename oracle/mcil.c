@@ -32,8 +32,9 @@
  *   - the L2 feature itself stays the plain Euclidean norm of the
  *     un-derived patterns (the CIL's own reading: a constant factor only
  *     rescales its radii), so it equals the single-norm CIL exactly;
- *   - with q0, qx, qy the canonical squared distances (the fixed FP64
- *     order of the CIL) of the patterns and of their Dx and Dy patterns, and
+ *   - with q0, qx, qy the squared distances of the CIL (the exact real sum
+ *     of squared differences, rounded once to the nearest double) of the
+ *     patterns and of their Dx and Dy patterns, and
  *     m0, mx, my the maxima of |difference| with every difference taken in
  *     FP64 (the same rounded difference as the squared distance uses: exact
  *     unless the two numbers' exponents differ by more than 29), every
@@ -57,7 +58,7 @@
 #include <stdint.h>
 #include <math.h>
 
-double orc_d2_canon(const float *x, const float *y, int64_t d);
+double orc_d2_exact(const float *x, const float *y, int64_t d);
 
 /* Features that are decided on their square (see above). */
 int orc_mcil_squared(int feature)
@@ -143,10 +144,10 @@ void orc_mcil_values(const float *X1, const float *Ax1, const float *Ay1, int64_
             const int64_t q = i * n2 + j;
             const float *x = X1 + i * d0, *y = X2 + j * d0;
             double q0 = 0, qx = 0, qy = 0, m0 = 0, mx = 0, my = 0;
-            if (mask & 0x0D) q0 = orc_d2_canon(x, y, d0);
+            if (mask & 0x0D) q0 = orc_d2_exact(x, y, d0);
             if (mask & 0x0C) {
-                qx = orc_d2_canon(Ax1 + i * dex, Ax2 + j * dex, dex);
-                qy = orc_d2_canon(Ay1 + i * dey, Ay2 + j * dey, dey);
+                qx = orc_d2_exact(Ax1 + i * dex, Ax2 + j * dex, dex);
+                qy = orc_d2_exact(Ay1 + i * dey, Ay2 + j * dey, dey);
             }
             if (mask & 0x32) m0 = orc_maxabs(x, y, d0);
             if (mask & 0x30) {

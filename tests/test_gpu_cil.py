@@ -188,11 +188,11 @@ def test_paper_scale_sampled_pairs(p):
     # ranks largest (its error bound is ~1e-4 relative)
     A, _ = p.cil_approx(t1, t2)
     top = torch.topk(A.reshape(-1), 16).indices.cpu().numpy()
-    best = max(oracle.d2_canon(X1[q // n], X2[q % n]) for q in top)
+    best = max(oracle.d2_exact(X1[q // n], X2[q % n]) for q in top)
     assert math.sqrt(best) == R0
     rng = np.random.default_rng(5)
     for i, j in zip(rng.integers(0, n, 2000), rng.integers(0, n, 2000)):
-        d2 = oracle.d2_canon(X1[i], X2[j])
+        d2 = oracle.d2_exact(X1[i], X2[j])
         assert math.sqrt(d2) <= R0
         K = sum(1 for r in radii if d2 < r * r)
         assert bins[i, j] == K, (i, j)

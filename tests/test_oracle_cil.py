@@ -106,15 +106,88 @@ def test_radii_power_law():
         assert r[k] == pytest.approx(4.0 * 1.3 ** -(k + 1), rel=1e-14)
 
 
-def test_pair_d2_matches_exact_sum_within_rounding():
+def exact_d2(x, y):
+    """The defined value written out with Python's exact rationals: the real
+    sum of squared differences of the FP32 inputs, rounded once to the
+    nearest double (float(Fraction) rounds correctly, ties to even)."""
+    from fractions import Fraction
+    s = sum((Fraction(float(a)) - Fraction(float(b))) ** 2 for a, b in zip(x, y))
+    return float(s)
+
+
+def wide_floats(rng, n):
+    """FP32 values spread over the whole exponent range: normals from 2^-126
+    to 2^127, subnormals, zeros, both signs."""
+    kind = rng.integers(0, 4, n)
+    mant = rng.uniform(1.0, 2.0, n)
+    e = rng.integers(-126, 100, n).astype(np.float64)
+    v = np.where(kind == 0, mant * 2.0 ** e, 0.0)
+    v = np.where(kind == 1, mant * 2.0 ** rng.integers(-10, 10, n), v)
+    v = np.where(kind == 2, rng.integers(1, 2 ** 23, n) * 2.0 ** -149, v)   # subnormals
+    v = v * np.where(rng.integers(0, 2, n) == 0, 1.0, -1.0)
+    return v.astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pair_d2_is_the_correctly_rounded_exact_sum(seed):
+    """Any exponent mix (subnormals, zeros, both signs, 2^-149 .. 2^100)."""
+    rng = np.random.default_rng(100 + seed)
+    for d in (1, 2, 3, 5, 17, 64):
+        x = wide_floats(rng, d)
+        y = wide_floats(rng, d)
+        if seed % 2:   # near-equal pairs: heavy cancellation in x^2 + y^2 - 2xy
+            y = (x.astype(np.float64) * (1 + rng.normal(size=d) * 1e-6)).astype(np.float32)
+        assert oracle.pair_d2(x[None], y[None])[0, 0] == exact_d2(x, y)
+
+
+def test_pair_d2_equals_fsum_of_exact_pieces():
+    """math.fsum (correctly rounded summation of doubles) of the pieces x^2,
+    y^2 and -2xy, each exact in a double for FP32 x, y."""
     rng = np.random.default_rng(7)
     X1 = rng.normal(size=(3, 1000)).astype(np.float32)
     X2 = rng.normal(size=(4, 1000)).astype(np.float32)
     d2 = oracle.pair_d2(X1, X2)
     for i in range(3):
         for j in range(4):
-            ex = math.fsum((float(a) - float(b)) ** 2 for a, b in zip(X1[i], X2[j]))
-            assert abs(d2[i, j] - ex) <= 1000 * 2.0 ** -53 * ex
+            pieces = []
+            for a, b in zip(X1[i].astype(np.float64), X2[j].astype(np.float64)):
+                pieces += [a * a, b * b, -2.0 * a * b]
+            assert d2[i, j] == math.fsum(pieces)
+
+
+def test_pair_d2_ties_round_to_even():
+    """Sums exactly half-way between two doubles round to the even one."""
+    t = np.float32(2.0 ** -27)          # t^2 = 2^-54
+    # 1 + 2^-54 + 2^-54 = 1 + 2^-53: half-way between 1 and 1 + 2^-52 -> 1
+    x = np.array([1.0, t, t], np.float32)
+    assert oracle.pair_d2(x[None], np.zeros((1, 3), np.float32))[0, 0] == 1.0
+    # (1 + 2^-52) + 2^-53: half-way between an odd and an even neighbour -> up
+    u = np.float32(2.0 ** -26)          # u^2 = 2^-52
+    x = np.array([1.0, u, t, t], np.float32)
+    assert oracle.pair_d2(x[None], np.zeros((1, 4), np.float32))[0, 0] == 1.0 + 2.0 ** -51
+    # one unit of 2^-54 more than half-way rounds up
+    x = np.array([1.0, t, t, t], np.float32)
+    assert oracle.pair_d2(x[None], np.zeros((1, 4), np.float32))[0, 0] == 1.0 + 2.0 ** -52
+    # order-free: four terms of 2^-54 after a 1 sum to 1 + 2^-52 exactly,
+    # which a left-to-right FP64 sum would lose (each 1 + 2^-54 rounds to 1)
+    x = np.array([1.0, t, t, t, t], np.float32)
+    assert oracle.pair_d2(x[None], np.zeros((1, 5), np.float32))[0, 0] == 1.0 + 2.0 ** -52
+    left_to_right = 0.0
+    for v in x.astype(np.float64):
+        left_to_right += v * v
+    assert left_to_right == 1.0
+
+
+def test_pair_d2_extremes():
+    big = np.float32(3.0e38)
+    tiny = np.float32(2.0 ** -149)
+    x = np.array([big, -big, tiny], np.float32)
+    y = np.array([-big, big, -tiny], np.float32)
+    assert oracle.pair_d2(x[None], y[None])[0, 0] == exact_d2(x, y)
+    assert oracle.pair_d2(x[None], x[None])[0, 0] == 0.0
+    z = np.zeros((1, 3), np.float32)
+    z[0, 1] = np.inf
+    assert math.isnan(oracle.pair_d2(z, np.zeros((1, 3), np.float32))[0, 0])
 
 
 # ------------------------------------------------------------ bootstrap
@@ -223,33 +296,6 @@ def test_inactive_constant_components():
     s = oracle.stats(Y, 10)
     assert list(s["active"]) == [0, 1, 0, 1]
     assert s["m_active"] == 2 and s["status"] == 0
-
-
-def test_canonical_order_matches_written_out_tree():
-    """The oracle's fixed FP64 order, written out here independently with
-    numpy float64 scalars: 256 interleaved partials, halving tree per group
-    of 32, then across the 8 groups."""
-    rng = np.random.default_rng(11)
-    for d in (1, 7, 255, 256, 257, 1000, 4100):
-        x = rng.normal(size=d).astype(np.float32)
-        y = rng.normal(size=d).astype(np.float32)
-        terms = [(np.float64(a) - np.float64(b)) ** 2 for a, b in zip(x, y)]
-        p = [np.float64(0.0)] * 256
-        for t, v in enumerate(terms):
-            p[t % 256] = p[t % 256] + v
-        for g in range(8):
-            s = 16
-            while s >= 1:
-                for i in range(s):
-                    p[32 * g + i] = p[32 * g + i] + p[32 * g + i + s]
-                s //= 2
-        w = [p[32 * g] for g in range(8)]
-        s = 4
-        while s >= 1:
-            for i in range(s):
-                w[i] = w[i] + w[i + s]
-            s //= 2
-        assert oracle.pair_d2(x[None], y[None])[0, 0] == w[0]
 
 
 def test_stats_mean_cov_are_exactly_rounded_rationals():
