@@ -35,7 +35,7 @@
 
 int orc_adjoint_one(int model, int G, const double *p, double dt,
                     int64_t n_steps, const double *w0, double *lam,
-                    double *grad);
+                    double *grad, double *gabs);
 void orc_step(int model, int G, int n_real, const double *p, double dt,
               int64_t n_steps, double *w);
 
@@ -48,13 +48,15 @@ void orc_step(int model, int G, int n_real, const double *p, double dt,
    How it is formed exactly.  A finite float is m 2^e with an integer
    |m| < 2^24 and e >= -149 (e = -149 for subnormals).  Each term
    (x - y)^2 = x^2 + y^2 - 2 x y is then three integers below 2^48 times
-   powers of two no smaller than 2^-298.  They are added into one integer N
-   that counts units of 2^-298 (S = N 2^-298 exactly), kept as base-2^64
-   digits in 128-bit signed accumulators so that no carry is lost before
-   the end.  N is then rounded to 53 significant bits.  A non-finite input
-   element gives NaN. */
-#define XD_DIGITS 10            /* 640 bits: N < 2^(48 + 209 + 298 + 33) */
-#define XD_UNIT_EXP (-298)      /* N counts units of 2^-298 */
+   powers of two 2^p with p >= -298.  The integers are added, exactly, into
+   one counter c_p per power of two (128-bit, so no counter can overflow),
+   giving S = sum_p c_p 2^p.  The binary digits of N = S 2^298 follow by
+   carrying from the lowest power upward (digit = c mod 2, carry = the
+   rest halved), and N is rounded to 53 significant bits.  A non-finite
+   input element gives NaN. */
+#define XP_OFFSET 298           /* counter index = p + 298 >= 0 */
+#define XP_COUNTERS 512         /* p + 298 <= 2 * 104 + 1 + 298 = 507 */
+#define XP_BITS 640             /* N < 2^(555 + 33) for d < 2^31 */
 
 /* float -> (signed integer significand, exponent); returns 0 if not finite */
 static int float_parts(float f, int64_t *m, int *e)
@@ -74,55 +76,43 @@ static int float_parts(float f, int64_t *m, int *e)
     return 1;
 }
 
-/* acc += v 2^(pos) in units of 2^-298 (pos >= 0) */
-static void acc_add(__int128 *acc, int64_t v, int pos)
-{
-    const int k = pos / 64, r = pos % 64;
-    const __int128 two64 = (__int128)1 << 64;
-    const __int128 w = (__int128)v * ((__int128)1 << r);   /* |w| < 2^111 */
-    const uint64_t low = (uint64_t)w;                       /* w mod 2^64 */
-    acc[k] += (__int128)low;
-    acc[k + 1] += (w - (__int128)low) / two64;             /* exact */
-}
-
 static double d2_f32(const float *x, const float *y, int64_t d)
 {
-    __int128 acc[XD_DIGITS + 1];
-    for (int k = 0; k <= XD_DIGITS; ++k) acc[k] = 0;
+    __int128 c[XP_COUNTERS];
+    for (int k = 0; k < XP_COUNTERS; ++k) c[k] = 0;
     for (int64_t t = 0; t < d; ++t) {
         int64_t mx, my;
         int ex, ey;
         if (!float_parts(x[t], &mx, &ex) || !float_parts(y[t], &my, &ey)) return NAN;
-        acc_add(acc, mx * mx, 2 * ex - XD_UNIT_EXP);             /* x^2 */
-        acc_add(acc, my * my, 2 * ey - XD_UNIT_EXP);             /* y^2 */
-        acc_add(acc, -(mx * my), ex + ey + 1 - XD_UNIT_EXP);     /* -2 x y */
+        c[2 * ex + XP_OFFSET] += mx * mx;              /* x^2 */
+        c[2 * ey + XP_OFFSET] += my * my;              /* y^2 */
+        c[ex + ey + 1 + XP_OFFSET] -= mx * my;         /* -2 x y */
     }
-    /* carries: N = sum dig[k] 2^(64 k) with 0 <= dig[k] < 2^64 */
-    uint64_t dig[XD_DIGITS + 1];
+    /* binary digits of N = sum_k c[k] 2^k */
+    unsigned char bit[XP_BITS];
     __int128 carry = 0;
-    const __int128 two64 = (__int128)1 << 64;
-    for (int k = 0; k <= XD_DIGITS; ++k) {
-        const __int128 t = acc[k] + carry;
-        dig[k] = (uint64_t)t;
-        carry = (t - (__int128)dig[k]) / two64;
+    for (int k = 0; k < XP_BITS; ++k) {
+        const __int128 t = carry + (k < XP_COUNTERS ? c[k] : 0);
+        const int digit = (t % 2) != 0;        /* t mod 2 in {0, 1} (t % 2 may be -1) */
+        bit[k] = (unsigned char)digit;
+        carry = (t - digit) / 2;               /* exact: t = 2 carry + digit */
     }
-    if (carry != 0) return NAN;   /* cannot happen: S >= 0 and fits */
+    if (carry != 0) return NAN;   /* cannot happen: S >= 0 and N < 2^640 */
     /* round N to 53 significant bits, ties to even */
-    const int nbits = 64 * (XD_DIGITS + 1);
     int p = -1;
-    for (int i = nbits - 1; i >= 0 && p < 0; --i)
-        if ((dig[i / 64] >> (i % 64)) & 1u) p = i;
+    for (int i = XP_BITS - 1; i >= 0 && p < 0; --i)
+        if (bit[i]) p = i;
     if (p < 0) return 0.0;
     const int low = p > 52 ? p - 52 : 0;   /* lowest kept bit */
     uint64_t mant = 0;
-    for (int i = p; i >= low; --i) mant = 2 * mant + ((dig[i / 64] >> (i % 64)) & 1u);
+    for (int i = p; i >= low; --i) mant = 2 * mant + bit[i];
     if (low > 0) {
-        const int half = (int)((dig[(low - 1) / 64] >> ((low - 1) % 64)) & 1u);
+        const int half = bit[low - 1];
         int sticky = 0;
-        for (int i = low - 2; i >= 0; --i) sticky |= (int)((dig[i / 64] >> (i % 64)) & 1u);
+        for (int i = low - 2; i >= 0; --i) sticky |= bit[i];
         if (half && (sticky || (mant & 1u))) mant += 1;   /* may reach 2^53: still exact */
     }
-    return ldexp((double)mant, low + XD_UNIT_EXP);
+    return ldexp((double)mant, low - XP_OFFSET);
 }
 
 /* The squared distance, for the other oracle files. */
@@ -421,7 +411,7 @@ int orc_smooth_cil_grad(int model, int G, int n_real, const double *p,
                         int species_mask, const int32_t *set1, int64_t n1,
                         const int32_t *set2, int64_t n2, const double *radii,
                         int M, double tau_frac, const double *cot,
-                        double *C_out, double *grad)
+                        double *C_out, double *grad, double *gabs)
 {
     int64_t cells = (int64_t)G * G, m = 2 * cells;
     int nsp = ((species_mask & 1) ? 1 : 0) + ((species_mask & 2) ? 1 : 0);
@@ -464,8 +454,11 @@ int orc_smooth_cil_grad(int model, int G, int n_real, const double *p,
         }
     }
     for (int i = 0; i < 4; ++i) grad[i] = 0.0;
+    if (gabs)
+        for (int i = 0; i < 4; ++i) gabs[i] = 0.0;
     int rc = 0;
     double *gr = (double *)calloc((size_t)(4 * n_real), sizeof(double));
+    double *ga = (double *)calloc((size_t)(4 * n_real), sizeof(double));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int r = 0; r < n_real; ++r) {
         int nz = 0;
@@ -473,12 +466,15 @@ int orc_smooth_cil_grad(int model, int G, int n_real, const double *p,
             if (lam[(int64_t)r * m + k] != 0.0) { nz = 1; break; }
         if (!nz) continue;
         if (orc_adjoint_one(model, G, p, dt, n_steps, w0 + (int64_t)r * m,
-                            lam + (int64_t)r * m, gr + 4 * r))
+                            lam + (int64_t)r * m, gr + 4 * r, ga + 4 * r))
             rc = 1;
     }
     for (int r = 0; r < n_real; ++r)
-        for (int i = 0; i < 4; ++i) grad[i] = grad[i] + gr[4 * r + i];
-    free(gr); free(lam); free(W); free(X1); free(X2); free(g1); free(g2);
+        for (int i = 0; i < 4; ++i) {
+            grad[i] = grad[i] + gr[4 * r + i];
+            if (gabs) gabs[i] = gabs[i] + ga[4 * r + i];
+        }
+    free(gr); free(ga); free(lam); free(W); free(X1); free(X2); free(g1); free(g2);
     return rc;
 }
 
