@@ -127,13 +127,39 @@ typedef struct rd_handle rd_handle;
  * groups/n_groups: host array, copied (may be freed after the call).
  * d_fields: device float32 array holding every group's fields.
  * out: receives the handle; the handle owns the device copy of the group
- *   table, the status word and (for RD_GROUP_ADJOINT groups) checkpoint
- *   memory.  Release with rd_free.
+ *   table, the status word, the step tables of rd_tables_size and (for
+ *   RD_GROUP_ADJOINT groups) checkpoint memory.  Release with rd_free.
  * Returns RD_ERR_INVALID_ARG for an unsupported G, model, n_real < 1,
  * misaligned field_offset, dt <= 0 or overlapping groups; RD_ERR_OOM when
  * the handle's device memory cannot be allocated. */
 rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_fields,
                   void *stream, rd_handle **out);
+
+/* rd_tables_size — device bytes of the step tables rd_init forms for this
+ * group list (host-only; no GPU needed): the stabilised RK2 coefficients
+ * and stability bounds when some group can run rd_integrate_rkc (about
+ * 1 MB), and the cosine-basis tables of rd_integrate_imex per grid side
+ * 32 or 64 present.  rd_init allocates and fills them once, on the current
+ * device, so rd_integrate_rkc and rd_integrate_imex allocate nothing and
+ * never synchronise (safe inside stream capture from the first call).
+ * RD_ERR_INVALID_ARG as rd_init for an invalid group list.
+ * rd_handle_table_bytes — the bytes a handle holds (0 for a null handle). */
+rd_status rd_tables_size(const rd_group *groups, int32_t n_groups, size_t *bytes);
+size_t rd_handle_table_bytes(const rd_handle *h);
+
+/* rd_set_params — replace the parameter vector (theta, params[6] host
+ * array, the layout of rd_group.params) of group `group` for every later
+ * call on the handle (integration, adjoint).  The initial states are not
+ * rewritten.  Enqueues the update on `stream` (a pageable host-to-device
+ * copy: not for use inside stream capture).  RD_ERR_INVALID_ARG for a bad
+ * group index or a parameter rd_init would refuse. */
+rd_status rd_set_params(rd_handle *h, int32_t group, const double *params, void *stream);
+
+/* rd_set_seed — replace the noise stream (rd_group.seed) of group `group`
+ * for later rd_reinit / initial-state writes (fresh random initial states
+ * per cost evaluation, Sec. 2.2: the likelihood is stochastic through them).
+ * Host-side only; RD_ERR_INVALID_ARG for a bad group index. */
+rd_status rd_set_seed(rd_handle *h, int32_t group, uint64_t seed);
 
 /* rd_reinit — write the initial states again (same rule as rd_init) into
  * d_fields, for a handle created earlier.  No allocation. */
@@ -367,8 +393,11 @@ const char *rd_status_str(rd_status s);
  * realisation r is d = G*G floats at offset r*2*G*G, both species d = 2*G*G.
  *
  * Definitions (both sides of every comparison use them exactly):
- *   d2_ij = sum_{t=0}^{d-1} (double(x_t) - double(y_t))^2, summed in t order
- *           in FP64 without fused multiply-add;
+ *   d2_ij = the real number sum_{t=0}^{d-1} (x_t - y_t)^2 of the FP32 inputs,
+ *           rounded once to the nearest double (ties to even).  The paper
+ *           defines the distance on the reals; this value depends on no
+ *           evaluation order.  Patterns must be finite (a non-finite element
+ *           makes d2 NaN and the pair's bin unspecified);
  *   R0    = sqrt(max_ij d2_ij)  (largest cross-set distance, Sec. 2.1);
  *   R_k   = R_{k-1} / b, k = 1..M (power law R0 b^-k), FP64;
  *   K_ij  = #{k : d2_ij < R_k * R_k}  (strict '<' of eq. eCDF);
@@ -388,9 +417,11 @@ const char *rd_status_str(rd_status s);
  * tensor-core Gram product (FP32 accumulation) gives
  * d2 ~ |x|^2 + |y|^2 - 2 x.y for every pair together with a rigorous error
  * bound; pairs whose bound straddles a threshold (or the maximum) are
- * re-evaluated with the exact sequential FP64 sum above, so K_ij and the
- * counts equal the definition bit for bit.
- * Limits: 1 <= n1, n2 <= 65535; 1 <= d; 1 <= M <= 32; b > 1.
+ * re-bounded by FP32 error-free sums and, if still undecided, evaluated
+ * exactly (integer fixed-point accumulation of every x^2, y^2 and -2xy,
+ * then one rounding), so K_ij and the counts equal the definition bit for
+ * bit.
+ * Limits: 1 <= n1, n2 <= 65535; 1 <= d <= 2^28; 1 <= M <= 32; b > 1.
  * d_work: caller scratch of cil_workspace_size bytes (256-byte aligned). */
 rd_status cil_workspace_size(int64_t n1, int64_t n2, int64_t d, size_t *bytes);
 rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1,
@@ -403,12 +434,12 @@ rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1,
 /* cil_features_linear — the same correlation integral with the linear radii
  * law of Sec. 2.1 / Sec. 3.2 (Table 1 uses it for the MC and RD-ODE models):
  *   R0 = sqrt(max_ij d2_ij), R_min = sqrt(min_ij d2_ij) (the largest and the
- *   smallest cross-set distance, both from the canonical d2),
+ *   smallest cross-set distance, both from d2 as defined above),
  *   h = (R0 - R_min) / M,  R_k = R0 - k h  (k = 1..M),
  * every operation FP64 rounded to nearest.  Bins and counts exactly as for
  * cil_features (K_ij = #{k : d2_ij < R_k * R_k}); d_radii_out[0] = R0,
  * d_radii_out[M] = R_M.  The smallest distance is found exactly like the
- * largest (tier-1 bounds, error-free tier 2, canonical tier 3 for the
+ * largest (tier-1 bounds, error-free tier 2, exact tier 3 for the
  * candidates left).  Arguments, workspace and limits as for cil_features
  * (no b). */
 rd_status cil_features_linear(const float *d_X1, int64_t ld1, int64_t n1,
@@ -420,7 +451,7 @@ rd_status cil_features_linear(const float *d_X1, int64_t ld1, int64_t n1,
 /* cil_features_fitted — the same correlation integral with the power law
  * whose decay is fitted to the range of the distances (Sec. 2.1, Sec. 3.2;
  * Table 1 uses it for the FHN, GM and BZ models): R0 and R_min the largest
- * and the smallest cross-set distance (from the canonical d2), b > 1 with
+ * and the smallest cross-set distance (from d2), b > 1 with
  * R_M / R0 = b^-M, R_k = R_{k-1} / b.  The paper gives the condition, not
  * how b is computed; here b is the smallest double whose M-th power, formed
  * as M - 1 sequential products rounded to nearest, reaches R0 / R_min,
@@ -471,8 +502,17 @@ rd_status cil_debug_approx(const float *d_X1, int64_t ld1, int64_t n1,
 rd_status cil_gram_only(int64_t n1, int64_t n2, int64_t d, void *d_work, size_t work_bytes,
                         double *flops, void *stream);
 
-/* cil_features_exact — the same outputs with every pair evaluated by the
- * exact sequential FP64 sum (no Gram product).  Slow; for checking. */
+/* cil_features_exact — the same outputs with every pair evaluated exactly
+ * (no Gram product, no bounds).  Slow; for checking. */
+/* cil_exact_d2 — checking entry point: d_out[e] = d2 (as defined above) of
+ * pattern d_pairs[2e] of set 1 and pattern d_pairs[2e+1] of set 2, for
+ * e < n_pairs (int64 index pairs, device memory; no bounds check of the
+ * indices, which must lie inside the sets).  The same exact evaluation as
+ * the correlation integral's last tier.  RD_ERR_INVALID_ARG for d outside
+ * 1..2^28, ld < d or n_pairs < 0. */
+rd_status cil_exact_d2(const float *d_X1, int64_t ld1, const float *d_X2, int64_t ld2, int64_t d,
+                       const int64_t *d_pairs, int64_t n_pairs, double *d_out, void *stream);
+
 rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1,
                              const float *d_X2, int64_t ld2, int64_t n2, int64_t d,
                              const double *d_radii_in, double b, int32_t M,
@@ -573,7 +613,8 @@ rd_status synlik_stats_ws(const uint8_t *d_bins, int32_t n_feat, int64_t n1, int
  * differences of each field, rounded to FP32 once (Dx: G x (G-1) values
  * s[y][x+1] - s[y][x], Dy: (G-1) x G values s[y+1][x] - s[y][x]).  With
  * q0, qx, qy the squared distances of the patterns and of their Dx and Dy
- * patterns in the canonical FP64 order of cil_features, and m0, mx, my the
+ * patterns as cil_features defines d2 (the exact real sum of squared
+ * differences rounded once to the nearest double), and m0, mx, my the
  * maxima of |difference| with each difference in FP64 (rounded to nearest,
  * as in the squared distance), feature f (bit f of `features`) is the FP64
  * expression (every operation rounded to nearest, no FMA)
@@ -594,16 +635,16 @@ rd_status synlik_stats_ws(const uint8_t *d_bins, int32_t n_feat, int64_t n1, int
  * order: d_radii_out [K][M+1] (R0, R_1..R_M); d_bins uint8 [K][n1][n2];
  * d_counts int64 [K][M]; d_C (nullable) float64 [K*M], the concatenated
  * correlation integral vector (counts / (n1 n2)); d_n_exact (nullable)
- * int64: pairs evaluated in the canonical order (-2 if a tensor-core stage
+ * int64: pairs evaluated exactly (-2 if a tensor-core stage
  * timed out; outputs invalid).  Bins and counts equal the definition bit
  * for bit: squared distances come from the tensor-core Gram with rigorous
  * intervals, maxima from an FP32 pass (whose rounding is within 2^-23 of
  * the maximum), and every pair whose interval may hold a maximum or meets
  * a threshold is re-bounded (FP32 error-free sums, exact maxima) and if
- * still undecided evaluated in the canonical order.
+ * still undecided evaluated exactly.
  * Workspace: d_work (256-byte aligned) of mcil_workspace_size bytes.
- * Limits: 1 <= n1, n2 <= 65535; 2 <= G <= 4096; 1 <= M <= 32; b > 1;
- * 1 <= features <= 63. */
+ * Limits: 1 <= n1, n2 <= 65535; 2 <= G <= 4096; n_species * G * G <= 2^28;
+ * 1 <= M <= 32; b > 1; 1 <= features <= 63. */
 rd_status mcil_workspace_size(int64_t n1, int64_t n2, int32_t G, int32_t n_species,
                               int32_t features, int32_t scale, int32_t M, size_t *bytes);
 rd_status mcil_features(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
@@ -636,8 +677,7 @@ rd_status mcil_features_rect(const float *d_X1, int64_t ld1, int64_t n1, const f
  * R_min) / M, R_k = R0 - k h, every operation FP64 rounded to nearest
  * (k h first, then the subtraction).  The smallest value of each feature
  * is found exactly like the largest: the pairs whose interval may hold it
- * are re-bounded and, if still undecided, evaluated in the canonical
- * order.  Bins, counts, outputs, workspace (mcil_workspace_size_rect) and
+ * are re-bounded and, if still undecided, evaluated exactly.  Bins, counts, outputs, workspace (mcil_workspace_size_rect) and
  * limits as for mcil_features_rect; no b. */
 rd_status mcil_features_linear_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
                                     int64_t ld2, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
@@ -658,6 +698,73 @@ rd_status mcil_features_fitted_rect(const float *d_X1, int64_t ld1, int64_t n1, 
                                     void *d_work, size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Synthetic correlation integral likelihood with bootstrapping (Alg. 6,
+ * Sec. 3.3): one evaluation of the cost f(theta) as one call.
+ *
+ *   1. simulate the N_syn = n_real patterns of group `group` at its
+ *      parameter vector (rd_set_params): with reinit, first the initial
+ *      states of that group (rd_reinit's rule, the group's seed,
+ *      rd_set_seed), then integrator 0 = explicit Euler (the group's n_steps
+ *      of dt, rd_integrate_batch's arithmetic) or 1 = the adaptive
+ *      stabilised RK2 of rd_integrate_rkc with `rkc`;
+ *   2. (reading of "from the remaining patterns") one fixed partition:
+ *      s^1 = realisations 0..n_set-1, s^2 = realisations n_set..N_syn-1;
+ *   3. the multi-feature correlation integral of s^1 against s^2 (as
+ *      mcil_features_rect / _linear_rect / _fitted_rect for law 0 / 1 / 2,
+ *      the power law taking b): d_radii [K][M+1] and the bin matrices;
+ *   4. y~(theta) = C(R_m, s_data, s^2) (eq. CIL_synth) with those radii:
+ *      d_y_data [K*M], the concatenated vector;
+ *   5. the bootstrap (Alg. 6 step 2, each part resampled with replacement
+ *      at its own size, synlik_stats_multi's index rule with stream seed),
+ *      T resamples: d_Y [T][K*M] counts, d_mu, d_cov, d_chol [K*M][K*M],
+ *      d_scalars = (logdet, f, loglik, M_act) with f = (y~ - mu)^T
+ *      Sigma^-1 (y~ - mu) on the active block (eq. cil:CF_synth),
+ *      d_active, d_status [1] as synlik_stats_ws.
+ * K = popcount(features).  Patterns: n_species = 1 (u only, G*G floats of
+ * each realisation) or 2 (both species, 2*G*G); data pattern i at d_data +
+ * i*ld_data with the same layout (ld_data >= n_species*G*G).  d_fields is
+ * the handle's field array (the group's patterns are read in place and
+ * left integrated).  d_n_exact (nullable) int64[2]: pairs evaluated exactly
+ * in steps 3 and 4 (-2: a tensor-core stage timed out).  d_work: caller
+ * scratch of scil_workspace_size bytes (256-byte aligned).  Asynchronous on
+ * `stream`, no allocation, no synchronisation.  Limits: 1 <= n_set <
+ * N_syn, n_data >= 1, T >= 2, K*M <= 96 and those of the calls above;
+ * RD_ERR_UNSUPPORTED for an RD_RDODE group. */
+typedef struct scil_spec {
+    int32_t group;        /* the group simulated at theta */
+    int32_t integrator;   /* 0 explicit Euler, 1 adaptive stabilised RK2 */
+    rd_rkc_opts rkc;      /* integrator 1 */
+    int64_t n_set;        /* N_set: size of s^1 */
+    int32_t n_species;    /* 1 or 2 */
+    int32_t features;     /* bit f = feature f of mcil_features */
+    int32_t scale;        /* nonzero: min-max scaled patterns (Sec. 4) */
+    int32_t law;          /* 0 power law with b, 1 linear, 2 power law fitted to the range */
+    double b;             /* law 0 */
+    int32_t M;            /* radii per feature */
+    int32_t T;            /* n_CIL resamples */
+    uint64_t seed;        /* resampling stream */
+    int32_t reinit;       /* nonzero: write fresh initial states first */
+    int32_t pad;
+} scil_spec;
+
+rd_status scil_workspace_size(const rd_handle *h, const scil_spec *spec, int64_t n_data, size_t *bytes);
+rd_status scil_evaluate(rd_handle *h, float *d_fields, const scil_spec *spec, const float *d_data,
+                        int64_t ld_data, int64_t n_data, double *d_radii, double *d_y_data, int64_t *d_Y,
+                        double *d_mu, double *d_cov, double *d_chol, double *d_scalars, uint8_t *d_active,
+                        int32_t *d_status, int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream);
+
+/* mcil_features_given_rect — mcil_features_rect with given radii:
+ * d_radii_in [K][M+1] per selected feature (R0 first, copied to
+ * d_radii_out and not used; R_1..R_M), thresholds R_k * R_k for the squared
+ * features and R_k for the others, bins and counts as mcil_features_rect
+ * (the data vector of Alg. 6 step 5, eq. CIL_synth).  No b. */
+rd_status mcil_features_given_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                   int64_t ld2, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
+                                   int32_t features, int32_t scale, int32_t M, const double *d_radii_in,
+                                   double *d_radii_out, uint8_t *d_bins, int64_t *d_counts, double *d_C,
+                                   int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Adjoint: gradient of a sigmoid-smoothed correlation integral with respect
  * to the four parameters of one group (the paper itself is gradient-free;
  * this serves proposal construction only, the likelihood keeps the exact
@@ -674,10 +781,12 @@ rd_status mcil_features_fitted_rect(const float *d_X1, int64_t ld1, int64_t n1, 
  * each segment from its checkpoint and runs
  *   lambda_n = lambda_{n+1} + dt J_F(w_n)^T lambda_{n+1},
  *   g       += dt (dF/dtheta(w_n))^T lambda_{n+1}   (accumulated in FP64).
- * Outputs: d_C[M] (float64, nullable), d_grad[4] (float64), d_final
- * (nullable) the group's final fields.  Requires the group to carry
- * RD_GROUP_ADJOINT (checkpoints reserved at rd_init).  Synchronous with
- * respect to the host only through stream order. */
+ * Outputs: d_C[M] (float64, nullable), d_grad[4] (float64).  Forward
+ * only: with d_cotangent and d_grad both NULL the call integrates once
+ * (no checkpoints, no reverse sweep) and writes d_C (then required).
+ * Requires the group to carry RD_GROUP_ADJOINT (checkpoints reserved at
+ * rd_init).  set1/set2 are host arrays of realisation indices.
+ * Synchronous with respect to the host only through stream order. */
 rd_status rd_adjoint(rd_handle *h, int32_t group, const float *d_fields0,
                      int32_t species_mask, const int32_t *d_set1, int64_t n1,
                      const int32_t *d_set2, int64_t n2, const double *d_radii,

@@ -94,7 +94,7 @@ def lib():
                                      C.c_double, dp, dp, dp, dp]
         L.orc_smooth_cil_grad.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_int64,
                                           dp, C.c_int, i32p, C.c_int64, i32p, C.c_int64, dp,
-                                          C.c_int, C.c_double, dp, dp, dp]
+                                          C.c_int, C.c_double, dp, dp, dp, dp]
         L.orc_smooth_cil_grad.restype = C.c_int
         L.orc_smooth_cil_loss.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_int64,
                                           dp, C.c_int, i32p, C.c_int64, i32p, C.c_int64, dp,
@@ -341,8 +341,12 @@ def smooth_cil(X1, X2, radii_, tau_frac, cot, grad=True):
 
 
 def smooth_cil_grad(model, p, dt, n_steps, w0, species_mask, set1, set2, radii_,
-                    tau_frac, cot):
-    """(C[M], grad[4]) of loss = cot . C_tau by the FP64 discrete adjoint."""
+                    tau_frac, cot, with_abs=False):
+    """(C[M], grad[4]) of loss = cot . C_tau by the FP64 discrete adjoint;
+    with_abs: also A[4], the sum over realisations, steps and cells of the
+    magnitudes of the terms whose sum is grad (A_i >= |grad_i|; a large
+    A_i / |grad_i| means cancellation, so relative errors of the terms
+    reach grad_i amplified by that ratio)."""
     p = _params(p)
     w0 = _d(w0)
     n_real, G = w0.shape[0], w0.shape[-1]
@@ -353,14 +357,15 @@ def smooth_cil_grad(model, p, dt, n_steps, w0, species_mask, set1, set2, radii_,
     M = r.size
     Cv = np.empty(M)
     g = np.empty(4)
+    A = np.empty(4)
     rc = lib().orc_smooth_cil_grad(model, G, n_real, _p(p, C.c_double), float(dt), int(n_steps),
                                    _p(w0, C.c_double), int(species_mask), _p(s1, C.c_int32),
                                    s1.size, _p(s2, C.c_int32), s2.size, _p(r, C.c_double), M,
                                    float(tau_frac), _p(c, C.c_double), _p(Cv, C.c_double),
-                                   _p(g, C.c_double))
+                                   _p(g, C.c_double), _p(A, C.c_double))
     if rc:
         raise MemoryError("oracle adjoint: allocation failed")
-    return Cv, g
+    return (Cv, g, A) if with_abs else (Cv, g)
 
 
 def smooth_cil_loss(model, p, dt, n_steps, w0, species_mask, set1, set2, radii_,
@@ -466,6 +471,50 @@ def mcil(X1, X2, G, nsp, b, M, mask=63, scale=False, Gy=None, law="power"):
                             _p(radii[a], C.c_double), _p(bins[a], C.c_uint8), _p(counts[a], C.c_int64))
     return {"features": feats, "values": V, "radii": radii, "bins": bins, "counts": counts,
             "C": counts.reshape(-1) / float(n1 * n2)}
+
+
+def mcil_given(X1, X2, G, nsp, radii, mask=63, scale=False, Gy=None):
+    """Multi-feature correlation integral with given radii [K, M+1] (R0
+    first, unused): per feature K_ij = #{k : V_ij < T_k}, T_k = R_k * R_k
+    for the squared features (L2, W12) and R_k for the others (eq. eCDF);
+    the data vector of Alg. 6 step 5 (eq. CIL_synth)."""
+    if scale:
+        X1, X2 = minmax(X1, G, nsp, Gy), minmax(X2, G, nsp, Gy)
+    V = mcil_values(X1, X2, G, nsp, mask, Gy)
+    feats = [f for f in range(6) if mask & (1 << f)]
+    radii = np.asarray(radii, np.float64)
+    K, M = len(feats), radii.shape[1] - 1
+    n1, n2 = V.shape[1], V.shape[2]
+    bins = np.zeros((K, n1, n2), np.uint8)
+    counts = np.zeros((K, M), np.int64)
+    for a, f in enumerate(feats):
+        for k in range(1, M + 1):
+            T = radii[a, k] * radii[a, k] if lib().orc_mcil_squared(f) else radii[a, k]
+            inside = V[f] < T
+            bins[a] += inside.astype(np.uint8)
+            counts[a, k - 1] = int(inside.sum())
+    return {"features": feats, "values": V, "radii": radii, "bins": bins, "counts": counts,
+            "C": counts.reshape(-1) / float(n1 * n2)}
+
+
+def scil(S, data, n_set, G, nsp, M, T, seed, mask=63, scale=False, law="fitted", b=None, Gy=None):
+    """Synthetic CIL with bootstrapping (Alg. 6) on given synthetic patterns
+    S (N_syn rows, simulated at theta) and data patterns (rows), in the
+    algorithm's order:
+      step 2 (reading: one fixed partition): s^1 = S[:n_set], s^2 = the
+        other N_syn - n_set rows; the radii and bins of the multi-feature
+        correlation integral of s^1 against s^2 (Alg. 2 step 2.2);
+      steps 2.1-3: T resamples (each part with replacement at its own
+        size), the concatenated count vectors, their mean and covariance;
+      steps 4-5: y~ = C(R, s_data, s^2) with those radii (eq. CIL_synth)
+        and the cost f = (y~ - mu)^T Sigma^-1 (y~ - mu) (eq. cil:CF_synth)."""
+    S = _f32(S)
+    S1, S2 = S[:n_set], S[n_set:]
+    syn = mcil(S1, S2, G, nsp, b, M, mask=mask, scale=scale, Gy=Gy, law=law)
+    dat = mcil_given(data, S2, G, nsp, syn["radii"], mask=mask, scale=scale, Gy=Gy)
+    st = synlik_multi(syn["bins"], M, T, seed, y_obs=dat["C"])
+    return {"radii": syn["radii"], "bins": syn["bins"], "y_data": dat["C"], "data_bins": dat["bins"],
+            "Y": st["Y"], "stats": st}
 
 
 def synlik_multi(bins, M, T, seed, y_obs=None):

@@ -219,14 +219,18 @@ void orc_residual(int model, int G, int n_real, const double *p,
  * --------------------------------------------------------------------- */
 
 /* y = J_F(w)^T lam and dg[4] = (dF/dtheta(w))^T lam for one realisation. */
-static void jt_vec(int model, int G, const double *p, const double *w,
-                   const double *lam, double *y, double *dg)
+/* y = J_F(w)^T lam, dg[i] = lam . dF/dtheta_i(w); dga (nullable) adds the
+   magnitudes of the terms of each dg[i] (sum over cells of |term|), a
+   measure of how much cancellation the gradient sum holds. */
+static void jt_vec_abs(int model, int G, const double *p, const double *w,
+                       const double *lam, double *y, double *dg, double *dga)
 {
     int64_t cells = (int64_t)G * G;
     const double *u = w, *v = w + cells;
     const double *lu = lam, *lv = lam + cells;
     double *yu = y, *yv = y + cells;
     double g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int yy = 0; yy < G; ++yy)
         for (int x = 0; x < G; ++x) {
             int64_t k = (int64_t)yy * G + x;
@@ -238,6 +242,8 @@ static void jt_vec(int model, int G, const double *p, const double *w,
             double su, sv;
             g0 = g0 + Lu * a;
             g1 = g1 + Lv * b;
+            a0 = a0 + fabs(Lu * a);
+            a1 = a1 + fabs(Lv * b);
             if (model == ORC_FHN) {
                 double eps = p[2], aa = p[3];
                 double duu = 1.0 - 3.0 * (uk * uk);
@@ -245,6 +251,8 @@ static void jt_vec(int model, int G, const double *p, const double *w,
                 sv = (-1.0) * a - (eps * aa) * b;
                 g2 = g2 + (uk - aa * vk) * b;
                 g3 = g3 + (-(eps * vk)) * b;
+                a2 = a2 + fabs((uk - aa * vk) * b);
+                a3 = a3 + fabs((-(eps * vk)) * b);
             } else if (model == ORC_GM) {
                 double rho = p[2], mu = p[3];
                 double dfu_du = rho * (2.0 * uk / vk - mu);
@@ -255,6 +263,8 @@ static void jt_vec(int model, int G, const double *p, const double *w,
                 sv = dfu_dv * a + dfv_dv * b;
                 g2 = g2 + ((uk * uk) / vk - mu * uk) * a + (uk * uk - vk) * b;
                 g3 = g3 + (-(rho * uk)) * a;
+                a2 = a2 + fabs(((uk * uk) / vk - mu * uk) * a) + fabs((uk * uk - vk) * b);
+                a3 = a3 + fabs((-(rho * uk)) * a);
             } else if (model == ORC_BZ) {
                 double B = p[3];
                 double dfu_du = -(B + 1.0) + 2.0 * uk * vk;
@@ -265,6 +275,8 @@ static void jt_vec(int model, int G, const double *p, const double *w,
                 sv = dfu_dv * a + dfv_dv * b;
                 g2 = g2 + a;                          /* dF_u/dA = 1, dF_v/dA = 0 */
                 g3 = g3 + (-uk) * a + uk * b;         /* dF_u/dB = -u, dF_v/dB = u */
+                a2 = a2 + fabs(a);
+                a3 = a3 + fabs((-uk) * a) + fabs(uk * b);
             } else {
                 su = 0.0;
                 sv = 0.0;
@@ -273,6 +285,15 @@ static void jt_vec(int model, int G, const double *p, const double *w,
             yv[k] = p[1] * Llv + sv;
         }
     dg[0] = g0; dg[1] = g1; dg[2] = g2; dg[3] = g3;
+    if (dga) {
+        dga[0] = a0; dga[1] = a1; dga[2] = a2; dga[3] = a3;
+    }
+}
+
+static void jt_vec(int model, int G, const double *p, const double *w,
+                   const double *lam, double *y, double *dg)
+{
+    jt_vec_abs(model, G, p, w, lam, y, dg, NULL);
 }
 
 /* Reverse sweep for one realisation.  w0: initial state [2][G][G];
@@ -280,7 +301,7 @@ static void jt_vec(int model, int G, const double *p, const double *w,
    All n_steps+1 states are stored (plain, memory O(n_steps * 2G^2)). */
 int orc_adjoint_one(int model, int G, const double *p, double dt,
                     int64_t n_steps, const double *w0, double *lam,
-                    double *grad)
+                    double *grad, double *gabs)
 {
     int64_t m = 2 * (int64_t)G * G;
     double *W = (double *)malloc(sizeof(double) * (size_t)m * (size_t)(n_steps + 1));
@@ -295,9 +316,11 @@ int orc_adjoint_one(int model, int G, const double *p, double dt,
         for (int64_t k = 0; k < m; ++k) wn1[k] = wn[k] + dt * F[k];
     }
     for (int64_t n = n_steps - 1; n >= 0; --n) {
-        double dg[4];
-        jt_vec(model, G, p, W + n * m, lam, y, dg);
+        double dg[4], da[4];
+        jt_vec_abs(model, G, p, W + n * m, lam, y, dg, da);
         for (int i = 0; i < 4; ++i) grad[i] = grad[i] + dt * dg[i];
+        if (gabs)
+            for (int i = 0; i < 4; ++i) gabs[i] = gabs[i] + dt * da[i];
         for (int64_t k = 0; k < m; ++k) lam[k] = lam[k] + dt * y[k];
     }
     free(W); free(F); free(y);

@@ -18,7 +18,8 @@ import os
 
 import torch
 
-__all__ = ["FHN", "GM", "DIFF", "BZ", "RDODE", "Group", "Simulation", "cil", "cil_exact", "synlik",
+__all__ = ["FHN", "GM", "DIFF", "BZ", "RDODE", "Group", "Simulation", "cil", "cil_exact", "exact_d2", "synlik",
+           "mcil", "mcil_given", "Scil",
            "SmoothCIL", "lib", "status_str"]
 
 FHN, GM, DIFF, BZ, RDODE = 0, 1, 2, 3, 4
@@ -41,6 +42,13 @@ class RdRkcOpts(C.Structure):
                 ("max_attempts", C.c_int64)]
 
 
+class ScilSpec(C.Structure):
+    _fields_ = [("group", C.c_int32), ("integrator", C.c_int32), ("rkc", RdRkcOpts), ("n_set", C.c_int64),
+                ("n_species", C.c_int32), ("features", C.c_int32), ("scale", C.c_int32), ("law", C.c_int32),
+                ("b", C.c_double), ("M", C.c_int32), ("T", C.c_int32), ("seed", C.c_uint64),
+                ("reinit", C.c_int32), ("pad", C.c_int32)]
+
+
 RKC_S_MAX = 256
 
 _vp, _i64, _i32, _dbl, _u64, _sz = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_uint64, C.c_size_t
@@ -48,6 +56,15 @@ _vp, _i64, _i32, _dbl, _u64, _sz = C.c_void_p, C.c_int64, C.c_int32, C.c_double,
 _SIGS = {
     "rd_init": (_i32, [C.POINTER(RdGroup), _i32, _vp, _vp, C.POINTER(_vp)]),
     "rd_reinit": (_i32, [_vp, _vp, _vp]),
+    "rd_set_params": (_i32, [_vp, _i32, C.POINTER(_dbl), _vp]),
+    "rd_set_seed": (_i32, [_vp, _i32, _u64]),
+    "scil_workspace_size": (_i32, [_vp, C.POINTER(ScilSpec), _i64, C.POINTER(_sz)]),
+    "scil_evaluate": (_i32, [_vp, _vp, C.POINTER(ScilSpec), _vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                             _vp, _vp, _vp, _vp, _sz, _vp]),
+    "mcil_features_given_rect": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _i32,
+                                        _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "rd_tables_size": (_i32, [C.POINTER(RdGroup), _i32, C.POINTER(_sz)]),
+    "rd_handle_table_bytes": (_sz, [_vp]),
     "rd_integrate_batch": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "rd_integrate_reference": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "rd_integrate_f64": (_i32, [_vp, _vp, _vp, _i64, _vp]),
@@ -72,6 +89,7 @@ _SIGS = {
                                    _vp, _sz, _vp]),
     "cil_features_exact": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _dbl, _i32, _vp, _vp,
                                   _vp, _vp, _vp, _sz, _vp]),
+    "cil_exact_d2": (_i32, [_vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _vp]),
     "cil_gram_only": (_i32, [_i64, _i64, _i64, _vp, _sz, C.POINTER(_dbl), _vp]),
     "cil_debug_approx": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _sz, _vp]),
     "synlik_stats": (_i32, [_vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -304,15 +322,33 @@ class Simulation:
     def sync_status(self):
         return lib().rd_sync_status(self.handle, _stream())
 
+    def table_bytes(self):
+        """Device bytes of the step tables the handle formed in rd_init."""
+        return int(lib().rd_handle_table_bytes(self.handle))
+
+    def set_params(self, group, params):
+        """Replace group `group`'s parameter vector (rd_set_params) for every
+        later call; params: up to 6 floats (the group's layout)."""
+        vals = [float(x) for x in params] + [0.0] * (6 - len(params))
+        arr = (C.c_double * 6)(*vals)
+        _check("rd_set_params", lib().rd_set_params(self.handle, int(group), arr, _stream()))
+        g = self.groups[group]
+        g.params = tuple(vals)
+        self._arr[group].params[:] = vals
+
     def adjoint(self, group, fields0, species_mask, set1, set2, radii, tau_frac, cotangent):
-        """(C[M], grad[4]) float64 tensors: smoothed CIL and its gradient."""
+        """(C[M], grad[4]) float64 tensors: smoothed CIL and its gradient.
+        cotangent=None: forward only (C, no reverse sweep; grad is None)."""
         s1 = (C.c_int32 * len(set1))(*[int(x) for x in set1])
         s2 = (C.c_int32 * len(set2))(*[int(x) for x in set2])
         radii = radii.to(device=self.device, dtype=torch.float64).contiguous()
-        cot = cotangent.to(device=self.device, dtype=torch.float64).contiguous()
         M = radii.numel()
         Cv = torch.empty(M, dtype=torch.float64, device=self.device)
-        g = torch.empty(4, dtype=torch.float64, device=self.device)
+        if cotangent is None:
+            cot, g = None, None
+        else:
+            cot = cotangent.to(device=self.device, dtype=torch.float64).contiguous()
+            g = torch.empty(4, dtype=torch.float64, device=self.device)
         _check("rd_adjoint", lib().rd_adjoint(self.handle, int(group), _ptr(fields0), int(species_mask),
                                               s1, len(set1), s2, len(set2), _ptr(radii), M,
                                               float(tau_frac), _ptr(cot), _ptr(Cv), _ptr(g), _stream()))
@@ -446,8 +482,25 @@ def cil_fitted(X1, X2, M=16, work=None, out=None):
 
 
 def cil_exact(X1, X2, b=1.3, M=16, radii=None, work=None):
-    """Same outputs, every pair by the exact sequential FP64 sum (checking)."""
+    """Same outputs, every pair evaluated exactly (checking)."""
     return _cil_call("cil_features_exact", X1, X2, b, M, radii, work)
+
+
+def exact_d2(X1, X2, pairs):
+    """d2 of the listed pairs (int64 [n, 2] of row indices into X1, X2): the
+    exact real sum of squared differences rounded once (checking)."""
+    X1, ld1, n1, d = _as_rows(X1)
+    X2, ld2, n2, d2_ = _as_rows(X2)
+    if d2_ != d:
+        raise ValueError("pattern lengths differ")
+    pairs = torch.as_tensor(pairs, dtype=torch.int64).to(X1.device).contiguous()
+    if pairs.numel() and (int(pairs[:, 0].min()) < 0 or int(pairs[:, 0].max()) >= n1 or
+                          int(pairs[:, 1].min()) < 0 or int(pairs[:, 1].max()) >= n2):
+        raise IndexError("pair index outside the sets")
+    out = torch.empty(pairs.shape[0], dtype=torch.float64, device=X1.device)
+    _check("cil_exact_d2", lib().cil_exact_d2(_ptr(X1), ld1, _ptr(X2), ld2, d, _ptr(pairs), pairs.shape[0],
+                                              _ptr(out), _stream()))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -567,6 +620,87 @@ def mcil(X1, X2, G, n_species, b=1.3, M=16, features=63, scale=False, work=None,
     return {"radii": radii, "bins": bins, "counts": counts, "C": Cv, "n_exact": nex}
 
 
+def mcil_given(X1, X2, G, n_species, radii, features=63, scale=False, work=None, Gy=None):
+    """Multi-feature correlation integral with given radii [K, M+1] (R0
+    first, not used): the data vector of Alg. 6 step 5 (eq. CIL_synth).
+    Returns bins [K, n1, n2], counts [K, M], C [K*M], n_exact."""
+    Gy = G if Gy is None else Gy
+    X1, ld1, n1, d = _as_rows(X1)
+    X2, ld2, n2, d2 = _as_rows(X2)
+    if d != d2 or d != n_species * Gy * G:
+        raise ValueError("pattern length must be n_species * Gy * G")
+    dev = X1.device
+    K = bin(int(features)).count("1")
+    radii = radii.to(device=dev, dtype=torch.float64).contiguous()
+    if radii.dim() != 2 or radii.shape[0] != K:
+        raise ValueError("radii: [K, M+1]")
+    M = radii.shape[1] - 1
+    if work is None:
+        work = mcil_workspace(n1, n2, G, n_species, features, scale, M, dev, Gy=Gy)
+    rout = torch.empty_like(radii)
+    bins = torch.empty((K, n1, n2), dtype=torch.uint8, device=dev)
+    counts = torch.empty((K, M), dtype=torch.int64, device=dev)
+    Cv = torch.empty(K * M, dtype=torch.float64, device=dev)
+    nex = torch.zeros(1, dtype=torch.int64, device=dev)
+    _check("mcil_features_given_rect", lib().mcil_features_given_rect(
+        _ptr(X1), ld1, n1, _ptr(X2), ld2, n2, int(Gy), int(G), int(n_species), int(features), 1 if scale else 0,
+        int(M), _ptr(radii), _ptr(rout), _ptr(bins), _ptr(counts), _ptr(Cv), _ptr(nex), _ptr(work), work.numel(),
+        _stream()))
+    return {"radii": rout, "bins": bins, "counts": counts, "C": Cv, "n_exact": nex}
+
+
+class Scil:
+    """One evaluation of the synthetic-likelihood cost f(theta) with
+    bootstrapping (Alg. 6) per call of run(): scil_evaluate on group `group`
+    of `sim` (its n_real = N_syn patterns at its parameters) against the
+    data patterns `data` (rows, n_species * G * G floats).  Outputs and the
+    workspace are allocated once here, so run() can be captured in a CUDA
+    graph.  law "power" (b), "linear" or "fitted"; integrator "euler" or
+    "rkc" (rkc = dict of h0, rtol, atol, s_max, max_attempts, t_end)."""
+
+    def __init__(self, sim, group, data, n_set, n_species=2, features=63, scale=False, law="fitted", b=1.3,
+                 M=13, T=1000, seed=0, reinit=True, integrator="euler", rkc=None):
+        self.sim, self.group = sim, int(group)
+        self.data, self.ld_data, self.n_data, d = _as_rows(data)
+        g = sim.groups[group]
+        if d != n_species * g.G * g.G:
+            raise ValueError("data rows must hold n_species * G * G floats")
+        r = dict(h0=1e-3, rtol=1e-5, atol=1e-5, s_max=RKC_S_MAX, max_attempts=100000, t_end=0.0)
+        r.update(rkc or {})
+        o = RdRkcOpts(float(r["t_end"]), float(r["h0"]), float(r["rtol"]), float(r["atol"]), int(r["s_max"]), 0, 0,
+                      int(r["max_attempts"]))
+        self.spec = ScilSpec(self.group, {"euler": 0, "rkc": 1}[integrator], o, int(n_set), int(n_species),
+                             int(features), 1 if scale else 0, {"power": 0, "linear": 1, "fitted": 2}[law],
+                             float(b), int(M), int(T), int(seed) & 0xFFFFFFFFFFFFFFFF, 1 if reinit else 0, 0)
+        sz = _sz(0)
+        _check("scil_workspace_size", lib().scil_workspace_size(sim.handle, C.byref(self.spec), self.n_data,
+                                                                C.byref(sz)))
+        dev = sim.device
+        self.work = torch.empty(sz.value, dtype=torch.uint8, device=dev)
+        K = bin(int(features)).count("1")
+        Mt = K * M
+        self.K, self.M, self.T = K, M, T
+        self.out = {"radii": torch.empty((K, M + 1), dtype=torch.float64, device=dev),
+                    "y_data": torch.empty(Mt, dtype=torch.float64, device=dev),
+                    "Y": torch.empty((T, Mt), dtype=torch.int64, device=dev),
+                    "mu": torch.empty(Mt, dtype=torch.float64, device=dev),
+                    "cov": torch.empty((Mt, Mt), dtype=torch.float64, device=dev),
+                    "chol": torch.empty((Mt, Mt), dtype=torch.float64, device=dev),
+                    "scalars": torch.empty(4, dtype=torch.float64, device=dev),
+                    "active": torch.empty(Mt, dtype=torch.uint8, device=dev),
+                    "status": torch.empty(1, dtype=torch.int32, device=dev),
+                    "n_exact": torch.zeros(2, dtype=torch.int64, device=dev)}
+
+    def run(self):
+        o = self.out
+        _check("scil_evaluate", lib().scil_evaluate(
+            self.sim.handle, _ptr(self.sim.fields), C.byref(self.spec), _ptr(self.data), self.ld_data, self.n_data,
+            _ptr(o["radii"]), _ptr(o["y_data"]), _ptr(o["Y"]), _ptr(o["mu"]), _ptr(o["cov"]), _ptr(o["chol"]),
+            _ptr(o["scalars"]), _ptr(o["active"]), _ptr(o["status"]), _ptr(o["n_exact"]), _ptr(self.work),
+            self.work.numel(), _stream()))
+        return o
+
+
 def mcil_rdode(fields, n1, b=1.3, M=13, scale=False, law="power"):
     """Multi-feature correlation integral of 1-D reaction-diffusion-ODE
     patterns (Sec. 5.2): fields [n, 2, N] (u, w); set 1 = rows 0..n1-1, set 2
@@ -678,25 +812,34 @@ class Pipeline:
 # ---------------------------------------------------------------------------
 class SmoothCIL(torch.autograd.Function):
     """C_tau(theta): the sigmoid-smoothed correlation integral of one group
-    after its n_steps, as a differentiable function of theta = params[4].
+    after its n_steps, as a differentiable function of theta (the group's
+    first four parameters: FHN (Du, Dv, eps, a), GM (Du, Dv, rho, mu), BZ
+    (Du, Dv, A, B)).
 
     forward(theta, sim, group, fields0, species_mask, set1, set2, radii,
-            tau_frac) -> C[M].  The backward pass needs the cotangent, so the
-    forward only evaluates C; backward calls rd_adjoint with the incoming
-    gradient as cotangent (the parameters inside `sim` must equal theta)."""
+            tau_frac) -> C[M]: writes theta into the group (rd_set_params,
+    keeping its other parameter slots) and evaluates C by one forward
+    integration (no reverse sweep).  backward calls rd_adjoint with the
+    incoming gradient as cotangent, at the theta of the forward pass."""
 
     @staticmethod
     def forward(ctx, theta, sim, group, fields0, species_mask, set1, set2, radii, tau_frac):
-        M = radii.numel()
-        ones = torch.zeros(M, dtype=torch.float64, device=fields0.device)
-        Cv, _ = sim.adjoint(group, fields0, species_mask, set1, set2, radii, tau_frac, ones)
+        th = [float(x) for x in theta.detach().cpu().tolist()]
+        if len(th) != 4:
+            raise ValueError("theta: 4 parameters")
+        full = list(th) + list(sim.groups[group].params[4:])
+        sim.set_params(group, full)
+        Cv, _ = sim.adjoint(group, fields0, species_mask, set1, set2, radii, tau_frac, None)
         ctx.args = (sim, group, fields0, species_mask, set1, set2, radii, tau_frac)
+        ctx.full = full
         ctx.theta_device = theta.device
         return Cv
 
     @staticmethod
     def backward(ctx, gC):
         sim, group, fields0, species_mask, set1, set2, radii, tau_frac = ctx.args
+        if list(sim.groups[group].params) != ctx.full:   # another call moved theta since
+            sim.set_params(group, ctx.full)
         _, g = sim.adjoint(group, fields0, species_mask, set1, set2, radii, tau_frac,
                            gC.detach().to(torch.float64))
         return (g.to(ctx.theta_device), None, None, None, None, None, None, None, None)

@@ -136,9 +136,9 @@ __global__ void smooth_fwd_kernel(const float *__restrict__ w, int64_t cells, in
             double z = (radii[k] - dd) / tau;
             double sg = 1.0 / (1.0 + exp(-z));
             atomicAdd(&Cout[k], sg * inv);
-            wsum += cot[k] * (-(sg * (1.0 - sg)) / tau) * inv;
+            if (cot) wsum += cot[k] * (-(sg * (1.0 - sg)) / tau) * inv;
         }
-        W[(int64_t)i * n2 + j] = dd > 0.0 ? wsum / dd : 0.0;
+        if (cot) W[(int64_t)i * n2 + j] = dd > 0.0 ? wsum / dd : 0.0;
     }
 }
 
@@ -291,10 +291,9 @@ static rd_status launch_reverse(const GroupDev &g, const float *traj, int64_t tr
     constexpr int TY = AdjTile<G>::TY, TX = AdjTile<G>::TX;
     using T = Tiling<G, TY, TX>;
     auto kern = rd_adjoint_reverse_kernel<MODEL, G, TY, TX>;
-    static bool attr = false;
-    if (!attr) {
-        RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM));
-        attr = true;
+    {
+        rd_status ast = smem_attr(kern, (int)T::SMEM);
+        if (ast) return ast;
     }
     kern<<<g.n_real, T::NT, T::SMEM, s>>>(traj, traj_stride, len, lam, cf, gacc, active);
     note_launch();
@@ -324,7 +323,11 @@ extern "C" rd_status rd_adjoint(rd_handle *hh, int32_t group, const float *d_fie
                                 const int32_t *set1, int64_t n1, const int32_t *set2, int64_t n2,
                                 const double *d_radii, int32_t M, double tau_frac, const double *d_cotangent,
                                 double *d_C, double *d_grad, void *stream) {
-    if (!hh || !d_fields0 || !set1 || !set2 || !d_radii || !d_cotangent || !d_grad) return RD_ERR_INVALID_ARG;
+    if (!hh || !d_fields0 || !set1 || !set2 || !d_radii) return RD_ERR_INVALID_ARG;
+    // forward only (C, no gradient) when neither cotangent nor gradient is given
+    const bool fwd_only = !d_cotangent && !d_grad;
+    if (!fwd_only && (!d_cotangent || !d_grad)) return RD_ERR_INVALID_ARG;
+    if (fwd_only && !d_C) return RD_ERR_INVALID_ARG;
     Handle &h = *reinterpret_cast<Handle *>(hh);
     if (group < 0 || group >= h.n_groups) return RD_ERR_INVALID_ARG;
     const GroupDev &g = h.h_groups[group];
@@ -354,6 +357,18 @@ extern "C" rd_status rd_adjoint(rd_handle *hh, int32_t group, const float *d_fie
     gl.field_offset = 0;
     gl.real_base = 0;
     RD_CUDA_TRY(cudaMemcpyAsync(a.cur, d_fields0 + g.field_offset, mall * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (fwd_only) {
+        if (N > 0) {
+            rd_status st = launch_integrate_group(gl, a.cur, N, nullptr, h.d_status, s);
+            if (st) return st;
+        }
+        RD_CUDA_TRY(cudaMemsetAsync(d_C, 0, M * sizeof(double), s));
+        dim3 gp((unsigned)n2, (unsigned)n1);
+        smooth_fwd_kernel<<<gp, 256, 0, s>>>(a.cur, cells, species_mask, d_s1, d_s2, (int)n1, (int)n2, d_radii, M,
+                                             tau_frac, nullptr, d_C, a.W);
+        note_launch();
+        return cuda_status(cudaGetLastError());
+    }
     for (int64_t q = 0; q < nseg; ++q) {
         int64_t len = std::min(C, N - q * C);
         RD_CUDA_TRY(cudaMemcpyAsync(a.ckpt + q * mall, a.cur, mall * sizeof(float), cudaMemcpyDeviceToDevice, s));

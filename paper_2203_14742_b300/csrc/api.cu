@@ -9,10 +9,6 @@
 
 using namespace rdcil;
 
-struct rd_handle {
-    Handle h;
-};
-
 namespace rdcil {
 rd_status adjoint_reserve(Handle &h);
 void adjoint_release(Handle &h);
@@ -102,6 +98,8 @@ extern "C" rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_
     if (st) { rd_free(hh); return st; }
     st = batch_plan_create(h.h_groups, n_groups, &h.batch);
     if (st) { rd_free(hh); return st; }
+    st = tables_create(h, s);
+    if (st) { rd_free(hh); return st; }
     for (int32_t i = 0; i < n_groups; ++i) {
         st = launch_init_fields(h.h_groups[i], d_fields, s);
         if (st) { rd_free(hh); return st; }
@@ -110,6 +108,109 @@ extern "C" rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_
     // sure the pageable source of the async copy is no longer needed
     if (cudaStreamSynchronize(s) != cudaSuccess) { rd_free(hh); return RD_ERR_CUDA; }
     *out = hh;
+    return RD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// step tables of the handle (formed once in rd_init, on the handle's device)
+// ---------------------------------------------------------------------------
+TableNeeds rdcil::table_needs(const GroupDev *groups, int n_groups) {
+    TableNeeds n{false, {false, false}};
+    for (int i = 0; i < n_groups; ++i) {
+        n.rkc |= rkc_supported(groups[i]);
+        if (imex_supported(groups[i])) n.imex[groups[i].G == 64] = true;
+    }
+    return n;
+}
+
+static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t rdcil::table_bytes(const TableNeeds &n) {
+    size_t b = n.rkc ? up256(rkc_table_bytes()) : 0;
+    for (int gi = 0; gi < 2; ++gi)
+        if (n.imex[gi]) {
+            const int G = gi ? 64 : 32;
+            b += up256(sizeof(float) * imex_table_floats(G)) + up256(sizeof(float) * imex_eo_table_floats(G));
+        }
+    return b;
+}
+
+rd_status rdcil::tables_create(Handle &h, cudaStream_t s) {
+    const TableNeeds n = table_needs(h.h_groups, h.n_groups);
+    const size_t bytes = table_bytes(n);
+    h.table_bytes = 0;
+    if (bytes == 0) return RD_OK;
+    char *base = nullptr;
+    if (cudaMalloc(&base, bytes) != cudaSuccess) return RD_ERR_OOM;
+    h.table_bytes = bytes;
+    size_t off = 0;
+    if (n.rkc) {
+        h.d_rkc_tab = (float4 *)(base + off);
+        h.d_rkc_beta = (double *)(base + off + sizeof(float4) * (size_t)(RD_RKC_S_MAX + 1) * (RD_RKC_S_MAX + 1));
+        off += up256(rkc_table_bytes());
+        rd_status st = rkc_tables_fill(h.d_rkc_tab, h.d_rkc_beta, s);
+        if (st) return st;
+    }
+    for (int gi = 0; gi < 2; ++gi) {
+        if (!n.imex[gi]) continue;
+        const int G = gi ? 64 : 32;
+        h.d_imex_tab[gi] = (float *)(base + off);
+        off += up256(sizeof(float) * imex_table_floats(G));
+        h.d_imex_eo_tab[gi] = (float *)(base + off);
+        off += up256(sizeof(float) * imex_eo_table_floats(G));
+        rd_status st = imex_tables_fill(G, h.d_imex_tab[gi], h.d_imex_eo_tab[gi], s);
+        if (st) return st;
+    }
+    return RD_OK;
+}
+
+void rdcil::tables_release(Handle &h) {
+    // one allocation: the first table in use holds its base
+    void *base = h.d_rkc_tab ? (void *)h.d_rkc_tab
+                             : (h.d_imex_tab[0] ? (void *)h.d_imex_tab[0] : (void *)h.d_imex_tab[1]);
+    if (base) cudaFree(base);
+    h.d_rkc_tab = nullptr;
+    h.d_rkc_beta = nullptr;
+    h.d_imex_tab[0] = h.d_imex_tab[1] = h.d_imex_eo_tab[0] = h.d_imex_eo_tab[1] = nullptr;
+    h.table_bytes = 0;
+}
+
+extern "C" rd_status rd_tables_size(const rd_group *groups, int32_t n_groups, size_t *bytes) {
+    if (!bytes) return RD_ERR_INVALID_ARG;
+    rd_status st = validate_groups(groups, n_groups);
+    if (st) return st;
+    std::vector<GroupDev> gd(n_groups);
+    for (int32_t i = 0; i < n_groups; ++i) {
+        gd[i] = GroupDev{};
+        gd[i].model = groups[i].model;
+        gd[i].G = groups[i].G;
+        gd[i].flags = groups[i].flags;
+    }
+    *bytes = table_bytes(table_needs(gd.data(), n_groups));
+    return RD_OK;
+}
+
+extern "C" size_t rd_handle_table_bytes(const rd_handle *hh) { return hh ? hh->h.table_bytes : 0; }
+
+extern "C" rd_status rd_set_params(rd_handle *hh, int32_t group, const double *params, void *stream) {
+    if (!hh || !params) return RD_ERR_INVALID_ARG;
+    Handle &h = hh->h;
+    if (group < 0 || group >= h.n_groups) return RD_ERR_INVALID_ARG;
+    GroupDev &g = h.h_groups[group];
+    for (int k = 0; k < 6; ++k)
+        if (!std::isfinite(params[k])) return RD_ERR_INVALID_ARG;
+    if (g.model == RD_GM && !(params[3] != 0.0)) return RD_ERR_INVALID_ARG;
+    if (g.model == RD_BZ && !(params[2] != 0.0)) return RD_ERR_INVALID_ARG;
+    for (int k = 0; k < 6; ++k) g.p[k] = params[k];
+    cudaStream_t s = (cudaStream_t)stream;
+    // pageable source: the copy is staged before the call returns
+    RD_CUDA_TRY(cudaMemcpyAsync(h.d_groups + group, &g, sizeof(GroupDev), cudaMemcpyHostToDevice, s));
+    return batch_plan_set_group(h.batch, group, g, s);
+}
+
+extern "C" rd_status rd_set_seed(rd_handle *hh, int32_t group, uint64_t seed) {
+    if (!hh || group < 0 || group >= hh->h.n_groups) return RD_ERR_INVALID_ARG;
+    hh->h.h_groups[group].seed = seed;   // read on the host by every initial-state launch
     return RD_OK;
 }
 
@@ -208,7 +309,8 @@ extern "C" rd_status rd_integrate_rkc(rd_handle *hh, float *d_fields, const rd_r
         if (!rkc_supported(h.h_groups[gi])) return RD_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     for (int gi = 0; gi < h.n_groups; ++gi) {
-        rd_status st = launch_rkc_group(h.h_groups[gi], d_fields, o, d_stats, d_residual, h.d_status, s);
+        rd_status st = launch_rkc_group(h.h_groups[gi], h.d_rkc_tab, h.d_rkc_beta, d_fields, o, d_stats, d_residual,
+                                        h.d_status, s);
         if (st != RD_OK) return st;
     }
     return RD_OK;
@@ -221,7 +323,9 @@ extern "C" rd_status rd_integrate_imex(rd_handle *hh, float *d_fields, double *d
         if (!imex_supported(h.h_groups[gi])) return RD_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     for (int gi = 0; gi < h.n_groups; ++gi) {
-        rd_status st = launch_imex_group(h.h_groups[gi], d_fields, d_residual, h.d_status, s);
+        const int gi2 = h.h_groups[gi].G == 64;
+        rd_status st = launch_imex_group(h.h_groups[gi], h.d_imex_tab[gi2], h.d_imex_eo_tab[gi2], d_fields,
+                                         d_residual, h.d_status, s);
         if (st != RD_OK) return st;
     }
     return RD_OK;
@@ -260,6 +364,7 @@ extern "C" void rd_free(rd_handle *hh) {
     Handle &h = hh->h;
     adjoint_release(h);
     stream_release(h);
+    tables_release(h);
     batch_plan_free(h.batch);
     if (h.d_groups) cudaFree(h.d_groups);
     if (h.d_status) cudaFree(h.d_status);
@@ -283,6 +388,22 @@ extern "C" const char *rd_status_str(rd_status s) {
 }
 
 #include <atomic>
+#include <map>
+#include <mutex>
+rd_status rdcil::smem_attr_of(const void *kern, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> done;   // (kernel, device) -> bytes set
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RD_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find({kern, dev});
+    if (it != done.end() && it->second >= bytes) return RD_OK;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+        return RD_ERR_CUDA;
+    done[{kern, dev}] = bytes;
+    return RD_OK;
+}
+
 static std::atomic<uint64_t> g_launches{0};
 void rdcil::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 

@@ -436,11 +436,8 @@ rd_status launch_bootstrap_tc(const uint8_t *bins, int nf, int64_t n1, int64_t n
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return RD_ERR_CUDA;
-    static size_t set = 0;
-    if (smem > set) {
-        RD_CUDA_TRY(cudaFuncSetAttribute(bootstrap_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        set = smem;
-    }
+    // the size varies with the problem and the attribute is per device: set it per call
+    RD_CUDA_TRY(cudaFuncSetAttribute(bootstrap_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     bootstrap_tc_kernel<<<(unsigned)(units * S), BT_THREADS, smem, s>>>(
         tm, w, S, reinterpret_cast<unsigned long long *>(Y), MBAR_WAIT_LIMIT);
     note_launch();

@@ -1,10 +1,12 @@
 // Correlation integral of two pattern sets (eq. eCDF, eq. CIL, Sec. 2.1).
 //
 // Exactness contract.  For every pair the library decides K_ij =
-// #{k : d2_ij < R_k^2} for the canonical d2_ij = sum_t (x_t - y_t)^2
-// evaluated in FP64 in one fixed order (term t into partial t mod 256, each
-// partial in increasing t, partials combined by a halving tree within groups
-// of 32 and then across the 8 groups; no FMA).  It does so in three stages:
+// #{k : d2_ij < R_k^2} for d2_ij = the real number sum_t (x_t - y_t)^2 of
+// the FP32 inputs rounded once to the nearest double (the distance of
+// Sec. 2.1 is defined on the reals; this value depends on no evaluation
+// order).  Every bound below encloses the exact real sum S; since rounding
+// to nearest is monotone, an interval with representable ends that holds S
+// also holds d2 = fl64(S).  It does so in three stages:
 //   1. pack:  centre every pattern by c = the mean of up to 16 patterns
 //      sampled from each set (translation does not change distances; any c
 //      is valid, a central one keeps the bf16 split accurate), split x - c
@@ -16,20 +18,20 @@
 //      TwoSum into FP32 hi/lo pairs per K segment, segments combined the
 //      same way);
 //   3. tier 1: A = N_i + N_j - 2 P_ij approximates d2_ij with a rigorous
-//      error bound (FP32 accumulation model, dropped lo.lo term, E_i + E_j,
-//      rounding of the canonical sum), kept as an FP32 interval rounded
-//      outwards;
+//      error bound (FP32 accumulation model, dropped lo.lo term, E_i + E_j),
+//      kept as an FP32 interval rounded outwards;
 //   4. tier 2: pairs whose interval could hold the maximum (which defines R0)
 //      or contain a threshold get an FP32 error-free evaluation of the exact
 //      sum of squares (TwoSum / exact products, double-float accumulation)
 //      with a ~1e-12 relative bound;
 //   5. tier 3: the few pairs still undecided (in practice the maximum) are
-//      evaluated in the canonical FP64 order, one warp per group of 32
-//      partial sums so that the 8 groups of a pair run on different SMs.
+//      evaluated exactly (integer fixed-point accumulation, one rounding;
+//      exact.cuh), one CTA per pair.
 // Counts per radius are reduced with warp ballot + popc.
 #include <cstdio>
 #include <cuda_bf16.h>
 #include "common.cuh"
+#include "exact.cuh"
 
 namespace rdcil {
 
@@ -123,11 +125,9 @@ struct CilWork {
     float *Ppart;           // [S][hi, lo][n1][n2] compensated segment sums
     float *lo32, *hi32;     // [n1*n2] tier-1 interval of d2 (rounded outwards)
     double *lo2, *hi2;      // [n1*n2] tier-2 interval (valid where flag >= 1)
-    double *ex;             // [n1*n2] canonical d2 (valid where flag == 2)
-    uint8_t *flag;          // [n1*n2] 0: tier 1 decides, 1: tier 2, 2: canonical
+    double *ex;             // [n1*n2] exact d2 (valid where flag == 2)
+    uint8_t *flag;          // [n1*n2] 0: tier 1 decides, 1: tier 2, 2: exact
     unsigned long long *q1, *q2;  // [n1*n2] tier-2 / tier-3 queues (bit 63: may hold the maximum)
-    double *grp;            // [n1*n2][8] canonical group sums by tier-3 slot
-    unsigned int *arrive;   // [n1*n2] groups finished, by tier-3 slot
     float *t1lo, *t1hi;     // [32] tier-1 threshold ranges (FP32, outward)
     double *t2lo, *t2hi;    // [32] tier-2 threshold ranges
     unsigned long long *scal;  // see SC_* below
@@ -182,8 +182,6 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     w.flag = (uint8_t *)take(sizeof(uint8_t) * np);
     w.q1 = (unsigned long long *)take(sizeof(unsigned long long) * np);
     w.q2 = (unsigned long long *)take(sizeof(unsigned long long) * np);
-    w.grp = (double *)take(sizeof(double) * 8 * np);
-    w.arrive = (unsigned int *)take(sizeof(unsigned int) * np);
     w.t1lo = (float *)take(sizeof(float) * 32);
     w.t1hi = (float *)take(sizeof(float) * 32);
     w.t2lo = (double *)take(sizeof(double) * 32);
@@ -191,42 +189,6 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     w.scal = (unsigned long long *)take(sizeof(unsigned long long) * 16);
     w.bytes = off;
     return w;
-}
-
-// ---------------------------------------------------------------------------
-// canonical distance: sequential FP64, no FMA
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double sq_diff(float a, float b) {
-    double df = __dsub_rn((double)a, (double)b);
-    return __dmul_rn(df, df);
-}
-
-// Canonical d2 of one pair by a whole 256-thread block, in the fixed order
-// above.  FP64 has a long dependent-operation latency on this GPU, so the
-// order is chosen for a short dependency chain: d/256 + 8 additions.
-// Result valid in thread 0; sw = 8 doubles of shared memory.
-__device__ double canonical_block(const float *__restrict__ x, const float *__restrict__ y, int64_t d,
-                                  double *sw) {
-    const int j = threadIdx.x, lane = j & 31, warp = j >> 5;
-    double acc = 0.0;
-    for (int64_t t = j; t < d; t += 256) acc = __dadd_rn(acc, sq_diff(__ldg(x + t), __ldg(y + t)));
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(0xffffffffu, acc, s));
-    if (lane == 0) sw[warp] = acc;
-    __syncthreads();
-    double r = 0.0;
-    if (j == 0) {
-        double w[8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) w[g] = sw[g];
-#pragma unroll
-        for (int s = 4; s >= 1; s >>= 1)
-#pragma unroll
-            for (int i = 0; i < s; ++i) w[i] = __dadd_rn(w[i], w[i + s]);
-        r = w[0];
-    }
-    __syncthreads();
-    return r;
 }
 
 // FP32 error-free sum accumulation (Knuth TwoSum): (hi, lo) holds a value
@@ -406,9 +368,7 @@ __global__ void d2_bound_kernel(CilWork w, float gam) {
         const float up = __fadd_ru(__double2float_ru(A), eg);
         const float D = __fadd_ru(w.Ef[a], w.Ef[bb]);
         const float er = __fmul_ru(D, __fadd_ru(__fmul_ru(2.f, __fsqrt_ru(fmaxf(up, 0.f))), D));
-        // canonical order vs the exact value: (d/256 + 10) 2^-52 relative
-        const float ec = __fmul_ru((float)(w.d / 256 + 10) * 2.3e-16f, __fadd_ru(fmaxf(up, 0.f), er));
-        float m = __fmul_ru(2.f, __fadd_ru(__fadd_ru(eg, er), ec));
+        float m = __fmul_ru(2.f, __fadd_ru(eg, er));
         m = __fadd_ru(m, __fmul_ru(1.2e-7f, Af)) + 1e-30f;   // FP32 rounding of A
         const float lo = __fsub_rd(__double2float_rd(A), m);
         const float hi = __fadd_ru(__double2float_ru(A), m);
@@ -522,7 +482,6 @@ __global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in,
     if (all) {   // exact path: every pair to tier 3; all may hold the maximum (and minimum)
         unsigned long long slot = atomicAdd(&w.scal[SC_Q2], 1ull);
         w.q2[slot] = (unsigned long long)q | (radii_in ? 0ull : Q_MAX) | (lin ? Q_MIN : 0ull);
-        w.arrive[slot] = 0u;
         return;
     }
     const float lo = w.lo32[q], hi = w.hi32[q];
@@ -543,8 +502,7 @@ __global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in,
 //     |L| <= (n + 3) 2^-24 S for n terms per thread and S = sum p, so its
 //     2n roundings cost at most 2 n (n + 4) 2^-48 S.  The 256
 //     thread pairs are combined in FP64 (error <= 300 2^-53).  The interval
-//     finally includes the distance of the canonical FP64 order from the
-//     exact value, (d/256 + 10) 2^-52 relative.
+//     holds the exact sum, hence (monotone rounding) its rounded value.
 __global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
                                                     const float *__restrict__ X2, int64_t ld2) {
     __shared__ double red[2][8];
@@ -576,8 +534,7 @@ __global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__re
             double D2 = 0.0;
             for (int g = 0; g < 8; ++g) D2 += red[0][g];
             const double n = (double)((w.d + 255) / 256);
-            const double rel = 2.0 * (2.9e-14 + 2.0 * n * (n + 4.0) * 3.56e-15 + 300.0 * 1.12e-16 +
-                                      (double)(w.d / 256 + 10) * 2.23e-16);
+            const double rel = 2.0 * (2.9e-14 + 2.0 * n * (n + 4.0) * 3.56e-15 + 300.0 * 1.12e-16);
             const double err = rel * fabs(D2) + 1e-300;
             const double lo = D2 - err, hi = D2 + err;
             w.lo2[q] = lo;
@@ -618,61 +575,38 @@ __global__ void classify2_kernel(CilWork w, int M) {
     if (!(maxc || minc || amb)) return;
     unsigned long long slot = atomicAdd(&w.scal[SC_Q2], 1ull);
     w.q2[slot] = (unsigned long long)q | (maxc ? Q_MAX : 0ull) | (minc ? Q_MIN : 0ull);
-    w.arrive[slot] = 0u;
 }
 
-// 5. tier 3: the canonical FP64 order.  One warp per (pair, group of 32
-//    partials): lane l of group g sums t = 32 g + l (mod 256) in increasing
-//    t, the warp combines its 32 partials by the halving tree; the last of
-//    the 8 warps of a pair to finish combines the 8 group sums by the same
-//    tree.  Spreading the 8 groups over SMs multiplies the FP64 pipes a pair
-//    can use.
-__global__ void __launch_bounds__(32) canonical_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
-                                                       const float *__restrict__ X2, int64_t ld2) {
+// 5. tier 3: the exact value (exact.cuh) of every queued pair, one CTA per
+//    pair (grid-stride over the queue).
+__global__ void __launch_bounds__(256) exact_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
+                                                    const float *__restrict__ X2, int64_t ld2) {
+    __shared__ XdShared<256> sh;
     const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[SC_Q2];
-    const int lane = threadIdx.x;
-    for (unsigned long long it = blockIdx.x; it < qlen * 8ull; it += gridDim.x) {
-        const unsigned long long slot = it >> 3;
-        const int g = (int)(it & 7ull);
+    for (unsigned long long slot = blockIdx.x; slot < qlen; slot += gridDim.x) {
         const unsigned long long ent = w.q2[slot];
         const int64_t q = (int64_t)(ent & Q_IDX);
         const int64_t i = q / w.n2, j = q - i * w.n2;
-        const float *x = X1 + i * ld1, *y = X2 + j * ld2;
-        // increasing t; the loads run eight elements ahead of the sum
-        double acc = 0.0;
-        int64_t t = 32 * g + lane;
-        for (; t + 7 * 256 < w.d; t += 8 * 256) {
-            float xa[8], ya[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                xa[u] = __ldg(x + t + 256 * u);
-                ya[u] = __ldg(y + t + 256 * u);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc = __dadd_rn(acc, sq_diff(xa[u], ya[u]));
+        const double v = xd_block<256, false>(X1 + i * ld1, X2 + j * ld2, w.d, sh, nullptr);
+        if (threadIdx.x == 0) {
+            w.ex[q] = v;
+            w.flag[q] = 2;
+            if (ent & Q_MAX) atomicMax(&w.scal[SC_MAX], (unsigned long long)__double_as_longlong(v));
+            if (ent & Q_MIN) atomic_min_d(&w.scal[SC_MIN], v);
         }
-        for (; t < w.d; t += 256) acc = __dadd_rn(acc, sq_diff(__ldg(x + t), __ldg(y + t)));
-#pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(0xffffffffu, acc, s));
-        if (lane == 0) {
-            w.grp[slot * 8 + g] = acc;
-            __threadfence();
-            const unsigned prev = atomicAdd(&w.arrive[slot], 1u);
-            if (prev == 7u) {
-                __threadfence();
-                double v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = *(volatile double *)&w.grp[slot * 8 + k];
-#pragma unroll
-                for (int s = 4; s >= 1; s >>= 1)
-#pragma unroll
-                    for (int k = 0; k < s; ++k) v[k] = __dadd_rn(v[k], v[k + s]);
-                w.ex[q] = v[0];
-                w.flag[q] = 2;
-                if (ent & Q_MAX) atomicMax(&w.scal[SC_MAX], (unsigned long long)__double_as_longlong(v[0]));
-                if (ent & Q_MIN) atomic_min_d(&w.scal[SC_MIN], v[0]);
-            }
-        }
+    }
+}
+
+// checking entry point: the exact d2 of listed pairs, one CTA per pair
+__global__ void __launch_bounds__(256) exact_pairs_kernel(const float *__restrict__ X1, int64_t ld1,
+                                                          const float *__restrict__ X2, int64_t ld2, int64_t d,
+                                                          const int64_t *__restrict__ pairs, int64_t n,
+                                                          double *__restrict__ out) {
+    __shared__ XdShared<256> sh;
+    for (int64_t e = blockIdx.x; e < n; e += gridDim.x) {
+        const int64_t i = pairs[2 * e], j = pairs[2 * e + 1];
+        const double v = xd_block<256, false>(X1 + i * ld1, X2 + j * ld2, d, sh, nullptr);
+        if (threadIdx.x == 0) out[e] = v;
     }
 }
 
@@ -760,7 +694,7 @@ __global__ void bins_counts_kernel(CilWork w, const double *__restrict__ radii_o
 __global__ void finish_kernel(CilWork w, int64_t *n_rechecked, const int64_t *counts, int M, double *Cv) {
     if (blockIdx.x != 0) return;
     // -2: a Gram wait timed out; -1: a pair was left undecided; else the
-    // number of pairs evaluated in the canonical FP64 order
+    // number of pairs evaluated exactly
     if (threadIdx.x == 0 && n_rechecked)
         *n_rechecked = w.scal[SC_TIMEOUT] ? -2 : (w.scal[SC_UNDECIDED] ? -1 : (int64_t)w.scal[SC_Q2]);
     if (Cv && (int)threadIdx.x < M)
@@ -781,7 +715,7 @@ __global__ void export_approx_kernel(CilWork w, double *__restrict__ A, double *
 // ---------------------------------------------------------------------------
 static rd_status check_args(int64_t ld1, int64_t n1, int64_t ld2, int64_t n2, int64_t d,
                             const double *radii_in, double b, int M, int law = LAW_POWER) {
-    if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535 || d < 1) return RD_ERR_INVALID_ARG;
+    if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535 || d < 1 || d > XD_MAX_D) return RD_ERR_INVALID_ARG;
     if (ld1 < d || ld2 < d) return RD_ERR_INVALID_ARG;
     if (M < 1 || M > 32) return RD_ERR_INVALID_ARG;
     if (!radii_in && law == LAW_POWER && !(b > 1.0)) return RD_ERR_INVALID_ARG;
@@ -831,13 +765,14 @@ static rd_status tier1(const CilWork &w, const float *X1, int64_t ld1, const flo
 }
 
 // Internal entry for the multi-feature correlation integral: tier-1
-// intervals [lo, hi] (FP32, outward) of the canonical squared distance of
+// intervals [lo, hi] (FP32, outward) of the exact squared distance of
 // every pair of two pattern arrays, left in the workspace; *timeout points
 // at the word the tensor-core stage raises on a timeout.
 rd_status cil_tier1_intervals(const float *X1, int64_t ld1, int64_t n1, const float *X2, int64_t ld2, int64_t n2,
                               int64_t d, void *work, size_t work_bytes, const float **lo, const float **hi,
                               const unsigned long long **timeout, cudaStream_t s) {
-    if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535 || d < 1 || ld1 < d || ld2 < d) return RD_ERR_INVALID_ARG;
+    if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535 || d < 1 || d > XD_MAX_D || ld1 < d || ld2 < d)
+        return RD_ERR_INVALID_ARG;
     if (!X1 || !X2 || !work || (((uintptr_t)work & 255) != 0)) return RD_ERR_INVALID_ARG;
     CilWork w = layout(n1, n2, d, work);
     if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
@@ -893,9 +828,8 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
         note_launch();
     }
     {
-        const int64_t items = 8 * np;
-        const unsigned g3 = (unsigned)(items < 16 * 148 ? items : 16 * 148);
-        canonical_kernel<<<g3, 32, 0, s>>>(w, X1, ld1, X2, ld2);
+        const unsigned g3 = (unsigned)(np < 2 * N_SM ? np : 2 * N_SM);
+        exact_kernel<<<g3, 256, 0, s>>>(w, X1, ld1, X2, ld2);
         note_launch();
     }
     radii_kernel<<<1, 32, 0, s>>>(w, radii_in, b, M, law, radii_out);
@@ -909,7 +843,7 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
 
 // Checking entry point: the tier-1 approximation of every pair as midpoint A
 // and half-width m of its interval (pack + tensor-core Gram + bound, before
-// any exact evaluation).  |A - canonical d2| <= m must hold for every pair.
+// any exact evaluation).  |A - d2| <= m must hold for every pair.
 extern "C" rd_status cil_debug_approx(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,
                                       int64_t n2, int64_t d, double *d_A, double *d_m, void *d_work,
                                       size_t work_bytes, void *stream) {
@@ -964,6 +898,17 @@ extern "C" rd_status cil_features_fitted(const float *d_X1, int64_t ld1, int64_t
                                          void *d_work, size_t work_bytes, void *stream) {
     return cil_run(d_X1, ld1, n1, d_X2, ld2, n2, d, nullptr, 0.0, M, d_radii_out, d_bins, d_counts, d_C,
                    d_n_rechecked, d_work, work_bytes, stream, false, LAW_FITTED);
+}
+
+extern "C" rd_status cil_exact_d2(const float *d_X1, int64_t ld1, const float *d_X2, int64_t ld2, int64_t d,
+                                  const int64_t *d_pairs, int64_t n_pairs, double *d_out, void *stream) {
+    if (d < 1 || d > XD_MAX_D || ld1 < d || ld2 < d || n_pairs < 0) return RD_ERR_INVALID_ARG;
+    if (n_pairs == 0) return RD_OK;
+    if (!d_X1 || !d_X2 || !d_pairs || !d_out) return RD_ERR_INVALID_ARG;
+    const unsigned g = (unsigned)(n_pairs < 4 * N_SM ? n_pairs : 4 * N_SM);
+    exact_pairs_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(d_X1, ld1, d_X2, ld2, d, d_pairs, n_pairs, d_out);
+    note_launch();
+    return cuda_status(cudaGetLastError());
 }
 
 extern "C" rd_status cil_features_exact(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,

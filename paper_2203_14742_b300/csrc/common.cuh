@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of librdcil.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 #include <cuda_runtime.h>
@@ -55,7 +56,27 @@ struct Handle {
     float *d_stream_tmp;      // the other HBM buffer of the ping-pong
     double *d_stream_part;    // residual partial sums
     int32_t stream_depth;     // Euler steps fused per launch (1, 2, 4 or 8)
+    // step tables, formed in rd_init on the handle's device (null when no
+    // group can use them): the stabilised RK2 coefficients and stability
+    // bounds, and the cosine-basis tables of the semi-implicit stepper per
+    // G = 32, 64 (full products, even/odd split)
+    float4 *d_rkc_tab;
+    double *d_rkc_beta;
+    float *d_imex_tab[2];
+    float *d_imex_eo_tab[2];
+    size_t table_bytes;
 };
+
+// Step tables a handle holds for its groups (rd_init allocates and fills
+// them; tables_release frees them).
+struct TableNeeds {
+    bool rkc;          // some group can run the stabilised RK2
+    bool imex[2];      // some group can run the semi-implicit stepper at G = 32 / 64
+};
+TableNeeds table_needs(const GroupDev *groups, int n_groups);
+size_t table_bytes(const TableNeeds &n);
+rd_status tables_create(Handle &h, cudaStream_t s);
+void tables_release(Handle &h);
 
 inline rd_status cuda_status(cudaError_t e) {
     return e == cudaSuccess ? RD_OK : RD_ERR_CUDA;
@@ -70,6 +91,15 @@ inline rd_status cuda_status(cudaError_t e) {
 // Count of kernels this library has launched (its own kernels only).
 void note_launch();
 
+// Raise kernel `kern`'s dynamic shared-memory limit to `bytes` on the
+// current device.  The attribute belongs to a (kernel, device) pair, so it
+// is set the first time each pair needs it (api.cu keeps the record).
+rd_status smem_attr_of(const void *kern, int bytes);
+template <class K>
+rd_status smem_attr(K kern, int bytes) {
+    return smem_attr_of(reinterpret_cast<const void *>(kern), bytes);
+}
+
 // ---- launchers implemented in the kernel translation units --------------
 rd_status launch_init_fields(const GroupDev &g, float *fields, cudaStream_t s);
 rd_status launch_integrate_group(const GroupDev &g, float *fields, int64_t steps,
@@ -83,6 +113,7 @@ rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int
 rd_status launch_integrate_variant(const GroupDev &g, float *fields, int64_t steps, double *residual,
                                    uint32_t *status, cudaStream_t s, int vi);
 rd_status batch_plan_create(const GroupDev *groups, int n_groups, void **out);
+rd_status batch_plan_set_group(void *plan, int i, const GroupDev &g, cudaStream_t s);
 void batch_plan_free(void *plan);
 rd_status launch_batch(void *plan, float *fields, int64_t steps_override, double *residual, uint32_t *status,
                        cudaStream_t s);
@@ -98,18 +129,31 @@ void set_gram_spin_limit(uint32_t n);
 bool variant_shape(int G, int vi, int *packed, int *TY, int *TX);
 bool rkc_supported(const GroupDev &g);
 bool rkc1d_supported(const GroupDev &g);
-rd_status launch_rkc1d_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats,
+rd_status launch_rkc1d_group(const GroupDev &g, const float4 *tab, const double *beta, float *fields,
+                             const rd_rkc_opts &o, int64_t *stats,
                              double *residual, uint32_t *status, cudaStream_t s);
 rd_status launch_rdode_init(const GroupDev &g, float *fields, cudaStream_t s);
 int rkc_n_variants();
 bool rkc_set_variant(int G, int v);
 int rkc_get_variant(int G);
-rd_status launch_rkc_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats, double *residual,
+rd_status launch_rkc_group(const GroupDev &g, const float4 *tab, const double *beta, float *fields,
+                           const rd_rkc_opts &o, int64_t *stats, double *residual,
                            uint32_t *status, cudaStream_t s);
 bool imex_supported(const GroupDev &g);
 int imex_n_variants();
 bool imex_set_variant(int G, int v);
 int imex_get_variant(int G);
-rd_status launch_imex_group(const GroupDev &g, float *fields, double *residual, uint32_t *status, cudaStream_t s);
+rd_status launch_imex_group(const GroupDev &g, const float *tab, const float *eo_tab, float *fields, double *residual,
+                            uint32_t *status, cudaStream_t s);
+rd_status rkc_tables_fill(float4 *tab, double *beta, cudaStream_t s);
+size_t rkc_table_bytes();
+rd_status imex_tables_fill(int G, float *tab, float *eo_tab, cudaStream_t s);
+size_t imex_table_floats(int G);
+size_t imex_eo_table_floats(int G);
 
 }  // namespace rdcil
+
+// the opaque handle of the C ABI
+struct rd_handle {
+    rdcil::Handle h;
+};

@@ -278,10 +278,9 @@ rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2,
     if (nti * ntj * S > 0x7FFFFFFF) return RD_ERR_UNSUPPORTED;
     CUtensorMap mh, ml;
     if (!make_map(&mh, hi, n1 + n2, dp) || !make_map(&ml, lo, n1 + n2, dp)) return RD_ERR_CUDA;
-    static bool attr = false;
-    if (!attr) {
-        RD_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-        attr = true;
+    {
+        rd_status ast = smem_attr(gram_tc_kernel, TC_SMEM);
+        if (ast) return ast;
     }
     gram_tc_kernel<<<(unsigned)(nti * ntj * S), 192, TC_SMEM, s>>>(mh, ml, (int)n1, (int)n2, (int)dp, (int)ntj,
                                                                    (int)S, (int)cs, Ppart, status, g_spin_limit);

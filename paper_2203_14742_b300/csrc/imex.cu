@@ -275,25 +275,8 @@ rd_imex_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, float
     residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, sC);
 }
 
-static float *g_imex_tab[2] = {nullptr, nullptr};   // G = 32, 64
-static std::once_flag g_imex_once[2];
-static rd_status g_imex_status[2] = {RD_OK, RD_OK};
-
-static rd_status imex_table(int G, cudaStream_t s, const float **tab) {
-    const int gi = G == 64;
-    std::call_once(g_imex_once[gi], [G, gi, s]() {
-        if (cudaMalloc(&g_imex_tab[gi], sizeof(float) * (2 * (size_t)G * G + G)) != cudaSuccess) {
-            g_imex_status[gi] = RD_ERR_OOM;
-            return;
-        }
-        imex_table_kernel<<<(G * G + 127) / 128, 128, 0, s>>>(G, g_imex_tab[gi]);
-        note_launch();
-        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
-            g_imex_status[gi] = RD_ERR_CUDA;
-    });
-    *tab = g_imex_tab[gi];
-    return g_imex_status[gi];
-}
+// floats of the full-product table (C, C^T, divisor eigenvalues) at G
+size_t imex_table_floats(int G) { return 2 * (size_t)G * G + G; }
 
 // ---------------------------------------------------------------------------
 // Even/odd split.  C[p][G-1-x] = (-1)^p C[p][x], so with the spectrum held in
@@ -590,32 +573,21 @@ bool imex_set_variant(int G, int v) {
 }
 int imex_get_variant(int G) { return (G == 32 || G == 64) ? g_imex_var[G == 64] : -1; }
 
-static float *g_imex_eo_tab[2] = {nullptr, nullptr};   // G = 32, 64
-static std::once_flag g_imex_eo_once[2];
-static rd_status g_imex_eo_status[2] = {RD_OK, RD_OK};
+// floats of the even/odd table at G
+size_t imex_eo_table_floats(int G) { return (size_t)G * G + G; }
 
-static rd_status imex_eo_table(int G, cudaStream_t s, const float **tab) {
-    const int gi = G == 64;
-    std::call_once(g_imex_eo_once[gi], [G, gi, s]() {
-        if (cudaMalloc(&g_imex_eo_tab[gi], sizeof(float) * ((size_t)G * G + G)) != cudaSuccess) {
-            g_imex_eo_status[gi] = RD_ERR_OOM;
-            return;
-        }
-        imex_eo_table_kernel<<<(G * G / 2 + 127) / 128, 128, 0, s>>>(G, g_imex_eo_tab[gi]);
-        note_launch();
-        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
-            g_imex_eo_status[gi] = RD_ERR_CUDA;
-    });
-    *tab = g_imex_eo_tab[gi];
-    return g_imex_eo_status[gi];
+// both tables of grid side G, into memory the handle owns (rd_init)
+rd_status imex_tables_fill(int G, float *tab, float *eo_tab, cudaStream_t s) {
+    imex_table_kernel<<<(G * G + 127) / 128, 128, 0, s>>>(G, tab);
+    note_launch();
+    imex_eo_table_kernel<<<(G * G / 2 + 127) / 128, 128, 0, s>>>(G, eo_tab);
+    note_launch();
+    return cuda_status(cudaGetLastError());
 }
 
 template <int MODEL, int G>
-static rd_status launch_imex_eo(const GroupDev &g, float *fields, double *residual, uint32_t *status,
-                                cudaStream_t s) {
-    const float *tab = nullptr;
-    rd_status st = imex_eo_table(G, s, &tab);
-    if (st != RD_OK) return st;
+static rd_status launch_imex_eo(const GroupDev &g, const float *tab, float *fields, double *residual,
+                                uint32_t *status, cudaStream_t s) {
     constexpr size_t smem = imex_eo_smem<G>();
     auto kern = rd_imex_eo_kernel<MODEL, G>;
     RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -644,25 +616,25 @@ static rd_status launch_imex_mgt(const GroupDev &g, float *fields, const float *
 }
 
 template <int MODEL, int G>
-static rd_status launch_imex_mg(const GroupDev &g, float *fields, const float *tab, double *residual,
-                                uint32_t *status, cudaStream_t s) {
+static rd_status launch_imex_mg(const GroupDev &g, float *fields, const float *tab, const float *eo_tab,
+                                double *residual, uint32_t *status, cudaStream_t s) {
     switch (g_imex_var[G == 64]) {
         case 1: return launch_imex_mgt<MODEL, G, 8, 4>(g, fields, tab, residual, status, s);
         case 2: return launch_imex_mgt<MODEL, G, 4, 8>(g, fields, tab, residual, status, s);
         case 3: return launch_imex_mgt<MODEL, G, 8, 8>(g, fields, tab, residual, status, s);
-        case 4: return launch_imex_eo<MODEL, G>(g, fields, residual, status, s);
+        case 4: return launch_imex_eo<MODEL, G>(g, eo_tab, fields, residual, status, s);
         default: return launch_imex_mgt<MODEL, G, 4, 4>(g, fields, tab, residual, status, s);
     }
 }
 
 template <int G>
-static rd_status launch_imex_g(const GroupDev &g, float *fields, const float *tab, double *residual,
-                               uint32_t *status, cudaStream_t s) {
+static rd_status launch_imex_g(const GroupDev &g, float *fields, const float *tab, const float *eo_tab,
+                               double *residual, uint32_t *status, cudaStream_t s) {
     switch (g.model) {
-        case RD_FHN: return launch_imex_mg<RD_FHN, G>(g, fields, tab, residual, status, s);
-        case RD_GM: return launch_imex_mg<RD_GM, G>(g, fields, tab, residual, status, s);
-        case RD_DIFF: return launch_imex_mg<RD_DIFF, G>(g, fields, tab, residual, status, s);
-        case RD_BZ: return launch_imex_mg<RD_BZ, G>(g, fields, tab, residual, status, s);
+        case RD_FHN: return launch_imex_mg<RD_FHN, G>(g, fields, tab, eo_tab, residual, status, s);
+        case RD_GM: return launch_imex_mg<RD_GM, G>(g, fields, tab, eo_tab, residual, status, s);
+        case RD_DIFF: return launch_imex_mg<RD_DIFF, G>(g, fields, tab, eo_tab, residual, status, s);
+        case RD_BZ: return launch_imex_mg<RD_BZ, G>(g, fields, tab, eo_tab, residual, status, s);
         default: return RD_ERR_UNSUPPORTED;
     }
 }
@@ -671,14 +643,12 @@ bool imex_supported(const GroupDev &g) {
     return g.model != RD_RDODE && (g.G == 32 || g.G == 64);
 }
 
-rd_status launch_imex_group(const GroupDev &g, float *fields, double *residual, uint32_t *status, cudaStream_t s) {
-    if (!imex_supported(g)) return RD_ERR_UNSUPPORTED;
-    const float *tab = nullptr;
-    rd_status st = imex_table(g.G, s, &tab);
-    if (st != RD_OK) return st;
+rd_status launch_imex_group(const GroupDev &g, const float *tab, const float *eo_tab, float *fields, double *residual,
+                            uint32_t *status, cudaStream_t s) {
+    if (!imex_supported(g) || !tab || !eo_tab) return RD_ERR_UNSUPPORTED;
     if (g.n_steps == 0 && !residual) return RD_OK;
-    return g.G == 32 ? launch_imex_g<32>(g, fields, tab, residual, status, s)
-                     : launch_imex_g<64>(g, fields, tab, residual, status, s);
+    return g.G == 32 ? launch_imex_g<32>(g, fields, tab, eo_tab, residual, status, s)
+                     : launch_imex_g<64>(g, fields, tab, eo_tab, residual, status, s);
 }
 
 }  // namespace rdcil

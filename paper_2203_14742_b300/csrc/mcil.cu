@@ -8,8 +8,9 @@
 // y differences: qy = my = 0); h = 1/(Gx-1), g = Gx-1.  The derivative
 // patterns are forward differences of each field rounded to FP32 once
 // (Dx: Gy x (Gx-1), Dy: (Gy-1) x Gx per species).  With q0, qx, qy the
-// canonical squared distances (the fixed FP64 order of the CIL: partial
-// t mod 256, halving trees) of the patterns and of their Dx and Dy patterns,
+// squared distances of the CIL (the exact real sum of squared differences,
+// rounded once to the nearest double) of the patterns and of their Dx and
+// Dy patterns,
 // and m0, mx, my the maxima of |difference| with each difference in FP64
 // (rounded to nearest, like the squared distance's), the features are
 //   0 L2      squared  q0                                  (eq. norm:L2)
@@ -35,13 +36,15 @@
 //      outward-rounded (_rd / _ru) evaluation of its expression (every
 //      operation is monotone on the non-negative inputs);
 //   4. pairs whose interval may hold a feature's maximum (linear law: or
-//      its minimum) are evaluated exactly (the canonical FP64 order, one
-//      CTA per pair), which fixes R0 (and R_min) and the radii; pairs whose interval meets a threshold get tier 2
-//      (FP32 error-free squared distances with a ~1e-12 bound, exact
-//      maxima) and, if still undecided, the canonical evaluation; every
+//      its minimum) are evaluated exactly (integer fixed-point sums rounded
+//      once, exact.cuh; one CTA per pair and pattern array), which fixes R0
+//      (and R_min) and the radii; pairs whose interval meets a threshold
+//      get tier 2 (FP32 error-free squared distances with a ~1e-12 bound,
+//      exact maxima) and, if still undecided, the exact evaluation; every
 //      other pair is decided by its interval.
 #include <cuda_runtime.h>
 #include "common.cuh"
+#include "exact.cuh"
 #include "tma.cuh"
 
 rd_status cil_tier1_intervals(const float *X1, int64_t ld1, int64_t n1, const float *X2, int64_t ld2, int64_t n2,
@@ -53,12 +56,13 @@ namespace rdcil {
 
 static constexpr int NF = 6;
 static constexpr int MC_SCAL = 32;   // control words of one call (see McilWork::scal)
-static constexpr int EX_CAP = 4096;  // queued pairs the split canonical evaluation takes per launch
+static constexpr int EX_CAP = 4096;  // queued pairs the split exact evaluation takes per launch
 __host__ __device__ constexpr bool feat_squared(int f) { return f == 0 || f == 2; }
 
 struct McilWork {
     int64_t n1, n2, np, d0, dex, dey;
-    int Gy, Gx, nsp, mask, M, law;   // law 0 power, 1 linear, 2 fitted power (1 and 2 need the minima)
+    int Gy, Gx, nsp, mask, M, law;   // law 0 power, 1 linear, 2 fitted power (1 and 2 need the minima),
+                                     // 3 given radii (no maxima or minima needed)
     float *S1, *S2;                 // min-max scaled patterns (scale only)
     float *Ax1, *Ay1, *Ax2, *Ay2;   // forward-difference patterns
     void *cw[3];                    // CIL workspaces for the pattern, Dx, Dy arrays
@@ -70,12 +74,12 @@ struct McilWork {
     int64_t *queue;                 // [np] pairs to evaluate exactly
     unsigned long long *scal;       // [0] queue length; [1] end of the maximum-candidate phase; [2 + f]
                                     // largest lower bound of feature f (bits); [8] start of the final
-                                    // canonical segment; [9] number of maximum candidates; [10] pairs
-                                    // evaluated in the canonical order; [16 + f] smallest upper
+                                    // exact segment; [9] number of maximum candidates; [10] pairs
+                                    // evaluated exactly; [16 + f] smallest upper
                                     // bound of feature f (complemented bits, linear law)
     double *thr;                    // [NF][32] thresholds of the decision (R_k^2 or R_k)
-    double *grp;                    // [EX_CAP][3][8][2] group sums and maxima of the canonical order
-    unsigned int *arrive;           // [EX_CAP] groups finished per queued pair
+    double *grp;                    // [EX_CAP][3][2] exact squared distance and maximum per array
+    unsigned int *arrive;           // [EX_CAP] arrays finished per queued pair
     size_t bytes;
 };
 
@@ -129,7 +133,7 @@ static McilWork mlayout(int64_t n1, int64_t n2, int Gy, int Gx, int nsp, int mas
     w.queue = (int64_t *)take(sizeof(int64_t) * w.np);
     w.scal = (unsigned long long *)take(sizeof(unsigned long long) * MC_SCAL);
     w.thr = (double *)take(sizeof(double) * NF * 32);
-    w.grp = (double *)take(sizeof(double) * EX_CAP * 48);
+    w.grp = (double *)take(sizeof(double) * EX_CAP * 6);
     w.arrive = (unsigned int *)take(sizeof(unsigned int) * EX_CAP);
     w.bytes = off;
     return w;
@@ -465,41 +469,7 @@ struct Arr3 {
     int64_t ld1[3], ld2[3], d[3];
 };
 
-// canonical squared distance (thread p = partial p) and max |x - y| of the
-// FP64 differences
-__device__ void exact_q_m(const float *x, const float *y, int64_t d, double *sred, double &q, double &m) {
-    double acc = 0.0, mx = 0.0;
-    for (int64_t t = threadIdx.x; t < d; t += 256) {
-        const double df = __dsub_rn((double)x[t], (double)y[t]);
-        acc = __dadd_rn(acc, __dmul_rn(df, df));
-        mx = fmax(mx, fabs(df));
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const double o = __shfl_down_sync(0xffffffffu, acc, s);
-        if (lane < s) acc = __dadd_rn(acc, o);
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s));
-    }
-    __syncthreads();
-    if (lane == 0) { sred[warp] = acc; sred[8 + warp] = mx; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double wv[8];
-        for (int gi = 0; gi < 8; ++gi) wv[gi] = sred[gi];
-        for (int s = 4; s >= 1; s >>= 1)
-            for (int i = 0; i < s; ++i) wv[i] = __dadd_rn(wv[i], wv[i + s]);
-        double mm = 0.0;
-        for (int gi = 0; gi < 8; ++gi) mm = fmax(mm, sred[8 + gi]);
-        sred[16] = wv[0];
-        sred[17] = mm;
-    }
-    __syncthreads();
-    q = sred[16];
-    m = sred[17];
-}
-
-// the six features of pair q from its canonical squared distances qv and
+// the six features of pair q from its exact squared distances qv and
 // maxima mv of the three arrays, each one FP64 expression rounded to nearest
 __device__ void exact_store(McilWork &w, int64_t q, const double (&qv)[3], const double (&mv)[3], double h,
                             double h2, double g) {
@@ -522,102 +492,64 @@ __device__ void exact_store(McilWork &w, int64_t q, const double (&qv)[3], const
 }
 
 // queued pairs from scal[start_slot] (0: from the start) to the end, one
-// CTA per pair (queues longer than EX_CAP; exact_grp_kernel takes the rest)
+// CTA per pair taking its arrays in turn (queues longer than EX_CAP;
+// exact_split_kernel takes the rest)
 __global__ void __launch_bounds__(256) exact_kernel(McilWork w, Arr3 A, double h, double h2, double g,
                                                     int start_slot) {
-    __shared__ double sred[18];
+    __shared__ XdShared<256> sh;
     const unsigned long long nq = w.scal[0];
     const unsigned long long first = start_slot == 0 ? 0ull : w.scal[start_slot];
     if (nq <= first + (unsigned long long)EX_CAP) return;
+    const int na = (w.mask & 0x3C) != 0 ? 3 : 1;
     for (unsigned long long e = first + blockIdx.x; e < nq; e += gridDim.x) {
         const int64_t q = w.queue[e];
         const int64_t i = q / w.n2, j = q - i * w.n2;
         double qv[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
-        const bool need[3] = {true, (w.mask & 0x3C) != 0, (w.mask & 0x3C) != 0};
-        for (int a = 0; a < 3; ++a)
-            if (need[a]) exact_q_m(A.a1[a] + i * A.ld1[a], A.a2[a] + j * A.ld2[a], A.d[a], sred, qv[a], mv[a]);
+        for (int a = 0; a < na; ++a) {
+            double m = 0.0;
+            const double v = xd_block<256, true>(A.a1[a] + i * A.ld1[a], A.a2[a] + j * A.ld2[a], A.d[a], sh, &m);
+            qv[a] = v;
+            mv[a] = m;
+        }
         if (threadIdx.x == 0) exact_store(w, q, qv, mv, h, h2, g);
         __syncthreads();
     }
 }
 
-// The same canonical evaluation spread over warps: one warp per (queued
-// pair, pattern array, group g of 32 partials) sums t = 32 g + lane (mod
-// 256) in increasing t and combines its 32 partials by the halving tree of
-// exact_q_m; the last warp of a pair to finish combines the 8 group sums of
-// each array by the same tree and stores the features.  Every sum is the
-// same FP64 operation sequence as in exact_kernel, on up to 24 SMs per pair
-// instead of one.  Takes the queue from scal[start_slot] when it holds at
-// most EX_CAP pairs (exact_kernel takes longer queues); arrive[] cleared by
-// the caller.
-__global__ void __launch_bounds__(32) exact_grp_kernel(McilWork w, Arr3 A, double h, double h2, double g,
-                                                       int start_slot) {
+// The same exact evaluation spread over CTAs: one CTA per (queued pair,
+// pattern array); the last CTA of a pair to finish forms its features.
+// Takes the queue from scal[start_slot] when it holds at most EX_CAP pairs
+// (exact_kernel takes longer queues); arrive[] cleared by the caller.
+__global__ void __launch_bounds__(256) exact_split_kernel(McilWork w, Arr3 A, double h, double h2, double g,
+                                                          int start_slot) {
+    __shared__ XdShared<256> sh;
     const unsigned long long nq = w.scal[0], first = start_slot == 0 ? 0ull : w.scal[start_slot];
     const unsigned long long cnt = nq > first ? nq - first : 0ull;
     if (cnt > (unsigned long long)EX_CAP) return;
     const int na = (w.mask & 0x3C) != 0 ? 3 : 1;
-    const unsigned long long items = cnt * (unsigned long long)(na * 8);
-    const int lane = threadIdx.x;
+    const unsigned long long items = cnt * (unsigned long long)na;
     for (unsigned long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const unsigned long long sl = it / (unsigned long long)(na * 8);
-        const int rem = (int)(it - sl * (unsigned long long)(na * 8));
-        const int a = rem >> 3, gi = rem & 7;
+        const unsigned long long sl = it / (unsigned long long)na;
+        const int a = (int)(it - sl * (unsigned long long)na);
         const int64_t q = w.queue[first + sl];
         const int64_t i = q / w.n2, j = q - i * w.n2;
-        const float *x = A.a1[a] + i * A.ld1[a], *y = A.a2[a] + j * A.ld2[a];
-        // increasing t; the loads run eight elements ahead of the sum
-        double acc = 0.0, mx = 0.0;
-        const int64_t d = A.d[a];
-        int64_t t = 32 * gi + lane;
-        for (; t + 7 * 256 < d; t += 8 * 256) {
-            float xa[8], ya[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                xa[u] = __ldg(x + t + 256 * u);
-                ya[u] = __ldg(y + t + 256 * u);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const double df = __dsub_rn((double)xa[u], (double)ya[u]);
-                acc = __dadd_rn(acc, __dmul_rn(df, df));
-                mx = fmax(mx, fabs(df));
-            }
-        }
-        for (; t < d; t += 256) {
-            const double df = __dsub_rn((double)x[t], (double)y[t]);
-            acc = __dadd_rn(acc, __dmul_rn(df, df));
-            mx = fmax(mx, fabs(df));
-        }
-#pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) {
-            const double o = __shfl_down_sync(0xffffffffu, acc, s);
-            if (lane < s) acc = __dadd_rn(acc, o);
-            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s));
-        }
-        unsigned last = 0;
-        if (lane == 0) {
-            double *gp = w.grp + (sl * 3 + a) * 16;
-            gp[2 * gi] = acc;
-            gp[2 * gi + 1] = mx;
+        double m = 0.0;
+        const double v = xd_block<256, true>(A.a1[a] + i * A.ld1[a], A.a2[a] + j * A.ld2[a], A.d[a], sh, &m);
+        if (threadIdx.x == 0) {
+            double *gp = w.grp + (sl * 3 + a) * 2;
+            gp[0] = v;
+            gp[1] = m;
             __threadfence();
-            last = atomicAdd(&w.arrive[sl], 1u) == (unsigned)(na * 8 - 1) ? 1u : 0u;
-        }
-        if (lane == 0 && last) {
-            __threadfence();
-            double qv[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
-            for (int a2 = 0; a2 < na; ++a2) {
-                const volatile double *gq = w.grp + (sl * 3 + a2) * 16;
-                double wv[8], mm = 0.0;
-                for (int k = 0; k < 8; ++k) {
-                    wv[k] = gq[2 * k];
-                    mm = fmax(mm, gq[2 * k + 1]);
+            if (atomicAdd(&w.arrive[sl], 1u) == (unsigned)(na - 1)) {
+                __threadfence();
+                double qv[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+                for (int a2 = 0; a2 < na; ++a2) {
+                    const volatile double *gq = w.grp + (sl * 3 + a2) * 2;
+                    qv[a2] = gq[0];
+                    mv[a2] = gq[1];
                 }
-                for (int s = 4; s >= 1; s >>= 1)
-                    for (int k = 0; k < s; ++k) wv[k] = __dadd_rn(wv[k], wv[k + s]);
-                qv[a2] = wv[0];
-                mv[a2] = mm;
+                exact_store(w, q, qv, mv, h, h2, g);
             }
-            exact_store(w, q, qv, mv, h, h2, g);
         }
     }
 }
@@ -627,8 +559,8 @@ __global__ void __launch_bounds__(32) exact_grp_kernel(McilWork w, Arr3 A, doubl
 //     squared distance from FP32 error-free transformations (s = fl(x - y)
 //     and e with s + e = x - y exactly; s^2 = p + pe exactly; 2 s e rounded;
 //     e^2 dropped; per thread an error-free (H, L) accumulation), as an
-//     interval that also covers the canonical order (the bound of the
-//     single-norm tier 2), and the maximum of |x - y| without FP64 work per
+//     interval that holds the exact sum (the bound of the single-norm
+//     tier 2), and the maximum of |x - y| without FP64 work per
 //     element: |x - y| = |s| + sign(s) e orders like the pair
 //     (|s|, sign(s) e), compared lexicographically in FP32; the winner's
 //     |s| + sign(s) e rounded to FP64 is the defined value (FP64 rounding
@@ -682,8 +614,7 @@ __device__ void t2_q_m(const float *x, const float *y, int64_t d, double *sred, 
             mm = fmax(mm, sred[8 + gi]);
         }
         const double n = (double)((d + 255) / 256);
-        const double rel = 2.0 * (2.9e-14 + 2.0 * n * (n + 4.0) * 3.56e-15 + 300.0 * 1.12e-16 +
-                                  (double)(d / 256 + 10) * 2.23e-16);
+        const double rel = 2.0 * (2.9e-14 + 2.0 * n * (n + 4.0) * 3.56e-15 + 300.0 * 1.12e-16);
         const double err = rel * fabs(D2) + 1e-300;
         sred[16] = fmax(D2 - err, 0.0);
         sred[17] = D2 + err;
@@ -718,7 +649,7 @@ __global__ void __launch_bounds__(256) tier2_kernel_m(McilWork w, Arr3 A, double
             lo[3] = __dadd_rd(__dadd_rd(__dmul_rd(h, __dsqrt_rd(ql[0])), __dsqrt_rd(ql[1])), __dsqrt_rd(ql[2]));
             hi[3] = __dadd_ru(__dadd_ru(__dmul_ru(h, __dsqrt_ru(qh[0])), __dsqrt_ru(qh[1])), __dsqrt_ru(qh[2]));
             // the maxima are exact: the max features are evaluated exactly as
-            // in the canonical expression
+            // in the defining expression
             {
                 const double bx = __dmul_rn(g, mv[1]), by = __dmul_rn(g, mv[2]);
                 const double b = bx > by ? bx : by;
@@ -757,7 +688,7 @@ __global__ void lb2_kernel_m(McilWork w) {
 
 // candidates whose interval of some feature is not a single value and may
 // still hold that feature's maximum (or, linear law, its minimum) are
-// evaluated in the canonical order
+// evaluated exactly
 __global__ void cand2_kernel_m(McilWork w) {
     const unsigned long long nA = w.scal[9];
     for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < nA;
@@ -801,14 +732,28 @@ __device__ double fitted_b_m(double c, int M) {
     return hi;
 }
 
-__global__ void radii_kernel_m(McilWork w, double b, double *radii_out) {
+__global__ void radii_kernel_m(McilWork w, double b, const double *__restrict__ radii_in, double *radii_out) {
     // one warp per feature; the maximum is among the queued candidates
     const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long nq = w.scal[0], nA = w.scal[9];
     if (threadIdx.x == 0) w.scal[1] = nq;   // end of the candidate phase
     if (f >= NF || !(w.mask & (1 << f))) return;
+    if (w.law == 3) {   // given radii [K][M+1] (R0 first, copied, not used)
+        if (lane != 0) return;
+        int slot = 0;
+        for (int f2 = 0; f2 < f; ++f2) slot += (w.mask >> f2) & 1;
+        const double *Ri = radii_in + (int64_t)slot * (w.M + 1);
+        double *R = radii_out + (int64_t)slot * (w.M + 1);
+        R[0] = Ri[0];
+        for (int k = 1; k <= w.M; ++k) {
+            const double r = Ri[k];
+            R[k] = r;
+            w.thr[f * 32 + k - 1] = feat_squared(f) ? __dmul_rn(r, r) : r;
+        }
+        return;
+    }
     // every pair that may hold the maximum (or the minimum) now has its
-    // value exactly: from the canonical pass (flag 2) or a single-value
+    // value exactly: from the exact pass (flag 2) or a single-value
     // tier-2 interval; every other candidate's value lies strictly inside
     // (smallest upper bound, largest lower bound)
     double mx = 0.0, mn = __longlong_as_double(0x7ff0000000000000ll);
@@ -908,6 +853,7 @@ __global__ void finish_kernel_m(McilWork w, const unsigned long long *t0, const 
 static rd_status mcil_check(int64_t n1, int64_t n2, int Gy, int Gx, int nsp, int mask, int M, double b) {
     if (n1 < 1 || n2 < 1 || n1 > 65535 || n2 > 65535) return RD_ERR_INVALID_ARG;
     if (Gx < 2 || Gx > 4096 || Gy < 1 || Gy > 4096 || nsp < 1 || nsp > 2) return RD_ERR_INVALID_ARG;
+    if ((int64_t)nsp * Gy * Gx > XD_MAX_D) return RD_ERR_INVALID_ARG;
     if (mask < 1 || mask > 63 || M < 1 || M > 32 || !(b > 1.0)) return RD_ERR_INVALID_ARG;
     return RD_OK;
 }
@@ -919,7 +865,9 @@ using namespace rdcil;
 static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2, int64_t n2,
                           int32_t Gy, int32_t Gx, int32_t n_species, int32_t features, int32_t scale, double b,
                           int law, int32_t M, double *d_radii_out, uint8_t *d_bins, int64_t *d_counts, double *d_C,
-                          int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream) {
+                          int64_t *d_n_exact, void *d_work, size_t work_bytes, void *stream,
+                          const double *d_radii_in = nullptr) {
+    if (law == 3 && !d_radii_in) return RD_ERR_INVALID_ARG;
     rd_status st = mcil_check(n1, n2, Gy, Gx, n_species, features, M, b);
     if (st) return st;
     const int64_t d0 = (int64_t)n_species * Gy * Gx;
@@ -1002,21 +950,14 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
         const int64_t nk = (A.d[a] + kch - 1) / kch;
         dim3 grid((unsigned)((n2 + TB - 1) / TB), (unsigned)((n1 + TA - 1) / TA), (unsigned)nk);
         if (narrow) {
-            static bool set64 = false;
-            if (!set64) {
-                RD_CUDA_TRY(cudaFuncSetAttribute(maxabs_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)MaxTile<64>::SMEM));
-                set64 = true;
-            }
+            // the attribute belongs to the current device: set it on every call
+            RD_CUDA_TRY(cudaFuncSetAttribute(maxabs_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)MaxTile<64>::SMEM));
             maxabs_kernel<64><<<grid, 256, MaxTile<64>::SMEM, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2,
                                                                    A.d[a], kch, w.mabs + a * np);
         } else {
-            static bool set128 = false;
-            if (!set128) {
-                RD_CUDA_TRY(cudaFuncSetAttribute(maxabs_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)MaxTile<128>::SMEM));
-                set128 = true;
-            }
+            RD_CUDA_TRY(cudaFuncSetAttribute(maxabs_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)MaxTile<128>::SMEM));
             maxabs_kernel<128><<<grid, 256, MaxTile<128>::SMEM, s>>>(A.a1[a], A.ld1[a], n1, A.a2[a], A.ld2[a], n2,
                                                                      A.d[a], kch, w.mabs + a * np);
         }
@@ -1025,8 +966,10 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
     const double g = (double)(Gx - 1), h = 1.0 / g, h2 = 1.0 / (g * g);
     intervals_kernel<<<gp, 256, 0, s>>>(w, qi, h, h2, g);
     note_launch();
-    candidates_kernel<<<gp, 256, 0, s>>>(w);
-    note_launch();
+    if (law != 3) {   // given radii need no maxima or minima
+        candidates_kernel<<<gp, 256, 0, s>>>(w);
+        note_launch();
+    }
     mark_kernel_m<<<1, 32, 0, s>>>(w, 9);
     note_launch();
     const unsigned ge = 4 * 148;
@@ -1037,11 +980,11 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
     cand2_kernel_m<<<148, 256, 0, s>>>(w);
     note_launch();
     RD_CUDA_TRY(cudaMemsetAsync(w.arrive, 0, sizeof(unsigned int) * EX_CAP, s));
-    exact_grp_kernel<<<16 * 148, 32, 0, s>>>(w, A, h, h2, g, 9);
+    exact_split_kernel<<<2 * 148, 256, 0, s>>>(w, A, h, h2, g, 9);
     note_launch();
     exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 9);
     note_launch();
-    radii_kernel_m<<<1, 32 * NF, 0, s>>>(w, b, d_radii_out);
+    radii_kernel_m<<<1, 32 * NF, 0, s>>>(w, b, d_radii_in, d_radii_out);
     note_launch();
     classify_kernel_m<<<gp, 256, 0, s>>>(w, 0);
     note_launch();
@@ -1052,7 +995,7 @@ static rd_status mcil_run(const float *d_X1, int64_t ld1, int64_t n1, const floa
     classify_kernel_m<<<gp, 256, 0, s>>>(w, 1);
     note_launch();
     RD_CUDA_TRY(cudaMemsetAsync(w.arrive, 0, sizeof(unsigned int) * EX_CAP, s));
-    exact_grp_kernel<<<16 * 148, 32, 0, s>>>(w, A, h, h2, g, 8);
+    exact_split_kernel<<<2 * 148, 256, 0, s>>>(w, A, h, h2, g, 8);
     note_launch();
     exact_kernel<<<ge, 256, 0, s>>>(w, A, h, h2, g, 8);
     note_launch();
@@ -1110,4 +1053,14 @@ extern "C" rd_status mcil_features_linear_rect(const float *d_X1, int64_t ld1, i
                                                void *d_work, size_t work_bytes, void *stream) {
     return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, Gy, Gx, n_species, features, scale, 2.0, 1, M, d_radii_out,
                     d_bins, d_counts, d_C, d_n_exact, d_work, work_bytes, stream);
+}
+
+extern "C" rd_status mcil_features_given_rect(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2,
+                                              int64_t ld2, int64_t n2, int32_t Gy, int32_t Gx, int32_t n_species,
+                                              int32_t features, int32_t scale, int32_t M,
+                                              const double *d_radii_in, double *d_radii_out, uint8_t *d_bins,
+                                              int64_t *d_counts, double *d_C, int64_t *d_n_exact, void *d_work,
+                                              size_t work_bytes, void *stream) {
+    return mcil_run(d_X1, ld1, n1, d_X2, ld2, n2, Gy, Gx, n_species, features, scale, 2.0, 3, M, d_radii_out, d_bins,
+                    d_counts, d_C, d_n_exact, d_work, work_bytes, stream, d_radii_in);
 }

@@ -83,26 +83,17 @@ __global__ void rkc_table_kernel(float4 *__restrict__ tab, double *__restrict__ 
     }
 }
 
-static float4 *g_tab = nullptr;
-static double *g_beta = nullptr;
-static std::once_flag g_tab_once;
-static rd_status g_tab_status = RD_OK;
+// bytes of the coefficient table followed by the beta table (one
+// allocation of the handle; the beta part starts 16-byte aligned)
+size_t rkc_table_bytes() {
+    return sizeof(float4) * (size_t)RKC_STRIDE * RKC_STRIDE + sizeof(double) * RKC_STRIDE;
+}
 
-rd_status rkc_tables(cudaStream_t s, const float4 **tab, const double **beta) {
-    std::call_once(g_tab_once, [s]() {
-        if (cudaMalloc(&g_tab, sizeof(float4) * (size_t)RKC_STRIDE * RKC_STRIDE) != cudaSuccess ||
-            cudaMalloc(&g_beta, sizeof(double) * RKC_STRIDE) != cudaSuccess) {
-            g_tab_status = RD_ERR_OOM;
-            return;
-        }
-        cudaMemsetAsync(g_beta, 0, sizeof(double) * RKC_STRIDE, s);
-        rkc_table_kernel<<<(RKC_STRIDE + 127) / 128, 128, 0, s>>>(g_tab, g_beta);
-        note_launch();
-        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) g_tab_status = RD_ERR_CUDA;
-    });
-    *tab = g_tab;
-    *beta = g_beta;
-    return g_tab_status;
+rd_status rkc_tables_fill(float4 *tab, double *beta, cudaStream_t s) {
+    RD_CUDA_TRY(cudaMemsetAsync(beta, 0, sizeof(double) * RKC_STRIDE, s));
+    rkc_table_kernel<<<(RKC_STRIDE + 127) / 128, 128, 0, s>>>(tab, beta);
+    note_launch();
+    return cuda_status(cudaGetLastError());
 }
 
 // Exchange the edge rows of a tile quantity (yu, yv) through ring buffer hb
@@ -466,15 +457,16 @@ bool rkc_set_variant(int G, int v) {
 int rkc_get_variant(int G) { return (G == 32 || G == 64) ? g_rkc_var[G == 64] : -1; }
 
 template <int MODEL, int G, int V>
-static rd_status launch_rkc_mg(const GroupDev &g, float *fields, const RkcRun &run, int64_t *stats,
-                               double *residual, uint32_t *status, cudaStream_t s) {
+static rd_status launch_rkc_mg(const GroupDev &g, const float4 *tab, const double *beta, float *fields,
+                               const RkcRun &run, int64_t *stats, double *residual, uint32_t *status,
+                               cudaStream_t s) {
     constexpr int TY = RkcShape<G, V>::TY, TX = RkcShape<G, V>::TX;
     using T = Tiling<G, TY, TX>;
     const size_t smem = rkc_smem<G, TY, TX>();
     auto kern = rd_rkc_kernel<MODEL, G, TY, TX>;
     RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const double t_end = run.t_end > 0.0 ? run.t_end : g.dt * (double)g.n_steps;
-    kern<<<g.n_real, T::NT, smem, s>>>(fields, g.field_offset, make_rkc_k(g), run, t_end, g_tab, g_beta,
+    kern<<<g.n_real, T::NT, smem, s>>>(fields, g.field_offset, make_rkc_k(g), run, t_end, tab, beta,
                                        stats ? stats + 4 * g.real_base : nullptr, g.p[0], g.p[1], g.p[2], g.p[3],
                                        residual ? residual + 2 * g.real_base : nullptr, status);
     note_launch();
@@ -482,18 +474,19 @@ static rd_status launch_rkc_mg(const GroupDev &g, float *fields, const RkcRun &r
 }
 
 template <int MODEL>
-static rd_status launch_rkc_m(const GroupDev &g, float *fields, const RkcRun &run, int64_t *stats, double *residual,
-                              uint32_t *status, cudaStream_t s) {
+static rd_status launch_rkc_m(const GroupDev &g, const float4 *tab, const double *beta, float *fields,
+                              const RkcRun &run, int64_t *stats, double *residual, uint32_t *status,
+                              cudaStream_t s) {
     const int v = rkc_get_variant(g.G);
     if (g.G == 32) {
-        if (v == 1) return launch_rkc_mg<MODEL, 32, 1>(g, fields, run, stats, residual, status, s);
-        if (v == 2) return launch_rkc_mg<MODEL, 32, 2>(g, fields, run, stats, residual, status, s);
-        return launch_rkc_mg<MODEL, 32, 0>(g, fields, run, stats, residual, status, s);
+        if (v == 1) return launch_rkc_mg<MODEL, 32, 1>(g, tab, beta, fields, run, stats, residual, status, s);
+        if (v == 2) return launch_rkc_mg<MODEL, 32, 2>(g, tab, beta, fields, run, stats, residual, status, s);
+        return launch_rkc_mg<MODEL, 32, 0>(g, tab, beta, fields, run, stats, residual, status, s);
     }
     if (g.G == 64) {
-        if (v == 1) return launch_rkc_mg<MODEL, 64, 1>(g, fields, run, stats, residual, status, s);
-        if (v == 2) return launch_rkc_mg<MODEL, 64, 2>(g, fields, run, stats, residual, status, s);
-        return launch_rkc_mg<MODEL, 64, 0>(g, fields, run, stats, residual, status, s);
+        if (v == 1) return launch_rkc_mg<MODEL, 64, 1>(g, tab, beta, fields, run, stats, residual, status, s);
+        if (v == 2) return launch_rkc_mg<MODEL, 64, 2>(g, tab, beta, fields, run, stats, residual, status, s);
+        return launch_rkc_mg<MODEL, 64, 0>(g, tab, beta, fields, run, stats, residual, status, s);
     }
     return RD_ERR_UNSUPPORTED;
 }
@@ -503,20 +496,18 @@ bool rkc_supported(const GroupDev &g) {
     return g.G == 32 || g.G == 64 || g.G == 128;
 }
 
-rd_status launch_rkc_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats, double *residual,
-                           uint32_t *status, cudaStream_t s) {
-    const float4 *tab = nullptr;
-    const double *beta = nullptr;
-    rd_status st = rkc_tables(s, &tab, &beta);
-    if (st != RD_OK) return st;
-    if (g.model == RD_RDODE) return launch_rkc1d_group(g, fields, o, stats, residual, status, s);
+rd_status launch_rkc_group(const GroupDev &g, const float4 *tab, const double *beta, float *fields,
+                           const rd_rkc_opts &o, int64_t *stats, double *residual, uint32_t *status,
+                           cudaStream_t s) {
+    if (!tab || !beta) return RD_ERR_UNSUPPORTED;
+    if (g.model == RD_RDODE) return launch_rkc1d_group(g, tab, beta, fields, o, stats, residual, status, s);
     RkcRun run{o.t_end, o.h0, o.rtol, o.atol, o.s_max, o.s_fixed, o.n_fixed, o.max_attempts};
     if (g.G == 128) return launch_rkc_cluster_group(g, fields, run, tab, beta, stats, residual, status, s);
     switch (g.model) {
-        case RD_FHN: return launch_rkc_m<RD_FHN>(g, fields, run, stats, residual, status, s);
-        case RD_GM: return launch_rkc_m<RD_GM>(g, fields, run, stats, residual, status, s);
-        case RD_DIFF: return launch_rkc_m<RD_DIFF>(g, fields, run, stats, residual, status, s);
-        case RD_BZ: return launch_rkc_m<RD_BZ>(g, fields, run, stats, residual, status, s);
+        case RD_FHN: return launch_rkc_m<RD_FHN>(g, tab, beta, fields, run, stats, residual, status, s);
+        case RD_GM: return launch_rkc_m<RD_GM>(g, tab, beta, fields, run, stats, residual, status, s);
+        case RD_DIFF: return launch_rkc_m<RD_DIFF>(g, tab, beta, fields, run, stats, residual, status, s);
+        case RD_BZ: return launch_rkc_m<RD_BZ>(g, tab, beta, fields, run, stats, residual, status, s);
         default: return RD_ERR_INVALID_ARG;
     }
 }

@@ -2,8 +2,9 @@
 // (App. B.2), shared by the 2-D kernel (rkc.cu, thread 0 of a CTA owns the
 // state in shared memory) and the 1-D kernel (rkc1d.cu, every lane of a
 // warp holds an identical copy in registers).  Coefficient tables:
-// rkc_tables() builds, once per process, tab[s][j] = (mu_j, nu_j, mt_j,
-// gt_j) (FP32, s = 2..RD_RKC_S_MAX, j = 1..s) and beta[s] (FP64).
+// rkc_tables_fill() forms tab[s][j] = (mu_j, nu_j, mt_j, gt_j) (FP32,
+// s = 2..RD_RKC_S_MAX, j = 1..s) and beta[s] (FP64) into memory the handle
+// owns (rd_init, once per handle and so per device).
 #pragma once
 #include "common.cuh"
 #include "tile.cuh"
@@ -13,7 +14,6 @@ namespace rdcil {
 constexpr int RKC_SMAX = RD_RKC_S_MAX;
 constexpr int RKC_STRIDE = RKC_SMAX + 1;
 
-rd_status rkc_tables(cudaStream_t s, const float4 **tab, const double **beta);
 
 // Step control state of one realisation.
 struct RkcCtl {

@@ -397,12 +397,9 @@ bool rkc1d_supported(const GroupDev &g) {
     return g.model == RD_RDODE && (g.G == 32 || g.G == 64 || g.G == 128 || g.G == 256);
 }
 
-rd_status launch_rkc1d_group(const GroupDev &g, float *fields, const rd_rkc_opts &o, int64_t *stats,
-                             double *residual, uint32_t *status, cudaStream_t s) {
-    const float4 *tab = nullptr;
-    const double *beta = nullptr;
-    rd_status st = rkc_tables(s, &tab, &beta);
-    if (st != RD_OK) return st;
+rd_status launch_rkc1d_group(const GroupDev &g, const float4 *tab, const double *beta, float *fields,
+                             const rd_rkc_opts &o, int64_t *stats, double *residual, uint32_t *status,
+                             cudaStream_t s) {
     RkcRun run{o.t_end, o.h0, o.rtol, o.atol, o.s_max, o.s_fixed, o.n_fixed, o.max_attempts};
     const double g2 = (double)(g.G - 1) * (double)(g.G - 1);
     Rkc1K K{(float)(g.p[1] * g2), (float)g.p[2], (float)g.p[3], (float)g.p[4], (float)g.p[5]};

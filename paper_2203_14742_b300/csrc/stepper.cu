@@ -209,21 +209,15 @@ static rd_status launch_variant(const GroupDev &g, float *fields, int64_t steps,
     if constexpr (V.packed || RECORD) {
         using T = Tiling2<G, V.TY, V.TX>;
         auto kern = rd_resident_kernel<MODEL, G, V.TY, V.TX, RECORD>;
-        static bool attr_set = false;
-        if (!attr_set) {
-            RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM));
-            attr_set = true;
-        }
+        rd_status ast = smem_attr(kern, (int)T::SMEM);
+        if (ast) return ast;
         kern<<<g.n_real, T::NT, T::SMEM, s>>>(fields, g.field_offset, steps, cf, g.p[0], g.p[1], g.p[2], g.p[3],
                                               res, status, traj, traj_stride);
     } else {
         using T = Tiling<G, V.TY, V.TX>;
         auto kern = rd_resident_scalar_kernel<MODEL, G, V.TY, V.TX>;
-        static bool attr_set = false;
-        if (!attr_set) {
-            RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM));
-            attr_set = true;
-        }
+        rd_status ast = smem_attr(kern, (int)T::SMEM);
+        if (ast) return ast;
         kern<<<g.n_real, T::NT, T::SMEM, s>>>(fields, g.field_offset, steps, cf, g.p[0], g.p[1], g.p[2], g.p[3],
                                               res, status);
     }
@@ -375,6 +369,20 @@ struct BatchPlan {
     int n_sm = 148;
 };
 
+static BatchGroup batch_group_of(const GroupDev &g) {
+    BatchGroup b;
+    b.cf = make_coef(g);
+    for (int k = 0; k < 4; ++k) b.p[k] = g.p[k];
+    b.field_offset = g.field_offset;
+    b.n_steps = g.n_steps;
+    b.real_base = g.real_base;
+    b.model = g.model;
+    b.G = g.G;
+    b.n_real = g.n_real;
+    b.pad = 0;
+    return b;
+}
+
 rd_status batch_plan_create(const GroupDev *groups, int n_groups, void **out) {
     *out = nullptr;
     std::vector<BatchGroup> bg((size_t)n_groups);
@@ -382,16 +390,7 @@ rd_status batch_plan_create(const GroupDev *groups, int n_groups, void **out) {
     std::vector<double> cost;
     for (int i = 0; i < n_groups; ++i) {
         const GroupDev &g = groups[i];
-        BatchGroup &b = bg[(size_t)i];
-        b.cf = make_coef(g);
-        for (int k = 0; k < 4; ++k) b.p[k] = g.p[k];
-        b.field_offset = g.field_offset;
-        b.n_steps = g.n_steps;
-        b.real_base = g.real_base;
-        b.model = g.model;
-        b.G = g.G;
-        b.n_real = g.n_real;
-        b.pad = 0;
+        bg[(size_t)i] = batch_group_of(g);
         // streaming groups run on their own launches; the 1-D model is not stepped here
         if (!group_is_resident(g) || g.model == RD_RDODE) continue;
         for (int r = 0; r < g.n_real; ++r) items.push_back(BatchItem{i, r});
@@ -417,6 +416,15 @@ rd_status batch_plan_create(const GroupDev *groups, int n_groups, void **out) {
     return ok ? RD_OK : RD_ERR_OOM;
 }
 
+// new parameters of group i (rd_set_params); the staged copy of the
+// pageable source completes before the call returns
+rd_status batch_plan_set_group(void *pp, int i, const GroupDev &g, cudaStream_t s) {
+    BatchPlan *p = (BatchPlan *)pp;
+    if (!p) return RD_OK;
+    const BatchGroup b = batch_group_of(g);
+    return cuda_status(cudaMemcpyAsync(p->d_groups + i, &b, sizeof(BatchGroup), cudaMemcpyHostToDevice, s));
+}
+
 void batch_plan_free(void *pp) {
     BatchPlan *p = (BatchPlan *)pp;
     if (!p) return;
@@ -431,11 +439,9 @@ rd_status launch_batch(void *pp, float *fields, int64_t steps_override, double *
     BatchPlan *p = (BatchPlan *)pp;
     if (!p) return RD_ERR_INVALID_ARG;
     if (p->n_items == 0) return RD_OK;
-    static bool attr = false;
-    if (!attr) {
-        RD_CUDA_TRY(cudaFuncSetAttribute(rd_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)BATCH_SMEM));
-        attr = true;
+    {
+        rd_status ast = smem_attr(rd_batch_kernel, (int)BATCH_SMEM);
+        if (ast) return ast;
     }
     RD_CUDA_TRY(cudaMemsetAsync(p->d_head, 0, sizeof(unsigned int), s));
     int grid = p->n_sm < p->n_items ? p->n_sm : p->n_items;

@@ -272,10 +272,9 @@ static rd_status stream_launch(const float *src, float *dst, const GroupDev &g, 
     CUtensorMap tm;
     if (!stream_map<S>(&tm, src, g.G, 2 * (int64_t)g.n_real)) return RD_ERR_CUDA;
     auto kern = rd_stream_kernel<MODEL, S>;
-    static bool attr = false;
-    if (!attr) {
-        RD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS::SMEM));
-        attr = true;
+    {
+        rd_status ast = smem_attr(kern, (int)SS::SMEM);
+        if (ast) return ast;
     }
     dim3 grid((unsigned)((g.G + ST_TX - 1) / ST_TX), (unsigned)((g.G + ST_TY - 1) / ST_TY), (unsigned)g.n_real);
     kern<<<grid, ST_THREADS, SS::SMEM, s>>>(tm, dst, g.G, nst, cf, in_dev, out_dev, status);

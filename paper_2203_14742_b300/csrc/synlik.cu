@@ -288,11 +288,9 @@ static rd_status launch_bootstrap_simt(const uint8_t *d_bins, int32_t n_feat, in
                                        const uint32_t *only_if, cudaStream_t s) {
     const size_t smem = (size_t)n2 * sizeof(uint16_t);
     if (smem > 48 * 1024) {
-        static size_t set = 0;
-        if (smem > set) {
+        {   // the size varies with the problem and the attribute is per device: set it per call
             RD_CUDA_TRY(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
-            set = smem;
         }
     }
     // row blocks per resample: about eight CTAs of 256 threads per SM over
@@ -313,11 +311,9 @@ static rd_status launch_stats(const int64_t *d_Y, int32_t Mt, int32_t T, int64_t
     const size_t smem2 = sizeof(double) * (3 * (size_t)Mt + 2 * (size_t)Mt * Mt) + sizeof(long long) * Mt +
                          2 * sizeof(int) * Mt;
     if (smem2 > 48 * 1024) {
-        static size_t set2 = 0;
-        if (smem2 > set2) {
+        {
             RD_CUDA_TRY(cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem2));
-            set2 = smem2;
         }
     }
     moments_clear_kernel<<<64, 256, 0, s>>>(Mt, n_problems, d_mu, d_cov, d_chol);

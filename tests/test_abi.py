@@ -141,3 +141,74 @@ def test_imex_argument_checks_without_gpu(libpath):
     assert L.rd_imex_n_variants() == 5
     assert L.rd_imex_get_variant(128) == -1
     assert L.rd_imex_set_variant(128, 0) == 1 and L.rd_imex_set_variant(64, 5) == 1
+
+
+def test_step_table_sizes_without_gpu(libpath):
+    """rd_tables_size (host only): the stabilised RK2 tables ((S+1)^2 float4
+    coefficients + (S+1) doubles, S = 256) when a group can run the RK2
+    integrator, plus the semi-implicit cosine-basis tables (2 G^2 + G and
+    G^2 + G floats) per grid side 32 / 64 present, each rounded up to 256
+    bytes; none for groups no table-using integrator runs (G = 256)."""
+    import paper_2203_14742_b300 as p
+
+    def up(b):
+        return (b + 255) // 256 * 256
+
+    rkc = up(257 * 257 * 16 + 257 * 8)
+
+    def imex(G):
+        return up(4 * (2 * G * G + G)) + up(4 * (G * G + G))
+
+    def size(spec):
+        arr = (p.RdGroup * len(spec))()
+        off = 0
+        for i, (model, G) in enumerate(spec):
+            a = arr[i]
+            a.model, a.G, a.n_real, a.n_steps, a.dt, a.field_offset = model, G, 2, 10, 1e-4, off
+            a.params[0], a.params[1], a.params[2], a.params[3] = 1e-4, 1e-2, 1.0, 0.5
+            a.noise_hi = 0.01
+            off += 2 * 2 * G * (1 if model == p.RDODE else G)
+        sz = ctypes.c_size_t()
+        assert p.lib().rd_tables_size(arr, len(spec), ctypes.byref(sz)) == 0
+        return sz.value
+
+    assert size([(p.FHN, 64)]) == rkc + imex(64)
+    assert size([(p.GM, 128)]) == rkc
+    assert size([(p.FHN, 32), (p.GM, 64), (p.FHN, 64)]) == rkc + imex(32) + imex(64)
+    assert size([(p.FHN, 256)]) == 0
+    assert size([(p.RDODE, 256)]) == rkc
+    sz = ctypes.c_size_t()
+    assert p.lib().rd_tables_size(None, 1, ctypes.byref(sz)) == 1
+
+
+def test_structs_match_the_header_layout(tmp_path, libpath):
+    """The binding's ctypes structs have the C compiler's layout of the
+    header's structs (offsets from offsetof in a compiled probe)."""
+    import paper_2203_14742_b300 as p
+    src = tmp_path / "probe.c"
+    fields = {"rd_group": ("RdGroup", ["model", "G", "n_real", "flags", "n_steps", "field_offset", "dt", "params",
+                                       "noise_lo", "noise_hi", "seed"]),
+              "rd_rkc_opts": ("RdRkcOpts", ["t_end", "h0", "rtol", "atol", "s_max", "s_fixed", "n_fixed",
+                                            "max_attempts"]),
+              "scil_spec": ("ScilSpec", ["group", "integrator", "rkc", "n_set", "n_species", "features", "scale",
+                                         "law", "b", "M", "T", "seed", "reinit", "pad"])}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rdcil.h"', 'int main(void) {']
+    for cs, (_, names) in fields.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cs, cs))
+        for n in names:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cs, n, cs, n))
+    lines += ['return 0;', '}']
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cs, n, v = line.split()
+            got[(cs, n)] = int(v)
+    for cs, (py, names) in fields.items():
+        cls = getattr(p, py)
+        assert ctypes.sizeof(cls) == got[(cs, "sizeof")], cs
+        for n in names:
+            assert getattr(cls, n).offset == got[(cs, n)], (cs, n)

@@ -164,13 +164,67 @@ def test_tensor_core_bound_holds_with_slack(p, n1, n2, d, off):
     assert np.all(m <= 1e-3 * ex + 1e-9)
 
 
-def test_paper_scale_sampled_pairs(p):
+def wide_floats(rng, n):
+    """FP32 values over the whole exponent range: normals, subnormals,
+    zeros, both signs."""
+    kind = rng.integers(0, 4, n)
+    mant = rng.uniform(1.0, 2.0, n)
+    v = np.where(kind == 0, mant * 2.0 ** rng.integers(-126, 100, n).astype(np.float64), 0.0)
+    v = np.where(kind == 1, mant * 2.0 ** rng.integers(-10, 10, n), v)
+    v = np.where(kind == 2, rng.integers(1, 2 ** 23, n) * 2.0 ** -149, v)
+    v = v * np.where(rng.integers(0, 2, n) == 0, 1.0, -1.0)
+    return v.astype(np.float32)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 17, 64, 1000, 4099])
+def test_exact_d2_bit_exact_over_the_exponent_range(p, d):
+    """The exact kernel (the last tier of every correlation integral) equals
+    the oracle's exactly rounded sum bit for bit, for inputs spanning
+    subnormals to 2^100 and for near-equal pairs (heavy cancellation)."""
+    rng = np.random.default_rng(d)
+    n1, n2 = 9, 7
+    X1 = np.stack([wide_floats(rng, d) for _ in range(n1)])
+    X2 = np.stack([wide_floats(rng, d) for _ in range(n2)])
+    X2[:3] = (X1[:3].astype(np.float64) * (1 + 1e-6 * rng.normal(size=(3, d)))).astype(np.float32)
+    pairs = np.array([(i, j) for i in range(n1) for j in range(n2)], np.int64)
+    g = p.exact_d2(torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda(), torch.from_numpy(pairs))
+    o = oracle.pair_d2(X1, X2).reshape(-1)
+    assert np.array_equal(g.cpu().numpy(), o)
+
+
+def test_exact_d2_ties_and_non_finite(p):
+    t, u = np.float32(2.0 ** -27), np.float32(2.0 ** -26)
+    X1 = np.zeros((5, 5), np.float32)
+    X1[0, :3] = [1.0, t, t]              # 1 + 2^-53: tie, to even -> 1
+    X1[1, :4] = [1.0, u, t, t]           # 1 + 2^-52 + 2^-53: tie -> 1 + 2^-51
+    X1[2, :4] = [1.0, t, t, t]           # above half-way -> 1 + 2^-52
+    X1[3, :] = [1.0, t, t, t, t]         # exactly 1 + 2^-52
+    X1[4, 2] = np.inf
+    X2 = np.zeros((1, 5), np.float32)
+    pairs = np.array([(i, 0) for i in range(5)], np.int64)
+    g = p.exact_d2(torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda(), torch.from_numpy(pairs)).cpu().numpy()
+    assert list(g[:4]) == [1.0, 1.0 + 2.0 ** -51, 1.0 + 2.0 ** -52, 1.0 + 2.0 ** -52]
+    assert math.isnan(g[4])
+
+
+def test_exact_d2_long_patterns(p):
+    """d = 32768 (GM 128^2, both species): equal to the oracle on 64 pairs."""
+    X = W.cosine_patterns(16, 128, 2, 41, amp=0.8, offset=2.0)
+    rng = np.random.default_rng(3)
+    pairs = rng.integers(0, 8, size=(64, 2)).astype(np.int64)
+    g = p.exact_d2(torch.from_numpy(X[:8]).cuda(), torch.from_numpy(X[8:]).cuda(), torch.from_numpy(pairs))
+    o = np.array([oracle.d2_exact(X[i], X[8 + j]) for i, j in pairs])
+    assert np.array_equal(g.cpu().numpy(), o)
+
+
+def test_paper_scale_every_pair(p):
     """2 x 1024 patterns of d = 32768 (the SCIL scale, as timed by bench.py
-    --gram-large): too many pairs for the brute-force oracle, so the bins of
-    2000 random pairs are recomputed from the oracle's canonical distance
-    and the GPU's radii, R0 is checked against the oracle's distance of the
-    pair the approximate stage ranks largest (and bounds every sampled
-    distance), and the counts are checked against the bin matrix."""
+    --gram-large), every one of the 1.05e6 bins checked without the GPU's
+    approximate stage: a float64 Gram on the host (numpy/BLAS) gives every
+    d2 within the dot-product error bound (d + 2) 2^-53 (|x|^2 + |y|^2 +
+    2 |x| |y|); pairs whose interval could hold the maximum or meets a
+    threshold are evaluated by the oracle exactly, all others are decided
+    by their interval."""
     n, G = 1024, 128
     X = W.cosine_patterns(2 * n, G, 2, 77, amp=0.8, offset=2.0)
     X1, X2 = X[:n], X[n:]
@@ -184,15 +238,26 @@ def test_paper_scale_sampled_pairs(p):
     counts = g["counts"].cpu().numpy()
     for k in range(1, 17):
         assert counts[k - 1] == int((bins >= k).sum())
-    # the largest distance is among the 16 pairs the approximate stage
-    # ranks largest (its error bound is ~1e-4 relative)
-    A, _ = p.cil_approx(t1, t2)
-    top = torch.topk(A.reshape(-1), 16).indices.cpu().numpy()
-    best = max(oracle.d2_exact(X1[q // n], X2[q % n]) for q in top)
+    # host float64 intervals of every d2 (the GPU plays no part)
+    A1, A2 = X1.astype(np.float64), X2.astype(np.float64)
+    n1s, n2s = (A1 * A1).sum(1), (A2 * A2).sum(1)
+    D = n1s[:, None] + n2s[None, :] - 2.0 * (A1 @ A2.T)
+    d = X.shape[1]
+    err = (d + 2) * 2.0 ** -53 * (n1s[:, None] + n2s[None, :] + 2.0 * np.sqrt(n1s[:, None] * n2s[None, :]))
+    err = 2.0 * err + 1e-300                    # slack for the rounding of D and err themselves
+    lo, hi = D - err, D + err
+    # the maximum: exact over every pair whose interval reaches the largest lower bound
+    cand = np.argwhere(hi >= lo.max())
+    best = max(oracle.d2_exact(X1[i], X2[j]) for i, j in cand)
     assert math.sqrt(best) == R0
-    rng = np.random.default_rng(5)
-    for i, j in zip(rng.integers(0, n, 2000), rng.integers(0, n, 2000)):
+    # bins: decided by the interval unless it meets a threshold
+    T = radii * radii
+    K = np.zeros((n, n), np.int64)
+    open_ = np.zeros((n, n), bool)
+    for t in T:
+        K += hi < t
+        open_ |= ~((hi < t) | (lo >= t))
+    for i, j in np.argwhere(open_):
         d2 = oracle.d2_exact(X1[i], X2[j])
-        assert math.sqrt(d2) <= R0
-        K = sum(1 for r in radii if d2 < r * r)
-        assert bins[i, j] == K, (i, j)
+        K[i, j] = int(sum(d2 < t for t in T))
+    assert np.array_equal(bins, K.astype(np.uint8))

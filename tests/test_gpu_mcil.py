@@ -218,7 +218,7 @@ def test_linear_law_bit_exact(p, n1, n2, Gy, Gx, nsp, scale):
 def test_linear_near_duplicates(p):
     # set 2 holds slightly perturbed copies of set 1: the smallest values
     # are tiny differences, where the tensor-core interval is widest, so the
-    # minimum goes through the re-bounding and the canonical order
+    # minimum goes through the re-bounding and the exact evaluation
     rng = np.random.default_rng(42)
     G, n = 32, 40
     X1 = (rng.standard_normal((n, G * G)) * 0.5 + 1.0).astype(np.float32)

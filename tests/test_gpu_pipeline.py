@@ -138,3 +138,39 @@ def test_pipeline_with_the_semi_implicit_stepper(p):
     for i, (X1, X2) in enumerate(pipe.views):
         o = oracle.cil(X1.cpu().numpy(), X2.cpu().numpy(), 1.3, 10)
         assert np.array_equal(pipe.cil_out[i]["counts"].cpu().numpy(), o["counts"])
+
+
+@pytest.mark.parametrize("kind", ["rkc", "imex"])
+def test_first_call_of_a_handle_captures_in_a_graph(p, kind):
+    """The stabilised RK2 and semi-implicit step tables belong to the
+    handle (formed by rd_init on its device), so the very first
+    rd_integrate_rkc / rd_integrate_imex call of a fresh handle launches
+    only the integrator (no table set-up, no allocation, no synchronise)
+    and can be captured in a CUDA graph; replaying it gives the eager
+    result bit for bit."""
+    import ctypes
+    g = p.Group(W.FHN, 64, 4, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -10, 120, (-0.05, 0.05), 77)
+    sim = p.Simulation([g])
+    sz = ctypes.c_size_t()
+    assert p.lib().rd_tables_size(sim._arr, 1, ctypes.byref(sz)) == 0
+    assert sim.table_bytes() == sz.value > 0
+
+    def call(s):
+        if kind == "rkc":
+            s.integrate_rkc(h0=2 ** -10, s_fixed=6, n_fixed=40, stats=False)
+        else:
+            s.integrate_imex()
+
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    n0 = p.lib().rd_kernel_launches()
+    with torch.cuda.graph(graph):
+        call(sim)
+    assert p.lib().rd_kernel_launches() - n0 == 1
+    graph.replay()
+    torch.cuda.synchronize()
+    eager = p.Simulation([g])
+    call(eager)
+    torch.cuda.synchronize()
+    assert torch.equal(sim.fields, eager.fields)
+    assert sim.sync_status() == 0 and eager.sync_status() == 0

@@ -129,3 +129,21 @@ def test_smooth_cil_tends_to_indicator():
                                 X2.astype(np.float32).astype(np.float64),
                                 radii, 1e-9, np.ones(4), grad=False)
     assert np.allclose(C * 42, counts, atol=1e-6)
+
+
+@pytest.mark.parametrize("model", [FHN, GM, BZ])
+def test_gradient_term_magnitudes(model):
+    """A (the summed magnitudes of the gradient's terms, used to set the
+    GPU comparison's per-component tolerance) bounds |grad|, is unchanged
+    by flipping the cotangent's sign and scales with its magnitude, while
+    the gradient itself is untouched by asking for it."""
+    P = small_problem(model)
+    args = (P["model"], P["p"], P["dt"], P["steps"], P["w0"], P["mask"], P["set1"], P["set2"], P["radii"], 0.05)
+    C, g, A = oracle.smooth_cil_grad(*args, P["cot"], with_abs=True)
+    C0, g0 = oracle.smooth_cil_grad(*args, P["cot"])
+    assert np.array_equal(g, g0) and np.array_equal(C, C0)
+    assert np.all(A >= np.abs(g)) and np.all(A > 0)
+    _, gm, Am = oracle.smooth_cil_grad(*args, -P["cot"], with_abs=True)
+    assert np.array_equal(gm, -g) and np.array_equal(Am, A)
+    _, g2, A2 = oracle.smooth_cil_grad(*args, 2.0 * P["cot"], with_abs=True)
+    assert np.allclose(A2, 2.0 * A, rtol=1e-12) and np.allclose(g2, 2.0 * g, rtol=1e-12)

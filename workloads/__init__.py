@@ -31,6 +31,12 @@ Workloads (sizes follow the paper's Table 1 models and the hot-path configs):
       t in [0, 50] by the adaptive stabilised RK2 (rtol = atol = 1e-6),
       initial u = U(0, 2) noise smoothed by 10 moving-average passes, w = 0;
       (m1, m2) within +-5 % of (1.44, 4.1); both species (d = 128), M = 13.
+  c8  synthetic CIL with bootstrapping (Alg. 6) in Table 1's setting: FHN
+      64x64 to T = 100 (102400 Euler steps of 2^-10), N_syn = 1000 model
+      runs at theta (Sec. 5: 1000 runs per cost evaluation), N_set = 50,
+      the six features on both species, M = 13 radii per feature with the
+      power law fitted to the range, n_CIL = 1000 resamples; the data set is
+      50 patterns simulated at theta_0 (seed + 1000).
   glarge  the paper's SCIL scale (N_syn = 1000, Sec. 5.3): 2 sets x 1024
       patterns of d = 32768 for the Gram kernel alone.
 """
@@ -156,6 +162,14 @@ def config(name: str, steps_scale: float = 1.0):
         g = group(RDODE, 64, 200, p, 2.0 ** -10, steps(51200), (0.0, 2.0), s, 3)
         return {"name": name, "groups": [g], "n1": 100, "n2": 100, "M": 13, "b": 1.3,
                 "T_res": 200, "seed": s, "rkc_tol": 1e-6}
+    if name == "c8":
+        s = seed_of(8)
+        p = draw_params(FHN, s)[0]
+        p0 = draw_params(FHN, s + 1000)[0]
+        g = group(FHN, 64, 1000, p, 2.0 ** -10, steps(102400), (-0.05, 0.05), s, 3)
+        gd = group(FHN, 64, 50, p0, 2.0 ** -10, steps(102400), (-0.05, 0.05), s + 1000, 3)
+        return {"name": name, "groups": [g], "data_group": gd, "n_set": 50, "M": 13, "law": "fitted",
+                "features": 63, "T_res": 1000, "seed": s}
     if name == "c5":
         s = seed_of(5)
         p = draw_params(FHN, s)[0]
