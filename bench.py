@@ -1,21 +1,29 @@
 """Benchmark of the CIL hot path on B300 (one JSON line on rank 0).
 
-One step = one pass of the whole hot path over one batch of synthetic input
-(the 64x64 FitzHugh-Nagumo workload: 2 sets x 64 realisations, 10^4 FP32
-Euler steps, u-only patterns of d = 4096, 16 radii, 200 resamples):
+One step = one pass of the whole hot path over one batch of synthetic input.
+The default workload is the largest single-GPU configuration, the batched
+sampler sweep: 64 parameter vectors x 128 realisations, FHN and GM on 64x64
+(10^4 Euler steps) and 128x128 (2x10^4 steps) in one persistent launch,
+then per parameter vector the correlation integral of 2 sets x 64 patterns
+(16 radii) and the bootstrap statistics (200 resamples):
   initial state -> integration (+ FP64 residual) -> pattern Gram + exact
   recheck -> radii / bins / counts -> bootstrap counts -> mean, covariance,
   Cholesky, log-determinant, cost and log-likelihood.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config c4|c2|...]
 
 value  = cell-updates per second of the whole step (a cell-update = one grid
          node, both species, one time step), device-timed with CUDA events,
          max over ranks, inputs resident in HBM.
 e2e    = the same through the public API with host buffers: every step
          copies the initial fields host->device and the statistics back.
+The default run adds keys for the FHN 64x64 workload (c2), the tensor-core
+Gram at the paper's SCIL scale, the streaming stepper against HBM, the
+adjoint (c5) and one whole synthetic-likelihood cost evaluation (Alg. 6,
+workload c8).
 --impl reference runs the plain FP64 CPU oracle on a bounded sample of the
-same workload (rank 0 only; other ranks exit).
+same workload (every group, a stated slice of its steps; rank 0 only).
 """
 import argparse
 import json
@@ -41,22 +49,63 @@ import workloads as W  # noqa: E402
 # fma g, fma, fma, fma -4, ...); DIFF 2 + 2.
 FP32_INST_PER_CELL = {W.FHN: 15, W.GM: 20, W.DIFF: 10, W.BZ: 22}
 
-# DRAM bytes (read + write) of one stepper launch on this workload, from the
-# ncu capture summarised in profiles/rd_resident_scalar_kernel_fhn64_c2.md,
-# keyed by a hash of the stepper sources: reported only while the kernel is
-# the one that was measured.
-STEPPER_TRAFFIC = {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488, "7c8c62601c860730": 4223488}
+# DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload
+# and a hash of the stepper sources: reported, labelled as that capture's,
+# only while the kernel is the one that was measured.  The resident and
+# persistent steppers read the initial fields and write the final ones once
+# per launch whatever the step count, so a capture of a shortened run gives
+# the full launch's traffic.
+STEPPER_TRAFFIC = {
+    "c2": {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488, "7c8c62601c860730": 4223488},
+    "c4": {},
+}
 STEPPER_SOURCES = ["paper_2203_14742_b300/csrc/stepper.cu", "paper_2203_14742_b300/csrc/tile.cuh",
                    "paper_2203_14742_b300/csrc/common.cuh"]
 
 
-def stepper_traffic():
+def sources_hash():
     import hashlib
     h = hashlib.sha256()
     for f in STEPPER_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return STEPPER_TRAFFIC.get(h.hexdigest()[:16])
+    return h.hexdigest()[:16]
+
+
+def stepper_traffic(config):
+    """(bytes, source label) of the committed capture for this workload and
+    the current stepper sources, or (None, reason)."""
+    hs = sources_hash()
+    v = STEPPER_TRAFFIC.get(config, {}).get(hs)
+    if v is None:
+        return None, "no ncu capture of the current stepper sources (hash %s) on this workload" % hs
+    return v, "ncu capture of the stepper sources with hash %s (dram__bytes_read.sum + dram__bytes_write.sum)" % hs
+
+
+WORKLOADS = {
+    "c1": "c1: FHN 32x32, 2 x 16, 2000 steps, d=2048, M=8, 50 resamples",
+    "c2": "c2: FHN 64x64, 2 sets x 64 realisations, 10^4 Euler steps, u-only d=4096, M=16, b=1.3, "
+          "200 resamples",
+    "c3": "c3: GM 128x128, 2 x 256, 2x10^4 steps, d=32768, M=16, 200 resamples",
+    "c4": "c4: 64 parameter vectors x 128 realisations, FHN+GM at 64^2 (10^4 steps) and 128^2 "
+          "(2x10^4 steps) in one persistent launch, 2 x 64 sets per vector, M=16, b=1.3, 200 resamples",
+    "c5": "c5: FHN 64x64, 32 realisations, 5000 steps",
+    "c6": "c6: Brusselator 64x64, 2 sets x 64 realisations, 25600 Euler steps (T = 100), both "
+          "species d=8192, M=16, b=1.3, 200 resamples",
+}
+
+
+def config_json(name, cfg):
+    """The `config` object of the JSON line (both arms)."""
+    groups = cfg["groups"]
+    return {"workload": WORKLOADS[name], "groups": len(groups),
+            "realisations_per_gpu": sum(g["n_real"] for g in groups),
+            "grids": sorted(set(g["G"] for g in groups)), "pairs": cfg["n1"] * cfg["n2"] * len(groups),
+            "radii": cfg["M"], "resamples": cfg["T_res"],
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -66,7 +115,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c4")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the c2, tensor-core Gram, streaming-stepper, adjoint and SCIL keys of the default run")
+    ap.add_argument("--stepper-only", action="store_true",
+                    help="initial state and integration only, steps overridden by --steps-override "
+                         "(for profiling the stepper on a shortened run)")
+    ap.add_argument("--steps-override", type=int, default=-1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-reference-path", action="store_true")
     ap.add_argument("--variant", type=int, default=-1,
@@ -369,15 +424,10 @@ def run_ours(args, rank, world, local_rank):
         kname = "%s<%s,%d,%dx%d> variant %s" % ("rd_resident_kernel" if pk_ else "rd_resident_scalar_kernel",
                                                {0: "FHN", 1: "GM", 2: "DIFF", 3: "BZ"}[groups[0].model],
                                                groups[0].G, ty_, tx_, variant)
-    workload = {"c2": "c2: FHN 64x64, 2 sets x 64 realisations, 10^4 Euler steps, u-only d=4096, M=16, "
-                      "b=1.3, 200 resamples",
-                "c4": "c4: 64 parameter vectors x 128 realisations, FHN+GM at 64^2 (10^4 steps) and 128^2 "
-                      "(2x10^4 steps) in one persistent launch, 2 x 64 sets per vector, M=16, 200 resamples",
-                "c1": "c1: FHN 32x32, 2 x 16, 2000 steps, d=2048, M=8, 50 resamples",
-                "c3": "c3: GM 128x128, 2 x 256, 2x10^4 steps, d=32768, M=16, 200 resamples",
-                "c5": "c5: FHN 64x64, 32 realisations, 5000 steps",
-                "c6": "c6: Brusselator 64x64, 2 sets x 64 realisations, 25600 Euler steps (T = 100), both "
-                      "species d=8192, M=16, b=1.3, 200 resamples"}[args.config]
+    if multi or variant == 0:
+        traffic, tsrc = stepper_traffic(args.config)
+    else:
+        traffic, tsrc = None, "no ncu capture of this tile variant"
     out = {
         "metric": "RD cell-updates/s + CIL pair-dists/s at stated tol; % HBM/tensor roofline",
         "value": value,
@@ -391,10 +441,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32 stepper, bf16x3 Gram + f64 recheck, f64 statistics",
         "data": "synthetic (seeded counter-based initial noise; the paper's data are simulated too)",
-        "config": {"workload": workload, "groups": len(groups),
-                   "realisations_per_gpu": sum(g.n_real for g in groups),
-                   "grids": sorted(set(g.G for g in groups)), "pairs": pairs, "radii": M, "resamples": T,
-                   "l2": "flushed between timed steps (256 MB write)"},
+        "config": config_json(args.config, cfg),
         "pair_dists_per_s": pairs / (cil_avg * 1e-3),
         "cil_pairs_rechecked_exactly": nre,
         "stepper_variant": variant,
@@ -407,7 +454,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tinst/s",
                      "frac": achieved / peak_alu,
-                     "traffic": stepper_traffic() if variant == 0 and args.config == "c2" else None,
+                     "traffic": traffic, "traffic_source": tsrc,
                      "kernel": kname,
                      "note": "FP32 pipe instructions of the update (FHN 15, GM 20, BZ 22 per cell-update) x "
                              "cell-updates / stepper time; peak = 148 SM x 128 FP32 lanes x max SM clock "
@@ -418,14 +465,18 @@ def run_ours(args, rank, world, local_rank):
     cs = clk.summary()
     if cs:
         out["clocks"] = cs
-    if args.gram_large and rank == 0:
+    extras = not args.no_extras and rank == 0
+    if extras and args.config != "c2":
+        out["c2"] = c2_bench(p, torch, dev, stream, pk, src)
+    if (args.gram_large or extras) and rank == 0:
         out["gram_large"] = gram_large(p, torch, dev, stream, pk, src)
-    if args.adjoint and rank == 0:
+    if (args.adjoint or extras) and rank == 0:
         out["adjoint"] = adjoint_c5(p, torch, dev, stream)
     if args.mcil and rank == 0:
         out["mcil"] = mcil_bench(p, torch, dev, stream)
+    if (args.mcil or extras) and rank == 0:
         out["scil"] = scil_bench(p, torch, dev, stream)
-    if args.stream and rank == 0:
+    if (args.stream or extras) and rank == 0:
         out["stream"] = stream_bench(p, torch, dev, stream, pk, src)
     if args.rkc and rank == 0:
         out["rkc"] = rkc_bench(p, torch, dev, stream, pk, src)
@@ -442,6 +493,83 @@ def _check_int(p, sim, pipe):
                                     ctypes.c_void_p(__import__("torch").cuda.current_stream().cuda_stream))
     if st != 0:
         raise RuntimeError("rd_integrate_batch failed: %d" % st)
+
+
+def stepper_only(p, torch, dev, args):
+    """Initial state and integration of the workload's groups only, every
+    group advanced --steps-override steps (default: its own step count):
+    one warm-up launch, then --steps timed launches (for profiling the
+    stepper on a shortened run; the persistent launch's DRAM traffic does
+    not depend on the step count)."""
+    cfg = W.config(args.config)
+    groups = [p.Group.from_dict(gd) for gd in cfg["groups"]]
+    sim = p.Simulation(groups, device=dev)
+    steps = int(args.steps_override)
+    stream = torch.cuda.current_stream(dev)
+    sim.integrate(steps=steps, residual=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sim.reinit()
+    e0.record(stream)
+    for _ in range(max(1, args.steps)):
+        sim.integrate(steps=steps, residual=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert sim.sync_status() == 0
+    cells = sum(g.n_real * g.G * g.G * (steps if steps >= 0 else g.n_steps) for g in groups)
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    return {"workload": WORKLOADS[args.config], "steps_override": steps, "ms_per_launch": ms,
+            "cell_updates_per_s": cells / (ms * 1e-3)}
+
+
+def c2_bench(p, torch, dev, stream, pk, src, reps=5):
+    """The FHN 64x64 workload (c2: 2 sets x 64 realisations, 10^4 Euler
+    steps, u-only patterns, 16 radii, 200 resamples) as a key of the default
+    run: whole pass and stepper time (CUDA events, L2 flushed between
+    passes), the autotuned tile variant and the stepper against the FP32
+    issue peak."""
+    cfg = W.config("c2")
+    gd = cfg["groups"][0]
+    g = p.Group.from_dict(gd)
+    pipe = p.Pipeline([g], [(cfg["n1"], cfg["n2"], gd["species_mask"])], cfg["M"], cfg["b"], cfg["T_res"],
+                      cfg["seed"], device=dev)
+    sim = pipe.sim
+    chosen = sim.autotune(steps=300)
+    variant = chosen[g.model * 3 + 1]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        pipe.run()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps)]
+    for i in range(reps):
+        flush.fill_(float(i))
+        e = ev[i]
+        e[0].record(stream)
+        sim.reinit()
+        e[1].record(stream)
+        _check_int(p, sim, pipe)
+        e[2].record(stream)
+        for (X1, X2), out in zip(pipe.views, pipe.cil_out):
+            p.cil(X1, X2, b=cfg["b"], M=cfg["M"], work=pipe.work, out=out)
+        p.synlik(pipe.bins, cfg["M"], cfg["T_res"], pipe.seed, y_obs=pipe.C, out=pipe.stats, work=pipe.syn_work)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    assert sim.sync_status() == 0
+    step_ms = sum(e[0].elapsed_time(e[3]) for e in ev) / reps
+    k_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / reps
+    cells = g.n_real * g.G * g.G * g.n_steps
+    inst = cells * FP32_INST_PER_CELL[g.model]
+    peak = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    ach = inst / (k_ms * 1e-3) / 1e12
+    pk_, ty_, tx_ = p.variant_shape(g.G, variant)
+    traffic, tsrc = stepper_traffic("c2") if variant == 0 else (None, "no ncu capture of this tile variant")
+    return {"workload": WORKLOADS["c2"], "ms_per_step": step_ms, "cell_updates_per_s": cells / (step_ms * 1e-3),
+            "stepper_ms": k_ms, "stepper_variant": variant,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tinst/s", "frac": ach / peak,
+                         "traffic": traffic, "traffic_source": tsrc,
+                         "kernel": "%s<FHN,64,%dx%d> variant %d" % (
+                             "rd_resident_kernel" if pk_ else "rd_resident_scalar_kernel", ty_, tx_, variant)},
+            "cil_pairs_rechecked_exactly": int(sum(int(o["n_rechecked"]) for o in pipe.cil_out))}
 
 
 def gram_large(p, torch, dev, stream, pk, src):
@@ -831,43 +959,65 @@ def mcil_bench(p, torch, dev, stream):
     return res
 
 
-def scil_bench(p, torch, dev, stream):
-    """The synthetic-likelihood cost after the simulations, at the paper's
-    SCIL scale (Alg. 6 with bootstrapping, Sec. 5.1: N_syn = 1000 patterns,
-    N_set = 50 of them against the other 950, n_CIL = 1000 resampled set
-    pairs, the six features): multi-feature CIL of GM-sized fields (2 species
-    of 128x128, synthetic cosine modes), then bootstrap counts of the
-    96-component vector and its statistics (tensor-core and SIMT counts)."""
-    n_syn, n_set, G, nsp, M, T = 1000, 50, 128, 2, 16, 1000
-    X = torch.from_numpy(W.cosine_patterns(n_syn, G, nsp, 93, amp=0.8, offset=2.0)).to(dev)
-    X1, X2 = X[:n_set], X[n_set:]
-    n2 = n_syn - n_set
-    work = p.mcil_workspace(n_set, n2, G, nsp, 63, False, M, dev)
-    swork = p.synlik_workspace(n_set, n2, M, T, 6, 1, dev)
-    sout = p.synlik_outputs(1, 6 * M, T, dev)
-    r = p.mcil(X1, X2, G, nsp, b=1.3, M=M, work=work)
-    bins = r["bins"].unsqueeze(0).contiguous()
-    yobs = r["C"].unsqueeze(0).contiguous()
-    p.synlik(bins, M, T, 2203, y_obs=yobs, n_feat=6, work=swork, out=sout)
+def scil_bench(p, torch, dev, stream, reps=3):
+    """One evaluation of the synthetic-likelihood cost f(theta) with
+    bootstrapping (Alg. 6) as one call (scil_evaluate), in Table 1's SCIL
+    setting (workload c8): FHN 64x64 to T = 100 (102400 Euler steps), N_syn
+    = 1000 model runs at theta from fresh initial states, N_set = 50 against
+    the other 950, the six features on both species, M = 13 radii per
+    feature (power law fitted to the range), n_CIL = 1000 resamples, the
+    data vector of 50 patterns simulated at theta_0.  Whole-call time
+    (CUDA events), and the stage split from the same stages run as separate
+    calls."""
+    cfg = W.config("c8")
+    g = p.Group.from_dict(cfg["groups"][0])
+    gd = p.Group.from_dict(cfg["data_group"])
+    sim = p.Simulation([g], device=dev)
+    dsim = p.Simulation([gd], device=dev)
+    dsim.integrate(residual=False)
+    data = dsim.fields.view(gd.n_real, -1)
+    n_set, M, T, feats = cfg["n_set"], cfg["M"], cfg["T_res"], cfg["features"]
+    sc = p.Scil(sim, 0, data, n_set=n_set, n_species=2, features=feats, law=cfg["law"], M=M, T=T, seed=cfg["seed"])
+    sc.run()
     torch.cuda.synchronize()
 
-    def timed(fn, reps=5):
+    def timed(fn, n=reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(reps):
+        for _ in range(n):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return e0.elapsed_time(e1) / n
 
-    t_mcil = timed(lambda: p.mcil(X1, X2, G, nsp, b=1.3, M=M, work=work))
-    t_syn = timed(lambda: p.synlik(bins, M, T, 2203, y_obs=yobs, n_feat=6, work=swork, out=sout))
-    Y_tc = sout["Y"].clone()
-    t_simt = timed(lambda: p.synlik(bins, M, T, 2203, y_obs=yobs, n_feat=6, out=sout, simt=True), reps=2)
-    return {"n_syn": n_syn, "n_set": n_set, "d": nsp * G * G, "features": 6, "M": M, "n_cil": T,
-            "mcil_ms": t_mcil, "bootstrap_stats_ms": t_syn, "bootstrap_stats_simt_ms": t_simt,
-            "same_counts": bool(torch.equal(Y_tc, sout["Y"])), "status": int(sout["status"][0]),
-            "cost_f": float(sout["scalars"][0, 1]), "total_ms": t_mcil + t_syn}
+    t_total = timed(sc.run)
+    out = sc.out
+    assert sim.sync_status() == 0
+    # the stages as separate calls on the same fields
+    X = sim.fields.view(g.n_real, -1)
+    S1, S2 = X[:n_set], X[n_set:]
+    work = p.mcil_workspace(max(n_set, gd.n_real), g.n_real - n_set, g.G, 2, feats, False, M, dev)
+    t_sim = timed(lambda: (sim.reinit(), sim.integrate(residual=False)))
+    r = p.mcil(S1, S2, g.G, 2, M=M, features=feats, work=work, law=cfg["law"])
+    t_mcil = timed(lambda: p.mcil(S1, S2, g.G, 2, M=M, features=feats, work=work, law=cfg["law"]))
+    t_data = timed(lambda: p.mcil_given(data, S2, g.G, 2, r["radii"], features=feats, work=work))
+    K = bin(feats).count("1")
+    bins = r["bins"].unsqueeze(0).contiguous()
+    swork = p.synlik_workspace(n_set, g.n_real - n_set, M, T, K, 1, dev)
+    sout = p.synlik_outputs(1, K * M, T, dev)
+    yv = out["y_data"].unsqueeze(0).contiguous()
+    t_stats = timed(lambda: p.synlik(bins, M, T, cfg["seed"], y_obs=yv, n_feat=K, work=swork, out=sout))
+    cells = g.n_real * g.G * g.G * g.n_steps
+    return {"workload": "c8: Alg. 6 in Table 1's SCIL setting: FHN 64x64 to T = 100 (102400 Euler steps), "
+                        "N_syn = 1000 runs at theta, N_set = 50, six features (both species), M = 13, fitted "
+                        "power law, n_CIL = 1000 resamples, data = 50 patterns at theta_0",
+            "f_theta_ms": t_total, "evaluations_per_s": 1e3 / t_total,
+            "stages_ms": {"simulate": t_sim, "mcil_s1_s2": t_mcil, "data_vector": t_data,
+                          "bootstrap_stats": t_stats},
+            "simulate_cell_updates_per_s": cells / (t_sim * 1e-3),
+            "status": int(out["status"][0]), "cost_f": float(out["scalars"][1]),
+            "loglik": float(out["scalars"][2]), "m_active": int(out["scalars"][3]),
+            "pairs_exact": [int(x) for x in out["n_exact"].cpu()]}
 
 
 def adjoint_c5(p, torch, dev, stream):
@@ -922,63 +1072,78 @@ def cpu_model():
     return None
 
 
-def oracle_sample(cfg, n_steps_sample):
-    """Time the oracle on a bounded sample: all realisations for
-    n_steps_sample Euler steps (scaled to the full step count), plus the full
-    CIL and bootstrap statistics.  Returns (cell-updates/s, seconds, note)."""
+# sizing of the oracle samples only (not a measurement): the FP64 oracle
+# steps about 2e9 cell-updates/s on the GPU machine's 16 host cores
+ORACLE_RATE_GUESS = 2e9
+
+
+def full_cells(cfg):
+    return sum(g["n_real"] * g["G"] * g["G"] * g["n_steps"] for g in cfg["groups"])
+
+
+def oracle_sample(cfg, frac):
+    """Time the oracle on a bounded sample of the whole workload: every group,
+    all its realisations for max(1, round(frac * n_steps)) of its Euler steps
+    (stepping time scaled to the full step count), then the full correlation
+    integral and bootstrap statistics of every group on the stepped fields.
+    Returns (cell-updates/s, seconds spent, description)."""
     import oracle
-    g = cfg["groups"][0]
-    G, n = g["G"], g["n_real"]
-    t0 = time.perf_counter()
-    f0 = oracle.init_fields(g["model"], G, n, g["params"], g["noise"][0], g["noise"][1], g["seed"])
-    f = oracle.step(g["model"], g["params"], g["dt"], n_steps_sample, f0.astype(np.float64))
-    oracle.residual(g["model"], g["params"], f)
-    t_step = time.perf_counter() - t0
-    t1 = time.perf_counter()
-    X = oracle.patterns(f.astype(np.float32), g["species_mask"])
-    o = oracle.cil(X[:cfg["n1"]], X[cfg["n1"]:cfg["n1"] + cfg["n2"]], b=cfg["b"], M=cfg["M"])
-    oracle.synlik(o["bins"], cfg["M"], cfg["T_res"], cfg["seed"], y_obs=o["counts"] / (cfg["n1"] * cfg["n2"]))
-    t_cil = time.perf_counter() - t1
-    full_cells = n * G * G * g["n_steps"]
-    t_full = t_step * (g["n_steps"] / n_steps_sample) + t_cil
-    if n_steps_sample >= g["n_steps"]:
-        note = ("the whole workload: all %d realisations x %d Euler steps + CIL + bootstrap statistics"
-                % (n, g["n_steps"]))
+    t_full = spent = 0.0
+    slices = set()
+    for g in cfg["groups"]:
+        G, n, N = g["G"], g["n_real"], g["n_steps"]
+        ns = N if frac >= 1.0 else max(1, int(round(N * frac)))
+        slices.add((ns, N))
+        t0 = time.perf_counter()
+        f0 = oracle.init_fields(g["model"], G, n, g["params"], g["noise"][0], g["noise"][1], g["seed"])
+        f = oracle.step(g["model"], g["params"], g["dt"], ns, f0.astype(np.float64))
+        oracle.residual(g["model"], g["params"], f)
+        t_step = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        X = oracle.patterns(f.astype(np.float32), g["species_mask"])
+        o = oracle.cil(X[:cfg["n1"]], X[cfg["n1"]:cfg["n1"] + cfg["n2"]], b=cfg["b"], M=cfg["M"])
+        oracle.synlik(o["bins"], cfg["M"], cfg["T_res"], cfg["seed"], y_obs=o["counts"] / (cfg["n1"] * cfg["n2"]))
+        t_cil = time.perf_counter() - t1
+        t_full += t_step * (N / ns) + t_cil
+        spent += t_step + t_cil
+    ng = len(cfg["groups"])
+    steps_txt = ", ".join("%d of %d" % sl for sl in sorted(slices))
+    if frac >= 1.0:
+        note = "the whole workload: every group (%d) x all realisations x all Euler steps + CIL + bootstrap " \
+               "statistics" % ng
     else:
-        note = ("all %d realisations x %d of %d Euler steps (stepping time scaled by %.0fx) + full CIL "
-                "and bootstrap statistics" % (n, n_steps_sample, g["n_steps"], g["n_steps"] / n_steps_sample))
-    return full_cells / t_full, t_step + t_cil, note
+        note = ("every group (%d), all realisations x %s Euler steps (stepping time scaled to the full step "
+                "count) + the full CIL and bootstrap statistics of every group" % (ng, steps_txt))
+    return full_cells(cfg) / t_full, spent, note
 
 
 def run_reference(args):
     import oracle
     cfg = W.config(args.config)
-    # each step is the whole workload (about 5 s on 16 cores) while the run
-    # stays within a few minutes; beyond 20 steps a proportional sample
-    n_full = cfg["groups"][0]["n_steps"]
-    n_sample = n_full if args.steps + args.warmup <= 20 else max(1000, n_full * 20 // (args.steps + args.warmup))
-    oracle_sample(cfg, 10)           # warm (builds the library)
-    vals, secs = [], 0.0
+    # each step a bounded sample, sized so that warm-up and timed steps
+    # together stay within about 150 s of CPU work
+    per_step = 150.0 / (args.steps + args.warmup + 1)
+    frac = min(1.0, per_step * ORACLE_RATE_GUESS / full_cells(cfg))
+    oracle_sample(W.config("c1", steps_scale=0.01), 1.0)      # warm (builds the library)
+    vals = []
+    note = ""
     for _ in range(args.warmup):
-        oracle_sample(cfg, n_sample)
+        oracle_sample(cfg, frac)
     for _ in range(args.steps):
-        v, s, note = oracle_sample(cfg, n_sample)
+        v, _, note = oracle_sample(cfg, frac)
         vals.append(v)
-        secs += s
     value = statistics.mean(vals)
     cores = oracle.threads()
-    g = cfg["groups"][0]
     return {
         "impl": "reference",
         "metric": "RD cell-updates/s + CIL pair-dists/s at stated tol; % HBM/tensor roofline",
         "value": value, "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": g["n_real"] * g["G"] ** 2 * g["n_steps"] / value * 1e3,
+        "warmup": args.warmup, "ms_per_step": full_cells(cfg) / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "c2: FHN 64x64, 2 sets x 64 realisations, 10^4 Euler steps, "
-                               "u-only d=4096, M=16, b=1.3, 200 resamples"},
+        "config": config_json(args.config, cfg),
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": note},
+                         "sample": note, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -1034,6 +1199,15 @@ def main():
         pk, src = peaks()
         print(json.dumps(imex_bench(p, torch, dev, torch.cuda.current_stream(dev), pk, src)))
         return
+    if args.stepper_only:
+        import torch
+        import paper_2203_14742_b300 as p
+        from paper_2203_14742_b300 import build as B
+        B.build()
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        print(json.dumps(stepper_only(p, torch, dev, args)))
+        return
     if args.gram_large_only:
         import torch
         import paper_2203_14742_b300 as p
@@ -1051,17 +1225,19 @@ def main():
     out = run_ours(args, rank, world, local_rank)
     if rank == 0 and not args.no_cpu_baseline:
         cfg = W.config(args.config)
-        v, secs, note = oracle_sample(cfg, cfg["groups"][0]["n_steps"])
+        # about 15 s of CPU work on all cores, a sixteenth of that on one
+        frac = min(1.0, 15.0 * ORACLE_RATE_GUESS / full_cells(cfg))
+        v, secs, note = oracle_sample(cfg, frac)
         import oracle
         cores = oracle.threads()
-        # one thread, on a sixteenth of the steps (stepping time scaled)
-        oracle.set_threads(1)
-        v1, secs1, note1 = oracle_sample(cfg, max(1, cfg["groups"][0]["n_steps"] // 16))
-        oracle.set_threads(cores)
         out["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": cores,
                                "kind": "oracle", "sample": note + " (%.1f s of CPU work)" % secs,
-                               "one_thread": {"value": v1, "sample": note1 + " (%.1f s)" % secs1},
                                "cpu_model": cpu_model()}
+        if len(cfg["groups"]) == 1:   # one thread on a sixteenth of the sample (single-group workloads)
+            oracle.set_threads(1)
+            v1, secs1, note1 = oracle_sample(cfg, frac / 16)
+            oracle.set_threads(cores)
+            out["cpu_baseline"]["one_thread"] = {"value": v1, "sample": note1 + " (%.1f s)" % secs1}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
