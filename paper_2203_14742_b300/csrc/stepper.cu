@@ -141,14 +141,16 @@ rd_resident_kernel(float *__restrict__ fields, int64_t field_offset, int64_t ste
 // ---------------------------------------------------------------------------
 // One realisation r of a group, by a whole CTA of Tiling<G,TY,TX>::NT
 // threads; sm = the halo ring (Tiling::SMEM bytes).
-template <int MODEL, int G, int TY, int TX>
+// sy: the threads that run this realisation (the whole CTA, or one half of
+// a 512-thread CTA in the persistent launch), Tiling::NT of them.
+template <int MODEL, int G, int TY, int TX, class Sync = SyncAll>
 __device__ __forceinline__ void run_scalar(float *__restrict__ fields, int64_t field_offset, int r, int64_t steps,
                                            const CoefF &cf, double p0, double p1, double p2, double p3,
                                            double *__restrict__ residual, uint32_t *__restrict__ status,
-                                           float *sm) {
+                                           float *sm, Sync sy = Sync{}) {
     using T = Tiling<G, TY, TX>;
     constexpr int NX = T::NX;
-    const int tid = threadIdx.x;
+    const int tid = sy.tid();
     const int tx = tid % NX, ty = tid / NX;
     float *base = fields + field_offset + (int64_t)r * 2 * G * G;
     float u[TY][TX], v[TY][TX];
@@ -158,12 +160,12 @@ __device__ __forceinline__ void run_scalar(float *__restrict__ fields, int64_t f
     for (int64_t n = 0; n < steps; ++n) {
         float *hb = sm + (int)(n & 1) * (T::HALO_FLOATS / 2);
         halo_put<G, TY, TX>(hb, tx, ty, u, v);
-        __syncthreads();
+        sy.sync();
         tile_step_s<MODEL, G, TY, TX>(hb, tx, ty, src, u, v, cf);
     }
     tile_from_state<MODEL, TY, TX>(u, v, cf);
     tile_store_s<G, TY, TX>(base, tx, ty, u, v);
-    residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, sm);
+    residual_from_global<MODEL, G, Sync>(base, p0, p1, p2, p3, residual, status, r, sm, sy);
 }
 
 template <int MODEL, int G, int TY, int TX>
@@ -298,12 +300,14 @@ rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int
 
 // ---------------------------------------------------------------------------
 // Persistent batched stepper: one launch for a whole mixed batch (several
-// parameter groups, models and grid sizes).  Every CTA has 256 threads and
-// loops: take the next (group, realisation) item from a global queue
-// (items ordered longest first), integrate it to the end, repeat.  The tile
-// shape per grid size keeps 256 threads for every item type (G = 32: 2x2,
-// 64: 4x4, 128: 8x8), and the per-node arithmetic is the same as in the
-// per-group kernels, so results are bit-identical to them.
+// parameter groups, models and grid sizes).  Every CTA has 512 threads and
+// loops: take the next work unit from a global queue (units ordered
+// longest first), integrate it to the end, repeat.  A unit is one 128x128
+// realisation on all 512 threads (8x4 tiles), or two realisations of 64x64
+// (4x4 tiles) or 32x32 (2x2 tiles) side by side, one per half of the CTA
+// (256 threads, named barrier 1 + half), so every SM keeps 16 warps.  The
+// per-node arithmetic is the same as in the per-group kernels, so results
+// are bit-identical to them.
 // ---------------------------------------------------------------------------
 struct BatchGroup {
     CoefF cf;
@@ -311,51 +315,76 @@ struct BatchGroup {
     int64_t field_offset, n_steps, real_base;
     int32_t model, G, n_real, pad;
 };
-struct BatchItem {
-    int32_t group, real;
+struct BatchUnit {
+    int32_t group[2], real[2];   // group[1] = -1: the second half has no item (or a 128^2 unit)
 };
 
-constexpr int BATCH_THREADS = 256;
-constexpr size_t BATCH_SMEM = Tiling<128, 8, 8>::SMEM;   // largest halo ring of the three shapes
-static_assert(Tiling<32, 2, 2>::NT == BATCH_THREADS && Tiling<64, 4, 4>::NT == BATCH_THREADS &&
-                  Tiling<128, 8, 8>::NT == BATCH_THREADS, "batch tile shapes must use 256 threads");
-static_assert(Tiling<32, 2, 2>::SMEM <= BATCH_SMEM && Tiling<64, 4, 4>::SMEM <= BATCH_SMEM, "halo ring");
+constexpr int BATCH_THREADS = 512;
+constexpr size_t BATCH_HALF_FLOATS = Tiling<64, 4, 4>::HALO_FLOATS;   // one half's halo ring
+constexpr size_t BATCH_SMEM = Tiling<128, 8, 4>::SMEM;                // = both halves' rings
+static_assert(Tiling<128, 8, 4>::NT == BATCH_THREADS && Tiling<64, 4, 4>::NT == BATCH_THREADS / 2 &&
+                  Tiling<32, 2, 2>::NT == BATCH_THREADS / 2, "batch tile shapes");
+static_assert(2 * Tiling<64, 4, 4>::SMEM <= BATCH_SMEM && Tiling<32, 2, 2>::SMEM <= Tiling<64, 4, 4>::SMEM,
+              "halo rings");
 
 template <int MODEL>
-__device__ __forceinline__ void batch_item(float *fields, const BatchGroup &g, int r, int64_t steps, double *res,
+__device__ __forceinline__ void batch_full(float *fields, const BatchGroup &g, int r, int64_t steps, double *res,
                                            uint32_t *status, float *sm) {
-    switch (g.G) {
-        case 32: run_scalar<MODEL, 32, 2, 2>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2], g.p[3],
-                                             res, status, sm); break;
-        case 64: run_scalar<MODEL, 64, 4, 4>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2], g.p[3],
-                                             res, status, sm); break;
-        default: run_scalar<MODEL, 128, 8, 8>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2],
-                                              g.p[3], res, status, sm); break;
-    }
+    run_scalar<MODEL, 128, 8, 4>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2], g.p[3], res,
+                                 status, sm, SyncAll{});
+}
+
+template <int MODEL>
+__device__ __forceinline__ void batch_half(float *fields, const BatchGroup &g, int r, int64_t steps, double *res,
+                                           uint32_t *status, float *sm, SyncHalf sy) {
+    if (g.G == 64)
+        run_scalar<MODEL, 64, 4, 4>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2], g.p[3], res,
+                                    status, sm, sy);
+    else
+        run_scalar<MODEL, 32, 2, 2>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2], g.p[3], res,
+                                    status, sm, sy);
 }
 
 __global__ void __launch_bounds__(BATCH_THREADS, 1)
-rd_batch_kernel(float *__restrict__ fields, const BatchGroup *__restrict__ groups, const BatchItem *__restrict__ items,
-                int n_items, unsigned int *__restrict__ head, int64_t steps_override, double *__restrict__ residual,
+rd_batch_kernel(float *__restrict__ fields, const BatchGroup *__restrict__ groups, const BatchUnit *__restrict__ units,
+                int n_units, unsigned int *__restrict__ head, int64_t steps_override, double *__restrict__ residual,
                 uint32_t *__restrict__ status) {
     extern __shared__ float4 smem_f4[];
     float *sm = reinterpret_cast<float *>(smem_f4);
-    __shared__ int s_item;
+    __shared__ int s_unit;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        if (threadIdx.x == 0) s_unit = (int)atomicAdd(head, 1u);
         __syncthreads();
-        const int it = s_item;
+        const int it = s_unit;
         __syncthreads();
-        if (it >= n_items) break;
-        const BatchItem w = items[it];
-        const BatchGroup g = groups[w.group];
-        const int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
-        double *res = residual ? residual + 2 * g.real_base : nullptr;
-        switch (g.model) {
-            case RD_FHN: batch_item<RD_FHN>(fields, g, w.real, steps, res, status, sm); break;
-            case RD_GM: batch_item<RD_GM>(fields, g, w.real, steps, res, status, sm); break;
-            case RD_BZ: batch_item<RD_BZ>(fields, g, w.real, steps, res, status, sm); break;
-            default: batch_item<RD_DIFF>(fields, g, w.real, steps, res, status, sm); break;
+        if (it >= n_units) break;
+        const BatchUnit w = units[it];
+        const BatchGroup g0 = groups[w.group[0]];
+        if (g0.G == 128) {
+            const int64_t steps = steps_override >= 0 ? steps_override : g0.n_steps;
+            double *res = residual ? residual + 2 * g0.real_base : nullptr;
+            switch (g0.model) {
+                case RD_FHN: batch_full<RD_FHN>(fields, g0, w.real[0], steps, res, status, sm); break;
+                case RD_GM: batch_full<RD_GM>(fields, g0, w.real[0], steps, res, status, sm); break;
+                case RD_BZ: batch_full<RD_BZ>(fields, g0, w.real[0], steps, res, status, sm); break;
+                default: batch_full<RD_DIFF>(fields, g0, w.real[0], steps, res, status, sm); break;
+            }
+        } else {
+            const int h = threadIdx.x >> 8;
+            const int gi = w.group[h];
+            if (gi >= 0) {   // uniform over the half
+                const BatchGroup g = groups[gi];
+                const int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
+                double *res = residual ? residual + 2 * g.real_base : nullptr;
+                float *smh = sm + h * BATCH_HALF_FLOATS;
+                const SyncHalf sy{h};
+                switch (g.model) {
+                    case RD_FHN: batch_half<RD_FHN>(fields, g, w.real[h], steps, res, status, smh, sy); break;
+                    case RD_GM: batch_half<RD_GM>(fields, g, w.real[h], steps, res, status, smh, sy); break;
+                    case RD_BZ: batch_half<RD_BZ>(fields, g, w.real[h], steps, res, status, smh, sy); break;
+                    default: batch_half<RD_DIFF>(fields, g, w.real[h], steps, res, status, smh, sy); break;
+                }
+            }
         }
         __syncthreads();
     }
@@ -363,9 +392,9 @@ rd_batch_kernel(float *__restrict__ fields, const BatchGroup *__restrict__ group
 
 struct BatchPlan {
     BatchGroup *d_groups = nullptr;
-    BatchItem *d_items = nullptr;
+    BatchUnit *d_units = nullptr;
     unsigned int *d_head = nullptr;
-    int n_items = 0;
+    int n_units = 0;
     int n_sm = 148;
 };
 
@@ -386,32 +415,53 @@ static BatchGroup batch_group_of(const GroupDev &g) {
 rd_status batch_plan_create(const GroupDev *groups, int n_groups, void **out) {
     *out = nullptr;
     std::vector<BatchGroup> bg((size_t)n_groups);
-    std::vector<BatchItem> items;
-    std::vector<double> cost;
+    struct Item {
+        int group, real;
+        double cost;
+    };
+    std::vector<Item> items[3];   // by grid side 32, 64, 128
     for (int i = 0; i < n_groups; ++i) {
         const GroupDev &g = groups[i];
         bg[(size_t)i] = batch_group_of(g);
         // streaming groups run on their own launches; the 1-D model is not stepped here
         if (!group_is_resident(g) || g.model == RD_RDODE) continue;
-        for (int r = 0; r < g.n_real; ++r) items.push_back(BatchItem{i, r});
+        const int gi = g.G == 32 ? 0 : (g.G == 64 ? 1 : 2);
+        for (int r = 0; r < g.n_real; ++r) items[gi].push_back(Item{i, r, (double)g.G * g.G * (double)g.n_steps});
     }
-    // longest first: cost ~ G^2 * steps
-    std::stable_sort(items.begin(), items.end(), [&](const BatchItem &a, const BatchItem &b) {
-        const GroupDev &ga = groups[a.group], &gb = groups[b.group];
-        return (double)ga.G * ga.G * (double)ga.n_steps > (double)gb.G * gb.G * (double)gb.n_steps;
-    });
+    // units: a 128^2 item alone, smaller items two by two (longest with
+    // longest), then all units longest first
+    std::vector<std::pair<double, BatchUnit>> units;
+    for (int gi = 0; gi < 3; ++gi) {
+        auto &v = items[gi];
+        std::stable_sort(v.begin(), v.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+        const size_t step = gi == 2 ? 1 : 2;
+        for (size_t k = 0; k < v.size(); k += step) {
+            BatchUnit u{{v[k].group, -1}, {v[k].real, 0}};
+            if (step == 2 && k + 1 < v.size()) {
+                u.group[1] = v[k + 1].group;
+                u.real[1] = v[k + 1].real;
+            }
+            units.push_back({v[k].cost, u});
+        }
+    }
+    std::stable_sort(units.begin(), units.end(),
+                     [](const std::pair<double, BatchUnit> &a, const std::pair<double, BatchUnit> &b) {
+                         return a.first > b.first;
+                     });
+    std::vector<BatchUnit> uv;
+    for (auto &u : units) uv.push_back(u.second);
     BatchPlan *p = new BatchPlan();
-    p->n_items = (int)items.size();
+    p->n_units = (int)uv.size();
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev);
     bool ok = cudaMalloc(&p->d_groups, sizeof(BatchGroup) * bg.size()) == cudaSuccess &&
-              cudaMalloc(&p->d_items, sizeof(BatchItem) * items.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_units, sizeof(BatchUnit) * (uv.empty() ? 1 : uv.size())) == cudaSuccess &&
               cudaMalloc(&p->d_head, sizeof(unsigned int)) == cudaSuccess &&
               cudaMemcpy(p->d_groups, bg.data(), sizeof(BatchGroup) * bg.size(), cudaMemcpyHostToDevice) ==
                   cudaSuccess &&
-              cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice) ==
-                  cudaSuccess;
+              (uv.empty() || cudaMemcpy(p->d_units, uv.data(), sizeof(BatchUnit) * uv.size(),
+                                        cudaMemcpyHostToDevice) == cudaSuccess);
     *out = p;
     return ok ? RD_OK : RD_ERR_OOM;
 }
@@ -429,7 +479,7 @@ void batch_plan_free(void *pp) {
     BatchPlan *p = (BatchPlan *)pp;
     if (!p) return;
     cudaFree(p->d_groups);
-    cudaFree(p->d_items);
+    cudaFree(p->d_units);
     cudaFree(p->d_head);
     delete p;
 }
@@ -438,14 +488,14 @@ rd_status launch_batch(void *pp, float *fields, int64_t steps_override, double *
                        cudaStream_t s) {
     BatchPlan *p = (BatchPlan *)pp;
     if (!p) return RD_ERR_INVALID_ARG;
-    if (p->n_items == 0) return RD_OK;
+    if (p->n_units == 0) return RD_OK;
     {
         rd_status ast = smem_attr(rd_batch_kernel, (int)BATCH_SMEM);
         if (ast) return ast;
     }
     RD_CUDA_TRY(cudaMemsetAsync(p->d_head, 0, sizeof(unsigned int), s));
-    int grid = p->n_sm < p->n_items ? p->n_sm : p->n_items;
-    rd_batch_kernel<<<grid, BATCH_THREADS, BATCH_SMEM, s>>>(fields, p->d_groups, p->d_items, p->n_items, p->d_head,
+    int grid = p->n_sm < p->n_units ? p->n_sm : p->n_units;
+    rd_batch_kernel<<<grid, BATCH_THREADS, BATCH_SMEM, s>>>(fields, p->d_groups, p->d_units, p->n_units, p->d_head,
                                                            steps_override, residual, status);
     note_launch();
     return cuda_status(cudaGetLastError());

@@ -252,22 +252,56 @@ __device__ __forceinline__ void rhs_f64(double u, double v, double nu, double su
     Fv = p[1] * lv + rv;
 }
 
+// Barrier policies for code that one group of threads runs on one
+// realisation: the whole CTA (barrier 0), or one half of a 512-thread CTA
+// (named barrier 1 + h over its 256 threads, so the two halves integrate
+// two realisations independently).
+struct SyncAll {
+    __device__ __forceinline__ int tid() const { return threadIdx.x; }
+    __device__ __forceinline__ int nthreads() const { return blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ int sync_or(int p) const { return __syncthreads_or(p); }
+};
+struct SyncHalf {
+    int h;   // 0 or 1
+    __device__ __forceinline__ int tid() const { return threadIdx.x & 255; }
+    __device__ __forceinline__ int nthreads() const { return 256; }
+    __device__ __forceinline__ void sync() const {
+        asm volatile("bar.sync %0, 256;" ::"r"(1 + h) : "memory");
+    }
+    __device__ __forceinline__ int sync_or(int p) const {
+        int r;
+        asm volatile(
+            "{\n\t.reg .pred q, o;\n\t"
+            "setp.ne.s32 q, %1, 0;\n\t"
+            "bar.red.or.pred o, %2, 256, q;\n\t"
+            "selp.s32 %0, 1, 0, o;\n\t}"
+            : "=r"(r)
+            : "r"(p), "r"(1 + h)
+            : "memory");
+        return r;
+    }
+};
+
 // FP64 steady-state residual of the final state of realisation r, read
 // back from global memory after the block stored it (block-visible after
 // the barrier): max |F| and sqrt(mean F^2) over both species, F from the
 // stored FP32 values in the plain operation order.  Thread t takes nodes
 // t, t + NT, ...; the sum is reduced with warp shuffles, then across warps.
-template <int MODEL, int G>
+// sy: the threads that integrate this realisation (barrier policy above).
+template <int MODEL, int G, class Sync = SyncAll>
 __device__ __forceinline__ void residual_from_global(const float *__restrict__ base, double p0, double p1, double p2,
                                                      double p3, double *__restrict__ residual,
-                                                     uint32_t *__restrict__ status, int r, void *smem) {
-    __syncthreads();
+                                                     uint32_t *__restrict__ status, int r, void *smem,
+                                                     Sync sy = Sync{}) {
+    sy.sync();
     const double p[4] = {p0, p1, p2, p3};
     const double h2 = (double)(G - 1) * (double)(G - 1);
     const float *u = base, *v = base + G * G;
+    const int tid = sy.tid(), nt = sy.nthreads();
     double mx = 0.0, ss = 0.0;
     bool bad = false;
-    for (int k = threadIdx.x; k < G * G; k += blockDim.x) {
+    for (int k = tid; k < G * G; k += nt) {
         const int y = k / G, x = k - y * G;
         const int kn = (y > 0 ? k - G : k), ks = (y < G - 1 ? k + G : k);
         const int kw = (x > 0 ? k - 1 : k), ke = (x < G - 1 ? k + 1 : k);
@@ -282,12 +316,12 @@ __device__ __forceinline__ void residual_from_global(const float *__restrict__ b
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         ss += __shfl_xor_sync(0xffffffffu, ss, o);
     }
-    const int anybad = __syncthreads_or(bad ? 1 : 0);
+    const int anybad = sy.sync_or(bad ? 1 : 0);
     double *red = reinterpret_cast<double *>(smem);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     if (lane == 0) { red[warp] = mx; red[nw + warp] = ss; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    sy.sync();
+    if (tid == 0) {
         double m = 0.0, s = 0.0;
         for (int wi = 0; wi < nw; ++wi) { m = fmax(m, red[wi]); s += red[nw + wi]; }
         if (anybad) {
@@ -300,7 +334,7 @@ __device__ __forceinline__ void residual_from_global(const float *__restrict__ b
             residual[2 * r + 1] = sqrt(s / (double)(2 * G * G));
         }
     }
-    __syncthreads();
+    sy.sync();
 }
 
 template <int MODEL, int TY, int TX>
