@@ -184,6 +184,18 @@ __device__ __forceinline__ void from_state(float &u, float &v, const CoefF &c) {
     if (MODEL == RD_GM || MODEL == RD_BZ) { u += c.u0; v += c.v0; }
 }
 
+// x / y for the GM kinetics: x times the hardware approximate reciprocal of
+// y (PTX rcp.approx.ftz.f32; the ISA bounds its error by one unit in the
+// last place, subnormals flushed).  y is the inhibitor concentration, about
+// 1/mu^2, far from both ends of the FP32 range.  Every explicit GM stepper
+// path uses it, so they stay bit-identical to one another; the FP32 field
+// tolerance against the FP64 oracle covers its rounding.
+__device__ __forceinline__ float quot_fast(float x, float y) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+    return x * r;
+}
+
 // One explicit Euler update of a node given the neighbour sums
 // su = (N + S) + (W + E) of both species (of the state registers; the
 // Laplacian of a deviation equals that of the field):
@@ -206,7 +218,7 @@ __device__ __forceinline__ void euler_cell(float u, float v, float su, float sv,
         const float a = u, b = v;
         float U = a + c.u0, V = b + c.v0;
         float t = fmaf(-c.k3, b, a + c.e0);
-        float f = __fdividef(U * t, V);
+        float f = quot_fast(U * t, V);
         un = fmaf(c.cu, fmaf(-4.f, a, su), fmaf(c.k2, f, a));
         vn = fmaf(c.be, b, fmaf(c.k2 * a, a + c.tu0, fmaf(c.cv, sv, c.k2e1)));
     } else if (MODEL == RD_BZ) {
@@ -569,7 +581,7 @@ __device__ __forceinline__ float2 euler2(float2 C, float2 S, const CoefF &c) {
         const float a = C.x, b = C.y;
         float U = a + c.u0, V = b + c.v0;
         float t = fmaf(-c.k3, b, a + c.e0);
-        float f = __fdividef(U * t, V);
+        float f = quot_fast(U * t, V);
         return make_float2(fmaf(c.cu, fmaf(-4.f, a, S.x), fmaf(c.k2, f, a)),
                            fmaf(c.be, b, fmaf(c.k2 * a, a + c.tu0, fmaf(c.cv, S.y, c.k2e1))));
     } else if (MODEL == RD_BZ) {
