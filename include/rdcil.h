@@ -344,9 +344,11 @@ int32_t rd_rkc_get_variant(int32_t G);
  * rd_n_variants: number of variants (indices 0..n-1, 0 = default).
  * rd_set_variant / rd_get_variant: choose / read the variant of (model, G).
  * rd_variant_shape: the tile shape of variant `variant` at grid side G
- *   (32, 64 or 128): shape = host int32[3] receiving {packed (1 = float2
- *   (u, v) tiles, 0 = separate u and v tiles), TY, TX}.  RD_ERR_INVALID_ARG
- *   for an unknown G or variant or a null shape.
+ *   (32, 64 or 128): shape = host int32[3] receiving {kind (0 = separate u
+ *   and v tiles, 1 = float2 (u, v) tiles, 2 = separate tiles kept in TY + 1
+ *   rotating row slots, which saves a register copy per node and step),
+ *   TY, TX}.  RD_ERR_INVALID_ARG for an unknown G or variant or a null
+ *   shape.
  * rd_autotune: time every variant on the largest group of each (model, G)
  *   class present in h for `steps` Euler steps, keep the fastest (and, if
  *   h holds streaming groups, the fastest temporal depth on the largest of

@@ -471,6 +471,74 @@ __device__ __forceinline__ void tile_step_s(const float *hb, int tx, int ty, int
     }
 }
 
+// ---------------------------------------------------------------------------
+// Rotating serpentine tiles.  Updating a tile in place keeps every old row
+// alive until the row below it is done (it is that row's north neighbour),
+// which costs a register copy of every node per step.  Here the TY rows live
+// in R = TY + 1 row slots: logical row i in slot (i + OFF) mod R, one slot
+// free.  New row i is written into the slot of old row i - 1 (the free slot
+// for row 0), node by node right after that node's north value was read, so
+// nothing is copied; the mapping moves by one slot per step (OFF -> OFF - 1
+// mod R) and the caller unrolls R steps so that every slot index is a
+// compile-time constant.  Per node the arithmetic and its order are those of
+// tile_step_s, so the fields are bit-identical.
+// ---------------------------------------------------------------------------
+template <int G, int TY, int TX, int OFF>
+__device__ __forceinline__ void halo_put_rot(float *hb, int tx, int ty, const float (&u)[TY + 1][TX],
+                                             const float (&v)[TY + 1][TX]) {
+    constexpr int NY = Tiling<G, TY, TX>::NY, R = TY + 1;
+    const int x0 = tx * TX;
+    st_row<TX>(hb + ((0 * 2 + 0) * NY + ty) * G + x0, u[OFF % R]);
+    st_row<TX>(hb + ((0 * 2 + 1) * NY + ty) * G + x0, u[(TY - 1 + OFF) % R]);
+    st_row<TX>(hb + ((1 * 2 + 0) * NY + ty) * G + x0, v[OFF % R]);
+    st_row<TX>(hb + ((1 * 2 + 1) * NY + ty) * G + x0, v[(TY - 1 + OFF) % R]);
+}
+
+template <int MODEL, int G, int TY, int TX, int OFF>
+__device__ __forceinline__ void tile_step_rot(const float *hb, int tx, int ty, int src, float (&u)[TY + 1][TX],
+                                              float (&v)[TY + 1][TX], const CoefF &cf) {
+    constexpr int NY = Tiling<G, TY, TX>::NY, R = TY + 1;
+    const int x0 = tx * TX;
+    float nu0[TX], nv0[TX];   // north neighbours of row 0: halo, or the row itself at the top edge
+    if (ty > 0) {
+        ld_row<TX>(hb + ((0 * 2 + 1) * NY + ty - 1) * G + x0, nu0);
+        ld_row<TX>(hb + ((1 * 2 + 1) * NY + ty - 1) * G + x0, nv0);
+    } else {
+#pragma unroll
+        for (int c = 0; c < TX; ++c) { nu0[c] = u[OFF % R][c]; nv0[c] = v[OFF % R][c]; }
+    }
+#pragma unroll
+    for (int i = 0; i < TY; ++i) {
+        const int pr = (i + OFF) % R;            // old row i
+        const int qr = (i + OFF + R - 1) % R;    // old row i - 1 (free slot for i = 0): receives new row i
+        const int sr = (i + 1 + OFF) % R;        // old row i + 1
+        float sl_u[TX], sl_v[TX];                // south neighbours of the last row
+        if (i == TY - 1) {
+            if (ty < NY - 1) {
+                ld_row<TX>(hb + ((0 * 2 + 0) * NY + ty + 1) * G + x0, sl_u);
+                ld_row<TX>(hb + ((1 * 2 + 0) * NY + ty + 1) * G + x0, sl_v);
+            } else {
+#pragma unroll
+                for (int c = 0; c < TX; ++c) { sl_u[c] = u[pr][c]; sl_v[c] = v[pr][c]; }
+            }
+        }
+        const float xu0 = __shfl_xor_sync(0xffffffffu, u[pr][0], 1);
+        const float xv0 = __shfl_xor_sync(0xffffffffu, v[pr][0], 1);
+        const float xu1 = __shfl_sync(0xffffffffu, u[pr][TX - 1], src);
+        const float xv1 = __shfl_sync(0xffffffffu, v[pr][TX - 1], src);
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            const float Nu = i == 0 ? nu0[c] : u[qr][c], Nv = i == 0 ? nv0[c] : v[qr][c];
+            const float Su = i == TY - 1 ? sl_u[c] : u[sr][c], Sv = i == TY - 1 ? sl_v[c] : v[sr][c];
+            const float Lu = c > 0 ? u[pr][c - 1] : xu0, Ru = c < TX - 1 ? u[pr][c + 1] : xu1;
+            const float Lv = c > 0 ? v[pr][c - 1] : xv0, Rv = c < TX - 1 ? v[pr][c + 1] : xv1;
+            const float nu = (Nu + Su) + (Lu + Ru);
+            const float nv = (Nv + Sv) + (Lv + Rv);
+            euler_cell<MODEL>(u[pr][c], v[pr][c], nu, nv, cf, u[qr][c], v[qr][c]);
+        }
+    }
+}
+
 }  // namespace rdcil
 
 // ===========================================================================
