@@ -58,7 +58,7 @@ FP32_INST_PER_CELL = {W.FHN: 15, W.GM: 20, W.DIFF: 10, W.BZ: 22}
 # the full launch's traffic.
 STEPPER_TRAFFIC = {
     "c2": {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488, "7c8c62601c860730": 4223488},
-    "c4": {},
+    "c4": {"250da058b95b29c7": 1285591296},
 }
 STEPPER_SOURCES = ["paper_2203_14742_b300/csrc/stepper.cu", "paper_2203_14742_b300/csrc/tile.cuh",
                    "paper_2203_14742_b300/csrc/common.cuh"]
@@ -563,7 +563,30 @@ def c2_bench(p, torch, dev, stream, pk, src, reps=5):
     ach = inst / (k_ms * 1e-3) / 1e12
     pk_, ty_, tx_ = p.variant_shape(g.G, variant)
     traffic, tsrc = stepper_traffic("c2") if variant == 0 else (None, "no ncu capture of this tile variant")
+    # accuracy against the oracle: the fields of two realisations after the
+    # full step count (FP64 oracle from the same FP32 initial state; per
+    # realisation and species max |a - b| / max |b|), and the correlation
+    # integral recomputed by the oracle on the GPU's own fields
+    import oracle
+    sim.reinit()
+    w0 = sim.group_fields(0)[:2].cpu().numpy().astype(np.float64)
+    _check_int(p, sim, pipe)
+    for (X1, X2), o in zip(pipe.views, pipe.cil_out):
+        p.cil(X1, X2, b=cfg["b"], M=cfg["M"], work=pipe.work, out=o)
+    torch.cuda.synchronize()
+    wg = sim.group_fields(0)[:2].cpu().numpy().astype(np.float64).reshape(2, 2, -1)
+    wo = oracle.step(g.model, g.params[:4], g.dt, g.n_steps, w0).reshape(2, 2, -1)
+    field_err = float((np.abs(wg - wo).max(-1) / np.abs(wo).max(-1)).max())
+    X1, X2 = pipe.views[0]
+    oc = oracle.cil(X1.cpu().numpy(), X2.cpu().numpy(), b=cfg["b"], M=cfg["M"])
+    cil_exact = bool(np.array_equal(pipe.cil_out[0]["counts"].cpu().numpy(), oc["counts"]) and
+                     float(pipe.cil_out[0]["radii"][0]) == oc["R0"] and
+                     np.array_equal(pipe.cil_out[0]["radii"][1:].cpu().numpy(), oc["radii"]))
     return {"workload": WORKLOADS["c2"], "ms_per_step": step_ms, "cell_updates_per_s": cells / (step_ms * 1e-3),
+            "accuracy": {"field_rel_err_2_realisations": field_err, "field_tolerance": 1e-5,
+                         "cil_radii_counts_equal_oracle": cil_exact,
+                         "note": "fields: FP32 GPU vs FP64 oracle after 10^4 steps from the same initial state; "
+                                 "CIL: the oracle's exact counts on the GPU's fields"},
             "stepper_ms": k_ms, "stepper_variant": variant,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tinst/s", "frac": ach / peak,
                          "traffic": traffic, "traffic_source": tsrc,
