@@ -14,13 +14,14 @@ def _mode(G, p, q):
     return np.outer(np.cos(q * x), np.cos(p * x))   # [y][x]: p along x, q along y
 
 
-@pytest.mark.parametrize("G", [8, 12])
+@pytest.mark.parametrize("G", [8, 12, 128])
 def test_cosine_modes_decay_by_the_closed_form_factor(G):
     """Pure diffusion: the cosine modes cos(pi p (x+1/2)/G) cos(pi q (y+1/2)/G)
     are the eigenvectors of the mirrored-ghost Laplacian with eigenvalue
     -(G-1)^2 (4 sin^2(pi p/2G) + 4 sin^2(pi q/2G)), so one implicit step
     divides each by 1 + dt D (G-1)^2 (...).  Fixes the ghost rule, the
-    (G-1)^2 scaling and the sign of the implicit term."""
+    (G-1)^2 scaling and the sign of the implicit term; G = 128 runs the
+    sparse factorisation."""
     D = (0.003, 0.02)
     dt = 0.01
     for (p, q) in ((0, 0), (1, 0), (0, 3), (2, 5), (G - 1, G - 1)):
@@ -86,3 +87,31 @@ def test_first_order_agreement_with_explicit_euler():
         gaps.append(abs(a - b).max())
     for g0, g1 in zip(gaps, gaps[1:]):
         assert 3.6 < g0 / g1 < 4.4, gaps
+
+
+@pytest.mark.parametrize("G", [5, 9])
+def test_sparse_and_dense_operators_are_the_same_matrix(G):
+    """The sparse assembly holds exactly the dense matrix's entries, each row
+    sums to zero (Neumann: constants are in the kernel) and the matrix is
+    symmetric."""
+    dense = I.laplacian_matrix(G)
+    sparse = I.laplacian_sparse(G).toarray()
+    np.testing.assert_array_equal(sparse, dense)
+    np.testing.assert_array_equal(dense.sum(axis=1), np.zeros(G * G))
+    np.testing.assert_array_equal(dense, dense.T)
+    # interior row: the 5-point stencil scaled by (G-1)^2
+    k = 2 * G + 2
+    g2 = (G - 1) ** 2
+    assert dense[k, k] == -4 * g2
+    assert sorted(dense[k][dense[k] > 0].tolist()) == [g2] * 4
+
+
+def test_sparse_and_dense_solves_agree():
+    """The two factorisations of the same step give the same fields to FP64
+    rounding."""
+    G = 12
+    p = (2.8e-4, 0.05, 10.0, 0.95)
+    w0 = O.init_fields(O.FHN, G, 2, p, -0.05, 0.05, 41).astype(np.float64)
+    a = I.imex_run(O.FHN, p, 0.02, 5, w0, sparse=False)
+    b = I.imex_run(O.FHN, p, 0.02, 5, w0, sparse=True)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
