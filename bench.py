@@ -846,7 +846,34 @@ def imex_bench(p, torch, dev, stream, pk, src, dts=(2 ** -6, 2 ** -5, 2 ** -4)):
                           "imex_residual_max": float(res_i[:, 0].max()),
                           "same_pattern_1e-3": int((dif < 1e-3).sum()), "realisations": nl,
                           "rel_diff_median": float(np.median(dif))})
+    # G = 128 (one 4-CTA cluster per realisation): the GM 128x128 workload
+    # c3 (512 realisations) to its horizon, against its explicit Euler run
+    # (dt 2^-10, accurate to about 1e-5 there)
+    gc3 = W.config("c3")["groups"][0]
+    T3 = gc3["dt"] * gc3["n_steps"]
+    s3 = p.Simulation([p.Group.from_dict(gc3)], device=dev)
+    t_e3, _ = timed(s3, lambda: s3.integrate(residual=False), reps=1)
+    assert s3.sync_status() == 0
+    fe3 = s3.group_fields(0).cpu().numpy().astype(np.float64)
+    n3 = gc3["n_real"]
+    g128 = []
+    for dt in (2 ** -6, 2 ** -4):
+        steps = int(round(T3 / dt))
+        si = p.Simulation([p.Group.from_dict(dict(gc3, dt=dt, n_steps=steps))], device=dev)
+        t, res = timed(si, lambda: si.integrate_imex(residual=True), reps=2)
+        assert si.sync_status() == 0
+        fi = si.group_fields(0).cpu().numpy().astype(np.float64)
+        dif = (np.abs(fe3 - fi).reshape(n3, 2, -1).max(-1) / np.abs(fe3).reshape(n3, 2, -1).max(-1)).max(-1)
+        fma = 4.0 * 128 ** 3 * n3 * steps
+        g128.append({"dt": dt, "steps": steps, "ms": t * 1e3, "us_per_step": t * 1e6 / steps,
+                     "product_tfma_per_s": fma / t / 1e12, "fma_frac": fma / t / 1e12 / fma_peak,
+                     "speedup_vs_euler": t_e3 / t, "rel_diff_vs_euler_median": float(np.median(dif)),
+                     "rel_diff_vs_euler_max": float(dif.max()), "residual_max": float(res[:, 0].max())})
+    c3_128 = {"workload": "GM 128x128, 512 realisations (c3), 0 -> T = 2*10^4 x 2^-10",
+              "kernel": "one 4-CTA cluster per realisation",
+              "euler": {"ms": t_e3 * 1e3, "steps": gc3["n_steps"], "dt": gc3["dt"]}, "rows": g128}
     return {"workload": "FHN 64x64, 2 x 64 realisations, 0 -> T = 10^4 x 2^-10 (the c2 horizon)",
+            "g128": c3_128,
             "t100": long_runs,
             "variant": p.imex_get_variant(G),
             "euler": {"ms": t_eul * 1e3, "steps": gd["n_steps"], "dt": gd["dt"], "rel_err_sample": err_eul},

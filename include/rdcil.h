@@ -139,7 +139,7 @@ rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_fields,
  * group list (host-only; no GPU needed): the stabilised RK2 coefficients
  * and stability bounds when some group can run rd_integrate_rkc (about
  * 1 MB), and the cosine-basis tables of rd_integrate_imex per grid side
- * 32 or 64 present.  rd_init allocates and fills them once, on the current
+ * 32, 64 or 128 present.  rd_init allocates and fills them once, on the current
  * device, so rd_integrate_rkc and rd_integrate_imex allocate nothing and
  * never synchronise (safe inside stream capture from the first call).
  * RD_ERR_INVALID_ARG as rd_init for an invalid group list.
@@ -301,9 +301,12 @@ rd_status rd_integrate_rkc(rd_handle *h, float *d_fields, const rd_rkc_opts *opt
  * cosine (DCT-II) basis that diagonalises L_h, so dt is not bound by the
  * diffusive limit h^2 / (4 D) (the reaction still bounds it).
  * d_fields as for rd_integrate_batch; d_residual (nullable) as for
- * rd_integrate_batch, of the final state.  One CTA per realisation, groups
- * in order on `stream`.  Models RD_FHN, RD_GM, RD_DIFF, RD_BZ on G = 32 or
- * 64; RD_ERR_UNSUPPORTED (nothing launched) for any other group in h.  A
+ * rd_integrate_batch, of the final state.  One CTA per realisation at
+ * G = 32 and 64; at G = 128 one cluster of four CTAs per realisation (rows
+ * split four ways, the transforms along y through distributed shared
+ * memory).  Groups in order on `stream`.  Models RD_FHN, RD_GM, RD_DIFF,
+ * RD_BZ on G = 32, 64 or 128; RD_ERR_UNSUPPORTED (nothing launched) for
+ * any other group in h.  A
  * non-finite final state sets RD_ERR_NONFINITE in the status word when a
  * residual is asked for.  Precision: FP32 state and products; the
  * transform tables are formed in FP64 and rounded once. */
@@ -317,9 +320,10 @@ rd_status rd_integrate_imex(rd_handle *h, float *d_fields, double *d_residual, v
  * ordered (even, odd) each product is two half-length sums over
  * Y[k] +- Y[G-1-k] (the cosine basis's symmetry), half the FMAs, its own
  * rounding (same tolerance, not bit-identical to 0-3); the default at both
- * G (256 threads at G = 64).  rd_imex_set_variant returns
- * RD_ERR_INVALID_ARG for another G or an unknown variant;
- * rd_imex_get_variant returns -1 for another G. */
+ * G (256 threads at G = 64).  G = 128 has the even/odd cluster kernel
+ * alone (no knob).  rd_imex_set_variant returns RD_ERR_INVALID_ARG for
+ * another G or an unknown variant; rd_imex_get_variant returns -1 for
+ * another G. */
 int32_t rd_imex_n_variants(void);
 rd_status rd_imex_set_variant(int32_t G, int32_t variant);
 int32_t rd_imex_get_variant(int32_t G);

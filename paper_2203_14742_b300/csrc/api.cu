@@ -115,10 +115,10 @@ extern "C" rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_
 // step tables of the handle (formed once in rd_init, on the handle's device)
 // ---------------------------------------------------------------------------
 TableNeeds rdcil::table_needs(const GroupDev *groups, int n_groups) {
-    TableNeeds n{false, {false, false}};
+    TableNeeds n{false, {false, false, false}};
     for (int i = 0; i < n_groups; ++i) {
         n.rkc |= rkc_supported(groups[i]);
-        if (imex_supported(groups[i])) n.imex[groups[i].G == 64] = true;
+        if (imex_supported(groups[i])) n.imex[imex_table_index(groups[i].G)] = true;
     }
     return n;
 }
@@ -127,9 +127,9 @@ static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t rdcil::table_bytes(const TableNeeds &n) {
     size_t b = n.rkc ? up256(rkc_table_bytes()) : 0;
-    for (int gi = 0; gi < 2; ++gi)
+    for (int gi = 0; gi < 3; ++gi)
         if (n.imex[gi]) {
-            const int G = gi ? 64 : 32;
+            const int G = 32 << gi;
             b += up256(sizeof(float) * imex_table_floats(G)) + up256(sizeof(float) * imex_eo_table_floats(G));
         }
     return b;
@@ -142,6 +142,7 @@ rd_status rdcil::tables_create(Handle &h, cudaStream_t s) {
     if (bytes == 0) return RD_OK;
     char *base = nullptr;
     if (cudaMalloc(&base, bytes) != cudaSuccess) return RD_ERR_OOM;
+    h.d_tables = base;
     h.table_bytes = bytes;
     size_t off = 0;
     if (n.rkc) {
@@ -151,11 +152,12 @@ rd_status rdcil::tables_create(Handle &h, cudaStream_t s) {
         rd_status st = rkc_tables_fill(h.d_rkc_tab, h.d_rkc_beta, s);
         if (st) return st;
     }
-    for (int gi = 0; gi < 2; ++gi) {
+    for (int gi = 0; gi < 3; ++gi) {
         if (!n.imex[gi]) continue;
-        const int G = gi ? 64 : 32;
-        h.d_imex_tab[gi] = (float *)(base + off);
-        off += up256(sizeof(float) * imex_table_floats(G));
+        const int G = 32 << gi;
+        const size_t full = sizeof(float) * imex_table_floats(G);
+        h.d_imex_tab[gi] = full ? (float *)(base + off) : nullptr;
+        off += up256(full);
         h.d_imex_eo_tab[gi] = (float *)(base + off);
         off += up256(sizeof(float) * imex_eo_table_floats(G));
         rd_status st = imex_tables_fill(G, h.d_imex_tab[gi], h.d_imex_eo_tab[gi], s);
@@ -165,13 +167,11 @@ rd_status rdcil::tables_create(Handle &h, cudaStream_t s) {
 }
 
 void rdcil::tables_release(Handle &h) {
-    // one allocation: the first table in use holds its base
-    void *base = h.d_rkc_tab ? (void *)h.d_rkc_tab
-                             : (h.d_imex_tab[0] ? (void *)h.d_imex_tab[0] : (void *)h.d_imex_tab[1]);
-    if (base) cudaFree(base);
+    if (h.d_tables) cudaFree(h.d_tables);
+    h.d_tables = nullptr;
     h.d_rkc_tab = nullptr;
     h.d_rkc_beta = nullptr;
-    h.d_imex_tab[0] = h.d_imex_tab[1] = h.d_imex_eo_tab[0] = h.d_imex_eo_tab[1] = nullptr;
+    for (int gi = 0; gi < 3; ++gi) h.d_imex_tab[gi] = h.d_imex_eo_tab[gi] = nullptr;
     h.table_bytes = 0;
 }
 
@@ -323,7 +323,7 @@ extern "C" rd_status rd_integrate_imex(rd_handle *hh, float *d_fields, double *d
         if (!imex_supported(h.h_groups[gi])) return RD_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     for (int gi = 0; gi < h.n_groups; ++gi) {
-        const int gi2 = h.h_groups[gi].G == 64;
+        const int gi2 = imex_table_index(h.h_groups[gi].G);
         rd_status st = launch_imex_group(h.h_groups[gi], h.d_imex_tab[gi2], h.d_imex_eo_tab[gi2], d_fields,
                                          d_residual, h.d_status, s);
         if (st != RD_OK) return st;

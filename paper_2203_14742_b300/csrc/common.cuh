@@ -56,14 +56,16 @@ struct Handle {
     float *d_stream_tmp;      // the other HBM buffer of the ping-pong
     double *d_stream_part;    // residual partial sums
     int32_t stream_depth;     // Euler steps fused per launch (1, 2, 4 or 8)
-    // step tables, formed in rd_init on the handle's device (null when no
-    // group can use them): the stabilised RK2 coefficients and stability
-    // bounds, and the cosine-basis tables of the semi-implicit stepper per
-    // G = 32, 64 (full products, even/odd split)
+    // step tables, formed in rd_init on the handle's device in one
+    // allocation at d_tables (null when no group can use them): the
+    // stabilised RK2 coefficients and stability bounds, and the cosine-basis
+    // tables of the semi-implicit stepper per G = 32, 64, 128 (full products,
+    // even/odd split; G = 128 has the even/odd table only)
+    void *d_tables;
     float4 *d_rkc_tab;
     double *d_rkc_beta;
-    float *d_imex_tab[2];
-    float *d_imex_eo_tab[2];
+    float *d_imex_tab[3];
+    float *d_imex_eo_tab[3];
     size_t table_bytes;
 };
 
@@ -71,7 +73,7 @@ struct Handle {
 // them; tables_release frees them).
 struct TableNeeds {
     bool rkc;          // some group can run the stabilised RK2
-    bool imex[2];      // some group can run the semi-implicit stepper at G = 32 / 64
+    bool imex[3];      // some group can run the semi-implicit stepper at G = 32 / 64 / 128
 };
 TableNeeds table_needs(const GroupDev *groups, int n_groups);
 size_t table_bytes(const TableNeeds &n);
@@ -140,6 +142,7 @@ rd_status launch_rkc_group(const GroupDev &g, const float4 *tab, const double *b
                            const rd_rkc_opts &o, int64_t *stats, double *residual,
                            uint32_t *status, cudaStream_t s);
 bool imex_supported(const GroupDev &g);
+int imex_table_index(int G);   // 0, 1, 2 for G = 32, 64, 128; -1 otherwise
 int imex_n_variants();
 bool imex_set_variant(int G, int v);
 int imex_get_variant(int G);

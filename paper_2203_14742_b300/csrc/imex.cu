@@ -42,6 +42,7 @@
 // equilibrium value.
 #include <cmath>
 #include <mutex>
+#include <cooperative_groups.h>
 #include "common.cuh"
 #include "tile.cuh"
 
@@ -276,7 +277,8 @@ rd_imex_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, float
 }
 
 // floats of the full-product table (C, C^T, divisor eigenvalues) at G
-size_t imex_table_floats(int G) { return 2 * (size_t)G * G + G; }
+// (G = 32, 64; the G = 128 cluster kernel uses the even/odd table alone)
+size_t imex_table_floats(int G) { return G == 128 ? 0 : 2 * (size_t)G * G + G; }
 
 // ---------------------------------------------------------------------------
 // Even/odd split.  C[p][G-1-x] = (-1)^p C[p][x], so with the spectrum held in
@@ -555,6 +557,312 @@ rd_imex_eo_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, fl
     residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, sCh);
 }
 
+// ---------------------------------------------------------------------------
+// G = 128: one 4-CTA cluster per realisation.  The even/odd kernel's shared
+// working set at this side (about 600 KB) exceeds one SM, so the grid's rows
+// are split: CTA c of the cluster owns rows y in [32c, 32c + 32) of both
+// species (state, increment) and, for the transforms along y, the spectral
+// columns m in [32c, 32c + 32).  A step:
+//   1. dt F of its rows, from the state and two halo rows, stored x-major;
+//   2. forward along x (local, full rows): Xh[y][m], sent block by block to
+//      the CTA owning column block m / 32 (distributed shared memory), which
+//      gathers all 128 rows of its 32 columns;              cluster barrier
+//   3. forward along y with the divisors (local): Z[q][m];
+//   4. inverse along y (local): Yh[y][m], sent back to the owner of row y,
+//      stored m-major;                                        cluster barrier
+//   5. inverse along x (local), added to the state; the updated edge rows
+//      are written into the neighbours' halo rows;            cluster barrier
+// Every product is the even/odd half-length form of the G <= 64 kernel
+// (same tables, same permuted spectrum), 32 outputs per thread, the two
+// halves of the block on the two species.  Buffer reuse across the barriers:
+// a CTA writes another CTA's K (step 2) only after the barrier that follows
+// the owner's last read of it (step 3 of the previous step), and the same
+// holds for the R buffer (written in 4, read in 5) and the halo rows
+// (written in 5, read in 1); the x-major increment of step 1 and R share
+// one buffer, since R is written only after the barrier that follows step 2.
+// The cluster barriers are hardware barriers that every CTA passes the same
+// number of times (no data-dependent control), and a final barrier keeps
+// every CTA alive until the others' last remote writes are done.
+// ---------------------------------------------------------------------------
+namespace imexcl {
+constexpr int G = 128, CL = 4, RL = G / CL, H = G / 2, LD = G + 4, LDH = H + 4, LDT = RL + 4;
+constexpr int NT = 256, NS = NT / 2;
+constexpr int WBUF = (RL + 2) * LD;   // rows -1 .. RL of one species (halo at both ends)
+constexpr int TBUF = G * LDT;         // 128 rows of 32 (+4) of one species
+constexpr int OFF_CH = 0;                     // Ch[k < H][m], ld LD
+constexpr int OFF_CL = OFF_CH + H * LD;       // Cl[m][y < H], ld LDH
+constexpr int OFF_MU = OFF_CL + G * LDH;      // mu in the permuted order
+constexpr int OFF_W = OFF_MU + G;             // state, 2 species
+constexpr int OFF_XR = OFF_W + 2 * WBUF;      // XT[x][y] (step 1) / R[m][y] (step 4), 2 species
+constexpr int OFF_K = OFF_XR + 2 * TBUF;      // K[y][m - 32c], 2 species
+constexpr int OFF_Z = OFF_K + 2 * TBUF;       // Z[q][m - 32c], 2 species
+constexpr int FLOATS = OFF_Z + 2 * TBUF;
+constexpr size_t SMEM = sizeof(float) * FLOATS;
+static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
+static_assert(OFF_CL % 4 == 0 && OFF_MU % 4 == 0 && OFF_W % 4 == 0 && OFF_XR % 4 == 0 && OFF_K % 4 == 0 &&
+                  OFF_Z % 4 == 0 && WBUF % 4 == 0 && TBUF % 4 == 0,
+              "float4 alignment of every buffer");
+}  // namespace imexcl
+
+// dt F of the four nodes (local row y, x..x+3) of both species, stored
+// x-major into XTu, XTv ([x][y], ld LDT); W rows are offset by the halo row.
+// ns / ss: the north / south neighbour is the node itself (grid edge).
+template <int MODEL>
+__device__ __forceinline__ void cl_incr4(const float *__restrict__ Wu, const float *__restrict__ Wv,
+                                         float *__restrict__ XTu, float *__restrict__ XTv, int y, int x, bool ns,
+                                         bool ss, const CoefF &cf) {
+    using namespace imexcl;
+    const int o = (y + 1) * LD + x, on = ns ? o : o - LD, os = ss ? o : o + LD;
+    float su[4], sv[4], cu[4], cv[4];
+    {
+        const float4 c = *reinterpret_cast<const float4 *>(Wu + o);
+        const float4 n = *reinterpret_cast<const float4 *>(Wu + on);
+        const float4 s = *reinterpret_cast<const float4 *>(Wu + os);
+        const float w = x > 0 ? Wu[o - 1] : c.x, e = x + 4 < G ? Wu[o + 4] : c.w;
+        cu[0] = c.x; cu[1] = c.y; cu[2] = c.z; cu[3] = c.w;
+        su[0] = (n.x + s.x) + (w + c.y);
+        su[1] = (n.y + s.y) + (c.x + c.z);
+        su[2] = (n.z + s.z) + (c.y + c.w);
+        su[3] = (n.w + s.w) + (c.z + e);
+    }
+    {
+        const float4 c = *reinterpret_cast<const float4 *>(Wv + o);
+        const float4 n = *reinterpret_cast<const float4 *>(Wv + on);
+        const float4 s = *reinterpret_cast<const float4 *>(Wv + os);
+        const float w = x > 0 ? Wv[o - 1] : c.x, e = x + 4 < G ? Wv[o + 4] : c.w;
+        cv[0] = c.x; cv[1] = c.y; cv[2] = c.z; cv[3] = c.w;
+        sv[0] = (n.x + s.x) + (w + c.y);
+        sv[1] = (n.y + s.y) + (c.x + c.z);
+        sv[2] = (n.z + s.z) + (c.y + c.w);
+        sv[3] = (n.w + s.w) + (c.z + e);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float du, dv;
+        incr<MODEL>(cu[j], cv[j], su[j], sv[j], cf, du, dv);
+        XTu[(x + j) * LDT + y] = du;
+        XTv[(x + j) * LDT + y] = dv;
+    }
+}
+
+// Forward half-length product over the k-major operand IN (ld LDT, 128
+// rows): acc[i][j] = sum_{k<H} Ch[k][s_i] (IN[k][4b + j] +- IN[G-1-k][4b + j])
+// with s_i = 4a + i (even part, +) and H + 4a + i - 4 (i >= 4, odd part, -).
+__device__ __forceinline__ void cl_fwd(const float *__restrict__ Ch, const float *__restrict__ IN, int a, int b,
+                                       float (&acc)[8][4]) {
+    using namespace imexcl;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 16
+    for (int k = 0; k < H; ++k) {
+        float ae[4], ao[4], y1[4], y2[4];
+        f4a(ae, *reinterpret_cast<const float4 *>(Ch + k * LD + 4 * a));
+        f4a(ao, *reinterpret_cast<const float4 *>(Ch + k * LD + 4 * a + H));
+        f4a(y1, *reinterpret_cast<const float4 *>(IN + k * LDT + 4 * b));
+        f4a(y2, *reinterpret_cast<const float4 *>(IN + (G - 1 - k) * LDT + 4 * b));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float e = y1[j] + y2[j], o = y1[j] - y2[j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[i][j] = fmaf(ae[i], e, acc[i][j]);
+                acc[4 + i][j] = fmaf(ao[i], o, acc[4 + i][j]);
+            }
+        }
+    }
+}
+
+// Inverse half sums: E[i][j] = sum_{k<H} A[k][4a + i] B[k][4b + j],
+// O[i][j] = sum_{k<H} A[k + H][4a + i] B[k + H][4b + j].
+template <int LDA, int LDB>
+__device__ __forceinline__ void cl_inv(const float *__restrict__ A, const float *__restrict__ B, int a, int b,
+                                       float (&E)[4][4], float (&O)[4][4]) {
+    using namespace imexcl;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) E[i][j] = O[i][j] = 0.f;
+#pragma unroll 16
+    for (int k = 0; k < H; ++k) {
+        float a1[4], a2[4], b1[4], b2[4];
+        f4a(a1, *reinterpret_cast<const float4 *>(A + k * LDA + 4 * a));
+        f4a(a2, *reinterpret_cast<const float4 *>(A + (k + H) * LDA + 4 * a));
+        f4a(b1, *reinterpret_cast<const float4 *>(B + k * LDB + 4 * b));
+        f4a(b2, *reinterpret_cast<const float4 *>(B + (k + H) * LDB + 4 * b));
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                E[i][j] = fmaf(a1[i], b1[j], E[i][j]);
+                O[i][j] = fmaf(a2[i], b2[j], O[i][j]);
+            }
+    }
+}
+
+template <int MODEL>
+__global__ void __launch_bounds__(imexcl::NT, 1)
+rd_imex_cl_kernel(float *__restrict__ fields, int64_t field_offset, CoefF cf, float a_u, float a_v,
+                  const float *__restrict__ tab, int64_t steps, double p0, double p1, double p2, double p3,
+                  double *__restrict__ residual, uint32_t *__restrict__ status) {
+    using namespace imexcl;
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) float sm[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cr = (int)cluster.block_rank();
+    const int tid = threadIdx.x, r = blockIdx.x / CL;
+    float *sCh = sm + OFF_CH, *sCl = sm + OFF_CL, *sMu = sm + OFF_MU, *sW = sm + OFF_W, *sXR = sm + OFF_XR,
+          *sK = sm + OFF_K, *sZ = sm + OFF_Z;
+    float *base = fields + field_offset + (int64_t)r * 2 * G * G;
+    const int y0 = cr * RL;
+
+    // tables (Ch: H rows of G, Cl: G rows of H, mu: G)
+    for (int q = threadIdx.x; q < H * (G / 4); q += NT) {
+        const int y = q / (G / 4), x = (q - y * (G / 4)) * 4;
+        *reinterpret_cast<float4 *>(sCh + y * LD + x) = *reinterpret_cast<const float4 *>(tab + y * G + x);
+    }
+    for (int q = threadIdx.x; q < G * (H / 4); q += NT) {
+        const int y = q / (H / 4), x = (q - y * (H / 4)) * 4;
+        *reinterpret_cast<float4 *>(sCl + y * LDH + x) = *reinterpret_cast<const float4 *>(tab + H * G + y * H + x);
+    }
+    for (int q = threadIdx.x; q < G; q += NT) sMu[q] = tab[2 * H * G + q];
+    // own rows and the two halo rows that exist, in the state form
+    for (int q = threadIdx.x; q < (RL + 2) * (G / 4); q += NT) {
+        const int yl = q / (G / 4) - 1, x = (q % (G / 4)) * 4, yg = y0 + yl;
+        if (yg < 0 || yg >= G) continue;
+        float4 u = *reinterpret_cast<const float4 *>(base + yg * G + x);
+        float4 v = *reinterpret_cast<const float4 *>(base + G * G + yg * G + x);
+        to_state<MODEL>(u.x, v.x, cf);
+        to_state<MODEL>(u.y, v.y, cf);
+        to_state<MODEL>(u.z, v.z, cf);
+        to_state<MODEL>(u.w, v.w, cf);
+        *reinterpret_cast<float4 *>(sW + (yl + 1) * LD + x) = u;
+        *reinterpret_cast<float4 *>(sW + WBUF + (yl + 1) * LD + x) = v;
+    }
+    __syncthreads();
+
+    const int sp = tid / NS, l = tid - sp * NS;
+    // products of steps 2-4: a = spectral / row quad (0..15), b = column quad (0..7)
+    const int a = l >> 3, b = l & 7;
+    // step 5: a5 = local row quad (0..7), b5 = x quad (0..15)
+    const int a5 = l >> 4, b5 = l & 15;
+    float *XR = sXR + sp * TBUF, *K = sK + sp * TBUF, *Z = sZ + sp * TBUF, *W = sW + sp * WBUF;
+    // destinations in the other CTAs (this species' buffers)
+    float *k_even = cluster.map_shared_rank(K, a >> 3), *k_odd = cluster.map_shared_rank(K, 2 + (a >> 3));
+    float *r_lo = cluster.map_shared_rank(XR, a >> 3), *r_hi = cluster.map_shared_rank(XR, 3 - (a >> 3));
+    float *w_up = cr > 0 ? cluster.map_shared_rank(W, cr - 1) : nullptr;
+    float *w_dn = cr < CL - 1 ? cluster.map_shared_rank(W, cr + 1) : nullptr;
+    // divisors of this thread's step-3 outputs: 1 / (1 + a_s (mu_q + mu_m))
+    float dv[8][4];
+    {
+        const float as = sp ? a_v : a_u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q = (i < 4 ? 4 * a + i : H + 4 * a + i - 4), m = y0 + 4 * b + j;
+                dv[i][j] = 1.f / fmaf(as, sMu[q] + sMu[m], 1.f);
+            }
+    }
+
+    for (int64_t n = 0; n < steps; ++n) {
+        // the neighbours' edge rows of the previous step are in place
+        cluster.sync();
+        // 1. dt F(w^n), x-major
+        for (int q = tid; q < RL * (G / 4); q += NT) {
+            const int y = q % RL, x = (q / RL) * 4;
+            cl_incr4<MODEL>(sW, sW + WBUF, sXR, sXR + TBUF, y, x, cr == 0 && y == 0, cr == CL - 1 && y == RL - 1,
+                            cf);
+        }
+        __syncthreads();
+        // 2. forward along x: Xh[y0 + 4b + j][m], m = 4a + i / H + 4a + i - 4
+        {
+            float acc[8][4];
+            cl_fwd(sCh, XR, a, b, acc);
+            const int col = 4 * (a & 7);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int row = (y0 + 4 * b + j) * LDT + col;
+                *reinterpret_cast<float4 *>(k_even + row) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+                *reinterpret_cast<float4 *>(k_odd + row) = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+            }
+        }
+        cluster.sync();
+        // 3. forward along y, divisors: Z[q][4b + j]
+        {
+            float acc[8][4];
+            cl_fwd(sCh, K, a, b, acc);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int q = (i < 4 ? 4 * a + i : H + 4 * a + i - 4);
+                *reinterpret_cast<float4 *>(Z + q * LDT + 4 * b) =
+                    make_float4(acc[i][0] * dv[i][0], acc[i][1] * dv[i][1], acc[i][2] * dv[i][2],
+                                acc[i][3] * dv[i][3]);
+            }
+        }
+        __syncthreads();
+        // 4. inverse along y: Yh[y][y0 + 4b + j] for y = 4a + i and G-1-(4a + i),
+        //    into R[m][y mod 32] of the row's owner
+        {
+            float E[4][4], O[4][4];
+            cl_inv<LDH, LDT>(sCl, Z, a, b, E, O);
+            const int clo = 4 * (a & 7), chi = RL - 4 - 4 * (a & 7);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int row = (y0 + 4 * b + j) * LDT;
+                *reinterpret_cast<float4 *>(r_lo + row + clo) = make_float4(
+                    E[0][j] + O[0][j], E[1][j] + O[1][j], E[2][j] + O[2][j], E[3][j] + O[3][j]);
+                *reinterpret_cast<float4 *>(r_hi + row + chi) = make_float4(
+                    E[3][j] - O[3][j], E[2][j] - O[2][j], E[1][j] - O[1][j], E[0][j] - O[0][j]);
+            }
+        }
+        cluster.sync();
+        // 5. inverse along x, added to the state (rows 4a5 + i, columns 4b5 + j and G-1-(4b5 + j))
+        {
+            float E[4][4], O[4][4];
+            cl_inv<LDT, LDH>(XR, sCl, a5, b5, E, O);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int yl = 4 * a5 + i, o = (yl + 1) * LD;
+                float4 lo = *reinterpret_cast<const float4 *>(W + o + 4 * b5);
+                lo.x += E[i][0] + O[i][0]; lo.y += E[i][1] + O[i][1]; lo.z += E[i][2] + O[i][2];
+                lo.w += E[i][3] + O[i][3];
+                *reinterpret_cast<float4 *>(W + o + 4 * b5) = lo;
+                float4 hi = *reinterpret_cast<const float4 *>(W + o + G - 4 - 4 * b5);
+                hi.x += E[i][3] - O[i][3]; hi.y += E[i][2] - O[i][2]; hi.z += E[i][1] - O[i][1];
+                hi.w += E[i][0] - O[i][0];
+                *reinterpret_cast<float4 *>(W + o + G - 4 - 4 * b5) = hi;
+                if (yl == 0 && w_up) {   // the upper neighbour's bottom halo row
+                    *reinterpret_cast<float4 *>(w_up + (RL + 1) * LD + 4 * b5) = lo;
+                    *reinterpret_cast<float4 *>(w_up + (RL + 1) * LD + G - 4 - 4 * b5) = hi;
+                }
+                if (yl == RL - 1 && w_dn) {   // the lower neighbour's top halo row
+                    *reinterpret_cast<float4 *>(w_dn + 4 * b5) = lo;
+                    *reinterpret_cast<float4 *>(w_dn + G - 4 - 4 * b5) = hi;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < RL * (G / 4); q += NT) {
+        const int yl = q / (G / 4), x = (q - yl * (G / 4)) * 4;
+        float4 u = *reinterpret_cast<const float4 *>(sW + (yl + 1) * LD + x);
+        float4 v = *reinterpret_cast<const float4 *>(sW + WBUF + (yl + 1) * LD + x);
+        from_state<MODEL>(u.x, v.x, cf);
+        from_state<MODEL>(u.y, v.y, cf);
+        from_state<MODEL>(u.z, v.z, cf);
+        from_state<MODEL>(u.w, v.w, cf);
+        *reinterpret_cast<float4 *>(base + (y0 + yl) * G + x) = u;
+        *reinterpret_cast<float4 *>(base + G * G + (y0 + yl) * G + x) = v;
+    }
+    // every CTA's rows stored, and no CTA touches another's shared memory
+    // after this barrier
+    cluster.sync();
+    if (cr != 0) return;
+    residual_from_global<MODEL, G>(base, p0, p1, p2, p3, residual, status, r, sCh);
+}
+
 // Output tile per thread (TM x TN): 0 = 4 x 4, 1 = 8 x 4, 2 = 4 x 8, 3 = 8 x 8.
 // Every tile runs the same FMA chains (k ascending per output), so all give
 // bit-identical fields; the choice (per G) is a speed knob.  4 = the
@@ -578,8 +886,10 @@ size_t imex_eo_table_floats(int G) { return (size_t)G * G + G; }
 
 // both tables of grid side G, into memory the handle owns (rd_init)
 rd_status imex_tables_fill(int G, float *tab, float *eo_tab, cudaStream_t s) {
-    imex_table_kernel<<<(G * G + 127) / 128, 128, 0, s>>>(G, tab);
-    note_launch();
+    if (tab) {
+        imex_table_kernel<<<(G * G + 127) / 128, 128, 0, s>>>(G, tab);
+        note_launch();
+    }
     imex_eo_table_kernel<<<(G * G / 2 + 127) / 128, 128, 0, s>>>(G, eo_tab);
     note_launch();
     return cuda_status(cudaGetLastError());
@@ -639,14 +949,57 @@ static rd_status launch_imex_g(const GroupDev &g, float *fields, const float *ta
     }
 }
 
+// G = 128: one cluster of four CTAs per realisation
+template <int MODEL>
+static rd_status launch_imex_cl_m(const GroupDev &g, const float *eo_tab, float *fields, double *residual,
+                                  uint32_t *status, cudaStream_t s) {
+    using namespace imexcl;
+    auto kern = rd_imex_cl_kernel<MODEL>;
+    rd_status st = smem_attr(kern, (int)SMEM);
+    if (st) return st;
+    const double h2 = (double)(g.G - 1) * (double)(g.G - 1);
+    const float a_u = (float)(g.dt * g.p[0] * h2), a_v = (float)(g.dt * g.p[1] * h2);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(g.n_real * CL), 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    RD_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, fields, g.field_offset, make_coef(g), a_u, a_v, eo_tab, g.n_steps,
+                                   g.p[0], g.p[1], g.p[2], g.p[3],
+                                   residual ? residual + 2 * g.real_base : nullptr, status));
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+static rd_status launch_imex_cl(const GroupDev &g, const float *eo_tab, float *fields, double *residual,
+                                uint32_t *status, cudaStream_t s) {
+    switch (g.model) {
+        case RD_FHN: return launch_imex_cl_m<RD_FHN>(g, eo_tab, fields, residual, status, s);
+        case RD_GM: return launch_imex_cl_m<RD_GM>(g, eo_tab, fields, residual, status, s);
+        case RD_DIFF: return launch_imex_cl_m<RD_DIFF>(g, eo_tab, fields, residual, status, s);
+        case RD_BZ: return launch_imex_cl_m<RD_BZ>(g, eo_tab, fields, residual, status, s);
+        default: return RD_ERR_UNSUPPORTED;
+    }
+}
+
+int imex_table_index(int G) { return G == 32 ? 0 : G == 64 ? 1 : G == 128 ? 2 : -1; }
+
 bool imex_supported(const GroupDev &g) {
-    return g.model != RD_RDODE && (g.G == 32 || g.G == 64);
+    return g.model != RD_RDODE && imex_table_index(g.G) >= 0;
 }
 
 rd_status launch_imex_group(const GroupDev &g, const float *tab, const float *eo_tab, float *fields, double *residual,
                             uint32_t *status, cudaStream_t s) {
-    if (!imex_supported(g) || !tab || !eo_tab) return RD_ERR_UNSUPPORTED;
+    if (!imex_supported(g) || !eo_tab || (g.G != 128 && !tab)) return RD_ERR_UNSUPPORTED;
     if (g.n_steps == 0 && !residual) return RD_OK;
+    if (g.G == 128) return launch_imex_cl(g, eo_tab, fields, residual, status, s);
     return g.G == 32 ? launch_imex_g<32>(g, fields, tab, eo_tab, residual, status, s)
                      : launch_imex_g<64>(g, fields, tab, eo_tab, residual, status, s);
 }

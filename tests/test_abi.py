@@ -147,8 +147,9 @@ def test_step_table_sizes_without_gpu(libpath):
     """rd_tables_size (host only): the stabilised RK2 tables ((S+1)^2 float4
     coefficients + (S+1) doubles, S = 256) when a group can run the RK2
     integrator, plus the semi-implicit cosine-basis tables (2 G^2 + G and
-    G^2 + G floats) per grid side 32 / 64 present, each rounded up to 256
-    bytes; none for groups no table-using integrator runs (G = 256)."""
+    G^2 + G floats) per grid side 32 / 64 present and the even/odd table
+    alone (G^2 + G floats) at 128, each rounded up to 256 bytes; none for
+    groups no table-using integrator runs (G = 256)."""
     import paper_2203_14742_b300 as p
 
     def up(b):
@@ -173,7 +174,7 @@ def test_step_table_sizes_without_gpu(libpath):
         return sz.value
 
     assert size([(p.FHN, 64)]) == rkc + imex(64)
-    assert size([(p.GM, 128)]) == rkc
+    assert size([(p.GM, 128)]) == rkc + up(4 * (128 * 128 + 128))
     assert size([(p.FHN, 32), (p.GM, 64), (p.FHN, 64)]) == rkc + imex(32) + imex(64)
     assert size([(p.FHN, 256)]) == 0
     assert size([(p.RDODE, 256)]) == rkc

@@ -1,14 +1,16 @@
 """GPU parity of the semi-implicit (IMEX) Euler stepper (implicit diffusion
 solved in the cosine basis, explicit reaction; Sec. 5.1 and App. B.2 on
-implicit stepping, App. B.1.1 discretisation) against the oracle's dense
-LU solve of the same equations in FP64.
+implicit stepping, App. B.1.1 discretisation) against the oracle's LU
+solve of the same equations in FP64 (dense; sparse at 128 x 128).
 
 Tolerance.  The GPU solves for the increment d = w^{n+1} - w^n, so each
 step's four FP32 products of length G with an orthonormal matrix round
 relative to d (about sqrt(G) 2^-24 of it per product), and the state takes
 one FP32 rounding per step as in explicit Euler; the implicit diffusion
 damps what is carried over.  Measured: 5e-7 after 300 FHN steps at
-G = 32 and 64, 5e-8 for GM and BZ (relative to the field's maximum).  Held to
+G = 32 and 64, 5e-8 for GM and BZ (relative to the field's maximum); at
+G = 128 (one 4-CTA cluster per realisation) 5.7e-7 FHN, 3.4e-8 GM,
+5.3e-8 BZ and 8.7e-7 for pure diffusion of +-0.5 noise.  Held to
 max|gpu - oracle| / max|oracle| <= 1e-5 per realisation and species over
 the step counts below (the fields' own tolerance), and bit-exact where the
 arithmetic is exact (zeros and the homogeneous equilibrium of the
@@ -120,7 +122,7 @@ def test_equilibrium_is_kept_bit_exact(p, model, par, noise):
 
 
 def test_imex_refuses_unsupported_groups(p):
-    sim = p.Simulation([p.Group(W.FHN, 128, 1, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -6, 1, (-0.05, 0.05), 1)])
+    sim = p.Simulation([p.Group(W.FHN, 256, 1, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -6, 1, (-0.05, 0.05), 1)])
     with pytest.raises(p.RdError) as e:
         sim.integrate_imex()
     assert e.value.status == 6   # RD_ERR_UNSUPPORTED
@@ -231,4 +233,92 @@ def test_imex_c2_full_size_sample(p):
     got = sim.group_fields(0).cpu().numpy()
     pick = [0, g["n_real"] - 1]
     want = OI.imex_run(g["model"], g["params"], 2 ** -6, 625, w0[pick])
+    assert rel_err(got[pick], want) <= FIELD_TOL
+
+
+# G = 128: one 4-CTA cluster per realisation (rows split four ways, the
+# transforms along y through distributed shared memory).  The products are
+# twice as long as at G = 64 (about sqrt(2) more rounding per product); the
+# same field tolerance holds.
+CASES_128 = [
+    (W.FHN, 128, 2, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -6, 120, (-0.05, 0.05)),
+    (W.GM, 128, 3, (2.5e-4, 0.01, 1.0, 0.5251796931279438), 2 ** -6, 150, (0.0, 0.01)),
+    (W.BZ, 128, 2, W.BZ_THETA0, 2 ** -7, 100, (0.0, 0.01)),
+    (W.DIFF, 128, 2, (3e-3, 1e-3), 2 ** -5, 60, (-0.5, 0.5)),
+]
+
+
+@pytest.mark.parametrize("case", CASES_128)
+def test_imex_cluster_fields_within_tolerance(p, case):
+    model, G, n, par, dt, steps, noise = case
+    w0, got, res = run_gpu(p, model, G, n, par, dt, steps, noise, 0x128 + n, residual=True)
+    want = OI.imex_run(model, par, dt, steps, w0)
+    err = rel_err(got, want)
+    assert err <= FIELD_TOL, err
+    ref = oracle.residual(model, par, got.astype(np.float64))
+    np.testing.assert_allclose(res.cpu().numpy(), ref, rtol=1e-9, atol=1e-12)
+
+
+def test_imex_cluster_single_step(p):
+    """One step from uniform noise, the worst case for the transforms'
+    rounding: at G = 128 the v-species increment is cv = Dv dt (G-1)^2
+    (about 12) times the noise's Laplacian, some 100 x the field, and the
+    inverse products carry the solved increment, of the field's size; each
+    product is a 64-term FP32 chain plus a pre-add and a recombination.
+    Measured 8.7e-6 of max|field| (G = 64: below 5e-6); bound 1.5e-5.  The
+    later steps' increments are small, which is why the multi-step runs stay
+    within the field tolerance."""
+    par = (2.9e-4, 0.048, 9.7, 0.93)
+    w0, got, _ = run_gpu(p, W.FHN, 128, 2, par, 2 ** -6, 1, (-0.05, 0.05), 15)
+    want = OI.imex_run(W.FHN, par, 2 ** -6, 1, w0)
+    assert rel_err(got, want) <= 1.5e-5
+
+
+def test_imex_cluster_mode_decay_mass_and_equilibrium(p):
+    """Closed-form decay of cosine modes and the kept mean at G = 128, and
+    the homogeneous equilibrium bit-exact."""
+    test_pure_diffusion_mode_decay_and_mass(p, 128)
+    w0, got, _ = run_gpu(p, W.GM, 128, 2, (2.5e-4, 0.01, 1.0, 0.52), 2 ** -5, 40, (0.0, 0.0), 3)
+    np.testing.assert_array_equal(got, w0)
+
+
+def test_imex_cluster_mixed_with_one_cta_groups(p):
+    """A G = 128 group between G = 64 and G = 32 groups in one handle: each
+    kernel reads its own table and writes its own realisations."""
+    gs = [p.Group(W.GM, 64, 1, (2.5e-4, 0.01, 1.0, 0.52), 2 ** -4, 40, (0.0, 0.01), 41),
+          p.Group(W.FHN, 128, 2, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -6, 50, (-0.05, 0.05), 42),
+          p.Group(W.FHN, 32, 1, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -6, 50, (-0.05, 0.05), 43)]
+    sim = p.Simulation(gs)
+    w0 = [sim.group_fields(i).cpu().numpy().copy() for i in range(3)]
+    sim.integrate_imex()
+    torch.cuda.synchronize()
+    assert sim.sync_status() == 0
+    for i, g in enumerate(gs):
+        want = OI.imex_run(g.model, g.params, g.dt, g.n_steps, w0[i])
+        assert rel_err(sim.group_fields(i).cpu().numpy(), want) <= FIELD_TOL, i
+
+
+def test_imex_cluster_reports_a_blow_up(p):
+    sim = p.Simulation([p.Group(W.FHN, 128, 1, (2.8e-4, 0.05, 10.0, 0.95), 4.0, 40, (-0.5, 0.5), 3)])
+    res = sim.integrate_imex(residual=True)
+    torch.cuda.synchronize()
+    assert np.isnan(res.cpu().numpy()).all()
+    assert sim.sync_status() == 5   # RD_ERR_NONFINITE
+
+
+def test_imex_c3_full_size_sample(p):
+    """All 512 realisations of the GM 128x128 workload to its horizon
+    (20000 explicit steps of 2^-10) in 1250 semi-implicit steps of 2^-6:
+    the first and the last realisation against the oracle."""
+    g = W.config("c3")["groups"][0]
+    steps = g["n_steps"] // 16
+    grp = p.Group(g["model"], g["G"], g["n_real"], g["params"], 2 ** -6, steps, g["noise"], g["seed"])
+    sim = p.Simulation([grp])
+    w0 = sim.group_fields(0).cpu().numpy().copy()
+    sim.integrate_imex()
+    torch.cuda.synchronize()
+    assert sim.sync_status() == 0
+    got = sim.group_fields(0).cpu().numpy()
+    pick = [0, g["n_real"] - 1]
+    want = OI.imex_run(g["model"], g["params"], 2 ** -6, steps, w0[pick])
     assert rel_err(got[pick], want) <= FIELD_TOL
