@@ -598,39 +598,56 @@ def c2_bench(p, torch, dev, stream, pk, src, reps=5):
 def gram_large(p, torch, dev, stream, pk, src):
     """Tensor-core Gram at the paper's SCIL scale (N_syn = 1000): 2 sets x
     1024 patterns of d = 32768 (GM 128x128 both species, synthetic cosine
-    fields), plus the whole correlation integral on them."""
+    fields), plus the whole correlation integral on them; the default form
+    (three bf16 products, hi.hi + hi.lo + lo.hi) and, for comparison, one
+    product (hi.hi, the cross terms in the bound), with the pairs each
+    leaves to tiers 2 and 3."""
     n, G = 1024, 128
     X = torch.from_numpy(W.cosine_patterns(2 * n, G, 2, 77, amp=0.8, offset=2.0)).to(dev)
     X1, X2 = X[:n], X[n:]
     d = X.shape[1]
-    c = p.cil(X1, X2, b=1.3, M=16)          # packs the workspace (and warms up)
-    torch.cuda.synchronize()
     reps = 5
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        fl = p.gram_only(n, n, d, dev)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_gram = e0.elapsed_time(e1) / reps * 1e-3
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    for _ in range(reps):
-        c = p.cil(X1, X2, b=1.3, M=16)
-    c1.record(stream)
-    torch.cuda.synchronize()
-    t_cil = c0.elapsed_time(c1) / reps * 1e-3
-    tf = fl / t_gram / 1e12                  # bf16 MMA work executed: 3 products per element pair
+
+    def measure():
+        c = p.cil(X1, X2, b=1.3, M=16)          # packs the workspace (and warms up)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fl = p.gram_only(n, n, d, dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_gram = e0.elapsed_time(e1) / reps * 1e-3
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(reps):
+            c = p.cil(X1, X2, b=1.3, M=16)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        return fl, t_gram, c0.elapsed_time(c1) / reps * 1e-3, p.cil_queue_lengths(n, n, d, dev)
+
+    products = p.gram_products(n, n, d)
+    fl, t_gram, t_cil, rech = measure()
+    try:
+        p.set_gram_products(1)
+        fl1, t_gram1, t_cil1, rech1 = measure()
+    finally:
+        p.set_gram_products(0)
+    tf = fl / t_gram / 1e12                  # bf16 MMA work executed
     alg = 2.0 * n * n * d / t_gram / 1e12    # algorithmic: one product per element pair
-    return {"pairs": n * n, "d": d, "gram_ms": t_gram * 1e3,
+    return {"pairs": n * n, "d": d, "products": products, "gram_ms": t_gram * 1e3,
             "gram_tflops_executed": tf, "gram_tflops_algorithmic": alg,
             "peak_bf16_tflops": pk["bf16_tflops"], "frac_of_peak": tf / pk["bf16_tflops"],
             "frac_of_peak_algorithmic": alg / pk["bf16_tflops"],
             "frac_of_sustained_peak": tf / pk.get("bf16_tflops_sustained", pk["bf16_tflops"]),
-            "peak_note": "bf16 dense burst peak (%s peaks file); executed = hi.hi + hi.lo + lo.hi bf16 "
-                         "products (3 x 2 n1 n2 d flops), algorithmic = 2 n1 n2 d" % src,
+            "peak_note": "bf16 dense burst peak (%s peaks file); executed = the bf16 products the form "
+                         "runs (products x 2 n1 n2 d_padded flops), algorithmic = 2 n1 n2 d" % src,
             "cil_ms": t_cil * 1e3, "pair_dists_per_s": n * n / t_cil,
-            "rechecked": int(c["n_rechecked"])}
+            "tier2_pairs": rech[0], "exact_pairs": rech[1],
+            "one_product": {"gram_ms": t_gram1 * 1e3,
+                            "frac_of_peak": fl1 / t_gram1 / 1e12 / pk["bf16_tflops"],
+                            "frac_of_peak_algorithmic": 2.0 * n * n * d / t_gram1 / 1e12 / pk["bf16_tflops"],
+                            "cil_ms": t_cil1 * 1e3, "tier2_pairs": rech1[0], "exact_pairs": rech1[1]}}
 
 
 def stream_bench(p, torch, dev, stream, pk, src, depths=(1, 2, 4, 8)):

@@ -420,7 +420,8 @@ const char *rd_status_str(rd_status s);
  *   invalid; not expected to occur).
  *
  * Method: the patterns are centred and split into bf16 hi + lo parts; a
- * tensor-core Gram product (FP32 accumulation) gives
+ * tensor-core Gram product (FP32 accumulation; hi.hi + hi.lo + lo.hi, or
+ * hi.hi alone when asked, see cil_set_gram_products) gives
  * d2 ~ |x|^2 + |y|^2 - 2 x.y for every pair together with a rigorous error
  * bound; pairs whose bound straddles a threshold (or the maximum) are
  * re-bounded by FP32 error-free sums and, if still undecided, evaluated
@@ -503,10 +504,35 @@ rd_status cil_debug_approx(const float *d_X1, int64_t ld1, int64_t n1,
 
 /* cil_gram_only — benchmarking entry point: re-run only the tensor-core Gram
  * stage on a workspace already packed by cil_features or cil_debug_approx
- * with the same (n1, n2, d).  *flops (host, nullable) receives the FLOPs of
- * the launch: 3 bf16 products x 2 x n1 x n2 x d_padded. */
+ * with the same (n1, n2, d) and product count.  *flops (host, nullable)
+ * receives the FLOPs of the launch: (3 or 1) bf16 products x 2 x n1 x n2 x
+ * d_padded. */
 rd_status cil_gram_only(int64_t n1, int64_t n2, int64_t d, void *d_work, size_t work_bytes,
                         double *flops, void *stream);
+
+/* cil_set_gram_products — the tensor-core Gram's form, process-wide, for
+ * every correlation integral (cil_*, mcil_*, scil_evaluate) started after
+ * the call: 3 = hi.hi + hi.lo + lo.hi (only lo.lo dropped: the tightest
+ * interval, the fewest pairs re-evaluated), 1 = hi.hi alone (a third of the
+ * tensor-core work and half its operand bytes; the dropped cross terms are
+ * bounded by Cauchy-Schwarz, |hi_i| |lo_j| + |lo_i| |hi_j|, about 2^-8 of
+ * |x_i| |x_j|, so more pairs near the radii are re-evaluated one by one:
+ * worth it only when the distances sit far from the thresholds), 0 = the
+ * default (three).  Results are identical in every form (the bounds are
+ * rigorous and every undecided pair is re-evaluated); only the time
+ * changes.  RD_ERR_INVALID_ARG for another value.
+ * cil_gram_products — the form a correlation integral of (n1, n2, d) takes
+ * under the current setting (1 or 3; -1 for sizes below 1).  Host only. */
+rd_status cil_set_gram_products(int32_t mode);
+int32_t cil_gram_products(int64_t n1, int64_t n2, int64_t d);
+
+/* cil_queue_lengths — checking entry point: after a cil_features* call on
+ * d_work with the same (n1, n2, d), the number of pairs that call sent to
+ * tier 2 (FP32 error-free re-evaluation: their tier-1 interval met a
+ * threshold or could hold the maximum) and to tier 3 (exact), as two int64
+ * written to d_out (device), in stream order. */
+rd_status cil_queue_lengths(int64_t n1, int64_t n2, int64_t d, const void *d_work, size_t work_bytes,
+                            int64_t *d_out, void *stream);
 
 /* cil_features_exact — the same outputs with every pair evaluated exactly
  * (no Gram product, no bounds).  Slow; for checking. */

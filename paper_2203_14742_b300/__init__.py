@@ -91,6 +91,9 @@ _SIGS = {
                                   _vp, _vp, _vp, _sz, _vp]),
     "cil_exact_d2": (_i32, [_vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _vp]),
     "cil_gram_only": (_i32, [_i64, _i64, _i64, _vp, _sz, C.POINTER(_dbl), _vp]),
+    "cil_set_gram_products": (_i32, [_i32]),
+    "cil_gram_products": (_i32, [_i64, _i64, _i64]),
+    "cil_queue_lengths": (_i32, [_i64, _i64, _i64, _vp, _sz, _vp, _vp]),
     "cil_debug_approx": (_i32, [_vp, _i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _sz, _vp]),
     "synlik_stats": (_i32, [_vp, _i64, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                             _vp, _vp, _vp]),
@@ -389,6 +392,9 @@ def variant_shape(G, variant):
 
 
 def _workspace(n1, n2, d, device):
+    device = torch.device(device)
+    if device.type == "cuda" and device.index is None:
+        device = torch.device("cuda", torch.cuda.current_device())
     sz = C.c_size_t()
     _check("cil_workspace_size", lib().cil_workspace_size(n1, n2, d, C.byref(sz)))
     key = (device, )
@@ -459,6 +465,30 @@ def gram_only(n1, n2, d, device=None):
     fl = C.c_double()
     _check("cil_gram_only", lib().cil_gram_only(n1, n2, d, _ptr(w), wb, C.byref(fl), _stream()))
     return fl.value
+
+
+def set_gram_products(mode):
+    """The tensor-core Gram's form for every later correlation integral,
+    process-wide: 3 (hi.hi + hi.lo + lo.hi, the default; 0 restores it) or
+    1 (hi.hi alone, a wider rigorous interval).  Results are identical; only
+    the time changes."""
+    _check("cil_set_gram_products", lib().cil_set_gram_products(int(mode)))
+
+
+def cil_queue_lengths(n1, n2, d, device=None):
+    """(tier-2 pairs, tier-3 pairs) of the last correlation integral of this
+    size on the cached workspace (checking and benchmarking)."""
+    dev = torch.device(device or "cuda")
+    w, wb = _workspace(n1, n2, d, dev)
+    out = torch.zeros(2, dtype=torch.int64, device=dev)
+    _check("cil_queue_lengths", lib().cil_queue_lengths(int(n1), int(n2), int(d), _ptr(w), wb, _ptr(out),
+                                                        _stream()))
+    return tuple(int(v) for v in out.cpu())
+
+
+def gram_products(n1, n2, d):
+    """The product count (1 or 3) a correlation integral of this size uses."""
+    return int(lib().cil_gram_products(int(n1), int(n2), int(d)))
 
 
 def cil(X1, X2, b=1.3, M=16, radii=None, work=None, out=None):

@@ -13,13 +13,16 @@
 //      into bf16 hi + lo, and record per
 //      pattern N = |hi+lo|^2, H = |hi| + |lo|, L = |lo| and the
 //      representation error E = |(x - c) - (hi + lo)| (all FP64);
-//   2. Gram:  P_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j (bf16 products, FP32
-//      accumulation per K chunk in tensor memory, chunk partials summed with
-//      TwoSum into FP32 hi/lo pairs per K segment, segments combined the
-//      same way);
+//   2. Gram:  P_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j (three bf16
+//      products, the default), or P_ij = hi_i.hi_j alone when asked (one
+//      product: a third of the tensor-core work and half its operand bytes,
+//      for a wider interval); FP32 accumulation per K chunk in tensor
+//      memory, chunk partials summed with TwoSum into FP32 hi/lo pairs per
+//      K segment, segments combined the same way;
 //   3. tier 1: A = N_i + N_j - 2 P_ij approximates d2_ij with a rigorous
-//      error bound (FP32 accumulation model, dropped lo.lo term, E_i + E_j),
-//      kept as an FP32 interval rounded outwards;
+//      error bound (FP32 accumulation model, the dropped terms: lo.lo, and
+//      for one product hi.lo + lo.hi, each by Cauchy-Schwarz on the parts'
+//      norms; E_i + E_j), kept as an FP32 interval rounded outwards;
 //   4. tier 2: pairs whose interval could hold the maximum (which defines R0)
 //      or contain a threshold get an FP32 error-free evaluation of the exact
 //      sum of squares (TwoSum / exact products, double-float accumulation)
@@ -28,6 +31,7 @@
 //      evaluated exactly (integer fixed-point accumulation, one rounding;
 //      exact.cuh), one CTA per pair.
 // Counts per radius are reduced with warp ballot + popc.
+#include <atomic>
 #include <cstdio>
 #include <cuda_bf16.h>
 #include "common.cuh"
@@ -36,11 +40,19 @@
 namespace rdcil {
 
 rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2, int64_t dp, int64_t S,
-                         int64_t cs, float *Ppart, uint32_t *status, cudaStream_t s);
+                         int64_t cs, int np_, float *Ppart, uint32_t *status, cudaStream_t s);
 
-static constexpr int KSTEPS_MAX = 4;     // longest accumulator chunk, in K steps of 64 (bounds FP32 error)
+// longest accumulator chunk, in K steps of 64 (bounds the FP32 accumulation
+// error), for three products / one product: with one product the dropped
+// cross terms dominate the bound, so longer chunks (fewer drains) cost
+// nothing in interval width
+static constexpr int KSTEPS_MAX = 4, KSTEPS_MAX1 = 16;
 static constexpr int PAD = 64;           // padded pattern length granularity
 static constexpr int TILE = 128;         // Gram output tile (pairs per side)
+// tier 3: queues of at most EXS_CAP pairs are spread over CTAs by segments of
+// EXS_SEG elements (every pair's exact digit sums meet in global memory);
+// longer queues take one CTA per pair
+static constexpr int EXS_CAP = 64, EXS_SEG = 2048;
 static constexpr int N_SM = 148;
 
 static inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -116,6 +128,7 @@ __device__ __forceinline__ double read_min_d(unsigned long long s) {
 struct CilWork {
     int64_t n1, n2, d, dp;
     int64_t ntj, S, cs;     // Gram: tiles along set 2, K segments per tile, K steps per chunk
+    int64_t np_;            // Gram products: 3 (hi.hi + hi.lo + lo.hi) or 1 (hi.hi)
     int64_t nchunk;         // upper bound on the chunk partials summed per pair
     float *centre;          // [dp]
     __nv_bfloat16 *hi;      // [(n1+n2)][dp]
@@ -128,11 +141,24 @@ struct CilWork {
     double *ex;             // [n1*n2] exact d2 (valid where flag == 2)
     uint8_t *flag;          // [n1*n2] 0: tier 1 decides, 1: tier 2, 2: exact
     unsigned long long *q1, *q2;  // [n1*n2] tier-2 / tier-3 queues (bit 63: may hold the maximum)
+    long long *xacc;        // [EXS_CAP][XD] digit sums of the split tier 3 (zeroed per call)
+    unsigned *xarr;         // [2][EXS_CAP] CTAs arrived per queued pair, non-finite flags
     float *t1lo, *t1hi;     // [32] tier-1 threshold ranges (FP32, outward)
     double *t2lo, *t2hi;    // [32] tier-2 threshold ranges
     unsigned long long *scal;  // see SC_* below
     size_t bytes;
 };
+
+// Gram product count, process-wide (cil_set_gram_products): 3 by default.
+// One product halves the Gram's time at the paper's scale, but its interval
+// (the cross terms' Cauchy-Schwarz bound, about 2^-8 |x_i| |x_j|) leaves
+// some twenty times more pairs to tier 2 near the radii, whose per-pair
+// re-evaluation then costs more than the Gram saved on the workloads
+// measured; it stays available for data whose distances sit far from the
+// thresholds.
+static std::atomic<int> g_gram_products{3};
+
+static int gram_products_for(int64_t, int64_t) { return g_gram_products.load(); }
 
 static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     CilWork w{};
@@ -153,7 +179,9 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     const int64_t seg_max = (n64 + S - 1) / S;
     w.ntj = ntj;
     w.S = S;
-    w.cs = tiles * n64 <= 4096 ? 1 : (seg_max < KSTEPS_MAX ? seg_max : KSTEPS_MAX);
+    w.np_ = gram_products_for(tiles, n64);
+    const int64_t kmax = w.np_ == 1 ? KSTEPS_MAX1 : KSTEPS_MAX;
+    w.cs = tiles * n64 <= 4096 ? 1 : (seg_max < kmax ? seg_max : kmax);
     w.nchunk = S * ((seg_max + w.cs - 1) / w.cs);
     int64_t n = n1 + n2;
     size_t off = 0;
@@ -182,6 +210,8 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     w.flag = (uint8_t *)take(sizeof(uint8_t) * np);
     w.q1 = (unsigned long long *)take(sizeof(unsigned long long) * np);
     w.q2 = (unsigned long long *)take(sizeof(unsigned long long) * np);
+    w.xacc = (long long *)take(sizeof(long long) * EXS_CAP * XD + sizeof(unsigned) * 2 * EXS_CAP);
+    w.xarr = (unsigned *)(w.xacc + EXS_CAP * XD);
     w.t1lo = (float *)take(sizeof(float) * 32);
     w.t1hi = (float *)take(sizeof(float) * 32);
     w.t2lo = (double *)take(sizeof(double) * 32);
@@ -255,6 +285,8 @@ __device__ __forceinline__ void pack_elem(float xv, float cv, __nv_bfloat16 &h, 
 
 // One block per pattern; each thread takes groups of 8 elements (float4
 // loads, 16-byte bf16 stores when the pattern row is 16-byte aligned).
+// lo == nullptr: the lo parts are formed (for N, L and E) but not stored
+// (the one-product Gram does not read them).
 __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n1,
                             const float *__restrict__ X2, int64_t ld2, int64_t d, int64_t dp,
                             const float *__restrict__ centre, __nv_bfloat16 *__restrict__ hi,
@@ -291,7 +323,7 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
             }
         }
         *reinterpret_cast<uint4 *>(hi + i * dp + t0) = *reinterpret_cast<const uint4 *>(h);
-        *reinterpret_cast<uint4 *>(lo + i * dp + t0) = *reinterpret_cast<const uint4 *>(l);
+        if (lo) *reinterpret_cast<uint4 *>(lo + i * dp + t0) = *reinterpret_cast<const uint4 *>(l);
     }
     float nh = A.nh, nl = A.nl, sH = A.sH, sL = A.sL, sE = A.sE;
     __shared__ float red[5][32];
@@ -338,9 +370,12 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
 // accumulator errs by at most n * u * S, S = sum of the magnitudes of the
 // products, u the unit roundoff of one accumulation step (gam = n * u is
 // passed in per Gram kernel).  Here S = sum |hi||hi'| + |hi||lo'| + |lo||hi'|
-// <= H_i H_j.  The dropped lo.lo' term is bounded by L_i L_j.  The interval
-// arithmetic below rounds every bound upwards (FP32 _ru intrinsics).
-__global__ void d2_bound_kernel(CilWork w, float gam) {
+// <= H_i H_j (one product: sum |hi||hi'| <= H_i H_j too).  The dropped
+// lo.lo' term is bounded by L_i L_j (Cauchy-Schwarz); with one product the
+// dropped hi.lo' + lo.hi' terms by |hi_i| L_j + L_i |hi_j| <= H_i L_j +
+// L_i H_j (cross = 1).  The interval arithmetic below rounds every bound
+// upwards (FP32 _ru intrinsics).
+__global__ void d2_bound_kernel(CilWork w, float gam, int cross) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t np = w.n1 * w.n2;
     float lb = 0.f, ub = 0.f;
@@ -362,8 +397,10 @@ __global__ void d2_bound_kernel(CilWork w, float gam) {
                                    __fmul_ru(2.f, fabsf(__double2float_ru(fabs(P)))));
         // Gram accumulation, dropped lo.lo, norms' compensated sums (2^-44),
         // the double rounding of A above (2^-52 of the terms)
-        float eg = __fmul_ru(2.f, __fadd_ru(__fmul_ru(__fmul_ru(gam, w.Hf[a]), w.Hf[bb]),
-                                            __fmul_ru(w.Lf[a], w.Lf[bb])));
+        float dropped = __fmul_ru(w.Lf[a], w.Lf[bb]);
+        if (cross)
+            dropped = __fadd_ru(dropped, __fadd_ru(__fmul_ru(w.Hf[a], w.Lf[bb]), __fmul_ru(w.Lf[a], w.Hf[bb])));
+        float eg = __fmul_ru(2.f, __fadd_ru(__fmul_ru(__fmul_ru(gam, w.Hf[a]), w.Hf[bb]), dropped));
         eg = __fadd_ru(eg, __fmul_ru((float)(w.dp + 64) * 5.7e-14f + 4.5e-16f, Ns));
         const float up = __fadd_ru(__double2float_ru(A), eg);
         const float D = __fadd_ru(w.Ef[a], w.Ef[bb]);
@@ -497,12 +534,26 @@ __global__ void classify1_kernel(CilWork w, const double *__restrict__ radii_in,
 // 4b. tier 2: d2 = sum (x - y)^2 from FP32 error-free transformations.
 //     Per element: s = fl(x - y) and e with s + e = x - y exactly (TwoSum);
 //     s^2 = p + pe exactly (product and its FMA error); 2 s e rounded
-//     (error <= 2^-47 s^2); e^2 <= 2^-48 s^2 dropped.  Each thread keeps a
-//     (H, L) pair: H += p error-free (TwoSum), L collects the rest in FP32:
-//     |L| <= (n + 3) 2^-24 S for n terms per thread and S = sum p, so its
-//     2n roundings cost at most 2 n (n + 4) 2^-48 S.  The 256
-//     thread pairs are combined in FP64 (error <= 300 2^-53).  The interval
-//     holds the exact sum, hence (monotone rounding) its rounded value.
+//     (error <= 2^-47 s^2); e^2 <= 2^-48 s^2 dropped.  Each thread keeps
+//     four (H, L) pairs (element t into pair t mod 4 of its float4, so four
+//     independent chains and 16-byte loads; unaligned rows and the last
+//     d mod 4 elements into pair 0): H += p error-free (TwoSum), L
+//     collects the rest in FP32: |L| <= (n + 3) 2^-24 S for n terms per pair
+//     and S = sum p, so its 2n roundings cost at most 2 n (n + 4) 2^-48 S,
+//     n <= ceil(d / 256) either way.  The 1024 pairs are combined in FP64
+//     (error <= 1100 2^-53 of the positive sum).  The interval holds the
+//     exact sum, hence (monotone rounding) its rounded value.
+__device__ __forceinline__ void t2_acc(float &H, float &L, float a, float bv) {
+    const float sd = a - bv;
+    const float bb = sd - a;
+    const float e = (a - (sd - bb)) + (-bv - bb);
+    const float p = sd * sd;
+    const float pe = fmaf(sd, sd, -p);
+    const float cr = (2.f * sd) * e;
+    two_sum_acc(H, L, p);
+    L += pe + cr;
+}
+
 __global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
                                                     const float *__restrict__ X2, int64_t ld2) {
     __shared__ double red[2][8];
@@ -513,19 +564,24 @@ __global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__re
         const int64_t q = (int64_t)(ent & Q_IDX);
         const int64_t i = q / w.n2, j = q - i * w.n2;
         const float *x = X1 + i * ld1, *y = X2 + j * ld2;
-        float H = 0.f, L = 0.f;
-        for (int64_t t = threadIdx.x; t < w.d; t += 256) {
-            const float a = __ldg(x + t), bv = __ldg(y + t);
-            const float sd = a - bv;
-            const float bb = sd - a;
-            const float e = (a - (sd - bb)) + (-bv - bb);
-            const float p = sd * sd;
-            const float pe = fmaf(sd, sd, -p);
-            const float cr = (2.f * sd) * e;
-            two_sum_acc(H, L, p);
-            L += pe + cr;
+        float H[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
+        int64_t t0 = 0;
+        if ((((uintptr_t)x | (uintptr_t)y) & 15) == 0) {
+            const int64_t d4 = w.d >> 2;
+            const float4 *x4 = reinterpret_cast<const float4 *>(x), *y4 = reinterpret_cast<const float4 *>(y);
+#pragma unroll 4
+            for (int64_t t = threadIdx.x; t < d4; t += 256) {
+                const float4 a = __ldg(x4 + t), bv = __ldg(y4 + t);
+                t2_acc(H[0], L[0], a.x, bv.x);
+                t2_acc(H[1], L[1], a.y, bv.y);
+                t2_acc(H[2], L[2], a.z, bv.z);
+                t2_acc(H[3], L[3], a.w, bv.w);
+            }
+            t0 = d4 << 2;
         }
-        double v = (double)H + (double)L;
+        for (int64_t t = t0 + threadIdx.x; t < w.d; t += 256) t2_acc(H[0], L[0], __ldg(x + t), __ldg(y + t));
+        double v = ((double)H[0] + (double)L[0]) + ((double)H[1] + (double)L[1]) +
+                   (((double)H[2] + (double)L[2]) + ((double)H[3] + (double)L[3]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[0][warp] = v;
@@ -534,7 +590,7 @@ __global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__re
             double D2 = 0.0;
             for (int g = 0; g < 8; ++g) D2 += red[0][g];
             const double n = (double)((w.d + 255) / 256);
-            const double rel = 2.0 * (2.9e-14 + 2.0 * n * (n + 4.0) * 3.56e-15 + 300.0 * 1.12e-16);
+            const double rel = 2.0 * (2.9e-14 + 2.0 * n * (n + 4.0) * 3.56e-15 + 1100.0 * 1.12e-16);
             const double err = rel * fabs(D2) + 1e-300;
             const double lo = D2 - err, hi = D2 + err;
             w.lo2[q] = lo;
@@ -577,12 +633,57 @@ __global__ void classify2_kernel(CilWork w, int M) {
     w.q2[slot] = (unsigned long long)q | (maxc ? Q_MAX : 0ull) | (minc ? Q_MIN : 0ull);
 }
 
-// 5. tier 3: the exact value (exact.cuh) of every queued pair, one CTA per
-//    pair (grid-stride over the queue).
+// 5. tier 3: the exact value (exact.cuh) of every queued pair.
+//    exact_split_kernel (queues of at most EXS_CAP pairs): one CTA per
+//    (pair, segment of EXS_SEG elements); each adds its segment's exact digit
+//    sums into the pair's global accumulator (integer addition, so the
+//    order of the CTAs does not matter), and the pair's last CTA to arrive
+//    rounds the total once.  xacc and xarr are zeroed before the launch.
+__global__ void __launch_bounds__(256) exact_split_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
+                                                          const float *__restrict__ X2, int64_t ld2) {
+    __shared__ XdShared<256> sh;
+    const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[SC_Q2];
+    if (qlen > (unsigned long long)EXS_CAP) return;
+    const int64_t nseg = (w.d + EXS_SEG - 1) / EXS_SEG;
+    const int64_t items = (int64_t)qlen * nseg;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int64_t slot = it / nseg, sg = it - slot * nseg;
+        const unsigned long long ent = w.q2[slot];
+        const int64_t q = (int64_t)(ent & Q_IDX);
+        const int64_t i = q / w.n2, j = q - i * w.n2;
+        const int64_t t0 = sg * EXS_SEG, len = min((int64_t)EXS_SEG, w.d - t0);
+        long long S[XD];
+        const bool good = xd_block_digits<256>(X1 + i * ld1 + t0, X2 + j * ld2 + t0, len, sh, S);
+        if (threadIdx.x == 0) {
+            long long *acc = w.xacc + slot * XD;
+#pragma unroll 1
+            for (int k = 0; k < XD; ++k) atomicAdd((unsigned long long *)(acc + k), (unsigned long long)S[k]);
+            if (!good) atomicOr(&w.xarr[EXS_CAP + slot], 1u);
+            __threadfence();
+            if (atomicAdd(&w.xarr[slot], 1u) == (unsigned)(nseg - 1)) {
+                __threadfence();
+                long long T[XD];
+                const volatile long long *va = acc;
+#pragma unroll 1
+                for (int k = 0; k < XD; ++k) T[k] = va[k];
+                const bool bad = *(volatile unsigned *)&w.xarr[EXS_CAP + slot] != 0u;
+                const double v = bad ? __longlong_as_double(0x7ff8000000000000ll) : xd_round(T);
+                w.ex[q] = v;
+                w.flag[q] = 2;
+                if (ent & Q_MAX) atomicMax(&w.scal[SC_MAX], (unsigned long long)__double_as_longlong(v));
+                if (ent & Q_MIN) atomic_min_d(&w.scal[SC_MIN], v);
+            }
+        }
+    }
+}
+
+//    exact_kernel (longer queues): one CTA per pair (grid-stride over the
+//    queue).
 __global__ void __launch_bounds__(256) exact_kernel(CilWork w, const float *__restrict__ X1, int64_t ld1,
                                                     const float *__restrict__ X2, int64_t ld2) {
     __shared__ XdShared<256> sh;
     const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[SC_Q2];
+    if (qlen <= (unsigned long long)EXS_CAP) return;
     for (unsigned long long slot = blockIdx.x; slot < qlen; slot += gridDim.x) {
         const unsigned long long ent = w.q2[slot];
         const int64_t q = (int64_t)(ent & Q_IDX);
@@ -742,7 +843,7 @@ extern "C" rd_status cil_workspace_size(int64_t n1, int64_t n2, int64_t d, size_
 // magnitudes (u = 2^-24), taken here as (nchunk + S + 4)^2 2^-47.
 static float gram_gamma(const CilWork &w) {
     const double n = (double)(w.nchunk + w.S + 4);
-    const double g = (3.0 * 64.0 * (double)w.cs / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
+    const double g = ((double)w.np_ * 64.0 * (double)w.cs / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
                      n * n * 7.105427357601002e-15;
     return (float)(g * (1.0 + 1e-6));
 }
@@ -753,13 +854,14 @@ static rd_status tier1(const CilWork &w, const float *X1, int64_t ld1, const flo
     const int64_t n1 = w.n1, n2 = w.n2, np = n1 * n2;
     centre_kernel<<<(unsigned)((w.dp + 255) / 256), 256, 0, s>>>(X1, ld1, n1, X2, ld2, n2, w.d, w.dp, w.centre);
     note_launch();
-    pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(X1, ld1, n1, X2, ld2, w.d, w.dp, w.centre, w.hi, w.lo, w.N,
-                                                    w.H, w.L, w.E, w.Hf, w.Lf, w.Ef);
+    pack_kernel<<<(unsigned)(n1 + n2), 256, 0, s>>>(X1, ld1, n1, X2, ld2, w.d, w.dp, w.centre, w.hi,
+                                                    w.np_ == 3 ? w.lo : nullptr, w.N, w.H, w.L, w.E, w.Hf, w.Lf,
+                                                    w.Ef);
     note_launch();
-    rd_status st = launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.S, w.cs, w.Ppart,
+    rd_status st = launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.S, w.cs, (int)w.np_, w.Ppart,
                                   reinterpret_cast<uint32_t *>(&w.scal[SC_TIMEOUT]), s);
     if (st) return st;
-    d2_bound_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(w, gram_gamma(w));
+    d2_bound_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(w, gram_gamma(w), w.np_ == 1 ? 1 : 0);
     note_launch();
     return RD_OK;
 }
@@ -828,6 +930,10 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
         note_launch();
     }
     {
+        RD_CUDA_TRY(cudaMemsetAsync(w.xacc, 0, sizeof(long long) * EXS_CAP * XD + sizeof(unsigned) * 2 * EXS_CAP,
+                                    s));
+        exact_split_kernel<<<2 * N_SM, 256, 0, s>>>(w, X1, ld1, X2, ld2);
+        note_launch();
         const unsigned g3 = (unsigned)(np < 2 * N_SM ? np : 2 * N_SM);
         exact_kernel<<<g3, 256, 0, s>>>(w, X1, ld1, X2, ld2);
         note_launch();
@@ -871,9 +977,31 @@ extern "C" rd_status cil_gram_only(int64_t n1, int64_t n2, int64_t d, void *d_wo
     if (n1 < 1 || n2 < 1 || d < 1 || !d_work || (((uintptr_t)d_work) & 255)) return RD_ERR_INVALID_ARG;
     CilWork w = layout(n1, n2, d, d_work);
     if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
-    if (flops) *flops = 3.0 * 2.0 * (double)n1 * (double)n2 * (double)w.dp;
-    return launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.S, w.cs, w.Ppart,
+    if (flops) *flops = (double)w.np_ * 2.0 * (double)n1 * (double)n2 * (double)w.dp;
+    return launch_gram_tc(w.hi, w.lo, n1, n2, w.dp, w.S, w.cs, (int)w.np_, w.Ppart,
                           reinterpret_cast<uint32_t *>(&w.scal[SC_TIMEOUT]), (cudaStream_t)stream);
+}
+
+extern "C" rd_status cil_set_gram_products(int32_t mode) {
+    if (mode != 0 && mode != 1 && mode != 3) return RD_ERR_INVALID_ARG;
+    g_gram_products.store(mode == 0 ? 3 : mode);
+    return RD_OK;
+}
+
+extern "C" rd_status cil_queue_lengths(int64_t n1, int64_t n2, int64_t d, const void *d_work, size_t work_bytes,
+                                      int64_t *d_out, void *stream) {
+    if (n1 < 1 || n2 < 1 || d < 1 || !d_work || !d_out || (((uintptr_t)d_work) & 255)) return RD_ERR_INVALID_ARG;
+    CilWork w = layout(n1, n2, d, const_cast<void *>(d_work));
+    if (w.bytes > work_bytes) return RD_ERR_INVALID_ARG;
+    static_assert(SC_Q2 == SC_Q1 + 1, "adjacent queue slots");
+    RD_CUDA_TRY(cudaMemcpyAsync(d_out, &w.scal[SC_Q1], 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                                (cudaStream_t)stream));
+    return RD_OK;
+}
+
+extern "C" int32_t cil_gram_products(int64_t n1, int64_t n2, int64_t d) {
+    if (n1 < 1 || n2 < 1 || d < 1) return -1;
+    return (int32_t)layout(n1, n2, d, nullptr).np_;
 }
 
 extern "C" rd_status cil_features(const float *d_X1, int64_t ld1, int64_t n1, const float *d_X2, int64_t ld2,

@@ -109,6 +109,46 @@ struct XdShared {
     int bad;
 };
 
+// The digit sums S[0..XD-1] of x[0..d) and y[0..d) (every thread of the
+// block calls it; S and the return value valid in thread 0): the exact
+// integer N of the segment's terms, sum S[k] 2^(32 k), unnormalised, so the
+// sums of several segments add digit by digit in any order (each stays
+// below 3 d_total 2^32 < 2^63 for d_total < 2^28).  Returns false when an
+// element is not finite.
+template <int NT>
+__device__ bool xd_block_digits(const float *__restrict__ x, const float *__restrict__ y, int64_t d,
+                                XdShared<NT> &sh, long long *S) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    long long *a = sh.acc + tid;
+#pragma unroll
+    for (int k = 0; k < XD; ++k) a[k * NT] = 0ll;
+    if (tid == 0) sh.bad = 0;
+    bool ok = true;
+    for (int64_t t = tid; t < d; t += NT) ok &= xd_term(a, NT, __ldg(x + t), __ldg(y + t));
+    __syncthreads();   // sh.bad cleared before any thread sets it
+    if (!ok) sh.bad = 1;
+#pragma unroll 1
+    for (int k = 0; k < XD; ++k) {
+        long long v = a[k * NT];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh.wsum[k * (NT / 32) + warp] = v;
+    }
+    __syncthreads();
+    bool good = true;
+    if (tid == 0) {
+#pragma unroll 1
+        for (int k = 0; k < XD; ++k) {
+            long long s = 0;
+            for (int w = 0; w < NT / 32; ++w) s += sh.wsum[k * (NT / 32) + w];
+            S[k] = s;
+        }
+        good = !sh.bad;
+    }
+    __syncthreads();   // the shared arrays may be reused by the next call
+    return good;
+}
+
 // d2 of x[0..d) and y[0..d) by a whole block of NT threads (every thread
 // calls it); with MAX also max_t |fl64(x_t - y_t)| (the FP64 difference
 // rounded to nearest).  Results valid in thread 0; d2 is NaN when an

@@ -1,12 +1,18 @@
 // Tensor-core Gram product for the correlation integral (the one dense
-// contraction of the path): P_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j, bf16
-// operands, FP32 accumulation in tensor memory, accumulated over K chunks
-// whose partials are summed with compensation.
+// contraction of the path), in one of two forms:
+//   three products  P_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j (tight: only
+//                   lo.lo is dropped),
+//   one product     P_ij = hi_i.hi_j (a third of the MMA work and half the
+//                   operand bytes; the caller's bound covers the dropped
+//                   cross terms by Cauchy-Schwarz on the parts' norms),
+// bf16 operands, FP32 accumulation in tensor memory, accumulated over K
+// chunks whose partials are summed with compensation.
 //
 // Blackwell (sm_100 family) structure, written with inline PTX:
 //   * TMA (cp.async.bulk.tensor) loads 128-row x 64-column bf16 tiles of the
-//     hi and lo parts of both pattern sets into 128-byte-swizzled shared
-//     memory, three stages deep, completion tracked by mbarriers;
+//     hi (and lo) parts of both pattern sets into 128-byte-swizzled shared
+//     memory, three stages of four tiles (six of two for one product) deep,
+//     completion tracked by mbarriers;
 //   * one elected thread issues tcgen05.mma (M = N = 128, K = 16, kind::f16
 //     with bf16 inputs, FP32 accumulator in TMEM) into two alternating TMEM
 //     accumulators, one K chunk each (the chunk length bounds the FP32
@@ -30,11 +36,19 @@
 
 namespace rdcil {
 
-static constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
+static constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;
 static constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;              // 16 KiB
-static constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;             // A hi, A lo, B hi, B lo
-static constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
-static_assert((2 * TC_STAGES + 5) * 8 + 4 <= 256, "barrier area");
+// per product count: tiles per stage (A hi, A lo, B hi, B lo / A hi, B hi)
+// and stages, 192 KiB of operands either way
+template <int NP> struct GramShape {
+    static constexpr int TILES = NP == 3 ? 4 : 2;
+    static constexpr int STAGES = NP == 3 ? 3 : 6;
+    static constexpr int STAGE_BYTES = TILES * TC_TILE_BYTES;
+    static_assert(NP == 1 || NP == 3, "one or three products");
+    static_assert((2 * STAGES + 5) * 8 + 4 <= 256, "barrier area");
+};
+static constexpr int TC_SMEM = 3 * 4 * TC_TILE_BYTES + 1024 + 256;
+static_assert(GramShape<1>::STAGES * GramShape<1>::STAGE_BYTES == 3 * 4 * TC_TILE_BYTES, "same operand area");
 static constexpr uint32_t TC_WAIT_LIMIT = MBAR_WAIT_LIMIT;           // bounded spin (~seconds)
 
 // One CTA per (output tile t, K segment s): grid = ntiles * S, block = 192
@@ -51,10 +65,13 @@ static constexpr uint32_t TC_WAIT_LIMIT = MBAR_WAIT_LIMIT;           // bounded 
 //             Ppart[(s * 2 + {0, 1}) * n1 * n2 + i * n2 + j].
 // TMEM columns: [0,128) and [128,256) accumulators, [256,384) sum hi,
 // [384,512) sum lo; warp w may access TMEM lanes 32 (w % 4) .. +31 (rows).
+// NP = 1 never reads tm_lo.
+template <int NP>
 __global__ void __launch_bounds__(192, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int n1, int n2,
                int dp, int ntj, int S, int cs, float *__restrict__ Ppart, uint32_t *__restrict__ status,
                uint32_t spin) {
+    constexpr int TC_STAGES = GramShape<NP>::STAGES, TC_STAGE_BYTES = GramShape<NP>::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + TC_STAGES * TC_STAGE_BYTES);
@@ -107,10 +124,15 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
             uint8_t *st = smem + q * TC_STAGE_BYTES;
             mbar_expect_tx(&full[q], TC_STAGE_BYTES);
             const int k = (k_lo + it) * TC_BK;
-            tma_load_2d(st, &tm_hi, k, i0, &full[q]);
-            tma_load_2d(st + TC_TILE_BYTES, &tm_lo, k, i0, &full[q]);
-            tma_load_2d(st + 2 * TC_TILE_BYTES, &tm_hi, k, n1 + j0, &full[q]);
-            tma_load_2d(st + 3 * TC_TILE_BYTES, &tm_lo, k, n1 + j0, &full[q]);
+            if (NP == 3) {
+                tma_load_2d(st, &tm_hi, k, i0, &full[q]);
+                tma_load_2d(st + TC_TILE_BYTES, &tm_lo, k, i0, &full[q]);
+                tma_load_2d(st + 2 * TC_TILE_BYTES, &tm_hi, k, n1 + j0, &full[q]);
+                tma_load_2d(st + 3 * TC_TILE_BYTES, &tm_lo, k, n1 + j0, &full[q]);
+            } else {
+                tma_load_2d(st, &tm_hi, k, i0, &full[q]);
+                tma_load_2d(st + TC_TILE_BYTES, &tm_hi, k, n1 + j0, &full[q]);
+            }
             issued = it + 1;
         }
     } else if (threadIdx.x == 32) {
@@ -133,13 +155,19 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
 #pragma unroll
                 for (int kk = 0; kk < TC_BK / 16; ++kk) {
                     const uint32_t off = kk * 32;   // 16 bf16 = 32 bytes along K inside the swizzle atom
-                    const uint64_t ah = smem_desc_sw128(base + off);
-                    const uint64_t al = smem_desc_sw128(base + TC_TILE_BYTES + off);
-                    const uint64_t bh = smem_desc_sw128(base + 2 * TC_TILE_BYTES + off);
-                    const uint64_t bl = smem_desc_sw128(base + 3 * TC_TILE_BYTES + off);
-                    mma_bf16(dacc, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
-                    mma_bf16(dacc, ah, bl, idesc, 1u);
-                    mma_bf16(dacc, al, bh, idesc, 1u);
+                    if (NP == 3) {
+                        const uint64_t ah = smem_desc_sw128(base + off);
+                        const uint64_t al = smem_desc_sw128(base + TC_TILE_BYTES + off);
+                        const uint64_t bh = smem_desc_sw128(base + 2 * TC_TILE_BYTES + off);
+                        const uint64_t bl = smem_desc_sw128(base + 3 * TC_TILE_BYTES + off);
+                        mma_bf16(dacc, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
+                        mma_bf16(dacc, ah, bl, idesc, 1u);
+                        mma_bf16(dacc, al, bh, idesc, 1u);
+                    } else {
+                        const uint64_t ah = smem_desc_sw128(base + off);
+                        const uint64_t bh = smem_desc_sw128(base + TC_TILE_BYTES + off);
+                        mma_bf16(dacc, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
+                    }
                 }
                 mma_commit(&empty[q]);   // stage free once these MMAs have read it
             }
@@ -262,14 +290,17 @@ static bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t dp)
     return r == CUDA_SUCCESS;
 }
 
-// Preconditions (checked): hi/lo 16-byte aligned, dp a multiple of 64,
-// 1 <= S <= dp / 64, cs >= 1 (K steps of 64 per accumulator chunk).
-// Ppart holds S * 2 * n1 * n2 floats (16-byte aligned).
+// Preconditions (checked): hi (and lo for three products) 16-byte aligned,
+// dp a multiple of 64, 1 <= S <= dp / 64, cs >= 1 (K steps of 64 per
+// accumulator chunk), np_ 1 or 3.  Ppart holds S * 2 * n1 * n2 floats
+// (16-byte aligned).
 static uint32_t g_spin_limit = TC_WAIT_LIMIT;
 void set_gram_spin_limit(uint32_t n) { g_spin_limit = n ? n : TC_WAIT_LIMIT; }
 
 rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2, int64_t dp, int64_t S, int64_t cs,
-                         float *Ppart, uint32_t *status, cudaStream_t s) {
+                         int np_, float *Ppart, uint32_t *status, cudaStream_t s) {
+    if (np_ != 1 && np_ != 3) return RD_ERR_INVALID_ARG;
+    if (np_ == 1) lo = hi;   // not read
     if ((((uintptr_t)hi | (uintptr_t)lo | (uintptr_t)Ppart) & 15) || (dp % TC_BK) || n1 < 1 || n2 < 1 || S < 1 ||
         S > dp / TC_BK || cs < 1 || cs > dp / TC_BK)
         return RD_ERR_INVALID_ARG;
@@ -278,12 +309,13 @@ rd_status launch_gram_tc(const void *hi, const void *lo, int64_t n1, int64_t n2,
     if (nti * ntj * S > 0x7FFFFFFF) return RD_ERR_UNSUPPORTED;
     CUtensorMap mh, ml;
     if (!make_map(&mh, hi, n1 + n2, dp) || !make_map(&ml, lo, n1 + n2, dp)) return RD_ERR_CUDA;
+    auto kern = np_ == 3 ? gram_tc_kernel<3> : gram_tc_kernel<1>;
     {
-        rd_status ast = smem_attr(gram_tc_kernel, TC_SMEM);
+        rd_status ast = smem_attr(kern, TC_SMEM);
         if (ast) return ast;
     }
-    gram_tc_kernel<<<(unsigned)(nti * ntj * S), 192, TC_SMEM, s>>>(mh, ml, (int)n1, (int)n2, (int)dp, (int)ntj,
-                                                                   (int)S, (int)cs, Ppart, status, g_spin_limit);
+    kern<<<(unsigned)(nti * ntj * S), 192, TC_SMEM, s>>>(mh, ml, (int)n1, (int)n2, (int)dp, (int)ntj, (int)S,
+                                                         (int)cs, Ppart, status, g_spin_limit);
     note_launch();
     return cuda_status(cudaGetLastError());
 }

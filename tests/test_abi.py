@@ -213,3 +213,26 @@ def test_structs_match_the_header_layout(tmp_path, libpath):
         assert ctypes.sizeof(cls) == got[(cs, "sizeof")], cs
         for n in names:
             assert getattr(cls, n).offset == got[(cs, n)], (cs, n)
+
+
+def test_gram_product_count_choice_without_gpu(libpath):
+    """cil_gram_products (host only): three products by default at every
+    size; cil_set_gram_products selects one or three, 0 restores the
+    default, anything else is rejected."""
+    L = ctypes.CDLL(libpath)
+    L.cil_gram_products.restype = ctypes.c_int32
+    L.cil_gram_products.argtypes = [ctypes.c_int64] * 3
+    L.cil_set_gram_products.restype = ctypes.c_int32
+    L.cil_set_gram_products.argtypes = [ctypes.c_int32]
+    try:
+        assert L.cil_gram_products(1024, 1024, 32768) == 3
+        assert L.cil_gram_products(64, 64, 4096) == 3
+        assert L.cil_gram_products(0, 64, 4096) == -1
+        assert L.cil_set_gram_products(1) == 0
+        assert L.cil_gram_products(1024, 1024, 32768) == 1
+        assert L.cil_gram_products(64, 64, 4096) == 1
+        assert L.cil_set_gram_products(0) == 0
+        assert L.cil_gram_products(64, 64, 4096) == 3
+        assert L.cil_set_gram_products(2) == 1                 # RD_ERR_INVALID_ARG
+    finally:
+        L.cil_set_gram_products(0)

@@ -217,20 +217,27 @@ def test_exact_d2_long_patterns(p):
     assert np.array_equal(g.cpu().numpy(), o)
 
 
-def test_paper_scale_every_pair(p):
+@pytest.mark.parametrize("products", [1, 3])
+def test_paper_scale_every_pair(p, products):
     """2 x 1024 patterns of d = 32768 (the SCIL scale, as timed by bench.py
     --gram-large), every one of the 1.05e6 bins checked without the GPU's
     approximate stage: a float64 Gram on the host (numpy/BLAS) gives every
     d2 within the dot-product error bound (d + 2) 2^-53 (|x|^2 + |y|^2 +
     2 |x| |y|); pairs whose interval could hold the maximum or meets a
     threshold are evaluated by the oracle exactly, all others are decided
-    by their interval."""
+    by their interval.  Both forms of the tensor-core Gram (three products,
+    the default, and one)."""
     n, G = 1024, 128
     X = W.cosine_patterns(2 * n, G, 2, 77, amp=0.8, offset=2.0)
     X1, X2 = X[:n], X[n:]
     t1, t2 = torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda()
-    g = p.cil(t1, t2, b=1.3, M=16)
-    torch.cuda.synchronize()
+    assert p.gram_products(n, n, X.shape[1]) == 3
+    try:
+        p.set_gram_products(products)
+        g = p.cil(t1, t2, b=1.3, M=16)
+        torch.cuda.synchronize()
+    finally:
+        p.set_gram_products(0)
     assert int(g["n_rechecked"]) >= 0
     R0 = float(g["R0"])
     radii = g["radii"].cpu().numpy()
@@ -261,3 +268,91 @@ def test_paper_scale_every_pair(p):
         d2 = oracle.d2_exact(X1[i], X2[j])
         K[i, j] = int(sum(d2 < t for t in T))
     assert np.array_equal(bins, K.astype(np.uint8))
+
+
+# ---------------------------------------------------------------------------
+# The one-product Gram (hi.hi alone, cross terms bounded by Cauchy-Schwarz),
+# selected in place of the default three products: same bits, only the
+# number of pairs re-evaluated beyond tier 1 moves.
+# ---------------------------------------------------------------------------
+@pytest.fixture
+def one_product(p):
+    p.set_gram_products(1)
+    yield
+    p.set_gram_products(0)
+
+
+@pytest.mark.parametrize("n1,n2,d", [(1, 1, 1), (3, 5, 7), (64, 64, 4096), (65, 130, 4100), (200, 200, 3000)])
+def test_one_product_clustered_bit_exact(p, one_product, n1, n2, d):
+    assert p.gram_products(n1, n2, d) == 1
+    X1 = W.clustered_patterns(n1, d, 100 + n1)
+    X2 = W.clustered_patterns(n2, d, 200 + n2)
+    g, o = run_both(p, X1, X2, b=1.1, M=16)
+    assert_same(g, o)
+
+
+def test_one_product_c3_shape_and_far_data(p, one_product):
+    X = W.cosine_patterns(512, 128, 2, 33, amp=0.8, offset=2.0)
+    res, o = run_both(p, X[:256], X[256:], b=1.3, M=16)
+    assert_same(res, o)
+    assert int(res["n_rechecked"]) < 0.05 * 256 * 256
+    X1 = W.clustered_patterns(90, 2000, 9) + 50.0
+    X2 = W.clustered_patterns(70, 2000, 10) + 50.0
+    t1, t2 = torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda()
+    a = p.cil(t1, t2, b=1.02, M=32)
+    e = p.cil_exact(t1, t2, b=1.02, M=32)
+    assert float(a["R0"]) == float(e["R0"])
+    assert torch.equal(a["bins"], e["bins"])
+
+
+@pytest.mark.parametrize("n1,n2,d,off", [(64, 64, 4096, 0.0), (130, 70, 3000, 20.0), (256, 256, 32768, 2.0),
+                                         (5, 300, 128, 0.0)])
+def test_one_product_bound_holds(p, one_product, n1, n2, d, off):
+    """The one-product interval holds every pair's exact d2 with room to
+    spare (error below half the bound: the Cauchy-Schwarz terms assume the
+    worst alignment of the dropped parts); its width stays within the
+    predicted scale: 4 (|hi_i| |lo_j| + |lo_i| |hi_j|), about 2^-7 |x_i| |x_j|
+    (bound 2^-5, since the library's centre is a sample mean)."""
+    X1 = W.clustered_patterns(n1, d, 500 + n1) + off
+    X2 = W.clustered_patterns(n2, d, 600 + n2) + off
+    A, m = p.cil_approx(torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda())
+    ex = oracle.pair_d2(X1, X2)
+    A, m = A.cpu().numpy(), m.cpu().numpy()
+    assert np.all(np.abs(A - ex) <= 0.5 * m), (np.abs(A - ex) / m).max()
+    c = np.concatenate([X1, X2]).astype(np.float64)
+    c = c - c.mean(0)       # near the library's centre; the norms set the scale only
+    nrm = np.sqrt((c * c).sum(1))
+    scale = nrm[:n1, None] * nrm[None, n1:] + 1e-30
+    assert np.all(m <= 2.0 ** -5 * scale + 1e-6 * ex + 1e-9)
+
+
+def test_one_product_mcil_bit_exact(p, one_product):
+    """The multi-feature correlation integral takes the same tier-1 stage."""
+    X = W.cosine_patterns(37 + 90, 32, 2, 31 + 32 + 37, amp=1.2, offset=0.7)
+    g = p.mcil(torch.from_numpy(X[:37]).cuda(), torch.from_numpy(X[37:]).cuda(), 32, 2, b=1.3, M=12)
+    o = oracle.mcil(X[:37], X[37:], 32, 2, b=1.3, M=12, mask=63, scale=False)
+    torch.cuda.synchronize()
+    assert np.array_equal(g["bins"].cpu().numpy(), o["bins"])
+    assert np.array_equal(g["counts"].cpu().numpy(), o["counts"])
+
+
+def test_both_forms_at_paper_scale_agree(p):
+    """The G-large shape under both forms: identical radii, bins and counts."""
+    n = 1024
+    X = W.cosine_patterns(2 * n, 128, 2, 78, amp=0.8, offset=2.0)
+    t1, t2 = torch.from_numpy(X[:n]).cuda(), torch.from_numpy(X[n:]).cuda()
+    out, ql = {}, {}
+    try:
+        for k in (1, 3):
+            p.set_gram_products(k)
+            out[k] = p.cil(t1, t2, b=1.3, M=16)
+            ql[k] = p.cil_queue_lengths(n, n, X.shape[1])
+    finally:
+        p.set_gram_products(0)
+    for key in ("radii", "bins", "counts"):
+        assert torch.equal(out[1][key], out[3][key]), key
+    # tier 3 is what n_rechecked reports; the wider interval leaves more to tier 2
+    for k in (1, 3):
+        assert ql[k][1] == int(out[k]["n_rechecked"]) >= 1      # the maximum at least
+        assert ql[k][0] >= ql[k][1]
+    assert ql[1][0] > ql[3][0]
