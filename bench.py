@@ -58,7 +58,7 @@ FP32_INST_PER_CELL = {W.FHN: 15, W.GM: 20, W.DIFF: 10, W.BZ: 22}
 # the full launch's traffic.
 STEPPER_TRAFFIC = {
     "c2": {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488, "7c8c62601c860730": 4223488},
-    "c4": {"250da058b95b29c7": 1285591296},
+    "c4": {"250da058b95b29c7": 1285591296, "02a4865c70d95aa1": 1284856064},
 }
 STEPPER_SOURCES = ["paper_2203_14742_b300/csrc/stepper.cu", "paper_2203_14742_b300/csrc/tile.cuh",
                    "paper_2203_14742_b300/csrc/common.cuh"]
