@@ -332,8 +332,7 @@ def run_ours(args, rank, world, local_rank):
             e[1].record(stream)
             _check_int(p, sim, pipe)
             e[2].record(stream)
-            for (X1, X2), out in zip(pipe.views, pipe.cil_out):
-                p.cil(X1, X2, b=b, M=M, work=pipe.work, out=out)
+            pipe.run_cils()
             e[3].record(stream)
             p.synlik(pipe.bins, M, T, pipe.seed, y_obs=pipe.C, out=pipe.stats, work=pipe.syn_work)
             e[4].record(stream)
@@ -549,8 +548,7 @@ def c2_bench(p, torch, dev, stream, pk, src, reps=5):
         e[1].record(stream)
         _check_int(p, sim, pipe)
         e[2].record(stream)
-        for (X1, X2), out in zip(pipe.views, pipe.cil_out):
-            p.cil(X1, X2, b=cfg["b"], M=cfg["M"], work=pipe.work, out=out)
+        pipe.run_cils()
         p.synlik(pipe.bins, cfg["M"], cfg["T_res"], pipe.seed, y_obs=pipe.C, out=pipe.stats, work=pipe.syn_work)
         e[3].record(stream)
     torch.cuda.synchronize()

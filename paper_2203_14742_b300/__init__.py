@@ -761,9 +761,14 @@ class Pipeline:
     rtol, atol, s_max, max_attempts) or "imex" (rd_integrate_imex, each
     group's n_steps of its dt, diffusion implicit); law: "power" (R0 b^-k), "linear"
     (R0 - k (R0 - R_min) / M, b unused) or "fitted" (R0 b^-k with b fitted
-    so that R_M = R_min, b unused).  RDODE groups need "rkc"."""
+    so that R_M = R_min, b unused).  RDODE groups need "rkc".  cil_streams:
+    the groups' correlation integrals (independent problems of a few small
+    launches each) run on that many side streams at once, each with its own
+    workspace, forked from and joined back into the calling stream (1: all
+    on the calling stream)."""
 
-    def __init__(self, groups, sets, M, b, T, seed, device=None, integrator="euler", rkc=None, law="power"):
+    def __init__(self, groups, sets, M, b, T, seed, device=None, integrator="euler", rkc=None, law="power",
+                 cil_streams=8):
         if integrator not in ("euler", "rkc", "imex") or law not in ("power", "linear", "fitted"):
             raise ValueError("integrator / law")
         self.sim = Simulation(groups, device=device)
@@ -799,7 +804,33 @@ class Pipeline:
         self.residual = torch.empty((self.sim.n_real_total, 2), dtype=torch.float64, device=self.dev)
         dmax = max(x.shape[1] for x, _ in self.views)
         self.work, self.work_bytes = _workspace(self.n1, self.n2, dmax, self.dev)
+        ns = max(1, min(int(cil_streams), P))
+        self.side = [torch.cuda.Stream(device=self.dev) for _ in range(ns)] if ns > 1 else []
+        self.side_work = [torch.empty(self.work_bytes, dtype=torch.uint8, device=self.dev) for _ in self.side]
         self.graph = None
+
+    def run_cils(self):
+        """Every group's correlation integral (radii, bins, counts, C), in
+        stream order after the calling stream's prior work and before its
+        later work."""
+        fn = {"linear": "cil_features_linear", "fitted": "cil_features_fitted"}.get(self.law, "cil_features")
+        if not self.side:
+            for (X1, X2), out in zip(self.views, self.cil_out):
+                _cil_call(fn, X1, X2, self.b, self.M, None, self.work, out)
+            return
+        main = torch.cuda.current_stream(self.dev)
+        fork = torch.cuda.Event()
+        fork.record(main)
+        for st in self.side:
+            st.wait_event(fork)
+        for i, ((X1, X2), out) in enumerate(zip(self.views, self.cil_out)):
+            k = i % len(self.side)
+            with torch.cuda.stream(self.side[k]):
+                _cil_call(fn, X1, X2, self.b, self.M, None, self.side_work[k], out)
+        for st in self.side:
+            join = torch.cuda.Event()
+            join.record(st)
+            main.wait_event(join)
 
     def run(self, reinit=True):
         if reinit:
@@ -814,9 +845,7 @@ class Pipeline:
             _check("rd_integrate_rkc", lib().rd_integrate_rkc(
                 self.sim.handle, _ptr(self.sim.fields), C.byref(self.rkc_opts), _ptr(self.rkc_stats),
                 _ptr(self.residual), _stream()))
-        fn = {"linear": "cil_features_linear", "fitted": "cil_features_fitted"}.get(self.law, "cil_features")
-        for (X1, X2), out in zip(self.views, self.cil_out):
-            _cil_call(fn, X1, X2, self.b, self.M, None, self.work, out)
+        self.run_cils()
         synlik(self.bins, self.M, self.T, self.seed, y_obs=self.C, out=self.stats, work=self.syn_work)
 
     def capture(self):

@@ -174,3 +174,31 @@ def test_first_call_of_a_handle_captures_in_a_graph(p, kind):
     torch.cuda.synchronize()
     assert torch.equal(sim.fields, eager.fields)
     assert sim.sync_status() == 0 and eager.sync_status() == 0
+
+
+def test_concurrent_correlation_integrals_match_sequential(p):
+    """Twelve groups: their correlation integrals forked over four side
+    streams (each with its own workspace) give the same bits as one after
+    another on the calling stream, eagerly and replayed from a graph."""
+    gds = [W.group(W.FHN if i % 2 == 0 else W.GM, 32, 32,
+                   (2.8e-4, 0.05, 10.0, 0.95) if i % 2 == 0 else (2.5e-4, 0.01, 1.0, 0.5),
+                   2 ** -8, 60 + 10 * i, (-0.05, 0.05) if i % 2 == 0 else (0.0, 0.01), 900 + i, 1 + 2 * (i % 2))
+           for i in range(12)]
+    outs = []
+    for ns in (1, 4):
+        groups = [p.Group.from_dict(g) for g in gds]
+        pipe = p.Pipeline(groups, [(16, 16, g["species_mask"]) for g in gds], M=8, b=1.3, T=40, seed=5,
+                          cil_streams=ns)
+        assert len(pipe.side) == (0 if ns == 1 else ns)
+        pipe.run()
+        torch.cuda.synchronize()
+        outs.append(snapshot(pipe))
+        if ns > 1:
+            pipe.capture()
+            pipe.replay()
+            torch.cuda.synchronize()
+            again = snapshot(pipe)
+            for k in outs[-1]:
+                assert torch.equal(outs[-1][k], again[k]), k
+    for k in outs[0]:
+        assert torch.equal(outs[0][k], outs[1][k]), k
