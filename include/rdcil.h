@@ -350,8 +350,9 @@ int32_t rd_rkc_get_variant(int32_t G);
  * rd_variant_shape: the tile shape of variant `variant` at grid side G
  *   (32, 64 or 128): shape = host int32[3] receiving {kind (0 = separate u
  *   and v tiles, 1 = float2 (u, v) tiles, 2 = separate tiles kept in TY + 1
- *   rotating row slots, which saves a register copy per node and step),
- *   TY, TX}.  RD_ERR_INVALID_ARG for an unknown G or variant or a null
+ *   rotating row slots, which saves a register copy per node and step,
+ *   3 = float2 (u, v) tiles in rotating row slots, whose neighbour sums are
+ *   paired adds), TY, TX}.  RD_ERR_INVALID_ARG for an unknown G or variant or a null
  *   shape.
  * rd_autotune: time every variant on the largest group of each (model, G)
  *   class present in h for `steps` Euler steps, keep the fastest (and, if

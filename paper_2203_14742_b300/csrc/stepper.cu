@@ -264,6 +264,103 @@ __device__ __forceinline__ void run_rot(float *__restrict__ fields, int64_t fiel
     residual_from_global<MODEL, G, Sync>(base, p0, p1, p2, p3, residual, status, r, sm, sy);
 }
 
+// The packed form of run_rot (tile2_step_rot: (u, v) pairs, paired
+// neighbour sums), bit-identical to it.
+template <int MODEL, int G, int TY, int TX, int OFF, class Sync>
+__device__ __forceinline__ void rot2_one(float *sm, int64_t n, int tx, int ty, int src, float2 (&w)[TY + 1][TX],
+                                         const CoefF &cf, Sync sy) {
+    using T = Tiling2<G, TY, TX>;
+    float2 *hb = reinterpret_cast<float2 *>(sm) + (int)(n & 1) * (T::HALO_F2 / 2);
+    halo2_put_rot<G, TY, TX, OFF>(hb, tx, ty, w);
+    sy.sync();
+    tile2_step_rot<MODEL, G, TY, TX, OFF>(hb, tx, ty, src, w, cf);
+}
+
+template <int MODEL, int G, int TY, int TX, int OFF, class Sync>
+__device__ __forceinline__ int rot2_chain(float *sm, int64_t &n, int64_t steps, int tx, int ty, int src,
+                                          float2 (&w)[TY + 1][TX], const CoefF &cf, Sync sy) {
+    if constexpr (OFF == 0) {
+        return -1;
+    } else {
+        if (n >= steps) return OFF;
+        rot2_one<MODEL, G, TY, TX, OFF>(sm, n, tx, ty, src, w, cf, sy);
+        ++n;
+        return rot2_chain<MODEL, G, TY, TX, OFF - 1>(sm, n, steps, tx, ty, src, w, cf, sy);
+    }
+}
+
+template <int G, int TY, int TX, int OFF>
+__device__ __forceinline__ void rot2_store_any(float *base, int tx, int ty, int off, const float2 (&w)[TY + 1][TX]) {
+    if constexpr (OFF > TY) {
+        return;
+    } else {
+        if (off == OFF) {
+            float a[TY][TX], b[TY][TX];
+#pragma unroll
+            for (int i = 0; i < TY; ++i)
+#pragma unroll
+                for (int c = 0; c < TX; ++c) {
+                    a[i][c] = w[(i + OFF) % (TY + 1)][c].x;
+                    b[i][c] = w[(i + OFF) % (TY + 1)][c].y;
+                }
+            tile_store_s<G, TY, TX>(base, tx, ty, a, b);
+        } else {
+            rot2_store_any<G, TY, TX, OFF + 1>(base, tx, ty, off, w);
+        }
+    }
+}
+
+template <int MODEL, int G, int TY, int TX, class Sync = SyncAll>
+__device__ __forceinline__ void run_rot2(float *__restrict__ fields, int64_t field_offset, int r, int64_t steps,
+                                         const CoefF &cf, double p0, double p1, double p2, double p3,
+                                         double *__restrict__ residual, uint32_t *__restrict__ status, float *sm,
+                                         Sync sy = Sync{}) {
+    using T = Tiling<G, TY, TX>;
+    static_assert(Tiling2<G, TY, TX>::SMEM == T::SMEM, "same halo ring bytes as the scalar tiles");
+    constexpr int NX = T::NX, R = TY + 1;
+    const int tid = sy.tid();
+    const int tx = tid % NX, ty = tid / NX;
+    float *base = fields + field_offset + (int64_t)r * 2 * G * G;
+    float2 w[R][TX];
+    {
+        float a[TY][TX], b[TY][TX];
+        tile_load_s<G, TY, TX>(base, tx, ty, a, b);
+        tile_to_state<MODEL, TY, TX>(a, b, cf);
+#pragma unroll
+        for (int i = 0; i < TY; ++i)
+#pragma unroll
+            for (int c = 0; c < TX; ++c) w[i][c] = make_float2(a[i][c], b[i][c]);
+#pragma unroll
+        for (int c = 0; c < TX; ++c) w[TY][c] = make_float2(0.f, 0.f);
+    }
+    const int src = serp_src<NX>(tx);
+    int64_t n = 0;
+    int off = 0;
+    for (;;) {
+        if (n >= steps) { off = 0; break; }
+        rot2_one<MODEL, G, TY, TX, 0>(sm, n, tx, ty, src, w, cf, sy);
+        ++n;
+        const int o = rot2_chain<MODEL, G, TY, TX, R - 1>(sm, n, steps, tx, ty, src, w, cf, sy);
+        if (o >= 0) { off = o; break; }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int c = 0; c < TX; ++c) from_state<MODEL>(w[i][c].x, w[i][c].y, cf);
+    rot2_store_any<G, TY, TX, 0>(base, tx, ty, off, w);
+    residual_from_global<MODEL, G, Sync>(base, p0, p1, p2, p3, residual, status, r, sm, sy);
+}
+
+template <int MODEL, int G, int TY, int TX>
+__global__ void __launch_bounds__(Tiling<G, TY, TX>::NT, 1)
+rd_resident_rot2_kernel(float *__restrict__ fields, int64_t field_offset, int64_t steps, CoefF cf, double p0,
+                        double p1, double p2, double p3, double *__restrict__ residual,
+                        uint32_t *__restrict__ status) {
+    extern __shared__ float4 smem_f4[];
+    run_rot2<MODEL, G, TY, TX>(fields, field_offset, (int)blockIdx.x, steps, cf, p0, p1, p2, p3, residual, status,
+                               reinterpret_cast<float *>(smem_f4));
+}
+
 template <int MODEL, int G, int TY, int TX>
 __global__ void __launch_bounds__(Tiling<G, TY, TX>::NT, 1)
 rd_resident_rot_kernel(float *__restrict__ fields, int64_t field_offset, int64_t steps, CoefF cf, double p0,
@@ -290,15 +387,16 @@ rd_resident_scalar_kernel(float *__restrict__ fields, int64_t field_offset, int6
 // rd_autotune or the default table below.
 // ---------------------------------------------------------------------------
 struct Variant {
-    int packed, TY, TX;   // packed: 0 scalar u, v tiles; 1 float2 (u, v) tiles; 2 rotating scalar tiles
+    int packed, TY, TX;   // packed: 0 scalar u, v tiles; 1 float2 (u, v) tiles; 2 rotating scalar tiles;
+                          // 3 rotating float2 tiles
 };
 static constexpr int NVAR = 8;
 static constexpr Variant VAR32[NVAR] = {{0, 4, 4}, {1, 4, 4}, {0, 2, 4}, {1, 2, 4},
                                         {1, 2, 8}, {0, 2, 8}, {0, 4, 8}, {0, 2, 2}};
 static constexpr Variant VAR64[NVAR] = {{2, 4, 4}, {1, 4, 4}, {0, 2, 4}, {0, 4, 4},
                                         {0, 4, 8}, {0, 8, 4}, {2, 8, 4}, {0, 8, 8}};
-static constexpr Variant VAR128[NVAR] = {{2, 8, 4}, {1, 8, 4}, {2, 4, 8}, {0, 8, 4},
-                                         {0, 8, 8}, {0, 16, 4}, {0, 4, 8}, {1, 16, 4}};
+static constexpr Variant VAR128[NVAR] = {{3, 8, 4}, {2, 8, 4}, {1, 8, 4}, {2, 4, 8},
+                                         {0, 8, 4}, {0, 8, 8}, {0, 16, 4}, {1, 16, 4}};
 
 template <int G> constexpr Variant var_of(int i) {
     return G == 32 ? VAR32[i] : (G == 64 ? VAR64[i] : VAR128[i]);
@@ -313,7 +411,14 @@ static rd_status launch_variant(const GroupDev &g, float *fields, int64_t steps,
     constexpr Variant V = var_of<G>(VI);
     CoefF cf = make_coef(g);
     double *res = residual ? residual + 2 * g.real_base : nullptr;
-    if constexpr (V.packed == 2 && !RECORD) {
+    if constexpr (V.packed == 3 && !RECORD) {
+        using T = Tiling<G, V.TY, V.TX>;
+        auto kern = rd_resident_rot2_kernel<MODEL, G, V.TY, V.TX>;
+        rd_status ast = smem_attr(kern, (int)T::SMEM);
+        if (ast) return ast;
+        kern<<<g.n_real, T::NT, T::SMEM, s>>>(fields, g.field_offset, steps, cf, g.p[0], g.p[1], g.p[2], g.p[3],
+                                              res, status);
+    } else if constexpr (V.packed == 2 && !RECORD) {
         using T = Tiling<G, V.TY, V.TX>;
         auto kern = rd_resident_rot_kernel<MODEL, G, V.TY, V.TX>;
         rd_status ast = smem_attr(kern, (int)T::SMEM);
@@ -415,10 +520,11 @@ rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int
 // parameter groups, models and grid sizes).  Every CTA has 512 threads and
 // loops: take the next work unit from a global queue (units ordered
 // longest first), integrate it to the end, repeat.  A unit is one 128x128
-// realisation on all 512 threads (rotating 8x4 tiles), or two realisations
-// of 64x64 (rotating 4x4 tiles) or 32x32 (2x2 tiles) side by side, one per
-// half of the CTA (256 threads, named barrier 1 + half), so every SM keeps
-// 16 warps.  The per-node arithmetic is the same as in the per-group
+// realisation on all 512 threads (packed rotating 8x4 tiles: +6.5 % on FHN
+// and GM 128x128 over the scalar rotating tiles), or two realisations of
+// 64x64 (scalar rotating 4x4 tiles; packed measured 2-3 % slower there) or
+// 32x32 (2x2 tiles) side by side, one per half of the CTA (256 threads,
+// named barrier 1 + half), so every SM keeps 16 warps.  The per-node arithmetic is the same as in the per-group
 // kernels, so results are bit-identical to them.
 // ---------------------------------------------------------------------------
 struct BatchGroup {
@@ -442,8 +548,8 @@ static_assert(2 * Tiling<64, 4, 4>::SMEM <= BATCH_SMEM && Tiling<32, 2, 2>::SMEM
 template <int MODEL>
 __device__ __forceinline__ void batch_full(float *fields, const BatchGroup &g, int r, int64_t steps, double *res,
                                            uint32_t *status, float *sm) {
-    run_rot<MODEL, 128, 8, 4>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2], g.p[3], res, status,
-                              sm, SyncAll{});
+    run_rot2<MODEL, 128, 8, 4>(fields, g.field_offset, r, steps, g.cf, g.p[0], g.p[1], g.p[2], g.p[3], res, status,
+                               sm, SyncAll{});
 }
 
 template <int MODEL>

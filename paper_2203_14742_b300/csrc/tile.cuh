@@ -714,4 +714,82 @@ __device__ __forceinline__ void tile2_step(const float2 *hb, int tx, int ty, flo
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Packed rotating serpentine tiles: the rotating tiles above with each node's
+// (u, v) in one float2, so the neighbour sums of both species are three
+// paired adds (add.f32x2) instead of six, and the reaction update is euler2
+// (the operations of euler_cell in the same order).  Per node the
+// arithmetic is that of tile_step_rot, so the fields are bit-identical.
+// Halo ring: [buf 2][edge 2][NY][G] float2 in register order; within a
+// tile row, chunk h (nodes 2h, 2h+1 of every lane) of lane tx sits at float4
+// index h NX + tx, so each 16-byte store or load of a warp covers one
+// contiguous 512-byte run.
+// ---------------------------------------------------------------------------
+template <int NX, int TX>
+__device__ __forceinline__ void st_row2s(float2 *row, int tx, const float2 (&a)[TX]) {
+#pragma unroll
+    for (int h = 0; h < TX / 2; ++h)
+        *reinterpret_cast<float4 *>(row + 2 * (h * NX + tx)) =
+            make_float4(a[2 * h].x, a[2 * h].y, a[2 * h + 1].x, a[2 * h + 1].y);
+}
+
+template <int NX, int TX>
+__device__ __forceinline__ void ld_row2s(const float2 *row, int tx, float2 (&a)[TX]) {
+#pragma unroll
+    for (int h = 0; h < TX / 2; ++h) {
+        const float4 t = *reinterpret_cast<const float4 *>(row + 2 * (h * NX + tx));
+        a[2 * h] = make_float2(t.x, t.y);
+        a[2 * h + 1] = make_float2(t.z, t.w);
+    }
+}
+
+template <int G, int TY, int TX, int OFF>
+__device__ __forceinline__ void halo2_put_rot(float2 *hb, int tx, int ty, const float2 (&w)[TY + 1][TX]) {
+    constexpr int NY = Tiling2<G, TY, TX>::NY, NX = Tiling2<G, TY, TX>::NX, R = TY + 1;
+    st_row2s<NX, TX>(hb + (0 * NY + ty) * G, tx, w[OFF % R]);
+    st_row2s<NX, TX>(hb + (1 * NY + ty) * G, tx, w[(TY - 1 + OFF) % R]);
+}
+
+template <int MODEL, int G, int TY, int TX, int OFF>
+__device__ __forceinline__ void tile2_step_rot(const float2 *hb, int tx, int ty, int src, float2 (&w)[TY + 1][TX],
+                                               const CoefF &cf) {
+    constexpr int NY = Tiling2<G, TY, TX>::NY, NX = Tiling2<G, TY, TX>::NX, R = TY + 1;
+    float2 n0[TX];   // north neighbours of row 0: halo, or the row itself at the top edge
+    if (ty > 0) {
+        ld_row2s<NX, TX>(hb + (1 * NY + ty - 1) * G, tx, n0);
+    } else {
+#pragma unroll
+        for (int c = 0; c < TX; ++c) n0[c] = w[OFF % R][c];
+    }
+#pragma unroll
+    for (int i = 0; i < TY; ++i) {
+        const int pr = (i + OFF) % R;            // old row i
+        const int qr = (i + OFF + R - 1) % R;    // old row i - 1 (free slot for i = 0): receives new row i
+        const int sr = (i + 1 + OFF) % R;        // old row i + 1
+        float2 sl[TX];                           // south neighbours of the last row
+        if (i == TY - 1) {
+            if (ty < NY - 1) {
+                ld_row2s<NX, TX>(hb + (0 * NY + ty + 1) * G, tx, sl);
+            } else {
+#pragma unroll
+                for (int c = 0; c < TX; ++c) sl[c] = w[pr][c];
+            }
+        }
+        float2 x0, x1;
+        x0.x = __shfl_xor_sync(0xffffffffu, w[pr][0].x, 1);
+        x0.y = __shfl_xor_sync(0xffffffffu, w[pr][0].y, 1);
+        x1.x = __shfl_sync(0xffffffffu, w[pr][TX - 1].x, src);
+        x1.y = __shfl_sync(0xffffffffu, w[pr][TX - 1].y, src);
+#pragma unroll
+        for (int c = 0; c < TX; ++c) {
+            const float2 N = i == 0 ? n0[c] : w[qr][c];
+            const float2 S = i == TY - 1 ? sl[c] : w[sr][c];
+            const float2 L = c > 0 ? w[pr][c - 1] : x0, E = c < TX - 1 ? w[pr][c + 1] : x1;
+            const float2 sum = __fadd2_rn(__fadd2_rn(N, S), __fadd2_rn(L, E));
+            w[qr][c] = euler2<MODEL>(w[pr][c], sum, cf);
+        }
+    }
+}
+
 }  // namespace rdcil

@@ -96,14 +96,15 @@ def test_variant_shapes_are_valid_tilings(libpath):
     for G in (32, 64, 128):
         for v in range(p.lib().rd_n_variants()):
             packed, TY, TX = p.variant_shape(G, v)
-            assert packed in (0, 1, 2) and G % TY == 0 and G % TX == 0
+            assert packed in (0, 1, 2, 3) and G % TY == 0 and G % TX == 0
             NX, NY = G // TX, G // TY
             assert NX <= 32 and NX & (NX - 1) == 0 and NX % 2 == 0
             assert (NX * NY) % 32 == 0 and NX * NY <= 1024
             # the double-buffered halo ring of the variant fits one CTA
-            ring = {0: 2 * 2 * 2 * NY * G * 4, 1: 2 * 2 * NY * G * 8, 2: 2 * 2 * 2 * NY * G * 4}[packed]
+            ring = {0: 2 * 2 * 2 * NY * G * 4, 1: 2 * 2 * NY * G * 8, 2: 2 * 2 * 2 * NY * G * 4,
+                    3: 2 * 2 * NY * G * 8}[packed]
             assert ring <= 227 * 1024, (G, v, ring)
-        assert p.variant_shape(G, 0)[0] in (0, 2)   # the default is a scalar (plain or rotating) tile
+        assert p.variant_shape(G, 0)[0] in (0, 2, 3)   # the default: a plain or rotating tile
     sh = (ctypes.c_int32 * 3)()
     assert p.lib().rd_variant_shape(48, 0, sh) == 1
     assert p.lib().rd_variant_shape(64, p.lib().rd_n_variants(), sh) == 1
