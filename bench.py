@@ -49,6 +49,10 @@ import workloads as W  # noqa: E402
 # fma g, fma, fma, fma -4, ...); DIFF 2 + 2.
 FP32_INST_PER_CELL = {W.FHN: 15, W.GM: 20, W.DIFF: 10, W.BZ: 22}
 
+# resident stepper kernel of each tile kind (rd_variant_shape)
+RESIDENT_KERNEL = {0: "rd_resident_scalar_kernel", 1: "rd_resident_kernel", 2: "rd_resident_rot_kernel",
+                   3: "rd_resident_rot2_kernel"}
+
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload
 # and a hash of the stepper sources: reported, labelled as that capture's,
@@ -58,7 +62,7 @@ FP32_INST_PER_CELL = {W.FHN: 15, W.GM: 20, W.DIFF: 10, W.BZ: 22}
 # the full launch's traffic.
 STEPPER_TRAFFIC = {
     "c2": {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488, "7c8c62601c860730": 4223488},
-    "c4": {"250da058b95b29c7": 1285591296, "02a4865c70d95aa1": 1284856064},
+    "c4": {"250da058b95b29c7": 1285591296, "02a4865c70d95aa1": 1284856064, "60c7c52369dee980": 1290298112},
 }
 STEPPER_SOURCES = ["paper_2203_14742_b300/csrc/stepper.cu", "paper_2203_14742_b300/csrc/tile.cuh",
                    "paper_2203_14742_b300/csrc/common.cuh"]
@@ -420,7 +424,7 @@ def run_ours(args, rank, world, local_rank):
         kname = "rd_batch_kernel (persistent)"
     else:
         pk_, ty_, tx_ = p.variant_shape(groups[0].G, variant)
-        kname = "%s<%s,%d,%dx%d> variant %s" % ("rd_resident_kernel" if pk_ else "rd_resident_scalar_kernel",
+        kname = "%s<%s,%d,%dx%d> variant %s" % (RESIDENT_KERNEL[pk_],
                                                {0: "FHN", 1: "GM", 2: "DIFF", 3: "BZ"}[groups[0].model],
                                                groups[0].G, ty_, tx_, variant)
     if multi or variant == 0:
@@ -589,7 +593,7 @@ def c2_bench(p, torch, dev, stream, pk, src, reps=5):
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tinst/s", "frac": ach / peak,
                          "traffic": traffic, "traffic_source": tsrc,
                          "kernel": "%s<FHN,64,%dx%d> variant %d" % (
-                             "rd_resident_kernel" if pk_ else "rd_resident_scalar_kernel", ty_, tx_, variant)},
+                             RESIDENT_KERNEL[pk_], ty_, tx_, variant)},
             "cil_pairs_rechecked_exactly": int(sum(int(o["n_rechecked"]) for o in pipe.cil_out))}
 
 
