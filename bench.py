@@ -62,8 +62,9 @@ RESIDENT_KERNEL = {0: "rd_resident_scalar_kernel", 1: "rd_resident_kernel", 2: "
 # the full launch's traffic.
 STEPPER_TRAFFIC = {
     "c2": {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488, "7c8c62601c860730": 4223488,
-           "60c7c52369dee980": 4297216},
-    "c4": {"250da058b95b29c7": 1285591296, "02a4865c70d95aa1": 1284856064, "60c7c52369dee980": 1290298112},
+           "60c7c52369dee980": 4297216, "bf9071c73da591c1": 4297216},
+    "c4": {"250da058b95b29c7": 1285591296, "02a4865c70d95aa1": 1284856064, "60c7c52369dee980": 1290298112,
+           "bf9071c73da591c1": 1290150912},
 }
 STEPPER_SOURCES = ["paper_2203_14742_b300/csrc/stepper.cu", "paper_2203_14742_b300/csrc/tile.cuh",
                    "paper_2203_14742_b300/csrc/common.cuh"]
@@ -415,6 +416,23 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ref_rate = 2 * gsl["G"] ** 2 * nsl / (r0.elapsed_time(r1) * 1e-3)
 
+    # ---- plain batched FP32 path (every realisation of a group per launch,
+    # one step per launch, state through HBM) on every group, 50 steps -----
+    plain_rate = None
+    if not args.no_reference_path and rank == 0:
+        spl = p.Simulation(groups, device=dev)
+        tmp = torch.empty(max(2 * g.G * g.G * g.n_real for g in groups), dtype=torch.float32, device=dev)
+        npl = 50
+        spl.integrate_plain(steps=5, tmp=tmp)
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        spl.integrate_plain(steps=npl, tmp=tmp)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        plain_rate = sum(g.n_real * g.G * g.G for g in groups) * npl / (r0.elapsed_time(r1) * 1e-3)
+        del spl, tmp
+
     # ---- roofline of the dominant kernel (the stepper) ----------------------
     pk, src = peaks()
     k_avg_ms = sum(k_ms) / len(k_ms)
@@ -465,6 +483,11 @@ def run_ours(args, rank, world, local_rank):
                              "(%s peaks file)" % src},
         "plain_fp32_path_cell_updates_per_s": ref_rate,
         "batched_vs_plain": (cell_updates / (k_avg_ms * 1e-3)) / ref_rate if ref_rate else None,
+        "plain_batched_fp32_path_cell_updates_per_s": plain_rate,
+        "batched_vs_plain_batched": (cell_updates / (k_avg_ms * 1e-3)) / plain_rate if plain_rate else None,
+        "plain_note": "plain = one Euler step per launch, state through HBM, the same FP32 update; "
+                      "single-realisation: one realisation per launch (2 realisations of the first group, "
+                      "500 steps); batched: every realisation of a group per launch (every group, 50 steps)",
     }
     cs = clk.summary()
     if cs:

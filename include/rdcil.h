@@ -209,9 +209,17 @@ int32_t rd_get_stream_depth(const rd_handle *h);
  * against: one realisation per launch, one Euler step per launch, state
  * round-tripping through global memory.  Same arithmetic contract as
  * rd_integrate_batch for FP32 (results agree to FP32 rounding, not bit for
- * bit).  d_tmp: caller scratch of 2*G*G floats of the largest group. */
+ * bit: GM and BZ nodes go through their deviation form per step).  d_tmp:
+ * caller scratch of 2*G*G floats of the largest group.
+ * rd_integrate_plain — the same plain step with every realisation of a
+ * group in one launch (one Euler step per launch, state through global
+ * memory): the fields equal rd_integrate_reference's bit for bit.  d_tmp:
+ * caller scratch of 2*G*G*n_real floats of the largest group.  Groups of
+ * more than 65535 realisations: RD_ERR_UNSUPPORTED. */
 rd_status rd_integrate_reference(rd_handle *h, float *d_fields, float *d_tmp,
                                  int64_t steps_override, void *stream);
+rd_status rd_integrate_plain(rd_handle *h, float *d_fields, float *d_tmp,
+                             int64_t steps_override, void *stream);
 
 /* rd_integrate_f64 — the same Euler recursion on a float64 copy of the
  * fields (layout as d_fields, offsets in doubles), in the operation order

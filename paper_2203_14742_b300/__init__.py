@@ -67,6 +67,7 @@ _SIGS = {
     "rd_handle_table_bytes": (_sz, [_vp]),
     "rd_integrate_batch": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "rd_integrate_reference": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+    "rd_integrate_plain": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "rd_integrate_f64": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "rd_integrate_rkc": (_i32, [_vp, _vp, C.POINTER(RdRkcOpts), _vp, _vp, _vp]),
     "rd_integrate_imex": (_i32, [_vp, _vp, _vp, _vp]),
@@ -272,6 +273,14 @@ class Simulation:
             tmp = torch.empty(max(2 * g.G * g.G for g in self.groups), dtype=torch.float32,
                               device=self.device)
         _check("rd_integrate_reference", lib().rd_integrate_reference(
+            self.handle, _ptr(self.fields), _ptr(tmp), int(steps), _stream()))
+
+    def integrate_plain(self, steps=-1, tmp=None):
+        """The plain step with every realisation of a group in one launch."""
+        if tmp is None:
+            tmp = torch.empty(max(2 * g.G * g.G * g.n_real for g in self.groups), dtype=torch.float32,
+                              device=self.device)
+        _check("rd_integrate_plain", lib().rd_integrate_plain(
             self.handle, _ptr(self.fields), _ptr(tmp), int(steps), _stream()))
 
     def integrate_f64(self, fields64, steps=-1):

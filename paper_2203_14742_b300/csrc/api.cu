@@ -277,6 +277,20 @@ extern "C" rd_status rd_integrate_reference(rd_handle *hh, float *d_fields, floa
     return RD_OK;
 }
 
+extern "C" rd_status rd_integrate_plain(rd_handle *hh, float *d_fields, float *d_tmp, int64_t steps_override,
+                                        void *stream) {
+    if (!hh || !d_fields || !d_tmp) return RD_ERR_INVALID_ARG;
+    Handle &h = hh->h;
+    if (has_rdode(h)) return RD_ERR_UNSUPPORTED;
+    for (int32_t i = 0; i < h.n_groups; ++i) {
+        const GroupDev &g = h.h_groups[i];
+        int64_t steps = steps_override >= 0 ? steps_override : g.n_steps;
+        rd_status st = launch_integrate_plain(g, d_fields, d_tmp, steps, (cudaStream_t)stream);
+        if (st) return st;
+    }
+    return RD_OK;
+}
+
 extern "C" rd_status rd_integrate_f64(rd_handle *hh, double *d_fields64, double *d_tmp64, int64_t steps_override,
                                       void *stream) {
     if (!hh || !d_fields64 || !d_tmp64) return RD_ERR_INVALID_ARG;

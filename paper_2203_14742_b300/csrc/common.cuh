@@ -108,6 +108,7 @@ rd_status launch_integrate_group(const GroupDev &g, float *fields, int64_t steps
                                  double *residual, uint32_t *status, cudaStream_t s);
 rd_status launch_integrate_reference(const GroupDev &g, float *fields, float *tmp,
                                      int64_t steps, cudaStream_t s);
+rd_status launch_integrate_plain(const GroupDev &g, float *fields, float *tmp, int64_t steps, cudaStream_t s);
 rd_status launch_integrate_f64(const GroupDev &g, double *fields, double *tmp, int64_t steps,
                                cudaStream_t s);
 rd_status launch_record_group(const GroupDev &g, float *fields, float *traj, int64_t steps,

@@ -720,47 +720,74 @@ rd_status launch_batch(void *pp, float *fields, int64_t steps_override, double *
 }
 
 // ---------------------------------------------------------------------------
-// Plain reference path: one cell per thread, one step of one realisation per
-// launch, reading src and writing dst in global memory.
+// Plain paths: one cell per thread, one Euler step per launch, reading src
+// and writing dst in global memory (blockIdx.z = realisation; the
+// single-realisation path launches one realisation at a time).  GM and BZ
+// nodes are converted to the deviation form that euler_cell takes (the
+// Laplacian of a deviation is that of the field) and back.
 // ---------------------------------------------------------------------------
 template <int MODEL>
 __global__ void rd_reference_step_kernel(const float *__restrict__ src, float *__restrict__ dst, int G,
-                                         CoefF cf) {
+                                         int64_t stride, CoefF cf) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= G || y >= G) return;
+    src += (int64_t)blockIdx.z * stride;
+    dst += (int64_t)blockIdx.z * stride;
     const float *u = src, *v = src + G * G;
     int k = y * G + x;
     int kn = (y > 0 ? y - 1 : y) * G + x, ks = (y < G - 1 ? y + 1 : y) * G + x;
     int kw = y * G + (x > 0 ? x - 1 : x), ke = y * G + (x < G - 1 ? x + 1 : x);
-    float nu = (u[kn] + u[ks]) + (u[kw] + u[ke]);
-    float nv = (v[kn] + v[ks]) + (v[kw] + v[ke]);
+    float uc = u[k], vc = v[k], un_ = u[kn], us = u[ks], uw = u[kw], ue = u[ke];
+    float vn_ = v[kn], vs = v[ks], vw = v[kw], ve = v[ke];
+    to_state<MODEL>(uc, vc, cf);
+    to_state<MODEL>(un_, vn_, cf);
+    to_state<MODEL>(us, vs, cf);
+    to_state<MODEL>(uw, vw, cf);
+    to_state<MODEL>(ue, ve, cf);
+    float nu = (un_ + us) + (uw + ue);
+    float nv = (vn_ + vs) + (vw + ve);
     float un, vn;
-    euler_cell<MODEL>(u[k], v[k], nu, nv, cf, un, vn);
+    euler_cell<MODEL>(uc, vc, nu, nv, cf, un, vn);
+    from_state<MODEL>(un, vn, cf);
     dst[k] = un;
     dst[G * G + k] = vn;
 }
 
-rd_status launch_integrate_reference(const GroupDev &g, float *fields, float *tmp, int64_t steps,
-                                     cudaStream_t s) {
+// n_at_once realisations per launch (1: the single-realisation path; n_real:
+// the whole group); tmp holds 2 G^2 n_at_once floats
+static rd_status plain_steps(const GroupDev &g, float *fields, float *tmp, int64_t steps, int n_at_once,
+                             cudaStream_t s) {
     CoefF cf = make_coef(g);
-    dim3 blk(32, 8), grd((g.G + 31) / 32, (g.G + 7) / 8);
-    int64_t m = 2 * (int64_t)g.G * g.G;
-    for (int r = 0; r < g.n_real; ++r) {
-        float *a = fields + g.field_offset + r * m;
+    const int64_t m = 2 * (int64_t)g.G * g.G;
+    for (int r0 = 0; r0 < g.n_real; r0 += n_at_once) {
+        const int nr = min(n_at_once, g.n_real - r0);
+        dim3 blk(32, 8), grd((g.G + 31) / 32, (g.G + 7) / 8, nr);
+        float *a = fields + g.field_offset + r0 * m;
         for (int64_t n = 0; n < steps; ++n) {
             const float *src = (n & 1) ? tmp : a;
             float *dst = (n & 1) ? a : tmp;
             switch (g.model) {
-                case RD_FHN: rd_reference_step_kernel<RD_FHN><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
-                case RD_GM: rd_reference_step_kernel<RD_GM><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
-                case RD_BZ: rd_reference_step_kernel<RD_BZ><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
-                default: rd_reference_step_kernel<RD_DIFF><<<grd, blk, 0, s>>>(src, dst, g.G, cf); note_launch(); break;
+                case RD_FHN: rd_reference_step_kernel<RD_FHN><<<grd, blk, 0, s>>>(src, dst, g.G, m, cf); break;
+                case RD_GM: rd_reference_step_kernel<RD_GM><<<grd, blk, 0, s>>>(src, dst, g.G, m, cf); break;
+                case RD_BZ: rd_reference_step_kernel<RD_BZ><<<grd, blk, 0, s>>>(src, dst, g.G, m, cf); break;
+                default: rd_reference_step_kernel<RD_DIFF><<<grd, blk, 0, s>>>(src, dst, g.G, m, cf); break;
             }
+            note_launch();
         }
-        if (steps & 1) RD_CUDA_TRY(cudaMemcpyAsync(a, tmp, m * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        if (steps & 1) RD_CUDA_TRY(cudaMemcpyAsync(a, tmp, nr * m * sizeof(float), cudaMemcpyDeviceToDevice, s));
     }
     return cuda_status(cudaGetLastError());
+}
+
+rd_status launch_integrate_reference(const GroupDev &g, float *fields, float *tmp, int64_t steps,
+                                     cudaStream_t s) {
+    return plain_steps(g, fields, tmp, steps, 1, s);
+}
+
+rd_status launch_integrate_plain(const GroupDev &g, float *fields, float *tmp, int64_t steps, cudaStream_t s) {
+    if (g.n_real > 65535) return RD_ERR_UNSUPPORTED;
+    return plain_steps(g, fields, tmp, steps, g.n_real, s);
 }
 
 // ---------------------------------------------------------------------------

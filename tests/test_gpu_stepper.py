@@ -118,18 +118,29 @@ def test_residual_of_initial_state(p, case):
     assert np.allclose(res, ref, rtol=1e-12, atol=0)
 
 
-def test_reference_path_agrees(p):
-    par = (2.8e-4, 0.05, 10.0, 0.95)
-    g = mkgroup(p, W.FHN, 64, 2, par, 2 ** -10, 300, (-0.05, 0.05), 3)
+@pytest.mark.parametrize("model,G,par,dt,noise", [
+    (W.FHN, 64, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -10, (-0.05, 0.05)),
+    (W.GM, 64, (2.5e-4, 0.01, 1.0, 0.52), 2 ** -8, (0.0, 0.01)),
+    (W.BZ, 32, (1.6e-3, 1.32e-2, 4.4, 7.1), 2 ** -8, (0.0, 0.01)),
+    (W.GM, 128, (2.5e-4, 0.01, 1.0, 0.48), 2 ** -10, (0.0, 0.01)),
+])
+def test_reference_path_agrees(p, model, G, par, dt, noise):
+    """The plain paths (one realisation per launch, and the whole group per
+    launch) agree with the oracle like the resident stepper, and with each
+    other bit for bit (same per-node arithmetic)."""
+    g = mkgroup(p, model, G, 3, par, dt, 301, noise, 3)
     a = p.Simulation([g])
     b = p.Simulation([g])
+    c = p.Simulation([g])
     a.integrate()
     b.integrate_reference()
+    c.integrate_plain()
     torch.cuda.synchronize()
-    ref = oracle.step(W.FHN, par, 2 ** -10, 300,
-                      oracle.init_fields(W.FHN, 64, 2, par, -0.05, 0.05, 3).astype(np.float64))
+    ref = oracle.step(model, par, dt, 301, oracle.init_fields(model, G, 3, par, noise[0], noise[1], 3)
+                      .astype(np.float64))
     assert rel_err(a.group_fields(0).cpu().numpy(), ref) <= FIELD_TOL
     assert rel_err(b.group_fields(0).cpu().numpy(), ref) <= FIELD_TOL
+    assert torch.equal(b.fields, c.fields)
 
 
 def test_split_integration_is_bit_identical(p):
