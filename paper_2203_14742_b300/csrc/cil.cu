@@ -423,7 +423,24 @@ __global__ void d2_bound_kernel(CilWork w, float gam, int cross) {
         lbm = fminf(lbm, __shfl_xor_sync(0xffffffffu, lbm, o));
         ubm = fminf(ubm, __shfl_xor_sync(0xffffffffu, ubm, o));
     }
+    // then across the block's warps, so that one thread per block meets the
+    // four global slots (same-address atomics from every warp serialised)
+    __shared__ float red[4][8];
+    const int warp = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
+        red[0][warp] = lb;
+        red[1][warp] = ub;
+        red[2][warp] = lbm;
+        red[3][warp] = ubm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            lb = fmaxf(lb, red[0][k]);
+            ub = fmaxf(ub, red[1][k]);
+            lbm = fminf(lbm, red[2][k]);
+            ubm = fminf(ubm, red[3][k]);
+        }
         // non-negative floats order like their bit patterns
         atomicMax(&w.scal[SC_LB1], (unsigned long long)__float_as_uint(lb));
         atomicMax(&w.scal[SC_UB1], (unsigned long long)__float_as_uint(ub));
