@@ -97,6 +97,31 @@ def test_adjoint_small_matches_oracle(p, model, par, dt, noise):
     compare(sim, f0, w0, s1, s2, radii, cot, model, par, dt, steps, 3)
 
 
+@pytest.mark.parametrize("model,par,dt,noise,steps", [
+    (W.FHN, (2.8e-4, 0.05, 10.0, 0.95), 2 ** -8, (-0.05, 0.05), 60),
+    (W.GM, (2.5e-4, 0.01, 1.0, 0.5), 2 ** -8, (0.0, 0.5), 60),
+    (W.BZ, W.BZ_THETA0, 2 ** -8, (0.0, 1.0), 60),
+])
+def test_adjoint_every_component_pinned(p, model, par, dt, noise, steps):
+    """Cases in which the derived per-component bound pins every parameter's
+    derivative (Du, Dv and the two reaction parameters) to within 10 % of
+    its value, not only the largest one.  The bound scales with the FP32
+    field error relative to the pattern's range; GM and BZ patterns that are
+    0.01-deviations from an equilibrium of order 2-5 carry the equilibrium's
+    rounding (e_f ~ 2e-5, and the reaction components sum terms far larger
+    than their values), so here the initial perturbations are of order one
+    and the horizon short."""
+    sim, f0, w0, s1, s2, radii, cot = problem(p, model, 32, 8, par, dt, steps, noise, 57, 3)
+    Cg, gg = sim.adjoint(0, f0, 3, s1, s2, torch.from_numpy(radii), 0.05, torch.from_numpy(cot))
+    Co, go, A = oracle.smooth_cil_grad(model, par, dt, steps, w0, 3, s1, s2, radii, 0.05, cot, with_abs=True)
+    gg = gg.cpu().numpy()
+    e_f = field_error(sim, f0, w0, model, par, dt, steps)
+    tol = 1e-9 * np.abs(go) + K_GRAD * max(e_f, 2.0 ** -24) * A
+    print("pinned", model, "gpu", gg, "oracle", go, "tol/|g|", tol / np.abs(go), "e_f", e_f)
+    assert np.all(np.abs(gg - go) <= tol), (gg, go, tol)
+    assert np.all(tol <= 0.1 * np.abs(go)), tol / np.abs(go)
+
+
 def test_adjoint_u_only_mask_and_ragged_segments(p):
     # 97 steps: segments of 10 with a short last one
     par = (3e-4, 0.05, 10.0, 0.93)
