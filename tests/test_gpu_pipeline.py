@@ -202,3 +202,52 @@ def test_concurrent_correlation_integrals_match_sequential(p):
                 assert torch.equal(outs[-1][k], again[k]), k
     for k in outs[0]:
         assert torch.equal(outs[0][k], outs[1][k]), k
+
+
+def rel_field_err(a, b):
+    a = np.asarray(a, np.float64).reshape(2, -1)
+    b = np.asarray(b, np.float64).reshape(2, -1)
+    return float((np.abs(a - b).max(-1) / np.abs(b).max(-1)).max())
+
+
+def test_c4_full_size_in_the_benchmark_launch(p):
+    """The benchmark's step, c4 in full: 64 parameter vectors x 128
+    realisations, FHN and GM at 64^2 (10^4 steps) and 128^2 (2 x 10^4) in
+    one persistent launch, the 64 correlation integrals forked over side
+    streams and the batched bootstrap statistics, as bench.py times it.
+    Sampled against the oracle for the first group of every model and grid:
+    the last realisation's fields at the full horizon (field tolerance
+    1e-5), the correlation integral's radii, bins and counts on the GPU's
+    fields, and the bootstrap counts, mean, covariance and factor (bit for
+    bit)."""
+    cfg = W.config("c4")
+    gds = cfg["groups"]
+    n1, n2, M, b, T = cfg["n1"], cfg["n2"], cfg["M"], cfg["b"], cfg["T_res"]
+    groups = [p.Group.from_dict(g) for g in gds]
+    pipe = p.Pipeline(groups, [(n1, n2, g["species_mask"]) for g in gds], M, b, T, cfg["seed"])
+    assert len(pipe.side) > 1
+    picks = {}
+    for i, g in enumerate(gds):
+        picks.setdefault((g["model"], g["G"]), i)
+    assert len(picks) == 4
+    f0 = {i: pipe.sim.group_fields(i)[-1:].cpu().numpy().astype(np.float64) for i in picks.values()}
+    pipe.run(reinit=False)
+    torch.cuda.synchronize()
+    assert pipe.sim.sync_status() == 0
+    for i in picks.values():
+        g = gds[i]
+        ref = oracle.step(g["model"], g["params"], g["dt"], g["n_steps"], f0[i])
+        assert rel_field_err(pipe.sim.group_fields(i)[-1:].cpu().numpy(), ref) <= 1e-5, i
+        X = oracle.patterns(pipe.sim.group_fields(i).cpu().numpy(), g["species_mask"])
+        o = oracle.cil(X[:n1], X[n1:n1 + n2], b=b, M=M)
+        assert float(pipe.cil_out[i]["radii"][0]) == o["R0"]
+        assert np.array_equal(pipe.cil_out[i]["radii"][1:].cpu().numpy(), o["radii"])
+        assert np.array_equal(pipe.bins[i].cpu().numpy(), o["bins"])
+        assert np.array_equal(pipe.cil_out[i]["counts"].cpu().numpy(), o["counts"])
+        so = oracle.synlik(o["bins"], M, T, cfg["seed"] + i, y_obs=o["counts"] / float(n1 * n2))
+        assert np.array_equal(pipe.stats["Y"][i].cpu().numpy(), so["Y"])
+        assert np.array_equal(pipe.stats["mu"][i].cpu().numpy(), so["mu"])
+        assert np.array_equal(pipe.stats["cov"][i].cpu().numpy(), so["cov"])
+        assert int(pipe.stats["status"][i]) == so["status"]
+        if so["status"] == 0:
+            assert np.array_equal(pipe.stats["chol"][i].cpu().numpy(), so["chol"])
