@@ -654,6 +654,28 @@ def gram_large(p, torch, dev, stream, pk, src):
 
     products = p.gram_products(n, n, d)
     fl, t_gram, t_cil, rech = measure()
+
+    # the HBM-bound shapes (arithmetic intensity n1 n2 / (n1 + n2) below the
+    # ridge): c2's 2 x 64 x 4096 and c3's 2 x 256 x 32768, against the HBM
+    # roofline on the algorithmic bytes 2 (n1 + n2) d (bf16 patterns once;
+    # the kernel reads hi and lo, twice that)
+    hbm = []
+    for (ns_, G_, nsp_) in ((64, 64, 1), (256, 128, 2)):
+        Xs = torch.from_numpy(W.cosine_patterns(2 * ns_, G_, nsp_, 81, amp=0.8, offset=2.0)).to(dev)
+        ds = Xs.shape[1]
+        p.cil(Xs[:ns_], Xs[ns_:], b=1.3, M=16)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(20):
+            p.gram_only(ns_, ns_, ds, dev)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        th = h0.elapsed_time(h1) / 20 * 1e-3
+        alg_b = 2.0 * 2 * ns_ * ds
+        hbm.append({"shape": "2 x %d x %d" % (ns_, ds), "gram_us": th * 1e6,
+                    "algorithmic_gbs": alg_b / th / 1e9, "hbm_frac": alg_b / th / 1e9 / pk["hbm_gbs"],
+                    "executed_gbs": 2 * alg_b / th / 1e9})
     try:
         p.set_gram_products(1)
         fl1, t_gram1, t_cil1, rech1 = measure()
@@ -670,6 +692,7 @@ def gram_large(p, torch, dev, stream, pk, src):
                          "runs (products x 2 n1 n2 d_padded flops), algorithmic = 2 n1 n2 d" % src,
             "cil_ms": t_cil * 1e3, "pair_dists_per_s": n * n / t_cil,
             "tier2_pairs": rech[0], "exact_pairs": rech[1],
+            "hbm_bound_shapes": hbm,
             "one_product": {"gram_ms": t_gram1 * 1e3,
                             "frac_of_peak": fl1 / t_gram1 / 1e12 / pk["bf16_tflops"],
                             "frac_of_peak_algorithmic": 2.0 * n * n * d / t_gram1 / 1e12 / pk["bf16_tflops"],
@@ -1331,6 +1354,21 @@ def main():
             v1, secs1, note1 = oracle_sample(cfg, frac / 16)
             oracle.set_threads(cores)
             out["cpu_baseline"]["one_thread"] = {"value": v1, "sample": note1 + " (%.1f s)" % secs1}
+        else:   # one thread, stepping only, every eighth group on a sixteenth of the step slice
+            oracle.set_threads(1)
+            cells = 0
+            t0 = time.perf_counter()
+            for g in cfg["groups"][::8]:
+                ns = max(1, int(round(g["n_steps"] * frac / 16)))
+                f0 = oracle.init_fields(g["model"], g["G"], g["n_real"], g["params"], g["noise"][0], g["noise"][1],
+                                        g["seed"])
+                oracle.step(g["model"], g["params"], g["dt"], ns, f0.astype(np.float64))
+                cells += g["n_real"] * g["G"] * g["G"] * ns
+            secs1 = time.perf_counter() - t0
+            oracle.set_threads(cores)
+            out["cpu_baseline"]["one_thread"] = {
+                "value": cells / secs1, "unit": "cell-updates/s (stepping only)",
+                "sample": "every eighth group, all realisations x 1/16 of the step slice (%.1f s)" % secs1}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
