@@ -7,17 +7,25 @@
 // keeps one whole simulation per thread block, on-chip, for the whole run).
 //
 // Kernels
-//   init_fields_kernel       counter-based noise, FP64 then one rounding to FP32
-//   rd_resident_kernel<...>  one realisation per CTA, the whole field held in
-//                            registers as TYxTX tiles per thread for the whole
-//                            run; north/south tile edges exchanged through a
-//                            double-buffered shared-memory ring (one barrier
-//                            per step), east/west edges through warp shuffles
-//                            (serpentine column order, see tile.cuh);
-//                            FP64 residual reduced with warp shuffles at exit
-//   rd_reference_step_kernel one cell per thread, one step and one realisation
-//                            per launch (the plain path for comparison)
-//   rd_f64_step_kernel       FP64 in the paper's operation order, no FMA
+//   init_fields_kernel        counter-based noise, FP64 then one rounding to FP32
+//   rd_resident_*_kernel      one realisation per CTA, the whole field held in
+//                             registers as TYxTX tiles per thread for the whole
+//                             run; north/south tile edges exchanged through a
+//                             double-buffered shared-memory ring (one barrier
+//                             per step), east/west edges through warp shuffles
+//                             (serpentine column order, see tile.cuh); FP64
+//                             residual reduced with warp shuffles at exit.
+//                             Tile kinds: _scalar (u, v tiles), plain
+//                             (packed (u, v) float2 tiles; also the adjoint's
+//                             recording pass), _rot (rows in TY + 1 rotating
+//                             slots), _rot2 (packed and rotating)
+//   rd_batch_kernel           persistent: every group of a handle in one
+//                             launch, work units longest first from a device
+//                             queue (one 128^2 or two smaller realisations per
+//                             512-thread CTA)
+//   rd_reference_step_kernel  one cell per thread, one Euler step per launch
+//                             (the plain paths for comparison)
+//   rd_f64_step_kernel        FP64 in the paper's operation order, no FMA
 #include <algorithm>
 #include <cstdio>
 #include <vector>
