@@ -55,7 +55,8 @@ RESIDENT_KERNEL = {0: "rd_resident_scalar_kernel", 1: "rd_resident_kernel", 2: "
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload
-# and a hash of the stepper sources: reported, labelled as that capture's,
+# (with ":v<n>" for a resident tile variant other than 0) and a hash of the
+# stepper sources: reported, labelled as that capture's,
 # only while the kernel is the one that was measured.  The resident and
 # persistent steppers read the initial fields and write the final ones once
 # per launch whatever the step count, so a capture of a shortened run gives
@@ -63,6 +64,7 @@ RESIDENT_KERNEL = {0: "rd_resident_scalar_kernel", 1: "rd_resident_kernel", 2: "
 STEPPER_TRAFFIC = {
     "c2": {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488, "7c8c62601c860730": 4223488,
            "60c7c52369dee980": 4297216, "bf9071c73da591c1": 4297216, "730afce9ca60e453": 4314112},
+    "c2:v3": {"730afce9ca60e453": 4223488},
     "c4": {"250da058b95b29c7": 1285591296, "02a4865c70d95aa1": 1284856064, "60c7c52369dee980": 1290298112,
            "bf9071c73da591c1": 1290150912, "730afce9ca60e453": 1291938816},
 }
@@ -449,7 +451,7 @@ def run_ours(args, rank, world, local_rank):
     if multi or variant == 0:
         traffic, tsrc = stepper_traffic(args.config)
     else:
-        traffic, tsrc = None, "no ncu capture of this tile variant"
+        traffic, tsrc = stepper_traffic("%s:v%d" % (args.config, variant))
     out = {
         "metric": "RD cell-updates/s + CIL pair-dists/s at stated tol; % HBM/tensor roofline",
         "value": value,
@@ -588,7 +590,7 @@ def c2_bench(p, torch, dev, stream, pk, src, reps=5):
     peak = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     ach = inst / (k_ms * 1e-3) / 1e12
     pk_, ty_, tx_ = p.variant_shape(g.G, variant)
-    traffic, tsrc = stepper_traffic("c2") if variant == 0 else (None, "no ncu capture of this tile variant")
+    traffic, tsrc = stepper_traffic("c2" if variant == 0 else "c2:v%d" % variant)
     # accuracy against the oracle: the fields of two realisations after the
     # full step count (FP64 oracle from the same FP32 initial state; per
     # realisation and species max |a - b| / max |b|), and the correlation
