@@ -226,9 +226,18 @@ rd_adjoint_reverse_kernel(const float *__restrict__ traj, int64_t traj_stride, i
     float lu[TY][TX], lv[TY][TX];
     tile_load<G, TY, TX>(lbase, tx, ty, lu, lv);
     double g[4] = {0.0, 0.0, 0.0, 0.0};
+    // the state of step n is loaded one step ahead (un, vn), so its global
+    // loads overlap the previous step's arithmetic
+    const float *tr = traj + (int64_t)r * traj_stride;
+    float un[TY][TX], vn[TY][TX];
+    if (len > 0) tile_load<G, TY, TX>(tr + (len - 1) * 2 * G * G, tx, ty, un, vn);
     for (int64_t n = len - 1; n >= 0; --n) {
         float u[TY][TX], v[TY][TX];
-        tile_load<G, TY, TX>(traj + (int64_t)r * traj_stride + n * 2 * G * G, tx, ty, u, v);
+#pragma unroll
+        for (int i = 0; i < TY; ++i)
+#pragma unroll
+            for (int c = 0; c < TX; ++c) { u[i][c] = un[i][c]; v[i][c] = vn[i][c]; }
+        if (n > 0) tile_load<G, TY, TX>(tr + (n - 1) * 2 * G * G, tx, ty, un, vn);
         float *hb = sm + (int)(n & 1) * (T::HALO_FLOATS / 2);
         halo_put<G, TY, TX>(hb, tx, ty, lu, lv);
         __syncthreads();
