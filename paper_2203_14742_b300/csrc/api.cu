@@ -100,10 +100,8 @@ extern "C" rd_status rd_init(const rd_group *groups, int32_t n_groups, float *d_
     if (st) { rd_free(hh); return st; }
     st = tables_create(h, s);
     if (st) { rd_free(hh); return st; }
-    for (int32_t i = 0; i < n_groups; ++i) {
-        st = launch_init_fields(h.h_groups[i], d_fields, s);
-        if (st) { rd_free(hh); return st; }
-    }
+    st = launch_init_all(h.h_groups, n_groups, d_fields, s);
+    if (st) { rd_free(hh); return st; }
     // the group table is read by the host copy only after this point; make
     // sure the pageable source of the async copy is no longer needed
     if (cudaStreamSynchronize(s) != cudaSuccess) { rd_free(hh); return RD_ERR_CUDA; }
@@ -216,11 +214,7 @@ extern "C" rd_status rd_set_seed(rd_handle *hh, int32_t group, uint64_t seed) {
 
 extern "C" rd_status rd_reinit(rd_handle *hh, float *d_fields, void *stream) {
     if (!hh || !d_fields || ((uintptr_t)d_fields & 15)) return RD_ERR_INVALID_ARG;
-    for (int32_t i = 0; i < hh->h.n_groups; ++i) {
-        rd_status st = launch_init_fields(hh->h.h_groups[i], d_fields, (cudaStream_t)stream);
-        if (st) return st;
-    }
-    return RD_OK;
+    return launch_init_all(hh->h.h_groups, hh->h.n_groups, d_fields, (cudaStream_t)stream);
 }
 
 extern "C" rd_status rd_set_stream_depth(rd_handle *hh, int32_t depth) {

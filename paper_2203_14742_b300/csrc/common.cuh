@@ -104,6 +104,7 @@ rd_status smem_attr(K kern, int bytes) {
 
 // ---- launchers implemented in the kernel translation units --------------
 rd_status launch_init_fields(const GroupDev &g, float *fields, cudaStream_t s);
+rd_status launch_init_all(const GroupDev *groups, int n_groups, float *fields, cudaStream_t s);
 rd_status launch_integrate_group(const GroupDev &g, float *fields, int64_t steps,
                                  double *residual, uint32_t *status, cudaStream_t s);
 rd_status launch_integrate_reference(const GroupDev &g, float *fields, float *tmp,

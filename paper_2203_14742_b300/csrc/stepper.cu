@@ -36,21 +36,49 @@ namespace rdcil {
 // ---------------------------------------------------------------------------
 // initial state
 // ---------------------------------------------------------------------------
+// Element i of a group's initial state (i = (r*2 + s)*cells + c is exactly
+// the generator counter): equilibrium + lo + (hi - lo) U, U = the top 53
+// bits of SplitMix64 output i times 2^-53, in FP64, rounded once.
+__device__ __forceinline__ float init_value(int64_t i, int64_t cells, uint64_t seed, double x0u, double x0v,
+                                            double lo, double hi) {
+    int64_t rs = i / cells;
+    int s = (int)(rs & 1);
+    uint64_t z = splitmix64_at(seed, (uint64_t)i);
+    double U = __dmul_rn(__ull2double_rn(z >> 11), 1.1102230246251565404e-16);  // 2^-53
+    double span = __dsub_rn(hi, lo);
+    double t = __dmul_rn(span, U);
+    double t2 = __dadd_rn(lo, t);
+    double v = __dadd_rn(s ? x0v : x0u, t2);
+    return __double2float_rn(v);
+}
+
 __global__ void init_fields_kernel(float *__restrict__ out, int64_t n_total, int64_t cells,
                                    uint64_t seed, double x0u, double x0v, double lo, double hi) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_total; i += stride) {
-        // i = (r*2 + s)*cells + c is exactly the generator counter
-        int64_t rs = i / cells;
-        int s = (int)(rs & 1);
-        uint64_t z = splitmix64_at(seed, (uint64_t)i);
-        double U = __dmul_rn(__ull2double_rn(z >> 11), 1.1102230246251565404e-16);  // 2^-53
-        double span = __dsub_rn(hi, lo);
-        double t = __dmul_rn(span, U);
-        double t2 = __dadd_rn(lo, t);
-        double v = __dadd_rn(s ? x0v : x0u, t2);
-        out[i] = __double2float_rn(v);
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_total; i += stride)
+        out[i] = init_value(i, cells, seed, x0u, x0v, lo, hi);
+}
+
+// Several groups' initial states in one launch (blockIdx.y = item), each
+// item's values taken on the host at launch time exactly as for the
+// single-group launch, passed by value.
+struct InitItem {
+    int64_t offset, n, cells;
+    uint64_t seed;
+    double u0, v0, lo, hi;
+};
+constexpr int INIT_MAX = 120;
+struct InitBatch {
+    InitItem item[INIT_MAX];
+};
+static_assert(sizeof(InitBatch) <= 8192, "kernel parameter table");
+
+__global__ void init_batch_kernel(float *__restrict__ fields, const __grid_constant__ InitBatch b) {
+    const InitItem &it = b.item[blockIdx.y];
+    float *out = fields + it.offset;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < it.n; i += stride)
+        out[i] = init_value(i, it.cells, it.seed, it.u0, it.v0, it.lo, it.hi);
 }
 
 static void equilibrium(const GroupDev &g, double &u0, double &v0) {
@@ -66,6 +94,50 @@ static void equilibrium(const GroupDev &g, double &u0, double &v0) {
         u0 = 0.0;
         v0 = 0.0;
     }
+}
+
+// every group of a handle: the 2-D groups INIT_MAX at a time in one launch,
+// each RD-ODE group in its own
+rd_status launch_init_all(const GroupDev *groups, int n_groups, float *fields, cudaStream_t s) {
+    InitBatch b;
+    int cnt = 0;
+    int64_t most = 0;
+    auto flush = [&]() -> rd_status {
+        if (cnt == 0) return RD_OK;
+        const int block = 256;
+        int64_t gx = (most + block - 1) / block;
+        if (gx > 148 * 4) gx = 148 * 4;
+        init_batch_kernel<<<dim3((unsigned)gx, (unsigned)cnt), block, 0, s>>>(fields, b);
+        note_launch();
+        cnt = 0;
+        most = 0;
+        return cuda_status(cudaGetLastError());
+    };
+    for (int i = 0; i < n_groups; ++i) {
+        const GroupDev &g = groups[i];
+        if (g.model == RD_RDODE) {
+            rd_status st = launch_rdode_init(g, fields, s);
+            if (st) return st;
+            continue;
+        }
+        double u0, v0;
+        equilibrium(g, u0, v0);
+        InitItem &it = b.item[cnt++];
+        it.offset = g.field_offset;
+        it.cells = (int64_t)g.G * g.G;
+        it.n = (int64_t)g.n_real * 2 * it.cells;
+        it.seed = g.seed;
+        it.u0 = u0;
+        it.v0 = v0;
+        it.lo = g.noise_lo;
+        it.hi = g.noise_hi;
+        most = std::max(most, it.n);
+        if (cnt == INIT_MAX) {
+            rd_status st = flush();
+            if (st) return st;
+        }
+    }
+    return flush();
 }
 
 rd_status launch_init_fields(const GroupDev &g, float *fields, cudaStream_t s) {
