@@ -135,7 +135,7 @@ struct CilWork {
     __nv_bfloat16 *lo;      // [(n1+n2)][dp]
     double *N, *H, *L, *E;  // [(n1+n2)]
     float *Hf, *Lf, *Ef;    // [(n1+n2)] the same bounds as FP32, rounded up
-    float *Ppart;           // [S][hi, lo][n1][n2] compensated segment sums
+    float *Ppart;           // [S][n1][n2] segment sums (FP32 running sums of the chunks)
     float *lo32, *hi32;     // [n1*n2] tier-1 interval of d2 (rounded outwards)
     double *lo2, *hi2;      // [n1*n2] tier-2 interval (valid where flag >= 1)
     double *ex;             // [n1*n2] exact d2 (valid where flag == 2)
@@ -201,7 +201,7 @@ static CilWork layout(int64_t n1, int64_t n2, int64_t d, void *base) {
     w.Lf = (float *)take(sizeof(float) * n);
     w.Ef = (float *)take(sizeof(float) * n);
     const int64_t np = n1 * n2;
-    w.Ppart = (float *)take(sizeof(float) * S * 2 * np);
+    w.Ppart = (float *)take(sizeof(float) * S * np);
     w.lo32 = (float *)take(sizeof(float) * np);
     w.hi32 = (float *)take(sizeof(float) * np);
     w.lo2 = (double *)take(sizeof(double) * np);
@@ -360,7 +360,7 @@ __global__ void pack_kernel(const float *__restrict__ X1, int64_t ld1, int64_t n
 }
 
 // ---------------------------------------------------------------------------
-// 2. Gram product: tensor cores (gram_tc.cu), K segments of compensated chunks.
+// 2. Gram product: tensor cores (gram_tc.cu), K segments of summed chunks.
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
@@ -383,12 +383,9 @@ __global__ void d2_bound_kernel(CilWork w, float gam, int cross) {
     if (q < np) {
         const int64_t i = q / w.n2, j = q - i * w.n2;
         const int64_t a = i, bb = w.n1 + j;
-        // segment sums (hi, lo) of this pair, in segment order
+        // segment sums of this pair, added with compensation in segment order
         float ph = 0.f, pl = 0.f;
-        for (int64_t sg = 0; sg < w.S; ++sg) {
-            two_sum_acc(ph, pl, w.Ppart[(2 * sg) * np + q]);
-            pl += w.Ppart[(2 * sg + 1) * np + q];
-        }
+        for (int64_t sg = 0; sg < w.S; ++sg) two_sum_acc(ph, pl, w.Ppart[sg * np + q]);
         const double P = (double)ph + (double)pl;
         const double Ni = w.N[a], Nj = w.N[bb];
         const double A = (Ni + Nj) - 2.0 * P;
@@ -852,16 +849,20 @@ extern "C" rd_status cil_workspace_size(int64_t n1, int64_t n2, int64_t d, size_
 }
 
 // Tensor-core accumulation model (tier 1): per chunk of cs K steps,
-// 3*64*cs/16 instructions add into the FP32 accumulator; each adds 16 exact
-// bf16 products and the accumulator with at most 17 roundings of 2^-23
-// relative to the magnitudes involved.  The chunk partials are summed with
-// TwoSum into an FP32 hi/lo pair, in the kernel within a segment and then
-// across segments: for n terms that errs by at most about (n u)^2 of their
-// magnitudes (u = 2^-24), taken here as (nchunk + S + 4)^2 2^-47.
+// np * 64 * cs / 16 instructions add into the FP32 accumulator; each adds 16
+// exact bf16 products and the accumulator with at most 17 roundings of
+// 2^-23 relative to the magnitudes involved.  Within a segment the kernel
+// adds its m = nchunk / S chunk partials into a plain FP32 running sum: m - 1
+// roundings of at most 2^-24 of the running magnitude, bounded by
+// m 2^-24 (1.01) of the magnitudes (the partials' own accumulation errors
+// are far below the 1 %).  The S segment sums are then added with TwoSum
+// into an FP32 hi/lo pair: for n terms that errs by at most about (n u)^2
+// of their magnitudes (u = 2^-24), taken here as (S + 4)^2 2^-47.
 static float gram_gamma(const CilWork &w) {
-    const double n = (double)(w.nchunk + w.S + 4);
+    const double m = (double)(w.nchunk / w.S);
+    const double n = (double)(w.S + 4);
     const double g = ((double)w.np_ * 64.0 * (double)w.cs / 16.0 + 1.0) * 17.0 * 1.1920928955078125e-7 +
-                     n * n * 7.105427357601002e-15;
+                     m * 5.9604644775390625e-8 * 1.01 + n * n * 7.105427357601002e-15;
     return (float)(g * (1.0 + 1e-6));
 }
 
