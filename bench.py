@@ -64,11 +64,11 @@ RESIDENT_KERNEL = {0: "rd_resident_scalar_kernel", 1: "rd_resident_kernel", 2: "
 STEPPER_TRAFFIC = {
     "c2": {"6f89ac52bd0c99eb": 4223232, "a1b8429f6f299483": 4223488, "7c8c62601c860730": 4223488,
            "60c7c52369dee980": 4297216, "bf9071c73da591c1": 4297216, "730afce9ca60e453": 4314112,
-           "3af7521f7d8ea050": 4278016},
-    "c2:v3": {"730afce9ca60e453": 4223488, "3af7521f7d8ea050": 4301312},
+           "3af7521f7d8ea050": 4278016, "4a973e1119f01943": 4244480},
+    "c2:v3": {"730afce9ca60e453": 4223488, "3af7521f7d8ea050": 4301312, "4a973e1119f01943": 4239872},
     "c4": {"250da058b95b29c7": 1285591296, "02a4865c70d95aa1": 1284856064, "60c7c52369dee980": 1290298112,
            "bf9071c73da591c1": 1290150912, "730afce9ca60e453": 1291938816,
-           "3af7521f7d8ea050": 1289928192},
+           "3af7521f7d8ea050": 1289928192, "4a973e1119f01943": 1290087168},
 }
 STEPPER_SOURCES = ["paper_2203_14742_b300/csrc/stepper.cu", "paper_2203_14742_b300/csrc/tile.cuh",
                    "paper_2203_14742_b300/csrc/common.cuh"]

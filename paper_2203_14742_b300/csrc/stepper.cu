@@ -8,6 +8,7 @@
 //
 // Kernels
 //   init_fields_kernel        counter-based noise, FP64 then one rounding to FP32
+//   init_batch_kernel         the same for every 2-D group of a handle in one launch
 //   rd_resident_*_kernel      one realisation per CTA, the whole field held in
 //                             registers as TYxTX tiles per thread for the whole
 //                             run; north/south tile edges exchanged through a

@@ -70,6 +70,41 @@ def test_initial_state_multi_group_offsets(p):
         assert np.array_equal(sim.group_fields(i).cpu().numpy(), ref)
 
 
+def test_initial_state_many_groups_and_new_seeds(p):
+    """More groups than one initial-state launch takes (120), every model,
+    an RD-ODE group among them; then new seeds for some groups and a
+    re-initialisation: every group's state equals the oracle's for the seed
+    it holds at that moment."""
+    models = [(W.FHN, (2.8e-4, 0.05, 10.0, 0.95), (-0.05, 0.05)),
+              (W.GM, (2.5e-4, 0.01, 1.0, 0.52), (0.0, 0.01)),
+              (W.BZ, W.BZ_THETA0, (0.0, 0.01)),
+              (W.DIFF, (3e-3, 1e-3), (-1.0, 1.0))]
+    gs = []
+    for i in range(125):
+        model, par, noise = models[i % 4]
+        gs.append(mkgroup(p, model, 32 if i % 3 else 64, 1 + i % 2, par, 2 ** -10, 0, noise, 1000 + 7 * i))
+    gs.insert(61, p.Group(W.RDODE, 64, 2, W.RDODE_THETA0, 1e-3, 0, (0.0, 2.0), 555))
+
+    def check(sim, seeds):
+        for i, g in enumerate(gs):
+            got = sim.group_fields(i).cpu().numpy()
+            if g.model == W.RDODE:
+                ref = oracle.rdode_init(g.G, g.n_real, g.noise[0], g.noise[1], seeds[i], 10)
+            else:
+                ref = oracle.init_fields(g.model, g.G, g.n_real, g.params, g.noise[0], g.noise[1], seeds[i])
+            assert np.array_equal(got, ref), i
+
+    sim = p.Simulation(gs)
+    seeds = [g.seed for g in gs]
+    check(sim, seeds)
+    for i in (0, 61, 119, 120, 125):
+        seeds[i] = seeds[i] + 99991
+        assert p.lib().rd_set_seed(sim.handle, i, seeds[i]) == 0
+    sim.reinit()
+    torch.cuda.synchronize()
+    check(sim, seeds)
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_f64_path_bit_exact(p, case):
     model, G, n, par, dt, noise = case
