@@ -666,21 +666,24 @@ __global__ void __launch_bounds__(256) exact_split_kernel(CilWork w, const float
         const int64_t q = (int64_t)(ent & Q_IDX);
         const int64_t i = q / w.n2, j = q - i * w.n2;
         const int64_t t0 = sg * EXS_SEG, len = min((int64_t)EXS_SEG, w.d - t0);
-        long long S[XD];
-        const bool good = xd_block_digits<256>(X1 + i * ld1 + t0, X2 + j * ld2 + t0, len, sh, S);
+        const bool good = xd_block_digits<256>(X1 + i * ld1 + t0, X2 + j * ld2 + t0, len, sh);
+        long long *acc = w.xacc + slot * XD;
+        // thread k adds digit k; each fences its addition before the
+        // arrival is counted
+        if (threadIdx.x < XD) {
+            atomicAdd((unsigned long long *)(acc + threadIdx.x), (unsigned long long)sh.tot[threadIdx.x]);
+            __threadfence();
+        }
+        __syncthreads();   // sh.tot read; the block may reuse it
         if (threadIdx.x == 0) {
-            long long *acc = w.xacc + slot * XD;
-#pragma unroll 1
-            for (int k = 0; k < XD; ++k) atomicAdd((unsigned long long *)(acc + k), (unsigned long long)S[k]);
             if (!good) atomicOr(&w.xarr[EXS_CAP + slot], 1u);
             __threadfence();
             if (atomicAdd(&w.xarr[slot], 1u) == (unsigned)(nseg - 1)) {
                 __threadfence();
                 long long T[XD];
-                const volatile long long *va = acc;
-#pragma unroll 1
-                for (int k = 0; k < XD; ++k) T[k] = va[k];
-                const bool bad = *(volatile unsigned *)&w.xarr[EXS_CAP + slot] != 0u;
+#pragma unroll
+                for (int k = 0; k < XD; ++k) T[k] = (long long)__ldcg((const unsigned long long *)(acc + k));
+                const bool bad = __ldcg(&w.xarr[EXS_CAP + slot]) != 0u;
                 const double v = bad ? __longlong_as_double(0x7ff8000000000000ll) : xd_round(T);
                 w.ex[q] = v;
                 w.flag[q] = 2;

@@ -100,25 +100,55 @@ __device__ inline double xd_round(const long long *S) {
     return __longlong_as_double((long long)bits);
 }
 
-// Shared memory of xd_block: XD digits per thread plus XD per warp.
+// Shared memory of xd_block: XD digits per thread, XD per warp and the
+// block's XD totals.
 template <int NT>
 struct XdShared {
     long long acc[XD * NT];
     long long wsum[XD * (NT / 32)];
+    long long tot[XD];
     double wmax[NT / 32];
     int bad;
 };
 
-// The digit sums S[0..XD-1] of x[0..d) and y[0..d) (every thread of the
-// block calls it; S and the return value valid in thread 0): the exact
-// integer N of the segment's terms, sum S[k] 2^(32 k), unnormalised, so the
-// sums of several segments add digit by digit in any order (each stays
-// below 3 d_total 2^32 < 2^63 for d_total < 2^28).  Returns false when an
-// element is not finite.
+// The block's digit totals into sh.tot (every thread calls it after adding
+// its terms into sh.acc; sh.tot valid in every thread on return).  The XD
+// warp reductions are unrolled so their shuffle chains overlap, and thread
+// k < XD adds digit k over the warps: integer sums, so no order matters.
+template <int NT>
+__device__ __forceinline__ void xd_reduce(XdShared<NT> &sh) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    long long v[XD];
+#pragma unroll
+    for (int k = 0; k < XD; ++k) v[k] = sh.acc[k * NT + tid];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < XD; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < XD; ++k) sh.wsum[k * (NT / 32) + warp] = v[k];
+    __syncthreads();
+    if (tid < XD) {
+        long long t = 0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) t += sh.wsum[tid * (NT / 32) + w];
+        sh.tot[tid] = t;
+    }
+    __syncthreads();
+}
+
+// The digit sums of x[0..d) and y[0..d) (every thread of the block calls
+// it): on return sh.tot[0..XD-1] holds the exact integer N of the
+// segment's terms, sum tot[k] 2^(32 k), unnormalised, so the sums of
+// several segments add digit by digit in any order (each stays below
+// 3 d_total 2^32 < 2^63 for d_total < 2^28).  Returns false (in every
+// thread) when an element is not finite.  The caller synchronises the
+// block after reading sh.tot and before its next call.
 template <int NT>
 __device__ bool xd_block_digits(const float *__restrict__ x, const float *__restrict__ y, int64_t d,
-                                XdShared<NT> &sh, long long *S) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+                                XdShared<NT> &sh) {
+    const int tid = threadIdx.x;
     long long *a = sh.acc + tid;
 #pragma unroll
     for (int k = 0; k < XD; ++k) a[k * NT] = 0ll;
@@ -127,26 +157,8 @@ __device__ bool xd_block_digits(const float *__restrict__ x, const float *__rest
     for (int64_t t = tid; t < d; t += NT) ok &= xd_term(a, NT, __ldg(x + t), __ldg(y + t));
     __syncthreads();   // sh.bad cleared before any thread sets it
     if (!ok) sh.bad = 1;
-#pragma unroll 1
-    for (int k = 0; k < XD; ++k) {
-        long long v = a[k * NT];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh.wsum[k * (NT / 32) + warp] = v;
-    }
-    __syncthreads();
-    bool good = true;
-    if (tid == 0) {
-#pragma unroll 1
-        for (int k = 0; k < XD; ++k) {
-            long long s = 0;
-            for (int w = 0; w < NT / 32; ++w) s += sh.wsum[k * (NT / 32) + w];
-            S[k] = s;
-        }
-        good = !sh.bad;
-    }
-    __syncthreads();   // the shared arrays may be reused by the next call
-    return good;
+    xd_reduce<NT>(sh);
+    return sh.bad == 0;
 }
 
 // d2 of x[0..d) and y[0..d) by a whole block of NT threads (every thread
@@ -170,28 +182,17 @@ __device__ double xd_block(const float *__restrict__ x, const float *__restrict_
     }
     __syncthreads();   // sh.bad cleared before any thread sets it
     if (!ok) sh.bad = 1;
-#pragma unroll 1
-    for (int k = 0; k < XD; ++k) {
-        long long v = a[k * NT];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh.wsum[k * (NT / 32) + warp] = v;
-    }
     if (MAX) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) sh.wmax[warp] = mx;
     }
-    __syncthreads();
+    xd_reduce<NT>(sh);
     double r = 0.0;
     if (tid == 0) {
         long long S[XD];
-#pragma unroll 1
-        for (int k = 0; k < XD; ++k) {
-            long long s = 0;
-            for (int w = 0; w < NT / 32; ++w) s += sh.wsum[k * (NT / 32) + w];
-            S[k] = s;
-        }
+#pragma unroll
+        for (int k = 0; k < XD; ++k) S[k] = sh.tot[k];
         r = sh.bad ? __longlong_as_double(0x7ff8000000000000ll) : xd_round(S);
         if (MAX) {
             double m = 0.0;
