@@ -164,6 +164,27 @@ def test_tensor_core_bound_holds_with_slack(p, n1, n2, d, off):
     assert np.all(m <= 1e-3 * ex + 1e-9)
 
 
+def test_tensor_core_bound_at_paper_scale(p):
+    """The tier-1 bound at the SCIL scale, 2 x 1024 patterns of d = 32768,
+    where every K segment adds 64 chunk partials in an FP32 running sum:
+    each pair's approximation error stays below a quarter of its bound.  The
+    reference is a float64 Gram on the host, within (d + 2) 2^-53 (|x|^2 +
+    |y|^2 + 2 |x| |y|) of every d2, far below the bound."""
+    n = 1024
+    X = W.cosine_patterns(2 * n, 128, 2, 78, amp=0.8, offset=2.0)
+    X1, X2 = X[:n], X[n:]
+    A, m = p.cil_approx(torch.from_numpy(X1).cuda(), torch.from_numpy(X2).cuda())
+    A, m = A.cpu().numpy(), m.cpu().numpy()
+    A1, A2 = X1.astype(np.float64), X2.astype(np.float64)
+    n1s, n2s = (A1 * A1).sum(1), (A2 * A2).sum(1)
+    D = n1s[:, None] + n2s[None, :] - 2.0 * (A1 @ A2.T)
+    d = X.shape[1]
+    eD = (d + 2) * 2.0 ** -53 * (n1s[:, None] + n2s[None, :] + 2.0 * np.sqrt(n1s[:, None] * n2s[None, :]))
+    err = np.abs(A - D)
+    assert np.all(err <= 0.25 * m + 2.0 * eD), (err / m).max()
+    assert np.all(m <= 1e-3 * D + 1e-9)
+
+
 def wide_floats(rng, n):
     """FP32 values over the whole exponent range: normals, subnormals,
     zeros, both signs."""
