@@ -627,24 +627,26 @@ __global__ void __launch_bounds__(256) tier2_kernel(CilWork w, const float *__re
 //     tier-2 interval meets a threshold range go to tier 3.
 __global__ void classify2_kernel(CilWork w, int M) {
     __shared__ double tlo[32], thi[32];
+    const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[SC_Q1];
+    if ((unsigned long long)blockIdx.x * blockDim.x >= qlen) return;   // whole block past the queue
     if ((int)threadIdx.x < M) {
         tlo[threadIdx.x] = w.t2lo[threadIdx.x];
         thi[threadIdx.x] = w.t2hi[threadIdx.x];
     }
     __syncthreads();
-    const unsigned long long qlen = *(volatile unsigned long long *)&w.scal[SC_Q1];
-    const unsigned long long qi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (qi >= qlen) return;
-    const unsigned long long ent = w.q1[qi];
-    const int64_t q = (int64_t)(ent & Q_IDX);
-    const double lo = w.lo2[q], hi = w.hi2[q];
-    const bool maxc = (ent & Q_MAX) && hi >= __longlong_as_double((long long)w.scal[SC_LB2]);
-    const bool minc = (ent & Q_MIN) && lo <= read_min_d(w.scal[SC_UBM2]);
-    bool amb = false;
-    for (int k = 0; k < M && !amb; ++k) amb = !(hi < tlo[k] || lo >= thi[k]);
-    if (!(maxc || minc || amb)) return;
-    unsigned long long slot = atomicAdd(&w.scal[SC_Q2], 1ull);
-    w.q2[slot] = (unsigned long long)q | (maxc ? Q_MAX : 0ull) | (minc ? Q_MIN : 0ull);
+    for (unsigned long long qi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; qi < qlen;
+         qi += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long ent = w.q1[qi];
+        const int64_t q = (int64_t)(ent & Q_IDX);
+        const double lo = w.lo2[q], hi = w.hi2[q];
+        const bool maxc = (ent & Q_MAX) && hi >= __longlong_as_double((long long)w.scal[SC_LB2]);
+        const bool minc = (ent & Q_MIN) && lo <= read_min_d(w.scal[SC_UBM2]);
+        bool amb = false;
+        for (int k = 0; k < M && !amb; ++k) amb = !(hi < tlo[k] || lo >= thi[k]);
+        if (!(maxc || minc || amb)) continue;
+        unsigned long long slot = atomicAdd(&w.scal[SC_Q2], 1ull);
+        w.q2[slot] = (unsigned long long)q | (maxc ? Q_MAX : 0ull) | (minc ? Q_MIN : 0ull);
+    }
 }
 
 // 5. tier 3: the exact value (exact.cuh) of every queued pair.
@@ -952,7 +954,8 @@ static rd_status cil_run(const float *X1, int64_t ld1, int64_t n1, const float *
         note_launch();
         ranges_kernel<<<1, 32, 0, s>>>(w, radii_in, beta, M, 2, law);
         note_launch();
-        classify2_kernel<<<gp, 256, 0, s>>>(w, M);
+        // the queue is short: blocks past it exit before loading anything
+        classify2_kernel<<<(gp < 8 * N_SM ? gp : 8 * N_SM), 256, 0, s>>>(w, M);
         note_launch();
     }
     {
